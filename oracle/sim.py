@@ -1,0 +1,184 @@
+"""Subspace iteration (Alg. 1) and the hierarchical driver (Alg. 3).
+
+Oracle; test infrastructure only.  Plain FP64 NumPy/SciPy: a pivoting sparse
+LU (SuperLU) stands in for the paper's symmetric indefinite LDL^T of the
+shifted matrix (it factors the same matrix, so the solves agree up to
+rounding), ``scipy.linalg.eigh`` is the dense generalised eigensolver.
+
+Steps and readings (each listed in the design notes):
+
+* SIM (Alg. 1): factor K = S - mu M once; repeat { Psi = K^-1 M Phi applied
+  twice (Sec. 4.2, two inverse iterations before orthonormalising); scale each
+  column of Psi to unit M-norm (does not change the span); S_bar = Psi^T S Psi,
+  M_bar = Psi^T M Psi; solve S_bar Phi_bar = M_bar Phi_bar Lambda_bar;
+  Phi = Psi Phi_bar } until the convergence test holds for i < p.
+* Convergence test (eq. conv2): ||S Phi_i - lambda_i M Phi_i|| / den_i < eps
+  with the M^{-1}-norm on the finest level (M diagonal) and the Euclidean
+  norm on coarser levels (Sec. 5, termination criterion).  den_i =
+  max(||S Phi_i||, lambda_ref ||M Phi_i||) where lambda_ref is the first Ritz
+  value above 1e-8 * Lambda_{q-1}: the plain denominator vanishes for the
+  constant eigenvector of a closed surface.
+* Locking (Sec. 4.2): the leading run of pairs whose residual is below
+  eps/10 (at most p of them) gets no further inverse iterations; those
+  columns stay in the Rayleigh-Ritz basis unchanged.
+* Shift (Alg. 3): mu = Lambda^{tau+1}_j with j = floor(alpha p), 0-based into
+  the ascending Ritz values of the coarser level; if j == 0 the shift is
+  -1e-8 * Lambda_{q-1} instead (mu = lambda_0 = 0 would make K singular).
+* At most ``max_iters`` (100) iterations per level, else NoConvergence.
+* Output: the p lowest pairs, ascending; each eigenvector's entry of largest
+  magnitude is made positive.
+
+Parity unpinned: iteration counts (only the paper's qualitative patterns
+apply) and eigenvectors inside a cluster that straddles index p.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from .assembly import lumped_mass, stiffness
+from .galerkin import level_matrices
+from .hierarchy import build_hierarchy, subspace_size
+
+
+class NoConvergence(RuntimeError):
+    pass
+
+
+def residuals(S, M, Phi, lam, m_inverse_diag=None):
+    """Relative residuals of eq. conv2 for every column of Phi."""
+    SP = S @ Phi
+    MP = M @ Phi
+    R = SP - MP * lam[None, :]
+    if m_inverse_diag is not None:
+        nr = np.sqrt(np.sum(R * R * m_inverse_diag[:, None], axis=0))
+        ns = np.sqrt(np.sum(SP * SP * m_inverse_diag[:, None], axis=0))
+        nm = np.sqrt(np.sum(MP * MP * m_inverse_diag[:, None], axis=0))
+    else:
+        nr = np.linalg.norm(R, axis=0)
+        ns = np.linalg.norm(SP, axis=0)
+        nm = np.linalg.norm(MP, axis=0)
+    top = lam[-1]
+    above = lam[lam > 1e-8 * top]
+    lam_ref = above[0] if len(above) else top
+    den = np.maximum(ns, lam_ref * nm)
+    return nr / den
+
+
+@dataclass
+class SimResult:
+    lam: np.ndarray
+    Phi: np.ndarray
+    iters: int
+    res: np.ndarray
+    history: list = field(default_factory=list)
+
+
+def sim(S, M, Phi, p, eps, mu, finest: bool, max_iters=100, inv_iters=2, lock_factor=0.1):
+    """Alg. 1 with the HSIM refinements of Sec. 4.2."""
+    S = S.tocsr()
+    M = M.tocsr()
+    K = (S - mu * M).tocsc()
+    lu = spla.splu(K)
+    minv = 1.0 / M.diagonal() if finest else None
+    Phi = np.array(Phi, dtype=np.float64, copy=True)
+    locked = 0
+    history = []
+    for it in range(1, max_iters + 1):
+        Psi = Phi.copy()
+        for _ in range(inv_iters):
+            Psi[:, locked:] = lu.solve(np.asarray(M @ Psi[:, locked:]))
+        Psi /= np.sqrt(np.einsum("ij,ij->j", Psi, M @ Psi))[None, :]
+        Sbar = Psi.T @ (S @ Psi)
+        Mbar = Psi.T @ (M @ Psi)
+        lam, Phibar = sla.eigh(Sbar, Mbar)
+        Phi = Psi @ Phibar
+        res = residuals(S, M, Phi, lam, minv)
+        history.append(float(res[:p].max()))
+        if np.all(res[:p] < eps):
+            return SimResult(lam, Phi, it, res, history)
+        r = 0
+        while r < p and res[r] < lock_factor * eps:
+            r += 1
+        locked = r
+    raise NoConvergence(f"SIM did not converge in {max_iters} iterations "
+                        f"(max residual {history[-1]:.3e})")
+
+
+def shift(lam_coarse, p, alpha=0.1):
+    j = int(math.floor(alpha * p))
+    if j == 0:
+        return -1e-8 * lam_coarse[-1]
+    return float(lam_coarse[j])
+
+
+def normalise_signs(Phi):
+    idx = np.argmax(np.abs(Phi), axis=0)
+    s = np.sign(Phi[idx, np.arange(Phi.shape[1])])
+    s[s == 0] = 1.0
+    return Phi * s[None, :]
+
+
+@dataclass
+class HsimResult:
+    lam: np.ndarray
+    Phi: np.ndarray
+    iters: list
+    shifts: list
+    coarse_lam: list
+    hierarchy: object
+    S: list
+    M: list
+
+
+def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
+                  inv_iters=2, lock_factor=0.1):
+    """Alg. 3 after the hierarchy is built: coarse dense solve, then SIM on
+    every finer level starting from the prolonged basis."""
+    T = len(S_levels)
+    q = subspace_size(p)
+    Sc = S_levels[-1].toarray()
+    Mc = M_levels[-1].toarray()
+    lam, Phi = sla.eigh(Sc, Mc, subset_by_index=[0, q - 1])
+    coarse = [lam.copy()]
+    iters, shifts = [], []
+    for tau in range(T - 2, -1, -1):
+        Phi = U_list[tau] @ Phi
+        mu = shift(lam, p, alpha)
+        r = sim(S_levels[tau], M_levels[tau], Phi, p, eps, mu, finest=(tau == 0),
+                max_iters=max_iters, inv_iters=inv_iters, lock_factor=lock_factor)
+        lam, Phi = r.lam, r.Phi
+        iters.append(r.iters)
+        shifts.append(mu)
+        coarse.append(lam.copy())
+    return lam, Phi, iters, shifts, coarse
+
+
+def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100):
+    """Full HSIM (Alg. 3) on a mesh: p lowest eigenpairs of S Phi = lambda M Phi."""
+    S0 = stiffness(mesh)
+    M0 = lumped_mass(mesh)
+    H = build_hierarchy(mesh, p, levels, start_vertex, sigma)
+    S, M = level_matrices(S0, M0, H.U)
+    if len(S) == 1:
+        q = subspace_size(p)
+        lam, Phi = sla.eigh(S0.toarray(), np.diag(M0), subset_by_index=[0, q - 1])
+        iters, shifts, coarse = [], [], [lam]
+    else:
+        lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, H.U, p, eps, alpha, max_iters)
+    return HsimResult(lam[:p], normalise_signs(Phi[:, :p]), iters, shifts, coarse, H, S, M)
+
+
+def dense_reference(S, M_diag_or_matrix, count):
+    """Plain definition: the lowest ``count`` pairs of the dense generalised
+    problem (eq. eigenProb), for meshes of at most a few thousand vertices."""
+    A = S.toarray() if sp.issparse(S) else np.asarray(S)
+    Mm = M_diag_or_matrix
+    B = np.diag(Mm) if np.ndim(Mm) == 1 else (Mm.toarray() if sp.issparse(Mm) else Mm)
+    lam, Phi = sla.eigh(A, B, subset_by_index=[0, count - 1])
+    return lam, normalise_signs(Phi)

@@ -1,0 +1,11 @@
+"""Seeded synthetic inputs shared by the CPU oracle, the tests and the benchmark.
+
+Nothing here computes any part of the eigensolver; see ``synth.workloads`` for
+the named workloads (mesh family, sizes, p, levels, tolerance).
+"""
+from .meshes import (Mesh, bumpy_torus, displaced_icosphere, flat_torus,
+                     grid_torus_faces, icosphere)
+from .workloads import WORKLOADS, Workload, make_workload
+
+__all__ = ["Mesh", "bumpy_torus", "displaced_icosphere", "flat_torus",
+           "grid_torus_faces", "icosphere", "WORKLOADS", "Workload", "make_workload"]

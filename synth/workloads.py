@@ -1,0 +1,60 @@
+"""Named synthetic workloads: mesh family and size, p, levels, tolerance.
+
+Each workload also fixes the start vertex of farthest-point sampling (the one
+random draw of the hierarchy construction, Alg. 2), drawn here from the
+workload's seed so that every consumer receives it as an input.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import meshes
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    family: str
+    params: tuple
+    p: int
+    levels: int
+    tol: float
+    seed: int
+
+    def mesh(self) -> meshes.Mesh:
+        fam = getattr(meshes, self.family)
+        return fam(*self.params)
+
+    def start_vertex(self, n: int) -> int:
+        return int(np.random.default_rng(1000 + self.seed).integers(0, n))
+
+
+WORKLOADS = {
+    # periodic 64 x 64 right-triangulated flat torus, closed-form spectrum
+    "flat_torus_64": Workload("flat_torus_64", "flat_torus", (64,), p=20, levels=3,
+                              tol=1e-10, seed=1),
+    # icosphere subdivision 7 (163,842 vertices), 16-harmonic radial noise
+    "icosphere7_noise": Workload("icosphere7_noise", "displaced_icosphere", (7, 2), p=200,
+                                 levels=2, tol=1e-10, seed=2),
+    # bumpy torus R=1, r=0.3 on a 1000 x 1000 grid (10^6 vertices)
+    "bumpy_torus_1000": Workload("bumpy_torus_1000", "bumpy_torus", (1000, 1000, 3), p=500,
+                                 levels=3, tol=1e-5, seed=3),
+    # icosphere subdivision 6 (40,962 vertices), noise seed 5: spectral loss source
+    "icosphere6_grad": Workload("icosphere6_grad", "displaced_icosphere", (6, 5), p=50,
+                                levels=2, tol=1e-10, seed=5),
+    # small cases used by tests
+    "icosphere3_noise": Workload("icosphere3_noise", "displaced_icosphere", (3, 7), p=20,
+                                 levels=2, tol=1e-10, seed=7),
+    "bumpy_torus_64": Workload("bumpy_torus_64", "bumpy_torus", (64, 48, 11), p=40,
+                               levels=3, tol=1e-10, seed=11),
+}
+
+
+def make_workload(name: str):
+    """Return (workload, mesh, start_vertex)."""
+    w = WORKLOADS[name]
+    m = w.mesh()
+    return w, m, w.start_vertex(m.n)
+

@@ -1,0 +1,159 @@
+"""Pins for the oracle's subspace iteration and hierarchical driver (Alg. 1,
+Alg. 3): closed-form spectrum of the flat torus, dense brute force, the
+invariants of the generalised problem, Courant-Fischer across levels, the
+sphere's l(l+1) pattern and the scaling law."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import synth
+from oracle import assembly, galerkin, hierarchy, sim
+
+
+def flat_torus_spectrum(N, count):
+    h = 1.0 / N
+    s = np.sin(np.pi * np.arange(N) / N) ** 2
+    return np.sort(((4.0 / h**2) * (s[:, None] + s[None, :])).ravel())[:count]
+
+
+def flat_torus_eigenspace(N, lam_value, rtol=1e-9):
+    """Real Fourier modes cos/sin(2 pi (k i + l j)/N) with that eigenvalue."""
+    h = 1.0 / N
+    i, j = np.meshgrid(np.arange(N), np.arange(N), indexing="xy")
+    i, j = i.ravel(), j.ravel()
+    cols = []
+    for k in range(N):
+        for l in range(N):
+            lam = (4.0 / h**2) * (np.sin(np.pi * k / N) ** 2 + np.sin(np.pi * l / N) ** 2)
+            if abs(lam - lam_value) <= rtol * max(lam_value, 1.0):
+                ph = 2 * np.pi * (k * i + l * j) / N
+                cols += [np.cos(ph), np.sin(ph)]
+    B = np.array(cols).T
+    U, s, _ = np.linalg.svd(B, full_matrices=False)
+    return U[:, s > 1e-8 * s[0]]
+
+
+def principal_angle_sin(Q1, Q2):
+    """Largest sine of the principal angles between two orthonormal bases of
+    equal dimension: the 2-norm of the part of Q2 outside span(Q1)."""
+    R = Q2 - Q1 @ (Q1.T @ Q2)
+    return float(np.linalg.norm(R, 2))
+
+
+@pytest.fixture(scope="module")
+def torus64():
+    w, m, s = synth.make_workload("flat_torus_64")
+    return w, m, sim.hsim(m, w.p, w.levels, w.tol, s)
+
+
+def test_flat_torus_closed_form_eigenvalues(torus64):
+    w, m, r = torus64
+    exact = flat_torus_spectrum(64, w.p)
+    assert abs(r.lam[0]) < 1e-10
+    np.testing.assert_allclose(r.lam[1:], exact[1:], rtol=1e-12)
+
+
+def test_flat_torus_eigenvectors_per_cluster(torus64):
+    """Clusters of size 1, 4, 4, 4 lie below index 13; the 8-fold cluster at
+    indices 13..20 is cut by p = 20, so only the first 13 vectors are pinned."""
+    w, m, r = torus64
+    h = 1.0 / 64
+    Phi = r.Phi * h                      # M = h^2 I: M-orthonormal -> orthonormal
+    for lo, hi in ((0, 1), (1, 5), (5, 9), (9, 13)):
+        Q = flat_torus_eigenspace(64, r.lam[lo])
+        assert Q.shape[1] == hi - lo
+        assert principal_angle_sin(Q, Phi[:, lo:hi]) < 1e-8
+
+
+def test_invariants_of_result(torus64):
+    w, m, r = torus64
+    S = assembly.stiffness(m)
+    M = assembly.lumped_mass(m)
+    G = r.Phi.T @ (M[:, None] * r.Phi)
+    np.testing.assert_allclose(G, np.eye(w.p), atol=1e-10)
+    np.testing.assert_allclose(r.Phi.T @ (S @ r.Phi), np.diag(r.lam), atol=1e-8 * r.lam[-1])
+    res = sim.residuals(S, sp.diags(M), r.Phi, r.lam, 1.0 / M)
+    assert res.max() < w.tol
+    # constant eigenvector on a closed surface
+    c = r.Phi[:, 0] / r.Phi[0, 0]
+    np.testing.assert_allclose(c, 1.0, atol=1e-9)
+
+
+def test_courant_fischer_across_levels(torus64):
+    w, m, r = torus64
+    fine = r.lam
+    for lam_level in r.coarse_lam[:-1]:
+        assert np.all(lam_level[: w.p] >= fine - 1e-9 * np.maximum(fine, 1.0))
+
+
+def test_dense_brute_force_two_levels():
+    mesh = synth.bumpy_torus(40, 44, 21)
+    S = assembly.stiffness(mesh)
+    M = assembly.lumped_mass(mesh)
+    p = 30
+    r = sim.hsim(mesh, p, 2, 1e-10, 5)
+    assert r.hierarchy.sizes == [1760, 1000]
+    lam_ref, Phi_ref = sim.dense_reference(S, M, p + 10)
+    np.testing.assert_allclose(r.lam, lam_ref[:p], rtol=1e-10, atol=1e-10)
+    # subspace per cluster (no degeneracy on this jittered mesh: clusters of one)
+    gaps = np.diff(lam_ref) / lam_ref[1:]
+    sqrtM = np.sqrt(M)[:, None]
+    for i in range(1, p):
+        if gaps[i - 1] > 1e-6 and gaps[i] > 1e-6:
+            a = r.Phi[:, i] * sqrtM[:, 0]
+            b = Phi_ref[:, i] * sqrtM[:, 0]
+            assert np.linalg.norm(a - np.sign(a @ b) * b) < 1e-7
+
+
+def test_sphere_multiplicity_pattern():
+    """Unit sphere: lambda -> l(l+1) with multiplicity 2l+1 (O(h^2) error)."""
+    mesh = synth.icosphere(4)
+    S = assembly.stiffness(mesh)
+    M = assembly.lumped_mass(mesh)
+    r = sim.hsim(mesh, 25, 2, 1e-8, 0)
+    k = 0
+    for l in range(5):
+        block = r.lam[k:k + 2 * l + 1]
+        target = l * (l + 1)
+        if l == 0:
+            assert abs(block[0]) < 1e-8
+        else:
+            assert np.all(np.abs(block - target) / target < 0.02)
+        k += 2 * l + 1
+
+
+def test_scaling_law():
+    mesh = synth.bumpy_torus(36, 40, 8)
+    big = synth.Mesh(V=2.0 * mesh.V, F=mesh.F)
+    a = sim.hsim(mesh, 20, 2, 1e-10, 3).lam
+    b = sim.hsim(big, 20, 2, 1e-10, 3).lam
+    np.testing.assert_allclose(b[1:], a[1:] / 4.0, rtol=1e-9)
+
+
+def test_shift_rule():
+    lam = np.arange(30, dtype=float)
+    assert sim.shift(lam, 20) == 2.0
+    assert sim.shift(lam, 25) == 2.0
+    assert sim.shift(lam, 100) == 10.0
+    assert sim.shift(lam, 5) == -1e-8 * 29.0
+
+
+def test_planted_swapped_ritz_matrices_is_caught(monkeypatch):
+    """Swapping S_bar and M_bar in the dense Ritz step must break the
+    brute-force pin (by wrong eigenvalues or by non-convergence)."""
+    mesh = synth.bumpy_torus(40, 44, 21)
+    S = assembly.stiffness(mesh)
+    M = assembly.lumped_mass(mesh)
+    lam_ref, _ = sim.dense_reference(S, M, 20)
+    real = sla.eigh
+
+    def swapped(A, B=None, **kw):
+        if B is not None and not kw:
+            return real(B, A)
+        return real(A, B, **kw)
+
+    monkeypatch.setattr(sim.sla, "eigh", swapped)
+    with pytest.raises((AssertionError, sim.NoConvergence, np.linalg.LinAlgError)):
+        r = sim.hsim(mesh, 20, 2, 1e-10, 5, max_iters=5)
+        np.testing.assert_allclose(r.lam, lam_ref, rtol=1e-8)
