@@ -81,8 +81,11 @@ def lumped_mass(mesh) -> np.ndarray:
 
 
 def total_area(mesh) -> float:
-    import math
-    return math.fsum(triangle_areas(squared_lengths(mesh)).tolist())
+    """Surface area A, the plain sum of the triangle areas in triangle order."""
+    total = 0.0
+    for a in triangle_areas(squared_lengths(mesh)).tolist():
+        total += a
+    return total
 
 
 def edge_graph(mesh):
