@@ -1,0 +1,226 @@
+/*
+ * hsim.h -- C ABI of the GB300 Hierarchical Subspace Iteration Method.
+ *
+ * Computes the p lowest eigenpairs of the generalised Laplace-Beltrami
+ * problem  S Phi = lambda M Phi  (eq. eigenProb, Sec. 3.1) on a triangle mesh
+ * with the Hierarchical Subspace Iteration Method (Alg. 3): a vertex
+ * hierarchy with nested function spaces (Sec. 4.1, Alg. 2), a dense solve on
+ * the coarsest level, then subspace iterations (Alg. 1) on every finer level
+ * started from the prolonged coarse eigenbasis.
+ *
+ * Conventions shared by every call
+ *   - Pointers named *_dev are CUDA device pointers on the device of the
+ *     context; pointers named *_host are host pointers.  The caller owns
+ *     every buffer it passes; the library owns the hierarchy, the
+ *     factorisations and all workspace.
+ *   - All device work is issued on the context's stream.  A call returns
+ *     after the stream has drained, unless its comment says otherwise.
+ *   - Dense matrices are stored row-major unless stated: element (i, j) of
+ *     an r x c matrix with leading dimension ld is at [i * ld + j].
+ *   - Errors: a call returns HSIM_OK or an error status; the thread-local
+ *     message is then available from hsim_last_error().  On error, outputs
+ *     are undefined.  No C++ exception crosses this boundary.
+ *   - Sparse matrices are CSR with int32 row pointers and column indices,
+ *     sorted column indices per row, and double values.
+ */
+#ifndef HSIM_H
+#define HSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HSIM_OK = 0,
+    HSIM_E_INVALID_ARG = 1,    /* bad size, pointer or option */
+    HSIM_E_NOMEM = 2,          /* host or device allocation failed */
+    HSIM_E_CUDA = 3,           /* a CUDA call failed */
+    HSIM_E_BREAKDOWN = 4,      /* tiny pivot in the LDL^T factorisation */
+    HSIM_E_NOT_SPD = 5,        /* reduced mass matrix not positive definite */
+    HSIM_E_NO_CONVERGENCE = 6, /* max_iters reached on some level */
+    HSIM_E_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    HSIM_E_INTERNAL = 8
+} hsim_status;
+
+enum { HSIM_FP64 = 0, HSIM_MIXED = 1 };
+
+/* Solver options.  Defaults (hsim_default_options) follow the paper:
+ * sigma = 7 (Sec. 5, support region), alpha = 0.1 (Alg. 3 shift index
+ * floor(alpha p)), two inverse iterations per Rayleigh-Ritz step and locking
+ * at tolerance/10 (Sec. 4.2). */
+typedef struct {
+    int levels;          /* T >= 1; <= 0 selects 3, or 2 when p <= 200 (Sec. 5) */
+    double sigma;        /* prolongation support: ~sigma centres per row (eq. radius) */
+    double alpha;        /* shift index j = floor(alpha p) (Alg. 3) */
+    int max_iters;       /* subspace iterations per level before HSIM_E_NO_CONVERGENCE */
+    int inv_iters;       /* inverse iterations per Rayleigh-Ritz step (paper: 2) */
+    double lock_factor;  /* lock a converged prefix below lock_factor * tol */
+    int precision;       /* HSIM_FP64 or HSIM_MIXED */
+    int start_vertex;    /* first vertex of farthest-point sampling (Alg. 2) */
+    int leaf_size;       /* nested-dissection leaf size (tuning, default 32) */
+    int q;               /* subspace size; <= 0 selects max(ceil(1.5p), p+8) */
+} hsim_options;
+
+/* Per-solve report (host struct, optional). */
+typedef struct {
+    int levels;
+    int sizes[8];          /* n^tau, tau = 0..levels-1 */
+    int iters[8];          /* subspace iterations per level (index tau) */
+    double shift[8];       /* mu per level */
+    double max_residual;   /* eq. conv2 on the finest level, i < p */
+    int64_t factor_nnz[8]; /* stored entries of L per level */
+    double factor_flops[8];
+    double ms_galerkin, ms_coarse, ms_prolong, ms_factor, ms_solve, ms_spmm,
+           ms_gram, ms_ritz, ms_update, ms_residual, ms_total;
+    int q;
+} hsim_info;
+
+typedef struct hsim_ctx hsim_ctx;
+typedef struct hsim_hier hsim_hier;
+
+void hsim_default_options(hsim_options *opts);
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is
+ * borrowed, not owned. */
+hsim_status hsim_create(int device, void *cuda_stream, hsim_ctx **out);
+void hsim_destroy(hsim_ctx *ctx);
+
+/* Thread-local message of the last failed call on this thread. */
+const char *hsim_last_error(void);
+
+/* Number of compute kernels this library has launched since the process
+ * started (all contexts). */
+uint64_t hsim_kernel_launches(void);
+
+/* --------------------------------------------------------------------------
+ * Hierarchy (Sec. 4.1).  Host-side construction, run once per mesh:
+ *   - level sizes n^{T-1} = max(ceil(1.5p), 1000) and geometric growth
+ *     (eqs. nT-1, growthRate; growth rate read as the (T-1)-th root);
+ *   - farthest-point sampling with Dijkstra distances (Alg. 2);
+ *   - prolongations U^tau (eqs. radius, basis and row normalisation), rows =
+ *     level-tau vertices, columns = level-(tau+1) vertices;
+ *   - patterns of the Galerkin products S^tau = U^T S U (Alg. 3);
+ *   - a nested-dissection ordering and supernodal symbolic analysis for each
+ *     level's shifted matrix S^tau - mu M^tau.
+ * V_host (n x 3 positions) or L2_host (n_tris x 3 squared edge lengths, L2[t*3+k]
+ * = edge opposite corner k of triangle t, for intrinsic meshes) must be
+ * given; F_host is n_tris x 3 vertex indices.  Result uploaded to the device.
+ * ------------------------------------------------------------------------ */
+hsim_status hsim_build_hierarchy(hsim_ctx *ctx, int n_verts, int n_tris, const double *V_host,
+                                 const int32_t *F_host, const double *L2_host, int p,
+                                 const hsim_options *opts, hsim_hier **out);
+void hsim_hier_destroy(hsim_hier *hier);
+
+/* Level sizes and the farthest-point order (mesh vertex ids of the first
+ * n^1 samples) of a hierarchy.  sizes_host has room for 8; order_host may be
+ * NULL or have room for sizes[1] entries. */
+hsim_status hsim_hier_info(const hsim_hier *hier, int *levels, int *sizes_host,
+                           int32_t *order_host);
+
+/* The CSR pattern of S^0 that hsim_solve expects (rows in mesh order, every
+ * mesh edge plus the diagonal), as device pointers owned by the hierarchy. */
+hsim_status hsim_hier_pattern(const hsim_hier *hier, int *n, int64_t *nnz,
+                              const int32_t **row_ptr_dev, const int32_t **col_dev);
+
+/* Prolongation U^tau (natural orders: rows level-tau vertices, columns
+ * level-(tau+1) vertices) copied to host arrays; call with NULL arrays to get
+ * the sizes first. */
+hsim_status hsim_hier_prolongation(const hsim_hier *hier, int tau, int *rows, int *cols,
+                                   int64_t *nnz, int32_t *row_ptr_host, int32_t *col_host,
+                                   double *val_host);
+
+/* Cotan stiffness S^0 and lumped mass diag(M^0) on the device (Sec. 3.1,
+ * eq. massStiffMatrices; S_ij = -1/2 (cot a_ij + cot b_ij), S_ii = -sum_j
+ * S_ij, M_ii = sum of A_t/3 over incident triangles), written into the
+ * hierarchy's pattern.  Exactly one of V_dev (n x 3) and L2_dev (n_tris x 3)
+ * is non-NULL. */
+hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *hier, const double *V_dev,
+                          const double *L2_dev, double *S_val_dev, double *M_diag_dev);
+
+/* HSIM (Alg. 3): the p lowest eigenpairs of S Phi = lambda M Phi.
+ *   S_val_dev   values of S^0 in the hierarchy's pattern (hsim_hier_pattern)
+ *   M_diag_dev  diagonal of the lumped mass M^0 (n)
+ *   tol         relative residual tolerance of eq. conv2 (M^{-1}-norm)
+ *   evals_dev   out: p eigenvalues, ascending
+ *   evecs_dev   out: n x p, COLUMN-major (evecs[i + k n] = Phi_k(i)),
+ *               M-orthonormal, entry of largest magnitude positive
+ *   info        optional host report */
+hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *hier, const double *S_val_dev,
+                       const double *M_diag_dev, int p, double tol, const hsim_options *opts,
+                       double *evals_dev, double *evecs_dev, hsim_info *info);
+
+/* --------------------------------------------------------------------------
+ * Step-level entry points: each runs one step of the hot path on caller
+ * buffers, for parity tests and benchmarking of single kernels.
+ * ------------------------------------------------------------------------ */
+
+/* Y[r, 0:k] = sum_c A[r, c] X[c, 0:k]  (CSR SpMM; the products S Psi,
+ * M Psi of Alg. 1 and the prolongation U Phi of Alg. 3).  X is n_cols x k with
+ * leading dimension ldx, Y is n_rows x k with leading dimension ldy. */
+hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
+                      const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
+                      int ldx, double *Y_dev, int ldy);
+
+/* G = A^T B (k_a x k_b, row-major, ld k_b) for tall A (n x k_a, ld lda) and
+ * B (n x k_b, ld ldb): the reduced matrices Psi^T S Psi, Psi^T M Psi of Alg. 1. */
+hsim_status hsim_gram(hsim_ctx *ctx, int n, int k_a, int k_b, const double *A_dev, int lda,
+                      const double *B_dev, int ldb, double *G_dev);
+
+/* C = A B for A (n x k, ld lda) and small B (k x m, ld ldb), C (n x m, ld ldc):
+ * the basis update Phi = Psi Phi_bar of Alg. 1. */
+hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int k, int m, const double *A_dev, int lda,
+                             const double *B_dev, int ldb, double *C_dev, int ldc);
+
+/* Dense generalised symmetric eigenproblem S_bar X = M_bar X Lambda (Alg. 1,
+ * dense eigenproblem step; also the coarsest level of Alg. 3): Cholesky of
+ * M_bar, cyclic Jacobi on C^-1 S_bar C^-T, back-transformation.  S_bar and
+ * M_bar are k x k row-major (read only); evals (k) ascending; X (k x k,
+ * row-major, column j = eigenvector j, X^T M_bar X = I).  Returns
+ * HSIM_E_NOT_SPD if M_bar is not positive definite.  sweeps_out (host) may
+ * be NULL. */
+hsim_status hsim_ritz(hsim_ctx *ctx, int k, const double *Sbar_dev, const double *Mbar_dev,
+                      double *evals_dev, double *X_dev, int *sweeps_out);
+
+/* Galerkin restriction C = U^T A U of a level matrix (Alg. 3): A is n x n
+ * CSR, U is n x nc CSR; C is returned in the CSR pattern computed on the
+ * host by this call (row_ptr/col/val device buffers allocated by the library
+ * and released with hsim_free). */
+hsim_status hsim_galerkin(hsim_ctx *ctx, int n, int nc, const int32_t *A_ptr_host,
+                          const int32_t *A_col_host, const double *A_val_dev,
+                          const int32_t *U_ptr_host, const int32_t *U_col_host,
+                          const double *U_val_dev, int64_t *nnz_out, int32_t **C_ptr_dev,
+                          int32_t **C_col_dev, double **C_val_dev);
+void hsim_free(void *dev_ptr);
+
+/* Sparse symmetric indefinite factorisation K = S - mu M = P^T L D L^T P
+ * (Alg. 1, factorisation step; Sec. 3.2 "Direct solver") and the solve
+ * K X = B for k right-hand sides, on one level of a hierarchy: tau selects
+ * the level's pattern and ordering.  S_val/M_val are values in the level's
+ * natural-order pattern (tau = 0: hsim_hier_pattern and the diagonal M^0;
+ * tau >= 1: the Galerkin pattern, M in the same pattern).  B is n x k
+ * row-major in the level's natural vertex order; X overwrites B. */
+hsim_status hsim_level_pattern(const hsim_hier *hier, int tau, int *n, int64_t *nnz,
+                               int32_t *row_ptr_host, int32_t *col_host);
+hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *hier, int tau, const double *S_val_dev,
+                               const double *M_val_dev, double mu, int k, double *B_dev, int ldb,
+                               int *negative_pivots);
+
+/* Host-only check of the ordering and symbolic analysis: factors the
+ * natural-order symmetric CSR matrix (ptr/col/val, host) over the same front
+ * structures and in the same order as the GPU kernels and solves K X = B for
+ * nrhs right-hand sides (B, X: n x nrhs row-major, host).  Reports the number
+ * of negative pivots (Sylvester inertia: eigenvalues below the shift) and the
+ * stored entries of L.  Needs no GPU; the solver never uses it. */
+hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int32_t *col, const double *val,
+                                int leaf_size, int nrhs, const double *B, double *X,
+                                int *negative_pivots, int64_t *nnz_L);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSIM_H */

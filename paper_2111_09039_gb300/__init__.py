@@ -1,0 +1,275 @@
+"""GB300-native Hierarchical Subspace Iteration Method (HSIM).
+
+Python binding of ``libhsim.so`` (C ABI in ``include/hsim.h``): argument
+marshalling only, with torch tensors as device memory.  The p lowest
+eigenpairs of the cotan Laplace-Beltrami problem S Phi = lambda M Phi
+(eq. eigenProb) are computed on the GPU by hierarchical subspace iteration
+(Alg. 3 of Nasikun & Hildebrandt).
+
+    ctx = Context()
+    hier = Hierarchy(ctx, F, V=V, p=50)            # host: FPS, U, symbolic
+    S, Md = assemble(ctx, hier, V=V_cuda)          # cotan + lumped mass (GPU)
+    lam, Phi, info = solve(ctx, hier, S, Md, p=50, tol=1e-5)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import HSIM_FP64, HSIM_MIXED, HsimError, Info, Options, check, default_options, lib, ptr
+
+__all__ = ["Context", "Hierarchy", "assemble", "solve", "spmm", "gram", "gemm_update", "ritz",
+           "galerkin", "shifted_solve", "check_symbolic", "default_options", "HsimError",
+           "HSIM_FP64", "HSIM_MIXED", "kernel_launches"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def kernel_launches() -> int:
+    return int(lib().hsim_kernel_launches())
+
+
+class Context:
+    """A device and the stream all work is issued on (torch's current stream
+    by default)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("HSIM needs a CUDA device")
+        self.device = device
+        with torch.cuda.device(device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        check(lib().hsim_create(device, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hsim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """Vertex hierarchy, prolongations and symbolic analyses (host build)."""
+
+    def __init__(self, ctx: Context, F, V=None, L2=None, p: int = 50, options: Options | None = None, **kw):
+        F = np.ascontiguousarray(F, dtype=np.int32)
+        n = int(V.shape[0]) if V is not None else int(F.max()) + 1
+        Vh = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
+        Lh = None if L2 is None else np.ascontiguousarray(L2, dtype=np.float64)
+        o = options if options is not None else default_options(**kw)
+        h = ctypes.c_void_p()
+        check(lib().hsim_build_hierarchy(ctx.handle, n, F.shape[0], ptr(Vh), ptr(F), ptr(Lh), p,
+                                         ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.ctx = ctx
+        self.n = n
+        self.m = F.shape[0]
+        self.p = p
+        self.options = o
+        T = ctypes.c_int()
+        sizes = (ctypes.c_int * 8)()
+        check(lib().hsim_hier_info(h, ctypes.byref(T), sizes, None))
+        self.levels = T.value
+        self.sizes = list(sizes[: T.value])
+        self.order = np.zeros(self.sizes[1] if self.levels > 1 else 0, dtype=np.int32)
+        if self.levels > 1:
+            check(lib().hsim_hier_info(h, None, None, ptr(self.order)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def pattern(self):
+        """(row_ptr, col) of S^0 as torch int32 device tensors (copies)."""
+        torch = _torch()
+        n = ctypes.c_int()
+        nnz = ctypes.c_int64()
+        rp = ctypes.c_void_p()
+        cp = ctypes.c_void_p()
+        check(lib().hsim_hier_pattern(self._h, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(rp),
+                                      ctypes.byref(cp)))
+        row_ptr = _tensor_at(rp.value, 4 * (n.value + 1)).view(torch.int32).clone()
+        col = _tensor_at(cp.value, 4 * nnz.value).view(torch.int32).clone()
+        return row_ptr, col
+
+    def level_pattern(self, tau: int):
+        """Natural-order CSR pattern (numpy) of level tau's matrices."""
+        n = ctypes.c_int()
+        nnz = ctypes.c_int64()
+        check(lib().hsim_level_pattern(self._h, tau, ctypes.byref(n), ctypes.byref(nnz), None, None))
+        rp = np.empty(n.value + 1, dtype=np.int32)
+        cl = np.empty(nnz.value, dtype=np.int32)
+        check(lib().hsim_level_pattern(self._h, tau, None, None, ptr(rp), ptr(cl)))
+        return rp, cl
+
+    def prolongation(self, tau: int):
+        """U^tau as numpy CSR arrays (rows, cols, row_ptr, col, val)."""
+        r, c, nnz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        check(lib().hsim_hier_prolongation(self._h, tau, ctypes.byref(r), ctypes.byref(c), ctypes.byref(nnz),
+                                           None, None, None))
+        rp = np.empty(r.value + 1, dtype=np.int32)
+        cl = np.empty(nnz.value, dtype=np.int32)
+        vl = np.empty(nnz.value, dtype=np.float64)
+        check(lib().hsim_hier_prolongation(self._h, tau, None, None, None, ptr(rp), ptr(cl), ptr(vl)))
+        return r.value, c.value, rp, cl, vl
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hsim_hier_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _tensor_at(addr: int, nbytes: int):
+    """A uint8 CUDA tensor viewing existing device memory (no ownership)."""
+    torch = _torch()
+
+    class _Holder:
+        pass
+
+    h = _Holder()
+    h.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (addr, False), "version": 2}
+    return torch.as_tensor(h, device="cuda")
+
+
+def assemble(ctx: Context, hier: Hierarchy, V=None, L2=None):
+    """Cotan S^0 values (hierarchy pattern) and lumped mass diagonal on the GPU."""
+    torch = _torch()
+    dev = f"cuda:{ctx.device}"
+    S = torch.empty(int(_pattern_nnz(hier)), dtype=torch.float64, device=dev)
+    Md = torch.empty(hier.n, dtype=torch.float64, device=dev)
+    Vt = None if V is None else torch.as_tensor(V, dtype=torch.float64, device=dev).contiguous()
+    Lt = None if L2 is None else torch.as_tensor(L2, dtype=torch.float64, device=dev).contiguous()
+    check(lib().hsim_assemble(ctx.handle, hier.handle, ptr(Vt), ptr(Lt), ptr(S), ptr(Md)))
+    return S, Md
+
+
+def _pattern_nnz(hier: Hierarchy) -> int:
+    nnz = ctypes.c_int64()
+    check(lib().hsim_hier_pattern(hier.handle, None, ctypes.byref(nnz), None, None))
+    return nnz.value
+
+
+def solve(ctx: Context, hier: Hierarchy, S_val, M_diag, p: int, tol: float,
+          options: Options | None = None, **kw):
+    """HSIM: (eigenvalues (p,), eigenvectors (n, p), info dict) on the GPU."""
+    torch = _torch()
+    dev = f"cuda:{ctx.device}"
+    o = options if options is not None else (default_options(**kw) if kw else hier.options)
+    if kw and options is None:
+        o.start_vertex = hier.options.start_vertex
+        o.levels = hier.options.levels
+    lam = torch.empty(p, dtype=torch.float64, device=dev)
+    vecs = torch.empty((p, hier.n), dtype=torch.float64, device=dev)   # column-major n x p
+    info = Info()
+    check(lib().hsim_solve(ctx.handle, hier.handle, ptr(S_val), ptr(M_diag), p, float(tol), ctypes.byref(o),
+                           ptr(lam), ptr(vecs), ctypes.byref(info)))
+    return lam, vecs.t(), info.to_dict()
+
+
+# ---- step-level entry points -------------------------------------------------
+def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None):
+    torch = _torch()
+    n_rows = row_ptr.numel() - 1
+    k = X.shape[1]
+    Y = torch.empty((n_rows, k), dtype=torch.float64, device=X.device)
+    check(lib().hsim_spmm(ctx.handle, n_rows, n_cols if n_cols is not None else X.shape[0], ptr(row_ptr),
+                          ptr(col), ptr(val), k, ptr(X), X.stride(0), ptr(Y), k))
+    return Y
+
+
+def gram(ctx: Context, A, B):
+    torch = _torch()
+    G = torch.empty((A.shape[1], B.shape[1]), dtype=torch.float64, device=A.device)
+    check(lib().hsim_gram(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
+                          B.stride(0), ptr(G)))
+    return G
+
+
+def gemm_update(ctx: Context, A, B):
+    torch = _torch()
+    C = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=A.device)
+    check(lib().hsim_gemm_update(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
+                                 B.stride(0), ptr(C), C.stride(0)))
+    return C
+
+
+def ritz(ctx: Context, Sbar, Mbar):
+    torch = _torch()
+    k = Sbar.shape[0]
+    lam = torch.empty(k, dtype=torch.float64, device=Sbar.device)
+    X = torch.empty((k, k), dtype=torch.float64, device=Sbar.device)
+    sweeps = ctypes.c_int()
+    check(lib().hsim_ritz(ctx.handle, k, ptr(Sbar.contiguous()), ptr(Mbar.contiguous()), ptr(lam), ptr(X),
+                          ctypes.byref(sweeps)))
+    return lam, X, sweeps.value
+
+
+def galerkin(ctx: Context, n: int, nc: int, A_ptr: np.ndarray, A_col: np.ndarray, A_val, U_ptr: np.ndarray,
+             U_col: np.ndarray, U_val):
+    """C = U^T A U; returns (row_ptr numpy, col numpy, val torch)."""
+    torch = _torch()
+    A_ptr = np.ascontiguousarray(A_ptr, dtype=np.int32)
+    A_col = np.ascontiguousarray(A_col, dtype=np.int32)
+    U_ptr = np.ascontiguousarray(U_ptr, dtype=np.int32)
+    U_col = np.ascontiguousarray(U_col, dtype=np.int32)
+    nnz = ctypes.c_int64()
+    cp, cc, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    check(lib().hsim_galerkin(ctx.handle, n, nc, ptr(A_ptr), ptr(A_col), ptr(A_val), ptr(U_ptr), ptr(U_col),
+                              ptr(U_val), ctypes.byref(nnz), ctypes.byref(cp), ctypes.byref(cc), ctypes.byref(cv)))
+    try:
+        rp = _tensor_at(cp.value, 4 * (nc + 1)).view(torch.int32).cpu().numpy().copy()
+        cl = _tensor_at(cc.value, 4 * nnz.value).view(torch.int32).cpu().numpy().copy()
+        vals = _tensor_at(cv.value, 8 * nnz.value).view(torch.float64).clone()
+    finally:
+        lib().hsim_free(cp)
+        lib().hsim_free(cc)
+        lib().hsim_free(cv)
+    return rp, cl, vals
+
+
+def shifted_solve(ctx: Context, hier: Hierarchy, tau: int, S_val, M_val, mu: float, B):
+    """X = (S - mu M)^-1 B on level tau (natural order); returns (X, #negative pivots)."""
+    X = B.clone().contiguous()
+    neg = ctypes.c_int()
+    check(lib().hsim_shifted_solve(ctx.handle, hier.handle, tau, ptr(S_val), ptr(M_val), float(mu), X.shape[1],
+                                   ptr(X), X.stride(0), ctypes.byref(neg)))
+    return X, neg.value
+
+
+def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32):
+    """Host replay of the factorisation over the symbolic analysis (no GPU)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    X = np.empty_like(B)
+    neg = ctypes.c_int()
+    nnzL = ctypes.c_int64()
+    check(lib().hsim_check_symbolic(len(row_ptr) - 1, ptr(row_ptr), ptr(col), ptr(val), leaf_size, B.shape[1],
+                                    ptr(B), ptr(X), ctypes.byref(neg), ctypes.byref(nnzL)))
+    return X, neg.value, nnzL.value

@@ -1,0 +1,73 @@
+// Host-side structures: mesh graph, hierarchy construction and the symbolic
+// analysis (nested dissection + supernodal fronts) of each level's matrix.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "common.h"
+
+namespace hsim {
+
+struct MeshGraph {
+    int n = 0, m = 0;
+    std::vector<int> ptr, idx;  // sorted neighbours
+    std::vector<double> w;      // edge lengths
+    std::vector<double> l2;     // per triangle, squared length opposite each corner
+    double area = 0.0;
+};
+
+MeshGraph build_mesh_graph(int n, int m, const double *V, const int *F, const double *L2);
+std::vector<int> level_sizes(int n, int p, int levels);
+std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count);
+Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int nc,
+                 bool fine_is_mesh, double sigma, double *rho_out, int *fallback_rows);
+
+// ---- sparse pattern algebra -------------------------------------------
+Csr mesh_pattern(const MeshGraph &g);                 // edges + diagonal, sorted
+Csr transpose_pattern(const Csr &A);                  // pattern (and values if present)
+Csr pattern_product(const Csr &A, const Csr &B);      // pattern of A*B (sorted)
+Csr permute_symmetric(const Csr &A, const std::vector<int> &iperm,
+                      std::vector<int64_t> *value_map);  // P A P^T, map new entry -> old entry
+Csr permute_rows_cols(const Csr &A, const std::vector<int> &row_iperm,
+                      const std::vector<int> &col_iperm);  // with values
+
+// ---- supernodal symbolic analysis ---------------------------------------
+// Fronts are the nodes of a nested-dissection tree: every leaf domain and
+// every separator is one dense front (a supernode).  Positions are indices
+// in the internal (elimination) order.
+struct FrontSymbolic {
+    int n = 0;
+    std::vector<int> perm;   // perm[pos] = natural index
+    std::vector<int> iperm;  // iperm[natural] = pos
+    int n_nodes = 0;
+    std::vector<int> pstart, ns, nf, parent, height, nsteps;
+    std::vector<int64_t> rows_off;   // node -> offset into rows (nf entries)
+    std::vector<int> rows;           // front row lists (positions), pivots first
+    std::vector<int64_t> foff;       // node -> arena offset (column-major nf x nf)
+    int64_t arena = 0;
+    std::vector<int64_t> relmap_off; // node -> offset into relmap (nf - ns entries)
+    std::vector<int> relmap;         // struct row -> parent-local row
+    int max_height = 0;
+    // per height: nodes sorted by decreasing panel-step count
+    std::vector<std::vector<int>> by_height;
+    // per height: children (of nodes at this height) that feed an extend-add
+    std::vector<std::vector<int>> ea_children;
+    std::vector<int> pos_node;       // pos -> owning node
+    int64_t nnz_L = 0;
+    double flops = 0.0;
+    int max_front = 0;
+};
+
+constexpr int kPanel = 32;  // panel width of the blocked front kernels
+
+// Nested dissection of the symmetric pattern A (natural order, diagonal
+// ignored) and the front structure of the permuted matrix.
+FrontSymbolic analyse(const Csr &A, int leaf_size);
+
+// Destination offsets in the front arena of every entry of the
+// internal-order CSR A (already permuted by fs.perm) in the lower triangle
+// (-1 for upper entries).
+std::vector<int64_t> assembly_map(const FrontSymbolic &fs, const Csr &A_internal);
+
+}  // namespace hsim

@@ -1,0 +1,150 @@
+// Host replay of the multifrontal factorisation and solve over the symbolic
+// structures of host_symbolic.cpp, in the same order and with the same index
+// arithmetic as the GPU kernels of k_front.cu (front arena layout, panels of
+// kPanel columns, extend-add through relmap, row lists of the solves).  It
+// lets the symbolic analysis be checked on a machine without a GPU; the
+// solver itself never calls it.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "host.h"
+
+using namespace hsim;
+
+extern "C" hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int32_t *col, const double *val,
+                                           int leaf_size, int nrhs, const double *B, double *X, int *neg_pivots,
+                                           int64_t *nnz_L) {
+    try {
+        HSIM_CHECK_ARG(n > 0 && ptr && col && val && B && X && nrhs >= 1, "bad arguments");
+        Csr A;
+        A.n_rows = A.n_cols = n;
+        A.ptr.assign(ptr, ptr + n + 1);
+        A.col.assign(col, col + A.ptr[n]);
+        A.val.assign(val, val + A.ptr[n]);
+        FrontSymbolic fs = analyse(A, leaf_size);
+        std::vector<int64_t> vmap;
+        Csr Ai = permute_symmetric(A, fs.iperm, &vmap);
+        std::vector<int64_t> dst = assembly_map(fs, Ai);
+        std::vector<double> arena(fs.arena, 0.0);
+        for (int64_t e = 0; e < Ai.nnz(); ++e) {
+            if (dst[e] < 0) continue;
+            if (dst[e] >= fs.arena) fail(HSIM_E_INTERNAL, "assembly destination outside the arena");
+            arena[dst[e]] = A.val[vmap[e]];
+        }
+        int neg = 0;
+        for (int h = 0; h <= fs.max_height; ++h) {
+            for (int c : fs.ea_children[h]) {
+                int p = fs.parent[c];
+                int u = fs.nf[c] - fs.ns[c];
+                const double *Fc = arena.data() + fs.foff[c];
+                double *Fp = arena.data() + fs.foff[p];
+                const int *rel = fs.relmap.data() + fs.relmap_off[c];
+                for (int j = 0; j < u; ++j)
+                    for (int i = j; i < u; ++i) {
+                        int64_t di = (int64_t)rel[j] * fs.nf[p] + rel[i];
+                        if (rel[i] < rel[j] || di >= (int64_t)fs.nf[p] * fs.nf[p])
+                            fail(HSIM_E_INTERNAL, "extend-add outside the parent's lower triangle");
+                        Fp[di] += Fc[(int64_t)(fs.ns[c] + j) * fs.nf[c] + fs.ns[c] + i];
+                    }
+            }
+            for (int t : fs.by_height[h]) {
+                const int nf = fs.nf[t], ns = fs.ns[t];
+                double *F = arena.data() + fs.foff[t];
+                for (int k0 = 0; k0 < ns; k0 += kPanel) {
+                    int kb = std::min(kPanel, ns - k0);
+                    // panel: LDL^T of the diagonal block, then rows below
+                    for (int j = 0; j < kb; ++j) {
+                        double d = F[(int64_t)(k0 + j) * nf + k0 + j];
+                        for (int r = j + 1; r < kb; ++r) {
+                            double l = F[(int64_t)(k0 + j) * nf + k0 + r] / d;
+                            for (int c = j + 1; c <= r; ++c)
+                                F[(int64_t)(k0 + c) * nf + k0 + r] -= l * d * F[(int64_t)(k0 + j) * nf + k0 + c] / d;
+                        }
+                        for (int r = j + 1; r < kb; ++r) F[(int64_t)(k0 + j) * nf + k0 + r] /= d;
+                    }
+                    for (int r = k0 + kb; r < nf; ++r) {
+                        double x[kPanel];
+                        for (int c = 0; c < kb; ++c) {
+                            double v = F[(int64_t)(k0 + c) * nf + r];
+                            for (int cc = 0; cc < c; ++cc) v -= x[cc] * F[(int64_t)(k0 + cc) * nf + k0 + c];
+                            x[c] = v;
+                        }
+                        for (int c = 0; c < kb; ++c) F[(int64_t)(k0 + c) * nf + r] = x[c] / F[(int64_t)(k0 + c) * nf + k0 + c];
+                    }
+                    // trailing update
+                    for (int c = k0 + kb; c < nf; ++c)
+                        for (int r = c; r < nf; ++r) {
+                            double acc = 0.0;
+                            for (int kk = 0; kk < kb; ++kk)
+                                acc += F[(int64_t)(k0 + kk) * nf + r] * F[(int64_t)(k0 + kk) * nf + k0 + kk] *
+                                       F[(int64_t)(k0 + kk) * nf + c];
+                            F[(int64_t)c * nf + r] -= acc;
+                        }
+                }
+                for (int i = 0; i < ns; ++i) neg += F[(int64_t)i * nf + i] < 0.0;
+            }
+        }
+        // solve in the internal order
+        std::vector<double> Y((size_t)n * nrhs);
+        for (int pos = 0; pos < n; ++pos)
+            std::memcpy(&Y[(size_t)pos * nrhs], &B[(size_t)fs.perm[pos] * nrhs], nrhs * sizeof(double));
+        auto row = [&](int t, int r) { return fs.rows[fs.rows_off[t] + r]; };
+        for (int h = 0; h <= fs.max_height; ++h)
+            for (int t : fs.by_height[h]) {
+                const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+                const double *F = arena.data() + fs.foff[t];
+                for (int k0 = 0; k0 < ns; k0 += kPanel) {
+                    int kb = std::min(kPanel, ns - k0);
+                    for (int r = 1; r < kb; ++r)
+                        for (int c = 0; c < r; ++c)
+                            for (int j = 0; j < nrhs; ++j)
+                                Y[(size_t)(ps + k0 + r) * nrhs + j] -=
+                                    F[(int64_t)(k0 + c) * nf + k0 + r] * Y[(size_t)(ps + k0 + c) * nrhs + j];
+                    for (int r = k0 + kb; r < nf; ++r) {
+                        int g = row(t, r);
+                        if (g < 0 || g >= n) fail(HSIM_E_INTERNAL, "front row outside the matrix");
+                        for (int c = 0; c < kb; ++c)
+                            for (int j = 0; j < nrhs; ++j)
+                                Y[(size_t)g * nrhs + j] -= F[(int64_t)(k0 + c) * nf + r] * Y[(size_t)(ps + k0 + c) * nrhs + j];
+                    }
+                }
+            }
+        for (int t = 0; t < fs.n_nodes; ++t) {
+            const double *F = arena.data() + fs.foff[t];
+            for (int i = 0; i < fs.ns[t]; ++i)
+                for (int j = 0; j < nrhs; ++j)
+                    Y[(size_t)(fs.pstart[t] + i) * nrhs + j] /= F[(int64_t)i * fs.nf[t] + i];
+        }
+        for (int h = fs.max_height; h >= 0; --h)
+            for (int t : fs.by_height[h]) {
+                const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+                const double *F = arena.data() + fs.foff[t];
+                int nst = (ns + kPanel - 1) / kPanel;
+                for (int st = nst - 1; st >= 0; --st) {
+                    int k0 = st * kPanel;
+                    int kb = std::min(kPanel, ns - k0);
+                    for (int r = k0 + kb; r < nf; ++r) {
+                        int g = row(t, r);
+                        for (int c = 0; c < kb; ++c)
+                            for (int j = 0; j < nrhs; ++j)
+                                Y[(size_t)(ps + k0 + c) * nrhs + j] -= F[(int64_t)(k0 + c) * nf + r] * Y[(size_t)g * nrhs + j];
+                    }
+                    for (int r = kb - 2; r >= 0; --r)
+                        for (int c = r + 1; c < kb; ++c)
+                            for (int j = 0; j < nrhs; ++j)
+                                Y[(size_t)(ps + k0 + r) * nrhs + j] -=
+                                    F[(int64_t)(k0 + r) * nf + k0 + c] * Y[(size_t)(ps + k0 + c) * nrhs + j];
+                }
+            }
+        for (int pos = 0; pos < n; ++pos)
+            std::memcpy(&X[(size_t)fs.perm[pos] * nrhs], &Y[(size_t)pos * nrhs], nrhs * sizeof(double));
+        if (neg_pivots) *neg_pivots = neg;
+        if (nnz_L) *nnz_L = fs.nnz_L;
+        return HSIM_OK;
+    } catch (const Error &e) {
+        return e.status;
+    } catch (...) {
+        return HSIM_E_INTERNAL;
+    }
+}

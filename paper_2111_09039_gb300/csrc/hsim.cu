@@ -1,0 +1,900 @@
+// HSIM driver and C ABI.
+//
+// hsim_build_hierarchy: host construction of the vertex hierarchy, the
+//   prolongations and every level's symbolic analysis (Sec. 4.1, Alg. 2).
+// hsim_solve: the hot path, all on the GPU (Alg. 3):
+//   Galerkin products S^tau, M^tau -> dense coarsest eigenproblem ->
+//   for tau = T-2 .. 0: prolongation U Phi, shift mu = Lambda_floor(alpha p),
+//   numeric LDL^T of S - mu M, subspace iterations (Alg. 1: two inverse
+//   iterations, Rayleigh-Ritz with FP64 Jacobi, update, convergence test of
+//   eq. conv2, locking) until the p lowest pairs have converged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <functional>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "host.h"
+#include "kernels.h"
+
+namespace hsim {
+std::atomic<uint64_t> g_launches{0};
+}
+
+using namespace hsim;
+
+namespace {
+thread_local std::string g_last_error;
+
+hsim_status guard(const std::function<void()> &f) {
+    try {
+        f();
+        return HSIM_OK;
+    } catch (const Error &e) {
+        g_last_error = e.what();
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return HSIM_E_NOMEM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return HSIM_E_INTERNAL;
+    }
+}
+}  // namespace
+
+struct hsim_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf<int> flags;        // small device flag area
+    std::vector<int> hflags;  // host mirror
+    DevBuf<unsigned long long> scratch_u64;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) HSIM_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct LevelData {
+    int n = 0;
+    bool dense = false;
+    Csr pat_nat;                 // natural-order pattern
+    std::vector<int64_t> vmap;   // internal entry -> natural entry
+    Csr pat_int;                 // internal-order pattern
+    DevCsr dpat;                 // internal pattern on the device
+    DevBuf<int64_t> dvmap;
+    DevBuf<int> drow_of;         // row of each internal entry
+    FrontSymbolic fs;
+    DevBuf<int64_t> d_foff, d_rows_off, d_relmap_off, d_asm;
+    DevBuf<int> d_nf, d_ns, d_pstart, d_rows, d_relmap, d_parent, d_perm, d_iperm, d_hnodes, d_ea;
+    std::vector<int64_t> hnodes_off, ea_off;
+    std::vector<std::vector<int>> step_cnt, step_maxnf;
+    std::vector<int> ea_maxu;
+    k::FrontDev fd{};
+};
+
+struct ProlongData {
+    Csr U_nat;    // rows: level tau natural, cols: level tau+1 natural
+    Csr U_int;    // internal orders
+    Csr Ut_int;   // transpose (with values)
+    Csr T_pat;    // pattern of S_int^tau U_int
+    DevCsr dU, dUt, dT;
+    DevBuf<double> dUval, dUtval;
+    double rho = 0.0;
+    int fallback = 0;
+};
+
+}  // namespace
+
+struct hsim_hier {
+    hsim_ctx *ctx = nullptr;
+    int n = 0, m = 0, p = 0, T = 0;
+    hsim_options opts{};
+    std::vector<int> sizes, order;
+    std::vector<LevelData> lev;
+    std::vector<ProlongData> pro;
+    // level-0 assembly data (natural pattern)
+    DevCsr pat0;
+    DevBuf<int> dF, d_ecot, d_vt_ptr, d_vt_idx, d_diag_ptr, d_diag_col;
+    // workspaces, grown on demand
+    DevBuf<double> S0int, M0int, Md0int, dinv0, arena, dpos, ritz_work, Sbar, Mbar, lam, phibar, res_sums,
+        Phi, Psi, SP, MP, coarseX, coarseLam, colw, tmpv, signs, tval_s, tval_m;
+    std::vector<DevBuf<double>> Sv, Mv;  // level values (internal), index tau
+};
+
+namespace {
+
+void upload_level(LevelData &L, cudaStream_t s) {
+    L.dpat.upload(L.pat_int, s);
+    L.dvmap.upload(L.vmap, s);
+    std::vector<int> row_of(L.pat_int.nnz());
+    for (int i = 0; i < L.pat_int.n_rows; ++i)
+        for (int e = L.pat_int.ptr[i]; e < L.pat_int.ptr[i + 1]; ++e) row_of[e] = i;
+    L.drow_of.upload(row_of, s);
+    if (L.dense) return;
+    FrontSymbolic &fs = L.fs;
+    L.d_foff.upload(fs.foff, s);
+    L.d_rows_off.upload(fs.rows_off, s);
+    L.d_relmap_off.upload(fs.relmap_off, s);
+    L.d_nf.upload(fs.nf, s);
+    L.d_ns.upload(fs.ns, s);
+    L.d_pstart.upload(fs.pstart, s);
+    L.d_rows.upload(fs.rows, s);
+    L.d_relmap.upload(fs.relmap.empty() ? std::vector<int>{0} : fs.relmap, s);
+    L.d_parent.upload(fs.parent, s);
+    L.d_perm.upload(fs.perm, s);
+    L.d_iperm.upload(fs.iperm, s);
+    L.d_asm.upload(assembly_map(fs, L.pat_int), s);
+    std::vector<int> hn, ea;
+    L.hnodes_off.clear();
+    L.ea_off.clear();
+    L.step_cnt.assign(fs.max_height + 1, {});
+    L.step_maxnf.assign(fs.max_height + 1, {});
+    L.ea_maxu.assign(fs.max_height + 1, 0);
+    for (int h = 0; h <= fs.max_height; ++h) {
+        const auto &nodes = fs.by_height[h];
+        L.hnodes_off.push_back((int64_t)hn.size());
+        hn.insert(hn.end(), nodes.begin(), nodes.end());
+        int steps = nodes.empty() ? 0 : fs.nsteps[nodes[0]];
+        for (int kst = 0; kst < steps; ++kst) {
+            int cnt = 0, mx = 0;
+            for (int t : nodes) {
+                if (fs.nsteps[t] <= kst) break;
+                ++cnt;
+                mx = std::max(mx, fs.nf[t]);
+            }
+            L.step_cnt[h].push_back(cnt);
+            L.step_maxnf[h].push_back(mx);
+        }
+        L.ea_off.push_back((int64_t)ea.size());
+        for (int c : fs.ea_children[h]) {
+            ea.push_back(c);
+            L.ea_maxu[h] = std::max(L.ea_maxu[h], fs.nf[c] - fs.ns[c]);
+        }
+    }
+    L.hnodes_off.push_back((int64_t)hn.size());
+    L.ea_off.push_back((int64_t)ea.size());
+    L.d_hnodes.upload(hn.empty() ? std::vector<int>{0} : hn, s);
+    L.d_ea.upload(ea.empty() ? std::vector<int>{0} : ea, s);
+    L.fd = k::FrontDev{L.d_foff.p, L.d_nf.p, L.d_ns.p, L.d_pstart.p, L.d_rows_off.p, L.d_rows.p, L.d_relmap_off.p,
+                       L.d_relmap.p};
+}
+
+// Numeric LDL^T of K = S - mu M on level L (values in internal order).
+// Returns the number of negative pivots (eigenvalues of (S, M) below mu).
+int factor_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, const double *S, const double *M, const double *Md,
+                 double mu) {
+    cudaStream_t s = ctx->stream;
+    FrontSymbolic &fs = L.fs;
+    H->arena.reserve((size_t)fs.arena);
+    H->dpos.reserve((size_t)L.n);
+    HSIM_CUDA(cudaMemsetAsync(H->arena.p, 0, (size_t)fs.arena * sizeof(double), s));
+    k::front_assemble(s, L.dpat.nnz, L.drow_of.p, L.dpat.col.p, L.d_asm.p, S, M, Md, mu, H->arena.p);
+    unsigned long long *mx = ctx->scratch_u64.p;
+    HSIM_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+    k::front_maxdiag(s, L.fd, fs.n_nodes, H->arena.p, mx);
+    unsigned long long hmx = 0;
+    HSIM_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    double maxdiag;
+    std::memcpy(&maxdiag, &hmx, sizeof(double));
+    const double tol = std::max(1e-13 * maxdiag, 1e-300);
+    int *flags = ctx->flags.p;
+    HSIM_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
+    for (int h = 0; h <= fs.max_height; ++h) {
+        const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
+        int nea = (int)(L.ea_off[h + 1] - L.ea_off[h]);
+        if (nea > 0)
+            k::front_extend_add(s, L.fd, L.d_parent.p, L.d_ea.p + L.ea_off[h], nea, L.ea_maxu[h], H->arena.p);
+        for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
+            int cnt = L.step_cnt[h][kst];
+            int k0 = (int)kst * kPanel;
+            int mrows = L.step_maxnf[h][kst] - k0 - 1;
+            k::front_panel(s, L.fd, nodes, cnt, k0, mrows, H->arena.p, tol, flags);
+            k::front_update(s, L.fd, nodes, cnt, k0, mrows, H->arena.p);
+        }
+    }
+    // all nodes: 0..N-1 are listed in d_hnodes grouped by height; front_diag
+    // walks the concatenated list
+    k::front_diag(s, L.fd, L.d_hnodes.p, fs.n_nodes, H->arena.p, H->dpos.p, flags + 2);
+    HSIM_CUDA(cudaMemcpyAsync(ctx->hflags.data(), flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    if (ctx->hflags[0] != 0)
+        fail(HSIM_E_BREAKDOWN, "LDL^T breakdown: " + std::to_string(ctx->hflags[0]) +
+                                   " pivot(s) below tolerance (shift " + std::to_string(mu) + ")");
+    return ctx->hflags[2];
+}
+
+void solve_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, double *X, int k, int ldx) {
+    cudaStream_t s = ctx->stream;
+    const FrontSymbolic &fs = L.fs;
+    for (int h = 0; h <= fs.max_height; ++h) {
+        const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
+        for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
+            int cnt = L.step_cnt[h][kst];
+            int k0 = (int)kst * kPanel;
+            k::solve_fwd_tri(s, L.fd, nodes, cnt, k0, H->arena.p, k, X, ldx);
+            k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, H->arena.p, k, X, ldx);
+        }
+    }
+    k::solve_diag(s, L.n, k, H->dpos.p, X, ldx);
+    for (int h = fs.max_height; h >= 0; --h) {
+        const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
+        for (int kst = (int)L.step_cnt[h].size() - 1; kst >= 0; --kst) {
+            int cnt = L.step_cnt[h][kst];
+            int k0 = kst * kPanel;
+            k::solve_bwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, H->arena.p, k, X, ldx);
+            k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, H->arena.p, k, X, ldx);
+        }
+    }
+}
+
+int subspace_q(int p, const hsim_options &o) {
+    if (o.q > 0) return o.q;
+    return std::max((int)std::ceil(1.5 * p), p + 8);
+}
+
+struct Timer {
+    cudaStream_t s;
+    cudaEvent_t a{}, b{};
+    explicit Timer(cudaStream_t st) : s(st) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    double stop() {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventRecord(a, s);
+        return ms;
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+// M Y on level tau: diagonal at tau = 0, CSR otherwise
+void apply_M(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int ldx, double *Y, int ldy) {
+    LevelData &L = H->lev[tau];
+    if (tau == 0)
+        k::diag_scale(ctx->stream, L.n, k, H->Md0int.p, X, ldx, Y, ldy);
+    else
+        k::spmm(ctx->stream, L.n, L.dpat.ptr.p, L.dpat.col.p, H->Mv[tau].p, k, X, ldx, Y, ldy);
+}
+void apply_S(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int ldx, double *Y, int ldy) {
+    LevelData &L = H->lev[tau];
+    const double *v = tau == 0 ? H->S0int.p : H->Sv[tau].p;
+    k::spmm(ctx->stream, L.n, L.dpat.ptr.p, L.dpat.col.p, v, k, X, ldx, Y, ldy);
+}
+
+// Rayleigh-Ritz on q x q reduced matrices; throws on failure
+void ritz_step(hsim_ctx *ctx, hsim_hier *H, int q, const double *Sbar, const double *Mbar, double *lam, double *X,
+               int ldx, int *sweeps) {
+    H->ritz_work.reserve(k::ritz_work_size(q));
+    int rc = k::ritz(ctx->stream, q, Sbar, q, Mbar, q, lam, X, ldx, H->ritz_work.p, sweeps, ctx->flags.p,
+                     ctx->hflags.data());
+    if (rc != 0) fail(HSIM_E_NOT_SPD, "reduced mass matrix is not positive definite (q = " + std::to_string(q) + ")");
+}
+
+void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M_diag, int p, double tol,
+               const hsim_options &o, double *evals, double *evecs, hsim_info *info) {
+    cudaStream_t s = ctx->stream;
+    Timer tm(s), total(s);
+    hsim_info inf{};
+    const int T = H->T;
+    inf.levels = T;
+    for (int t = 0; t < T && t < 8; ++t) inf.sizes[t] = H->sizes[t];
+    const int q = subspace_q(p, o);
+    HSIM_CHECK_ARG(q >= p && q <= H->sizes[T - 1], "subspace size q exceeds the coarsest level");
+    inf.q = q;
+    LevelData &L0 = H->lev[0];
+    const int n0 = L0.n;
+    // level-0 values in internal order
+    H->S0int.reserve(L0.dpat.nnz);
+    H->Md0int.reserve(n0);
+    H->dinv0.reserve(n0);
+    k::gather_values(s, L0.dpat.nnz, L0.dvmap.p, S_val, H->S0int.p);
+    if (T > 1 || !L0.dense) {
+        k::gather_values_i(s, n0, L0.dense ? nullptr : L0.d_perm.p, M_diag, H->Md0int.p);
+    }
+    H->Sv.resize(T);
+    H->Mv.resize(T);
+    // Galerkin products (Alg. 3, restriction step)
+    for (int tau = 0; tau + 1 < T; ++tau) {
+        ProlongData &P = H->pro[tau];
+        LevelData &Lf = H->lev[tau];
+        LevelData &Lc = H->lev[tau + 1];
+        H->tval_s.reserve(P.T_pat.nnz());
+        H->tval_m.reserve(P.T_pat.nnz());
+        const double *Sf = tau == 0 ? H->S0int.p : H->Sv[tau].p;
+        k::galerkin_au(s, Lf.n, Lf.dpat.ptr.p, Lf.dpat.col.p, Sf, P.dU.ptr.p, P.dU.col.p, P.dUval.p, P.dT.ptr.p,
+                       P.dT.col.p, H->tval_s.p);
+        if (tau == 0)
+            k::galerkin_au(s, Lf.n, H->d_diag_ptr.p, H->d_diag_col.p, H->Md0int.p, P.dU.ptr.p, P.dU.col.p, P.dUval.p,
+                           P.dT.ptr.p, P.dT.col.p, H->tval_m.p);
+        else
+            k::galerkin_au(s, Lf.n, Lf.dpat.ptr.p, Lf.dpat.col.p, H->Mv[tau].p, P.dU.ptr.p, P.dU.col.p, P.dUval.p,
+                           P.dT.ptr.p, P.dT.col.p, H->tval_m.p);
+        H->Sv[tau + 1].reserve(Lc.dpat.nnz);
+        H->Mv[tau + 1].reserve(Lc.dpat.nnz);
+        k::galerkin_utt(s, Lc.n, P.dUt.ptr.p, P.dUt.col.p, P.dUtval.p, P.dT.ptr.p, P.dT.col.p, H->tval_s.p,
+                        Lc.dpat.ptr.p, Lc.dpat.col.p, H->Sv[tau + 1].p);
+        k::galerkin_utt(s, Lc.n, P.dUt.ptr.p, P.dUt.col.p, P.dUtval.p, P.dT.ptr.p, P.dT.col.p, H->tval_m.p,
+                        Lc.dpat.ptr.p, Lc.dpat.col.p, H->Mv[tau + 1].p);
+    }
+    inf.ms_galerkin = tm.stop();
+    // coarsest level: dense generalised eigenproblem (Alg. 3)
+    LevelData &Lc = H->lev[T - 1];
+    const int nc = Lc.n;
+    H->Sbar.reserve((size_t)nc * nc);
+    H->Mbar.reserve((size_t)nc * nc);
+    if (T == 1) {
+        k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->S0int.p, H->Sbar.p);
+        k::densify_diag(s, nc, M_diag, H->Mbar.p);
+    } else {
+        k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Sv[T - 1].p, H->Sbar.p);
+        k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Mv[T - 1].p, H->Mbar.p);
+    }
+    H->coarseX.reserve((size_t)nc * nc);
+    H->coarseLam.reserve(nc);
+    int sweeps = 0;
+    ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps);
+    inf.ms_coarse = tm.stop();
+    std::vector<double> lam_h(q);
+    HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->coarseLam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    H->signs.reserve(std::max(p, 1));
+    if (T == 1) {
+        HSIM_CUDA(cudaMemcpyAsync(evals, H->coarseLam.p, p * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        k::output_evecs(s, nc, p, nullptr, H->coarseX.p, nc, evecs, H->signs.p);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        inf.ms_total = total.stop();
+        if (info) *info = inf;
+        return;
+    }
+    // SIM on every finer level
+    const size_t nq = (size_t)n0 * q;
+    H->Phi.reserve(nq);
+    H->Psi.reserve(nq);
+    H->SP.reserve(nq);
+    H->MP.reserve(nq);
+    H->Sbar.reserve((size_t)q * q);
+    H->Mbar.reserve((size_t)q * q);
+    H->phibar.reserve((size_t)q * q);
+    H->lam.reserve(q);
+    H->colw.reserve(q);
+    H->res_sums.reserve(3 * (size_t)q);
+    const double *Xc = H->coarseX.p;
+    int ldxc = nc;
+    std::vector<double> rs(3 * (size_t)q), res(q);
+    for (int tau = T - 2; tau >= 0; --tau) {
+        LevelData &L = H->lev[tau];
+        ProlongData &P = H->pro[tau];
+        const int n = L.n;
+        // prolongation of the basis (Alg. 3)
+        Timer tp(s);
+        k::spmm(s, n, P.dU.ptr.p, P.dU.col.p, P.dUval.p, q, Xc, ldxc, H->Phi.p, q);
+        inf.ms_prolong += tp.stop();
+        // shift (Alg. 3): Lambda_j of the coarser level, j = floor(alpha p)
+        int j = (int)std::floor(o.alpha * p);
+        double mu = j == 0 ? -1e-8 * lam_h[q - 1] : lam_h[j];
+        inf.shift[tau] = mu;
+        const double *Sx = tau == 0 ? H->S0int.p : H->Sv[tau].p;
+        const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
+        const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
+        Timer tf(s);
+        factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
+        inf.ms_factor += tf.stop();
+        inf.factor_nnz[tau] = L.fs.nnz_L;
+        inf.factor_flops[tau] = L.fs.flops;
+        // 1 / diag(M) for the M^-1 norm of the finest level (Sec. 5, termination criterion)
+        const double *dinv = nullptr;
+        if (tau == 0) {
+            H->dinv0.reserve(n);
+            k::reciprocal(s, n, H->Md0int.p, H->dinv0.p);
+            dinv = H->dinv0.p;
+        }
+        // M Phi
+        apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
+        int locked = 0, it = 0;
+        double maxres = 0.0;
+        for (it = 1; it <= o.max_iters; ++it) {
+            const int a = q - locked;
+            Timer ts(s);
+            // inverse iterations on the active columns (Alg. 1, solve step; twice)
+            k::copy_matrix(s, n, a, H->MP.p + locked, q, H->Psi.p + locked, q);
+            solve_level(ctx, H, L, H->Psi.p + locked, a, q);
+            for (int extra = 1; extra < o.inv_iters; ++extra) {
+                apply_M(ctx, H, tau, a, H->Psi.p + locked, q, H->SP.p + locked, q);
+                k::copy_matrix(s, n, a, H->SP.p + locked, q, H->Psi.p + locked, q);
+                solve_level(ctx, H, L, H->Psi.p + locked, a, q);
+            }
+            if (locked > 0) k::copy_matrix(s, n, locked, H->Phi.p, q, H->Psi.p, q);
+            inf.ms_solve += ts.stop();
+            // column scaling to unit M-norm, then S Psi, M Psi (Alg. 1, reduced matrices)
+            apply_M(ctx, H, tau, q, H->Psi.p, q, H->MP.p, q);
+            k::col_dots(s, n, q, H->Psi.p, q, H->MP.p, q, nullptr, H->colw.p);
+            k::scale_cols_rsqrt(s, n, q, H->colw.p, H->Psi.p, q);
+            k::scale_cols_rsqrt(s, n, q, H->colw.p, H->MP.p, q);
+            apply_S(ctx, H, tau, q, H->Psi.p, q, H->SP.p, q);
+            inf.ms_spmm += ts.stop();
+            k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
+            k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);
+            inf.ms_gram += ts.stop();
+            // dense eigenproblem (Alg. 1): Ritz values ascending, M-orthonormal
+            ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps);
+            inf.ms_ritz += ts.stop();
+            // update Phi = Psi Phi_bar (Alg. 1)
+            k::gemm_nn(s, n, q, q, H->Psi.p, q, H->phibar.p, q, H->Phi.p, q);
+            inf.ms_update += ts.stop();
+            // convergence test (eq. conv2)
+            apply_S(ctx, H, tau, q, H->Phi.p, q, H->SP.p, q);
+            apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
+            k::residual_sums(s, n, q, H->SP.p, q, H->MP.p, q, H->lam.p, dinv, H->res_sums.p);
+            HSIM_CUDA(cudaMemcpyAsync(rs.data(), H->res_sums.p, 3 * q * sizeof(double), cudaMemcpyDeviceToHost, s));
+            HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->lam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
+            HSIM_CUDA(cudaStreamSynchronize(s));
+            inf.ms_residual += ts.stop();
+            double lam_ref = lam_h[q - 1];
+            for (int i = 0; i < q; ++i)
+                if (lam_h[i] > 1e-8 * lam_h[q - 1]) {
+                    lam_ref = lam_h[i];
+                    break;
+                }
+            maxres = 0.0;
+            for (int i = 0; i < q; ++i) {
+                double den = std::max(std::sqrt(rs[3 * i + 1]), lam_ref * std::sqrt(rs[3 * i + 2]));
+                res[i] = std::sqrt(rs[3 * i]) / den;
+                if (i < p) maxres = std::max(maxres, res[i]);
+            }
+            if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
+            if (maxres < tol) break;
+            int r = 0;
+            while (r < p && res[r] < o.lock_factor * tol) ++r;
+            locked = r;
+        }
+        if (it > o.max_iters) {
+            inf.iters[tau] = o.max_iters;
+            if (info) *info = inf;
+            fail(HSIM_E_NO_CONVERGENCE, "level " + std::to_string(tau) + ": no convergence in " +
+                                            std::to_string(o.max_iters) + " iterations (max residual " +
+                                            std::to_string(maxres) + ")");
+        }
+        inf.iters[tau] = it;
+        if (tau == 0) inf.max_residual = maxres;
+        // the next finer level starts from this level's basis
+        Xc = H->Phi.p;
+        ldxc = q;
+        if (tau > 0) {
+            // Phi is overwritten by the prolongation on the next level: keep a copy
+            H->coarseX.reserve((size_t)n * q);
+            k::copy_matrix(s, n, q, H->Phi.p, q, H->coarseX.p, q);
+            Xc = H->coarseX.p;
+        }
+    }
+    HSIM_CUDA(cudaMemcpyAsync(evals, H->lam.p, p * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k::output_evecs(s, n0, p, L0.d_iperm.p, H->Phi.p, q, evecs, H->signs.p);
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    inf.ms_total = total.stop();
+    if (info) *info = inf;
+}
+
+hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F, const double *L2, int p,
+                 const hsim_options &o) {
+    HSIM_CHECK_ARG(p >= 1, "p must be >= 1");
+    cudaStream_t s = ctx->stream;
+    auto H = std::make_unique<hsim_hier>();
+    H->ctx = ctx;
+    H->n = n;
+    H->m = m;
+    H->p = p;
+    H->opts = o;
+    int T = o.levels > 0 ? o.levels : (p <= 200 ? 2 : 3);
+    MeshGraph g = build_mesh_graph(n, m, V, F, L2);
+    H->sizes = level_sizes(n, p, T);
+    T = (int)H->sizes.size();
+    H->T = T;
+    HSIM_CHECK_ARG(T <= 8, "at most 8 levels");
+    HSIM_CHECK_ARG(subspace_q(p, o) <= H->sizes[T - 1], "p too large for the mesh");
+    if (T > 1) H->order = farthest_point_order(g, o.start_vertex, H->sizes[1]);
+    // natural patterns and prolongations
+    H->lev.resize(T);
+    H->pro.resize(T > 0 ? T - 1 : 0);
+    H->lev[0].n = n;
+    H->lev[0].pat_nat = mesh_pattern(g);
+    for (int tau = 0; tau + 1 < T; ++tau) {
+        ProlongData &P = H->pro[tau];
+        P.U_nat = prolongation(g, H->order, H->sizes[tau], H->sizes[tau + 1], tau == 0, o.sigma, &P.rho, &P.fallback);
+        Csr Ut = transpose_pattern(P.U_nat);
+        Csr AU = pattern_product(H->lev[tau].pat_nat, P.U_nat);
+        H->lev[tau + 1].n = H->sizes[tau + 1];
+        H->lev[tau + 1].pat_nat = pattern_product(Ut, AU);
+    }
+    // orderings and symbolic analyses
+    const int leaf = o.leaf_size > 0 ? o.leaf_size : 32;
+    for (int tau = 0; tau < T; ++tau) {
+        LevelData &L = H->lev[tau];
+        L.dense = (tau == T - 1);
+        if (!L.dense) {
+            L.fs = analyse(L.pat_nat, leaf);
+        } else {
+            L.fs.n = L.n;
+            L.fs.perm.resize(L.n);
+            L.fs.iperm.resize(L.n);
+            for (int i = 0; i < L.n; ++i) L.fs.perm[i] = L.fs.iperm[i] = i;
+        }
+        L.pat_int = permute_symmetric(L.pat_nat, L.fs.iperm, &L.vmap);
+    }
+    for (int tau = 0; tau + 1 < T; ++tau) {
+        ProlongData &P = H->pro[tau];
+        P.U_int = permute_rows_cols(P.U_nat, H->lev[tau].fs.iperm, H->lev[tau + 1].fs.iperm);
+        P.Ut_int = transpose_pattern(P.U_int);
+        P.T_pat = pattern_product(H->lev[tau].pat_int, P.U_int);
+        Csr C = pattern_product(P.Ut_int, P.T_pat);
+        if (C.ptr != H->lev[tau + 1].pat_int.ptr || C.col != H->lev[tau + 1].pat_int.col)
+            fail(HSIM_E_INTERNAL, "Galerkin pattern mismatch between orders");
+    }
+    // device uploads
+    for (int tau = 0; tau < T; ++tau) upload_level(H->lev[tau], s);
+    for (int tau = 0; tau + 1 < T; ++tau) {
+        ProlongData &P = H->pro[tau];
+        P.dU.upload(P.U_int, s);
+        P.dUval.upload(P.U_int.val, s);
+        P.dUt.upload(P.Ut_int, s);
+        P.dUtval.upload(P.Ut_int.val, s);
+        P.dT.upload(P.T_pat, s);
+    }
+    {
+        std::vector<int> dp(n + 1), dc(n);
+        for (int i = 0; i <= n; ++i) dp[i] = i;
+        for (int i = 0; i < n; ++i) dc[i] = i;
+        H->d_diag_ptr.upload(dp, s);
+        H->d_diag_col.upload(dc, s);
+    }
+    // level-0 assembly data in the natural pattern
+    const Csr &A0 = H->lev[0].pat_nat;
+    H->pat0.upload(A0, s);
+    std::vector<int> ecot(2 * (size_t)A0.nnz(), -1);
+    auto find = [&](int i, int j) -> int64_t {
+        auto b = A0.col.begin() + A0.ptr[i], e = A0.col.begin() + A0.ptr[i + 1];
+        auto it = std::lower_bound(b, e, j);
+        if (it == e || *it != j) fail(HSIM_E_INTERNAL, "mesh edge missing in pattern");
+        return it - A0.col.begin();
+    };
+    std::vector<int> vcount(n + 1, 0);
+    std::vector<int> Fv(F, F + 3 * (size_t)m);
+    for (int t = 0; t < m; ++t)
+        for (int kc = 0; kc < 3; ++kc) {
+            int a = F[3 * t + (kc + 1) % 3], b = F[3 * t + (kc + 2) % 3];
+            for (int64_t e : {find(a, b), find(b, a)}) {
+                if (ecot[2 * e] < 0) ecot[2 * e] = 3 * t + kc;
+                else if (ecot[2 * e + 1] < 0) ecot[2 * e + 1] = 3 * t + kc;
+                else fail(HSIM_E_INVALID_ARG, "non-manifold edge (more than two triangles)");
+            }
+            vcount[F[3 * t + kc] + 1]++;
+        }
+    for (int i = 0; i < n; ++i) vcount[i + 1] += vcount[i];
+    std::vector<int> vt(vcount.back());
+    std::vector<int> fill(vcount.begin(), vcount.end() - 1);
+    for (int t = 0; t < m; ++t)
+        for (int kc = 0; kc < 3; ++kc) vt[fill[F[3 * t + kc]]++] = t;
+    H->d_ecot.upload(ecot, s);
+    H->d_vt_ptr.upload(vcount, s);
+    H->d_vt_idx.upload(vt, s);
+    H->dF.upload(Fv, s);
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    return H.release();
+}
+
+hsim_options checked(const hsim_options *o) {
+    hsim_options d;
+    hsim_default_options(&d);
+    if (!o) return d;
+    hsim_options r = *o;
+    HSIM_CHECK_ARG(r.sigma > 0, "sigma must be positive");
+    HSIM_CHECK_ARG(r.alpha >= 0 && r.alpha < 1, "alpha must be in [0, 1)");
+    HSIM_CHECK_ARG(r.max_iters >= 1, "max_iters must be >= 1");
+    HSIM_CHECK_ARG(r.inv_iters >= 1, "inv_iters must be >= 1");
+    HSIM_CHECK_ARG(r.precision == HSIM_FP64 || r.precision == HSIM_MIXED, "unknown precision");
+    return r;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void hsim_default_options(hsim_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->levels = 0;
+    o->sigma = 7.0;
+    o->alpha = 0.1;
+    o->max_iters = 100;
+    o->inv_iters = 2;
+    o->lock_factor = 0.1;
+    o->precision = HSIM_FP64;
+    o->start_vertex = 0;
+    o->leaf_size = 32;
+    o->q = 0;
+}
+
+const char *hsim_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t hsim_kernel_launches(void) { return g_launches.load(); }
+
+hsim_status hsim_create(int device, void *stream, hsim_ctx **out) {
+    return guard([&] {
+        HSIM_CHECK_ARG(out != nullptr, "out is NULL");
+        int count = 0;
+        HSIM_CUDA(cudaGetDeviceCount(&count));
+        HSIM_CHECK_ARG(device >= 0 && device < count, "no such CUDA device");
+        DeviceGuard dg(device);
+        auto c = std::make_unique<hsim_ctx>();
+        c->device = device;
+        c->stream = (cudaStream_t)stream;
+        c->flags.alloc(16);
+        c->hflags.assign(16, 0);
+        c->scratch_u64.alloc(4);
+        *out = c.release();
+    });
+}
+
+void hsim_destroy(hsim_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard dg(ctx->device);
+    delete ctx;
+}
+
+hsim_status hsim_build_hierarchy(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F, const double *L2,
+                                 int p, const hsim_options *opts, hsim_hier **out) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && out, "NULL argument");
+        DeviceGuard dg(ctx->device);
+        hsim_options o = checked(opts);
+        HSIM_CHECK_ARG(o.start_vertex >= 0 && o.start_vertex < n, "start_vertex out of range");
+        *out = build(ctx, n, m, V, F, L2, p, o);
+    });
+}
+
+void hsim_hier_destroy(hsim_hier *h) {
+    if (!h) return;
+    DeviceGuard dg(h->ctx->device);
+    delete h;
+}
+
+hsim_status hsim_hier_info(const hsim_hier *h, int *levels, int *sizes, int32_t *order) {
+    return guard([&] {
+        HSIM_CHECK_ARG(h, "NULL hierarchy");
+        if (levels) *levels = h->T;
+        if (sizes)
+            for (int t = 0; t < h->T && t < 8; ++t) sizes[t] = h->sizes[t];
+        if (order && !h->order.empty()) std::memcpy(order, h->order.data(), h->order.size() * sizeof(int32_t));
+    });
+}
+
+hsim_status hsim_hier_pattern(const hsim_hier *h, int *n, int64_t *nnz, const int32_t **ptr, const int32_t **col) {
+    return guard([&] {
+        HSIM_CHECK_ARG(h, "NULL hierarchy");
+        if (n) *n = h->n;
+        if (nnz) *nnz = h->pat0.nnz;
+        if (ptr) *ptr = h->pat0.ptr.p;
+        if (col) *col = h->pat0.col.p;
+    });
+}
+
+hsim_status hsim_hier_prolongation(const hsim_hier *h, int tau, int *rows, int *cols, int64_t *nnz, int32_t *ptr,
+                                   int32_t *col, double *val) {
+    return guard([&] {
+        HSIM_CHECK_ARG(h && tau >= 0 && tau + 1 < h->T, "bad level");
+        const Csr &U = h->pro[tau].U_nat;
+        if (rows) *rows = U.n_rows;
+        if (cols) *cols = U.n_cols;
+        if (nnz) *nnz = U.nnz();
+        if (ptr) std::memcpy(ptr, U.ptr.data(), U.ptr.size() * sizeof(int));
+        if (col) std::memcpy(col, U.col.data(), U.col.size() * sizeof(int));
+        if (val) std::memcpy(val, U.val.data(), U.val.size() * sizeof(double));
+    });
+}
+
+hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *h, const double *V_dev, const double *L2_dev,
+                          double *S_val, double *M_diag) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && h && S_val && M_diag, "NULL argument");
+        HSIM_CHECK_ARG((V_dev != nullptr) != (L2_dev != nullptr), "exactly one of V and L2 must be given");
+        DeviceGuard dg(ctx->device);
+        cudaStream_t s = ctx->stream;
+        DevBuf<double> cot((size_t)3 * h->m), area((size_t)h->m);
+        k::triangle_geometry(s, h->m, h->dF.p, V_dev, L2_dev, cot.p, area.p);
+        k::assemble_sm(s, h->n, h->pat0.ptr.p, h->pat0.col.p, h->d_ecot.p, cot.p, h->d_vt_ptr.p, h->d_vt_idx.p, area.p,
+                       S_val, M_diag);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *h, const double *S_val, const double *M_diag, int p, double tol,
+                       const hsim_options *opts, double *evals, double *evecs, hsim_info *info) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && h && S_val && M_diag && evals && evecs, "NULL argument");
+        HSIM_CHECK_ARG(p >= 1 && p <= h->n, "bad p");
+        HSIM_CHECK_ARG(tol > 0, "tol must be positive");
+        DeviceGuard dg(ctx->device);
+        hsim_options o = checked(opts ? opts : &h->opts);
+        HSIM_CHECK_ARG(o.precision == HSIM_FP64, "this build solves in FP64 only");
+        run_solve(ctx, h, S_val, M_diag, p, tol, o, evals, evecs, info);
+    });
+}
+
+hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *ptr, const int32_t *col,
+                      const double *val, int k, const double *X, int ldx, double *Y, int ldy) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && ptr && col && val && X && Y, "NULL argument");
+        HSIM_CHECK_ARG(n_rows >= 0 && n_cols >= 0 && k >= 0 && ldx >= k && ldy >= k, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        k::spmm(ctx->stream, n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+hsim_status hsim_gram(hsim_ctx *ctx, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb,
+                      double *G) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && A && B && G, "NULL argument");
+        HSIM_CHECK_ARG(n >= 0 && ka >= 0 && kb >= 0 && lda >= ka && ldb >= kb, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        k::gram(ctx->stream, n, ka, kb, A, lda, B, ldb, G, kb, false);
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int kk, int m, const double *A, int lda, const double *B, int ldb,
+                             double *C, int ldc) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && A && B && C, "NULL argument");
+        HSIM_CHECK_ARG(n >= 0 && kk >= 0 && m >= 0 && lda >= kk && ldb >= m && ldc >= m, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        k::gemm_nn(ctx->stream, n, kk, m, A, lda, B, ldb, C, ldc);
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+hsim_status hsim_ritz(hsim_ctx *ctx, int kk, const double *Sbar, const double *Mbar, double *evals, double *X,
+                      int *sweeps_out) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && Sbar && Mbar && evals && X, "NULL argument");
+        HSIM_CHECK_ARG(kk >= 1, "bad size");
+        DeviceGuard dg(ctx->device);
+        DevBuf<double> work(k::ritz_work_size(kk));
+        int sw = 0;
+        int rc = k::ritz(ctx->stream, kk, Sbar, kk, Mbar, kk, evals, X, kk, work.p, &sw, ctx->flags.p,
+                         ctx->hflags.data());
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (sweeps_out) *sweeps_out = sw;
+        if (rc != 0) fail(HSIM_E_NOT_SPD, "M_bar is not positive definite");
+    });
+}
+
+hsim_status hsim_galerkin(hsim_ctx *ctx, int n, int nc, const int32_t *A_ptr, const int32_t *A_col,
+                          const double *A_val, const int32_t *U_ptr, const int32_t *U_col, const double *U_val,
+                          int64_t *nnz_out, int32_t **C_ptr, int32_t **C_col, double **C_val) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && A_ptr && A_col && A_val && U_ptr && U_col && U_val && nnz_out && C_ptr && C_col && C_val,
+                       "NULL argument");
+        DeviceGuard dg(ctx->device);
+        cudaStream_t s = ctx->stream;
+        Csr A, U;
+        A.n_rows = A.n_cols = n;
+        A.ptr.assign(A_ptr, A_ptr + n + 1);
+        A.col.assign(A_col, A_col + A.ptr[n]);
+        U.n_rows = n;
+        U.n_cols = nc;
+        U.ptr.assign(U_ptr, U_ptr + n + 1);
+        U.col.assign(U_col, U_col + U.ptr[n]);
+        for (int c : A.col) HSIM_CHECK_ARG(c >= 0 && c < n, "A column out of range");
+        for (int c : U.col) HSIM_CHECK_ARG(c >= 0 && c < nc, "U column out of range");
+        // U^T pattern with a map to U's entries
+        Csr Ut;
+        Ut.n_rows = nc;
+        Ut.n_cols = n;
+        Ut.ptr.assign(nc + 1, 0);
+        for (int c : U.col) Ut.ptr[c + 1]++;
+        for (int i = 0; i < nc; ++i) Ut.ptr[i + 1] += Ut.ptr[i];
+        Ut.col.resize(U.col.size());
+        std::vector<int> map(U.col.size());
+        std::vector<int> fill(Ut.ptr.begin(), Ut.ptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int e = U.ptr[i]; e < U.ptr[i + 1]; ++e) {
+                int d = fill[U.col[e]]++;
+                Ut.col[d] = i;
+                map[d] = e;
+            }
+        Csr Tp = pattern_product(A, U);
+        Csr Cp = pattern_product(Ut, Tp);
+        DevCsr dA, dU, dUt, dT;
+        dA.upload(A, s);
+        dU.upload(U, s);
+        dUt.upload(Ut, s);
+        dT.upload(Tp, s);
+        DevBuf<int> dmap;
+        dmap.upload(map, s);
+        DevBuf<double> utv(map.size()), tv((size_t)Tp.nnz());
+        k::gather_values_i(s, (int64_t)map.size(), dmap.p, U_val, utv.p);
+        k::galerkin_au(s, n, dA.ptr.p, dA.col.p, A_val, dU.ptr.p, dU.col.p, U_val, dT.ptr.p, dT.col.p, tv.p);
+        int32_t *cp = nullptr, *cc = nullptr;
+        double *cv = nullptr;
+        HSIM_CUDA(cudaMalloc(&cp, (nc + 1) * sizeof(int32_t)));
+        HSIM_CUDA(cudaMalloc(&cc, std::max<int64_t>(1, Cp.nnz()) * sizeof(int32_t)));
+        HSIM_CUDA(cudaMalloc(&cv, std::max<int64_t>(1, Cp.nnz()) * sizeof(double)));
+        HSIM_CUDA(cudaMemcpyAsync(cp, Cp.ptr.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        if (Cp.nnz())
+            HSIM_CUDA(cudaMemcpyAsync(cc, Cp.col.data(), Cp.nnz() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        k::galerkin_utt(s, nc, dUt.ptr.p, dUt.col.p, utv.p, dT.ptr.p, dT.col.p, tv.p, cp, cc, cv);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        *nnz_out = Cp.nnz();
+        *C_ptr = cp;
+        *C_col = cc;
+        *C_val = cv;
+    });
+}
+
+void hsim_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+hsim_status hsim_level_pattern(const hsim_hier *h, int tau, int *n, int64_t *nnz, int32_t *ptr, int32_t *col) {
+    return guard([&] {
+        HSIM_CHECK_ARG(h && tau >= 0 && tau < h->T, "bad level");
+        const Csr &A = h->lev[tau].pat_nat;
+        if (n) *n = A.n_rows;
+        if (nnz) *nnz = A.nnz();
+        if (ptr) std::memcpy(ptr, A.ptr.data(), A.ptr.size() * sizeof(int));
+        if (col) std::memcpy(col, A.col.data(), A.col.size() * sizeof(int));
+    });
+}
+
+hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *h, int tau, const double *S_val, const double *M_val,
+                               double mu, int kk, double *B, int ldb, int *neg) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && h && S_val && M_val && B, "NULL argument");
+        HSIM_CHECK_ARG(tau >= 0 && tau + 1 < h->T, "level has no sparse factorisation");
+        HSIM_CHECK_ARG(kk >= 1 && ldb >= kk, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        cudaStream_t s = ctx->stream;
+        LevelData &L = h->lev[tau];
+        DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(tau == 0 ? (size_t)L.n : (size_t)L.dpat.nnz);
+        k::gather_values(s, L.dpat.nnz, L.dvmap.p, S_val, Sv.p);
+        if (tau == 0) k::gather_values_i(s, L.n, L.d_perm.p, M_val, Mv.p);
+        else k::gather_values(s, L.dpat.nnz, L.dvmap.p, M_val, Mv.p);
+        int negp = factor_level(ctx, h, L, Sv.p, tau == 0 ? nullptr : Mv.p, tau == 0 ? Mv.p : nullptr, mu);
+        DevBuf<double> X((size_t)L.n * kk);
+        k::gather_rows(s, L.n, kk, L.d_perm.p, B, ldb, X.p, kk);
+        solve_level(ctx, h, L, X.p, kk, kk);
+        k::gather_rows(s, L.n, kk, L.d_iperm.p, X.p, kk, B, ldb);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        if (neg) *neg = negp;
+    });
+}
+
+}  // extern "C"

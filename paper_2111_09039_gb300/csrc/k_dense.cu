@@ -1,0 +1,549 @@
+// Dense FP64 kernels of the subspace iteration (Alg. 1):
+//   gram        S_bar = Psi^T (S Psi), M_bar = Psi^T (M Psi)  (tall-skinny, split-K)
+//   gemm_nn     Phi = Psi Phi_bar                                (basis update)
+//   col_dots    column M-norms, residual sums of eq. conv2
+//   ritz        S_bar Phi_bar = M_bar Phi_bar Lambda_bar: M_bar = L D L^T
+//               (front kernels on one dense front), A = C^-1 S_bar C^-T with
+//               C = L D^1/2, cyclic parallel Jacobi on A (one cooperative
+//               launch per sweep, round-robin pairing), Phi_bar = C^-T V,
+//               eigenpairs sorted ascending.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+
+#include "common.h"
+#include "host.h"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace hsim {
+namespace k {
+
+namespace {
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+constexpr int TB = 64;  // output tile
+constexpr int TK = 16;  // k step
+
+// G[i0:i0+64, j0:j0+64] += sum_{r in chunk} A[r, i] B[r, j]
+__global__ void __launch_bounds__(256) k_gram(int n, int ka, int kb, const double *__restrict__ A, int lda,
+                                              const double *__restrict__ B, int ldb, double *__restrict__ G,
+                                              int ldg, int rows_per_split, int lower_only) {
+    const int ti = blockIdx.x, tj = blockIdx.y;
+    if (lower_only && tj > ti) return;
+    const int i0 = ti * TB, j0 = tj * TB;
+    const int r_beg = blockIdx.z * rows_per_split;
+    const int r_end = min(n, r_beg + rows_per_split);
+    __shared__ double As[TK][TB];
+    __shared__ double Bs[TK][TB];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int r0 = r_beg; r0 < r_end; r0 += TK) {
+        for (int idx = threadIdx.x; idx < TK * TB; idx += 256) {
+            int c = idx & 63, rr = idx >> 6;
+            int r = r0 + rr;
+            As[rr][c] = (r < r_end && i0 + c < ka) ? A[(size_t)r * lda + i0 + c] : 0.0;
+            Bs[rr][c] = (r < r_end && j0 + c < kb) ? B[(size_t)r * ldb + j0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < TK; ++rr) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[rr][ty + 16 * u];
+                b[u] = Bs[rr][tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int i = i0 + ty + 16 * u;
+        if (i >= ka) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int j = j0 + tx + 16 * v;
+            if (j < kb && (!lower_only || j <= i)) atomicAdd(&G[(size_t)i * ldg + j], acc[u][v]);
+        }
+    }
+}
+
+__global__ void k_mirror_lower(int k, double *__restrict__ G, int ldg) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    if (j > i) G[(size_t)i * ldg + j] = G[(size_t)j * ldg + i];
+}
+
+// C[r0:r0+64, j0:j0+64] = A[r, :] B[:, j]
+__global__ void __launch_bounds__(256) k_gemm_nn(int n, int kk, int m, const double *__restrict__ A, int lda,
+                                                 const double *__restrict__ B, int ldb, double *__restrict__ C,
+                                                 int ldc) {
+    const int r0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
+    __shared__ double As[TK][TB + 1];
+    __shared__ double Bs[TK][TB];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < kk; k0 += TK) {
+        for (int idx = threadIdx.x; idx < TK * TB; idx += 256) {
+            int c = idx % TK, r = idx / TK;  // A tile: 64 rows x 16 cols
+            As[c][r] = (r0 + r < n && k0 + c < kk) ? A[(size_t)(r0 + r) * lda + k0 + c] : 0.0;
+            int jj = idx & 63, kr = idx >> 6;  // B tile: 16 rows x 64 cols
+            Bs[kr][jj] = (k0 + kr < kk && j0 + jj < m) ? B[(size_t)(k0 + kr) * ldb + j0 + jj] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < TK; ++c) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[c][ty + 16 * u];
+                b[u] = Bs[c][tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int r = r0 + ty + 16 * u;
+        if (r >= n) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int j = j0 + tx + 16 * v;
+            if (j < m) C[(size_t)r * ldc + j] = acc[u][v];
+        }
+    }
+}
+
+constexpr int kRowsPerBlock = 256;
+
+__global__ void k_col_dots(int n, int k, const double *__restrict__ X, int ldx, const double *__restrict__ Y, int ldy,
+                           const double *__restrict__ d, double *__restrict__ w) {
+    const int r_beg = blockIdx.x * kRowsPerBlock;
+    const int r_end = min(n, r_beg + kRowsPerBlock);
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
+        double acc = 0.0;
+        for (int r = r_beg; r < r_end; ++r) {
+            double v = X[(size_t)r * ldx + j] * Y[(size_t)r * ldy + j];
+            acc += d ? v * d[r] : v;
+        }
+        atomicAdd(&w[j], acc);
+    }
+}
+
+__global__ void k_scale_cols_rsqrt(int n, int k, const double *__restrict__ w, double *__restrict__ X, int ldx) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    X[(size_t)i * ldx + j] *= rsqrt(w[j]);
+}
+
+__global__ void k_residual_sums(int n, int k, const double *__restrict__ SP, int lds, const double *__restrict__ MP,
+                                int ldm, const double *__restrict__ lam, const double *__restrict__ dinv,
+                                double *__restrict__ out) {
+    const int r_beg = blockIdx.x * kRowsPerBlock;
+    const int r_end = min(n, r_beg + kRowsPerBlock);
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
+        double l = lam[j];
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int r = r_beg; r < r_end; ++r) {
+            double s = SP[(size_t)r * lds + j], m = MP[(size_t)r * ldm + j];
+            double rr = s - l * m;
+            double w = dinv ? dinv[r] : 1.0;
+            a0 += w * rr * rr;
+            a1 += w * s * s;
+            a2 += w * m * m;
+        }
+        atomicAdd(&out[3 * j], a0);
+        atomicAdd(&out[3 * j + 1], a1);
+        atomicAdd(&out[3 * j + 2], a2);
+    }
+}
+
+__global__ void k_transpose(int k, const double *__restrict__ X, int ldx, double *__restrict__ Y, int ldy) {
+    __shared__ double t[32][33];
+    int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        int r = by + yy, c = bx + threadIdx.x;
+        if (r < k && c < k) t[yy][threadIdx.x] = X[(size_t)r * ldx + c];
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        int r = bx + yy, c = by + threadIdx.x;
+        if (r < k && c < k) Y[(size_t)r * ldy + c] = t[threadIdx.x][yy];
+    }
+}
+
+// X[i, :] *= f(d[i]):  mode 0: 1/sqrt(d), mode 1: sqrt(d)
+__global__ void k_row_scale_sqrt(int k, const double *__restrict__ d, double *__restrict__ X, int ldx, int mode) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    double s = mode == 0 ? rsqrt(d[i]) : sqrt(d[i]);
+    X[(size_t)i * ldx + j] *= s;
+}
+
+__global__ void k_symmetrize(int k, double *__restrict__ A, int lda) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    if (j <= i) return;
+    double v = 0.5 * (A[(size_t)i * lda + j] + A[(size_t)j * lda + i]);
+    A[(size_t)i * lda + j] = v;
+    A[(size_t)j * lda + i] = v;
+}
+
+__global__ void k_identity(int k, double *__restrict__ V, int ldv) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    V[(size_t)i * ldv + j] = (i == j) ? 1.0 : 0.0;
+}
+
+// ---- cyclic parallel Jacobi -------------------------------------------------
+// Round-robin (circle) pairing of m (even) players over m - 1 rounds:
+// player m-1 meets r; for t = 1..m/2-1, (r + t) meets (r - t) mod (m - 1).
+__device__ __forceinline__ void pairing(int i, int r, int m, int &partner, int &pair_id, int &first) {
+    const int mm = m - 1;
+    if (i == mm) {
+        partner = r;
+        pair_id = 0;
+        first = 0;
+        return;
+    }
+    int d = i - r;
+    d %= mm;
+    if (d < 0) d += mm;
+    if (d == 0) {
+        partner = mm;
+        pair_id = 0;
+        first = 1;
+        return;
+    }
+    if (d <= (m - 2) / 2) {
+        pair_id = d;
+        partner = ((r - d) % mm + mm) % mm;
+        first = 1;
+    } else {
+        int t = mm - d;
+        pair_id = t;
+        partner = (r + t) % mm;
+        first = 0;
+    }
+}
+
+// column i of the rotation J restricted to i's pair: J[a][i] for a = first, second
+__device__ __forceinline__ void jcol(int first, double c, double s, double &jf, double &js) {
+    if (first) { jf = c; js = -s; }
+    else { jf = s; js = c; }
+}
+
+__global__ void k_jacobi_sweep(int k, int m, double *A, double *A2, double *V, double *V2, double *cs, int lda,
+                               double tol, double abs_tol, unsigned long long *rotations) {
+    cg::grid_group grid = cg::this_grid();
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int npairs = m / 2;
+    unsigned long long local_rot = 0;
+    for (int r = 0; r < m - 1; ++r) {
+        // rotations of this round
+        for (int64_t pidx = tid; pidx < npairs; pidx += nthreads) {
+            int p, q;
+            if (pidx == 0) {
+                p = r;
+                q = m - 1;
+            } else {
+                p = (r + (int)pidx) % (m - 1);
+                q = ((r - (int)pidx) % (m - 1) + (m - 1)) % (m - 1);
+            }
+            double c = 1.0, s = 0.0;
+            if (p < k && q < k) {
+                double app = A[(size_t)p * lda + p], aqq = A[(size_t)q * lda + q], apq = A[(size_t)p * lda + q];
+                if (fabs(apq) > abs_tol && fabs(apq) > tol * sqrt(fabs(app) * fabs(aqq))) {
+                    double theta = (aqq - app) / (2.0 * apq);
+                    double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + hypot(theta, 1.0));
+                    c = 1.0 / sqrt(1.0 + t * t);
+                    s = t * c;
+                    ++local_rot;
+                }
+            }
+            cs[2 * pidx] = c;
+            cs[2 * pidx + 1] = s;
+        }
+        grid.sync();
+        // A2 = J^T A J,  V2 = V J
+        for (int64_t idx = tid; idx < (int64_t)k * k; idx += nthreads) {
+            int i = (int)(idx / k), j = (int)(idx % k);
+            int pi_, idi, fi, pj_, idj, fj;
+            pairing(i, r, m, pi_, idi, fi);
+            pairing(j, r, m, pj_, idj, fj);
+            double ci = cs[2 * idi], si = cs[2 * idi + 1], cj = cs[2 * idj], sj = cs[2 * idj + 1];
+            // pair members of i: (ai0 = first, ai1 = second)
+            int ai0 = fi ? i : pi_, ai1 = fi ? pi_ : i;
+            int aj0 = fj ? j : pj_, aj1 = fj ? pj_ : j;
+            double jif, jis, jjf, jjs;
+            jcol(fi, ci, si, jif, jis);
+            jcol(fj, cj, sj, jjf, jjs);
+            if (ai1 >= k) { jif = (ai0 == i) ? 1.0 : 0.0; jis = 0.0; }
+            if (ai0 >= k) { jif = 0.0; jis = (ai1 == i) ? 1.0 : 0.0; }
+            if (aj1 >= k) { jjf = (aj0 == j) ? 1.0 : 0.0; jjs = 0.0; }
+            if (aj0 >= k) { jjf = 0.0; jjs = (aj1 == j) ? 1.0 : 0.0; }
+            double v = 0.0;
+            if (ai0 < k) {
+                double row0 = 0.0;
+                if (aj0 < k) row0 += A[(size_t)ai0 * lda + aj0] * jjf;
+                if (aj1 < k) row0 += A[(size_t)ai0 * lda + aj1] * jjs;
+                v += jif * row0;
+            }
+            if (ai1 < k) {
+                double row1 = 0.0;
+                if (aj0 < k) row1 += A[(size_t)ai1 * lda + aj0] * jjf;
+                if (aj1 < k) row1 += A[(size_t)ai1 * lda + aj1] * jjs;
+                v += jis * row1;
+            }
+            A2[(size_t)i * lda + j] = v;
+            double w = 0.0;
+            if (aj0 < k) w += V[(size_t)i * lda + aj0] * jjf;
+            if (aj1 < k) w += V[(size_t)i * lda + aj1] * jjs;
+            V2[(size_t)i * lda + j] = w;
+        }
+        grid.sync();
+        double *t = A; A = A2; A2 = t;
+        t = V; V = V2; V2 = t;
+    }
+    if (local_rot) atomicAdd(rotations, local_rot);
+}
+
+// rank of each eigenvalue in ascending order (ties by index)
+__global__ void k_rank(int k, const double *__restrict__ A, int lda, int *__restrict__ rank,
+                       double *__restrict__ evals_sorted) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k) return;
+    double li = A[(size_t)i * lda + i];
+    int r = 0;
+    for (int j = 0; j < k; ++j) {
+        double lj = A[(size_t)j * lda + j];
+        r += (lj < li) || (lj == li && j < i);
+    }
+    rank[i] = r;
+    evals_sorted[r] = li;
+}
+
+// Y[:, rank[j]] = X[:, j]
+__global__ void k_permute_cols(int k, const int *__restrict__ rank, const double *__restrict__ X, int ldx,
+                               double *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    Y[(size_t)i * ldy + rank[j]] = X[(size_t)i * ldx + j];
+}
+
+// one dense front of size k (pivots 0..k-1), cached per size
+struct DenseFront {
+    DevBuf<int64_t> foff, rows_off, relmap_off;
+    DevBuf<int> nf, ns, pstart, rows, relmap, node;
+    FrontDev fd{};
+};
+
+DenseFront &dense_front(int k, cudaStream_t s) {
+    static std::mutex mu;
+    static std::map<int, std::unique_ptr<DenseFront>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int key = dev * 1000000 + k;
+    auto it = cache.find(key);
+    if (it != cache.end()) return *it->second;
+    auto d = std::make_unique<DenseFront>();
+    d->foff.upload(std::vector<int64_t>{0, (int64_t)k * k}, s);
+    d->rows_off.upload(std::vector<int64_t>{0, (int64_t)k}, s);
+    d->relmap_off.upload(std::vector<int64_t>{0, 0}, s);
+    d->nf.upload(std::vector<int>{k}, s);
+    d->ns.upload(std::vector<int>{k}, s);
+    d->pstart.upload(std::vector<int>{0}, s);
+    std::vector<int> rows(k);
+    for (int i = 0; i < k; ++i) rows[i] = i;
+    d->rows.upload(rows, s);
+    d->relmap.upload(std::vector<int>{0}, s);
+    d->node.upload(std::vector<int>{0}, s);
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    d->fd = FrontDev{d->foff.p, d->nf.p, d->ns.p, d->pstart.p, d->rows_off.p, d->rows.p, d->relmap_off.p, d->relmap.p};
+    auto &ref = *d;
+    cache[key] = std::move(d);
+    return ref;
+}
+
+}  // namespace
+
+void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb, double *G,
+          int ldg, bool lower_only) {
+    for (int i = 0; i < ka; ++i) HSIM_CUDA(cudaMemsetAsync(G + (size_t)i * ldg, 0, (size_t)kb * sizeof(double), s));
+    if (n <= 0 || ka <= 0 || kb <= 0) return;
+    int ti = cdiv(ka, TB), tj = cdiv(kb, TB);
+    int64_t tiles = lower_only ? (int64_t)ti * (ti + 1) / 2 : (int64_t)ti * tj;
+    int64_t want = std::max<int64_t>(1, (4LL * sm_count() + tiles - 1) / tiles);
+    int64_t rows = std::max<int64_t>(256, (n + want - 1) / want);
+    rows = (rows + TK - 1) / TK * TK;
+    unsigned splits = cdiv(n, rows);
+    dim3 g(ti, tj, splits);
+    k_gram<<<g, 256, 0, s>>>(n, ka, kb, A, lda, B, ldb, G, ldg, (int)rows, lower_only ? 1 : 0);
+    HSIM_LAUNCHED();
+    if (lower_only) {
+        k_mirror_lower<<<cdiv((int64_t)ka * ka, 256), 256, 0, s>>>(ka, G, ldg);
+        HSIM_LAUNCHED();
+    }
+}
+
+void gemm_nn(cudaStream_t s, int n, int kk, int m, const double *A, int lda, const double *B, int ldb, double *C,
+             int ldc) {
+    if (n <= 0 || m <= 0) return;
+    dim3 g(cdiv(n, TB), cdiv(m, TB));
+    k_gemm_nn<<<g, 256, 0, s>>>(n, kk, m, A, lda, B, ldb, C, ldc);
+    HSIM_LAUNCHED();
+}
+
+void col_dots(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y, int ldy, const double *d,
+              double *w) {
+    HSIM_CUDA(cudaMemsetAsync(w, 0, (size_t)k * sizeof(double), s));
+    if (n <= 0 || k <= 0) return;
+    dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
+    k_col_dots<<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, d, w);
+    HSIM_LAUNCHED();
+}
+
+void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, double *X, int ldx) {
+    if (n <= 0 || k <= 0) return;
+    k_scale_cols_rsqrt<<<cdiv((int64_t)n * k, 256), 256, 0, s>>>(n, k, w, X, ldx);
+    HSIM_LAUNCHED();
+}
+
+void residual_sums(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
+                   const double *lam, const double *dinv, double *out) {
+    HSIM_CUDA(cudaMemsetAsync(out, 0, (size_t)3 * k * sizeof(double), s));
+    if (n <= 0 || k <= 0) return;
+    dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
+    k_residual_sums<<<g, 256, 0, s>>>(n, k, SP, lds, MP, ldm, lam, dinv, out);
+    HSIM_LAUNCHED();
+}
+
+size_t ritz_work_size(int k) { return (size_t)6 * k * k + 4 * (size_t)k + 64; }
+
+int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals, double *X,
+         int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host) {
+    // work layout: F (k*k) | A (k*k) | A2 (k*k) | V (k*k) | V2 (k*k) | W (k*k) | d (k) | cs (k+2) | misc
+    const size_t kk = (size_t)k * k;
+    double *F = work, *A = work + kk, *A2 = work + 2 * kk, *V = work + 3 * kk, *V2 = work + 4 * kk, *W = work + 5 * kk;
+    double *d = work + 6 * kk;
+    double *cs = d + k;
+    unsigned long long *rot = reinterpret_cast<unsigned long long *>(cs + k + 2);
+    DenseFront &df = dense_front(k, s);
+    const int *node = df.node.p;
+    // F = M_bar (symmetric: row-major == column-major)
+    copy_matrix(s, k, k, Mbar, ldm, F, k);
+    HSIM_CUDA(cudaMemsetAsync(flag_dev, 0, 4 * sizeof(int), s));
+    const int steps = (k + kPanel - 1) / kPanel;
+    for (int st = 0; st < steps; ++st) {
+        int k0 = st * kPanel;
+        int kb = std::min(kPanel, k - k0);
+        front_panel(s, df.fd, node, 1, k0, k - k0 - kb, F, 1e-300, flag_dev);
+        front_update(s, df.fd, node, 1, k0, k - k0 - kb, F);
+    }
+    front_diag(s, df.fd, node, 1, F, d, flag_dev + 2);
+    HSIM_CUDA(cudaMemcpyAsync(flag_host, flag_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    if (flag_host[0] != 0 || flag_host[2] != 0) return 1;  // not positive definite
+    // W = C^-1 S_bar = D^-1/2 L^-1 S_bar
+    copy_matrix(s, k, k, Sbar, lds, W, k);
+    auto forward = [&](double *Y) {
+        for (int st = 0; st < steps; ++st) {
+            int k0 = st * kPanel;
+            int kb = std::min(kPanel, k - k0);
+            solve_fwd_tri(s, df.fd, node, 1, k0, F, k, Y, k);
+            solve_fwd_upd(s, df.fd, node, 1, k0, k - k0 - kb, F, k, Y, k);
+        }
+        k_row_scale_sqrt<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, d, Y, k, 0);
+        HSIM_LAUNCHED();
+    };
+    forward(W);
+    dim3 tg(cdiv(k, 32), cdiv(k, 32)), tb(32, 8);
+    k_transpose<<<tg, tb, 0, s>>>(k, W, k, A, k);
+    HSIM_LAUNCHED();
+    forward(A);
+    // symmetrise against rounding: A = (A + A^T)/2
+    k_symmetrize<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, A, k);
+    HSIM_LAUNCHED();
+    k_identity<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, V, k);
+    HSIM_LAUNCHED();
+    // Jacobi sweeps
+    const int m = (k % 2) ? k + 1 : k;
+    int blocks_per_sm = 0;
+    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_jacobi_sweep, 256, 0));
+    int grid = std::max(1, std::min(blocks_per_sm, 4) * sm_count());
+    int64_t need = std::max<int64_t>((int64_t)k * k, m / 2);
+    grid = (int)std::min<int64_t>(grid, (need + 255) / 256);
+    grid = std::max(grid, 1);
+    double tol = 1e-15, abs_tol = 1e-300;
+    int sw = 0;
+    unsigned long long hrot = 1;
+    double *pA = A, *pA2 = A2, *pV = V, *pV2 = V2;
+    while (hrot != 0 && sw < 40) {
+        HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        int kk_ = k, mm = m, ld = k;
+        void *args[] = {&kk_, &mm, &pA, &pA2, &pV, &pV2, &cs, &ld, &tol, &abs_tol, &rot};
+        HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_jacobi_sweep, dim3(grid), dim3(256), args, 0, s));
+        HSIM_LAUNCHED();
+        // after m-1 rounds the newest data is in pA if m-1 is even, else pA2
+        if ((m - 1) % 2 == 1) {
+            std::swap(pA, pA2);
+            std::swap(pV, pV2);
+        }
+        HSIM_CUDA(cudaMemcpyAsync(&hrot, rot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        ++sw;
+    }
+    if (sweeps) *sweeps = sw;
+    // X = C^-T V = L^-T D^-1/2 V, then columns sorted by eigenvalue
+    int *rk = reinterpret_cast<int *>(W);
+    k_rank<<<cdiv(k, 128), 128, 0, s>>>(k, pA, k, rk, evals);
+    HSIM_LAUNCHED();
+    k_row_scale_sqrt<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, d, pV, k, 0);
+    HSIM_LAUNCHED();
+    for (int st = steps - 1; st >= 0; --st) {
+        int k0 = st * kPanel;
+        int kb = std::min(kPanel, k - k0);
+        solve_bwd_upd(s, df.fd, node, 1, k0, k - k0 - kb, F, k, pV, k);
+        solve_bwd_tri(s, df.fd, node, 1, k0, F, k, pV, k);
+    }
+    k_permute_cols<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, rk, pV, k, X, ldx);
+    HSIM_LAUNCHED();
+    return 0;
+}
+
+}  // namespace k
+}  // namespace hsim

@@ -1,0 +1,397 @@
+// Sparse kernels of the HSIM hot path: cotan/mass assembly (Sec. 3.1),
+// CSR SpMM for S Psi, M Psi (Alg. 1) and the prolongation U Phi (Alg. 3),
+// and the numeric Galerkin products U^T A U (Alg. 3), plus permutation and
+// layout helpers.
+//
+// SpMM is HBM-bound: one warp per sparse row, lanes stride over the k dense
+// columns so every X row read is a contiguous, coalesced 8k-byte segment; the
+// row's nonzeros are broadcast from registers with warp shuffles.
+#include <cuda_runtime.h>
+
+#include "common.h"
+#include "kernels.h"
+
+namespace hsim {
+namespace k {
+
+namespace {
+
+constexpr int kWarp = 32;
+
+inline unsigned grid1d(int64_t work, int per_block) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > 2147483647LL) g = 2147483647LL;
+    return (unsigned)g;
+}
+
+__global__ void k_triangle_geometry(int m, const int *__restrict__ F, const double *__restrict__ V,
+                                    const double *__restrict__ L2, double *__restrict__ cot,
+                                    double *__restrict__ area) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    double l[3];
+    for (int k = 0; k < 3; ++k) {
+        if (V) {
+            const double *a = V + 3 * (size_t)F[3 * t + (k + 1) % 3];
+            const double *b = V + 3 * (size_t)F[3 * t + (k + 2) % 3];
+            double e0 = __dsub_rn(b[0], a[0]), e1 = __dsub_rn(b[1], a[1]), e2 = __dsub_rn(b[2], a[2]);
+            l[k] = __dadd_rn(__dadd_rn(__dmul_rn(e0, e0), __dmul_rn(e1, e1)), __dmul_rn(e2, e2));
+        } else {
+            l[k] = L2[3 * (size_t)t + k];
+        }
+    }
+    double s16 = 2.0 * (l[0] * l[1] + l[1] * l[2] + l[2] * l[0]) - (l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    double A = 0.25 * sqrt(fmax(s16, 0.0));
+    area[t] = A;
+    for (int k = 0; k < 3; ++k)
+        cot[3 * (size_t)t + k] = (l[(k + 1) % 3] + l[(k + 2) % 3] - l[k]) / (4.0 * A);
+}
+
+__global__ void k_assemble_sm(int n, const int *__restrict__ ptr, const int *__restrict__ col,
+                              const int *__restrict__ ecot, const double *__restrict__ cot,
+                              const int *__restrict__ vt_ptr, const int *__restrict__ vt_idx,
+                              const double *__restrict__ area, double *__restrict__ S,
+                              double *__restrict__ M) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double diag = 0.0;
+    int de = -1;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) {
+        if (col[e] == i) {
+            de = e;
+            continue;
+        }
+        double c = 0.0;
+        int a = ecot[2 * (size_t)e], b = ecot[2 * (size_t)e + 1];
+        if (a >= 0) c += cot[a];
+        if (b >= 0) c += cot[b];
+        double v = -0.5 * c;
+        S[e] = v;
+        diag -= v;
+    }
+    if (de >= 0) S[de] = diag;
+    double mm = 0.0;
+    for (int e = vt_ptr[i]; e < vt_ptr[i + 1]; ++e) mm += area[vt_idx[e]] / 3.0;
+    M[i] = mm;
+}
+
+// One warp per row; each lane owns columns lane, lane+32, ...  Up to
+// kMaxCols/32 accumulators per lane are kept in registers; wider k is done in
+// several column passes.
+template <typename T, int kChunk>
+__global__ void k_spmm(int n_rows, const int *__restrict__ ptr, const int *__restrict__ col,
+                       const T *__restrict__ val, int k, const T *__restrict__ X, int ldx,
+                       T *__restrict__ Y, int ldy) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warps = blockDim.x / kWarp;
+    int64_t row = (int64_t)blockIdx.x * warps + threadIdx.x / kWarp;
+    if (row >= n_rows) return;
+    const int beg = ptr[row], end = ptr[row + 1];
+    for (int c0 = 0; c0 < k; c0 += kChunk * kWarp) {
+        T acc[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) acc[u] = T(0);
+        for (int e0 = beg; e0 < end; e0 += kWarp) {
+            int my_c = 0;
+            T my_v = T(0);
+            if (e0 + lane < end) {
+                my_c = col[e0 + lane];
+                my_v = val[e0 + lane];
+            }
+            const int cnt = min(kWarp, end - e0);
+            for (int t = 0; t < cnt; ++t) {
+                int c = __shfl_sync(0xffffffffu, my_c, t);
+                T v = __shfl_sync(0xffffffffu, my_v, t);
+                const T *xr = X + (size_t)c * ldx;
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) {
+                    int j = c0 + u * kWarp + lane;
+                    if (j < k) acc[u] += v * xr[j];
+                }
+            }
+        }
+        T *yr = Y + (size_t)row * ldy;
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            int j = c0 + u * kWarp + lane;
+            if (j < k) yr[j] = acc[u];
+        }
+    }
+}
+
+__global__ void k_diag_scale(int n, int k, const double *__restrict__ d, const double *__restrict__ X, int ldx,
+                             double *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    Y[(size_t)i * ldy + j] = d[i] * X[(size_t)i * ldx + j];
+}
+
+__device__ __forceinline__ int find_col(const int *__restrict__ c, int lo, int hi, int key) {
+    // position of key in the sorted range c[lo, hi), or -1
+    const int end = hi;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (c[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < end && c[lo] == key) ? lo : -1;
+}
+
+// T[i, j] = sum_k A[i,k] U[k,j] for every (i, j) of T's pattern; one warp per
+// row, one lane per output entry.
+__global__ void k_galerkin_au(int n, const int *__restrict__ a_ptr, const int *__restrict__ a_col,
+                              const double *__restrict__ a_val, const int *__restrict__ u_ptr,
+                              const int *__restrict__ u_col, const double *__restrict__ u_val,
+                              const int *__restrict__ t_ptr, const int *__restrict__ t_col,
+                              double *__restrict__ t_val) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+    if (i >= n) return;
+    for (int e = t_ptr[i] + lane; e < t_ptr[i + 1]; e += kWarp) {
+        int j = t_col[e];
+        double acc = 0.0;
+        for (int f = a_ptr[i]; f < a_ptr[i + 1]; ++f) {
+            int kk = a_col[f];
+            int pos = find_col(u_col, u_ptr[kk], u_ptr[kk + 1], j);
+            if (pos >= 0) acc += a_val[f] * u_val[pos];
+        }
+        t_val[e] = acc;
+    }
+}
+
+__global__ void k_galerkin_utt(int nc, const int *__restrict__ ut_ptr, const int *__restrict__ ut_col,
+                               const double *__restrict__ ut_val, const int *__restrict__ t_ptr,
+                               const int *__restrict__ t_col, const double *__restrict__ t_val,
+                               const int *__restrict__ c_ptr, const int *__restrict__ c_col,
+                               double *__restrict__ c_val) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    int64_t a = (int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+    if (a >= nc) return;
+    for (int e = c_ptr[a] + lane; e < c_ptr[a + 1]; e += kWarp) {
+        int b = c_col[e];
+        double acc = 0.0;
+        for (int f = ut_ptr[a]; f < ut_ptr[a + 1]; ++f) {
+            int i = ut_col[f];
+            int pos = find_col(t_col, t_ptr[i], t_ptr[i + 1], b);
+            if (pos >= 0) acc += ut_val[f] * t_val[pos];
+        }
+        c_val[e] = acc;
+    }
+}
+
+__global__ void k_gather_values(int64_t n, const int64_t *__restrict__ map, const double *__restrict__ in,
+                                double *__restrict__ out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = in[map[e]];
+}
+__global__ void k_gather_values_i(int64_t n, const int *__restrict__ map, const double *__restrict__ in,
+                                  double *__restrict__ out) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = in[map[e]];
+}
+
+__global__ void k_gather_rows(int n, int k, const int *__restrict__ perm, const double *__restrict__ X, int ldx,
+                              double *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    Y[(size_t)i * ldy + j] = X[(size_t)perm[i] * ldx + j];
+}
+
+__global__ void k_copy_matrix(int rows, int cols, const double *__restrict__ X, int ldx, double *__restrict__ Y,
+                              int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j];
+}
+
+__global__ void k_densify(int n, const int *__restrict__ ptr, const int *__restrict__ col,
+                          const double *__restrict__ val, double *__restrict__ D) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) D[(size_t)i * n + col[e]] = val[e];
+}
+__global__ void k_densify_diag(int n, const double *__restrict__ d, double *__restrict__ D) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) D[(size_t)i * n + i] = d[i];
+}
+
+// per column j: index of the entry of largest magnitude (lowest row on ties),
+// reduced over rows by one block per column
+__global__ void k_col_sign(int n, const double *__restrict__ Phi, int ldp, double *__restrict__ sign) {
+    int j = blockIdx.x;
+    double best = -1.0, bv = 0.0;
+    int bi = 0x7fffffff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double v = Phi[(size_t)i * ldp + j];
+        double a = fabs(v);
+        if (a > best || (a == best && i < bi)) { best = a; bi = i; bv = v; }
+    }
+    __shared__ double sb[256], sv[256];
+    __shared__ int si[256];
+    sb[threadIdx.x] = best;
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            int o = threadIdx.x + w;
+            if (sb[o] > sb[threadIdx.x] || (sb[o] == sb[threadIdx.x] && si[o] < si[threadIdx.x])) {
+                sb[threadIdx.x] = sb[o];
+                sv[threadIdx.x] = sv[o];
+                si[threadIdx.x] = si[o];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sign[j] = sv[0] < 0.0 ? -1.0 : 1.0;
+}
+
+__global__ void k_output_evecs(int n, int p, const int *__restrict__ iperm, const double *__restrict__ Phi, int ldp,
+                               const double *__restrict__ sign, double *__restrict__ out) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * p) return;
+    int j = (int)(idx / n), i = (int)(idx % n);
+    int r = iperm ? iperm[i] : i;
+    out[idx] = sign[j] * Phi[(size_t)r * ldp + j];
+}
+
+__global__ void k_reciprocal(int n, const double *__restrict__ x, double *__restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = 1.0 / x[i];
+}
+
+__global__ void k_f2d(int64_t n, const float *__restrict__ x, double *__restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (double)x[i];
+}
+__global__ void k_d2f(int64_t n, const double *__restrict__ x, float *__restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+
+}  // namespace
+
+void triangle_geometry(cudaStream_t s, int m, const int *F, const double *V, const double *L2, double *cot,
+                       double *area) {
+    k_triangle_geometry<<<grid1d(m, 256), 256, 0, s>>>(m, F, V, L2, cot, area);
+    HSIM_LAUNCHED();
+}
+
+void assemble_sm(cudaStream_t s, int n, const int *ptr, const int *col, const int *ecot, const double *cot,
+                 const int *vt_ptr, const int *vt_idx, const double *area, double *S_val, double *M_diag) {
+    k_assemble_sm<<<grid1d(n, 256), 256, 0, s>>>(n, ptr, col, ecot, cot, vt_ptr, vt_idx, area, S_val, M_diag);
+    HSIM_LAUNCHED();
+}
+
+void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *val, int k, const double *X,
+          int ldx, double *Y, int ldy) {
+    if (n_rows <= 0 || k <= 0) return;
+    const int warps = 8;
+    unsigned g = grid1d(n_rows, warps);
+    if (k <= 32 * 8)
+        k_spmm<double, 8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+    else
+        k_spmm<double, 24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void spmm_f(cudaStream_t s, int n_rows, const int *ptr, const int *col, const float *val, int k, const float *X,
+            int ldx, float *Y, int ldy) {
+    if (n_rows <= 0 || k <= 0) return;
+    const int warps = 8;
+    unsigned g = grid1d(n_rows, warps);
+    if (k <= 32 * 8)
+        k_spmm<float, 8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+    else
+        k_spmm<float, 24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void diag_scale(cudaStream_t s, int n, int k, const double *d, const double *X, int ldx, double *Y, int ldy) {
+    if (n <= 0 || k <= 0) return;
+    k_diag_scale<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, d, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void galerkin_au(cudaStream_t s, int n, const int *a_ptr, const int *a_col, const double *a_val, const int *u_ptr,
+                 const int *u_col, const double *u_val, const int *t_ptr, const int *t_col, double *t_val) {
+    k_galerkin_au<<<grid1d(n, 8), 256, 0, s>>>(n, a_ptr, a_col, a_val, u_ptr, u_col, u_val, t_ptr, t_col, t_val);
+    HSIM_LAUNCHED();
+}
+
+void galerkin_utt(cudaStream_t s, int nc, const int *ut_ptr, const int *ut_col, const double *ut_val,
+                  const int *t_ptr, const int *t_col, const double *t_val, const int *c_ptr, const int *c_col,
+                  double *c_val) {
+    k_galerkin_utt<<<grid1d(nc, 8), 256, 0, s>>>(nc, ut_ptr, ut_col, ut_val, t_ptr, t_col, t_val, c_ptr, c_col,
+                                                 c_val);
+    HSIM_LAUNCHED();
+}
+
+void gather_values(cudaStream_t s, int64_t n, const int64_t *map, const double *in, double *out) {
+    if (n <= 0) return;
+    k_gather_values<<<grid1d(n, 256), 256, 0, s>>>(n, map, in, out);
+    HSIM_LAUNCHED();
+}
+void gather_values_i(cudaStream_t s, int64_t n, const int *map, const double *in, double *out) {
+    if (n <= 0) return;
+    k_gather_values_i<<<grid1d(n, 256), 256, 0, s>>>(n, map, in, out);
+    HSIM_LAUNCHED();
+}
+
+void gather_rows(cudaStream_t s, int n, int k, const int *perm, const double *X, int ldx, double *Y, int ldy) {
+    if (n <= 0 || k <= 0) return;
+    k_gather_rows<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, perm, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void copy_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, double *Y, int ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_copy_matrix<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void densify(cudaStream_t s, int n, const int *ptr, const int *col, const double *val, double *D) {
+    HSIM_CUDA(cudaMemsetAsync(D, 0, (size_t)n * n * sizeof(double), s));
+    k_densify<<<grid1d(n, 128), 128, 0, s>>>(n, ptr, col, val, D);
+    HSIM_LAUNCHED();
+}
+void densify_diag(cudaStream_t s, int n, const double *d, double *D) {
+    HSIM_CUDA(cudaMemsetAsync(D, 0, (size_t)n * n * sizeof(double), s));
+    k_densify_diag<<<grid1d(n, 128), 128, 0, s>>>(n, d, D);
+    HSIM_LAUNCHED();
+}
+
+void output_evecs(cudaStream_t s, int n, int p, const int *iperm, const double *Phi, int ldp, double *out,
+                  double *scratch_p) {
+    if (n <= 0 || p <= 0) return;
+    // the sign is decided on the internal-order rows; the entry of largest
+    // magnitude is the same entry whichever order the rows are in, up to ties
+    k_col_sign<<<p, 256, 0, s>>>(n, Phi, ldp, scratch_p);
+    HSIM_LAUNCHED();
+    k_output_evecs<<<grid1d((int64_t)n * p, 256), 256, 0, s>>>(n, p, iperm, Phi, ldp, scratch_p, out);
+    HSIM_LAUNCHED();
+}
+
+void reciprocal(cudaStream_t s, int n, const double *x, double *y) {
+    if (n <= 0) return;
+    k_reciprocal<<<grid1d(n, 256), 256, 0, s>>>(n, x, y);
+    HSIM_LAUNCHED();
+}
+
+void convert_f2d(cudaStream_t s, int64_t n, const float *x, double *y) {
+    if (n <= 0) return;
+    k_f2d<<<grid1d(n, 256), 256, 0, s>>>(n, x, y);
+    HSIM_LAUNCHED();
+}
+void convert_d2f(cudaStream_t s, int64_t n, const double *x, float *y) {
+    if (n <= 0) return;
+    k_d2f<<<grid1d(n, 256), 256, 0, s>>>(n, x, y);
+    HSIM_LAUNCHED();
+}
+
+}  // namespace k
+}  // namespace hsim

@@ -1,0 +1,112 @@
+// Launchers of the HSIM CUDA kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hsim {
+namespace k {
+
+// ---- sparse (k_sparse.cu) -------------------------------------------------
+// per-triangle cotangents and areas from positions or squared lengths
+void triangle_geometry(cudaStream_t s, int m, const int *F, const double *V, const double *L2,
+                       double *cot, double *area);
+// S values in a CSR pattern: off-diagonal -1/2 sum of the opposite cotangents
+// listed in ecot (two slots per entry, -1 = none), diagonal = -row sum;
+// M diagonal = sum of incident areas / 3 (vertex -> triangle CSR vt_ptr/vt_idx)
+void assemble_sm(cudaStream_t s, int n, const int *ptr, const int *col, const int *ecot,
+                 const double *cot, const int *vt_ptr, const int *vt_idx, const double *area,
+                 double *S_val, double *M_diag);
+// Y[r, 0:k] = sum A[r,c] X[c, 0:k]
+void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *val, int k,
+          const double *X, int ldx, double *Y, int ldy);
+void spmm_f(cudaStream_t s, int n_rows, const int *ptr, const int *col, const float *val, int k,
+            const float *X, int ldx, float *Y, int ldy);
+// Y[r, :] = d[r] * X[r, :]
+void diag_scale(cudaStream_t s, int n, int k, const double *d, const double *X, int ldx, double *Y,
+                int ldy);
+// T = A U in a given pattern (rows of A)
+void galerkin_au(cudaStream_t s, int n, const int *a_ptr, const int *a_col, const double *a_val,
+                 const int *u_ptr, const int *u_col, const double *u_val, const int *t_ptr,
+                 const int *t_col, double *t_val);
+// C = U^T T in a given pattern; ut = transpose of U with values
+void galerkin_utt(cudaStream_t s, int nc, const int *ut_ptr, const int *ut_col, const double *ut_val,
+                  const int *t_ptr, const int *t_col, const double *t_val, const int *c_ptr,
+                  const int *c_col, double *c_val);
+// out[e] = in[map[e]]
+void gather_values(cudaStream_t s, int64_t n, const int64_t *map, const double *in, double *out);
+void gather_values_i(cudaStream_t s, int64_t n, const int *map, const double *in, double *out);
+// Y[i, 0:k] = X[perm[i], 0:k]   (row gather)
+void gather_rows(cudaStream_t s, int n, int k, const int *perm, const double *X, int ldx, double *Y,
+                 int ldy);
+// dense row-major n x n from CSR (zero elsewhere)
+void densify(cudaStream_t s, int n, const int *ptr, const int *col, const double *val, double *D);
+void densify_diag(cudaStream_t s, int n, const double *d, double *D);
+// evecs column-major n x p (natural order) from Phi row-major internal
+// (row iperm[i]); sign so that the entry of largest magnitude is positive
+void output_evecs(cudaStream_t s, int n, int p, const int *iperm, const double *Phi, int ldp,
+                  double *out, double *scratch_p);
+void copy_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, double *Y, int ldy);
+// y = 1 / x
+void reciprocal(cudaStream_t s, int n, const double *x, double *y);
+void convert_f2d(cudaStream_t s, int64_t n, const float *x, double *y);
+void convert_d2f(cudaStream_t s, int64_t n, const double *x, float *y);
+
+// ---- dense (k_dense.cu) ---------------------------------------------------
+// G (ka x kb, ld ldg) = A^T B over n rows; G is overwritten
+void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb,
+          double *G, int ldg, bool lower_only);
+// C (n x m) = A (n x k) B (k x m)
+void gemm_nn(cudaStream_t s, int n, int k, int m, const double *A, int lda, const double *B, int ldb,
+             double *C, int ldc);
+// w_j = sum_i X[i,j] * Y[i,j] * (d ? d[i] : 1)   (column dot products, w overwritten)
+void col_dots(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y, int ldy,
+              const double *d, double *w);
+// X[:, j] *= f[j] with f[j] = 1/sqrt(w[j])
+void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, double *X, int ldx);
+// residual sums: out[3j+0] = sum w R^2, +1 = sum w (S Phi)^2, +2 = sum w (M Phi)^2
+// with R = SPhi - lam * MPhi; w = dinv (M^{-1}-norm) or 1 (2-norm)
+void residual_sums(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
+                   const double *lam, const double *dinv, double *out);
+// dense symmetric generalised eigensolver (Cholesky + Jacobi), k x k
+// returns 0 ok, 1 not SPD; sweeps via *sweeps
+int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals,
+         double *X, int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host);
+size_t ritz_work_size(int k);
+
+// ---- fronts (k_front.cu) ----------------------------------------------------
+struct FrontDev {
+    const int64_t *foff;
+    const int *nf, *ns, *pstart;
+    const int64_t *rows_off;
+    const int *rows;
+    const int64_t *relmap_off;
+    const int *relmap;
+};
+void front_assemble(cudaStream_t s, int64_t nnz, const int *row_of, const int *col, const int64_t *dst,
+                    const double *S_val, const double *M_val, const double *M_diag, double mu,
+                    double *arena);
+void front_extend_add(cudaStream_t s, const FrontDev &fd, const int *parent, const int *children,
+                      int n_children, int max_upd, double *arena);
+void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
+                 int max_rows, double *arena, double pivot_tol, int *flags);
+void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
+                  int max_trail, double *arena);
+// max |F_t[i,i]| over the pivots of nodes 0..n_nodes-1 (bit pattern of a
+// non-negative double, atomically maximised into *out)
+void front_maxdiag(cudaStream_t s, const FrontDev &fd, int n_nodes, const double *arena, unsigned long long *out);
+void front_diag(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, const double *arena,
+                double *dpos, int *neg_count);
+void solve_fwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
+                   const double *arena, int k, double *X, int ldx);
+void solve_fwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
+                   int max_rows, const double *arena, int k, double *X, int ldx);
+void solve_diag(cudaStream_t s, int n, int k, const double *dpos, double *X, int ldx);
+void solve_bwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
+                   int max_rows, const double *arena, int k, double *X, int ldx);
+void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
+                   const double *arena, int k, double *X, int ldx);
+
+}  // namespace k
+}  // namespace hsim

@@ -1,0 +1,229 @@
+"""GPU parity of the single steps of the hot path, through the C ABI, against
+the FP64 oracle or plain SciPy/NumPy definitions on the same seeded inputs.
+
+Tolerances: every step here is FP64; the bounds are a few hundred ulps of the
+accumulated magnitudes (sum of |terms|), which leaves room for a different
+summation order and nothing else."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import assembly, galerkin, hierarchy
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def hs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_09039_gb300 import build
+    build.build()
+    import paper_2111_09039_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(hs):
+    return hs.Context(0)
+
+
+def dev(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda:0")
+
+
+def random_csr(n_rows, n_cols, density, seed, empty_rows=()):
+    rng = np.random.default_rng(seed)
+    A = sp.random(n_rows, n_cols, density=density, random_state=rng, format="csr")
+    A = A.tolil()
+    for r in empty_rows:
+        A.rows[r] = []
+        A.data[r] = []
+    A = A.tocsr()
+    A.sort_indices()
+    return A
+
+
+@pytest.mark.parametrize("k", [1, 7, 33, 256, 257, 750, 769])
+def test_spmm_matches_scipy(hs, ctx, k):
+    A = random_csr(1003, 517, 0.02, k, empty_rows=(0, 5, 1002))
+    X = np.random.default_rng(k).standard_normal((517, k))
+    Y = hs.spmm(ctx, dev(A.indptr.astype(np.int32)), dev(A.indices.astype(np.int32)), dev(A.data), dev(X))
+    ref = A @ X
+    bound = 64 * EPS * (abs(A) @ np.abs(X))
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound + 1e-300)
+
+
+def test_spmm_strided_and_empty(hs, ctx):
+    import torch
+    A = random_csr(64, 40, 0.1, 1)
+    Xf = np.random.default_rng(2).standard_normal((40, 20))
+    Xt = dev(Xf)[:, 3:15]  # leading dimension 20, 12 columns
+    Y = hs.spmm(ctx, dev(A.indptr.astype(np.int32)), dev(A.indices.astype(np.int32)), dev(A.data), Xt)
+    np.testing.assert_allclose(Y.cpu().numpy(), A @ Xf[:, 3:15], rtol=1e-13, atol=1e-13)
+    # zero rows: nothing to do, no error
+    Z = hs.spmm(ctx, dev(np.zeros(1, np.int32)), dev(np.zeros(1, np.int32)), dev(np.zeros(1)),
+                torch.zeros((4, 3), dtype=torch.float64, device="cuda:0"))
+    assert Z.shape == (0, 3)
+
+
+@pytest.mark.parametrize("n,ka,kb", [(1, 1, 1), (1000, 30, 30), (4099, 75, 150), (70001, 130, 65)])
+def test_gram_matches_numpy(hs, ctx, n, ka, kb):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, ka))
+    B = rng.standard_normal((n, kb))
+    G = hs.gram(ctx, dev(A), dev(B)).cpu().numpy()
+    bound = 4 * n * EPS * (np.abs(A).T @ np.abs(B))
+    assert np.all(np.abs(G - A.T @ B) <= bound)
+
+
+@pytest.mark.parametrize("n,k,m", [(1, 1, 1), (1000, 30, 30), (4099, 75, 75), (20011, 131, 67)])
+def test_gemm_update_matches_numpy(hs, ctx, n, k, m):
+    rng = np.random.default_rng(k)
+    A = rng.standard_normal((n, k))
+    B = rng.standard_normal((k, m))
+    C = hs.gemm_update(ctx, dev(A), dev(B)).cpu().numpy()
+    bound = 4 * k * EPS * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(C - A @ B) <= bound)
+
+
+def _spd_pair(k, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    M = Q @ np.diag(np.geomspace(1.0, 1.0 / cond, k)) @ Q.T
+    A = rng.standard_normal((k, k))
+    S = A @ A.T
+    return 0.5 * (S + S.T), 0.5 * (M + M.T)
+
+
+@pytest.mark.parametrize("k", [1, 2, 31, 64, 75, 200, 301])
+def test_ritz_matches_scipy_eigh(hs, ctx, k):
+    S, M = _spd_pair(k, k)
+    lam, X, sweeps = hs.ritz(ctx, dev(S), dev(M))
+    lam = lam.cpu().numpy()
+    X = X.cpu().numpy()
+    ref = sla.eigh(S, M, eigvals_only=True)
+    np.testing.assert_allclose(lam, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    np.testing.assert_allclose(X.T @ M @ X, np.eye(k), atol=1e-9)
+    np.testing.assert_allclose(X.T @ S @ X, np.diag(lam), atol=1e-9 * np.abs(ref).max())
+    assert np.all(np.diff(lam) >= 0)
+    assert sweeps <= 30
+
+
+def test_ritz_degenerate_and_diagonal(hs, ctx):
+    # repeated eigenvalues (sphere-like clusters) and an already diagonal pair
+    d = np.array([0.0, 2, 2, 2, 6, 6, 6, 6, 6, 12], dtype=float)
+    k = len(d)
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    S = Q @ np.diag(d) @ Q.T
+    lam, X, _ = hs.ritz(ctx, dev(S), dev(np.eye(k)))
+    np.testing.assert_allclose(lam.cpu().numpy(), d, atol=1e-12)
+    lam2, X2, sw = hs.ritz(ctx, dev(np.diag(d[::-1].copy())), dev(np.eye(k)))
+    np.testing.assert_allclose(lam2.cpu().numpy(), d, atol=0)
+
+
+def test_ritz_rejects_indefinite_mass(hs, ctx):
+    S, M = _spd_pair(20, 1)
+    M[3, 3] = -1.0
+    with pytest.raises(hs.HsimError) as e:
+        hs.ritz(ctx, dev(S), dev(M))
+    assert e.value.name == "HSIM_E_NOT_SPD"
+
+
+@pytest.fixture(scope="module")
+def torus_case(hs, ctx):
+    w, mesh, s = synth.make_workload("bumpy_torus_64")
+    H = hierarchy.build_hierarchy(mesh, w.p, w.levels, s)
+    hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, levels=w.levels, start_vertex=s)
+    return w, mesh, s, H, hier
+
+
+def test_hierarchy_matches_oracle(hs, torus_case):
+    w, mesh, s, H, hier = torus_case
+    assert hier.sizes == H.sizes
+    np.testing.assert_array_equal(hier.order, H.order)
+    for tau, U in enumerate(H.U):
+        r, c, rp, cl, vl = hier.prolongation(tau)
+        assert (r, c) == U.shape
+        np.testing.assert_array_equal(rp, U.indptr)
+        np.testing.assert_array_equal(cl, U.indices)
+        np.testing.assert_allclose(vl, U.data, rtol=1e-15, atol=0)
+
+
+def test_assembly_matches_oracle(hs, ctx, torus_case):
+    w, mesh, s, H, hier = torus_case
+    S, Md = hs.assemble(ctx, hier, V=dev(mesh.V))
+    So = assembly.stiffness(mesh)
+    rp, cl = hier.pattern()
+    Sg = sp.csr_matrix((S.cpu().numpy(), cl.cpu().numpy(), rp.cpu().numpy()), shape=So.shape)
+    assert abs(Sg - So).max() <= 1e-13 * abs(So).max()
+    np.testing.assert_allclose(Md.cpu().numpy(), assembly.lumped_mass(mesh), rtol=1e-14)
+
+
+def test_assembly_intrinsic_flat_torus(hs, ctx):
+    mesh = synth.flat_torus(32)
+    hier = hs.Hierarchy(ctx, mesh.F, L2=mesh.L2, p=10, levels=2)
+    S, Md = hs.assemble(ctx, hier, L2=dev(mesh.L2))
+    rp, cl = hier.pattern()
+    Sg = sp.csr_matrix((S.cpu().numpy(), cl.cpu().numpy(), rp.cpu().numpy()), shape=(mesh.n, mesh.n))
+    assert abs(Sg - assembly.stiffness(mesh)).max() == 0.0
+    np.testing.assert_allclose(Md.cpu().numpy(), (1.0 / 32) ** 2, rtol=1e-15)
+
+
+def test_galerkin_matches_oracle(hs, ctx, torus_case):
+    w, mesh, s, H, hier = torus_case
+    S0 = assembly.stiffness(mesh)
+    U = H.U[0]
+    rp, cl, vals = hs.galerkin(ctx, mesh.n, U.shape[1], S0.indptr, S0.indices, dev(S0.data), U.indptr,
+                               U.indices, dev(U.data))
+    C = sp.csr_matrix((vals.cpu().numpy(), cl, rp), shape=(U.shape[1], U.shape[1]))
+    ref = galerkin.restrict(S0, U)
+    assert abs(C - ref).max() <= 1e-13 * abs(ref).max()
+
+
+@pytest.mark.parametrize("tau,mu", [(0, 0.0), (0, 450.0), (1, 700.0)])
+def test_shifted_solve_matches_scipy(hs, ctx, torus_case, tau, mu):
+    w, mesh, s, H, hier = torus_case
+    S0 = assembly.stiffness(mesh)
+    M0 = assembly.lumped_mass(mesh)
+    S, M = galerkin.level_matrices(S0, M0, H.U)
+    rp, cl = hier.level_pattern(tau)
+    St = S[tau].tocsr()
+    Mt = M[tau].tocsr()
+    # values in the level's natural-order pattern
+    pat = sp.csr_matrix((np.ones(len(cl)), cl, rp), shape=St.shape)
+    assert (abs(St) > 0).multiply(pat).nnz == (abs(St) > 0).nnz
+    Sv = _values_in(St, rp, cl)
+    if tau == 0:
+        Mv = M0
+        mu_eff = mu if mu != 0.0 else -1e-6
+    else:
+        Mv = _values_in(Mt, rp, cl)
+        mu_eff = mu
+    B = np.random.default_rng(tau).standard_normal((St.shape[0], 9))
+    X, neg = hs.shifted_solve(ctx, hier, tau, dev(Sv), dev(Mv), mu_eff, dev(B))
+    K = (St - mu_eff * Mt).tocsc()
+    Xr = spla.spsolve(K, B)
+    err = np.abs(X.cpu().numpy() - Xr).max() / np.abs(Xr).max()
+    assert err < 1e-8
+    ev = sla.eigh(St.toarray(), Mt.toarray(), eigvals_only=True)
+    assert neg == int((ev < mu_eff).sum())
+
+
+def _values_in(A, rp, cl):
+    """values of A in the CSR pattern (rp, cl) (zeros where A has none)"""
+    A = A.tocsr()
+    out = np.zeros(len(cl))
+    for i in range(len(rp) - 1):
+        row = dict(zip(A.indices[A.indptr[i]:A.indptr[i + 1]].tolist(), A.data[A.indptr[i]:A.indptr[i + 1]].tolist()))
+        for e in range(rp[i], rp[i + 1]):
+            out[e] = row.get(int(cl[e]), 0.0)
+    return out

@@ -1,0 +1,104 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol that
+include/hsim.h declares, and its host-side symbolic analysis (nested
+dissection + fronts) factors correctly when replayed on the host."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import assembly, galerkin, hierarchy
+
+
+@pytest.fixture(scope="module")
+def hs(repo_root):
+    from paper_2111_09039_gb300 import build
+    build.build()
+    import paper_2111_09039_gb300 as m
+    m.lib()
+    return m
+
+
+def declared_symbols(repo_root):
+    txt = open(os.path.join(repo_root, "include", "hsim.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsim_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(hs, repo_root):
+    lib = hs.lib()
+    names = declared_symbols(repo_root)
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_no_gpu_calls_fail_cleanly(hs):
+    import ctypes
+    from paper_2111_09039_gb300 import _lib
+    h = ctypes.c_void_p()
+    # on a machine without a GPU, creating a context is an error, not a crash
+    st = _lib.lib().hsim_create(0, None, ctypes.byref(h))
+    if st == 0:
+        _lib.lib().hsim_destroy(h)
+    else:
+        assert st in (1, 3)
+        assert _lib.lib().hsim_last_error()
+
+
+def _shifted(mesh, mu):
+    S = assembly.stiffness(mesh)
+    M = assembly.lumped_mass(mesh)
+    K = (S - mu * sp.diags(M)).tocsr()
+    K.sort_indices()
+    return S, M, K
+
+
+@pytest.mark.parametrize("leaf", [4, 16, 32, 64])
+def test_symbolic_replay_solves_level0(hs, leaf):
+    mesh = synth.bumpy_torus(40, 36, 2)
+    S, M, K = _shifted(mesh, 300.0)
+    B = np.random.default_rng(leaf).standard_normal((mesh.n, 3))
+    X, neg, nnzL = hs.check_symbolic(K.indptr, K.indices, K.data, B, leaf)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-9 * np.abs(Xr).max()
+    # Sylvester inertia: negative pivots = eigenvalues of (S, M) below mu
+    ev = np.linalg.eigvalsh((S.toarray() / np.sqrt(M)[:, None]) / np.sqrt(M)[None, :])
+    assert neg == int((ev < 300.0).sum())
+
+
+def test_symbolic_replay_on_galerkin_level(hs):
+    w, mesh, s = synth.make_workload("bumpy_torus_64")
+    H = hierarchy.build_hierarchy(mesh, w.p, w.levels, s)
+    S0 = assembly.stiffness(mesh)
+    M0 = assembly.lumped_mass(mesh)
+    S, M = galerkin.level_matrices(S0, M0, H.U)
+    mu = 800.0
+    K = (S[1] - mu * M[1]).tocsr()
+    K.sort_indices()
+    B = np.random.default_rng(3).standard_normal((K.shape[0], 4))
+    X, neg, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, 32)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-9 * np.abs(Xr).max()
+
+
+def test_symbolic_replay_disconnected_and_tiny(hs):
+    # two disjoint tori: a forest of two elimination trees
+    a = synth.bumpy_torus(12, 10, 1)
+    b = synth.bumpy_torus(9, 11, 2)
+    V = np.concatenate([a.V, b.V + 5.0])
+    F = np.concatenate([a.F, b.F + a.n])
+    mesh = synth.Mesh(V=V, F=F)
+    S, M, K = _shifted(mesh, 5.0)
+    B = np.random.default_rng(0).standard_normal((mesh.n, 2))
+    X, _, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, 8)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-9 * np.abs(Xr).max()
+    # a 3 x 3 system is a single leaf front
+    K3 = sp.csr_matrix(np.array([[4.0, -1, 0], [-1, 4, -1], [0, -1, 4]]))
+    X3, neg3, _ = hs.check_symbolic(K3.indptr, K3.indices, K3.data, np.eye(3), 32)
+    np.testing.assert_allclose(X3, np.linalg.inv(K3.toarray()), rtol=1e-14)
+    assert neg3 == 0
