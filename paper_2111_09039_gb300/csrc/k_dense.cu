@@ -403,7 +403,11 @@ DenseFront &dense_front(int k, cudaStream_t s) {
 
 void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb, double *G,
           int ldg, bool lower_only) {
-    for (int i = 0; i < ka; ++i) HSIM_CUDA(cudaMemsetAsync(G + (size_t)i * ldg, 0, (size_t)kb * sizeof(double), s));
+    if (ldg == kb) {
+        HSIM_CUDA(cudaMemsetAsync(G, 0, (size_t)ka * kb * sizeof(double), s));
+    } else {
+        HSIM_CUDA(cudaMemset2DAsync(G, (size_t)ldg * sizeof(double), 0, (size_t)kb * sizeof(double), ka, s));
+    }
     if (n <= 0 || ka <= 0 || kb <= 0) return;
     int ti = cdiv(ka, TB), tj = cdiv(kb, TB);
     int64_t tiles = lower_only ? (int64_t)ti * (ti + 1) / 2 : (int64_t)ti * tj;
