@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the hierarchical subspace iteration on one GB300.
+
+Metric: wall seconds for hsim_solve to the p lowest eigenpairs of a synthetic
+mesh at a relative M^{-1}-norm residual (eq. conv2) of tol, with the level-0
+matrices and the hierarchy resident on the device when the timed region
+starts (the Galerkin products, every factorisation, solve, Gram, Ritz and
+update are inside it).  Default workload: bumpy torus R = 1, r = 0.3 on a
+1000 x 1000 grid (10^6 vertices, 2 x 10^6 triangles), p = 500, tol = 1e-5,
+three levels.
+
+One JSON line on stdout (rank 0).  Extra keys:
+  e2e           the same solve through the C ABI from pinned host buffers:
+                S values + M diagonal copied in, eigenpairs copied out
+  roofline      dominant kernel of the solve: algorithmic work / CUDA-event time
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (see oracle/baseline.py)
+  clocks        nvidia-smi samples taken during the timed region
+  info          iteration counts, shifts and per-phase times of the last solve
+
+--impl reference times the CPU oracle instead (bounded sample per step).
+Under torchrun with N > 1 every rank solves its own replica (the solve does
+not shard); the reported time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "s to 500 lowest eigenpairs, 1M-vert mesh, resid<=1e-5; mixed vs FP64 GPU"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 rate: no FP64 figure is measured by the pool; GB300's nominal FP64
+# rate is 1.25 TFLOP/s (152 SMs).  A probe on this machine measured 1.19.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9 or parts[0] != str(gpu_index):
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    """CPU oracle, bounded sample per step; rank 0 only."""
+    if rank != 0:
+        return
+    from oracle import baseline
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = baseline.sample(args.workload, cols=args.sample_cols)
+        if i >= args.warmup:
+            samples.append(r)
+    v = sum(s["value"] for s in samples) / len(samples)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1000.0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"kind": "oracle", "cores": samples[-1]["cores"], "sample": samples[-1]["sample"],
+                             "value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hsim", choices=["hsim", "reference"])
+    ap.add_argument("--workload", default="bumpy_torus_1000")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--sample-cols", type=int, default=8)
+    ap.add_argument("--max-iters", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_2111_09039_gb300 as hs
+    import synth
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    w, mesh, start = synth.make_workload(args.workload)
+    p = w.p
+    tol = args.tol if args.tol is not None else (1e-5 if w.tol < 1e-5 else w.tol)
+    prec = hs.HSIM_FP64 if args.precision == "fp64" else hs.HSIM_MIXED
+    ctx = hs.Context(local)
+    t0 = time.perf_counter()
+    if mesh.V is not None:
+        hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=p, levels=w.levels, start_vertex=start, precision=prec)
+        S, Md = hs.assemble(ctx, hier, V=torch.as_tensor(mesh.V, device=dev))
+    else:
+        hier = hs.Hierarchy(ctx, mesh.F, L2=mesh.L2, p=p, levels=w.levels, start_vertex=start, precision=prec)
+        S, Md = hs.assemble(ctx, hier, L2=torch.as_tensor(mesh.L2, device=dev))
+    torch.cuda.synchronize()
+    hier_s = time.perf_counter() - t0
+    opts = hs.default_options(levels=w.levels, start_vertex=start, precision=prec, max_iters=args.max_iters)
+    stream = ctx.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    info = None
+    for _ in range(args.warmup):
+        lam, Phi, info = hs.solve(ctx, hier, S, Md, p, tol, options=opts)
+    barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    launches0 = hs.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lam, Phi, info = hs.solve(ctx, hier, S, Md, p, tol, options=opts)
+        infos.append(info)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop(local)
+    launches = (hs.kernel_launches() - launches0) / args.steps
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI from pinned host buffers
+    S_h = S.cpu().pin_memory()
+    Md_h = Md.cpu().pin_memory()
+    lam_h = torch.empty(p, dtype=torch.float64).pin_memory()
+    vec_h = torch.empty((p, hier.n), dtype=torch.float64).pin_memory()
+    S_d = torch.empty_like(S)
+    Md_d = torch.empty_like(Md)
+    e2e_ms = []
+    for _ in range(max(1, args.e2e_steps)):
+        barrier()
+        t1 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            S_d.copy_(S_h, non_blocking=True)
+            Md_d.copy_(Md_h, non_blocking=True)
+        lam_d, Phi_d, _ = hs.solve(ctx, hier, S_d, Md_d, p, tol, options=opts)
+        with torch.cuda.stream(stream):
+            lam_h.copy_(lam_d, non_blocking=True)
+            vec_h.copy_(Phi_d.t(), non_blocking=True)
+        stream.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1000.0)
+    h2d = S.numel() * 8 + Md.numel() * 8
+    d2h = p * 8 + p * hier.n * 8
+
+    # residual check of the timed result, in FP64 on the device
+    res = check_residual(hier, S, Md, lam, Phi, ctx)
+
+    if rank != 0:
+        return
+    peaks, peak_src = load_peaks()
+    roof = roofline(info, infos, hier, p, peaks, peak_src, args.precision)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args.workload, info, args.sample_cols)
+    line = {
+        "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "vertices": hier.n, "triangles": hier.m, "p": p, "tol": tol,
+                   "levels": hier.sizes, "precision": args.precision, "parallelism": "replicas" if world > 1 else "1 gpu",
+                   "l2": "working set > L2 (n x q float64 blocks of 6 GB)"},
+        "hier_build_s": hier_s, "max_residual_check": res,
+        "e2e": {"value": min(e2e_ms) / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(round(launches)),
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "info": info,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def check_residual(hier, S, Md, lam, Phi, ctx):
+    """max_i ||S phi_i - lam_i M phi_i||_{M^-1} / ||S phi_i||_{M^-1}, FP64, with
+    torch's sparse CSR product (independent of the library's kernels)."""
+    import torch
+    rp, cl = hier.pattern()
+    A = torch.sparse_csr_tensor(rp.long(), cl.long(), S, size=(hier.n, hier.n))
+    SP = (A @ Phi.contiguous())
+    MP = Md[:, None] * Phi
+    R = SP - MP * lam[None, :]
+    w = (1.0 / Md)[:, None]
+    nr = torch.sqrt((R * R * w).sum(0))
+    ns = torch.sqrt((SP * SP * w).sum(0))
+    nm = torch.sqrt((MP * MP * w).sum(0))
+    above = lam[lam > 1e-8 * lam[-1]]
+    lref = above[0] if above.numel() else lam[-1]
+    return float((nr / torch.maximum(ns, lref * nm)).max().item())
+
+
+def roofline(info, infos, hier, p, peaks, peak_src, precision):
+    """Dominant phase of the solve and its achieved rate against the peak."""
+    q = info["q"]
+    sizes = info["sizes"]
+    iters = info["iters"]
+    steps = len(infos)
+    gram_flops = sum(iters[t] * 2.0 * sizes[t] * q * (q + 1) for t in range(len(sizes) - 1))
+    upd_flops = sum(iters[t] * 2.0 * sizes[t] * q * q for t in range(len(sizes) - 1))
+    ms_gram = sum(i["ms_gram"] for i in infos) / steps
+    ms_upd = sum(i["ms_update"] for i in infos) / steps
+    phases = {k: sum(i["ms_" + k] for i in infos) / steps for k in
+              ("galerkin", "coarse", "prolong", "factor", "solve", "spmm", "gram", "ritz", "update", "residual")}
+    dom = max(phases, key=phases.get)
+    gram_launches = sum(iters[:len(sizes) - 1]) * 2
+    if precision == "fp64":
+        peak = FP64_PEAK_TFLOPS
+        ach = gram_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0
+        r = {"kernel": "gram (FP64 DFMA, Psi^T S Psi and Psi^T M Psi)", "bound": "alu",
+             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s; probe measured 1.19)",
+             "traffic": None, "launches_per_step": gram_launches,
+             "flops_per_launch": gram_flops / max(1, gram_launches),
+             "update_gemm_tflops": upd_flops / (ms_upd * 1e-3) / 1e12 if ms_upd > 0 else 0.0}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", 1743.3)
+        ach = gram_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0
+        r = {"kernel": "gram", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "frac": ach / peak, "peak_source": peak_src, "traffic": None}
+    r["dominant_phase"] = dom
+    r["phase_ms"] = phases
+    return r
+
+
+def cpu_baseline(workload, info, cols):
+    """FP64 oracle on a bounded sample, in a fresh process (no CUDA state)."""
+    cmd = [sys.executable, "-c",
+           "import json,sys; sys.path.insert(0, %r); from oracle import baseline; "
+           "print(json.dumps(baseline.sample(%r, cols=%d, iters=%s)))" % (ROOT, workload, cols,
+                                                                           json.dumps(info["iters"]))]
+    try:
+        out = subprocess.run(cmd, capture_output=True, text=True, timeout=1200)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the baseline is a report, not the measurement
+        return {"kind": "oracle", "error": str(e)[:200]}
+
+
+if __name__ == "__main__":
+    main()

@@ -14,6 +14,8 @@
 #include <chrono>
 #include <functional>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -31,6 +33,16 @@ using namespace hsim;
 
 namespace {
 thread_local std::string g_last_error;
+
+// HSIM_TRACE=1 prints one line per subspace iteration to stderr.
+bool trace_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char *e = std::getenv("HSIM_TRACE");
+        on = (e && *e && *e != '0') ? 1 : 0;
+    }
+    return on == 1;
+}
 
 hsim_status guard(const std::function<void()> &f) {
     try {
@@ -403,8 +415,11 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
         const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
         Timer tf(s);
-        factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
+        int negp = factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
         inf.ms_factor += tf.stop();
+        if (trace_on())
+            std::fprintf(stderr, "[hsim] level %d n=%d q=%d shift=%.10g negative_pivots=%d fronts=%d nnzL=%lld\n", tau,
+                         n, q, mu, negp, L.fs.n_nodes, (long long)L.fs.nnz_L);
         inf.factor_nnz[tau] = L.fs.nnz_L;
         inf.factor_flops[tau] = L.fs.flops;
         // 1 / diag(M) for the M^-1 norm of the finest level (Sec. 5, termination criterion)
@@ -467,6 +482,9 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 res[i] = std::sqrt(rs[3 * i]) / den;
                 if (i < p) maxres = std::max(maxres, res[i]);
             }
+            if (trace_on())
+                std::fprintf(stderr, "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d lam0 %.6g lam_p %.6g\n",
+                             tau, it, locked, maxres, sweeps, lam_h[0], lam_h[p - 1]);
             if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
             if (maxres < tol) break;
             int r = 0;
@@ -750,8 +768,10 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *h, const double *S_val, const d
 hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *ptr, const int32_t *col,
                       const double *val, int k, const double *X, int ldx, double *Y, int ldy) {
     return guard([&] {
-        HSIM_CHECK_ARG(ctx && ptr && col && val && X && Y, "NULL argument");
+        HSIM_CHECK_ARG(ctx, "NULL context");
         HSIM_CHECK_ARG(n_rows >= 0 && n_cols >= 0 && k >= 0 && ldx >= k && ldy >= k, "bad sizes");
+        if (n_rows == 0 || k == 0) return;
+        HSIM_CHECK_ARG(ptr && col && X && Y && (val || n_cols == 0), "NULL argument");
         DeviceGuard dg(ctx->device);
         k::spmm(ctx->stream, n_rows, ptr, col, val, k, X, ldx, Y, ldy);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
