@@ -62,6 +62,10 @@ typedef struct {
     int start_vertex;    /* first vertex of farthest-point sampling (Alg. 2) */
     int leaf_size;       /* nested-dissection leaf size (tuning, default 32) */
     int q;               /* subspace size; <= 0 selects max(ceil(1.5p), p+8) */
+    int refine;          /* FP64 residual refinement of the last inverse iteration of
+                            each Rayleigh-Ritz step: 0 = automatic (switched on for a
+                            level once its residual stops decreasing), 1 = always,
+                            -1 = never */
 } hsim_options;
 
 /* Per-solve report (host struct, optional). */

@@ -30,7 +30,8 @@ class Options(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("sigma", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("inv_iters", ctypes.c_int),
                 ("lock_factor", ctypes.c_double), ("precision", ctypes.c_int),
-                ("start_vertex", ctypes.c_int), ("leaf_size", ctypes.c_int), ("q", ctypes.c_int)]
+                ("start_vertex", ctypes.c_int), ("leaf_size", ctypes.c_int), ("q", ctypes.c_int),
+                ("refine", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -117,6 +117,7 @@ struct ProlongData {
 
 struct hsim_hier {
     hsim_ctx *ctx = nullptr;
+    int device = 0;
     int n = 0, m = 0, p = 0, T = 0;
     hsim_options opts{};
     std::vector<int> sizes, order;
@@ -432,7 +433,13 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         // M Phi
         apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
         int locked = 0, it = 0;
-        double maxres = 0.0;
+        double maxres = 0.0, prev_maxres = 0.0;
+        // The shifted matrix is factored without pivoting; element growth can
+        // leave a backward error well above the unit roundoff, which puts a
+        // floor under the residual.  One step of FP64 refinement of the last
+        // inverse iteration removes it; in automatic mode it is switched on
+        // once a level's residual stops decreasing.
+        bool refine = o.refine > 0;
         for (it = 1; it <= o.max_iters; ++it) {
             const int a = q - locked;
             Timer ts(s);
@@ -443,6 +450,16 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 apply_M(ctx, H, tau, a, H->Psi.p + locked, q, H->SP.p + locked, q);
                 k::copy_matrix(s, n, a, H->SP.p + locked, q, H->Psi.p + locked, q);
                 solve_level(ctx, H, L, H->Psi.p + locked, a, q);
+            }
+            if (refine) {
+                // right-hand side of the last solve: SP (two or more inverse
+                // iterations) or MP (one); the residual goes to the other buffer
+                double *rhs = o.inv_iters >= 2 ? H->SP.p : H->MP.p;
+                double *res_buf = o.inv_iters >= 2 ? H->MP.p : H->SP.p;
+                k::shifted_residual(s, n, L.dpat.ptr.p, L.dpat.col.p, Sx, Mx, Mdx, mu, a, H->Psi.p + locked, q,
+                                    rhs + locked, q, res_buf + locked, q);
+                solve_level(ctx, H, L, res_buf + locked, a, q);
+                k::axpy_matrix(s, n, a, res_buf + locked, q, H->Psi.p + locked, q);
             }
             if (locked > 0) k::copy_matrix(s, n, locked, H->Phi.p, q, H->Psi.p, q);
             inf.ms_solve += ts.stop();
@@ -483,10 +500,12 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 if (i < p) maxres = std::max(maxres, res[i]);
             }
             if (trace_on())
-                std::fprintf(stderr, "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d lam0 %.6g lam_p %.6g\n",
-                             tau, it, locked, maxres, sweeps, lam_h[0], lam_h[p - 1]);
+                std::fprintf(stderr, "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g\n",
+                             tau, it, locked, maxres, sweeps, (int)refine, lam_h[0], lam_h[p - 1]);
             if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
             if (maxres < tol) break;
+            if (o.refine == 0 && !refine && it >= 2 && maxres > 0.7 * prev_maxres && maxres < 1e-6) refine = true;
+            prev_maxres = maxres;
             int r = 0;
             while (r < p && res[r] < o.lock_factor * tol) ++r;
             locked = r;
@@ -523,6 +542,7 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     cudaStream_t s = ctx->stream;
     auto H = std::make_unique<hsim_hier>();
     H->ctx = ctx;
+    H->device = ctx->device;
     H->n = n;
     H->m = m;
     H->p = p;
@@ -634,6 +654,7 @@ hsim_options checked(const hsim_options *o) {
     HSIM_CHECK_ARG(r.max_iters >= 1, "max_iters must be >= 1");
     HSIM_CHECK_ARG(r.inv_iters >= 1, "inv_iters must be >= 1");
     HSIM_CHECK_ARG(r.precision == HSIM_FP64 || r.precision == HSIM_MIXED, "unknown precision");
+    HSIM_CHECK_ARG(r.refine >= -1 && r.refine <= 1, "refine must be -1, 0 or 1");
     return r;
 }
 
@@ -657,6 +678,7 @@ void hsim_default_options(hsim_options *o) {
     o->start_vertex = 0;
     o->leaf_size = 32;
     o->q = 0;
+    o->refine = 0;
 }
 
 const char *hsim_last_error(void) { return g_last_error.c_str(); }
@@ -682,8 +704,13 @@ hsim_status hsim_create(int device, void *stream, hsim_ctx **out) {
 
 void hsim_destroy(hsim_ctx *ctx) {
     if (!ctx) return;
-    DeviceGuard dg(ctx->device);
+    // never throws: at process exit the CUDA runtime may already be gone
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
     delete ctx;
+    if (prev >= 0) cudaSetDevice(prev);
+    cudaGetLastError();
 }
 
 hsim_status hsim_build_hierarchy(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F, const double *L2,
@@ -699,8 +726,12 @@ hsim_status hsim_build_hierarchy(hsim_ctx *ctx, int n, int m, const double *V, c
 
 void hsim_hier_destroy(hsim_hier *h) {
     if (!h) return;
-    DeviceGuard dg(h->ctx->device);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
     delete h;
+    if (prev >= 0) cudaSetDevice(prev);
+    cudaGetLastError();
 }
 
 hsim_status hsim_hier_info(const hsim_hier *h, int *levels, int *sizes, int32_t *order) {

@@ -120,6 +120,58 @@ __global__ void k_spmm(int n_rows, const int *__restrict__ ptr, const int *__res
     }
 }
 
+// R[r, :] = B[r, :] - sum_e (S_e - mu M_e) X[col_e, :]  (M in S's pattern, or a
+// diagonal Md); the residual of the shifted system for iterative refinement
+template <int kChunk>
+__global__ void k_shifted_residual(int n_rows, const int *__restrict__ ptr, const int *__restrict__ col,
+                                   const double *__restrict__ S, const double *__restrict__ M,
+                                   const double *__restrict__ Md, double mu, int k, const double *__restrict__ X,
+                                   int ldx, const double *__restrict__ B, int ldb, double *__restrict__ R, int ldr) {
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int warps = blockDim.x / kWarp;
+    int64_t row = (int64_t)blockIdx.x * warps + threadIdx.x / kWarp;
+    if (row >= n_rows) return;
+    const int beg = ptr[row], end = ptr[row + 1];
+    for (int c0 = 0; c0 < k; c0 += kChunk * kWarp) {
+        double acc[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) acc[u] = 0.0;
+        for (int e0 = beg; e0 < end; e0 += kWarp) {
+            int my_c = 0;
+            double my_v = 0.0;
+            if (e0 + lane < end) {
+                my_c = col[e0 + lane];
+                my_v = S[e0 + lane];
+                if (M) my_v -= mu * M[e0 + lane];
+                else if (my_c == row) my_v -= mu * Md[row];
+            }
+            const int cnt = min(kWarp, end - e0);
+            for (int t = 0; t < cnt; ++t) {
+                int c = __shfl_sync(0xffffffffu, my_c, t);
+                double v = __shfl_sync(0xffffffffu, my_v, t);
+                const double *xr = X + (size_t)c * ldx;
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) {
+                    int j = c0 + u * kWarp + lane;
+                    if (j < k) acc[u] += v * xr[j];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            int j = c0 + u * kWarp + lane;
+            if (j < k) R[(size_t)row * ldr + j] = B[(size_t)row * ldb + j] - acc[u];
+        }
+    }
+}
+
+__global__ void k_axpy_matrix(int n, int k, const double *__restrict__ X, int ldx, double *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    Y[(size_t)i * ldy + j] += X[(size_t)i * ldx + j];
+}
+
 __global__ void k_diag_scale(int n, int k, const double *__restrict__ d, const double *__restrict__ X, int ldx,
                              double *__restrict__ Y, int ldy) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,6 +360,25 @@ void spmm_f(cudaStream_t s, int n_rows, const int *ptr, const int *col, const fl
         k_spmm<float, 8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
     else
         k_spmm<float, 24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *S, const double *M,
+                      const double *Md, double mu, int k, const double *X, int ldx, const double *B, int ldb,
+                      double *R, int ldr) {
+    if (n_rows <= 0 || k <= 0) return;
+    const int warps = 8;
+    unsigned g = grid1d(n_rows, warps);
+    if (k <= 32 * 8)
+        k_shifted_residual<8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, S, M, Md, mu, k, X, ldx, B, ldb, R, ldr);
+    else
+        k_shifted_residual<24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, S, M, Md, mu, k, X, ldx, B, ldb, R, ldr);
+    HSIM_LAUNCHED();
+}
+
+void axpy_matrix(cudaStream_t s, int n, int k, const double *X, int ldx, double *Y, int ldy) {
+    if (n <= 0 || k <= 0) return;
+    k_axpy_matrix<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 

@@ -23,6 +23,12 @@ void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const doub
           const double *X, int ldx, double *Y, int ldy);
 void spmm_f(cudaStream_t s, int n_rows, const int *ptr, const int *col, const float *val, int k,
             const float *X, int ldx, float *Y, int ldy);
+// R = B - (S - mu M) X with M in S's pattern (M) or diagonal (Md)
+void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *S,
+                      const double *M, const double *Md, double mu, int k, const double *X, int ldx,
+                      const double *B, int ldb, double *R, int ldr);
+// Y += X
+void axpy_matrix(cudaStream_t s, int n, int k, const double *X, int ldx, double *Y, int ldy);
 // Y[r, :] = d[r] * X[r, :]
 void diag_scale(cudaStream_t s, int n, int k, const double *d, const double *X, int ldx, double *Y,
                 int ldy);
