@@ -23,7 +23,9 @@ Steps and readings (each listed in the design notes):
   columns stay in the Rayleigh-Ritz basis unchanged.
 * Shift (Alg. 3): mu = Lambda^{tau+1}_j with j = floor(alpha p), 0-based into
   the ascending Ritz values of the coarser level; if j == 0 the shift is
-  -1e-8 * Lambda_{q-1} instead (mu = lambda_0 = 0 would make K singular).
+  -lambda_ref (the first coarse Ritz value above 1e-8 Lambda_{q-1}) instead:
+  mu = lambda_0 = 0 would make K singular, and a shift within rounding of it
+  would collapse every column onto the constant vector.
 * At most ``max_iters`` (100) iterations per level, else NoConvergence.
 * Output: the p lowest pairs, ascending; each eigenvector's entry of largest
   magnitude is made positive.
@@ -111,9 +113,14 @@ def sim(S, M, Phi, p, eps, mu, finest: bool, max_iters=100, inv_iters=2, lock_fa
 
 
 def shift(lam_coarse, p, alpha=0.1):
+    """mu = Lambda_j, j = floor(alpha p) (Alg. 3).  For j = 0 the rule would
+    put mu on lambda_0 = 0 of a closed surface, where S - mu M is singular;
+    the shift is then mirrored below zero to -lambda_ref, lambda_ref the first
+    coarse Ritz value above 1e-8 Lambda_{q-1}."""
     j = int(math.floor(alpha * p))
     if j == 0:
-        return -1e-8 * lam_coarse[-1]
+        above = lam_coarse[lam_coarse > 1e-8 * lam_coarse[-1]]
+        return -float(above[0] if len(above) else lam_coarse[-1])
     return float(lam_coarse[j])
 
 

@@ -136,7 +136,17 @@ def test_shift_rule():
     assert sim.shift(lam, 20) == 2.0
     assert sim.shift(lam, 25) == 2.0
     assert sim.shift(lam, 100) == 10.0
-    assert sim.shift(lam, 5) == -1e-8 * 29.0
+    assert sim.shift(lam, 5) == -1.0
+    assert sim.shift(np.array([1e-15, 2.0, 6.0]), 4) == -2.0
+
+
+def test_small_p_against_dense():
+    """p < 10 uses the mirrored shift; result still the plain definition."""
+    mesh = synth.bumpy_torus(40, 44, 21)
+    r = sim.hsim(mesh, 6, 2, 1e-10, 5)
+    assert r.shifts[0] < 0
+    lam_ref, _ = sim.dense_reference(assembly.stiffness(mesh), assembly.lumped_mass(mesh), 6)
+    np.testing.assert_allclose(r.lam, lam_ref, rtol=1e-10, atol=1e-10)
 
 
 def test_planted_swapped_ritz_matrices_is_caught(monkeypatch):
