@@ -409,8 +409,18 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         k::spmm(s, n, P.dU.ptr.p, P.dU.col.p, P.dUval.p, q, Xc, ldxc, H->Phi.p, q);
         inf.ms_prolong += tp.stop();
         // shift (Alg. 3): Lambda_j of the coarser level, j = floor(alpha p)
+        // shift (Alg. 3); for j = 0 mirrored below zero to -lambda_ref so that
+        // S - mu M stays away from the constant null vector
         int j = (int)std::floor(o.alpha * p);
-        double mu = j == 0 ? -1e-8 * lam_h[q - 1] : lam_h[j];
+        double mu = lam_h[j];
+        if (j == 0) {
+            mu = -lam_h[q - 1];
+            for (int i = 0; i < q; ++i)
+                if (lam_h[i] > 1e-8 * lam_h[q - 1]) {
+                    mu = -lam_h[i];
+                    break;
+                }
+        }
         inf.shift[tau] = mu;
         const double *Sx = tau == 0 ? H->S0int.p : H->Sv[tau].p;
         const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;

@@ -7,9 +7,9 @@
 // ns columns are the pivots.  Fronts of equal height in the elimination tree
 // are independent and are processed by the same launches.  A front is
 // factored in panels of kPanel = 32 columns (right-looking):
-//   panel:   LDL^T of the 32 x 32 diagonal block (in shared memory, redone by
-//            every CTA of the front) and L21 = A21 L11^-T D^-1 for a tile of
-//            rows below it;
+//   diag:    LDL^T of the 32 x 32 diagonal block in shared memory (one CTA
+//            per front), written back in place;
+//   panel:   L21 = A21 L11^-T D^-1, one tile of 128 rows per CTA;
 //   update:  A22 -= L21 D L21^T on lower-triangular 64 x 64 tiles;
 // and the children's update blocks are added into the parent front
 // (extend-add) before the parent is factored.  Pivoting is not used: the
@@ -93,7 +93,7 @@ __device__ void ldlt_block(double (*Dg)[P + 1], int kb, double tol, int *flags) 
         __syncthreads();
         double d = Dg[j][j];
         if (!(fabs(d) >= tol)) {  // also catches NaN
-            if (threadIdx.x == 0 && blockIdx.y == 0) atomicAdd(&flags[0], 1);
+            if (threadIdx.x == 0) atomicAdd(&flags[0], 1);
             d = (d < 0.0) ? -tol : tol;
         }
         for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) lj[i] = Dg[j][i] / d;
@@ -112,28 +112,44 @@ __device__ void ldlt_block(double (*Dg)[P + 1], int kb, double tol, int *flags) 
 
 constexpr int kPanelRows = 128;
 
-__global__ void __launch_bounds__(128) k_front_panel(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                     double *__restrict__ arena, double tol, int *flags) {
+// LDL^T of the kb x kb diagonal block of panel k0, one CTA per front,
+// written back in place (unit L below the diagonal, D on it).
+__global__ void __launch_bounds__(128) k_front_diag_block(FrontDev fd, const int *__restrict__ nodes, int k0,
+                                                          double *__restrict__ arena, double tol, int *flags) {
     __shared__ double Dg[P][P + 1];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t];
     const int kb = min(P, ns - k0);
     if (kb <= 0) return;
-    const int r0 = k0 + kb + blockIdx.y * kPanelRows;
-    if (blockIdx.y > 0 && r0 >= nf) return;
     double *F = arena + fd.foff[t];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
         Dg[c][r] = (r >= c) ? F[(int64_t)(k0 + c) * nf + (k0 + r)] : 0.0;
     }
     ldlt_block(Dg, kb, tol, flags);
-    if (blockIdx.y == 0) {
-        for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-            int r = idx % kb, c = idx / kb;
-            if (r >= c) F[(int64_t)(k0 + c) * nf + (k0 + r)] = Dg[c][r];
-        }
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int r = idx % kb, c = idx / kb;
+        if (r >= c) F[(int64_t)(k0 + c) * nf + (k0 + r)] = Dg[c][r];
     }
-    // rows below: x L11^T = a, l = x / d
+}
+
+// Rows below the diagonal block: x L11^T = a, l = x / d, with L11 and D
+// read from the block factored by k_front_diag_block in the previous launch.
+__global__ void __launch_bounds__(128) k_front_panel(FrontDev fd, const int *__restrict__ nodes, int k0,
+                                                     double *__restrict__ arena) {
+    __shared__ double Dg[P][P + 1];
+    const int t = nodes[blockIdx.x];
+    const int nf = fd.nf[t], ns = fd.ns[t];
+    const int kb = min(P, ns - k0);
+    if (kb <= 0) return;
+    const int r0 = k0 + kb + blockIdx.y * kPanelRows;
+    if (r0 >= nf) return;
+    double *F = arena + fd.foff[t];
+    for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+        int r = idx % kb, c = idx / kb;
+        Dg[c][r] = (r >= c) ? F[(int64_t)(k0 + c) * nf + (k0 + r)] : 0.0;
+    }
+    __syncthreads();
     const int r = r0 + threadIdx.x;
     if (r < nf) {
         double x[P];
@@ -451,8 +467,11 @@ void front_extend_add(cudaStream_t s, const FrontDev &fd, const int *parent, con
 void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_rows,
                  double *arena, double pivot_tol, int *flags) {
     if (n_nodes <= 0) return;
-    dim3 g((unsigned)n_nodes, max(1u, cdiv(max_rows, kPanelRows)));
-    k_front_panel<<<g, 128, 0, s>>>(fd, nodes, k0, arena, pivot_tol, flags);
+    k_front_diag_block<<<(unsigned)n_nodes, 128, 0, s>>>(fd, nodes, k0, arena, pivot_tol, flags);
+    HSIM_LAUNCHED();
+    if (max_rows <= 0) return;
+    dim3 g((unsigned)n_nodes, cdiv(max_rows, kPanelRows));
+    k_front_panel<<<g, 128, 0, s>>>(fd, nodes, k0, arena);
     HSIM_LAUNCHED();
 }
 
