@@ -44,6 +44,9 @@ WORKLOADS = {
     # icosphere subdivision 6 (40,962 vertices), noise seed 5: spectral loss source
     "icosphere6_grad": Workload("icosphere6_grad", "displaced_icosphere", (6, 5), p=50,
                                 levels=2, tol=1e-10, seed=5),
+    # a 10^4-vertex member of the bumpy-torus family (profiling, quick runs)
+    "bumpy_torus_100": Workload("bumpy_torus_100", "bumpy_torus", (100, 100, 3), p=50,
+                                levels=2, tol=1e-5, seed=3),
     # small cases used by tests
     "icosphere3_noise": Workload("icosphere3_noise", "displaced_icosphere", (3, 7), p=20,
                                  levels=2, tol=1e-10, seed=7),
