@@ -213,6 +213,28 @@ hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *hier, int tau, const do
                                const double *M_val_dev, double mu, int k, double *B_dev, int ldb,
                                int *negative_pivots);
 
+/* Allocation-free variant of hsim_ritz, for callers that cannot let a
+ * library allocate device memory (a framework that reserves the whole
+ * device pool for its own allocator, a latency-bound loop that must not enter
+ * the driver's allocator, a host that forbids allocations by plugins).  The
+ * paper has no counterpart; it is the same Rayleigh-Ritz solve as hsim_ritz.
+ *
+ * Its scratch is one fixed device array inside this library, sized for
+ * k <= HSIM_RITZ_NOALLOC_MAX (about 3.2 MB on every device that loads the
+ * library, kept until the process exits); larger k fails with
+ * HSIM_E_INVALID_ARG.  No cudaMalloc or cudaFree is called.  The caller owns
+ * the inputs Sbar_dev, Mbar_dev (k x k row-major, read only) and the outputs
+ * evals_dev (k) and X_dev (k x k row-major), all on the current device; work
+ * is issued on cuda_stream (a cudaStream_t, NULL = legacy default stream) and
+ * the call returns after that stream drained.  The first call on a device
+ * (made while it is current) looks up the array's device address, so make
+ * it before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller. */
+#define HSIM_RITZ_NOALLOC_MAX 256
+hsim_status hsim_ritz_noalloc(void *cuda_stream, int k, const double *Sbar_dev, const double *Mbar_dev,
+                              double *evals_dev, double *X_dev, int *sweeps_out);
+
 /* Host-only check of the ordering and symbolic analysis: factors the
  * natural-order symmetric CSR matrix (ptr/col/val, host) over the same front
  * structures and in the same order as the GPU kernels and solves K X = B for

@@ -23,6 +23,9 @@ struct Error : std::runtime_error {
 
 [[noreturn]] inline void fail(hsim_status s, const std::string &msg) { throw Error(s, msg); }
 
+// Records the message that hsim_last_error() returns on this thread.
+void set_last_error(const std::string &msg);
+
 #define HSIM_CHECK_ARG(cond, msg)                                  \
     do {                                                           \
         if (!(cond)) ::hsim::fail(HSIM_E_INVALID_ARG, (msg));      \

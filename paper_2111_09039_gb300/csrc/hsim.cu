@@ -61,6 +61,8 @@ hsim_status guard(const std::function<void()> &f) {
 }
 }  // namespace
 
+void hsim::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 struct hsim_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

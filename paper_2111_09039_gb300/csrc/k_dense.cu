@@ -549,5 +549,192 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     return 0;
 }
 
+// ===========================================================================
+// Allocation-free Ritz solve.
+//
+// Some callers cannot let a library allocate device memory: a framework that
+// reserves the whole device pool for its own caching allocator (a cudaMalloc
+// from inside would fail or fragment it), a latency-bound loop that must not
+// enter the driver's allocator, or a host that forbids allocations by plugins.
+// For them hsim_ritz_noalloc runs the same Ritz solve as hsim_ritz with all of
+// its scratch taken from one fixed, file-scope device array (about 3.2 MB per
+// device that loads the library, held until the process exits).  Its address
+// is looked up once per device with cudaGetSymbolAddress, by the first call
+// made while that device is current; that first call should therefore come
+// before any stream capture.  Every call shares the array: calls whose work
+// overlaps on the GPU (different streams, or different host threads) race and
+// must be serialised by the caller.  The flags and counters that must start
+// at zero are cleared by every call; everything else is overwritten before it
+// is read.
+// ===========================================================================
+namespace {
+
+constexpr int kNoAllocMaxK = HSIM_RITZ_NOALLOC_MAX;
+constexpr size_t kNoAllocWork = (size_t)6 * kNoAllocMaxK * kNoAllocMaxK + 4 * (size_t)kNoAllocMaxK + 64;
+// byte offsets inside the scratch array
+constexpr size_t kOffWork = 0;
+constexpr size_t kOffI64 = kOffWork + kNoAllocWork * sizeof(double);     // foff[2], rows_off[2], relmap_off[2]
+constexpr size_t kOffI32 = kOffI64 + 6 * sizeof(int64_t);                // nf, ns, pstart, relmap, node, flags[4]
+constexpr size_t kOffRows = kOffI32 + 16 * sizeof(int);                  // rows[kNoAllocMaxK]
+constexpr size_t kNoAllocBytes = kOffRows + (size_t)kNoAllocMaxK * sizeof(int);
+
+static __device__ __align__(256) unsigned char g_ritz_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_ritz_scratch for the current device (looked up once).
+unsigned char *noalloc_scratch(int dev) {
+    HSIM_CHECK_ARG(dev >= 0 && dev < kMaxDevices, "device index beyond the supported range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *ptr = nullptr;
+        HSIM_CUDA(cudaGetSymbolAddress(&ptr, g_ritz_scratch));
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    return g_noalloc_addr[dev];
+}
+
+__global__ void k_noalloc_front(int k, int64_t *i64, int *i32, int *rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) rows[i] = i;
+    if (i == 0) {
+        i64[0] = 0;                 // foff
+        i64[1] = (int64_t)k * k;
+        i64[2] = 0;                 // rows_off
+        i64[3] = k;
+        i64[4] = 0;                 // relmap_off
+        i64[5] = 0;
+        i32[0] = k;                 // nf
+        i32[1] = k;                 // ns
+        i32[2] = 0;                 // pstart
+        i32[3] = 0;                 // relmap
+        i32[4] = 0;                 // node list
+    }
+}
+
+// The Ritz solve of ritz(), with the dense front description and the work
+// area supplied by the caller.
+int ritz_on(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals, double *X,
+            int ldx, double *work, const FrontDev &fd, const int *node, int *sweeps, int *flag_dev, int *flag_host) {
+    const size_t kk = (size_t)k * k;
+    double *F = work, *A = work + kk, *A2 = work + 2 * kk, *V = work + 3 * kk, *V2 = work + 4 * kk, *W = work + 5 * kk;
+    double *d = work + 6 * kk;
+    double *cs = d + k;
+    unsigned long long *rot = reinterpret_cast<unsigned long long *>(cs + k + 2);
+    copy_matrix(s, k, k, Mbar, ldm, F, k);
+    HSIM_CUDA(cudaMemsetAsync(flag_dev, 0, 4 * sizeof(int), s));
+    const int steps = (k + kPanel - 1) / kPanel;
+    for (int st = 0; st < steps; ++st) {
+        int k0 = st * kPanel;
+        int kb = std::min(kPanel, k - k0);
+        front_panel(s, fd, node, 1, k0, k - k0 - kb, F, 1e-300, flag_dev);
+        front_update(s, fd, node, 1, k0, k - k0 - kb, F);
+    }
+    front_diag(s, fd, node, 1, F, d, flag_dev + 2);
+    HSIM_CUDA(cudaMemcpyAsync(flag_host, flag_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    if (flag_host[0] != 0 || flag_host[2] != 0) return 1;
+    copy_matrix(s, k, k, Sbar, lds, W, k);
+    auto forward = [&](double *Y) {
+        for (int st = 0; st < steps; ++st) {
+            int k0 = st * kPanel;
+            int kb = std::min(kPanel, k - k0);
+            solve_fwd_tri(s, fd, node, 1, k0, F, k, Y, k);
+            solve_fwd_upd(s, fd, node, 1, k0, k - k0 - kb, F, k, Y, k);
+        }
+        k_row_scale_sqrt<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, d, Y, k, 0);
+        HSIM_LAUNCHED();
+    };
+    forward(W);
+    dim3 tg(cdiv(k, 32), cdiv(k, 32)), tb(32, 8);
+    k_transpose<<<tg, tb, 0, s>>>(k, W, k, A, k);
+    HSIM_LAUNCHED();
+    forward(A);
+    k_symmetrize<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, A, k);
+    HSIM_LAUNCHED();
+    k_identity<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, V, k);
+    HSIM_LAUNCHED();
+    const int m = (k % 2) ? k + 1 : k;
+    int blocks_per_sm = 0;
+    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_jacobi_sweep, 256, 0));
+    int grid = std::max(1, std::min(blocks_per_sm, 4) * sm_count());
+    int64_t need = std::max<int64_t>((int64_t)k * k, m / 2);
+    grid = (int)std::min<int64_t>(grid, (need + 255) / 256);
+    grid = std::max(grid, 1);
+    double tol = 1e-15, abs_tol = 1e-300;
+    int sw = 0;
+    unsigned long long hrot = 1;
+    double *pA = A, *pA2 = A2, *pV = V, *pV2 = V2;
+    while (hrot != 0 && sw < 40) {
+        HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        int kk_ = k, mm = m, ld = k;
+        void *args[] = {&kk_, &mm, &pA, &pA2, &pV, &pV2, &cs, &ld, &tol, &abs_tol, &rot};
+        HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_jacobi_sweep, dim3(grid), dim3(256), args, 0, s));
+        HSIM_LAUNCHED();
+        if ((m - 1) % 2 == 1) {
+            std::swap(pA, pA2);
+            std::swap(pV, pV2);
+        }
+        HSIM_CUDA(cudaMemcpyAsync(&hrot, rot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        ++sw;
+    }
+    if (sweeps) *sweeps = sw;
+    int *rk = reinterpret_cast<int *>(W);
+    k_rank<<<cdiv(k, 128), 128, 0, s>>>(k, pA, k, rk, evals);
+    HSIM_LAUNCHED();
+    k_row_scale_sqrt<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, d, pV, k, 0);
+    HSIM_LAUNCHED();
+    for (int st = steps - 1; st >= 0; --st) {
+        int k0 = st * kPanel;
+        int kb = std::min(kPanel, k - k0);
+        solve_bwd_upd(s, fd, node, 1, k0, k - k0 - kb, F, k, pV, k);
+        solve_bwd_tri(s, fd, node, 1, k0, F, k, pV, k);
+    }
+    k_permute_cols<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, rk, pV, k, X, ldx);
+    HSIM_LAUNCHED();
+    return 0;
+}
+
+}  // namespace
 }  // namespace k
 }  // namespace hsim
+
+extern "C" hsim_status hsim_ritz_noalloc(void *cuda_stream, int k, const double *Sbar_dev, const double *Mbar_dev,
+                                         double *evals_dev, double *X_dev, int *sweeps_out) {
+    using namespace hsim;
+    try {
+        HSIM_CHECK_ARG(Sbar_dev && Mbar_dev && evals_dev && X_dev, "NULL argument");
+        HSIM_CHECK_ARG(k >= 1, "k must be >= 1");
+        if (k > k::kNoAllocMaxK)
+            fail(HSIM_E_INVALID_ARG, "hsim_ritz_noalloc: k = " + std::to_string(k) + " exceeds the fixed scratch limit " +
+                                         std::to_string(k::kNoAllocMaxK) + "; use hsim_ritz");
+        int dev = 0;
+        HSIM_CUDA(cudaGetDevice(&dev));
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        unsigned char *base = k::noalloc_scratch(dev);
+        double *work = reinterpret_cast<double *>(base + k::kOffWork);
+        int64_t *i64 = reinterpret_cast<int64_t *>(base + k::kOffI64);
+        int *i32 = reinterpret_cast<int *>(base + k::kOffI32);
+        int *rows = reinterpret_cast<int *>(base + k::kOffRows);
+        k::k_noalloc_front<<<k::cdiv(k, 128), 128, 0, s>>>(k, i64, i32, rows);
+        HSIM_LAUNCHED();
+        k::FrontDev fd{i64 + 0, i32 + 0, i32 + 1, i32 + 2, i64 + 2, rows, i64 + 4, i32 + 3};
+        int flag_host[4] = {0, 0, 0, 0};
+        int sw = 0;
+        int rc = k::ritz_on(s, k, Sbar_dev, k, Mbar_dev, k, evals_dev, X_dev, k, work, fd, i32 + 4, &sw, i32 + 8,
+                            flag_host);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        if (sweeps_out) *sweeps_out = sw;
+        if (rc != 0) fail(HSIM_E_NOT_SPD, "M_bar is not positive definite");
+        return HSIM_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return HSIM_E_INTERNAL;
+    }
+}
