@@ -136,7 +136,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hsim", choices=["hsim", "reference"])
     ap.add_argument("--workload", default="bumpy_torus_1000")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed FP64 solves for the mixed-vs-FP64 comparison (0 = skip)")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample-cols", type=int, default=8)
@@ -206,6 +208,26 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
+    # the FP64 GPU form of the same solve, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        o64 = hs.default_options(levels=w.levels, start_vertex=start, precision=hs.HSIM_FP64,
+                                 max_iters=args.max_iters)
+        hs.solve(ctx, hier, S, Md, p, tol, options=o64)  # warm-up
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            lam64, Phi64, info64 = hs.solve(ctx, hier, S, Md, p, tol, options=o64)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        dl = (lam - lam64).abs() / torch.clamp(lam64.abs(), min=float(lam64[1]))
+        fp64 = {"value": ms64 / 1000.0, "unit": "s", "steps": args.fp64_steps,
+                "speedup_mixed_vs_fp64": ms64 / ms, "max_rel_eigenvalue_diff": float(dl.max().item()),
+                "max_residual_check": check_residual(hier, S, Md, lam64, Phi64, ctx), "info": info64}
+
     # end to end through the C ABI from pinned host buffers
     S_h = S.cpu().pin_memory()
     Md_h = Md.cpu().pin_memory()
@@ -242,7 +264,7 @@ def main():
     line = {
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16+f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "vertices": hier.n, "triangles": hier.m, "p": p, "tol": tol,
                    "levels": hier.sizes, "precision": args.precision, "parallelism": "replicas" if world > 1 else "1 gpu",
@@ -251,6 +273,7 @@ def main():
         "e2e": ({"value": min(e2e_ms) / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
                 if e2e_ms else None),
         "gpu_launches": int(round(launches)),
+        "fp64_gpu": fp64,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "info": info,
     }
     print(json.dumps(line), flush=True)
@@ -298,10 +321,17 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
              "flops_per_launch": gram_flops / max(1, gram_launches),
              "update_gemm_tflops": upd_flops / (ms_upd * 1e-3) / 1e12 if ms_upd > 0 else 0.0}
     else:
+        # tensor-core Gram: 21 digit-pair products (6 digits, pairs s+t <= 5) of
+        # 2 n q^2 BF16 flops each, two Grams per iteration
+        pairs = 21
+        tc_flops = sum(iters[t] * 2 * pairs * 2.0 * sizes[t] * q * q for t in range(len(sizes) - 1))
         peak = peaks.get("bf16_tflops_sustained", 1743.3)
-        ach = gram_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0
-        r = {"kernel": "gram", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-             "frac": ach / peak, "peak_source": peak_src, "traffic": None}
+        ach = tc_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0
+        r = {"kernel": "k_ozaki_nt (FP64-accurate Gram on BF16 tensor cores, mma.sync)", "bound": "tensor",
+             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+             "peak_source": f"{peak_src} bf16_tflops_sustained", "traffic": None,
+             "fp64_equivalent_tflops": gram_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0,
+             "launches_per_step": gram_launches}
     r["dominant_phase"] = dom
     r["phase_ms"] = phases
     return r

@@ -179,6 +179,17 @@ hsim_status hsim_gram(hsim_ctx *ctx, int n, int k_a, int k_b, const double *A_de
 hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int k, int m, const double *A_dev, int lda,
                              const double *B_dev, int ldb, double *C_dev, int ldc);
 
+/* The same two products evaluated on BF16 tensor cores with FP64 accuracy
+ * (mixed-precision path): every FP64 operand is split against a power of two
+ * per row or column into 6 integer digits of at most 8 bits, digit products
+ * are accumulated exactly in FP32 over chunks of 128 and summed in FP64; the
+ * result matches the FP64 product to about 2^-47 of the row/column maxima.
+ * Arguments as hsim_gram and hsim_gemm_update (G is ka x kb, ld kb). */
+hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int k_a, int k_b, const double *A_dev, int lda,
+                         const double *B_dev, int ldb, double *G_dev);
+hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int k, int m, const double *A_dev, int lda,
+                                const double *B_dev, int ldb, double *C_dev, int ldc);
+
 /* Dense generalised symmetric eigenproblem S_bar X = M_bar X Lambda (Alg. 1,
  * dense eigenproblem step; also the coarsest level of Alg. 3): Cholesky of
  * M_bar, cyclic Jacobi on C^-1 S_bar C^-T, back-transformation.  S_bar and

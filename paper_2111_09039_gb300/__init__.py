@@ -20,7 +20,8 @@ import numpy as np
 from . import _lib
 from ._lib import HSIM_FP64, HSIM_MIXED, HsimError, Info, Options, check, default_options, lib, ptr
 
-__all__ = ["Context", "Hierarchy", "assemble", "solve", "spmm", "gram", "gemm_update", "ritz",
+__all__ = ["Context", "Hierarchy", "assemble", "solve", "spmm", "gram", "gemm_update", "gram_tc",
+           "gemm_update_tc", "ritz",
            "galerkin", "shifted_solve", "check_symbolic", "default_options", "HsimError",
            "HSIM_FP64", "HSIM_MIXED", "kernel_launches"]
 
@@ -206,6 +207,24 @@ def gram(ctx: Context, A, B):
     check(lib().hsim_gram(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
                           B.stride(0), ptr(G)))
     return G
+
+
+def gram_tc(ctx: Context, A, B):
+    """A^T B with FP64 accuracy on BF16 tensor cores (digit splitting)."""
+    torch = _torch()
+    G = torch.empty((A.shape[1], B.shape[1]), dtype=torch.float64, device=A.device)
+    check(lib().hsim_gram_tc(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
+                             B.stride(0), ptr(G)))
+    return G
+
+
+def gemm_update_tc(ctx: Context, A, B):
+    """A B with FP64 accuracy on BF16 tensor cores (digit splitting)."""
+    torch = _torch()
+    C = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=A.device)
+    check(lib().hsim_gemm_update_tc(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
+                                    B.stride(0), ptr(C), C.stride(0)))
+    return C
 
 
 def gemm_update(ctx: Context, A, B):

@@ -132,6 +132,9 @@ struct hsim_hier {
     DevBuf<double> S0int, M0int, Md0int, dinv0, arena, dpos, ritz_work, Sbar, Mbar, lam, phibar, res_sums,
         Phi, Psi, SP, MP, coarseX, coarseLam, colw, tmpv, signs, tval_s, tval_m;
     std::vector<DevBuf<double>> Sv, Mv;  // level values (internal), index tau
+    // mixed precision: FP32 factor and FP32 right-hand-side blocks
+    DevBuf<float> arena32, dpos32, X32, R32;
+    DevBuf<unsigned char> oz;  // digit slices of the tensor-core products
 };
 
 namespace {
@@ -192,43 +195,44 @@ void upload_level(LevelData &L, cudaStream_t s) {
                        L.d_relmap.p};
 }
 
-// Numeric LDL^T of K = S - mu M on level L (values in internal order).
-// Returns the number of negative pivots (eigenvalues of (S, M) below mu).
-int factor_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, const double *S, const double *M, const double *Md,
-                 double mu) {
+// Numeric LDL^T of K = S - mu M on level L (values in internal order), with
+// the factor stored in precision T.  Returns the number of negative pivots
+// (eigenvalues of (S, M) below mu).  Pivots below rel_tol * max|K_ii| count as
+// a breakdown.
+template <typename T>
+int factor_level_t(hsim_ctx *ctx, LevelData &L, const double *S, const double *M, const double *Md, double mu,
+                   DevBuf<T> &arena, DevBuf<T> &dpos, double rel_tol) {
     cudaStream_t s = ctx->stream;
     FrontSymbolic &fs = L.fs;
-    H->arena.reserve((size_t)fs.arena);
-    H->dpos.reserve((size_t)L.n);
-    HSIM_CUDA(cudaMemsetAsync(H->arena.p, 0, (size_t)fs.arena * sizeof(double), s));
-    k::front_assemble(s, L.dpat.nnz, L.drow_of.p, L.dpat.col.p, L.d_asm.p, S, M, Md, mu, H->arena.p);
+    arena.reserve((size_t)fs.arena);
+    dpos.reserve((size_t)L.n);
+    HSIM_CUDA(cudaMemsetAsync(arena.p, 0, (size_t)fs.arena * sizeof(T), s));
+    k::front_assemble(s, L.dpat.nnz, L.drow_of.p, L.dpat.col.p, L.d_asm.p, S, M, Md, mu, arena.p);
     unsigned long long *mx = ctx->scratch_u64.p;
     HSIM_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
-    k::front_maxdiag(s, L.fd, fs.n_nodes, H->arena.p, mx);
+    k::front_maxdiag(s, L.fd, fs.n_nodes, (const T *)arena.p, mx);
     unsigned long long hmx = 0;
     HSIM_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaStreamSynchronize(s));
     double maxdiag;
     std::memcpy(&maxdiag, &hmx, sizeof(double));
-    const double tol = std::max(1e-13 * maxdiag, 1e-300);
+    const double tol = std::max(rel_tol * maxdiag, 1e-300);
     int *flags = ctx->flags.p;
     HSIM_CUDA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         int nea = (int)(L.ea_off[h + 1] - L.ea_off[h]);
-        if (nea > 0)
-            k::front_extend_add(s, L.fd, L.d_parent.p, L.d_ea.p + L.ea_off[h], nea, L.ea_maxu[h], H->arena.p);
+        if (nea > 0) k::front_extend_add(s, L.fd, L.d_parent.p, L.d_ea.p + L.ea_off[h], nea, L.ea_maxu[h], arena.p);
         for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
             int cnt = L.step_cnt[h][kst];
             int k0 = (int)kst * kPanel;
             int mrows = L.step_maxnf[h][kst] - k0 - 1;
-            k::front_panel(s, L.fd, nodes, cnt, k0, mrows, H->arena.p, tol, flags);
-            k::front_update(s, L.fd, nodes, cnt, k0, mrows, H->arena.p);
+            k::front_panel(s, L.fd, nodes, cnt, k0, mrows, arena.p, tol, flags);
+            k::front_update(s, L.fd, nodes, cnt, k0, mrows, arena.p);
         }
     }
-    // all nodes: 0..N-1 are listed in d_hnodes grouped by height; front_diag
-    // walks the concatenated list
-    k::front_diag(s, L.fd, L.d_hnodes.p, fs.n_nodes, H->arena.p, H->dpos.p, flags + 2);
+    // all nodes 0..N-1 are listed in d_hnodes grouped by height
+    k::front_diag(s, L.fd, L.d_hnodes.p, fs.n_nodes, (const T *)arena.p, dpos.p, flags + 2);
     HSIM_CUDA(cudaMemcpyAsync(ctx->hflags.data(), flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaStreamSynchronize(s));
     if (ctx->hflags[0] != 0)
@@ -237,7 +241,8 @@ int factor_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, const double *S, con
     return ctx->hflags[2];
 }
 
-void solve_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, double *X, int k, int ldx) {
+template <typename T>
+void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T *X, int k, int ldx) {
     cudaStream_t s = ctx->stream;
     const FrontSymbolic &fs = L.fs;
     for (int h = 0; h <= fs.max_height; ++h) {
@@ -245,20 +250,29 @@ void solve_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, double *X, int k, in
         for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
             int cnt = L.step_cnt[h][kst];
             int k0 = (int)kst * kPanel;
-            k::solve_fwd_tri(s, L.fd, nodes, cnt, k0, H->arena.p, k, X, ldx);
-            k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, H->arena.p, k, X, ldx);
+            k::solve_fwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
+            k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
         }
     }
-    k::solve_diag(s, L.n, k, H->dpos.p, X, ldx);
+    k::solve_diag(s, L.n, k, dpos, X, ldx);
     for (int h = fs.max_height; h >= 0; --h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         for (int kst = (int)L.step_cnt[h].size() - 1; kst >= 0; --kst) {
             int cnt = L.step_cnt[h][kst];
             int k0 = kst * kPanel;
-            k::solve_bwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, H->arena.p, k, X, ldx);
-            k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, H->arena.p, k, X, ldx);
+            k::solve_bwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
+            k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
         }
     }
+}
+
+int factor_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, const double *S, const double *M, const double *Md,
+                 double mu) {
+    return factor_level_t<double>(ctx, L, S, M, Md, mu, H->arena, H->dpos, 1e-13);
+}
+
+void solve_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, double *X, int k, int ldx) {
+    solve_level_t<double>(ctx, L, H->arena.p, H->dpos.p, X, k, ldx);
 }
 
 int subspace_q(int p, const hsim_options &o) {
@@ -427,9 +441,47 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         const double *Sx = tau == 0 ? H->S0int.p : H->Sv[tau].p;
         const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
         const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
+        const bool mixed = o.precision == HSIM_MIXED;
         Timer tf(s);
-        int negp = factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
+        int negp = mixed ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, 1e-7)
+                         : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
         inf.ms_factor += tf.stop();
+        if (mixed) {
+            H->X32.reserve((size_t)n * q);
+            H->R32.reserve((size_t)n * q);
+        }
+        // K^-1 B in the mixed path: B (FP64, n x a, ld q) rounded to FP32, solved
+        // with the FP32 factor, widened into X (FP64)
+        auto solve32 = [&](const double *B, double *X, int a) {
+            k::convert_matrix(s, n, a, B, q, H->X32.p, q);
+            solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->X32.p, a, q);
+            k::convert_matrix(s, n, a, H->X32.p, q, X, q);
+        };
+        // FP64 iterative refinement of X = K^-1 B with the FP32 factor: R =
+        // B - K X in FP64, X += K^-1 R, until the largest relative column
+        // residual is below 1e-14 or stops decreasing (at most 6 steps)
+        std::vector<double> rw(q), bw(q);
+        auto refine32 = [&](const double *B, double *X, double *R, int a) {
+            k::col_dots(s, n, a, B, q, B, q, (const double *)nullptr, H->colw.p);
+            HSIM_CUDA(cudaMemcpyAsync(bw.data(), H->colw.p, a * sizeof(double), cudaMemcpyDeviceToHost, s));
+            HSIM_CUDA(cudaStreamSynchronize(s));
+            double prev = INFINITY;
+            int steps = 0;
+            for (; steps < 6; ++steps) {
+                k::shifted_residual(s, n, L.dpat.ptr.p, L.dpat.col.p, Sx, Mx, Mdx, mu, a, X, q, B, q, R, q);
+                k::col_dots(s, n, a, R, q, R, q, (const double *)nullptr, H->colw.p);
+                HSIM_CUDA(cudaMemcpyAsync(rw.data(), H->colw.p, a * sizeof(double), cudaMemcpyDeviceToHost, s));
+                HSIM_CUDA(cudaStreamSynchronize(s));
+                double worst = 0.0;
+                for (int j = 0; j < a; ++j) worst = std::max(worst, std::sqrt(rw[j] / std::max(bw[j], 1e-300)));
+                if (worst < 1e-14 || worst > 0.5 * prev) break;
+                prev = worst;
+                k::convert_matrix(s, n, a, R, q, H->R32.p, q);
+                solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->R32.p, a, q);
+                k::add_f2d(s, n, a, H->R32.p, q, X, q);
+            }
+            return steps;
+        };
         if (trace_on())
             std::fprintf(stderr, "[hsim] level %d n=%d q=%d shift=%.10g negative_pivots=%d fronts=%d nnzL=%lld\n", tau,
                          n, q, mu, negp, L.fs.n_nodes, (long long)L.fs.nnz_L);
@@ -456,14 +508,29 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             const int a = q - locked;
             Timer ts(s);
             // inverse iterations on the active columns (Alg. 1, solve step; twice)
-            k::copy_matrix(s, n, a, H->MP.p + locked, q, H->Psi.p + locked, q);
-            solve_level(ctx, H, L, H->Psi.p + locked, a, q);
-            for (int extra = 1; extra < o.inv_iters; ++extra) {
-                apply_M(ctx, H, tau, a, H->Psi.p + locked, q, H->SP.p + locked, q);
-                k::copy_matrix(s, n, a, H->SP.p + locked, q, H->Psi.p + locked, q);
+            int refine_steps = 0;
+            if (mixed) {
+                // first: FP32 solve; its rounding noise in high frequencies is
+                // damped by the next inverse iteration.  Last: FP32 solve plus
+                // FP64 residual refinement
+                solve32(H->MP.p + locked, H->Psi.p + locked, a);
+                for (int extra = 1; extra < o.inv_iters; ++extra) {
+                    apply_M(ctx, H, tau, a, H->Psi.p + locked, q, H->SP.p + locked, q);
+                    solve32(H->SP.p + locked, H->Psi.p + locked, a);
+                }
+                double *rhs = o.inv_iters >= 2 ? H->SP.p : H->MP.p;
+                double *res_buf = o.inv_iters >= 2 ? H->MP.p : H->SP.p;
+                if (o.refine >= 0) refine_steps = refine32(rhs + locked, H->Psi.p + locked, res_buf + locked, a);
+            } else {
+                k::copy_matrix(s, n, a, H->MP.p + locked, q, H->Psi.p + locked, q);
                 solve_level(ctx, H, L, H->Psi.p + locked, a, q);
+                for (int extra = 1; extra < o.inv_iters; ++extra) {
+                    apply_M(ctx, H, tau, a, H->Psi.p + locked, q, H->SP.p + locked, q);
+                    k::copy_matrix(s, n, a, H->SP.p + locked, q, H->Psi.p + locked, q);
+                    solve_level(ctx, H, L, H->Psi.p + locked, a, q);
+                }
             }
-            if (refine) {
+            if (refine && !mixed) {
                 // right-hand side of the last solve: SP (two or more inverse
                 // iterations) or MP (one); the residual goes to the other buffer
                 double *rhs = o.inv_iters >= 2 ? H->SP.p : H->MP.p;
@@ -482,14 +549,33 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             k::scale_cols_rsqrt(s, n, q, H->colw.p, H->MP.p, q);
             apply_S(ctx, H, tau, q, H->Psi.p, q, H->SP.p, q);
             inf.ms_spmm += ts.stop();
-            k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
-            k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);
+            if (mixed) {
+                // FP64-accurate Grams on BF16 tensor cores: Psi split once
+                const size_t part = k::ozaki_cols_scratch(n, q);
+                H->oz.reserve(3 * part);
+                k::OzakiOperand X = k::ozaki_split_cols(s, n, q, H->Psi.p, q, H->oz.p);
+                k::OzakiOperand YS = k::ozaki_split_cols(s, n, q, H->SP.p, q, H->oz.p + part);
+                k::OzakiOperand YM = k::ozaki_split_cols(s, n, q, H->MP.p, q, H->oz.p + 2 * part);
+                k::ozaki_product(s, X, YS, X.ld, H->Sbar.p, q, 0);
+                k::ozaki_product(s, X, YM, X.ld, H->Mbar.p, q, 0);
+            } else {
+                k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
+                k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);
+            }
             inf.ms_gram += ts.stop();
             // dense eigenproblem (Alg. 1): Ritz values ascending, M-orthonormal
             ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps);
             inf.ms_ritz += ts.stop();
             // update Phi = Psi Phi_bar (Alg. 1)
-            k::gemm_nn(s, n, q, q, H->Psi.p, q, H->phibar.p, q, H->Phi.p, q);
+            if (mixed) {
+                const size_t part = k::ozaki_rows_scratch(n, q);
+                H->oz.reserve(part + k::ozaki_cols_scratch(q, q));
+                k::OzakiOperand X = k::ozaki_split_rows(s, n, q, H->Psi.p, q, H->oz.p);
+                k::OzakiOperand Y = k::ozaki_split_cols(s, q, q, H->phibar.p, q, H->oz.p + part);
+                k::ozaki_product(s, X, Y, X.ld, H->Phi.p, q, 1);
+            } else {
+                k::gemm_nn(s, n, q, q, H->Psi.p, q, H->phibar.p, q, H->Phi.p, q);
+            }
             inf.ms_update += ts.stop();
             // convergence test (eq. conv2)
             apply_S(ctx, H, tau, q, H->Phi.p, q, H->SP.p, q);
@@ -512,8 +598,9 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 if (i < p) maxres = std::max(maxres, res[i]);
             }
             if (trace_on())
-                std::fprintf(stderr, "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g\n",
-                             tau, it, locked, maxres, sweeps, (int)refine, lam_h[0], lam_h[p - 1]);
+                std::fprintf(stderr,
+                             "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g\n",
+                             tau, it, locked, maxres, sweeps, mixed ? refine_steps : (int)refine, lam_h[0], lam_h[p - 1]);
             if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
             if (maxres < tol) break;
             if (o.refine == 0 && !refine && it >= 2 && maxres > 0.7 * prev_maxres && maxres < 1e-6) refine = true;
@@ -803,7 +890,6 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *h, const double *S_val, const d
         HSIM_CHECK_ARG(tol > 0, "tol must be positive");
         DeviceGuard dg(ctx->device);
         hsim_options o = checked(opts ? opts : &h->opts);
-        HSIM_CHECK_ARG(o.precision == HSIM_FP64, "this build solves in FP64 only");
         run_solve(ctx, h, S_val, M_diag, p, tol, o, evals, evecs, info);
     });
 }
@@ -839,6 +925,34 @@ hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int kk, int m, const double *
         HSIM_CHECK_ARG(n >= 0 && kk >= 0 && m >= 0 && lda >= kk && ldb >= m && ldc >= m, "bad sizes");
         DeviceGuard dg(ctx->device);
         k::gemm_nn(ctx->stream, n, kk, m, A, lda, B, ldb, C, ldc);
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb,
+                         double *G) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && A && B && G, "NULL argument");
+        HSIM_CHECK_ARG(n >= 1 && ka >= 1 && kb >= 1 && lda >= ka && ldb >= kb, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        DevBuf<unsigned char> scratch(k::ozaki_cols_scratch(n, ka) + k::ozaki_cols_scratch(n, kb));
+        k::OzakiOperand X = k::ozaki_split_cols(ctx->stream, n, ka, A, lda, scratch.p);
+        k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, n, kb, B, ldb, scratch.p + k::ozaki_cols_scratch(n, ka));
+        k::ozaki_product(ctx->stream, X, Y, X.ld, G, kb, 0);
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
+hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int kk, int m, const double *A, int lda, const double *B,
+                                int ldb, double *C, int ldc) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && A && B && C, "NULL argument");
+        HSIM_CHECK_ARG(n >= 1 && kk >= 1 && m >= 1 && lda >= kk && ldb >= m && ldc >= m, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        DevBuf<unsigned char> scratch(k::ozaki_rows_scratch(n, kk) + k::ozaki_cols_scratch(kk, m));
+        k::OzakiOperand X = k::ozaki_split_rows(ctx->stream, n, kk, A, lda, scratch.p);
+        k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, kk, m, B, ldb, scratch.p + k::ozaki_rows_scratch(n, kk));
+        k::ozaki_product(ctx->stream, X, Y, X.ld, C, ldc, 1);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
     });
 }

@@ -43,18 +43,19 @@ constexpr int TB = 64;  // output tile
 constexpr int TK = 16;  // k step
 
 // G[i0:i0+64, j0:j0+64] += sum_{r in chunk} A[r, i] B[r, j]
-__global__ void __launch_bounds__(256) k_gram(int n, int ka, int kb, const double *__restrict__ A, int lda,
-                                              const double *__restrict__ B, int ldb, double *__restrict__ G,
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(int n, int ka, int kb, const T *__restrict__ A, int lda,
+                                              const T *__restrict__ B, int ldb, double *__restrict__ G,
                                               int ldg, int rows_per_split, int lower_only) {
     const int ti = blockIdx.x, tj = blockIdx.y;
     if (lower_only && tj > ti) return;
     const int i0 = ti * TB, j0 = tj * TB;
     const int r_beg = blockIdx.z * rows_per_split;
     const int r_end = min(n, r_beg + rows_per_split);
-    __shared__ double As[TK][TB];
-    __shared__ double Bs[TK][TB];
+    __shared__ T As[TK][TB];
+    __shared__ T Bs[TK][TB];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4] = {};
+    T acc[4][4] = {};
     for (int r0 = r_beg; r0 < r_end; r0 += TK) {
         for (int idx = threadIdx.x; idx < TK * TB; idx += 256) {
             int c = idx & 63, rr = idx >> 6;
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(256) k_gram(int n, int ka, int kb, const doubl
         __syncthreads();
 #pragma unroll
         for (int rr = 0; rr < TK; ++rr) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 a[u] = As[rr][ty + 16 * u];
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) k_gram(int n, int ka, int kb, const doubl
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             int j = j0 + tx + 16 * v;
-            if (j < kb && (!lower_only || j <= i)) atomicAdd(&G[(size_t)i * ldg + j], acc[u][v]);
+            if (j < kb && (!lower_only || j <= i)) atomicAdd(&G[(size_t)i * ldg + j], (double)acc[u][v]);
         }
     }
 }
@@ -98,25 +99,26 @@ __global__ void k_mirror_lower(int k, double *__restrict__ G, int ldg) {
 }
 
 // C[r0:r0+64, j0:j0+64] = A[r, :] B[:, j]
-__global__ void __launch_bounds__(256) k_gemm_nn(int n, int kk, int m, const double *__restrict__ A, int lda,
-                                                 const double *__restrict__ B, int ldb, double *__restrict__ C,
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_nn(int n, int kk, int m, const T *__restrict__ A, int lda,
+                                                 const double *__restrict__ B, int ldb, T *__restrict__ C,
                                                  int ldc) {
     const int r0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
-    __shared__ double As[TK][TB + 1];
-    __shared__ double Bs[TK][TB];
+    __shared__ T As[TK][TB + 1];
+    __shared__ T Bs[TK][TB];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4] = {};
+    T acc[4][4] = {};
     for (int k0 = 0; k0 < kk; k0 += TK) {
         for (int idx = threadIdx.x; idx < TK * TB; idx += 256) {
             int c = idx % TK, r = idx / TK;  // A tile: 64 rows x 16 cols
             As[c][r] = (r0 + r < n && k0 + c < kk) ? A[(size_t)(r0 + r) * lda + k0 + c] : 0.0;
             int jj = idx & 63, kr = idx >> 6;  // B tile: 16 rows x 64 cols
-            Bs[kr][jj] = (k0 + kr < kk && j0 + jj < m) ? B[(size_t)(k0 + kr) * ldb + j0 + jj] : 0.0;
+            Bs[kr][jj] = (k0 + kr < kk && j0 + jj < m) ? (T)B[(size_t)(k0 + kr) * ldb + j0 + jj] : T(0);
         }
         __syncthreads();
 #pragma unroll
         for (int c = 0; c < TK; ++c) {
-            double a[4], b[4];
+            T a[4], b[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 a[u] = As[c][ty + 16 * u];
@@ -143,28 +145,31 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int n, int kk, int m, const dou
 
 constexpr int kRowsPerBlock = 256;
 
-__global__ void k_col_dots(int n, int k, const double *__restrict__ X, int ldx, const double *__restrict__ Y, int ldy,
+template <typename T>
+__global__ void k_col_dots(int n, int k, const T *__restrict__ X, int ldx, const T *__restrict__ Y, int ldy,
                            const double *__restrict__ d, double *__restrict__ w) {
     const int r_beg = blockIdx.x * kRowsPerBlock;
     const int r_end = min(n, r_beg + kRowsPerBlock);
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
         double acc = 0.0;
         for (int r = r_beg; r < r_end; ++r) {
-            double v = X[(size_t)r * ldx + j] * Y[(size_t)r * ldy + j];
+            double v = (double)X[(size_t)r * ldx + j] * (double)Y[(size_t)r * ldy + j];
             acc += d ? v * d[r] : v;
         }
         atomicAdd(&w[j], acc);
     }
 }
 
-__global__ void k_scale_cols_rsqrt(int n, int k, const double *__restrict__ w, double *__restrict__ X, int ldx) {
+template <typename T>
+__global__ void k_scale_cols_rsqrt(int n, int k, const double *__restrict__ w, T *__restrict__ X, int ldx) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * k) return;
     int i = (int)(idx / k), j = (int)(idx % k);
-    X[(size_t)i * ldx + j] *= rsqrt(w[j]);
+    X[(size_t)i * ldx + j] = (T)((double)X[(size_t)i * ldx + j] * rsqrt(w[j]));
 }
 
-__global__ void k_residual_sums(int n, int k, const double *__restrict__ SP, int lds, const double *__restrict__ MP,
+template <typename T>
+__global__ void k_residual_sums(int n, int k, const T *__restrict__ SP, int lds, const T *__restrict__ MP,
                                 int ldm, const double *__restrict__ lam, const double *__restrict__ dinv,
                                 double *__restrict__ out) {
     const int r_beg = blockIdx.x * kRowsPerBlock;
@@ -401,8 +406,9 @@ DenseFront &dense_front(int k, cudaStream_t s) {
 
 }  // namespace
 
-void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb, double *G,
-          int ldg, bool lower_only) {
+template <typename T>
+void gram(cudaStream_t s, int n, int ka, int kb, const T *A, int lda, const T *B, int ldb, double *G, int ldg,
+          bool lower_only) {
     if (ldg == kb) {
         HSIM_CUDA(cudaMemsetAsync(G, 0, (size_t)ka * kb * sizeof(double), s));
     } else {
@@ -416,7 +422,7 @@ void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const
     rows = (rows + TK - 1) / TK * TK;
     unsigned splits = cdiv(n, rows);
     dim3 g(ti, tj, splits);
-    k_gram<<<g, 256, 0, s>>>(n, ka, kb, A, lda, B, ldb, G, ldg, (int)rows, lower_only ? 1 : 0);
+    k_gram<T><<<g, 256, 0, s>>>(n, ka, kb, A, lda, B, ldb, G, ldg, (int)rows, lower_only ? 1 : 0);
     HSIM_LAUNCHED();
     if (lower_only) {
         k_mirror_lower<<<cdiv((int64_t)ka * ka, 256), 256, 0, s>>>(ka, G, ldg);
@@ -424,37 +430,50 @@ void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const
     }
 }
 
-void gemm_nn(cudaStream_t s, int n, int kk, int m, const double *A, int lda, const double *B, int ldb, double *C,
-             int ldc) {
+template <typename T>
+void gemm_nn(cudaStream_t s, int n, int kk, int m, const T *A, int lda, const double *B, int ldb, T *C, int ldc) {
     if (n <= 0 || m <= 0) return;
     dim3 g(cdiv(n, TB), cdiv(m, TB));
-    k_gemm_nn<<<g, 256, 0, s>>>(n, kk, m, A, lda, B, ldb, C, ldc);
+    k_gemm_nn<T><<<g, 256, 0, s>>>(n, kk, m, A, lda, B, ldb, C, ldc);
     HSIM_LAUNCHED();
 }
 
-void col_dots(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y, int ldy, const double *d,
-              double *w) {
+template <typename T>
+void col_dots(cudaStream_t s, int n, int k, const T *X, int ldx, const T *Y, int ldy, const double *d, double *w) {
     HSIM_CUDA(cudaMemsetAsync(w, 0, (size_t)k * sizeof(double), s));
     if (n <= 0 || k <= 0) return;
     dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
-    k_col_dots<<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, d, w);
+    k_col_dots<T><<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, d, w);
     HSIM_LAUNCHED();
 }
 
-void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, double *X, int ldx) {
+template <typename T>
+void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, T *X, int ldx) {
     if (n <= 0 || k <= 0) return;
-    k_scale_cols_rsqrt<<<cdiv((int64_t)n * k, 256), 256, 0, s>>>(n, k, w, X, ldx);
+    k_scale_cols_rsqrt<T><<<cdiv((int64_t)n * k, 256), 256, 0, s>>>(n, k, w, X, ldx);
     HSIM_LAUNCHED();
 }
 
-void residual_sums(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
-                   const double *lam, const double *dinv, double *out) {
+template <typename T>
+void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *MP, int ldm, const double *lam,
+                   const double *dinv, double *out) {
     HSIM_CUDA(cudaMemsetAsync(out, 0, (size_t)3 * k * sizeof(double), s));
     if (n <= 0 || k <= 0) return;
     dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
-    k_residual_sums<<<g, 256, 0, s>>>(n, k, SP, lds, MP, ldm, lam, dinv, out);
+    k_residual_sums<T><<<g, 256, 0, s>>>(n, k, SP, lds, MP, ldm, lam, dinv, out);
     HSIM_LAUNCHED();
 }
+
+#define HSIM_DENSE_INSTANTIATE(T)                                                                              \
+    template void gram<T>(cudaStream_t, int, int, int, const T *, int, const T *, int, double *, int, bool);  \
+    template void gemm_nn<T>(cudaStream_t, int, int, int, const T *, int, const double *, int, T *, int);    \
+    template void col_dots<T>(cudaStream_t, int, int, const T *, int, const T *, int, const double *, double *); \
+    template void scale_cols_rsqrt<T>(cudaStream_t, int, int, const double *, T *, int);                       \
+    template void residual_sums<T>(cudaStream_t, int, int, const T *, int, const T *, int, const double *,     \
+                                   const double *, double *);
+
+HSIM_DENSE_INSTANTIATE(float)
+HSIM_DENSE_INSTANTIATE(double)
 
 size_t ritz_work_size(int k) { return (size_t)6 * k * k + 4 * (size_t)k + 64; }
 

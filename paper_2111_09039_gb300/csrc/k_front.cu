@@ -40,10 +40,11 @@ __device__ __forceinline__ void tri_index(int64_t x, int &ti, int &tj) {
     tj = (int)(x - (int64_t)t * (t + 1) / 2);
 }
 
+template <typename T>
 __global__ void k_front_assemble(int64_t nnz, const int *__restrict__ row_of, const int *__restrict__ col,
                                  const int64_t *__restrict__ dst, const double *__restrict__ S,
                                  const double *__restrict__ M, const double *__restrict__ Md, double mu,
-                                 double *__restrict__ arena) {
+                                 T *__restrict__ arena) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nnz) return;
     int64_t d = dst[e];
@@ -55,24 +56,25 @@ __global__ void k_front_assemble(int64_t nnz, const int *__restrict__ row_of, co
         int r = row_of[e];
         if (r == col[e]) v -= mu * Md[r];
     }
-    arena[d] = v;
+    arena[d] = (T)v;
 }
 
 // extend-add of the update blocks of `children` into their parents
+template <typename T>
 __global__ void k_extend_add(FrontDev fd, const int *__restrict__ parent, const int *__restrict__ children,
-                             double *__restrict__ arena) {
+                             T *__restrict__ arena) {
     const int c = children[blockIdx.x];
     const int nsc = fd.ns[c], nfc = fd.nf[c];
     const int u = nfc - nsc;
-    const int T = (u + 31) / 32;
+    const int nt = (u + 31) / 32;
     int ti, tj;
     tri_index(blockIdx.y, ti, tj);
-    if (ti >= T) return;
+    if (ti >= nt) return;
     const int p = parent[c];
     const int nfp = fd.nf[p];
     const int *rel = fd.relmap + fd.relmap_off[c];
-    const double *Fc = arena + fd.foff[c];
-    double *Fp = arena + fd.foff[p];
+    const T *Fc = arena + fd.foff[c];
+    T *Fp = arena + fd.foff[p];
     const int jl = threadIdx.x & 31;
     const int j = tj * 32 + jl;
     if (j >= u) return;
@@ -80,21 +82,22 @@ __global__ void k_extend_add(FrontDev fd, const int *__restrict__ parent, const 
     for (int il = threadIdx.x >> 5; il < 32; il += blockDim.x >> 5) {
         int i = ti * 32 + il;
         if (i >= u || i < j) continue;
-        double v = Fc[(int64_t)(nsc + j) * nfc + (nsc + i)];
-        if (v != 0.0) atomicAdd(&Fp[(int64_t)pj * nfp + rel[i]], v);
+        T v = Fc[(int64_t)(nsc + j) * nfc + (nsc + i)];
+        if (v != T(0)) atomicAdd(&Fp[(int64_t)pj * nfp + rel[i]], v);
     }
 }
 
 // Factor the kb x kb diagonal block held in smem column-major D[c][r]
 // (LDL^T, unit L below the diagonal, D on the diagonal).
-__device__ void ldlt_block(double (*Dg)[P + 1], int kb, double tol, int *flags) {
-    __shared__ double lj[P];
+template <typename T>
+__device__ void ldlt_block(T (*Dg)[P + 1], int kb, double tol, int *flags) {
+    __shared__ T lj[P];
     for (int j = 0; j < kb; ++j) {
         __syncthreads();
-        double d = Dg[j][j];
-        if (!(fabs(d) >= tol)) {  // also catches NaN
+        T d = Dg[j][j];
+        if (!(fabs((double)d) >= tol)) {  // also catches NaN
             if (threadIdx.x == 0) atomicAdd(&flags[0], 1);
-            d = (d < 0.0) ? -tol : tol;
+            d = (d < T(0)) ? (T)-tol : (T)tol;
         }
         for (int i = j + 1 + threadIdx.x; i < kb; i += blockDim.x) lj[i] = Dg[j][i] / d;
         __syncthreads();
@@ -114,14 +117,15 @@ constexpr int kPanelRows = 128;
 
 // LDL^T of the kb x kb diagonal block of panel k0, one CTA per front,
 // written back in place (unit L below the diagonal, D on it).
+template <typename T>
 __global__ void __launch_bounds__(128) k_front_diag_block(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                          double *__restrict__ arena, double tol, int *flags) {
-    __shared__ double Dg[P][P + 1];
+                                                          T *__restrict__ arena, double tol, int *flags) {
+    __shared__ T Dg[P][P + 1];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t];
     const int kb = min(P, ns - k0);
     if (kb <= 0) return;
-    double *F = arena + fd.foff[t];
+    T *F = arena + fd.foff[t];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
         Dg[c][r] = (r >= c) ? F[(int64_t)(k0 + c) * nf + (k0 + r)] : 0.0;
@@ -135,16 +139,17 @@ __global__ void __launch_bounds__(128) k_front_diag_block(FrontDev fd, const int
 
 // Rows below the diagonal block: x L11^T = a, l = x / d, with L11 and D
 // read from the block factored by k_front_diag_block in the previous launch.
+template <typename T>
 __global__ void __launch_bounds__(128) k_front_panel(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                     double *__restrict__ arena) {
-    __shared__ double Dg[P][P + 1];
+                                                     T *__restrict__ arena) {
+    __shared__ T Dg[P][P + 1];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t];
     const int kb = min(P, ns - k0);
     if (kb <= 0) return;
     const int r0 = k0 + kb + blockIdx.y * kPanelRows;
     if (r0 >= nf) return;
-    double *F = arena + fd.foff[t];
+    T *F = arena + fd.foff[t];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
         Dg[c][r] = (r >= c) ? F[(int64_t)(k0 + c) * nf + (k0 + r)] : 0.0;
@@ -152,14 +157,14 @@ __global__ void __launch_bounds__(128) k_front_panel(FrontDev fd, const int *__r
     __syncthreads();
     const int r = r0 + threadIdx.x;
     if (r < nf) {
-        double x[P];
+        T x[P];
 #pragma unroll
         for (int c = 0; c < P; ++c)
             if (c < kb) x[c] = F[(int64_t)(k0 + c) * nf + r];
 #pragma unroll
         for (int c = 0; c < P; ++c) {
             if (c < kb) {
-                double v = x[c];
+                T v = x[c];
 #pragma unroll
                 for (int cc = 0; cc < P; ++cc)
                     if (cc < c) v -= x[cc] * Dg[cc][c];
@@ -173,10 +178,11 @@ __global__ void __launch_bounds__(128) k_front_panel(FrontDev fd, const int *__r
 }
 
 // A22 -= L21 D L21^T on 64 x 64 lower-triangular tiles of the trailing block
+template <typename T>
 __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                      double *__restrict__ arena) {
-    __shared__ double Lr[P][64];
-    __shared__ double Lc[P][64];
+                                                      T *__restrict__ arena) {
+    __shared__ T Lr[P][64];
+    __shared__ T Lc[P][64];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t];
     const int kb = min(P, ns - k0);
@@ -184,17 +190,17 @@ __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__
     const int base = k0 + kb;
     const int m = nf - base;
     if (m <= 0) return;
-    const int T = (m + 63) / 64;
+    const int nt = (m + 63) / 64;
     int ti, tj;
     tri_index(blockIdx.y, ti, tj);
-    if (ti >= T) return;
-    double *F = arena + fd.foff[t];
+    if (ti >= nt) return;
+    T *F = arena + fd.foff[t];
     const int r0 = base + ti * 64, c0 = base + tj * 64;
     for (int idx = threadIdx.x; idx < P * 64; idx += blockDim.x) {
         int i = idx & 63, kk = idx >> 6;
-        double vr = 0.0, vc = 0.0;
+        T vr = 0.0, vc = 0.0;
         if (kk < kb) {
-            double d = F[(int64_t)(k0 + kk) * nf + (k0 + kk)];
+            T d = F[(int64_t)(k0 + kk) * nf + (k0 + kk)];
             if (r0 + i < nf) vr = F[(int64_t)(k0 + kk) * nf + (r0 + i)];
             if (c0 + i < nf) vc = F[(int64_t)(k0 + kk) * nf + (c0 + i)] * d;
         }
@@ -203,9 +209,9 @@ __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__
     }
     __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4] = {};
+    T acc[4][4] = {};
     for (int kk = 0; kk < kb; ++kk) {
-        double a[4], b[4];
+        T a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             a[u] = Lr[kk][ty + 16 * u];
@@ -228,29 +234,31 @@ __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__
     }
 }
 
+template <typename T>
 __global__ void k_front_diag(FrontDev fd, const int *__restrict__ nodes, int n_nodes,
-                             const double *__restrict__ arena, double *__restrict__ dpos, int *neg) {
+                             const T *__restrict__ arena, T *__restrict__ dpos, int *neg) {
     int t_idx = blockIdx.x;
     if (t_idx >= n_nodes) return;
     int t = nodes[t_idx];
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
-    const double *F = arena + fd.foff[t];
+    const T *F = arena + fd.foff[t];
     int cnt = 0;
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-        double d = F[(int64_t)i * nf + i];
+        T d = F[(int64_t)i * nf + i];
         dpos[ps + i] = d;
-        cnt += (d < 0.0);
+        cnt += (d < T(0));
     }
     if (cnt) atomicAdd(neg, cnt);
 }
 
-__global__ void k_front_maxdiag(FrontDev fd, const double *__restrict__ arena, unsigned long long *out) {
+template <typename T>
+__global__ void k_front_maxdiag(FrontDev fd, const T *__restrict__ arena, unsigned long long *out) {
     const int t = blockIdx.x;
     const int nf = fd.nf[t], ns = fd.ns[t];
-    const double *F = arena + fd.foff[t];
+    const T *F = arena + fd.foff[t];
     unsigned long long best = 0;
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-        unsigned long long b = (unsigned long long)__double_as_longlong(fabs(F[(int64_t)i * nf + i]));
+        unsigned long long b = (unsigned long long)__double_as_longlong(fabs((double)F[(int64_t)i * nf + i]));
         best = b > best ? b : best;
     }
     if (best) atomicMax(out, best);
@@ -260,15 +268,16 @@ __global__ void k_front_maxdiag(FrontDev fd, const double *__restrict__ arena, u
 constexpr int kTriCols = 128;
 
 // X[panel rows, cols] = L11^-1 X[...]  (unit lower, forward)
+template <typename T>
 __global__ void __launch_bounds__(kTriCols) k_solve_fwd_tri(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                            const double *__restrict__ arena, int k,
-                                                            double *__restrict__ X, int ldx) {
-    __shared__ double L[P][P + 1];
+                                                            const T *__restrict__ arena, int k,
+                                                            T *__restrict__ X, int ldx) {
+    __shared__ T L[P][P + 1];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
     const int kb = min(P, ns - k0);
     if (kb <= 0) return;
-    const double *F = arena + fd.foff[t];
+    const T *F = arena + fd.foff[t];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
         L[r][c] = (r > c) ? F[(int64_t)(k0 + c) * nf + (k0 + r)] : 0.0;
@@ -276,15 +285,15 @@ __global__ void __launch_bounds__(kTriCols) k_solve_fwd_tri(FrontDev fd, const i
     __syncthreads();
     const int j = blockIdx.y * kTriCols + threadIdx.x;
     if (j >= k) return;
-    double x[P];
-    double *Xb = X + (size_t)(ps + k0) * ldx + j;
+    T x[P];
+    T *Xb = X + (size_t)(ps + k0) * ldx + j;
 #pragma unroll
     for (int r = 0; r < P; ++r)
         if (r < kb) x[r] = Xb[(size_t)r * ldx];
 #pragma unroll
     for (int r = 1; r < P; ++r) {
         if (r < kb) {
-            double v = x[r];
+            T v = x[r];
 #pragma unroll
             for (int c = 0; c < P; ++c)
                 if (c < r) v -= L[r][c] * x[c];
@@ -299,11 +308,12 @@ __global__ void __launch_bounds__(kTriCols) k_solve_fwd_tri(FrontDev fd, const i
 // X[row(r), cols] -= sum_c L[r, k0+c] X[panel row c, cols] for front rows
 // r >= k0 + kb; pivot rows of the front are updated in place, rows of
 // ancestor fronts with atomics (sibling fronts share them).
+template <typename T>
 __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                       const double *__restrict__ arena, int k,
-                                                       double *__restrict__ X, int ldx) {
-    __shared__ double Ls[P][64];
-    __shared__ double Xs[P][64];
+                                                       const T *__restrict__ arena, int k,
+                                                       T *__restrict__ X, int ldx) {
+    __shared__ T Ls[P][64];
+    __shared__ T Xs[P][64];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
     const int kb = min(P, ns - k0);
@@ -313,11 +323,11 @@ __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *_
     if (r0 >= nf) return;
     const int c0 = blockIdx.z * 64;
     if (c0 >= k) return;
-    const double *F = arena + fd.foff[t];
+    const T *F = arena + fd.foff[t];
     const int *rows = fd.rows + fd.rows_off[t];
     for (int idx = threadIdx.x; idx < P * 64; idx += blockDim.x) {
         int i = idx & 63, kk = idx >> 6;
-        double lv = 0.0, xv = 0.0;
+        T lv = 0.0, xv = 0.0;
         if (kk < kb) {
             if (r0 + i < nf) lv = F[(int64_t)(k0 + kk) * nf + (r0 + i)];
             if (c0 + i < k) xv = X[(size_t)(ps + k0 + kk) * ldx + c0 + i];
@@ -327,9 +337,9 @@ __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *_
     }
     __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[4][4] = {};
+    T acc[4][4] = {};
     for (int kk = 0; kk < kb; ++kk) {
-        double a[4], b[4];
+        T a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             a[u] = Ls[kk][ty + 16 * u];
@@ -345,7 +355,7 @@ __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *_
         int r = r0 + ty + 16 * u;
         if (r >= nf) continue;
         int grow = rows[r];
-        double *xr = X + (size_t)grow * ldx;
+        T *xr = X + (size_t)grow * ldx;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             int c = c0 + tx + 16 * v;
@@ -356,7 +366,8 @@ __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *_
     }
 }
 
-__global__ void k_solve_diag(int n, int k, const double *__restrict__ dpos, double *__restrict__ X, int ldx) {
+template <typename T>
+__global__ void k_solve_diag(int n, int k, const T *__restrict__ dpos, T *__restrict__ X, int ldx) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)n * k) return;
     int i = (int)(idx / k), j = (int)(idx % k);
@@ -365,11 +376,12 @@ __global__ void k_solve_diag(int n, int k, const double *__restrict__ dpos, doub
 
 // X[panel rows c, cols] -= sum_{r >= k0+kb} L[r, k0+c] X[row(r), cols]
 // split over 32-row chunks of r, accumulated with atomics.
+template <typename T>
 __global__ void __launch_bounds__(256) k_solve_bwd_upd(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                       const double *__restrict__ arena, int k,
-                                                       double *__restrict__ X, int ldx) {
-    __shared__ double Ls[P][P + 1];  // [r][c]
-    __shared__ double Xs[P][64];     // [r][col]
+                                                       const T *__restrict__ arena, int k,
+                                                       T *__restrict__ X, int ldx) {
+    __shared__ T Ls[P][P + 1];  // [r][c]
+    __shared__ T Xs[P][64];     // [r][col]
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
     const int kb = min(P, ns - k0);
@@ -379,7 +391,7 @@ __global__ void __launch_bounds__(256) k_solve_bwd_upd(FrontDev fd, const int *_
     if (r0 >= nf) return;
     const int c0 = blockIdx.z * 64;
     if (c0 >= k) return;
-    const double *F = arena + fd.foff[t];
+    const T *F = arena + fd.foff[t];
     const int *rows = fd.rows + fd.rows_off[t];
     for (int idx = threadIdx.x; idx < P * P; idx += blockDim.x) {
         int r = idx % P, c = idx / P;
@@ -392,9 +404,9 @@ __global__ void __launch_bounds__(256) k_solve_bwd_upd(FrontDev fd, const int *_
     __syncthreads();
     // 32 x 64 outputs, 8 per thread: thread -> column j = tid & 63, rows c = (tid >> 6) + 4u
     const int j = threadIdx.x & 63, cb = threadIdx.x >> 6;
-    double acc[8] = {};
+    T acc[8] = {};
     for (int r = 0; r < P; ++r) {
-        double xv = Xs[r][j];
+        T xv = Xs[r][j];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[u] += Ls[r][cb + 4 * u] * xv;
     }
@@ -408,15 +420,16 @@ __global__ void __launch_bounds__(256) k_solve_bwd_upd(FrontDev fd, const int *_
 }
 
 // X[panel rows, cols] = L11^-T X[...]  (unit upper, backward)
+template <typename T>
 __global__ void __launch_bounds__(kTriCols) k_solve_bwd_tri(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                            const double *__restrict__ arena, int k,
-                                                            double *__restrict__ X, int ldx) {
-    __shared__ double L[P][P + 1];
+                                                            const T *__restrict__ arena, int k,
+                                                            T *__restrict__ X, int ldx) {
+    __shared__ T L[P][P + 1];
     const int t = nodes[blockIdx.x];
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
     const int kb = min(P, ns - k0);
     if (kb <= 0) return;
-    const double *F = arena + fd.foff[t];
+    const T *F = arena + fd.foff[t];
     for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
         int r = idx % kb, c = idx / kb;
         L[r][c] = (r > c) ? F[(int64_t)(k0 + c) * nf + (k0 + r)] : 0.0;
@@ -424,15 +437,15 @@ __global__ void __launch_bounds__(kTriCols) k_solve_bwd_tri(FrontDev fd, const i
     __syncthreads();
     const int j = blockIdx.y * kTriCols + threadIdx.x;
     if (j >= k) return;
-    double x[P];
-    double *Xb = X + (size_t)(ps + k0) * ldx + j;
+    T x[P];
+    T *Xb = X + (size_t)(ps + k0) * ldx + j;
 #pragma unroll
     for (int r = 0; r < P; ++r)
         if (r < kb) x[r] = Xb[(size_t)r * ldx];
 #pragma unroll
     for (int r = P - 2; r >= 0; --r) {
         if (r < kb - 1) {
-            double v = x[r];
+            T v = x[r];
 #pragma unroll
             for (int c = 0; c < P; ++c)
                 if (c > r && c < kb) v -= L[c][r] * x[c];
@@ -448,92 +461,121 @@ inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b);
 
 }  // namespace
 
+template <typename T>
 void front_assemble(cudaStream_t s, int64_t nnz, const int *row_of, const int *col, const int64_t *dst,
-                    const double *S_val, const double *M_val, const double *M_diag, double mu, double *arena) {
+                    const double *S_val, const double *M_val, const double *M_diag, double mu, T *arena) {
     if (nnz <= 0) return;
-    k_front_assemble<<<cdiv(nnz, 256), 256, 0, s>>>(nnz, row_of, col, dst, S_val, M_val, M_diag, mu, arena);
+    k_front_assemble<T><<<cdiv(nnz, 256), 256, 0, s>>>(nnz, row_of, col, dst, S_val, M_val, M_diag, mu, arena);
     HSIM_LAUNCHED();
 }
 
+template <typename T>
 void front_extend_add(cudaStream_t s, const FrontDev &fd, const int *parent, const int *children, int n_children,
-                      int max_upd, double *arena) {
+                      int max_upd, T *arena) {
     if (n_children <= 0 || max_upd <= 0) return;
-    int64_t T = (max_upd + 31) / 32;
-    dim3 g((unsigned)n_children, (unsigned)(T * (T + 1) / 2));
-    k_extend_add<<<g, 256, 0, s>>>(fd, parent, children, arena);
+    int64_t Tt = (max_upd + 31) / 32;
+    dim3 g((unsigned)n_children, (unsigned)(Tt * (Tt + 1) / 2));
+    k_extend_add<T><<<g, 256, 0, s>>>(fd, parent, children, arena);
     HSIM_LAUNCHED();
 }
 
-void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_rows,
-                 double *arena, double pivot_tol, int *flags) {
+template <typename T>
+void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_rows, T *arena,
+                 double pivot_tol, int *flags) {
     if (n_nodes <= 0) return;
-    k_front_diag_block<<<(unsigned)n_nodes, 128, 0, s>>>(fd, nodes, k0, arena, pivot_tol, flags);
+    k_front_diag_block<T><<<(unsigned)n_nodes, 128, 0, s>>>(fd, nodes, k0, arena, pivot_tol, flags);
     HSIM_LAUNCHED();
     if (max_rows <= 0) return;
     dim3 g((unsigned)n_nodes, cdiv(max_rows, kPanelRows));
-    k_front_panel<<<g, 128, 0, s>>>(fd, nodes, k0, arena);
+    k_front_panel<T><<<g, 128, 0, s>>>(fd, nodes, k0, arena);
     HSIM_LAUNCHED();
 }
 
-void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_trail,
-                  double *arena) {
+template <typename T>
+void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_trail, T *arena) {
     if (n_nodes <= 0 || max_trail <= 0) return;
-    int64_t T = (max_trail + 63) / 64;
-    dim3 g((unsigned)n_nodes, (unsigned)(T * (T + 1) / 2));
-    k_front_update<<<g, 256, 0, s>>>(fd, nodes, k0, arena);
+    int64_t Tt = (max_trail + 63) / 64;
+    dim3 g((unsigned)n_nodes, (unsigned)(Tt * (Tt + 1) / 2));
+    k_front_update<T><<<g, 256, 0, s>>>(fd, nodes, k0, arena);
     HSIM_LAUNCHED();
 }
 
-void front_maxdiag(cudaStream_t s, const FrontDev &fd, int n_nodes, const double *arena, unsigned long long *out) {
+template <typename T>
+void front_maxdiag(cudaStream_t s, const FrontDev &fd, int n_nodes, const T *arena, unsigned long long *out) {
     if (n_nodes <= 0) return;
-    k_front_maxdiag<<<n_nodes, 128, 0, s>>>(fd, arena, out);
+    k_front_maxdiag<T><<<n_nodes, 128, 0, s>>>(fd, arena, out);
     HSIM_LAUNCHED();
 }
 
-void front_diag(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, const double *arena,
-                double *dpos, int *neg_count) {
+template <typename T>
+void front_diag(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, const T *arena, T *dpos,
+                int *neg_count) {
     if (n_nodes <= 0) return;
-    k_front_diag<<<n_nodes, 128, 0, s>>>(fd, nodes, n_nodes, arena, dpos, neg_count);
+    k_front_diag<T><<<n_nodes, 128, 0, s>>>(fd, nodes, n_nodes, arena, dpos, neg_count);
     HSIM_LAUNCHED();
 }
 
-void solve_fwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, const double *arena,
-                   int k, double *X, int ldx) {
+template <typename T>
+void solve_fwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, const T *arena, int k,
+                   T *X, int ldx) {
     if (n_nodes <= 0 || k <= 0) return;
     dim3 g((unsigned)n_nodes, cdiv(k, kTriCols));
-    k_solve_fwd_tri<<<g, kTriCols, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
+    k_solve_fwd_tri<T><<<g, kTriCols, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
     HSIM_LAUNCHED();
 }
 
+template <typename T>
 void solve_fwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_rows,
-                   const double *arena, int k, double *X, int ldx) {
+                   const T *arena, int k, T *X, int ldx) {
     if (n_nodes <= 0 || k <= 0 || max_rows <= 0) return;
     dim3 g((unsigned)n_nodes, cdiv(max_rows, 64), cdiv(k, 64));
-    k_solve_fwd_upd<<<g, 256, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
+    k_solve_fwd_upd<T><<<g, 256, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
     HSIM_LAUNCHED();
 }
 
-void solve_diag(cudaStream_t s, int n, int k, const double *dpos, double *X, int ldx) {
+template <typename T>
+void solve_diag(cudaStream_t s, int n, int k, const T *dpos, T *X, int ldx) {
     if (n <= 0 || k <= 0) return;
-    k_solve_diag<<<cdiv((int64_t)n * k, 256), 256, 0, s>>>(n, k, dpos, X, ldx);
+    k_solve_diag<T><<<cdiv((int64_t)n * k, 256), 256, 0, s>>>(n, k, dpos, X, ldx);
     HSIM_LAUNCHED();
 }
 
+template <typename T>
 void solve_bwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_rows,
-                   const double *arena, int k, double *X, int ldx) {
+                   const T *arena, int k, T *X, int ldx) {
     if (n_nodes <= 0 || k <= 0 || max_rows <= 0) return;
     dim3 g((unsigned)n_nodes, cdiv(max_rows, P), cdiv(k, 64));
-    k_solve_bwd_upd<<<g, 256, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
+    k_solve_bwd_upd<T><<<g, 256, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
     HSIM_LAUNCHED();
 }
 
-void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, const double *arena,
-                   int k, double *X, int ldx) {
+template <typename T>
+void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, const T *arena, int k,
+                   T *X, int ldx) {
     if (n_nodes <= 0 || k <= 0) return;
     dim3 g((unsigned)n_nodes, cdiv(k, kTriCols));
-    k_solve_bwd_tri<<<g, kTriCols, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
+    k_solve_bwd_tri<T><<<g, kTriCols, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
     HSIM_LAUNCHED();
 }
+
+#define HSIM_FRONT_INSTANTIATE(T)                                                                                  \
+    template void front_assemble<T>(cudaStream_t, int64_t, const int *, const int *, const int64_t *,            \
+                                    const double *, const double *, const double *, double, T *);               \
+    template void front_extend_add<T>(cudaStream_t, const FrontDev &, const int *, const int *, int, int, T *);  \
+    template void front_panel<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, T *, double, int *);  \
+    template void front_update<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, T *);              \
+    template void front_maxdiag<T>(cudaStream_t, const FrontDev &, int, const T *, unsigned long long *);        \
+    template void front_diag<T>(cudaStream_t, const FrontDev &, const int *, int, const T *, T *, int *);        \
+    template void solve_fwd_tri<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int); \
+    template void solve_fwd_upd<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, const T *, int, T *, \
+                                   int);                                                                         \
+    template void solve_diag<T>(cudaStream_t, int, int, const T *, T *, int);                                    \
+    template void solve_bwd_upd<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, const T *, int, T *, \
+                                   int);                                                                         \
+    template void solve_bwd_tri<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int);
+
+HSIM_FRONT_INSTANTIATE(float)
+HSIM_FRONT_INSTANTIATE(double)
 
 }  // namespace k
 }  // namespace hsim

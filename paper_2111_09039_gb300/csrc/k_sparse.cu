@@ -316,6 +316,38 @@ __global__ void k_reciprocal(int n, const double *__restrict__ x, double *__rest
     if (i < n) y[i] = 1.0 / x[i];
 }
 
+template <typename Tin, typename Tout>
+__global__ void k_convert_matrix(int rows, int cols, const Tin *__restrict__ X, int ldx, Tout *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    Y[(size_t)i * ldy + j] = (Tout)X[(size_t)i * ldx + j];
+}
+
+// Y (FP64) += X (FP32)
+__global__ void k_add_f2d(int rows, int cols, const float *__restrict__ X, int ldx, double *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    Y[(size_t)i * ldy + j] += (double)X[(size_t)i * ldx + j];
+}
+
+template <typename T>
+__global__ void k_copy_matrix_t(int rows, int cols, const T *__restrict__ X, int ldx, T *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j];
+}
+
+__global__ void k_diag_scale_f(int n, int k, const float *__restrict__ d, const float *__restrict__ X, int ldx,
+                               float *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * k) return;
+    int i = (int)(idx / k), j = (int)(idx % k);
+    Y[(size_t)i * ldy + j] = d[i] * X[(size_t)i * ldx + j];
+}
+
 __global__ void k_f2d(int64_t n, const float *__restrict__ x, double *__restrict__ y) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = (double)x[i];
@@ -444,6 +476,32 @@ void output_evecs(cudaStream_t s, int n, int p, const int *iperm, const double *
     k_col_sign<<<p, 256, 0, s>>>(n, Phi, ldp, scratch_p);
     HSIM_LAUNCHED();
     k_output_evecs<<<grid1d((int64_t)n * p, 256), 256, 0, s>>>(n, p, iperm, Phi, ldp, scratch_p, out);
+    HSIM_LAUNCHED();
+}
+
+void convert_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, float *Y, int ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_convert_matrix<double, float><<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_convert_matrix<float, double><<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_add_f2d<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+void copy_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, float *Y, int ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_copy_matrix_t<float><<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+void diag_scale(cudaStream_t s, int n, int k, const float *d, const float *X, int ldx, float *Y, int ldy) {
+    if (n <= 0 || k <= 0) return;
+    k_diag_scale_f<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, d, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+struct __nv_bfloat16;
+
 namespace hsim {
 namespace k {
 
@@ -54,26 +56,38 @@ void densify_diag(cudaStream_t s, int n, const double *d, double *D);
 void output_evecs(cudaStream_t s, int n, int p, const int *iperm, const double *Phi, int ldp,
                   double *out, double *scratch_p);
 void copy_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, double *Y, int ldy);
+// strided type conversions and FP32 helpers of the mixed-precision path
+void convert_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, float *Y, int ldy);
+void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
+// Y (FP64) += X (FP32)
+void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
+void copy_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, float *Y, int ldy);
+void diag_scale(cudaStream_t s, int n, int k, const float *d, const float *X, int ldx, float *Y, int ldy);
 // y = 1 / x
 void reciprocal(cudaStream_t s, int n, const double *x, double *y);
 void convert_f2d(cudaStream_t s, int64_t n, const float *x, double *y);
 void convert_d2f(cudaStream_t s, int64_t n, const double *x, float *y);
 
 // ---- dense (k_dense.cu) ---------------------------------------------------
-// G (ka x kb, ld ldg) = A^T B over n rows; G is overwritten
-void gram(cudaStream_t s, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb,
+// G (ka x kb, ld ldg, FP64) = A^T B over n rows; G is overwritten
+template <typename T>
+void gram(cudaStream_t s, int n, int ka, int kb, const T *A, int lda, const T *B, int ldb,
           double *G, int ldg, bool lower_only);
-// C (n x m) = A (n x k) B (k x m)
-void gemm_nn(cudaStream_t s, int n, int k, int m, const double *A, int lda, const double *B, int ldb,
-             double *C, int ldc);
-// w_j = sum_i X[i,j] * Y[i,j] * (d ? d[i] : 1)   (column dot products, w overwritten)
-void col_dots(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y, int ldy,
+// C (n x m) = A (n x k) B (k x m), B in FP64
+template <typename T>
+void gemm_nn(cudaStream_t s, int n, int k, int m, const T *A, int lda, const double *B, int ldb,
+             T *C, int ldc);
+// w_j = sum_i X[i,j] * Y[i,j] * (d ? d[i] : 1)   (column dot products in FP64, w overwritten)
+template <typename T>
+void col_dots(cudaStream_t s, int n, int k, const T *X, int ldx, const T *Y, int ldy,
               const double *d, double *w);
-// X[:, j] *= f[j] with f[j] = 1/sqrt(w[j])
-void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, double *X, int ldx);
+// X[:, j] *= 1/sqrt(w[j])
+template <typename T>
+void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, T *X, int ldx);
 // residual sums: out[3j+0] = sum w R^2, +1 = sum w (S Phi)^2, +2 = sum w (M Phi)^2
 // with R = SPhi - lam * MPhi; w = dinv (M^{-1}-norm) or 1 (2-norm)
-void residual_sums(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
+template <typename T>
+void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *MP, int ldm,
                    const double *lam, const double *dinv, double *out);
 // dense symmetric generalised eigensolver (Cholesky + Jacobi), k x k
 // returns 0 ok, 1 not SPD; sweeps via *sweeps
@@ -90,29 +104,62 @@ struct FrontDev {
     const int64_t *relmap_off;
     const int *relmap;
 };
+template <typename T>
 void front_assemble(cudaStream_t s, int64_t nnz, const int *row_of, const int *col, const int64_t *dst,
-                    const double *S_val, const double *M_val, const double *M_diag, double mu,
-                    double *arena);
+                    const double *S_val, const double *M_val, const double *M_diag, double mu, T *arena);
+template <typename T>
 void front_extend_add(cudaStream_t s, const FrontDev &fd, const int *parent, const int *children,
-                      int n_children, int max_upd, double *arena);
+                      int n_children, int max_upd, T *arena);
+template <typename T>
 void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                 int max_rows, double *arena, double pivot_tol, int *flags);
+                 int max_rows, T *arena, double pivot_tol, int *flags);
+template <typename T>
 void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                  int max_trail, double *arena);
+                  int max_trail, T *arena);
 // max |F_t[i,i]| over the pivots of nodes 0..n_nodes-1 (bit pattern of a
 // non-negative double, atomically maximised into *out)
-void front_maxdiag(cudaStream_t s, const FrontDev &fd, int n_nodes, const double *arena, unsigned long long *out);
-void front_diag(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, const double *arena,
-                double *dpos, int *neg_count);
+template <typename T>
+void front_maxdiag(cudaStream_t s, const FrontDev &fd, int n_nodes, const T *arena, unsigned long long *out);
+template <typename T>
+void front_diag(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, const T *arena,
+                T *dpos, int *neg_count);
+template <typename T>
 void solve_fwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                   const double *arena, int k, double *X, int ldx);
+                   const T *arena, int k, T *X, int ldx);
+template <typename T>
 void solve_fwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                   int max_rows, const double *arena, int k, double *X, int ldx);
-void solve_diag(cudaStream_t s, int n, int k, const double *dpos, double *X, int ldx);
+                   int max_rows, const T *arena, int k, T *X, int ldx);
+template <typename T>
+void solve_diag(cudaStream_t s, int n, int k, const T *dpos, T *X, int ldx);
+template <typename T>
 void solve_bwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                   int max_rows, const double *arena, int k, double *X, int ldx);
+                   int max_rows, const T *arena, int k, T *X, int ldx);
+template <typename T>
 void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                   const double *arena, int k, double *X, int ldx);
+                   const T *arena, int k, T *X, int ldx);
+
+// ---- FP64-accurate products on BF16 tensor cores (k_ozaki.cu) --------------
+constexpr int kOzakiSlices = 6;
+// digit slices of an FP64 block: kOzakiSlices arrays of `rows` x ld BF16
+// (K contiguous, zero padded), with one exponent per row
+struct OzakiOperand {
+    int rows = 0, ld = 0;
+    size_t stride = 0;
+    __nv_bfloat16 *slices = nullptr;
+    int *exps = nullptr;
+};
+// bytes of scratch for splitting an n x cols block per column (K = n), or a
+// rows x k block per row (K = k)
+size_t ozaki_cols_scratch(int n, int cols);
+size_t ozaki_rows_scratch(int rows, int k);
+// split X (row-major, K = n rows) per column into a transposed operand
+OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch);
+// split X (row-major rows x k, K = k) per row
+OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch);
+// C (X.rows x Y.rows, FP64) = X Y^T over K = k_len; splits <= 0 chooses a
+// split-K count (C accumulated with atomics), 1 stores directly
+void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y, int k_len, double *C, int ldc,
+                   int splits);
 
 }  // namespace k
 }  // namespace hsim

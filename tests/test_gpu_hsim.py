@@ -168,3 +168,38 @@ def test_no_convergence_is_reported(hs, ctx):
     with pytest.raises(hs.HsimError) as e:
         hs.solve(ctx, hier, S, Md, 20, 1e-14, max_iters=1)
     assert e.value.name == "HSIM_E_NO_CONVERGENCE"
+
+
+# ---- mixed precision: FP32 factor/solves with FP64 refinement, FP64-accurate
+# tensor-core Gram/update, FP64 Ritz ------------------------------------------
+def mixed_solve(hs, ctx, mesh, p, levels, tol, start):
+    hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=p, levels=levels, start_vertex=start,
+                        precision=hs.HSIM_MIXED)
+    S, Md = hs.assemble(ctx, hier, V=dev(mesh.V))
+    lam, Phi, info = hs.solve(ctx, hier, S, Md, p, tol, precision=hs.HSIM_MIXED, levels=levels,
+                              start_vertex=start)
+    return lam.cpu().numpy(), Phi.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("name", ["bumpy_torus_64", "icosphere3_noise"])
+def test_mixed_matches_oracle_tight(hs, ctx, name):
+    """At tol 1e-10 the mixed path reaches FP64 accuracy."""
+    w, mesh, s = synth.make_workload(name)
+    lam, Phi, info = mixed_solve(hs, ctx, mesh, w.p, w.levels, w.tol, s)
+    ref = sim.hsim(mesh, w.p, w.levels, w.tol, s)
+    scale = np.maximum(np.abs(ref.lam), ref.lam[1])
+    assert np.max(np.abs(lam - ref.lam) / scale) < 1e-9
+    res, S, M = residual_fp64(mesh, lam, Phi)
+    assert res.max() < 1e-9
+
+
+def test_mixed_three_levels_loose_tolerance(hs, ctx):
+    """tol 1e-5: eigenvalues within 1e-6 of the oracle, FP64 residual <= 1e-5."""
+    mesh = synth.displaced_icosphere(5, 9)
+    p, start = 60, 11
+    lam, Phi, info = mixed_solve(hs, ctx, mesh, p, 3, 1e-5, start)
+    ref = sim.hsim(mesh, p, 3, 1e-10, start)
+    scale = np.maximum(np.abs(ref.lam), ref.lam[1])
+    assert np.max(np.abs(lam - ref.lam) / scale) < 1e-6
+    res, S, M = residual_fp64(mesh, lam, Phi)
+    assert res[:p].max() <= 1e-5

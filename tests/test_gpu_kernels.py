@@ -227,3 +227,42 @@ def _values_in(A, rp, cl):
         for e in range(rp[i], rp[i + 1]):
             out[e] = row.get(int(cl[e]), 0.0)
     return out
+
+
+# ---- FP64-accurate products on BF16 tensor cores ----------------------------
+def _ozaki_bound(X, Y, K):
+    """K * 2^-45 * (row/col max of |X|) * (row/col max of |Y|): the digit split
+    keeps 47 bits per value relative to its group maximum."""
+    return K * 2.0 ** -45 * np.abs(X).max(axis=1)[:, None] * np.abs(Y).max(axis=1)[None, :]
+
+
+@pytest.mark.parametrize("n,ka,kb", [(1, 1, 1), (1000, 30, 30), (4099, 75, 150), (70001, 130, 65)])
+def test_gram_tc_matches_fp64(hs, ctx, n, ka, kb):
+    rng = np.random.default_rng(n + 7)
+    A = rng.standard_normal((n, ka)) * np.exp(rng.standard_normal((n, 1)))
+    B = rng.standard_normal((n, kb))
+    G = hs.gram_tc(ctx, dev(A), dev(B)).cpu().numpy()
+    ref = A.T @ B
+    bound = _ozaki_bound(A.T, B.T, n) + 8 * n * EPS * (np.abs(A).T @ np.abs(B))
+    assert np.all(np.abs(G - ref) <= bound)
+
+
+@pytest.mark.parametrize("n,k,m", [(1, 1, 1), (1000, 30, 30), (4099, 75, 75), (20011, 131, 67), (3001, 750, 750)])
+def test_gemm_update_tc_matches_fp64(hs, ctx, n, k, m):
+    rng = np.random.default_rng(k + 3)
+    A = rng.standard_normal((n, k))
+    B = rng.standard_normal((k, m)) * 10.0 ** rng.uniform(-3, 3, size=(1, m))
+    C = hs.gemm_update_tc(ctx, dev(A), dev(B)).cpu().numpy()
+    ref = A @ B
+    bound = _ozaki_bound(A, B.T, k) + 8 * k * EPS * (np.abs(A) @ np.abs(B))
+    assert np.all(np.abs(C - ref) <= bound)
+
+
+def test_gram_tc_exact_on_small_integers(hs, ctx):
+    """Integers with few significant bits are represented exactly by the
+    digits: the product must equal the exact integer result."""
+    rng = np.random.default_rng(5)
+    A = rng.integers(-1000, 1000, size=(3000, 40)).astype(np.float64)
+    B = rng.integers(-1000, 1000, size=(3000, 24)).astype(np.float64)
+    G = hs.gram_tc(ctx, dev(A), dev(B)).cpu().numpy()
+    np.testing.assert_array_equal(G, A.T @ B)
