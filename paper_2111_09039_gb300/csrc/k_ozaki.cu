@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "common.h"
 #include "kernels.h"
@@ -258,6 +259,12 @@ int sm_count_oz() {
 void launch_nt(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int ldx, size_t xstride,
                const __nv_bfloat16 *Ys, int ldy, size_t ystride, const int *ex, const int *ey, double *C, int ldc,
                int k_len, int splits) {
+    // the kernel reads the digit slices as 16-byte vectors: every slice base
+    // and every row start must be 16-byte aligned
+    auto aligned16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    HSIM_CHECK_ARG(aligned16(Xs) && aligned16(Ys) && ldx % 8 == 0 && ldy % 8 == 0 && xstride % 8 == 0 &&
+                       ystride % 8 == 0 && k_len % TKs == 0,
+                   "ozaki product: operand not 16-byte aligned");
     const size_t sm = smem_bytes();
     HSIM_CUDA(cudaFuncSetAttribute(k_ozaki_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int k_split = (int)((k_len + splits - 1) / splits);
@@ -273,14 +280,18 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
+// Scratch sizes are whole multiples of 256 bytes, so operands placed back to
+// back in one buffer keep the 16-byte alignment of the vector loads.
 size_t ozaki_cols_scratch(int n, int cols) {
     const int ldk = round_up(n, TKs);
-    return (size_t)kSlices * cols * ldk * sizeof(__nv_bfloat16) + sizeof(int) * (size_t)cols + 256;
+    size_t b = (size_t)kSlices * cols * ldk * sizeof(__nv_bfloat16) + sizeof(int) * (size_t)cols;
+    return (b + 511) / 256 * 256;
 }
 
 size_t ozaki_rows_scratch(int rows, int k) {
     const int ldk = round_up(k, TKs);
-    return (size_t)kSlices * rows * ldk * sizeof(__nv_bfloat16) + sizeof(int) * (size_t)rows + 256;
+    size_t b = (size_t)kSlices * rows * ldk * sizeof(__nv_bfloat16) + sizeof(int) * (size_t)rows;
+    return (b + 511) / 256 * 256;
 }
 
 OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch) {
