@@ -58,7 +58,10 @@ typedef struct {
     int max_iters;       /* subspace iterations per level before HSIM_E_NO_CONVERGENCE */
     int inv_iters;       /* inverse iterations per Rayleigh-Ritz step (paper: 2) */
     double lock_factor;  /* lock a converged prefix below lock_factor * tol */
-    int precision;       /* HSIM_FP64 or HSIM_MIXED */
+    int precision;       /* HSIM_FP64: every step in FP64.  HSIM_MIXED: the Gram
+                            products and the basis update on BF16 tensor cores with
+                            FP64-accurate digit splitting (hsim_gram_tc); factor,
+                            solves, Ritz and residuals stay FP64 */
     int start_vertex;    /* first vertex of farthest-point sampling (Alg. 2) */
     int leaf_size;       /* nested-dissection leaf size (tuning, default 32) */
     int q;               /* subspace size; <= 0 selects max(ceil(1.5p), p+8) */

@@ -441,12 +441,19 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         const double *Sx = tau == 0 ? H->S0int.p : H->Sv[tau].p;
         const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
         const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
+        // Mixed precision: the dense products run on BF16 tensor cores with
+        // FP64 accuracy (digit splitting); the factor and the solves stay FP64.
+        // (An FP32 factor with FP64 residual refinement was tried: the
+        // pivot-free indefinite LDL^T shows element growth near 5e4, so FP32
+        // solves are only ~3e-3 accurate and the refinement stops contracting
+        // when the shift lies inside the spectrum.)
         const bool mixed = o.precision == HSIM_MIXED;
+        const bool fp32_solves = false;
         Timer tf(s);
-        int negp = mixed ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, 1e-7)
-                         : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
+        int negp = fp32_solves ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, 1e-7)
+                               : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
         inf.ms_factor += tf.stop();
-        if (mixed) {
+        if (fp32_solves) {
             H->X32.reserve((size_t)n * q);
             H->R32.reserve((size_t)n * q);
         }
@@ -509,7 +516,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             Timer ts(s);
             // inverse iterations on the active columns (Alg. 1, solve step; twice)
             int refine_steps = 0;
-            if (mixed) {
+            if (fp32_solves) {
                 // first: FP32 solve; its rounding noise in high frequencies is
                 // damped by the next inverse iteration.  Last: FP32 solve plus
                 // FP64 residual refinement
@@ -530,7 +537,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                     solve_level(ctx, H, L, H->Psi.p + locked, a, q);
                 }
             }
-            if (refine && !mixed) {
+            if (refine && !fp32_solves) {
                 // right-hand side of the last solve: SP (two or more inverse
                 // iterations) or MP (one); the residual goes to the other buffer
                 double *rhs = o.inv_iters >= 2 ? H->SP.p : H->MP.p;
@@ -600,7 +607,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             if (trace_on())
                 std::fprintf(stderr,
                              "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g\n",
-                             tau, it, locked, maxres, sweeps, mixed ? refine_steps : (int)refine, lam_h[0], lam_h[p - 1]);
+                             tau, it, locked, maxres, sweeps, fp32_solves ? refine_steps : (int)refine, lam_h[0],
+                             lam_h[p - 1]);
             if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
             if (maxres < tol) break;
             if (o.refine == 0 && !refine && it >= 2 && maxres > 0.7 * prev_maxres && maxres < 1e-6) refine = true;
