@@ -135,23 +135,45 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// Error-free accumulation of x into (hi, lo): hi + lo gains x exactly up to
+// the rounding of lo (Knuth's TwoSum in FP32; the FP32 pipe is ~60x the FP64
+// pipe on this part).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    float s = __fadd_rn(hi, x);
+    float bp = __fsub_rn(s, hi);
+    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+constexpr int kStageElems = kSlices * (TM + TN) * kRow;  // bf16 per pipeline stage
+
 // C[i0.., j0..] (+)= 2^(ex_i + ey_j - 14) sum_D 2^(-8 D) sum_{s+t=D} X_s Y_t^T over
 // rows k in [k_beg, k_end).  X slices: M x ldx, Y slices: N x ldy (K contiguous,
-// ld multiples of 8, zero padded to a multiple of TKs).
+// ld multiples of 8, zero padded to a multiple of TKs).  Two pipeline stages
+// filled with cp.async; each 128-row chunk of exact FP32 digit sums is added
+// into an FP32 (hi, lo) pair per output with TwoSum.
 __global__ void __launch_bounds__(256, 1)
     k_ozaki_nt(int M, int N, const __nv_bfloat16 *__restrict__ Xs, int ldx, size_t xstride,
                const __nv_bfloat16 *__restrict__ Ys, int ldy, size_t ystride, const int *__restrict__ ex,
                const int *__restrict__ ey, double *__restrict__ C, int ldc, int k_len, int k_split, int atomic) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16 *As = reinterpret_cast<__nv_bfloat16 *>(smem_raw);  // [kSlices][TM][kRow]
-    __nv_bfloat16 *Bs = As + (size_t)kSlices * TM * kRow;              // [kSlices][TN][kRow]
+    __nv_bfloat16 *stage0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
     const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
     const int k_beg = blockIdx.z * k_split;
     const int k_end = min(k_len, k_beg + k_split);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp & 3, wn = warp >> 2;  // warp tile rows wm*16, cols wn*32
     float acc[kSlices][4][4];
-    double acc64[4][4];
+    float hi[4][4], lo[4][4];
 #pragma unroll
     for (int d = 0; d < kSlices; ++d)
 #pragma unroll
@@ -161,10 +183,13 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
     for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc64[t][e] = 0.0;
-    int since_flush = 0;
-    for (int kk = k_beg; kk < k_end; kk += TKs) {
-        // stage the K step: every slice of the 64 x 32 X and Y blocks, 16-byte chunks
+        for (int e = 0; e < 4; ++e) hi[t][e] = lo[t][e] = 0.f;
+
+    // stage the K step starting at kk into buffer `buf`: every slice of the
+    // 64 x 32 X and Y blocks, 16-byte chunks, zero-filled outside the operands
+    auto load_stage = [&](int buf, int kk) {
+        __nv_bfloat16 *As = stage0 + (size_t)buf * kStageElems;
+        __nv_bfloat16 *Bs = As + (size_t)kSlices * TM * kRow;
         constexpr int chunks = kSlices * TM * (TKs / 8);  // per operand
         for (int c = threadIdx.x; c < 2 * chunks; c += blockDim.x) {
             const bool isB = c >= chunks;
@@ -174,16 +199,25 @@ __global__ void __launch_bounds__(256, 1)
             const int row = rem / (TKs / 8), part = rem % (TKs / 8);
             const int grow = (isB ? j0 : i0) + row;
             const int lim = isB ? N : M;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (grow < lim && kk + part * 8 < k_end) {
-                const __nv_bfloat16 *src = isB ? Ys + (size_t)s * ystride + (size_t)grow * ldy + kk + part * 8
-                                               : Xs + (size_t)s * xstride + (size_t)grow * ldx + kk + part * 8;
-                v = *reinterpret_cast<const uint4 *>(src);
-            }
+            const bool ok = grow < lim && kk + part * 8 < k_end;
+            const __nv_bfloat16 *src = isB ? Ys + (size_t)s * ystride + (size_t)(ok ? grow : 0) * ldy + (ok ? kk + part * 8 : 0)
+                                           : Xs + (size_t)s * xstride + (size_t)(ok ? grow : 0) * ldx + (ok ? kk + part * 8 : 0);
             __nv_bfloat16 *dst = (isB ? Bs : As) + ((size_t)s * TM + row) * kRow + part * 8;
-            *reinterpret_cast<uint4 *>(dst) = v;
+            cp_async16(dst, src, ok ? 16 : 0);
         }
+    };
+
+    int buf = 0;
+    if (k_beg < k_end) load_stage(0, k_beg);
+    cp_async_commit();
+    int since_flush = 0;
+    for (int kk = k_beg; kk < k_end; kk += TKs) {
+        if (kk + TKs < k_end) load_stage(buf ^ 1, kk + TKs);
+        cp_async_commit();
+        cp_async_wait_1();
         __syncthreads();
+        const __nv_bfloat16 *As = stage0 + (size_t)buf * kStageElems;
+        const __nv_bfloat16 *Bs = As + (size_t)kSlices * TM * kRow;
 #pragma unroll
         for (int k16 = 0; k16 < TKs; k16 += 16) {
             unsigned a[kSlices][4];
@@ -211,22 +245,24 @@ __global__ void __launch_bounds__(256, 1)
             }
         }
         __syncthreads();
+        buf ^= 1;
         since_flush += TKs;
         if (since_flush >= kFlush || kk + TKs >= k_end) {
             since_flush = 0;
 #pragma unroll
             for (int d = 0; d < kSlices; ++d) {
-                const double w = ldexp(1.0, -8 * d);
+                const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8 d), exact
 #pragma unroll
                 for (int t = 0; t < 4; ++t)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        acc64[t][e] += w * (double)acc[d][t][e];
+                        two_sum_acc(hi[t][e], lo[t][e], __fmul_rn(acc[d][t][e], w));
                         acc[d][t][e] = 0.f;
                     }
             }
         }
     }
+    cp_async_wait_0();
     // epilogue: C fragment (row g / g+8, cols 2*tig + {0,1}) per n-tile
     const int g = lane >> 2, tig = lane & 3;
 #pragma unroll
@@ -236,14 +272,14 @@ __global__ void __launch_bounds__(256, 1)
             const int i = i0 + wm * 16 + g + (e >= 2 ? 8 : 0);
             const int j = j0 + wn * 32 + nt * 8 + tig * 2 + (e & 1);
             if (i < M && j < N) {
-                const double v = ldexp(acc64[nt][e], ex[i] + ey[j] - 14);
+                const double v = ldexp((double)hi[nt][e] + (double)lo[nt][e], ex[i] + ey[j] - 14);
                 if (atomic) atomicAdd(&C[(size_t)i * ldc + j], v);
                 else C[(size_t)i * ldc + j] = v;
             }
         }
 }
 
-size_t smem_bytes() { return (size_t)kSlices * (TM + TN) * kRow * sizeof(__nv_bfloat16); }
+size_t smem_bytes() { return 2 * (size_t)kStageElems * sizeof(__nv_bfloat16); }
 
 int sm_count_oz() {
     static int n = 0;
