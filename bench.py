@@ -144,7 +144,14 @@ def main():
     ap.add_argument("--sample-cols", type=int, default=8)
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm"],
+                    help="time one step-level kernel on random data instead of the solve (profiling)")
+    ap.add_argument("--rows", type=int, default=200000)
+    ap.add_argument("--cols", type=int, default=750)
     args = ap.parse_args()
+    if args.kernel:
+        run_kernel(args)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -277,6 +284,50 @@ def main():
         "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "info": info,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_kernel(args):
+    """One step-level kernel on seeded random data (rows x cols FP64 blocks):
+    two untimed calls, then `steps` timed calls with CUDA events."""
+    import torch
+
+    import paper_2111_09039_gb300 as hs
+    ctx = hs.Context(0)
+    g = torch.Generator(device="cuda:0").manual_seed(0)
+    n, q = args.rows, args.cols
+    A = torch.randn((n, q), dtype=torch.float64, device="cuda:0", generator=g)
+    B = torch.randn((n, q), dtype=torch.float64, device="cuda:0", generator=g)
+    P = torch.randn((q, q), dtype=torch.float64, device="cuda:0", generator=g)
+    if args.kernel == "spmm":
+        import synth
+        w, mesh, start = synth.make_workload("bumpy_torus_1000" if n >= 10**6 else "bumpy_torus_100")
+        hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, levels=w.levels, start_vertex=start)
+        S, Md = hs.assemble(ctx, hier, V=torch.as_tensor(mesh.V, device="cuda:0"))
+        rp, cl = hier.pattern()
+        A = torch.randn((mesh.n, q), dtype=torch.float64, device="cuda:0", generator=g)
+        fn = lambda: hs.spmm(ctx, rp, cl, S, A)
+        flops, nbytes = 2.0 * S.numel() * q, 16.0 * mesh.n * q + 12.0 * S.numel()
+    elif args.kernel in ("gram", "gram_tc"):
+        f = hs.gram if args.kernel == "gram" else hs.gram_tc
+        fn = lambda: f(ctx, A, B)
+        flops, nbytes = 2.0 * n * q * q, 16.0 * n * q
+    else:
+        f = hs.gemm_update if args.kernel == "update" else hs.gemm_update_tc
+        fn = lambda: f(ctx, A, P)
+        flops, nbytes = 2.0 * n * q * q, 16.0 * n * q
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(max(1, args.steps)):
+        fn()
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms,
+                      "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12,
+                      "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}), flush=True)
 
 
 def check_residual(hier, S, Md, lam, Phi, ctx):
