@@ -160,6 +160,27 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *hier, const double *S_val_dev,
                        const double *M_diag_dev, int p, double tol, const hsim_options *opts,
                        double *evals_dev, double *evecs_dev, hsim_info *info);
 
+/* Shape gradient of a loss of the eigenvalues (first-order perturbation of
+ * S Phi = lambda M Phi for M-normalised eigenvectors, differentiated through
+ * the cotan stiffness and lumped mass of Sec. 3.1, eq. massStiffMatrices):
+ *     dV[v] = sum_{i<p} dloss_dlambda[i] * phi_i^T (dS/dx_v - lambda_i dM/dx_v) phi_i.
+ * For the spectral loss sum_i (lambda_i - lambda*_i)^2 pass
+ * dloss_dlambda[i] = 2 (lambda_i - lambda*_i).  Valid for simple
+ * eigenvalues; inside a cluster of equal eigenvalues only a loss symmetric
+ * in the cluster has a gradient.
+ *   V_dev          n x 3 positions (row-major)
+ *   F_dev          n_tris x 3 vertex indices in [0, n); triangles of
+ *                  positive area (the cotangents divide by it)
+ *   evals_dev      p eigenvalues; evecs_dev n x p COLUMN-major, leading
+ *                  dimension n (as hsim_solve writes them), M-orthonormal
+ *   dloss_dlambda_dev  p weights
+ *   dV_dev         out: n x 3 row-major, overwritten
+ * All device pointers on the context's device; the call returns after the
+ * context's stream drained.  Indices are not range-checked on the device. */
+hsim_status hsim_eig_grad(hsim_ctx *ctx, int n, int n_tris, const double *V_dev, const int32_t *F_dev,
+                          int p, const double *evals_dev, const double *evecs_dev,
+                          const double *dloss_dlambda_dev, double *dV_dev);
+
 /* --------------------------------------------------------------------------
  * Step-level entry points: each runs one step of the hot path on caller
  * buffers, for parity tests and benchmarking of single kernels.

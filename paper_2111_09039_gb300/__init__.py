@@ -190,6 +190,56 @@ def solve(ctx: Context, hier: Hierarchy, S_val, M_diag, p: int, tol: float,
     return lam, vecs.t(), info.to_dict()
 
 
+def eig_grad(ctx: Context, V, F, evals, evecs, dloss_dlambda):
+    """sum_i dloss_dlambda[i] * d lambda_i / dV  (n x 3) on the GPU; evecs is
+    n x p, M-orthonormal (as ``solve`` returns it)."""
+    torch = _torch()
+    dev = f"cuda:{ctx.device}"
+    Vt = torch.as_tensor(V, dtype=torch.float64, device=dev).contiguous()
+    Ft = torch.as_tensor(F, dtype=torch.int32, device=dev).contiguous()
+    lam = torch.as_tensor(evals, dtype=torch.float64, device=dev).contiguous()
+    E = torch.as_tensor(evecs, dtype=torch.float64, device=dev).t().contiguous()   # column-major n x p
+    w = torch.as_tensor(dloss_dlambda, dtype=torch.float64, device=dev).contiguous()
+    n, p = Vt.shape[0], lam.numel()
+    if E.shape != (p, n) or w.numel() != p:
+        raise ValueError("evecs must be n x p and dloss_dlambda of length p")
+    dV = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    check(lib().hsim_eig_grad(ctx.handle, n, Ft.shape[0], ptr(Vt), ptr(Ft), p, ptr(lam), ptr(E), ptr(w), ptr(dV)))
+    return dV
+
+
+def _eigenvalue_function():
+    torch = _torch()
+
+    class Eigenvalues(torch.autograd.Function):
+        """lambda_{0..p-1}(V) through assemble + solve; the backward pass is
+        one ``hsim_eig_grad`` call (the hierarchy is held fixed: the
+        eigenpairs do not depend on it)."""
+
+        @staticmethod
+        def forward(fctx, V, ctx, hier, F, p, tol, options):
+            S, Md = assemble(ctx, hier, V=V.detach())
+            lam, vecs, _ = solve(ctx, hier, S, Md, p, tol, options)
+            fctx.save_for_backward(V, lam, vecs)
+            fctx.hsim = (ctx, F)
+            return lam
+
+        @staticmethod
+        def backward(fctx, grad_lam):
+            V, lam, vecs = fctx.saved_tensors
+            ctx, F = fctx.hsim
+            dV = eig_grad(ctx, V.detach(), F, lam, vecs, grad_lam.to(torch.float64))
+            return dV.to(V.dtype), None, None, None, None, None, None
+
+    return Eigenvalues
+
+
+def eigenvalues(ctx: Context, hier: Hierarchy, V, F, p: int, tol: float, options: Options | None = None):
+    """Differentiable p lowest eigenvalues of the cotan problem on positions V
+    (a CUDA tensor n x 3; F the hierarchy's triangles)."""
+    return _eigenvalue_function().apply(V, ctx, hier, F, p, tol, options)
+
+
 # ---- step-level entry points -------------------------------------------------
 def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None):
     torch = _torch()

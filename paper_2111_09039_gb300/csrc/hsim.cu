@@ -902,6 +902,20 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *h, const double *S_val, const d
     });
 }
 
+hsim_status hsim_eig_grad(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F, int p,
+                          const double *evals, const double *evecs, const double *dloss, double *dV) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx, "NULL context");
+        HSIM_CHECK_ARG(n >= 0 && m >= 0 && p >= 0, "bad sizes");
+        if (n == 0) return;
+        HSIM_CHECK_ARG(V && dV && (m == 0 || F), "NULL argument");
+        HSIM_CHECK_ARG(p == 0 || (evals && evecs && dloss), "NULL argument");
+        DeviceGuard dg(ctx->device);
+        k::eig_grad(ctx->stream, n, p == 0 ? 0 : m, p, V, F, evals, evecs, n, dloss, dV);
+        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+    });
+}
+
 hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *ptr, const int32_t *col,
                       const double *val, int k, const double *X, int ldx, double *Y, int ldy) {
     return guard([&] {

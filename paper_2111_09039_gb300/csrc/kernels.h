@@ -20,6 +20,9 @@ void triangle_geometry(cudaStream_t s, int m, const int *F, const double *V, con
 void assemble_sm(cudaStream_t s, int n, const int *ptr, const int *col, const int *ecot,
                  const double *cot, const int *vt_ptr, const int *vt_idx, const double *area,
                  double *S_val, double *M_diag);
+// dV = sum_i dloss[i] d lambda_i / dV (k_grad.cu); dV is zeroed first
+void eig_grad(cudaStream_t s, int n, int m, int p, const double *V, const int *F, const double *evals,
+              const double *evecs, int ld, const double *dloss, double *dV);
 // Y[r, 0:k] = sum A[r,c] X[c, 0:k]
 void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *val, int k,
           const double *X, int ldx, double *Y, int ldy);
