@@ -58,17 +58,21 @@ typedef struct {
     int max_iters;       /* subspace iterations per level before HSIM_E_NO_CONVERGENCE */
     int inv_iters;       /* inverse iterations per Rayleigh-Ritz step (paper: 2) */
     double lock_factor;  /* lock a converged prefix below lock_factor * tol */
-    int precision;       /* HSIM_FP64: every step in FP64.  HSIM_MIXED: the Gram
-                            products and the basis update on BF16 tensor cores with
-                            FP64-accurate digit splitting (hsim_gram_tc); factor,
-                            solves, Ritz and residuals stay FP64 */
+    int precision;       /* HSIM_FP64: every step in FP64, the paper's shift.
+                            HSIM_MIXED: shift below the spectrum,
+                            mu = -max(lambda_ref, 0.01 Lambda_{q-1}) (K positive
+                            definite), FP32 factor and FP32 solves of inverse
+                            iterations in correction form against FP64 bases; Gram
+                            products and basis update on BF16 tensor cores with
+                            FP64-accurate digit splitting (hsim_gram_tc); Ritz and
+                            residuals FP64 */
     int start_vertex;    /* first vertex of farthest-point sampling (Alg. 2) */
     int leaf_size;       /* nested-dissection leaf size (tuning, default 32) */
     int q;               /* subspace size; <= 0 selects max(ceil(1.5p), p+8) */
-    int refine;          /* FP64 residual refinement of the last inverse iteration of
-                            each Rayleigh-Ritz step: 0 = automatic (switched on for a
-                            level once its residual stops decreasing), 1 = always,
-                            -1 = never */
+    int refine;          /* HSIM_FP64 only: FP64 residual refinement of the last
+                            inverse iteration of each Rayleigh-Ritz step: 0 =
+                            automatic (switched on for a level once its residual
+                            stops decreasing), 1 = always, -1 = never */
 } hsim_options;
 
 /* Per-solve report (host struct, optional). */

@@ -133,7 +133,8 @@ struct hsim_hier {
         Phi, Psi, SP, MP, coarseX, coarseLam, colw, tmpv, signs, tval_s, tval_m;
     std::vector<DevBuf<double>> Sv, Mv;  // level values (internal), index tau
     // mixed precision: FP32 factor and FP32 right-hand-side blocks
-    DevBuf<float> arena32, dpos32, X32, R32;
+    DevBuf<float> arena32, dpos32, X32;
+    DevBuf<double> rho;
     DevBuf<unsigned char> oz;  // digit slices of the tensor-core products
 };
 
@@ -424,9 +425,9 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         Timer tp(s);
         k::spmm(s, n, P.dU.ptr.p, P.dU.col.p, P.dUval.p, q, Xc, ldxc, H->Phi.p, q);
         inf.ms_prolong += tp.stop();
-        // shift (Alg. 3): Lambda_j of the coarser level, j = floor(alpha p)
-        // shift (Alg. 3); for j = 0 mirrored below zero to -lambda_ref so that
-        // S - mu M stays away from the constant null vector
+        // shift (Alg. 3): Lambda_j of the coarser level, j = floor(alpha p); for
+        // j = 0 mirrored below zero to -lambda_ref so that S - mu M stays away
+        // from the constant null vector
         int j = (int)std::floor(o.alpha * p);
         double mu = lam_h[j];
         if (j == 0) {
@@ -437,57 +438,49 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                     break;
                 }
         }
+        // Mixed precision factors K in FP32.  The pivot-free LDL^T of an
+        // indefinite K shows element growth near 5e4 (an FP32 factor is then
+        // only ~3e-3 accurate), so the mixed path shifts below the spectrum,
+        // mu = -max(lambda_ref, 0.01 Lambda_{q-1}): K is positive definite,
+        // the factorisation is stable, and the convergence ratio of the top
+        // pairs, (lambda_i - mu) / (lambda_q - mu), changes by about 1 %.
+        const bool mixed = o.precision == HSIM_MIXED;
+        if (mixed) {
+            double lam_ref = lam_h[q - 1];
+            for (int i = 0; i < q; ++i)
+                if (lam_h[i] > 1e-8 * lam_h[q - 1]) {
+                    lam_ref = lam_h[i];
+                    break;
+                }
+            mu = -std::max(lam_ref, 0.01 * lam_h[q - 1]);
+        }
         inf.shift[tau] = mu;
         const double *Sx = tau == 0 ? H->S0int.p : H->Sv[tau].p;
         const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
         const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
-        // Mixed precision: the dense products run on BF16 tensor cores with
-        // FP64 accuracy (digit splitting); the factor and the solves stay FP64.
-        // (An FP32 factor with FP64 residual refinement was tried: the
-        // pivot-free indefinite LDL^T shows element growth near 5e4, so FP32
-        // solves are only ~3e-3 accurate and the refinement stops contracting
-        // when the shift lies inside the spectrum.)
-        const bool mixed = o.precision == HSIM_MIXED;
-        const bool fp32_solves = false;
         Timer tf(s);
-        int negp = fp32_solves ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, 1e-7)
-                               : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
+        int negp = mixed ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, 1e-7)
+                         : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
         inf.ms_factor += tf.stop();
-        if (fp32_solves) {
+        if (mixed) {
+            if (negp != 0)
+                fail(HSIM_E_BREAKDOWN, "FP32 factor of the positive definite shifted matrix has " +
+                                           std::to_string(negp) + " negative pivot(s)");
             H->X32.reserve((size_t)n * q);
-            H->R32.reserve((size_t)n * q);
+            H->rho.reserve(2 * (size_t)q);
         }
-        // K^-1 B in the mixed path: B (FP64, n x a, ld q) rounded to FP32, solved
-        // with the FP32 factor, widened into X (FP64)
-        auto solve32 = [&](const double *B, double *X, int a) {
-            k::convert_matrix(s, n, a, B, q, H->X32.p, q);
+        // One inverse iteration in correction form (mixed path): for any
+        // scalar rho, K^-1 M psi = (psi - K^-1 (S psi - rho M psi)) / (rho - mu).
+        // With rho the Rayleigh quotient the right-hand side is the residual,
+        // small next to psi, so the FP32 solve's error is small next to the
+        // FP64 psi it corrects; the factor 1 / (rho - mu) > 0 is dropped (the
+        // columns are rescaled before the Gram).  X, SX, MX: FP64, columns
+        // [0, a) with leading dimension q; num / den give rho per column.
+        auto correction_step = [&](const double *X, const double *SX, const double *MX, const double *num,
+                                   const double *den, double *Y, int a) {
+            k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->X32.p, q);
             solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->X32.p, a, q);
-            k::convert_matrix(s, n, a, H->X32.p, q, X, q);
-        };
-        // FP64 iterative refinement of X = K^-1 B with the FP32 factor: R =
-        // B - K X in FP64, X += K^-1 R, until the largest relative column
-        // residual is below 1e-14 or stops decreasing (at most 6 steps)
-        std::vector<double> rw(q), bw(q);
-        auto refine32 = [&](const double *B, double *X, double *R, int a) {
-            k::col_dots(s, n, a, B, q, B, q, (const double *)nullptr, H->colw.p);
-            HSIM_CUDA(cudaMemcpyAsync(bw.data(), H->colw.p, a * sizeof(double), cudaMemcpyDeviceToHost, s));
-            HSIM_CUDA(cudaStreamSynchronize(s));
-            double prev = INFINITY;
-            int steps = 0;
-            for (; steps < 6; ++steps) {
-                k::shifted_residual(s, n, L.dpat.ptr.p, L.dpat.col.p, Sx, Mx, Mdx, mu, a, X, q, B, q, R, q);
-                k::col_dots(s, n, a, R, q, R, q, (const double *)nullptr, H->colw.p);
-                HSIM_CUDA(cudaMemcpyAsync(rw.data(), H->colw.p, a * sizeof(double), cudaMemcpyDeviceToHost, s));
-                HSIM_CUDA(cudaStreamSynchronize(s));
-                double worst = 0.0;
-                for (int j = 0; j < a; ++j) worst = std::max(worst, std::sqrt(rw[j] / std::max(bw[j], 1e-300)));
-                if (worst < 1e-14 || worst > 0.5 * prev) break;
-                prev = worst;
-                k::convert_matrix(s, n, a, R, q, H->R32.p, q);
-                solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->R32.p, a, q);
-                k::add_f2d(s, n, a, H->R32.p, q, X, q);
-            }
-            return steps;
+            k::sub_f2d(s, n, a, X, q, H->X32.p, q, Y, q);
         };
         if (trace_on())
             std::fprintf(stderr, "[hsim] level %d n=%d q=%d shift=%.10g negative_pivots=%d fronts=%d nnzL=%lld\n", tau,
@@ -515,19 +508,22 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             const int a = q - locked;
             Timer ts(s);
             // inverse iterations on the active columns (Alg. 1, solve step; twice)
-            int refine_steps = 0;
-            if (fp32_solves) {
-                // first: FP32 solve; its rounding noise in high frequencies is
-                // damped by the next inverse iteration.  Last: FP32 solve plus
-                // FP64 residual refinement
-                solve32(H->MP.p + locked, H->Psi.p + locked, a);
+            if (mixed) {
+                // first: the current Ritz pairs (S Phi, M Phi and Lambda from the
+                // last convergence test; at it = 1 Phi is the prolonged basis,
+                // whose Rayleigh quotients are the coarse Ritz values)
+                if (it == 1) apply_S(ctx, H, tau, a, H->Phi.p + locked, q, H->SP.p + locked, q);
+                const double *lam_d = (it == 1 && tau == T - 2) ? H->coarseLam.p : H->lam.p;
+                correction_step(H->Phi.p + locked, H->SP.p + locked, H->MP.p + locked, lam_d + locked, nullptr,
+                                H->Psi.p + locked, a);
                 for (int extra = 1; extra < o.inv_iters; ++extra) {
-                    apply_M(ctx, H, tau, a, H->Psi.p + locked, q, H->SP.p + locked, q);
-                    solve32(H->SP.p + locked, H->Psi.p + locked, a);
+                    double *Pa = H->Psi.p + locked;
+                    apply_S(ctx, H, tau, a, Pa, q, H->SP.p + locked, q);
+                    apply_M(ctx, H, tau, a, Pa, q, H->MP.p + locked, q);
+                    k::col_dots(s, n, a, Pa, q, H->SP.p + locked, q, nullptr, H->rho.p);
+                    k::col_dots(s, n, a, Pa, q, H->MP.p + locked, q, nullptr, H->rho.p + q);
+                    correction_step(Pa, H->SP.p + locked, H->MP.p + locked, H->rho.p, H->rho.p + q, Pa, a);
                 }
-                double *rhs = o.inv_iters >= 2 ? H->SP.p : H->MP.p;
-                double *res_buf = o.inv_iters >= 2 ? H->MP.p : H->SP.p;
-                if (o.refine >= 0) refine_steps = refine32(rhs + locked, H->Psi.p + locked, res_buf + locked, a);
             } else {
                 k::copy_matrix(s, n, a, H->MP.p + locked, q, H->Psi.p + locked, q);
                 solve_level(ctx, H, L, H->Psi.p + locked, a, q);
@@ -537,7 +533,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                     solve_level(ctx, H, L, H->Psi.p + locked, a, q);
                 }
             }
-            if (refine && !fp32_solves) {
+            if (refine && !mixed) {
                 // right-hand side of the last solve: SP (two or more inverse
                 // iterations) or MP (one); the residual goes to the other buffer
                 double *rhs = o.inv_iters >= 2 ? H->SP.p : H->MP.p;
@@ -607,7 +603,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             if (trace_on())
                 std::fprintf(stderr,
                              "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g\n",
-                             tau, it, locked, maxres, sweeps, fp32_solves ? refine_steps : (int)refine, lam_h[0],
+                             tau, it, locked, maxres, sweeps, (int)refine, lam_h[0],
                              lam_h[p - 1]);
             if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
             if (maxres < tol) break;

@@ -332,6 +332,26 @@ __global__ void k_add_f2d(int rows, int cols, const float *__restrict__ X, int l
     Y[(size_t)i * ldy + j] += (double)X[(size_t)i * ldx + j];
 }
 
+// R (FP32) = SP - rho_j MP, rho_j = num[j] / den[j] (den NULL: rho_j = num[j])
+__global__ void k_residual_f32(int rows, int cols, const double *__restrict__ SP, int lds,
+                               const double *__restrict__ MP, int ldm, const double *__restrict__ num,
+                               const double *__restrict__ den, float *__restrict__ R, int ldr) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    double rho = den ? num[j] / den[j] : num[j];
+    R[(size_t)i * ldr + j] = (float)(SP[(size_t)i * lds + j] - rho * MP[(size_t)i * ldm + j]);
+}
+
+// Y (FP64) = X - Z (FP32)
+__global__ void k_sub_f2d(int rows, int cols, const double *__restrict__ X, int ldx, const float *__restrict__ Z,
+                          int ldz, double *__restrict__ Y, int ldy) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j] - (double)Z[(size_t)i * ldz + j];
+}
+
 template <typename T>
 __global__ void k_copy_matrix_t(int rows, int cols, const T *__restrict__ X, int ldx, T *__restrict__ Y, int ldy) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -492,6 +512,18 @@ void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx,
 void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy) {
     if (rows <= 0 || cols <= 0) return;
     k_add_f2d<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *MP, int ldm,
+                  const double *num, const double *den, float *R, int ldr) {
+    if (rows <= 0 || cols <= 0) return;
+    k_residual_f32<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, SP, lds, MP, ldm, num, den, R, ldr);
+    HSIM_LAUNCHED();
+}
+void sub_f2d(cudaStream_t s, int rows, int cols, const double *X, int ldx, const float *Z, int ldz, double *Y,
+             int ldy) {
+    if (rows <= 0 || cols <= 0) return;
+    k_sub_f2d<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Z, ldz, Y, ldy);
     HSIM_LAUNCHED();
 }
 void copy_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, float *Y, int ldy) {

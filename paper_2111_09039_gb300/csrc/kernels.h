@@ -64,6 +64,12 @@ void convert_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx
 void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
 // Y (FP64) += X (FP32)
 void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
+// R (FP32) = SP - rho MP column-wise, rho_j = num[j] / den[j] (den NULL: num[j])
+void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *MP, int ldm,
+                  const double *num, const double *den, float *R, int ldr);
+// Y (FP64) = X - Z (FP32)
+void sub_f2d(cudaStream_t s, int rows, int cols, const double *X, int ldx, const float *Z, int ldz, double *Y,
+             int ldy);
 void copy_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, float *Y, int ldy);
 void diag_scale(cudaStream_t s, int n, int k, const float *d, const float *X, int ldx, float *Y, int ldy);
 // y = 1 / x

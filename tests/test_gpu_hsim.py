@@ -170,7 +170,7 @@ def test_no_convergence_is_reported(hs, ctx):
     assert e.value.name == "HSIM_E_NO_CONVERGENCE"
 
 
-# ---- mixed precision: FP32 factor/solves with FP64 refinement, FP64-accurate
+# ---- mixed precision: SPD shift, FP32 factor and correction-form solves, FP64-accurate
 # tensor-core Gram/update, FP64 Ritz ------------------------------------------
 def mixed_solve(hs, ctx, mesh, p, levels, tol, start):
     hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=p, levels=levels, start_vertex=start,
