@@ -144,7 +144,7 @@ def main():
     ap.add_argument("--sample-cols", type=int, default=8)
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm"],
+    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz"],
                     help="time one step-level kernel on random data instead of the solve (profiling)")
     ap.add_argument("--rows", type=int, default=200000)
     ap.add_argument("--cols", type=int, default=750)
@@ -311,6 +311,13 @@ def run_kernel(args):
         f = hs.gram if args.kernel == "gram" else hs.gram_tc
         fn = lambda: f(ctx, A, B)
         flops, nbytes = 2.0 * n * q * q, 16.0 * n * q
+    elif args.kernel == "ritz":
+        # q x q symmetric S_bar and SPD M_bar with random eigenvectors
+        Sb = P + P.t()
+        C = torch.randn((q, q), dtype=torch.float64, device="cuda:0", generator=g)
+        Mb = torch.eye(q, dtype=torch.float64, device="cuda:0") + (C @ C.t()) / (10.0 * q)
+        fn = lambda: hs.ritz(ctx, Sb, Mb)
+        flops, nbytes = 0.0, 16.0 * q * q
     else:
         f = hs.gemm_update if args.kernel == "update" else hs.gemm_update_tc
         fn = lambda: f(ctx, A, P)
@@ -325,7 +332,10 @@ def run_kernel(args):
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
-    print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms,
+    extra = {}
+    if args.kernel == "ritz":
+        extra["sweeps"] = fn()[2]
+    print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms, **extra,
                       "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12,
                       "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}), flush=True)
 
