@@ -559,8 +559,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 k::OzakiOperand X = k::ozaki_split_cols(s, n, q, H->Psi.p, q, H->oz.p);
                 k::OzakiOperand YS = k::ozaki_split_cols(s, n, q, H->SP.p, q, H->oz.p + part);
                 k::OzakiOperand YM = k::ozaki_split_cols(s, n, q, H->MP.p, q, H->oz.p + 2 * part);
-                k::ozaki_product(s, X, YS, X.ld, H->Sbar.p, q, 0);
-                k::ozaki_product(s, X, YM, X.ld, H->Mbar.p, q, 0);
+                k::ozaki_product(s, X, YS, X.ld, H->Sbar.p, q, 0, true);
+                k::ozaki_product(s, X, YM, X.ld, H->Mbar.p, q, 0, true);
             } else {
                 k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
                 k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);

@@ -164,10 +164,13 @@ constexpr int kStageElems = kSlices * (TM + TN) * kRow;  // bf16 per pipeline st
 __global__ void __launch_bounds__(256, 1)
     k_ozaki_nt(int M, int N, const __nv_bfloat16 *__restrict__ Xs, int ldx, size_t xstride,
                const __nv_bfloat16 *__restrict__ Ys, int ldy, size_t ystride, const int *__restrict__ ex,
-               const int *__restrict__ ey, double *__restrict__ C, int ldc, int k_len, int k_split, int atomic) {
+               const int *__restrict__ ey, double *__restrict__ C, int ldc, int k_len, int k_split, int atomic,
+               int lower) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16 *stage0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
     const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+    // lower: only tiles that meet the lower triangle j <= i (square tiles)
+    if (lower && j0 > i0 + TM - 1) return;
     const int k_beg = blockIdx.z * k_split;
     const int k_end = min(k_len, k_beg + k_split);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -271,10 +274,14 @@ __global__ void __launch_bounds__(256, 1)
         for (int e = 0; e < 4; ++e) {
             const int i = i0 + wm * 16 + g + (e >= 2 ? 8 : 0);
             const int j = j0 + wn * 32 + nt * 8 + tig * 2 + (e & 1);
-            if (i < M && j < N) {
+            if (i < M && j < N && (!lower || j <= i)) {
                 const double v = ldexp((double)hi[nt][e] + (double)lo[nt][e], ex[i] + ey[j] - 14);
                 if (atomic) atomicAdd(&C[(size_t)i * ldc + j], v);
                 else C[(size_t)i * ldc + j] = v;
+                if (lower && j < i) {
+                    if (atomic) atomicAdd(&C[(size_t)j * ldc + i], v);
+                    else C[(size_t)j * ldc + i] = v;
+                }
             }
         }
 }
@@ -294,13 +301,14 @@ int sm_count_oz() {
 
 void launch_nt(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int ldx, size_t xstride,
                const __nv_bfloat16 *Ys, int ldy, size_t ystride, const int *ex, const int *ey, double *C, int ldc,
-               int k_len, int splits) {
+               int k_len, int splits, int lower) {
     // the kernel reads the digit slices as 16-byte vectors: every slice base
     // and every row start must be 16-byte aligned
     auto aligned16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     HSIM_CHECK_ARG(aligned16(Xs) && aligned16(Ys) && ldx % 8 == 0 && ldy % 8 == 0 && xstride % 8 == 0 &&
                        ystride % 8 == 0 && k_len % TKs == 0,
                    "ozaki product: operand not 16-byte aligned");
+    HSIM_CHECK_ARG(!lower || (M == N && TM == TN), "ozaki product: lower triangle needs a square result");
     const size_t sm = smem_bytes();
     HSIM_CUDA(cudaFuncSetAttribute(k_ozaki_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int k_split = (int)((k_len + splits - 1) / splits);
@@ -308,7 +316,7 @@ void launch_nt(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int ldx, s
     splits = (int)cdiv(k_len, k_split);
     dim3 g(cdiv(N, TN), cdiv(M, TM), (unsigned)splits);
     k_ozaki_nt<<<g, 256, sm, s>>>(M, N, Xs, ldx, xstride, Ys, ldy, ystride, ex, ey, C, ldc, k_len, k_split,
-                                  splits > 1 ? 1 : 0);
+                                  splits > 1 ? 1 : 0, lower);
     HSIM_LAUNCHED();
 }
 
@@ -365,11 +373,12 @@ OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, 
 }
 
 void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y, int k_len, double *C, int ldc,
-                   int splits) {
+                   int splits, bool lower) {
     if (X.rows <= 0 || Y.rows <= 0) return;
     HSIM_CHECK_ARG(X.ld == Y.ld, "ozaki_product: operands split over different K");
     if (splits <= 0) {
-        const int64_t tiles = (int64_t)cdiv(X.rows, TM) * cdiv(Y.rows, TN);
+        const int64_t tx = cdiv(X.rows, TM), ty = cdiv(Y.rows, TN);
+        const int64_t tiles = lower ? tx * (tx + 1) / 2 : tx * ty;
         splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sm_count_oz() + tiles - 1) / tiles,
                                                               (int64_t)cdiv(k_len, 1024)));
     }
@@ -378,7 +387,7 @@ void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y,
         else HSIM_CUDA(cudaMemset2DAsync(C, (size_t)ldc * sizeof(double), 0, (size_t)Y.rows * sizeof(double), X.rows, s));
     }
     launch_nt(s, X.rows, Y.rows, X.slices, X.ld, X.stride, Y.slices, Y.ld, Y.stride, X.exps, Y.exps, C, ldc, X.ld,
-              splits);
+              splits, lower ? 1 : 0);
 }
 
 }  // namespace k

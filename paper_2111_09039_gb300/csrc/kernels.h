@@ -166,9 +166,11 @@ OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, 
 // split X (row-major rows x k, K = k) per row
 OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch);
 // C (X.rows x Y.rows, FP64) = X Y^T over K = k_len; splits <= 0 chooses a
-// split-K count (C accumulated with atomics), 1 stores directly
+// split-K count (C accumulated with atomics), 1 stores directly; lower: C is
+// symmetric, only tiles meeting the lower triangle run and the epilogue
+// writes each value and its mirror image (X.rows == Y.rows)
 void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y, int k_len, double *C, int ldc,
-                   int splits);
+                   int splits, bool lower = false);
 
 }  // namespace k
 }  // namespace hsim
