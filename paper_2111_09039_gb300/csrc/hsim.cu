@@ -587,6 +587,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             HSIM_CUDA(cudaMemcpyAsync(rs.data(), H->res_sums.p, 3 * q * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->lam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaStreamSynchronize(s));
+            if (mixed) k::ozaki_check(s);
             inf.ms_residual += ts.stop();
             double lam_ref = lam_h[q - 1];
             for (int i = 0; i < q; ++i)
@@ -957,7 +958,7 @@ hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int ka, int kb, const double *A, 
         k::OzakiOperand X = k::ozaki_split_cols(ctx->stream, n, ka, A, lda, scratch.p);
         k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, n, kb, B, ldb, scratch.p + k::ozaki_cols_scratch(n, ka));
         k::ozaki_product(ctx->stream, X, Y, X.ld, G, kb, 0);
-        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+        k::ozaki_check(ctx->stream);
     });
 }
 
@@ -971,7 +972,7 @@ hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int kk, int m, const doubl
         k::OzakiOperand X = k::ozaki_split_rows(ctx->stream, n, kk, A, lda, scratch.p);
         k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, kk, m, B, ldb, scratch.p + k::ozaki_rows_scratch(n, kk));
         k::ozaki_product(ctx->stream, X, Y, X.ld, C, ldc, 1);
-        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
+        k::ozaki_check(ctx->stream);
     });
 }
 

@@ -10,13 +10,14 @@
 // 2^14, so up to 1024 of them sum exactly in an FP32 accumulator: the tensor
 // cores compute sum_r d_s(x_ir) d_t(y_jr) with no rounding, grouped by
 // D = s + t (pairs with D >= kSlices are dropped), over K-chunks of 128, and
-// every chunk is flushed into FP64 registers.  The result equals the FP64
+// every chunk is flushed into FP32 TwoSum pairs.  The result equals the FP64
 // product up to the dropped tail, about 2^-47 of max|x_i.| max|y_j.| per
 // term.
 //
 // Kernel shape: C (FP64, M x N) (+)= X Y^T with X (M x K) and Y (N x K) both
-// K-contiguous digit slices; CTA tile 64 x 64, eight warps of 16 x 32,
-// mma.sync m16n8k16 BF16 with FP32 accumulation.
+// K-contiguous digit slices, on the tcgen05 tensor cores (TMA-fed shared
+// memory, TMEM accumulators; k_ozaki_tc below).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,19 +33,20 @@ namespace k {
 namespace {
 
 constexpr int kSlices = kOzakiSlices;
-constexpr int TM = 64, TN = 64, TKs = 32;   // CTA tile and K step
-constexpr int kPad = 8;                      // smem row padding (bf16)
-constexpr int kRow = TKs + kPad;             // 40 bf16 = 80 bytes per smem row
-constexpr int kFlush = 128;                  // K rows between FP32 -> FP64 flushes
+constexpr int TKs = 32;      // K padding of the digit slices (one pipeline stage)
+constexpr int kFlush = 128;  // K rows per exact FP32 chunk
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-// exponent e with max|x| < 2^e (frexp convention); -1074 for all-zero groups
-__device__ __forceinline__ int exp_of(double a) {
-    if (a == 0.0) return -1074;
-    int e;
-    frexp(a, &e);
-    return e;
+// Exponents and digits are taken from the bits of the FP64 values with integer
+// arithmetic only (the FP64 pipe of this part is ~1/60 of the FP32 pipe).
+//
+// exponent e with |x| < 2^e for a nonzero x: biased exponent - 1022 (exact
+// for normal numbers, an upper bound for subnormals); -1074 marks zero
+__device__ __forceinline__ int exp_bits(double a) {
+    const long long b = __double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFLL;
+    if (b == 0) return -1074;
+    return (int)(b >> 52) - 1022;
 }
 
 // per-row exponents of a row-major R x C FP64 block: one warp per row
@@ -52,10 +54,10 @@ __global__ void k_row_exps(int R, int C, const double *__restrict__ X, int ldx, 
     int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (row >= R) return;
-    double m = 0.0;
-    for (int j = lane; j < C; j += 32) m = fmax(m, fabs(X[(size_t)row * ldx + j]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) ex[row] = exp_of(m);
+    int m = -1074;
+    for (int j = lane; j < C; j += 32) m = max(m, exp_bits(X[(size_t)row * ldx + j]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) ex[row] = m;
 }
 
 // per-column exponents of a row-major R x C FP64 block (ex pre-set to -1074)
@@ -63,25 +65,44 @@ __global__ void k_col_exps(int R, int C, const double *__restrict__ X, int ldx, 
     const int r0 = blockIdx.x * 256;
     const int r1 = min(R, r0 + 256);
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < C; j += gridDim.y * blockDim.x) {
-        double m = 0.0;
-        for (int r = r0; r < r1; ++r) m = fmax(m, fabs(X[(size_t)r * ldx + j]));
-        if (m != 0.0) atomicMax(&ex[j], exp_of(m));
+        int m = -1074;
+        for (int r = r0; r < r1; ++r) m = max(m, exp_bits(X[(size_t)r * ldx + j]));
+        if (m != -1074) atomicMax(&ex[j], m);
     }
 }
 
+// Digits of x against the group exponent e (|x| < 2^e): T = round(x 2^(47-e))
+// as an integer (|T| <= 2^47, ties to even), written in balanced base 256,
+//     T = sum_s d_s 2^(8 (5 - s)),  d_1..d_5 in [-128, 127],  |d_0| <= 128,
+// so x = 2^(e-7) sum_s d_s 2^(-8 s) up to 2^(e-48).
 __device__ __forceinline__ void split_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
-    // y = x 2^-e in (-1, 1); digits d_0 = rint(128 y), then 256 * remainder
-    double y = ldexp(x, 7 - e);
-    double d = rint(y);
-    out[0] = __double2bfloat16(d);
-    double r = y - d;
-#pragma unroll
-    for (int s = 1; s < kSlices; ++s) {
-        r *= 256.0;
-        d = rint(r);
-        out[(size_t)s * stride] = __double2bfloat16(d);
-        r -= d;
+    const long long bits = __double_as_longlong(x);
+    int E = (int)((bits >> 52) & 0x7FF);
+    long long M = bits & 0xFFFFFFFFFFFFFLL;
+    if (E == 0) E = 1;
+    else M |= 1LL << 52;
+    const int sh = E - 1075 + 47 - e;  // x 2^(47-e) = +-M 2^sh, sh <= -6 when |x| < 2^e
+    long long T = 0;
+    if (M != 0 && sh > -54) {
+        if (sh >= 0) {
+            T = M << min(sh, 10);
+        } else {
+            const int k = -sh;
+            long long q = M >> k;
+            const long long rem = M & ((1LL << k) - 1), half = 1LL << (k - 1);
+            if (rem > half || (rem == half && (q & 1))) ++q;
+            T = q;
+        }
     }
+    if (bits < 0) T = -T;
+#pragma unroll
+    for (int s = kSlices - 1; s >= 1; --s) {
+        int d = (int)(T & 255);
+        if (d >= 128) d -= 256;
+        out[(size_t)s * stride] = __int2bfloat16_rn(d);
+        T = (T - d) >> 8;
+    }
+    out[0] = __int2bfloat16_rn((int)T);
 }
 
 // slices of a row-major R x C block split per row: out[s] is R x ldo (K = C
@@ -121,28 +142,6 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, unsigned addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem),
-                 "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
 // Error-free accumulation of x into (hi, lo): hi + lo gains x exactly up to
 // the rounding of lo (Knuth's TwoSum in FP32; the FP32 pipe is ~60x the FP64
 // pipe on this part).
@@ -153,140 +152,6 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
     hi = s;
     lo = __fadd_rn(lo, err);
 }
-
-constexpr int kStageElems = kSlices * (TM + TN) * kRow;  // bf16 per pipeline stage
-
-// C[i0.., j0..] (+)= 2^(ex_i + ey_j - 14) sum_D 2^(-8 D) sum_{s+t=D} X_s Y_t^T over
-// rows k in [k_beg, k_end).  X slices: M x ldx, Y slices: N x ldy (K contiguous,
-// ld multiples of 8, zero padded to a multiple of TKs).  Two pipeline stages
-// filled with cp.async; each 128-row chunk of exact FP32 digit sums is added
-// into an FP32 (hi, lo) pair per output with TwoSum.
-__global__ void __launch_bounds__(256, 1)
-    k_ozaki_nt(int M, int N, const __nv_bfloat16 *__restrict__ Xs, int ldx, size_t xstride,
-               const __nv_bfloat16 *__restrict__ Ys, int ldy, size_t ystride, const int *__restrict__ ex,
-               const int *__restrict__ ey, double *__restrict__ C, int ldc, int k_len, int k_split, int atomic,
-               int lower) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16 *stage0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
-    // lower: only tiles that meet the lower triangle j <= i (square tiles)
-    if (lower && j0 > i0 + TM - 1) return;
-    const int k_beg = blockIdx.z * k_split;
-    const int k_end = min(k_len, k_beg + k_split);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp & 3, wn = warp >> 2;  // warp tile rows wm*16, cols wn*32
-    float acc[kSlices][4][4];
-    float hi[4][4], lo[4][4];
-#pragma unroll
-    for (int d = 0; d < kSlices; ++d)
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[d][t][e] = 0.f;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) hi[t][e] = lo[t][e] = 0.f;
-
-    // stage the K step starting at kk into buffer `buf`: every slice of the
-    // 64 x 32 X and Y blocks, 16-byte chunks, zero-filled outside the operands
-    auto load_stage = [&](int buf, int kk) {
-        __nv_bfloat16 *As = stage0 + (size_t)buf * kStageElems;
-        __nv_bfloat16 *Bs = As + (size_t)kSlices * TM * kRow;
-        constexpr int chunks = kSlices * TM * (TKs / 8);  // per operand
-        for (int c = threadIdx.x; c < 2 * chunks; c += blockDim.x) {
-            const bool isB = c >= chunks;
-            const int cc = isB ? c - chunks : c;
-            const int s = cc / (TM * (TKs / 8));
-            const int rem = cc % (TM * (TKs / 8));
-            const int row = rem / (TKs / 8), part = rem % (TKs / 8);
-            const int grow = (isB ? j0 : i0) + row;
-            const int lim = isB ? N : M;
-            const bool ok = grow < lim && kk + part * 8 < k_end;
-            const __nv_bfloat16 *src = isB ? Ys + (size_t)s * ystride + (size_t)(ok ? grow : 0) * ldy + (ok ? kk + part * 8 : 0)
-                                           : Xs + (size_t)s * xstride + (size_t)(ok ? grow : 0) * ldx + (ok ? kk + part * 8 : 0);
-            __nv_bfloat16 *dst = (isB ? Bs : As) + ((size_t)s * TM + row) * kRow + part * 8;
-            cp_async16(dst, src, ok ? 16 : 0);
-        }
-    };
-
-    int buf = 0;
-    if (k_beg < k_end) load_stage(0, k_beg);
-    cp_async_commit();
-    int since_flush = 0;
-    for (int kk = k_beg; kk < k_end; kk += TKs) {
-        if (kk + TKs < k_end) load_stage(buf ^ 1, kk + TKs);
-        cp_async_commit();
-        cp_async_wait_1();
-        __syncthreads();
-        const __nv_bfloat16 *As = stage0 + (size_t)buf * kStageElems;
-        const __nv_bfloat16 *Bs = As + (size_t)kSlices * TM * kRow;
-#pragma unroll
-        for (int k16 = 0; k16 < TKs; k16 += 16) {
-            unsigned a[kSlices][4];
-#pragma unroll
-            for (int s = 0; s < kSlices; ++s) {
-                const int r = wm * 16 + (lane & 15);
-                const int c = k16 + (lane >> 4) * 8;
-                ldsm_x4(a[s][0], a[s][1], a[s][2], a[s][3], smem_addr(As + ((size_t)s * TM + r) * kRow + c));
-            }
-#pragma unroll
-            for (int t = 0; t < kSlices; ++t) {
-                unsigned b[4][2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    // n rows wn*32 + h*16 + (0..15), k halves by lane groups
-                    const int nrow = wn * 32 + h * 16 + ((lane >> 4) << 3) + (lane & 7);
-                    const int c = k16 + ((lane >> 3) & 1) * 8;
-                    ldsm_x4(b[2 * h][0], b[2 * h][1], b[2 * h + 1][0], b[2 * h + 1][1],
-                            smem_addr(Bs + ((size_t)t * TN + nrow) * kRow + c));
-                }
-#pragma unroll
-                for (int s = 0; s + t < kSlices; ++s)
-#pragma unroll
-                    for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[s + t][nt], a[s], b[nt][0], b[nt][1]);
-            }
-        }
-        __syncthreads();
-        buf ^= 1;
-        since_flush += TKs;
-        if (since_flush >= kFlush || kk + TKs >= k_end) {
-            since_flush = 0;
-#pragma unroll
-            for (int d = 0; d < kSlices; ++d) {
-                const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8 d), exact
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        two_sum_acc(hi[t][e], lo[t][e], __fmul_rn(acc[d][t][e], w));
-                        acc[d][t][e] = 0.f;
-                    }
-            }
-        }
-    }
-    cp_async_wait_0();
-    // epilogue: C fragment (row g / g+8, cols 2*tig + {0,1}) per n-tile
-    const int g = lane >> 2, tig = lane & 3;
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = i0 + wm * 16 + g + (e >= 2 ? 8 : 0);
-            const int j = j0 + wn * 32 + nt * 8 + tig * 2 + (e & 1);
-            if (i < M && j < N && (!lower || j <= i)) {
-                const double v = ldexp((double)hi[nt][e] + (double)lo[nt][e], ex[i] + ey[j] - 14);
-                if (atomic) atomicAdd(&C[(size_t)i * ldc + j], v);
-                else C[(size_t)i * ldc + j] = v;
-                if (lower && j < i) {
-                    if (atomic) atomicAdd(&C[(size_t)j * ldc + i], v);
-                    else C[(size_t)j * ldc + i] = v;
-                }
-            }
-        }
-}
-
-size_t smem_bytes() { return 2 * (size_t)kStageElems * sizeof(__nv_bfloat16); }
 
 int sm_count_oz() {
     static int n = 0;
@@ -299,24 +164,310 @@ int sm_count_oz() {
     return n;
 }
 
-void launch_nt(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int ldx, size_t xstride,
+// tcgen05 form of the same product (5th-generation tensor cores, TMEM).
+//
+// CTA tile: 128 rows of X by 64 rows of Y, K staged 32 at a time by TMA into
+// three shared-memory stages.  A 4-D tensor map [8 elements, rows, slice,
+// K/8] puts every stage in core-matrix order (8 rows x 16 bytes contiguous):
+// byte offset ((kg * 6 + s) * R + r) * 16 for digit slice s, row r, K-group
+// kg, i.e. an MMA operand descriptor with SBO = 128 bytes between 8-row
+// groups and LBO = 6 R * 16 bytes between K-groups.  Because the Y slices of
+// one stage follow each other at the row-group stride, Y_0 .. Y_5 form one
+// N = 384 operand: one MMA multiplies X_s by [Y_0 .. Y_{5-s}] (N = 64 (6 - s),
+// split at 256) and its 64-column blocks land exactly on the accumulators
+// acc_{s} .. acc_{5} of the digit sums D = s + t, which sit side by side in
+// TMEM (columns 64 D .. 64 D + 63, 384 of the 512 allocated).  Per 16-deep
+// K step that is 8 MMAs instead of 21.
+//
+// Warp roles (320 threads): warp 0 issues the TMA loads, warp 1 owns the
+// TMEM allocation and issues the MMAs (one thread), warps 2..9 drain TMEM:
+// after every 128 K-rows (the exact-FP32 chunk) they read acc_0..acc_5 and
+// add 2^-8D acc_D into FP32 (hi, lo) TwoSum pairs held in registers, one
+// TMEM lane (output row) and 32 of the 64 columns per thread.  Every wait on an mbarrier gives up
+// after a bounded number of polls, records an error flag the host checks,
+// and the CTA still drains its own copies and MMAs and frees its TMEM.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_STAGES = 3;
+constexpr int TC_THREADS = 320, TC_DRAIN = 256;  // 10 warps, 8 of them drain TMEM
+constexpr int TC_KG = TC_K / 8;
+constexpr uint32_t TC_A_BYTES = 16u * TC_M * kSlices * TC_KG;  // 49,152
+constexpr uint32_t TC_B_BYTES = 16u * TC_N * kSlices * TC_KG;  // 24,576
+constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s per barrier wait
+
+__device__ int g_oz_error;
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    // shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29),
+    // SBO >> 4 (32-45), descriptor version 1 (bits 46-47), no swizzle (61-63 = 0)
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of the given parity; gives up after TC_WAIT_NS of wall time
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 0) {
+            const uint64_t t = global_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > TC_WAIT_NS) break;
+        }
+    }
+    atomicExch(&g_oz_error, 1);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c1, int c3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%"
+        "19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_ozaki_tc(int M, int N, const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+               const int *__restrict__ ex, const int *__restrict__ ey, double *__restrict__ C, int ldc, int k_len,
+               int k_split, int atomic, int lower) {
+    extern __shared__ unsigned char smem_dyn[];
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], accf_bar, acce_bar, drain_bar;
+    __shared__ uint32_t tmem_slot;
+    const int i0 = blockIdx.y * TC_M, j0 = blockIdx.x * TC_N;
+    if (lower && j0 > i0 + TC_M - 1) return;
+    const int k_beg = blockIdx.z * k_split;
+    const int k_end = min(k_len, k_beg + k_split);
+    const int nk = k_end > k_beg ? (k_end - k_beg) / TC_K : 0;
+    const int nchunks = (nk + (kFlush / TC_K) - 1) / (kFlush / TC_K);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // stages on a 1024-byte boundary
+    const uint32_t smem0 = (smem_addr(smem_dyn) + 1023u) & ~1023u;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < TC_STAGES; ++st) {
+            mbar_init(smem_addr(&full_bar[st]), 1);
+            mbar_init(smem_addr(&empty_bar[st]), 1);
+        }
+        mbar_init(smem_addr(&accf_bar), 1);
+        mbar_init(smem_addr(&acce_bar), TC_DRAIN);
+        mbar_init(smem_addr(&drain_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0 && nk > 0) {
+            // producer: stage kt % 3 is refilled once the MMAs of kt - 3 completed
+            bool ok = true;
+            int issued = 0;
+            for (int kt = 0; kt < nk && ok; ++kt) {
+                const int st = kt % TC_STAGES;
+                if (kt >= TC_STAGES) ok = mbar_wait(smem_addr(&empty_bar[st]), ((kt / TC_STAGES) & 1) ^ 1);
+                if (!ok) break;
+                const uint32_t fb = smem_addr(&full_bar[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(TC_STAGE_BYTES)
+                             : "memory");
+                const uint32_t a_dst = smem0 + st * TC_STAGE_BYTES;
+                const int kg = (k_beg + kt * TC_K) / 8;
+                tma_load_4d(a_dst, &mapX, i0, kg, fb);
+                tma_load_4d(a_dst + TC_A_BYTES, &mapY, j0, kg, fb);
+                issued = kt + 1;
+            }
+            // drain: the last loads of every stage have landed before the CTA exits
+            for (int kt = max(0, issued - TC_STAGES); kt < issued; ++kt)
+                mbar_wait(smem_addr(&full_bar[kt % TC_STAGES]), (kt / TC_STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && nk > 0) {
+            bool ok = true;
+            const uint32_t lbo_a = 16u * TC_M * kSlices, lbo_b = 16u * TC_N * kSlices;
+            for (int kt = 0; kt < nk && ok; ++kt) {
+                const int st = kt % TC_STAGES;
+                const int chunk = kt / (kFlush / TC_K);
+                const bool chunk_first = kt % (kFlush / TC_K) == 0;
+                ok = mbar_wait(smem_addr(&full_bar[st]), (kt / TC_STAGES) & 1);
+                if (ok && chunk_first && chunk > 0) ok = mbar_wait(smem_addr(&acce_bar), (chunk - 1) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a_base = smem0 + st * TC_STAGE_BYTES, b_base = a_base + TC_A_BYTES;
+#pragma unroll
+                for (int k16 = 0; k16 < TC_K / 16; ++k16) {
+                    const uint32_t a_k = a_base + 2 * k16 * lbo_a, b_k = b_base + 2 * k16 * lbo_b;
+#pragma unroll
+                    for (int sl = 0; sl < kSlices; ++sl) {
+                        const uint64_t ad = umma_desc(a_k + sl * 16u * TC_M, lbo_a, 128);
+                        const int acc = (chunk_first && k16 == 0 && sl == 0) ? 0 : 1;
+                        const int ncols = TC_N * (kSlices - sl);  // Y_0 .. Y_{5-s}
+                        const int n1 = ncols > 256 ? 256 : ncols;
+                        umma_f16(tmem + TC_N * sl, ad, umma_desc(b_k, lbo_b, 128), umma_idesc(TC_M, n1), acc);
+                        if (ncols > 256)
+                            umma_f16(tmem + TC_N * sl + 256, ad, umma_desc(b_k + 256u * 16u, lbo_b, 128),
+                                     umma_idesc(TC_M, ncols - 256), acc);
+                    }
+                }
+                umma_commit(smem_addr(&empty_bar[st]));
+                if (kt % (kFlush / TC_K) == (kFlush / TC_K) - 1 || kt == nk - 1) umma_commit(smem_addr(&accf_bar));
+            }
+            // every MMA issued by this thread has completed before teardown
+            umma_commit(smem_addr(&drain_bar));
+            mbar_wait(smem_addr(&drain_bar), 0);
+        }
+    } else {
+        // drain warps: TMEM lane quadrant = warp % 4, one output row and one
+        // 32-column half per thread
+        const int quad = warp & 3, c0 = 32 * ((warp - 2) >> 2);
+        const int row = 32 * quad + lane;
+        float hi[32], lo[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.f;
+        bool ok = true;
+        for (int ch = 0; ch < nchunks && ok; ++ch) {
+            ok = mbar_wait(smem_addr(&accf_bar), ch & 1);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int d = 0; d < kSlices; ++d) {
+                const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8 d), exact
+                uint32_t r[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + TC_N * d + c0, r);
+#pragma unroll
+                for (int c = 0; c < 32; ++c) two_sum_acc(hi[c], lo[c], __fmul_rn(__uint_as_float(r[c]), w));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(smem_addr(&acce_bar));
+        }
+        const int i = i0 + row;
+        if (ok && i < M) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int j = j0 + c0 + c;
+                if (j < N && (!lower || j <= i)) {
+                    const double v = ldexp((double)hi[c] + (double)lo[c], ex[i] + ey[j] - 14);
+                    if (atomic) atomicAdd(&C[(size_t)i * ldc + j], v);
+                    else C[(size_t)i * ldc + j] = v;
+                    if (lower && j < i) {
+                        if (atomic) atomicAdd(&C[(size_t)j * ldc + i], v);
+                        else C[(size_t)j * ldc + i] = v;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        HSIM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        if (!p || q != cudaDriverEntryPointSuccess) fail(HSIM_E_CUDA, "cuTensorMapEncodeTiled not available");
+        fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 4-D map [8 elements, rows, slice, K/8] over kSlices digit slices of rows x ld
+// BF16 (K contiguous), box [8, box_rows, kSlices, TC_KG]
+CUtensorMap slice_map(const __nv_bfloat16 *base, int rows, int ld, size_t stride, int box_rows) {
+    CUtensorMap m;
+    cuuint64_t dims[4] = {8, (cuuint64_t)rows, (cuuint64_t)kSlices, (cuuint64_t)(ld / 8)};
+    cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)stride * 2, 16};
+    cuuint32_t box[4] = {8, (cuuint32_t)box_rows, (cuuint32_t)kSlices, (cuuint32_t)TC_KG};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(base), dims, strides,
+                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(HSIM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return m;
+}
+
+void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int ldx, size_t xstride,
                const __nv_bfloat16 *Ys, int ldy, size_t ystride, const int *ex, const int *ey, double *C, int ldc,
                int k_len, int splits, int lower) {
-    // the kernel reads the digit slices as 16-byte vectors: every slice base
-    // and every row start must be 16-byte aligned
     auto aligned16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-    HSIM_CHECK_ARG(aligned16(Xs) && aligned16(Ys) && ldx % 8 == 0 && ldy % 8 == 0 && xstride % 8 == 0 &&
-                       ystride % 8 == 0 && k_len % TKs == 0,
-                   "ozaki product: operand not 16-byte aligned");
-    HSIM_CHECK_ARG(!lower || (M == N && TM == TN), "ozaki product: lower triangle needs a square result");
-    const size_t sm = smem_bytes();
-    HSIM_CUDA(cudaFuncSetAttribute(k_ozaki_nt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HSIM_CHECK_ARG(aligned16(Xs) && aligned16(Ys) && ldx == ldy && ldx % TC_K == 0 && xstride % 8 == 0 &&
+                       ystride % 8 == 0 && k_len % TC_K == 0 && k_len <= ldx,
+                   "ozaki product: operand layout not supported by the TMA maps");
+    HSIM_CHECK_ARG(!lower || M == N, "ozaki product: lower triangle needs a square result");
+    const CUtensorMap mx = slice_map(Xs, M, ldx, xstride, TC_M);
+    const CUtensorMap my = slice_map(Ys, N, ldy, ystride, TC_N);
+    HSIM_CUDA(cudaFuncSetAttribute(k_ozaki_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     int k_split = (int)((k_len + splits - 1) / splits);
     k_split = (k_split + kFlush - 1) / kFlush * kFlush;
     splits = (int)cdiv(k_len, k_split);
-    dim3 g(cdiv(N, TN), cdiv(M, TM), (unsigned)splits);
-    k_ozaki_nt<<<g, 256, sm, s>>>(M, N, Xs, ldx, xstride, Ys, ldy, ystride, ex, ey, C, ldc, k_len, k_split,
-                                  splits > 1 ? 1 : 0, lower);
+    dim3 g(cdiv(N, TC_N), cdiv(M, TC_M), (unsigned)splits);
+    k_ozaki_tc<<<g, TC_THREADS, TC_SMEM, s>>>(M, N, mx, my, ex, ey, C, ldc, k_len, k_split, splits > 1 ? 1 : 0, lower);
     HSIM_LAUNCHED();
 }
 
@@ -377,17 +528,43 @@ void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y,
     if (X.rows <= 0 || Y.rows <= 0) return;
     HSIM_CHECK_ARG(X.ld == Y.ld, "ozaki_product: operands split over different K");
     if (splits <= 0) {
-        const int64_t tx = cdiv(X.rows, TM), ty = cdiv(Y.rows, TN);
-        const int64_t tiles = lower ? tx * (tx + 1) / 2 : tx * ty;
-        splits = (int)std::max<int64_t>(1, std::min<int64_t>((4LL * sm_count_oz() + tiles - 1) / tiles,
-                                                              (int64_t)cdiv(k_len, 1024)));
+        // split K so that tiles x splits fills whole waves of one CTA per SM
+        const int64_t tx = cdiv(X.rows, TC_M), ty = cdiv(Y.rows, TC_N);
+        int64_t tiles = 0;
+        for (int64_t r = 0; r < tx; ++r) tiles += lower ? std::min<int64_t>(ty, (r * TC_M + TC_M - 1) / TC_N + 1) : ty;
+        const int64_t sms = sm_count_oz();
+        const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(k_len / 2048, 8 * sms / tiles + 1));
+        double best = -1.0;
+        splits = 1;
+        for (int64_t sp = 1; sp <= s_max; ++sp) {
+            const int64_t ctas = tiles * sp, waves = (ctas + sms - 1) / sms;
+            // fill of the last wave, with a small preference for fewer splits
+            const double eff = (double)ctas / (double)(waves * sms) - 0.002 * (double)sp;
+            if (sp * tiles >= sms / 2 && eff > best + 1e-9) {
+                best = eff;
+                splits = (int)sp;
+            }
+        }
+        if (best < 0) splits = (int)s_max;
     }
     if (splits > 1) {
         if (ldc == Y.rows) HSIM_CUDA(cudaMemsetAsync(C, 0, (size_t)X.rows * Y.rows * sizeof(double), s));
         else HSIM_CUDA(cudaMemset2DAsync(C, (size_t)ldc * sizeof(double), 0, (size_t)Y.rows * sizeof(double), X.rows, s));
     }
-    launch_nt(s, X.rows, Y.rows, X.slices, X.ld, X.stride, Y.slices, Y.ld, Y.stride, X.exps, Y.exps, C, ldc, X.ld,
+    launch_tc(s, X.rows, Y.rows, X.slices, X.ld, X.stride, Y.slices, Y.ld, Y.stride, X.exps, Y.exps, C, ldc, X.ld,
               splits, lower ? 1 : 0);
+}
+
+void ozaki_check(cudaStream_t s) {
+    int h = 0;
+    HSIM_CUDA(cudaMemcpyFromSymbolAsync(&h, g_oz_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    if (h != 0) {
+        const int zero = 0;
+        HSIM_CUDA(cudaMemcpyToSymbolAsync(g_oz_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        fail(HSIM_E_INTERNAL, "tensor-core product: an mbarrier wait timed out");
+    }
 }
 
 }  // namespace k

@@ -171,6 +171,9 @@ OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, 
 // writes each value and its mirror image (X.rows == Y.rows)
 void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y, int k_len, double *C, int ldc,
                    int splits, bool lower = false);
+// fails (HSIM_E_INTERNAL) if a tensor-core product kernel gave up waiting on
+// one of its barriers since the last check; synchronises the stream
+void ozaki_check(cudaStream_t s);
 
 }  // namespace k
 }  // namespace hsim
