@@ -544,14 +544,15 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 k::axpy_matrix(s, n, a, res_buf + locked, q, H->Psi.p + locked, q);
             }
             if (locked > 0) k::copy_matrix(s, n, locked, H->Phi.p, q, H->Psi.p, q);
-            inf.ms_solve += ts.stop();
+            double ph[6];
+            inf.ms_solve += (ph[0] = ts.stop());
             // column scaling to unit M-norm, then S Psi, M Psi (Alg. 1, reduced matrices)
             apply_M(ctx, H, tau, q, H->Psi.p, q, H->MP.p, q);
             k::col_dots(s, n, q, H->Psi.p, q, H->MP.p, q, nullptr, H->colw.p);
             k::scale_cols_rsqrt(s, n, q, H->colw.p, H->Psi.p, q);
             k::scale_cols_rsqrt(s, n, q, H->colw.p, H->MP.p, q);
             apply_S(ctx, H, tau, q, H->Psi.p, q, H->SP.p, q);
-            inf.ms_spmm += ts.stop();
+            inf.ms_spmm += (ph[1] = ts.stop());
             if (mixed) {
                 // FP64-accurate Grams on BF16 tensor cores: Psi split once
                 const size_t part = k::ozaki_cols_scratch(n, q);
@@ -559,27 +560,27 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 k::OzakiOperand X = k::ozaki_split_cols(s, n, q, H->Psi.p, q, H->oz.p);
                 k::OzakiOperand YS = k::ozaki_split_cols(s, n, q, H->SP.p, q, H->oz.p + part);
                 k::OzakiOperand YM = k::ozaki_split_cols(s, n, q, H->MP.p, q, H->oz.p + 2 * part);
-                k::ozaki_product(s, X, YS, X.ld, H->Sbar.p, q, 0, true);
-                k::ozaki_product(s, X, YM, X.ld, H->Mbar.p, q, 0, true);
+                k::ozaki_product(s, X, YS, X.kp, H->Sbar.p, q, 0, true);
+                k::ozaki_product(s, X, YM, X.kp, H->Mbar.p, q, 0, true);
             } else {
                 k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
                 k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);
             }
-            inf.ms_gram += ts.stop();
+            inf.ms_gram += (ph[2] = ts.stop());
             // dense eigenproblem (Alg. 1): Ritz values ascending, M-orthonormal
             ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps);
-            inf.ms_ritz += ts.stop();
+            inf.ms_ritz += (ph[3] = ts.stop());
             // update Phi = Psi Phi_bar (Alg. 1)
             if (mixed) {
                 const size_t part = k::ozaki_rows_scratch(n, q);
                 H->oz.reserve(part + k::ozaki_cols_scratch(q, q));
                 k::OzakiOperand X = k::ozaki_split_rows(s, n, q, H->Psi.p, q, H->oz.p);
                 k::OzakiOperand Y = k::ozaki_split_cols(s, q, q, H->phibar.p, q, H->oz.p + part);
-                k::ozaki_product(s, X, Y, X.ld, H->Phi.p, q, 1);
+                k::ozaki_product(s, X, Y, X.kp, H->Phi.p, q, 1);
             } else {
                 k::gemm_nn(s, n, q, q, H->Psi.p, q, H->phibar.p, q, H->Phi.p, q);
             }
-            inf.ms_update += ts.stop();
+            inf.ms_update += (ph[4] = ts.stop());
             // convergence test (eq. conv2)
             apply_S(ctx, H, tau, q, H->Phi.p, q, H->SP.p, q);
             apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
@@ -588,7 +589,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->lam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaStreamSynchronize(s));
             if (mixed) k::ozaki_check(s);
-            inf.ms_residual += ts.stop();
+            inf.ms_residual += (ph[5] = ts.stop());
             double lam_ref = lam_h[q - 1];
             for (int i = 0; i < q; ++i)
                 if (lam_h[i] > 1e-8 * lam_h[q - 1]) {
@@ -603,9 +604,10 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             }
             if (trace_on())
                 std::fprintf(stderr,
-                             "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g\n",
-                             tau, it, locked, maxres, sweeps, (int)refine, lam_h[0],
-                             lam_h[p - 1]);
+                             "[hsim] level %d it %d locked %d max_res %.3e ritz_sweeps %d refine %d lam0 %.6g lam_p %.6g"
+                             " ms solve %.1f spmm %.1f gram %.1f ritz %.1f update %.1f residual %.1f\n",
+                             tau, it, locked, maxres, sweeps, (int)refine, lam_h[0], lam_h[p - 1], ph[0], ph[1], ph[2],
+                             ph[3], ph[4], ph[5]);
             if (!(maxres < tol) && !std::isfinite(maxres)) fail(HSIM_E_INTERNAL, "non-finite residual");
             if (maxres < tol) break;
             if (o.refine == 0 && !refine && it >= 2 && maxres > 0.7 * prev_maxres && maxres < 1e-6) refine = true;
@@ -957,7 +959,7 @@ hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int ka, int kb, const double *A, 
         DevBuf<unsigned char> scratch(k::ozaki_cols_scratch(n, ka) + k::ozaki_cols_scratch(n, kb));
         k::OzakiOperand X = k::ozaki_split_cols(ctx->stream, n, ka, A, lda, scratch.p);
         k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, n, kb, B, ldb, scratch.p + k::ozaki_cols_scratch(n, ka));
-        k::ozaki_product(ctx->stream, X, Y, X.ld, G, kb, 0);
+        k::ozaki_product(ctx->stream, X, Y, X.kp, G, kb, 0);
         k::ozaki_check(ctx->stream);
     });
 }
@@ -971,7 +973,7 @@ hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int kk, int m, const doubl
         DevBuf<unsigned char> scratch(k::ozaki_rows_scratch(n, kk) + k::ozaki_cols_scratch(kk, m));
         k::OzakiOperand X = k::ozaki_split_rows(ctx->stream, n, kk, A, lda, scratch.p);
         k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, kk, m, B, ldb, scratch.p + k::ozaki_rows_scratch(n, kk));
-        k::ozaki_product(ctx->stream, X, Y, X.ld, C, ldc, 1);
+        k::ozaki_product(ctx->stream, X, Y, X.kp, C, ldc, 1);
         k::ozaki_check(ctx->stream);
     });
 }

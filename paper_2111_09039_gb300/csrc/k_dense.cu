@@ -492,6 +492,23 @@ __global__ void __launch_bounds__(256) k_jacobi_slots(int k, int m, double *A, d
     if (local_rot) atomicAdd(rotations, local_rot);
 }
 
+// number of pairs i < j < k that the next sweep would rotate
+__global__ void k_offdiag_count(int k, const double *__restrict__ A, int lda, double tol, double abs_tol,
+                                unsigned long long *count) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = 0;
+    if (idx < (int64_t)k * k) {
+        int i = (int)(idx / k), j = (int)(idx % k);
+        if (i < j) {
+            double apq = A[(size_t)i * lda + j];
+            double app = A[(size_t)i * lda + i], aqq = A[(size_t)j * lda + j];
+            c = (fabs(apq) > abs_tol && fabs(apq) > tol * sqrt(fabs(app) * fabs(aqq))) ? 1 : 0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 // rank of each eigenvalue in ascending order (ties by index)
 __global__ void k_rank(int k, const double *__restrict__ A, int lda, int *__restrict__ rank,
                        double *__restrict__ evals_sorted) {
@@ -684,7 +701,8 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     HSIM_LAUNCHED();
     k_jacobi_init<<<cdiv((int64_t)m * m, 256), 256, 0, s>>>(k, m, T, A, V);
     HSIM_LAUNCHED();
-    // Jacobi sweeps (one cooperative launch each) until a sweep rotates nothing
+    // Jacobi sweeps (one cooperative launch each) until no off-diagonal pair
+    // is left above the rotation threshold
     int blocks_per_sm = 0;
     HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_jacobi_slots, 256, 0));
     const int nt = (m / 2 + kJT - 1) / kJT;
@@ -692,8 +710,16 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     int grid = std::max(1, std::min(blocks_per_sm * sm_count(), tasks));
     double tol = 1e-15, abs_tol = 1e-300;
     int sw = 0;
-    unsigned long long hrot = 1;
+    unsigned long long hrot = 0;
     double *pA = A, *pA2 = A2, *pV = V, *pV2 = V2;
+    auto count_offdiag = [&]() {
+        HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        k_offdiag_count<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, pA, m, tol, abs_tol, rot);
+        HSIM_LAUNCHED();
+        HSIM_CUDA(cudaMemcpyAsync(&hrot, rot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        HSIM_CUDA(cudaStreamSynchronize(s));
+    };
+    count_offdiag();
     while (hrot != 0 && sw < 40) {
         HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
         int kk_ = k, mm_ = m;
@@ -705,9 +731,8 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
             std::swap(pA, pA2);
             std::swap(pV, pV2);
         }
-        HSIM_CUDA(cudaMemcpyAsync(&hrot, rot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        HSIM_CUDA(cudaStreamSynchronize(s));
         ++sw;
+        count_offdiag();
     }
     if (sweeps) *sweeps = sw;
     // X = C^-T V = L^-T D^-1/2 V (V copied to k x k in pA2), then columns sorted by eigenvalue

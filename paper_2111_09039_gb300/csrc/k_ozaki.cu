@@ -17,7 +17,6 @@
 // Kernel shape: C (FP64, M x N) (+)= X Y^T with X (M x K) and Y (N x K) both
 // K-contiguous digit slices, on the tcgen05 tensor cores (TMA-fed shared
 // memory, TMEM accumulators; k_ozaki_tc below).
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -105,32 +104,74 @@ __device__ __forceinline__ void split_value(double x, int e, __nv_bfloat16 *out,
     out[0] = __int2bfloat16_rn((int)T);
 }
 
-// slices of a row-major R x C block split per row: out[s] is R x ldo (K = C
-// contiguous), columns C..ldo-1 zero
-__global__ void k_split_rows(int R, int C, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
-                             __nv_bfloat16 *__restrict__ out, int ldo, size_t slice_stride) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)R * ldo) return;
-    int i = (int)(idx / ldo), j = (int)(idx % ldo);
-    double x = j < C ? X[(size_t)i * ldx + j] : 0.0;
-    split_value(x, ex[i], out + (size_t)i * ldo + j, slice_stride);
+// Global layout of the digit slices ("tiled"): for K-chunk kc = k / 32,
+// slice s, row r (rows padded to rows_p, a multiple of 128) and k,
+//     offset = ((kc * kSlices + s) * rows_p + 8 (r / 8)) * 32 + 64 ((k % 32) / 8)
+//              + 8 (r % 8) + k % 8     (BF16 elements),
+// i.e. 8 x 8 core matrices (8 rows x 16 bytes) ordered [kc][s][r/8][k%32/8].
+// A 32-deep K step of any 128 (or 64) consecutive rows of one slice is then
+// one contiguous 8 KB (4 KB) block that a bulk copy moves straight into the
+// core-matrix order the tensor-core descriptors read.
+__device__ __forceinline__ size_t tiled_off(int s, int r, int k, int rows_p) {
+    return (((size_t)(k >> 5) * kSlices + s) * (size_t)rows_p + (size_t)(r & ~7)) * 32 + (size_t)((k & 31) >> 3) * 64 +
+           (size_t)(r & 7) * 8 + (size_t)(k & 7);
 }
 
-// slices of a row-major R x C block split per column, transposed: out[s] is
-// C x ldo with K = R contiguous (rows R..ldo-1 zero)
-__global__ void k_split_cols_t(int R, int C, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
-                               __nv_bfloat16 *__restrict__ out, int ldo, size_t slice_stride) {
+// digits of the 8 values v[0..7] (consecutive k of one row, exponent e) as
+// one 16-byte vector per slice
+__device__ __forceinline__ void split8_store(const double (&v)[8], int e, __nv_bfloat16 *out, size_t off,
+                                             int rows_p) {
+    __nv_bfloat16 d[kSlices][8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        __nv_bfloat16 one[kSlices];
+        split_value(v[t], e, one, 1);
+#pragma unroll
+        for (int sl = 0; sl < kSlices; ++sl) d[sl][t] = one[sl];
+    }
+    const size_t slice_step = (size_t)rows_p * 32;  // next slice within the same K-chunk
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl)
+        *reinterpret_cast<uint4 *>(out + off + sl * slice_step) = *reinterpret_cast<const uint4 *>(d[sl]);
+}
+
+// split a row-major R x K block per row (K = columns): one thread per row and
+// 8-wide K group; a warp covers one 8-row group x one 32-deep K-chunk
+__global__ void k_split_rows_tiled(int R, int K, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
+                                   __nv_bfloat16 *__restrict__ out, int rows_p, int kp) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int KC = kp / 32;
+    if (gw >= (int64_t)(rows_p / 8) * KC) return;
+    const int rg = (int)(gw / KC), kc = (int)(gw % KC);
+    const int r = rg * 8 + (lane & 7), k0 = kc * 32 + (lane >> 3) * 8;
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = (r < R && k0 + t < K) ? X[(size_t)r * ldx + k0 + t] : 0.0;
+    split8_store(v, r < R ? ex[r] : -1074, out, tiled_off(0, r, k0, rows_p), rows_p);
+}
+
+// split a row-major K x C block per column (operand row r = column r, K =
+// rows of X), transposed through shared memory: a block handles 32 columns x
+// a 32-deep K-chunk
+__global__ void k_split_cols_tiled(int K, int C, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
+                                   __nv_bfloat16 *__restrict__ out, int rows_p) {
     __shared__ double tile[32][33];
-    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        int r = r0 + yy, c = c0 + threadIdx.x;
-        tile[yy][threadIdx.x] = (r < R && c < C) ? X[(size_t)r * ldx + c] : 0.0;
+    const int kc = blockIdx.x, c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 4 threads
+    for (int yy = ty; yy < 32; yy += 4) {
+        const int k = kc * 32 + yy, c = c0 + tx;
+        tile[yy][tx] = (k < K && c < C) ? X[(size_t)k * ldx + c] : 0.0;
     }
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        int c = c0 + yy, r = r0 + threadIdx.x;
-        if (c < C && r < ldo) split_value(tile[threadIdx.x][yy], ex[c], out + (size_t)c * ldo + r, slice_stride);
-    }
+    // thread -> (column c0 + lc, K group kg): 32 columns x 4 groups = 128 threads
+    const int lc = (threadIdx.x & 7) + 8 * (threadIdx.x >> 5), kg = (threadIdx.x >> 3) & 3;
+    const int r = c0 + lc;
+    if (r >= rows_p) return;
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = tile[kg * 8 + t][lc];
+    split8_store(v, r < C ? ex[r] : -1074, out, tiled_off(0, r, kc * 32 + kg * 8, rows_p), rows_p);
 }
 
 __global__ void k_fill_int(int n, int v, int *__restrict__ x) {
@@ -166,14 +207,14 @@ int sm_count_oz() {
 
 // tcgen05 form of the same product (5th-generation tensor cores, TMEM).
 //
-// CTA tile: 128 rows of X by 64 rows of Y, K staged 32 at a time by TMA into
-// three shared-memory stages.  A 4-D tensor map [8 elements, rows, slice,
-// K/8] puts every stage in core-matrix order (8 rows x 16 bytes contiguous):
-// byte offset ((kg * 6 + s) * R + r) * 16 for digit slice s, row r, K-group
-// kg, i.e. an MMA operand descriptor with SBO = 128 bytes between 8-row
-// groups and LBO = 6 R * 16 bytes between K-groups.  Because the Y slices of
-// one stage follow each other at the row-group stride, Y_0 .. Y_5 form one
-// N = 384 operand: one MMA multiplies X_s by [Y_0 .. Y_{5-s}] (N = 64 (6 - s),
+// CTA tile: 128 rows of X by 64 rows of Y, K staged 32 at a time into three
+// shared-memory stages by bulk copies (TMA, cp.async.bulk): the tiled global
+// layout makes each slice of a stage one contiguous block, so a stage is 6
+// copies of 8 KB (X) and 6 of 4 KB (Y), landing in core-matrix order
+// [s][r/8][k/8][8 x 16 bytes]: an MMA operand descriptor with LBO = 128 bytes
+// between K-groups and SBO = 512 bytes between 8-row groups.  Because the Y
+// slices of one stage follow each other at the row-group stride, Y_0 .. Y_5
+// form one N = 384 operand: one MMA multiplies X_s by [Y_0 .. Y_{5-s}] (N = 64 (6 - s),
 // split at 256) and its 64-column blocks land exactly on the accumulators
 // acc_{s} .. acc_{5} of the digit sums D = s + t, which sit side by side in
 // TMEM (columns 64 D .. 64 D + 63, 384 of the 512 allocated).  Per 16-deep
@@ -247,12 +288,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c1, int c3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];\n" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(c3), "r"(bar)
-        : "memory");
+// bulk copy (TMA) of `bytes` contiguous bytes global -> shared, completing on bar
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
@@ -280,9 +320,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_ozaki_tc(int M, int N, const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
-               const int *__restrict__ ex, const int *__restrict__ ey, double *__restrict__ C, int ldc, int k_len,
-               int k_split, int atomic, int lower) {
+    k_ozaki_tc(int M, int N, const __nv_bfloat16 *__restrict__ Xs, int rows_px, const __nv_bfloat16 *__restrict__ Ys,
+               int rows_py, const int *__restrict__ ex, const int *__restrict__ ey, double *__restrict__ C, int ldc,
+               int k_len, int k_split, int atomic, int lower) {
     extern __shared__ unsigned char smem_dyn[];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], accf_bar, acce_bar, drain_bar;
     __shared__ uint32_t tmem_slot;
@@ -328,9 +368,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(TC_STAGE_BYTES)
                              : "memory");
                 const uint32_t a_dst = smem0 + st * TC_STAGE_BYTES;
-                const int kg = (k_beg + kt * TC_K) / 8;
-                tma_load_4d(a_dst, &mapX, i0, kg, fb);
-                tma_load_4d(a_dst + TC_A_BYTES, &mapY, j0, kg, fb);
+                const size_t kc = (size_t)(k_beg + kt * TC_K) / TC_K;
+#pragma unroll 1
+                for (int sl = 0; sl < kSlices; ++sl) {
+                    bulk_load(a_dst + sl * (TC_A_BYTES / kSlices),
+                              Xs + ((kc * kSlices + sl) * rows_px + i0) * TC_K, TC_A_BYTES / kSlices, fb);
+                    bulk_load(a_dst + TC_A_BYTES + sl * (TC_B_BYTES / kSlices),
+                              Ys + ((kc * kSlices + sl) * rows_py + j0) * TC_K, TC_B_BYTES / kSlices, fb);
+                }
                 issued = kt + 1;
             }
             // drain: the last loads of every stage have landed before the CTA exits
@@ -340,7 +385,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0 && nk > 0) {
             bool ok = true;
-            const uint32_t lbo_a = 16u * TC_M * kSlices, lbo_b = 16u * TC_N * kSlices;
+            // core matrices: 128 bytes apart along K, 512 bytes apart along rows
+            constexpr uint32_t LBO = 128, SBO = 512;
             for (int kt = 0; kt < nk && ok; ++kt) {
                 const int st = kt % TC_STAGES;
                 const int chunk = kt / (kFlush / TC_K);
@@ -352,16 +398,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t a_base = smem0 + st * TC_STAGE_BYTES, b_base = a_base + TC_A_BYTES;
 #pragma unroll
                 for (int k16 = 0; k16 < TC_K / 16; ++k16) {
-                    const uint32_t a_k = a_base + 2 * k16 * lbo_a, b_k = b_base + 2 * k16 * lbo_b;
+                    const uint32_t a_k = a_base + 2 * k16 * LBO, b_k = b_base + 2 * k16 * LBO;
 #pragma unroll
                     for (int sl = 0; sl < kSlices; ++sl) {
-                        const uint64_t ad = umma_desc(a_k + sl * 16u * TC_M, lbo_a, 128);
+                        const uint64_t ad = umma_desc(a_k + sl * (TC_A_BYTES / kSlices), LBO, SBO);
                         const int acc = (chunk_first && k16 == 0 && sl == 0) ? 0 : 1;
                         const int ncols = TC_N * (kSlices - sl);  // Y_0 .. Y_{5-s}
                         const int n1 = ncols > 256 ? 256 : ncols;
-                        umma_f16(tmem + TC_N * sl, ad, umma_desc(b_k, lbo_b, 128), umma_idesc(TC_M, n1), acc);
-                        if (ncols > 256)
-                            umma_f16(tmem + TC_N * sl + 256, ad, umma_desc(b_k + 256u * 16u, lbo_b, 128),
+                        umma_f16(tmem + TC_N * sl, ad, umma_desc(b_k, LBO, SBO), umma_idesc(TC_M, n1), acc);
+                        if (ncols > 256)  // rows 256.. of [Y_0 .. Y_5]: 32 row groups further
+                            umma_f16(tmem + TC_N * sl + 256, ad, umma_desc(b_k + 32u * SBO, LBO, SBO),
                                      umma_idesc(TC_M, ncols - 256), acc);
                     }
                 }
@@ -420,54 +466,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        HSIM_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-        if (!p || q != cudaDriverEntryPointSuccess) fail(HSIM_E_CUDA, "cuTensorMapEncodeTiled not available");
-        fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-// 4-D map [8 elements, rows, slice, K/8] over kSlices digit slices of rows x ld
-// BF16 (K contiguous), box [8, box_rows, kSlices, TC_KG]
-CUtensorMap slice_map(const __nv_bfloat16 *base, int rows, int ld, size_t stride, int box_rows) {
-    CUtensorMap m;
-    cuuint64_t dims[4] = {8, (cuuint64_t)rows, (cuuint64_t)kSlices, (cuuint64_t)(ld / 8)};
-    cuuint64_t strides[3] = {(cuuint64_t)ld * 2, (cuuint64_t)stride * 2, 16};
-    cuuint32_t box[4] = {8, (cuuint32_t)box_rows, (cuuint32_t)kSlices, (cuuint32_t)TC_KG};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16 *>(base), dims, strides,
-                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) fail(HSIM_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    return m;
-}
-
-void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int ldx, size_t xstride,
-               const __nv_bfloat16 *Ys, int ldy, size_t ystride, const int *ex, const int *ey, double *C, int ldc,
-               int k_len, int splits, int lower) {
+void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int rows_px, const __nv_bfloat16 *Ys,
+               int rows_py, const int *ex, const int *ey, double *C, int ldc, int k_len, int splits, int lower) {
     auto aligned16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-    HSIM_CHECK_ARG(aligned16(Xs) && aligned16(Ys) && ldx == ldy && ldx % TC_K == 0 && xstride % 8 == 0 &&
-                       ystride % 8 == 0 && k_len % TC_K == 0 && k_len <= ldx,
-                   "ozaki product: operand layout not supported by the TMA maps");
+    HSIM_CHECK_ARG(aligned16(Xs) && aligned16(Ys) && rows_px % TC_M == 0 && rows_py % TC_M == 0 && M <= rows_px &&
+                       N <= rows_py && k_len % TC_K == 0,
+                   "ozaki product: operand layout not supported");
     HSIM_CHECK_ARG(!lower || M == N, "ozaki product: lower triangle needs a square result");
-    const CUtensorMap mx = slice_map(Xs, M, ldx, xstride, TC_M);
-    const CUtensorMap my = slice_map(Ys, N, ldy, ystride, TC_N);
     HSIM_CUDA(cudaFuncSetAttribute(k_ozaki_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     int k_split = (int)((k_len + splits - 1) / splits);
     k_split = (k_split + kFlush - 1) / kFlush * kFlush;
     splits = (int)cdiv(k_len, k_split);
     dim3 g(cdiv(N, TC_N), cdiv(M, TC_M), (unsigned)splits);
-    k_ozaki_tc<<<g, TC_THREADS, TC_SMEM, s>>>(M, N, mx, my, ex, ey, C, ldc, k_len, k_split, splits > 1 ? 1 : 0, lower);
+    k_ozaki_tc<<<g, TC_THREADS, TC_SMEM, s>>>(M, N, Xs, rows_px, Ys, rows_py, ex, ey, C, ldc, k_len, k_split,
+                                               splits > 1 ? 1 : 0, lower);
     HSIM_LAUNCHED();
 }
 
@@ -475,50 +487,48 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// Scratch sizes are whole multiples of 256 bytes, so operands placed back to
-// back in one buffer keep the 16-byte alignment of the vector loads.
-size_t ozaki_cols_scratch(int n, int cols) {
-    const int ldk = round_up(n, TKs);
-    size_t b = (size_t)kSlices * cols * ldk * sizeof(__nv_bfloat16) + sizeof(int) * (size_t)cols;
+// Scratch: kSlices x rows_p x kp BF16 digits (tiled layout) then rows_p
+// exponents, rounded to whole 256-byte blocks so operands placed back to back
+// in one buffer stay aligned for the bulk copies.
+static size_t operand_bytes(int rows, int kdim) {
+    const size_t rows_p = (size_t)round_up(std::max(rows, 1), TC_M), kp = (size_t)round_up(std::max(kdim, 1), TKs);
+    size_t b = (size_t)kSlices * rows_p * kp * sizeof(__nv_bfloat16) + sizeof(int) * rows_p;
     return (b + 511) / 256 * 256;
 }
 
-size_t ozaki_rows_scratch(int rows, int k) {
-    const int ldk = round_up(k, TKs);
-    size_t b = (size_t)kSlices * rows * ldk * sizeof(__nv_bfloat16) + sizeof(int) * (size_t)rows;
-    return (b + 511) / 256 * 256;
+size_t ozaki_cols_scratch(int n, int cols) { return operand_bytes(cols, n); }
+size_t ozaki_rows_scratch(int rows, int k) { return operand_bytes(rows, k); }
+
+static OzakiOperand make_operand(int rows, int kdim, void *scratch) {
+    OzakiOperand op;
+    op.rows = rows;
+    op.rows_p = round_up(std::max(rows, 1), TC_M);
+    op.kp = round_up(std::max(kdim, 1), TKs);
+    op.slices = static_cast<__nv_bfloat16 *>(scratch);
+    op.exps = reinterpret_cast<int *>(op.slices + (size_t)kSlices * op.rows_p * op.kp);
+    return op;
 }
 
 OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch) {
-    OzakiOperand op;
-    op.rows = cols;
-    op.ld = round_up(n, TKs);
-    op.stride = (size_t)cols * op.ld;
-    op.slices = static_cast<__nv_bfloat16 *>(scratch);
-    op.exps = reinterpret_cast<int *>(op.slices + (size_t)kSlices * op.stride);
+    OzakiOperand op = make_operand(cols, n, scratch);
     if (n <= 0 || cols <= 0) return op;
     k_fill_int<<<cdiv(cols, 256), 256, 0, s>>>(cols, -1074, op.exps);
     HSIM_LAUNCHED();
     k_col_exps<<<dim3(cdiv(n, 256), cdiv(cols, 256)), 256, 0, s>>>(n, cols, X, ldx, op.exps);
     HSIM_LAUNCHED();
-    k_split_cols_t<<<dim3(cdiv(op.ld, 32), cdiv(cols, 32)), dim3(32, 8), 0, s>>>(n, cols, X, ldx, op.exps,
-                                                                                  op.slices, op.ld, op.stride);
+    k_split_cols_tiled<<<dim3(op.kp / 32, cdiv(op.rows_p, 32)), 128, 0, s>>>(n, cols, X, ldx, op.exps, op.slices,
+                                                                          op.rows_p);
     HSIM_LAUNCHED();
     return op;
 }
 
 OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch) {
-    OzakiOperand op;
-    op.rows = rows;
-    op.ld = round_up(k, TKs);
-    op.stride = (size_t)rows * op.ld;
-    op.slices = static_cast<__nv_bfloat16 *>(scratch);
-    op.exps = reinterpret_cast<int *>(op.slices + (size_t)kSlices * op.stride);
+    OzakiOperand op = make_operand(rows, k, scratch);
     if (rows <= 0) return op;
     k_row_exps<<<cdiv(rows, 8), 256, 0, s>>>(rows, k, X, ldx, op.exps);
     HSIM_LAUNCHED();
-    k_split_rows<<<cdiv((int64_t)rows * op.ld, 256), 256, 0, s>>>(rows, k, X, ldx, op.exps, op.slices, op.ld,
-                                                                  op.stride);
+    const int64_t warps = (int64_t)(op.rows_p / 8) * (op.kp / 32);
+    k_split_rows_tiled<<<cdiv(warps * 32, 256), 256, 0, s>>>(rows, k, X, ldx, op.exps, op.slices, op.rows_p, op.kp);
     HSIM_LAUNCHED();
     return op;
 }
@@ -526,7 +536,7 @@ OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, 
 void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y, int k_len, double *C, int ldc,
                    int splits, bool lower) {
     if (X.rows <= 0 || Y.rows <= 0) return;
-    HSIM_CHECK_ARG(X.ld == Y.ld, "ozaki_product: operands split over different K");
+    HSIM_CHECK_ARG(X.kp == Y.kp, "ozaki_product: operands split over different K");
     if (splits <= 0) {
         // split K so that tiles x splits fills whole waves of one CTA per SM
         const int64_t tx = cdiv(X.rows, TC_M), ty = cdiv(Y.rows, TC_N);
@@ -551,8 +561,8 @@ void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y,
         if (ldc == Y.rows) HSIM_CUDA(cudaMemsetAsync(C, 0, (size_t)X.rows * Y.rows * sizeof(double), s));
         else HSIM_CUDA(cudaMemset2DAsync(C, (size_t)ldc * sizeof(double), 0, (size_t)Y.rows * sizeof(double), X.rows, s));
     }
-    launch_tc(s, X.rows, Y.rows, X.slices, X.ld, X.stride, Y.slices, Y.ld, Y.stride, X.exps, Y.exps, C, ldc, X.ld,
-              splits, lower ? 1 : 0);
+    launch_tc(s, X.rows, Y.rows, X.slices, X.rows_p, Y.slices, Y.rows_p, X.exps, Y.exps, C, ldc, X.kp, splits,
+              lower ? 1 : 0);
 }
 
 void ozaki_check(cudaStream_t s) {

@@ -149,11 +149,11 @@ void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
 
 // ---- FP64-accurate products on BF16 tensor cores (k_ozaki.cu) --------------
 constexpr int kOzakiSlices = 6;
-// digit slices of an FP64 block: kOzakiSlices arrays of `rows` x ld BF16
-// (K contiguous, zero padded), with one exponent per row
+// digit slices of an FP64 block in the tiled layout of k_ozaki.cu: rows
+// padded to rows_p (multiple of 128), K to kp (multiple of 32), zero filled;
+// one exponent per row
 struct OzakiOperand {
-    int rows = 0, ld = 0;
-    size_t stride = 0;
+    int rows = 0, rows_p = 0, kp = 0;
     __nv_bfloat16 *slices = nullptr;
     int *exps = nullptr;
 };
@@ -165,7 +165,7 @@ size_t ozaki_rows_scratch(int rows, int k);
 OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch);
 // split X (row-major rows x k, K = k) per row
 OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch);
-// C (X.rows x Y.rows, FP64) = X Y^T over K = k_len; splits <= 0 chooses a
+// C (X.rows x Y.rows, FP64) = X Y^T over K = k_len (= X.kp); splits <= 0 chooses a
 // split-K count (C accumulated with atomics), 1 stores directly; lower: C is
 // symmetric, only tiles meeting the lower triangle run and the epilogue
 // writes each value and its mirror image (X.rows == Y.rows)
