@@ -50,6 +50,7 @@ def load_peaks():
 # FP64 rate: no FP64 figure is measured by the pool; GB300's nominal FP64
 # rate is 1.25 TFLOP/s (152 SMs).  A probe on this machine measured 1.19.
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 class ClockSampler:
@@ -359,43 +360,77 @@ def check_residual(hier, S, Md, lam, Phi, ctx):
 
 
 def roofline(info, infos, hier, p, peaks, peak_src, precision):
-    """Dominant phase of the solve and its achieved rate against the peak."""
+    """Achieved rate against the peak for the kernels of the solve; the
+    top-level entry is the kernel of the dominant phase."""
     q = info["q"]
     sizes = info["sizes"]
     iters = info["iters"]
     steps = len(infos)
-    gram_flops = sum(iters[t] * 2.0 * sizes[t] * q * (q + 1) for t in range(len(sizes) - 1))
-    upd_flops = sum(iters[t] * 2.0 * sizes[t] * q * q for t in range(len(sizes) - 1))
-    ms_gram = sum(i["ms_gram"] for i in infos) / steps
-    ms_upd = sum(i["ms_update"] for i in infos) / steps
-    phases = {k: sum(i["ms_" + k] for i in infos) / steps for k in
+    avg = lambda key: sum(i[key] for i in infos) / steps
+    phases = {k: avg("ms_" + k) for k in
               ("galerkin", "coarse", "prolong", "factor", "solve", "spmm", "gram", "ritz", "update", "residual")}
     dom = max(phases, key=phases.get)
-    gram_launches = sum(iters[:len(sizes) - 1]) * 2
+    sim_levels = range(len(sizes) - 1)
+    n_products = sum(iters[t] for t in sim_levels)
+    kernels = {}
+    # Ritz: two-sided Jacobi, 6 q^3 FP64 flops per sweep (rotations applied to
+    # the two rows and columns of A and to V, A symmetric)
+    sweeps = avg("ritz_sweeps")
+    ms_ritz = phases["ritz"]
+    jac = 6.0 * q ** 3 * sweeps / (ms_ritz * 1e-3) / 1e12 if ms_ritz > 0 else 0.0
+    kernels["ritz"] = {"kernel": "k_jacobi_slots (cyclic parallel Jacobi, FP64)", "bound": "alu",
+                       "achieved": jac, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": jac / FP64_PEAK_TFLOPS,
+                       "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s; a DFMA probe measured 1.19)",
+                       "traffic": None, "flops_per_sweep": 6.0 * q ** 3, "sweeps_per_step": sweeps,
+                       "launches_per_step": sweeps, "note": "time includes the Cholesky of M_bar and the two "
+                       "triangular transforms of the Rayleigh-Ritz step"}
+    # supernodal triangular solves: 4 nnz(L) flops per right-hand side
+    sflops = avg("solve_flops")
+    ms_solve = phases["solve"]
+    fp_peak = FP32_PEAK_TFLOPS if precision != "fp64" else FP64_PEAK_TFLOPS
+    sach = sflops / (ms_solve * 1e-3) / 1e12 if ms_solve > 0 else 0.0
+    kernels["solve"] = {"kernel": "k_solve_* (supernodal LDL^T forward/backward solves, %s)" %
+                        ("FP32" if precision != "fp64" else "FP64"), "bound": "alu", "achieved": sach,
+                        "peak": fp_peak, "unit": "TFLOP/s", "frac": sach / fp_peak,
+                        "peak_source": "FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s"
+                        if precision != "fp64" else "GB300 nominal FP64 (1.25 TFLOP/s)",
+                        "traffic": None, "note": "phase time includes the residual and SpMM of the "
+                        "correction-form iteration"}
+    gram_flops = sum(iters[t] * 2.0 * sizes[t] * q * (q + 1) for t in sim_levels)
+    upd_flops = sum(iters[t] * 2.0 * sizes[t] * q * q for t in sim_levels)
     if precision == "fp64":
-        peak = FP64_PEAK_TFLOPS
+        ms_gram = phases["gram"]
         ach = gram_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0
-        r = {"kernel": "gram (FP64 DFMA, Psi^T S Psi and Psi^T M Psi)", "bound": "alu",
-             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-             "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s; probe measured 1.19)",
-             "traffic": None, "launches_per_step": gram_launches,
-             "flops_per_launch": gram_flops / max(1, gram_launches),
-             "update_gemm_tflops": upd_flops / (ms_upd * 1e-3) / 1e12 if ms_upd > 0 else 0.0}
+        kernels["gram"] = {"kernel": "k_gram (FP64 DFMA, Psi^T S Psi and Psi^T M Psi)", "bound": "alu",
+                           "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                           "frac": ach / FP64_PEAK_TFLOPS,
+                           "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s; a DFMA probe measured 1.19)",
+                           "traffic": None, "launches_per_step": 2 * n_products,
+                           "update_gemm_tflops": upd_flops / (phases["update"] * 1e-3) / 1e12
+                           if phases["update"] > 0 else 0.0}
+        kernels["update"] = kernels["gram"]
     else:
-        # tensor-core Gram: 21 digit-pair products (6 digits, pairs s+t <= 5) of
-        # 2 n q^2 BF16 flops each, two Grams per iteration
+        # tensor-core products: 21 digit-pair products (6 digits, pairs s+t <= 5)
+        # of 2 n q(q+1)/2 BF16 flops for each symmetric Gram (two per
+        # iteration) and 2 n q^2 for the update, timed without the digit split
         pairs = 21
-        tc_flops = sum(iters[t] * 2 * pairs * 2.0 * sizes[t] * q * q for t in range(len(sizes) - 1))
+        tc_flops = pairs * (2.0 * gram_flops / 2.0 + upd_flops)
+        ms_tc = avg("ms_tc_product")
         peak = peaks.get("bf16_tflops_sustained", 1743.3)
-        ach = tc_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0
-        r = {"kernel": "k_ozaki_nt (FP64-accurate Gram on BF16 tensor cores, mma.sync)", "bound": "tensor",
-             "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-             "peak_source": f"{peak_src} bf16_tflops_sustained", "traffic": None,
-             "fp64_equivalent_tflops": gram_flops / (ms_gram * 1e-3) / 1e12 if ms_gram > 0 else 0.0,
-             "launches_per_step": gram_launches}
-    r["dominant_phase"] = dom
-    r["phase_ms"] = phases
-    return r
+        ach = tc_flops / (ms_tc * 1e-3) / 1e12 if ms_tc > 0 else 0.0
+        kernels["gram"] = {"kernel": "k_ozaki_tc (FP64-accurate products on tcgen05 BF16 tensor cores)",
+                           "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                           "frac": ach / peak, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                           "traffic": None, "launches_per_step": 3 * n_products,
+                           "fp64_equivalent_tflops": (gram_flops + upd_flops) / (ms_tc * 1e-3) / 1e12
+                           if ms_tc > 0 else 0.0, "ms_per_step": ms_tc}
+        kernels["update"] = kernels["gram"]
+    top = dict(kernels.get(dom, kernels["ritz"] if dom == "coarse" else kernels["gram"]))
+    top["dominant_phase"] = dom
+    top["phase_ms"] = phases
+    top["kernels"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
+                      for k, v in kernels.items() if k != "update"}
+    return top
 
 
 def cpu_baseline(workload, info, cols):

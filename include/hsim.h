@@ -87,6 +87,12 @@ typedef struct {
     double ms_galerkin, ms_coarse, ms_prolong, ms_factor, ms_solve, ms_spmm,
            ms_gram, ms_ritz, ms_update, ms_residual, ms_total;
     int q;
+    int ritz_calls;        /* Rayleigh-Ritz solves of size q on the SIM levels */
+    int ritz_sweeps;       /* Jacobi sweeps summed over those solves */
+    int coarse_sweeps;     /* Jacobi sweeps of the coarsest dense eigenproblem */
+    double ms_tc_product;  /* HSIM_MIXED: tensor-core product kernels alone (part of
+                              ms_gram and ms_update, which include the digit split) */
+    double solve_flops;    /* triangular-solve flops, 4 nnz(L) per right-hand side */
 } hsim_info;
 
 typedef struct hsim_ctx hsim_ctx;

@@ -43,14 +43,18 @@ class Info(ctypes.Structure):
                 ("ms_solve", ctypes.c_double), ("ms_spmm", ctypes.c_double),
                 ("ms_gram", ctypes.c_double), ("ms_ritz", ctypes.c_double),
                 ("ms_update", ctypes.c_double), ("ms_residual", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("q", ctypes.c_int)]
+                ("ms_total", ctypes.c_double), ("q", ctypes.c_int), ("ritz_calls", ctypes.c_int),
+                ("ritz_sweeps", ctypes.c_int), ("coarse_sweeps", ctypes.c_int),
+                ("ms_tc_product", ctypes.c_double), ("solve_flops", ctypes.c_double)]
 
     def to_dict(self) -> dict:
         T = self.levels
         d = {"levels": T, "sizes": list(self.sizes[:T]), "iters": list(self.iters[:T]),
              "shift": list(self.shift[:T]), "max_residual": self.max_residual,
              "factor_nnz": list(self.factor_nnz[:T]), "factor_flops": list(self.factor_flops[:T]),
-             "q": self.q}
+             "q": self.q, "ritz_calls": self.ritz_calls, "ritz_sweeps": self.ritz_sweeps,
+             "coarse_sweeps": self.coarse_sweeps, "ms_tc_product": self.ms_tc_product,
+             "solve_flops": self.solve_flops}
         for k in ("galerkin", "coarse", "prolong", "factor", "solve", "spmm", "gram", "ritz",
                   "update", "residual", "total"):
             d["ms_" + k] = getattr(self, "ms_" + k)

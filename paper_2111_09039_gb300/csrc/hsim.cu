@@ -389,6 +389,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     H->coarseLam.reserve(nc);
     int sweeps = 0;
     ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps);
+    inf.coarse_sweeps = sweeps;
     inf.ms_coarse = tm.stop();
     std::vector<double> lam_h(q);
     HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->coarseLam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -544,6 +545,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 k::axpy_matrix(s, n, a, res_buf + locked, q, H->Psi.p + locked, q);
             }
             if (locked > 0) k::copy_matrix(s, n, locked, H->Phi.p, q, H->Psi.p, q);
+            inf.solve_flops += 4.0 * (double)L.fs.nnz_L * a * (o.inv_iters + ((refine && !mixed) ? 1 : 0));
             double ph[6];
             inf.ms_solve += (ph[0] = ts.stop());
             // column scaling to unit M-norm, then S Psi, M Psi (Alg. 1, reduced matrices)
@@ -560,15 +562,22 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 k::OzakiOperand X = k::ozaki_split_cols(s, n, q, H->Psi.p, q, H->oz.p);
                 k::OzakiOperand YS = k::ozaki_split_cols(s, n, q, H->SP.p, q, H->oz.p + part);
                 k::OzakiOperand YM = k::ozaki_split_cols(s, n, q, H->MP.p, q, H->oz.p + 2 * part);
+                const double t_split = ts.stop();
                 k::ozaki_product(s, X, YS, X.kp, H->Sbar.p, q, 0, true);
                 k::ozaki_product(s, X, YM, X.kp, H->Mbar.p, q, 0, true);
+                const double t_prod = ts.stop();
+                inf.ms_tc_product += t_prod;
+                ph[2] = t_split + t_prod;
             } else {
                 k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
                 k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);
             }
-            inf.ms_gram += (ph[2] = ts.stop());
+            if (mixed) inf.ms_gram += ph[2];
+            else inf.ms_gram += (ph[2] = ts.stop());
             // dense eigenproblem (Alg. 1): Ritz values ascending, M-orthonormal
             ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps);
+            inf.ritz_calls += 1;
+            inf.ritz_sweeps += sweeps;
             inf.ms_ritz += (ph[3] = ts.stop());
             // update Phi = Psi Phi_bar (Alg. 1)
             if (mixed) {
@@ -576,11 +585,16 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 H->oz.reserve(part + k::ozaki_cols_scratch(q, q));
                 k::OzakiOperand X = k::ozaki_split_rows(s, n, q, H->Psi.p, q, H->oz.p);
                 k::OzakiOperand Y = k::ozaki_split_cols(s, q, q, H->phibar.p, q, H->oz.p + part);
+                const double t_split = ts.stop();
                 k::ozaki_product(s, X, Y, X.kp, H->Phi.p, q, 1);
+                const double t_prod = ts.stop();
+                inf.ms_tc_product += t_prod;
+                ph[4] = t_split + t_prod;
             } else {
                 k::gemm_nn(s, n, q, q, H->Psi.p, q, H->phibar.p, q, H->Phi.p, q);
             }
-            inf.ms_update += (ph[4] = ts.stop());
+            if (mixed) inf.ms_update += ph[4];
+            else inf.ms_update += (ph[4] = ts.stop());
             // convergence test (eq. conv2)
             apply_S(ctx, H, tau, q, H->Phi.p, q, H->SP.p, q);
             apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
