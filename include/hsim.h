@@ -170,6 +170,26 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *hier, const double *S_val_dev,
                        const double *M_diag_dev, int p, double tol, const hsim_options *opts,
                        double *evals_dev, double *evecs_dev, hsim_info *info);
 
+/* A batch of independent HSIM solves (one per mesh, each with its own
+ * hierarchy), run concurrently: `streams` worker threads (<= 0: 8, at most
+ * nmesh), each with its own CUDA stream on the context's device, take the
+ * meshes in order; every solve is the hsim_solve path.  The paper has no
+ * batched form; many small meshes only fill the GPU when their solves
+ * overlap.
+ *   hiers, S_vals, M_diags, p, evals, evecs: nmesh entries each, as for
+ *       hsim_solve (device pointers on the context's device; a hierarchy may
+ *       appear once, since it holds its solve's workspace)
+ *   opts       applied to every mesh (NULL: each hierarchy's options)
+ *   infos      optional, nmesh host reports
+ * Work already queued on the context's stream (e.g. the assembly of S, M)
+ * completes before the batch starts; the call returns when every solve is
+ * done.  On error the status of the first failing mesh is returned, its
+ * index in hsim_last_error(); meshes not yet started are skipped and the
+ * outputs of the others are undefined. */
+hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers, const double *const *S_vals,
+                               const double *const *M_diags, const int *p, double tol, const hsim_options *opts,
+                               double *const *evals, double *const *evecs, hsim_info *infos, int streams);
+
 /* Shape gradient of a loss of the eigenvalues (first-order perturbation of
  * S Phi = lambda M Phi for M-normalised eigenvectors, differentiated through
  * the cotan stiffness and lumped mass of Sec. 3.1, eq. massStiffMatrices):

@@ -23,7 +23,7 @@ from ._lib import HSIM_FP64, HSIM_MIXED, HsimError, Info, Options, check, defaul
 __all__ = ["Context", "Hierarchy", "assemble", "solve", "spmm", "gram", "gemm_update", "gram_tc",
            "gemm_update_tc", "ritz",
            "galerkin", "shifted_solve", "check_symbolic", "default_options", "HsimError",
-           "HSIM_FP64", "HSIM_MIXED", "kernel_launches"]
+           "HSIM_FP64", "HSIM_MIXED", "kernel_launches", "solve_batched", "eig_grad", "eigenvalues"]
 
 
 def _torch():
@@ -188,6 +188,28 @@ def solve(ctx: Context, hier: Hierarchy, S_val, M_diag, p: int, tol: float,
     check(lib().hsim_solve(ctx.handle, hier.handle, ptr(S_val), ptr(M_diag), p, float(tol), ctypes.byref(o),
                            ptr(lam), ptr(vecs), ctypes.byref(info)))
     return lam, vecs.t(), info.to_dict()
+
+
+def solve_batched(ctx: Context, hiers, S_vals, M_diags, p, tol: float, options: Options | None = None,
+                  streams: int = 0):
+    """Independent HSIM solves of several meshes, run concurrently on
+    `streams` CUDA streams; returns a list of (eigenvalues, eigenvectors, info)."""
+    torch = _torch()
+    dev = f"cuda:{ctx.device}"
+    k = len(hiers)
+    ps = [int(x) for x in (p if hasattr(p, "__len__") else [p] * k)]
+    if not (len(S_vals) == len(M_diags) == len(ps) == k):
+        raise ValueError("one S, M and p per hierarchy")
+    lams = [torch.empty(ps[i], dtype=torch.float64, device=dev) for i in range(k)]
+    vecs = [torch.empty((ps[i], hiers[i].n), dtype=torch.float64, device=dev) for i in range(k)]
+    arr = lambda xs: (ctypes.c_void_p * max(k, 1))(*[ptr(x) if not isinstance(x, Hierarchy) else x.handle.value
+                                                     for x in xs])
+    infos = (Info * max(k, 1))()
+    pa = (ctypes.c_int * max(k, 1))(*ps)
+    check(lib().hsim_solve_batched(ctx.handle, k, arr(hiers), arr(S_vals), arr(M_diags), pa, float(tol),
+                                   ctypes.byref(options) if options is not None else None, arr(lams), arr(vecs),
+                                   infos, int(streams)))
+    return [(lams[i], vecs[i].t(), infos[i].to_dict()) for i in range(k)]
 
 
 def eig_grad(ctx: Context, V, F, evals, evecs, dloss_dlambda):

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <functional>
 #include <cmath>
@@ -18,7 +19,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.h"
@@ -36,12 +40,11 @@ thread_local std::string g_last_error;
 
 // HSIM_TRACE=1 prints one line per subspace iteration to stderr.
 bool trace_on() {
-    static int on = -1;
-    if (on < 0) {
+    static const bool on = [] {
         const char *e = std::getenv("HSIM_TRACE");
-        on = (e && *e && *e != '0') ? 1 : 0;
-    }
-    return on == 1;
+        return e && *e && *e != '0';
+    }();
+    return on;
 }
 
 hsim_status guard(const std::function<void()> &f) {
@@ -912,6 +915,100 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *h, const double *S_val, const d
         DeviceGuard dg(ctx->device);
         hsim_options o = checked(opts ? opts : &h->opts);
         run_solve(ctx, h, S_val, M_diag, p, tol, o, evals, evecs, info);
+    });
+}
+
+hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers, const double *const *S_vals,
+                               const double *const *M_diags, const int *p, double tol, const hsim_options *opts,
+                               double *const *evals, double *const *evecs, hsim_info *infos, int streams) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx, "NULL context");
+        HSIM_CHECK_ARG(nmesh >= 0 && tol > 0, "bad nmesh or tol");
+        if (nmesh == 0) return;
+        HSIM_CHECK_ARG(hiers && S_vals && M_diags && p && evals && evecs, "NULL argument");
+        std::set<const hsim_hier *> seen;
+        for (int i = 0; i < nmesh; ++i) {
+            HSIM_CHECK_ARG(hiers[i] && S_vals[i] && M_diags[i] && evals[i] && evecs[i],
+                           "NULL argument for mesh " + std::to_string(i));
+            HSIM_CHECK_ARG(p[i] >= 1 && p[i] <= hiers[i]->n, "bad p for mesh " + std::to_string(i));
+            HSIM_CHECK_ARG(hiers[i]->device == ctx->device, "mesh " + std::to_string(i) + " lives on another device");
+            // a hierarchy holds the workspace of its solve: one solve per hierarchy at a time
+            HSIM_CHECK_ARG(seen.insert(hiers[i]).second, "hierarchy listed twice (mesh " + std::to_string(i) + ")");
+        }
+        DeviceGuard dg(ctx->device);
+        const int W = std::max(1, std::min(nmesh, streams > 0 ? streams : 8));
+        // inputs produced on the caller's stream are complete before any worker starts
+        cudaEvent_t ready;
+        HSIM_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+        std::vector<std::unique_ptr<hsim_ctx>> wctx;
+        auto cleanup = [&] {
+            for (auto &c : wctx)
+                if (c && c->stream) {
+                    cudaStreamSynchronize(c->stream);
+                    cudaStreamDestroy(c->stream);
+                    c->stream = nullptr;
+                }
+            cudaEventDestroy(ready);
+        };
+        try {
+            HSIM_CUDA(cudaEventRecord(ready, ctx->stream));
+            for (int w = 0; w < W; ++w) {
+                auto c = std::make_unique<hsim_ctx>();
+                c->device = ctx->device;
+                HSIM_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+                c->flags.alloc(16);
+                c->hflags.assign(16, 0);
+                c->scratch_u64.alloc(4);
+                HSIM_CUDA(cudaStreamWaitEvent(c->stream, ready, 0));
+                wctx.push_back(std::move(c));
+            }
+        } catch (...) {
+            cleanup();
+            throw;
+        }
+        // workers take meshes in order from a shared counter; the first error
+        // stops the others before their next mesh
+        std::atomic<int> next{0};
+        std::atomic<bool> stop{false};
+        std::mutex emu;
+        hsim_status status = HSIM_OK;
+        std::string message;
+        auto record = [&](hsim_status st, int i, const std::string &m) {
+            std::lock_guard<std::mutex> lock(emu);
+            if (status == HSIM_OK) {
+                status = st;
+                message = "mesh " + std::to_string(i) + ": " + m;
+            }
+            stop = true;
+        };
+        std::vector<std::thread> pool;
+        for (int w = 0; w < W; ++w) {
+            pool.emplace_back([&, w] {
+                if (cudaSetDevice(ctx->device) != cudaSuccess) {
+                    record(HSIM_E_CUDA, -1, "cudaSetDevice failed in a worker");
+                    return;
+                }
+                for (;;) {
+                    if (stop) break;
+                    const int i = next.fetch_add(1);
+                    if (i >= nmesh) break;
+                    try {
+                        hsim_options o = checked(opts ? opts : &hiers[i]->opts);
+                        run_solve(wctx[w].get(), hiers[i], S_vals[i], M_diags[i], p[i], tol, o, evals[i], evecs[i],
+                                  infos ? &infos[i] : nullptr);
+                    } catch (const Error &e) {
+                        record(e.status, i, e.what());
+                    } catch (const std::bad_alloc &) {
+                        record(HSIM_E_NOMEM, i, "host allocation failed");
+                    } catch (const std::exception &e) {
+                        record(HSIM_E_INTERNAL, i, e.what());
+                    }
+                }
+            });
+        }
+        for (auto &t : pool) t.join();
+        cleanup();
+        if (status != HSIM_OK) fail(status, message);
     });
 }
 

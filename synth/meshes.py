@@ -154,6 +154,53 @@ def icosphere(subdiv: int) -> Mesh:
     return Mesh(V=V, F=F.astype(np.int32), name=f"icosphere_{subdiv}")
 
 
+def geodesic_icosphere(nu: int) -> Mesh:
+    """Unit sphere from the icosahedron with every face cut into nu^2
+    triangles (frequency nu, 10 nu^2 + 2 vertices), points projected radially.
+    Lattice points shared by neighbouring faces (edges, corners) are merged
+    on their coordinates rounded to 1e-9."""
+    V0, F0 = _icosahedron()
+    # lattice (i, j), i + j <= nu, of every face: a + i/nu (b - a) + j/nu (c - a)
+    ii, jj = np.meshgrid(np.arange(nu + 1), np.arange(nu + 1), indexing="ij")
+    keep = (ii + jj) <= nu
+    ii, jj = ii[keep], jj[keep]
+    lid = -np.ones((nu + 1, nu + 1), dtype=np.int64)
+    lid[ii, jj] = np.arange(ii.size)
+    a, b, c = V0[F0[:, 0]], V0[F0[:, 1]], V0[F0[:, 2]]
+    w0 = (nu - ii - jj)[None, :, None] / nu
+    P = w0 * a[:, None, :] + (ii / nu)[None, :, None] * b[:, None, :] + (jj / nu)[None, :, None] * c[:, None, :]
+    P = P.reshape(-1, 3)
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    key = np.round(P * 1e9).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    # keep vertices in the order of first appearance
+    order = np.argsort(first)
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.size)
+    vid = rank[inv.reshape(-1)]
+    V = P[first[order]]
+    # triangles of one face in lattice ids, then offset per face
+    ti, tj = np.meshgrid(np.arange(nu), np.arange(nu), indexing="ij")
+    up = (ti + tj) < nu
+    dn = (ti + tj + 1) < nu
+    t_up = np.stack([lid[ti[up], tj[up]], lid[ti[up] + 1, tj[up]], lid[ti[up], tj[up] + 1]], 1)
+    t_dn = np.stack([lid[ti[dn] + 1, tj[dn]], lid[ti[dn] + 1, tj[dn] + 1], lid[ti[dn], tj[dn] + 1]], 1)
+    tri = np.concatenate([t_up, t_dn], 0)
+    npf = ii.size
+    F = (tri[None, :, :] + (np.arange(F0.shape[0]) * npf)[:, None, None]).reshape(-1, 3)
+    F = vid[F].astype(np.int32)
+    return Mesh(V=V, F=F, name=f"geodesic_icosphere_{nu}", meta={"nu": nu})
+
+
+def displaced_geodesic_icosphere(nu: int, seed: int, amplitude: float = 0.05) -> Mesh:
+    """geodesic_icosphere(nu) with the radial noise of displaced_icosphere."""
+    base = geodesic_icosphere(nu)
+    f = smooth_sphere_field(base.V, seed)
+    V = base.V * (1.0 + amplitude * f)[:, None]
+    return Mesh(V=V, F=base.F, name=f"displaced_geodesic_icosphere_{nu}_s{seed}",
+                meta={"nu": nu, "seed": seed, "amplitude": amplitude})
+
+
 def _legendre_table(lmax: int, x: np.ndarray) -> dict:
     """Associated Legendre functions P_l^m(x), 0 <= m <= l <= lmax (no phase)."""
     P = {}

@@ -61,3 +61,29 @@ def make_workload(name: str):
     m = w.mesh()
     return w, m, w.start_vertex(m.n)
 
+
+
+def batch(count: int = 64, seed: int = 4, lo: int = 5000, hi: int = 80000):
+    """A batch of independent meshes for the batched solve: sizes log-uniform
+    in [lo, hi] (seeded), even entries displaced geodesic icospheres (frequency
+    nu, 10 nu^2 + 2 vertices, nearest to the drawn size), odd entries bumpy tori
+    with near-square cells (nu : nv ~ R : r).  Returns a list of
+    (mesh, start_vertex); every mesh is solved with p = 50, T = 2, tol 1e-5."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), count))
+    out = []
+    for i, N in enumerate(sizes):
+        ms = 100 * seed + i
+        if i % 2 == 0:
+            nu = max(2, int(round(np.sqrt((N - 2.0) / 10.0))))
+            mesh = meshes.displaced_geodesic_icosphere(nu, ms)
+        else:
+            nu = max(8, int(round(np.sqrt(N / 0.3))))
+            nv = max(8, int(round(N / nu)))
+            mesh = meshes.bumpy_torus(nu, nv, ms)
+        start = int(np.random.default_rng(1000 + ms).integers(0, mesh.n))
+        out.append((mesh, start))
+    return out
+
+
+BATCH_P, BATCH_LEVELS, BATCH_TOL = 50, 2, 1e-5
