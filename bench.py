@@ -446,17 +446,20 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
     sim_levels = range(len(sizes) - 1)
     n_products = sum(iters[t] for t in sim_levels)
     kernels = {}
-    # Ritz: two-sided Jacobi, 6 q^3 FP64 flops per sweep (rotations applied to
-    # the two rows and columns of A and to V, A symmetric)
-    sweeps = avg("ritz_sweeps")
+    # Ritz eigensolver: Householder tridiagonalisation (4/3 q^3 FP64 flops) and
+    # back transformation of the q eigenvectors (2 q^3), per call
+    calls = avg("ritz_calls")
     ms_ritz = phases["ritz"]
-    jac = 6.0 * q ** 3 * sweeps / (ms_ritz * 1e-3) / 1e12 if ms_ritz > 0 else 0.0
-    kernels["ritz"] = {"kernel": "k_jacobi_slots (cyclic parallel Jacobi, FP64)", "bound": "alu",
+    rflops = (4.0 / 3.0 + 2.0) * q ** 3 * calls
+    jac = rflops / (ms_ritz * 1e-3) / 1e12 if ms_ritz > 0 else 0.0
+    kernels["ritz"] = {"kernel": "k_tridiag + k_tri_* (Householder tridiagonalisation, bisection, inverse "
+                                 "iteration, back transformation; FP64)", "bound": "alu",
                        "achieved": jac, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": jac / FP64_PEAK_TFLOPS,
                        "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s; a DFMA probe measured 1.19)",
-                       "traffic": None, "flops_per_sweep": 6.0 * q ** 3, "sweeps_per_step": sweeps,
-                       "launches_per_step": sweeps, "note": "time includes the Cholesky of M_bar and the two "
-                       "triangular transforms of the Rayleigh-Ritz step"}
+                       "traffic": None, "flops_per_call": (4.0 / 3.0 + 2.0) * q ** 3, "calls_per_step": calls,
+                       "launches_per_step": 5 * calls, "note": "time includes the LDL^T of M_bar and the "
+                       "triangular transforms of the Rayleigh-Ritz step; the tridiagonalisation takes two grid "
+                       "barriers per column"}
     # supernodal triangular solves: 4 nnz(L) flops per right-hand side
     sflops = avg("solve_flops")
     ms_solve = phases["solve"]

@@ -321,11 +321,12 @@ void apply_S(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int l
 }
 
 // Rayleigh-Ritz on q x q reduced matrices; throws on failure
+// lowest m (<= 0: all q) Ritz pairs of the q x q problem
 void ritz_step(hsim_ctx *ctx, hsim_hier *H, int q, const double *Sbar, const double *Mbar, double *lam, double *X,
-               int ldx, int *sweeps) {
+               int ldx, int *sweeps, int m = 0) {
     H->ritz_work.reserve(k::ritz_work_size(q));
     int rc = k::ritz(ctx->stream, q, Sbar, q, Mbar, q, lam, X, ldx, H->ritz_work.p, sweeps, ctx->flags.p,
-                     ctx->hflags.data());
+                     ctx->hflags.data(), m);
     if (rc != 0) fail(HSIM_E_NOT_SPD, "reduced mass matrix is not positive definite (q = " + std::to_string(q) + ")");
 }
 
@@ -391,7 +392,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     H->coarseX.reserve((size_t)nc * nc);
     H->coarseLam.reserve(nc);
     int sweeps = 0;
-    ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps);
+    ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps, q);
     inf.coarse_sweeps = sweeps;
     inf.ms_coarse = tm.stop();
     std::vector<double> lam_h(q);

@@ -4,9 +4,8 @@
 //   col_dots    column M-norms, residual sums of eq. conv2
 //   ritz        S_bar Phi_bar = M_bar Phi_bar Lambda_bar: M_bar = L D L^T
 //               (front kernels on one dense front), A = C^-1 S_bar C^-T with
-//               C = L D^1/2, cyclic parallel Jacobi on A (one cooperative
-//               launch per sweep, round-robin pairing), Phi_bar = C^-T V,
-//               eigenpairs sorted ascending.
+//               C = L D^1/2, the lowest eigenpairs of A by the tridiagonal
+//               eigensolver of k_tridiag.cu, Phi_bar = C^-T V, ascending.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -344,170 +343,6 @@ __global__ void k_jacobi_sweep(int k, int m, double *A, double *A2, double *V, d
     if (local_rot) atomicAdd(rotations, local_rot);
 }
 
-// ---- cyclic parallel Jacobi in slot order ------------------------------------
-// The m x m matrix (m even; an odd k gets one zero row/column that never
-// rotates) is stored in tournament-slot order: the pairs of a round are the
-// adjacent slots (2P, 2P+1), so every rotation acts on whole 2 x 2 blocks.
-// After a round the players move along the circle schedule (slot 0 fixed,
-// the other m - 1 slots advance one place on the cycle top[1..h-1],
-// bottom[h-1..0]); every pair meets once in m - 1 rounds and the slots are
-// back in their original order after a sweep.  One cooperative launch runs a
-// sweep: per round every CTA takes 16 x 16-pair tiles of A (upper triangle,
-// written with its mirror image, so A stays exactly symmetric) or 32-row x
-// 16-pair tiles of V, computes the rotations of its pairs into shared memory
-// from the diagonal blocks, and writes the rotated blocks to their next-round
-// slots in the other buffer; one grid barrier separates the rounds.
-constexpr int kJT = 16;  // pairs per tile side
-
-__device__ __forceinline__ int jslot_next(int s, int h) {
-    if (h <= 1 || s == 0) return s;
-    int t = s >> 1;
-    if ((s & 1) == 0) return (t <= h - 2) ? 2 * (t + 1) : 2 * (h - 1) + 1;
-    return (t >= 1) ? 2 * (t - 1) + 1 : 2;
-}
-
-// rotation J = [[c, s], [-s, c]] that diagonalises the 2 x 2 block of pair P
-// (t = tan of the angle, 0 when the pair is left alone)
-__device__ __forceinline__ void jrotation(const double *A, int lda, int P, double tol, double abs_tol, double &c,
-                                          double &sn, double &t) {
-    double app = A[(size_t)(2 * P) * lda + 2 * P], aqq = A[(size_t)(2 * P + 1) * lda + 2 * P + 1];
-    double apq = A[(size_t)(2 * P) * lda + 2 * P + 1];
-    c = 1.0;
-    sn = 0.0;
-    t = 0.0;
-    if (fabs(apq) > abs_tol && fabs(apq) > tol * sqrt(fabs(app) * fabs(aqq))) {
-        double theta = (aqq - app) / (2.0 * apq);
-        t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + hypot(theta, 1.0));
-        c = 1.0 / sqrt(1.0 + t * t);
-        sn = t * c;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_jacobi_slots(int k, int m, double *A, double *A2, double *V, double *V2,
-                                                      double tol, double abs_tol, unsigned long long *rotations) {
-    cg::grid_group grid = cg::this_grid();
-    __shared__ double rc[2][kJT], rs[2][kJT], rt[2][kJT];
-    const int h = m / 2;
-    const int nt = (h + kJT - 1) / kJT;
-    const int nA = nt * (nt + 1) / 2;
-    const int nV = ((k + 31) / 32) * nt;
-    const int tid = threadIdx.x;
-    unsigned long long local_rot = 0;
-    for (int r = 0; r < m - 1; ++r) {
-        for (int task = blockIdx.x; task < nA + nV; task += gridDim.x) {
-            if (task < nA) {
-                // upper-triangle tile (ti <= tj) of pair blocks
-                int ti = 0, rem = task;
-                while (rem >= nt - ti) {
-                    rem -= nt - ti;
-                    ++ti;
-                }
-                int tj = ti + rem;
-                if (tid < 2 * kJT) {
-                    int side = tid / kJT, P = (side ? tj : ti) * kJT + tid % kJT;
-                    double c = 1.0, sn = 0.0, t = 0.0;
-                    if (P < h) {
-                        jrotation(A, m, P, tol, abs_tol, c, sn, t);
-                        if (side == 0 && ti == tj && t != 0.0) ++local_rot;
-                    }
-                    rc[side][tid % kJT] = c;
-                    rs[side][tid % kJT] = sn;
-                    rt[side][tid % kJT] = t;
-                }
-                __syncthreads();
-                int li = tid / kJT, lj = tid % kJT;
-                int I = ti * kJT + li, J = tj * kJT + lj;
-                if (I < h && J < h && I <= J) {
-                    const double *a0 = A + (size_t)(2 * I) * m + 2 * J;
-                    const double *a1 = a0 + m;
-                    double b00, b01, b10, b11;
-                    if (I == J) {
-                        double t = rt[0][li];
-                        b00 = a0[0] - t * a0[1];
-                        b11 = a1[1] + t * a0[1];
-                        b01 = 0.0;
-                        b10 = 0.0;
-                        if (t == 0.0) {
-                            b00 = a0[0];
-                            b01 = a0[1];
-                            b10 = a1[0];
-                            b11 = a1[1];
-                        }
-                    } else {
-                        double cI = rc[0][li], sI = rs[0][li], cJ = rc[1][lj], sJ = rs[1][lj];
-                        double x00 = a0[0] * cJ - a0[1] * sJ, x01 = a0[0] * sJ + a0[1] * cJ;
-                        double x10 = a1[0] * cJ - a1[1] * sJ, x11 = a1[0] * sJ + a1[1] * cJ;
-                        b00 = cI * x00 - sI * x10;
-                        b01 = cI * x01 - sI * x11;
-                        b10 = sI * x00 + cI * x10;
-                        b11 = sI * x01 + cI * x11;
-                    }
-                    int r0 = jslot_next(2 * I, h), r1 = jslot_next(2 * I + 1, h);
-                    int c0 = jslot_next(2 * J, h), c1 = jslot_next(2 * J + 1, h);
-                    A2[(size_t)r0 * m + c0] = b00;
-                    A2[(size_t)r0 * m + c1] = b01;
-                    A2[(size_t)r1 * m + c0] = b10;
-                    A2[(size_t)r1 * m + c1] = b11;
-                    if (I != J) {
-                        A2[(size_t)c0 * m + r0] = b00;
-                        A2[(size_t)c1 * m + r0] = b01;
-                        A2[(size_t)c0 * m + r1] = b10;
-                        A2[(size_t)c1 * m + r1] = b11;
-                    }
-                }
-            } else {
-                // V tile: rows [32 rc0, +32), pairs [16 tj, +16)
-                int vt = task - nA;
-                int rch = vt / nt, tj = vt % nt;
-                if (tid < kJT) {
-                    int P = tj * kJT + tid;
-                    double c = 1.0, sn = 0.0, t = 0.0;
-                    if (P < h) jrotation(A, m, P, tol, abs_tol, c, sn, t);
-                    rc[1][tid] = c;
-                    rs[1][tid] = sn;
-                }
-                __syncthreads();
-                for (int item = tid; item < 32 * kJT; item += blockDim.x) {
-                    int row = rch * 32 + item / kJT, lj = item % kJT, J = tj * kJT + lj;
-                    if (row < k && J < h) {
-                        const double *v = V + (size_t)row * m + 2 * J;
-                        double cJ = rc[1][lj], sJ = rs[1][lj];
-                        double v0 = v[0], v1 = v[1];
-                        V2[(size_t)row * m + jslot_next(2 * J, h)] = v0 * cJ - v1 * sJ;
-                        V2[(size_t)row * m + jslot_next(2 * J + 1, h)] = v0 * sJ + v1 * cJ;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        grid.sync();
-        double *t = A;
-        A = A2;
-        A2 = t;
-        t = V;
-        V = V2;
-        V2 = t;
-    }
-    if (local_rot) atomicAdd(rotations, local_rot);
-}
-
-// number of pairs i < j < k that the next sweep would rotate
-__global__ void k_offdiag_count(int k, const double *__restrict__ A, int lda, double tol, double abs_tol,
-                                unsigned long long *count) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long c = 0;
-    if (idx < (int64_t)k * k) {
-        int i = (int)(idx / k), j = (int)(idx % k);
-        if (i < j) {
-            double apq = A[(size_t)i * lda + j];
-            double app = A[(size_t)i * lda + i], aqq = A[(size_t)j * lda + j];
-            c = (fabs(apq) > abs_tol && fabs(apq) > tol * sqrt(fabs(app) * fabs(aqq))) ? 1 : 0;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
-}
-
 // rank of each eigenvalue in ascending order (ties by index)
 __global__ void k_rank(int k, const double *__restrict__ A, int lda, int *__restrict__ rank,
                        double *__restrict__ evals_sorted) {
@@ -639,31 +474,28 @@ HSIM_DENSE_INSTANTIATE(float)
 HSIM_DENSE_INSTANTIATE(double)
 
 size_t ritz_work_size(int k) {
-    const size_t m = (size_t)k + (k & 1);
-    return 2 * (size_t)k * k + 2 * m * m + 2 * (size_t)k * m + 4 * (size_t)k + 64;
+    return 3 * (size_t)k * k + 2 * (size_t)k + 64 + sym_eig_work_size(k, k);
 }
 
-// A (m x m, ld m) = T (k x k, ld k) padded with zeros; V (k x m, ld m) = [I 0]
-__global__ void k_jacobi_init(int k, int m, const double *__restrict__ T, double *__restrict__ A,
-                              double *__restrict__ V) {
+// X[i, 0:cols] *= 1/sqrt(d[i])
+__global__ void k_rows_rsqrt(int rows, int cols, const double *__restrict__ d, double *__restrict__ X, int ldx) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)m * m) return;
-    int i = (int)(idx / m), j = (int)(idx % m);
-    A[idx] = (i < k && j < k) ? T[(size_t)i * k + j] : 0.0;
-    if (i < k) V[(size_t)i * m + j] = (i == j) ? 1.0 : 0.0;
+    if (idx >= (int64_t)rows * cols) return;
+    int i = (int)(idx / cols), j = (int)(idx % cols);
+    X[(size_t)i * ldx + j] *= rsqrt(d[i]);
 }
 
 int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals, double *X,
-         int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host) {
-    // work layout: F (k*k) | W (k*k) | A (m*m) | A2 (m*m) | V (k*m) | V2 (k*m) | d (k) | misc
-    const int m = k + (k & 1);
-    const size_t kk = (size_t)k * k, mm2 = (size_t)m * m, km = (size_t)k * m;
-    double *F = work, *W = work + kk, *A = work + 2 * kk, *A2 = A + mm2, *V = A2 + mm2, *V2 = V + km;
-    double *d = V2 + km;
-    unsigned long long *rot = reinterpret_cast<unsigned long long *>(d + k + 2);
+         int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host, int m) {
+    // work layout: F (k*k) | W (k*k) | T (k*k) | d (k) | eigensolver work
+    if (m <= 0 || m > k) m = k;
+    const size_t kk = (size_t)k * k;
+    double *F = work, *W = work + kk, *T = work + 2 * kk;
+    double *d = T + kk;
+    double *ework = d + 2 * (size_t)k + 32;
     DenseFront &df = dense_front(k, s);
     const int *node = df.node.p;
-    // F = M_bar (symmetric: row-major == column-major)
+    // F = M_bar (symmetric: row-major == column-major); M_bar = L D L^T = C C^T
     copy_matrix(s, k, k, Mbar, ldm, F, k);
     HSIM_CUDA(cudaMemsetAsync(flag_dev, 0, 4 * sizeof(int), s));
     const int steps = (k + kPanel - 1) / kPanel;
@@ -677,7 +509,7 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     HSIM_CUDA(cudaMemcpyAsync(flag_host, flag_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaStreamSynchronize(s));
     if (flag_host[0] != 0 || flag_host[2] != 0) return 1;  // not positive definite
-    // W = C^-1 S_bar = D^-1/2 L^-1 S_bar; T = C^-1 W^T (in A2, k x k)
+    // A = C^-1 S_bar C^-T: W = D^-1/2 L^-1 S_bar, T = D^-1/2 L^-1 W^T
     copy_matrix(s, k, k, Sbar, lds, W, k);
     auto forward = [&](double *Y) {
         for (int st = 0; st < steps; ++st) {
@@ -690,7 +522,6 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
         HSIM_LAUNCHED();
     };
     forward(W);
-    double *T = A2;
     dim3 tg(cdiv(k, 32), cdiv(k, 32)), tb(32, 8);
     k_transpose<<<tg, tb, 0, s>>>(k, W, k, T, k);
     HSIM_LAUNCHED();
@@ -698,58 +529,18 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     // symmetrise against rounding: T = (T + T^T)/2
     k_symmetrize<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, T, k);
     HSIM_LAUNCHED();
-    k_jacobi_init<<<cdiv((int64_t)m * m, 256), 256, 0, s>>>(k, m, T, A, V);
-    HSIM_LAUNCHED();
-    // Jacobi sweeps (one cooperative launch each) until no off-diagonal pair
-    // is left above the rotation threshold
-    int blocks_per_sm = 0;
-    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_jacobi_slots, 256, 0));
-    const int nt = (m / 2 + kJT - 1) / kJT;
-    const int tasks = nt * (nt + 1) / 2 + ((k + 31) / 32) * nt;
-    int grid = std::max(1, std::min(blocks_per_sm * sm_count(), tasks));
-    double tol = 1e-15, abs_tol = 1e-300;
-    int sw = 0;
-    unsigned long long hrot = 0;
-    double *pA = A, *pA2 = A2, *pV = V, *pV2 = V2;
-    auto count_offdiag = [&]() {
-        HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
-        k_offdiag_count<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, pA, m, tol, abs_tol, rot);
-        HSIM_LAUNCHED();
-        HSIM_CUDA(cudaMemcpyAsync(&hrot, rot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        HSIM_CUDA(cudaStreamSynchronize(s));
-    };
-    count_offdiag();
-    while (hrot != 0 && sw < 40) {
-        HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
-        int kk_ = k, mm_ = m;
-        void *args[] = {&kk_, &mm_, &pA, &pA2, &pV, &pV2, &tol, &abs_tol, &rot};
-        HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_jacobi_slots, dim3(grid), dim3(256), args, 0, s));
-        HSIM_LAUNCHED();
-        // after m-1 rounds the newest data is in pA if m-1 is even, else pA2
-        if ((m - 1) % 2 == 1) {
-            std::swap(pA, pA2);
-            std::swap(pV, pV2);
-        }
-        ++sw;
-        count_offdiag();
-    }
-    if (sweeps) *sweeps = sw;
-    // X = C^-T V = L^-T D^-1/2 V (V copied to k x k in pA2), then columns sorted by eigenvalue
-    int *rk = reinterpret_cast<int *>(W);
-    k_rank<<<cdiv(k, 128), 128, 0, s>>>(k, pA, m, rk, evals);
-    HSIM_LAUNCHED();
-    double *Vk = pA2;
-    copy_matrix(s, k, k, pV, m, Vk, k);
-    k_row_scale_sqrt<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, d, Vk, k, 0);
+    // lowest m eigenpairs of A (ascending), eigenvectors into X (k x m)
+    sym_eig(s, k, m, T, evals, X, ldx, ework);
+    if (sweeps) *sweeps = 0;
+    // X = C^-T V = L^-T D^-1/2 V
+    k_rows_rsqrt<<<cdiv((int64_t)k * m, 256), 256, 0, s>>>(k, m, d, X, ldx);
     HSIM_LAUNCHED();
     for (int st = steps - 1; st >= 0; --st) {
         int k0 = st * kPanel;
         int kb = std::min(kPanel, k - k0);
-        solve_bwd_upd(s, df.fd, node, 1, k0, k - k0 - kb, F, k, Vk, k);
-        solve_bwd_tri(s, df.fd, node, 1, k0, F, k, Vk, k);
+        solve_bwd_upd(s, df.fd, node, 1, k0, k - k0 - kb, F, m, X, ldx);
+        solve_bwd_tri(s, df.fd, node, 1, k0, F, m, X, ldx);
     }
-    k_permute_cols<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, rk, Vk, k, X, ldx);
-    HSIM_LAUNCHED();
     return 0;
 }
 

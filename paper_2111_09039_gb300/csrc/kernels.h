@@ -98,10 +98,17 @@ void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, T *X, int l
 template <typename T>
 void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *MP, int ldm,
                    const double *lam, const double *dinv, double *out);
-// dense symmetric generalised eigensolver (Cholesky + Jacobi), k x k
-// returns 0 ok, 1 not SPD; sweeps via *sweeps
+// dense symmetric generalised eigensolver, k x k: LDL^T of M_bar, the lowest
+// m (<= 0: all k) pairs of C^-1 S_bar C^-T by sym_eig, X (k x m) = C^-T V;
+// returns 0 ok, 1 not SPD; *sweeps = 0 (kept for the Jacobi variant's report)
 int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals,
-         double *X, int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host);
+         double *X, int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host, int m = 0);
+// ---- tridiagonal eigensolver (k_tridiag.cu) ----------------------------------
+// lowest m eigenpairs of the symmetric n x n A (row-major, ld n, destroyed):
+// evals ascending (m), X (n x m, ld ldx) orthonormal eigenvectors; work of
+// sym_eig_work_size(n, m) doubles; synchronises the stream
+size_t sym_eig_work_size(int n, int m);
+void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, int ldx, double *work);
 size_t ritz_work_size(int k);
 
 // ---- fronts (k_front.cu) ----------------------------------------------------

@@ -125,9 +125,19 @@ def test_ritz_degenerate_and_diagonal(hs, ctx):
     Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
     S = Q @ np.diag(d) @ Q.T
     lam, X, _ = hs.ritz(ctx, dev(S), dev(np.eye(k)))
-    np.testing.assert_allclose(lam.cpu().numpy(), d, atol=1e-12)
-    lam2, X2, sw = hs.ritz(ctx, dev(np.diag(d[::-1].copy())), dev(np.eye(k)))
-    np.testing.assert_allclose(lam2.cpu().numpy(), d, atol=0)
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    np.testing.assert_allclose(lam, d, atol=1e-12)
+    # eigenvectors inside the clusters: orthonormal and exact for S
+    np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(S @ X, X * lam[None, :], atol=1e-12)
+    Sd = np.diag(d[::-1].copy())
+    lam2, X2, sw = hs.ritz(ctx, dev(Sd), dev(np.eye(k)))
+    lam2, X2 = lam2.cpu().numpy(), X2.cpu().numpy()
+    # already diagonal: eigenvalues to eps ||S||, eigenvectors a permutation
+    # within each cluster (orthonormal, exact for S)
+    np.testing.assert_allclose(lam2, d, atol=4 * np.finfo(float).eps * d.max())
+    np.testing.assert_allclose(X2.T @ X2, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(Sd @ X2, X2 * lam2[None, :], atol=1e-12)
 
 
 def test_ritz_rejects_indefinite_mass(hs, ctx):
