@@ -144,6 +144,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--sample-cols", type=int, default=8)
     ap.add_argument("--max-iters", type=int, default=100)
+    ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz"],
                     help="time one step-level kernel on random data instead of the solve (profiling)")
@@ -181,12 +182,13 @@ def main():
     tol = args.tol if args.tol is not None else (1e-5 if w.tol < 1e-5 else w.tol)
     prec = hs.HSIM_FP64 if args.precision == "fp64" else hs.HSIM_MIXED
     ctx = hs.Context(local)
+    leaf = {"leaf_size": args.leaf_size} if args.leaf_size > 0 else {}
     t0 = time.perf_counter()
     if mesh.V is not None:
-        hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=p, levels=w.levels, start_vertex=start, precision=prec)
+        hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=p, levels=w.levels, start_vertex=start, precision=prec, **leaf)
         S, Md = hs.assemble(ctx, hier, V=torch.as_tensor(mesh.V, device=dev))
     else:
-        hier = hs.Hierarchy(ctx, mesh.F, L2=mesh.L2, p=p, levels=w.levels, start_vertex=start, precision=prec)
+        hier = hs.Hierarchy(ctx, mesh.F, L2=mesh.L2, p=p, levels=w.levels, start_vertex=start, precision=prec, **leaf)
         S, Md = hs.assemble(ctx, hier, L2=torch.as_tensor(mesh.L2, device=dev))
     torch.cuda.synchronize()
     hier_s = time.perf_counter() - t0

@@ -39,13 +39,14 @@ namespace {
 thread_local std::string g_last_error;
 
 // HSIM_TRACE=1 prints one line per subspace iteration to stderr.
-bool trace_on() {
-    static const bool on = [] {
+int trace_level() {
+    static const int lv = [] {
         const char *e = std::getenv("HSIM_TRACE");
-        return e && *e && *e != '0';
+        return (e && *e) ? std::atoi(e) : 0;
     }();
-    return on;
+    return lv;
 }
+bool trace_on() { return trace_level() > 0; }
 
 hsim_status guard(const std::function<void()> &f) {
     try {
@@ -249,6 +250,17 @@ template <typename T>
 void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T *X, int k, int ldx) {
     cudaStream_t s = ctx->stream;
     const FrontSymbolic &fs = L.fs;
+    // HSIM_TRACE=2: time of every tree height of the forward and backward sweeps
+    const bool detail = trace_level() >= 2;
+    std::vector<cudaEvent_t> ev;
+    auto mark = [&] {
+        if (!detail) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+    };
+    mark();
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
@@ -257,8 +269,10 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
             k::solve_fwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
             k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
         }
+        mark();
     }
     k::solve_diag(s, L.n, k, dpos, X, ldx);
+    mark();
     for (int h = fs.max_height; h >= 0; --h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         for (int kst = (int)L.step_cnt[h].size() - 1; kst >= 0; --kst) {
@@ -267,6 +281,25 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
             k::solve_bwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
             k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
         }
+        mark();
+    }
+    if (detail) {
+        cudaEventSynchronize(ev.back());
+        const int H = fs.max_height + 1;
+        std::string line = "[hsim] solve n=" + std::to_string(L.n) + " rhs=" + std::to_string(k) + " fwd/bwd ms per height:";
+        for (int h = 0; h < H; ++h) {
+            float a = 0, b = 0;
+            cudaEventElapsedTime(&a, ev[h], ev[h + 1]);
+            cudaEventElapsedTime(&b, ev[2 * H - h], ev[2 * H - h + 1]);
+            line += " h" + std::to_string(h) + "(" + std::to_string(L.hnodes_off[h + 1] - L.hnodes_off[h]) + " fronts, " +
+                    std::to_string(L.step_cnt[h].size()) + " steps) " + std::to_string(a).substr(0, 5) + "/" +
+                    std::to_string(b).substr(0, 5);
+        }
+        float dg = 0;
+        cudaEventElapsedTime(&dg, ev[H], ev[H + 1]);
+        line += " diag " + std::to_string(dg).substr(0, 5);
+        std::fprintf(stderr, "%s\n", line.c_str());
+        for (auto e : ev) cudaEventDestroy(e);
     }
 }
 

@@ -276,3 +276,46 @@ def test_gram_tc_exact_on_small_integers(hs, ctx):
     B = rng.integers(-1000, 1000, size=(3000, 24)).astype(np.float64)
     G = hs.gram_tc(ctx, dev(A), dev(B)).cpu().numpy()
     np.testing.assert_array_equal(G, A.T @ B)
+
+
+# ---- dense eigensolver edge cases (tridiagonal path) -------------------------
+@pytest.mark.parametrize("k", [1, 2, 3, 33])
+def test_ritz_tiny_sizes(hs, ctx, k):
+    S, M = _spd_pair(k, 10 + k)
+    lam, X, _ = hs.ritz(ctx, dev(S), dev(M))
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    ref = sla.eigh(S, M, eigvals_only=True)
+    np.testing.assert_allclose(lam, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(X.T @ M @ X, np.eye(k), atol=1e-11)
+    np.testing.assert_allclose(S @ X, M @ X * lam[None, :], atol=1e-10 * np.abs(ref).max())
+
+
+def test_ritz_grid_laplacian_multiplicities(hs, ctx):
+    # spectrum of a periodic 12 x 12 grid Laplacian: clusters of size 2, 4 and 8
+    N = 12
+    lam_g = np.sort([4 * (np.sin(np.pi * a / N) ** 2 + np.sin(np.pi * b / N) ** 2) for a in range(N) for b in range(N)])
+    k = N * N
+    Q, _ = np.linalg.qr(np.random.default_rng(7).standard_normal((k, k)))
+    S = Q @ np.diag(lam_g) @ Q.T
+    S = 0.5 * (S + S.T)
+    lam, X, _ = hs.ritz(ctx, dev(S), dev(np.eye(k)))
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    np.testing.assert_allclose(lam, lam_g, atol=1e-13 * lam_g.max())
+    np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(S @ X, X * lam[None, :], atol=1e-12 * lam_g.max())
+
+
+def test_ritz_graded_spectrum_and_large_size(hs, ctx):
+    # eigenvalues spread over 12 decades (a zero mode, then 1e-8 .. 1e4), k = 1000
+    k = 1000
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    ev = np.concatenate([[0.0], np.geomspace(1e-8, 1e4, k - 1)])
+    S = Q @ np.diag(ev) @ Q.T
+    S = 0.5 * (S + S.T)
+    lam, X, _ = hs.ritz(ctx, dev(S), dev(np.eye(k)))
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    # absolute accuracy eps ||S|| (the LAPACK-type bound for a dense symmetric eigensolve)
+    np.testing.assert_allclose(lam, ev, atol=200 * np.finfo(float).eps * ev.max())
+    np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-11)
+    np.testing.assert_allclose(S @ X, X * lam[None, :], atol=200 * np.finfo(float).eps * ev.max())
