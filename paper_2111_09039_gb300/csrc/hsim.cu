@@ -585,11 +585,10 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             inf.solve_flops += 4.0 * (double)L.fs.nnz_L * a * (o.inv_iters + ((refine && !mixed) ? 1 : 0));
             double ph[6];
             inf.ms_solve += (ph[0] = ts.stop());
-            // column scaling to unit M-norm, then S Psi, M Psi (Alg. 1, reduced matrices)
+            // S Psi, M Psi (Alg. 1, reduced matrices).  The columns of Psi are
+            // scaled to unit M-norm on the q x q side: with W = diag(M_bar)^-1/2,
+            // S_bar = W Psi^T S Psi W, M_bar = W Psi^T M Psi W and Phi = Psi (W Phi_bar)
             apply_M(ctx, H, tau, q, H->Psi.p, q, H->MP.p, q);
-            k::col_dots(s, n, q, H->Psi.p, q, H->MP.p, q, nullptr, H->colw.p);
-            k::scale_cols_rsqrt(s, n, q, H->colw.p, H->Psi.p, q);
-            k::scale_cols_rsqrt(s, n, q, H->colw.p, H->MP.p, q);
             apply_S(ctx, H, tau, q, H->Psi.p, q, H->SP.p, q);
             inf.ms_spmm += (ph[1] = ts.stop());
             if (mixed) {
@@ -609,12 +608,14 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 k::gram(s, n, q, q, H->Psi.p, q, H->SP.p, q, H->Sbar.p, q, true);
                 k::gram(s, n, q, q, H->Psi.p, q, H->MP.p, q, H->Mbar.p, q, true);
             }
-            if (mixed) inf.ms_gram += ph[2];
+            k::scale_sym_unit_diag(s, q, H->Sbar.p, H->Mbar.p, q, H->colw.p);
+            if (mixed) inf.ms_gram += (ph[2] += ts.stop());
             else inf.ms_gram += (ph[2] = ts.stop());
             // dense eigenproblem (Alg. 1): Ritz values ascending, M-orthonormal
             ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps);
             inf.ritz_calls += 1;
             inf.ritz_sweeps += sweeps;
+            k::diag_scale(s, q, q, H->colw.p, H->phibar.p, q, H->phibar.p, q);  // W Phi_bar
             inf.ms_ritz += (ph[3] = ts.stop());
             // update Phi = Psi Phi_bar (Alg. 1)
             if (mixed) {

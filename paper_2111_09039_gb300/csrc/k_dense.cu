@@ -473,6 +473,29 @@ void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *
 HSIM_DENSE_INSTANTIATE(float)
 HSIM_DENSE_INSTANTIATE(double)
 
+// w = diag(M)^-1/2, then S <- W S W and M <- W M W (q x q, ld lda)
+__global__ void k_unit_diag_w(int q, const double *__restrict__ M, int lda, double *__restrict__ w) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < q) w[i] = 1.0 / sqrt(M[(size_t)i * lda + i]);
+}
+__global__ void k_scale_sym2(int q, double *__restrict__ S, double *__restrict__ M, int lda,
+                             const double *__restrict__ w) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)q * q) return;
+    int i = (int)(idx / q), j = (int)(idx % q);
+    const double f = w[i] * w[j];
+    S[(size_t)i * lda + j] *= f;
+    M[(size_t)i * lda + j] *= f;
+}
+
+void scale_sym_unit_diag(cudaStream_t s, int q, double *S, double *M, int lda, double *w) {
+    if (q <= 0) return;
+    k_unit_diag_w<<<cdiv(q, 128), 128, 0, s>>>(q, M, lda, w);
+    HSIM_LAUNCHED();
+    k_scale_sym2<<<cdiv((int64_t)q * q, 256), 256, 0, s>>>(q, S, M, lda, w);
+    HSIM_LAUNCHED();
+}
+
 size_t ritz_work_size(int k) {
     return 3 * (size_t)k * k + 2 * (size_t)k + 64 + sym_eig_work_size(k, k);
 }

@@ -110,6 +110,8 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
 size_t sym_eig_work_size(int n, int m);
 void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, int ldx, double *work);
 size_t ritz_work_size(int k);
+// w = diag(M)^-1/2; S <- W S W, M <- W M W (q x q): unit-M-norm columns on the reduced side
+void scale_sym_unit_diag(cudaStream_t s, int q, double *S, double *M, int lda, double *w);
 
 // ---- fronts (k_front.cu) ----------------------------------------------------
 struct FrontDev {
