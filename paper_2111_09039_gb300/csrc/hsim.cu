@@ -636,8 +636,9 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             // convergence test (eq. conv2)
             apply_S(ctx, H, tau, q, H->Phi.p, q, H->SP.p, q);
             apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
-            k::residual_sums(s, n, q, H->SP.p, q, H->MP.p, q, H->lam.p, dinv, H->res_sums.p);
-            HSIM_CUDA(cudaMemcpyAsync(rs.data(), H->res_sums.p, 3 * q * sizeof(double), cudaMemcpyDeviceToHost, s));
+            // only the pairs i < p enter the test and the locking
+            k::residual_sums(s, n, p, H->SP.p, q, H->MP.p, q, H->lam.p, dinv, H->res_sums.p);
+            HSIM_CUDA(cudaMemcpyAsync(rs.data(), H->res_sums.p, 3 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->lam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaStreamSynchronize(s));
             if (mixed) k::ozaki_check(s);
@@ -649,10 +650,10 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                     break;
                 }
             maxres = 0.0;
-            for (int i = 0; i < q; ++i) {
+            for (int i = 0; i < p; ++i) {
                 double den = std::max(std::sqrt(rs[3 * i + 1]), lam_ref * std::sqrt(rs[3 * i + 2]));
                 res[i] = std::sqrt(rs[3 * i]) / den;
-                if (i < p) maxres = std::max(maxres, res[i]);
+                maxres = std::max(maxres, res[i]);
             }
             if (trace_on())
                 std::fprintf(stderr,
