@@ -483,6 +483,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         // the factorisation is stable, and the convergence ratio of the top
         // pairs, (lambda_i - mu) / (lambda_q - mu), changes by about 1 %.
         const bool mixed = o.precision == HSIM_MIXED;
+        const int q32 = (q + 3) & ~3;  // FP32 block rows 16-byte aligned (vector atomics)
         if (mixed) {
             double lam_ref = lam_h[q - 1];
             for (int i = 0; i < q; ++i)
@@ -504,7 +505,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             if (negp != 0)
                 fail(HSIM_E_BREAKDOWN, "FP32 factor of the positive definite shifted matrix has " +
                                            std::to_string(negp) + " negative pivot(s)");
-            H->X32.reserve((size_t)n * q);
+            H->X32.reserve((size_t)n * q32);
             H->rho.reserve(2 * (size_t)q);
         }
         // One inverse iteration in correction form (mixed path): for any
@@ -516,9 +517,9 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         // [0, a) with leading dimension q; num / den give rho per column.
         auto correction_step = [&](const double *X, const double *SX, const double *MX, const double *num,
                                    const double *den, double *Y, int a) {
-            k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->X32.p, q);
-            solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->X32.p, a, q);
-            k::sub_f2d(s, n, a, X, q, H->X32.p, q, Y, q);
+            k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->X32.p, q32);
+            solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->X32.p, a, q32);
+            k::sub_f2d(s, n, a, X, q, H->X32.p, q32, Y, q);
         };
         if (trace_on())
             std::fprintf(stderr, "[hsim] level %d n=%d q=%d shift=%.10g negative_pivots=%d fronts=%d nnzL=%lld\n", tau,

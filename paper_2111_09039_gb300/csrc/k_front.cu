@@ -305,6 +305,18 @@ __global__ void __launch_bounds__(kTriCols) k_solve_fwd_tri(FrontDev fd, const i
         if (r < kb) Xb[(size_t)r * ldx] = x[r];
 }
 
+// x[0..3] -= a[0..3] with atomics (one vector atomic for four aligned floats)
+__device__ __forceinline__ void atomic_sub4(float *x, const float (&a)[4], int avail) {
+    if (avail >= 4 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+        atomicAdd(reinterpret_cast<float4 *>(x), make_float4(-a[0], -a[1], -a[2], -a[3]));
+    } else {
+        for (int v = 0; v < 4 && v < avail; ++v) atomicAdd(x + v, -a[v]);
+    }
+}
+__device__ __forceinline__ void atomic_sub4(double *x, const double (&a)[4], int avail) {
+    for (int v = 0; v < 4 && v < avail; ++v) atomicAdd(x + v, -a[v]);
+}
+
 // X[row(r), cols] -= sum_c L[r, k0+c] X[panel row c, cols] for front rows
 // r >= k0 + kb; pivot rows of the front are updated in place, rows of
 // ancestor fronts with atomics (sibling fronts share them).
@@ -336,6 +348,7 @@ __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *_
         Xs[kk][i] = xv;
     }
     __syncthreads();
+    // thread: rows ty + 16 u, four contiguous columns 4 tx .. 4 tx + 3
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     T acc[4][4] = {};
     for (int kk = 0; kk < kb; ++kk) {
@@ -343,25 +356,26 @@ __global__ void __launch_bounds__(256) k_solve_fwd_upd(FrontDev fd, const int *_
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             a[u] = Ls[kk][ty + 16 * u];
-            b[u] = Xs[kk][tx + 16 * u];
+            b[u] = Xs[kk][4 * tx + u];
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
     }
+    const int cb = c0 + 4 * tx;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         int r = r0 + ty + 16 * u;
         if (r >= nf) continue;
         int grow = rows[r];
-        T *xr = X + (size_t)grow * ldx;
+        T *xr = X + (size_t)grow * ldx + cb;
+        if (r < ns) {
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            int c = c0 + tx + 16 * v;
-            if (c >= k) continue;
-            if (r < ns) xr[c] -= acc[u][v];
-            else atomicAdd(&xr[c], -acc[u][v]);
+            for (int v = 0; v < 4; ++v)
+                if (cb + v < k) xr[v] -= acc[u][v];
+        } else {
+            atomic_sub4(xr, acc[u], k - cb);
         }
     }
 }
@@ -374,8 +388,11 @@ __global__ void k_solve_diag(int n, int k, const T *__restrict__ dpos, T *__rest
     X[(size_t)i * ldx + j] /= dpos[i];
 }
 
-// X[panel rows c, cols] -= sum_{r >= k0+kb} L[r, k0+c] X[row(r), cols]
-// split over 32-row chunks of r, accumulated with atomics.
+// X[panel rows c, cols] -= sum_{r >= k0+kb} L[r, k0+c] X[row(r), cols].  A CTA
+// covers kBwdChunks 32-row chunks of r; when one CTA covers all rows of the
+// front (grid.y == 1) it updates the panel rows with plain stores, otherwise
+// the partial sums are accumulated with atomics.
+constexpr int kBwdChunks = 1;
 template <typename T>
 __global__ void __launch_bounds__(256) k_solve_bwd_upd(FrontDev fd, const int *__restrict__ nodes, int k0,
                                                        const T *__restrict__ arena, int k,
@@ -387,34 +404,43 @@ __global__ void __launch_bounds__(256) k_solve_bwd_upd(FrontDev fd, const int *_
     const int kb = min(P, ns - k0);
     if (kb <= 0) return;
     const int base = k0 + kb;
-    const int r0 = base + blockIdx.y * P;
-    if (r0 >= nf) return;
+    const int rbeg = base + blockIdx.y * P * kBwdChunks;
+    if (rbeg >= nf) return;
+    const int rend = min(nf, rbeg + P * kBwdChunks);
     const int c0 = blockIdx.z * 64;
     if (c0 >= k) return;
     const T *F = arena + fd.foff[t];
     const int *rows = fd.rows + fd.rows_off[t];
-    for (int idx = threadIdx.x; idx < P * P; idx += blockDim.x) {
-        int r = idx % P, c = idx / P;
-        Ls[r][c] = (r0 + r < nf && c < kb) ? F[(int64_t)(k0 + c) * nf + (r0 + r)] : 0.0;
-    }
-    for (int idx = threadIdx.x; idx < P * 64; idx += blockDim.x) {
-        int j = idx & 63, r = idx >> 6;
-        Xs[r][j] = (r0 + r < nf && c0 + j < k) ? X[(size_t)rows[r0 + r] * ldx + c0 + j] : 0.0;
-    }
-    __syncthreads();
     // 32 x 64 outputs, 8 per thread: thread -> column j = tid & 63, rows c = (tid >> 6) + 4u
     const int j = threadIdx.x & 63, cb = threadIdx.x >> 6;
     T acc[8] = {};
-    for (int r = 0; r < P; ++r) {
-        T xv = Xs[r][j];
+    for (int r0 = rbeg; r0 < rend; r0 += P) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < P * P; idx += blockDim.x) {
+            int r = idx % P, c = idx / P;
+            Ls[r][c] = (r0 + r < rend && c < kb) ? F[(int64_t)(k0 + c) * nf + (r0 + r)] : T(0);
+        }
+        for (int idx = threadIdx.x; idx < P * 64; idx += blockDim.x) {
+            int jj = idx & 63, r = idx >> 6;
+            Xs[r][jj] = (r0 + r < rend && c0 + jj < k) ? X[(size_t)rows[r0 + r] * ldx + c0 + jj] : T(0);
+        }
+        __syncthreads();
+        for (int r = 0; r < P; ++r) {
+            T xv = Xs[r][j];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] += Ls[r][cb + 4 * u] * xv;
+            for (int u = 0; u < 8; ++u) acc[u] += Ls[r][cb + 4 * u] * xv;
+        }
     }
     if (c0 + j < k) {
+        const bool whole = gridDim.y == 1;
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             int c = cb + 4 * u;
-            if (c < kb) atomicAdd(&X[(size_t)(ps + k0 + c) * ldx + c0 + j], -acc[u]);
+            if (c < kb) {
+                T *x = &X[(size_t)(ps + k0 + c) * ldx + c0 + j];
+                if (whole) *x -= acc[u];
+                else atomicAdd(x, -acc[u]);
+            }
         }
     }
 }
@@ -544,7 +570,7 @@ template <typename T>
 void solve_bwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_rows,
                    const T *arena, int k, T *X, int ldx) {
     if (n_nodes <= 0 || k <= 0 || max_rows <= 0) return;
-    dim3 g((unsigned)n_nodes, cdiv(max_rows, P), cdiv(k, 64));
+    dim3 g((unsigned)n_nodes, cdiv(max_rows, P * kBwdChunks), cdiv(k, 64));
     k_solve_bwd_upd<T><<<g, 256, 0, s>>>(fd, nodes, k0, arena, k, X, ldx);
     HSIM_LAUNCHED();
 }
