@@ -26,6 +26,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "common.h"
@@ -443,6 +445,20 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     HSIM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     HSIM_CHECK_ARG(per_sm >= 1, "sym_eig: tridiagonalisation kernel does not fit on an SM");
     int grid = std::max(1, std::min(sms, (n + 7) / 8));
+    // HSIM_TRACE=2: stage times of every call
+    static const bool detail = [] {
+        const char *ev = std::getenv("HSIM_TRACE");
+        return ev && std::atoi(ev) >= 2;
+    }();
+    cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr, t4 = nullptr;
+    if (detail) {
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaEventCreate(&t2);
+        cudaEventCreate(&t3);
+        cudaEventCreate(&t4);
+        cudaEventRecord(t0, s);
+    }
     int nn = n;
     void *args[] = {&nn, &A, &d, &e, &tau, &Vh, &p};
     HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_tridiag, dim3(grid), dim3(kTriThreads), args, smem, s));
@@ -450,8 +466,10 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     // 2. eigenvalues
     k_tri_prep<<<1, kTriThreads, 0, s>>>(n, d, e, e2, bounds, d32, e232);
     HSIM_LAUNCHED();
+    if (detail) cudaEventRecord(t1, s);
     k_tri_bisect<<<cdiv((int64_t)m * 32, 128), 128, 0, s>>>(n, m, d, e2, d32, e232, bounds, lam);
     HSIM_LAUNCHED();
+    if (detail) cudaEventRecord(t2, s);
     // 3. clusters on the host, then inverse iteration
     std::vector<double> hl(m), hb(4);
     HSIM_CUDA(cudaMemcpyAsync(hl.data(), lam, m * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -463,8 +481,10 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     starts.push_back(m);
     const int nclusters = (int)starts.size() - 1;
     HSIM_CUDA(cudaMemcpyAsync(cst, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (detail) cudaEventRecord(t2, s);
     k_tri_invit<<<nclusters, 32, 0, s>>>(n, d, e, bounds, lam, cst, Z, lu, pivf);
     HSIM_LAUNCHED();
+    if (detail) cudaEventRecord(t3, s);
     // 4. back transformation
     const int per_cta = std::max(1, std::min(8, (int)((200 * 1024) / ((size_t)n * sizeof(double)))));
     const size_t bsm = (size_t)per_cta * n * sizeof(double);
@@ -474,6 +494,22 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     HSIM_CUDA(cudaMemcpyAsync(evals, lam, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     // the host vector `starts` must outlive the copy above
     HSIM_CUDA(cudaStreamSynchronize(s));
+    if (detail) {
+        cudaEventRecord(t4, s);
+        cudaEventSynchronize(t4);
+        float a = 0, b = 0, c = 0, dd = 0;
+        cudaEventElapsedTime(&a, t0, t1);
+        cudaEventElapsedTime(&b, t1, t2);
+        cudaEventElapsedTime(&c, t2, t3);
+        cudaEventElapsedTime(&dd, t3, t4);
+        int biggest = 0;
+        for (size_t i = 0; i + 1 < starts.size(); ++i) biggest = std::max(biggest, starts[i + 1] - starts[i]);
+        std::fprintf(stderr,
+                     "[hsim] sym_eig n=%d m=%d tridiag %.2f ms eigenvalues %.2f ms vectors %.2f ms (%d clusters, "
+                     "largest %d) back %.2f ms\n",
+                     n, m, a, b, c, nclusters, biggest, dd);
+        for (cudaEvent_t ev : {t0, t1, t2, t3, t4}) cudaEventDestroy(ev);
+    }
 }
 
 }  // namespace k
