@@ -261,13 +261,19 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
         ev.push_back(e);
     };
     mark();
+    // heights whose fronts are all one panel wide and small: fused kernels
+    auto small = [&](int h) { return L.step_cnt[h].size() == 1 && L.step_maxnf[h][0] <= k::kSmallNf; };
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
-        for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
-            int cnt = L.step_cnt[h][kst];
-            int k0 = (int)kst * kPanel;
-            k::solve_fwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
-            k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
+        if (small(h)) {
+            k::solve_fwd_small(s, L.fd, nodes, L.step_cnt[h][0], L.step_maxnf[h][0], arena, k, X, ldx);
+        } else {
+            for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
+                int cnt = L.step_cnt[h][kst];
+                int k0 = (int)kst * kPanel;
+                k::solve_fwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
+                k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
+            }
         }
         mark();
     }
@@ -275,11 +281,15 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
     mark();
     for (int h = fs.max_height; h >= 0; --h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
-        for (int kst = (int)L.step_cnt[h].size() - 1; kst >= 0; --kst) {
-            int cnt = L.step_cnt[h][kst];
-            int k0 = kst * kPanel;
-            k::solve_bwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
-            k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
+        if (small(h)) {
+            k::solve_bwd_small(s, L.fd, nodes, L.step_cnt[h][0], L.step_maxnf[h][0], arena, k, X, ldx);
+        } else {
+            for (int kst = (int)L.step_cnt[h].size() - 1; kst >= 0; --kst) {
+                int cnt = L.step_cnt[h][kst];
+                int k0 = kst * kPanel;
+                k::solve_bwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
+                k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
+            }
         }
         mark();
     }

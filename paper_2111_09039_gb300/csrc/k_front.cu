@@ -483,6 +483,151 @@ __global__ void __launch_bounds__(kTriCols) k_solve_bwd_tri(FrontDev fd, const i
         if (r < kb) Xb[(size_t)r * ldx] = x[r];
 }
 
+// ---- single-panel fronts (ns <= P, nf <= kSmallNf): fused solve kernels -------
+// One CTA per (front, column tile): the front's L panel and pivot rows are
+// staged in shared memory once; the forward kernel solves the unit lower
+// triangle and sends L21 x1 to the ancestors' rows (vector atomics), the
+// backward kernel gathers the ancestors' rows, subtracts L21^T x2 and solves
+// the unit upper triangle.  Thread layout for the products: 4 contiguous
+// columns per thread, 8 row groups.
+template <typename T>
+__host__ __device__ constexpr int small_cols() { return 512 / (int)sizeof(T); }  // 128 float, 64 double
+
+// copy n values of one row between global and shared memory: 16-byte vectors
+// when `vec` (both addresses 16-byte aligned, n a multiple of the vector)
+template <typename T>
+__device__ __forceinline__ void row_load(T *dst, const T *src, int n, int lane, int lanes, bool vec) {
+    constexpr int V = 16 / (int)sizeof(T);
+    if (vec && n % V == 0) {
+        for (int i = lane; i < n / V; i += lanes) reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+    } else {
+        for (int i = lane; i < n; i += lanes) dst[i] = src[i];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_fwd_small(FrontDev fd, const int *__restrict__ nodes,
+                                                         const T *__restrict__ arena, int k, T *__restrict__ X,
+                                                         int ldx, bool vec, int nf_max) {
+    constexpr int SC = small_cols<T>();
+    constexpr int CG = SC / 4;   // column groups of 4
+    constexpr int RG = 256 / CG; // row groups
+    extern __shared__ __align__(16) unsigned char small_smem[];
+    T *Ls = reinterpret_cast<T *>(small_smem);  // ns x nf (column-major panel)
+    T *Xp = Ls + P * nf_max;                    // [P][SC]
+    const int t = nodes[blockIdx.x];
+    const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
+    const int c0 = blockIdx.y * SC;
+    if (c0 >= k) return;
+    const int tid = threadIdx.x;
+    const T *F = arena + fd.foff[t];
+    for (int i = tid; i < ns * nf; i += 256) Ls[i] = F[i];
+    const int cols = min(SC, k - c0);
+    // pivot rows: one warp per row
+    for (int r = tid / 32; r < ns; r += 8) {
+        row_load(Xp + r * SC, X + (size_t)(ps + r) * ldx + c0, cols, tid % 32, 32, vec);
+        for (int c = cols + tid % 32; c < SC; c += 32) Xp[r * SC + c] = T(0);
+    }
+    __syncthreads();
+    if (tid < SC) {
+        for (int r = 1; r < ns; ++r) {
+            T acc = Xp[r * SC + tid];
+            for (int q = 0; q < r; ++q) acc -= Ls[q * nf + r] * Xp[q * SC + tid];
+            Xp[r * SC + tid] = acc;
+        }
+    }
+    __syncthreads();
+    for (int r = tid / 32; r < ns; r += 8) row_load(X + (size_t)(ps + r) * ldx + c0, Xp + r * SC, cols, tid % 32, 32, vec);
+    // ancestors' rows: x_r -= L_r. x_p
+    const int cg = (tid % CG) * 4, rg = tid / CG;
+    const int *rows = fd.rows + fd.rows_off[t];
+    for (int r = ns + rg; r < nf; r += RG) {
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int q = 0; q < ns; ++q) {
+            const T l = Ls[q * nf + r];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[v] += l * Xp[q * SC + cg + v];
+        }
+        atomic_sub4(X + (size_t)rows[r] * ldx + c0 + cg, acc, k - c0 - cg);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_bwd_small(FrontDev fd, const int *__restrict__ nodes,
+                                                         const T *__restrict__ arena, int k, T *__restrict__ X,
+                                                         int ldx, bool vec, int nf_max) {
+    constexpr int SC = small_cols<T>();
+    constexpr int CG = SC / 4;
+    constexpr int RG = 256 / CG;
+    extern __shared__ __align__(16) unsigned char small_smem[];
+    T *Ls = reinterpret_cast<T *>(small_smem);
+    T *Xp = Ls + P * nf_max;    // [P][SC]
+    T *Xu = Xp + P * SC;        // [P][SC] chunk of ancestor rows
+    const int t = nodes[blockIdx.x];
+    const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
+    const int c0 = blockIdx.y * SC;
+    if (c0 >= k) return;
+    const int tid = threadIdx.x;
+    const T *F = arena + fd.foff[t];
+    const int *rows = fd.rows + fd.rows_off[t];
+    for (int i = tid; i < ns * nf; i += 256) Ls[i] = F[i];
+    const int cols = min(SC, k - c0);
+    for (int r = tid / 32; r < ns; r += 8) {
+        row_load(Xp + r * SC, X + (size_t)(ps + r) * ldx + c0, cols, tid % 32, 32, vec);
+        for (int c = cols + tid % 32; c < SC; c += 32) Xp[r * SC + c] = T(0);
+    }
+    // x_p -= L21^T x_u over 32-row chunks of the ancestors' rows; thread: pivots
+    // q = rg + RG j, columns cg .. cg + 3
+    const int cg = (tid % CG) * 4, rg = tid / CG;
+    constexpr int QJ = (P + RG - 1) / RG;
+    T acc[QJ][4];
+#pragma unroll
+    for (int j = 0; j < QJ; ++j)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[j][v] = T(0);
+    for (int r0 = ns; r0 < nf; r0 += P) {
+        const int cnt = min(P, nf - r0);
+        __syncthreads();
+        for (int rr = tid / 32; rr < cnt; rr += 8) {
+            row_load(Xu + rr * SC, X + (size_t)rows[r0 + rr] * ldx + c0, cols, tid % 32, 32, vec);
+            for (int c = cols + tid % 32; c < SC; c += 32) Xu[rr * SC + c] = T(0);
+        }
+        __syncthreads();
+        for (int rr = 0; rr < cnt; ++rr) {
+            T xu[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) xu[v] = Xu[rr * SC + cg + v];
+#pragma unroll
+            for (int j = 0; j < QJ; ++j) {
+                const int q = rg + RG * j;
+                if (q < ns) {
+                    const T l = Ls[q * nf + r0 + rr];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[j][v] += l * xu[v];
+                }
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < QJ; ++j) {
+        const int q = rg + RG * j;
+        if (q < ns)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Xp[q * SC + cg + v] -= acc[j][v];
+    }
+    __syncthreads();
+    if (tid < SC) {
+        for (int r = ns - 2; r >= 0; --r) {
+            T a = Xp[r * SC + tid];
+            for (int q = r + 1; q < ns; ++q) a -= Ls[r * nf + q] * Xp[q * SC + tid];
+            Xp[r * SC + tid] = a;
+        }
+    }
+    __syncthreads();
+    for (int r = tid / 32; r < ns; r += 8) row_load(X + (size_t)(ps + r) * ldx + c0, Xp + r * SC, cols, tid % 32, 32, vec);
+}
+
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
@@ -584,6 +729,32 @@ void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
     HSIM_LAUNCHED();
 }
 
+template <typename T>
+void solve_fwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int nf_max, const T *arena,
+                     int k, T *X, int ldx) {
+    if (n_nodes <= 0 || k <= 0) return;
+    nf_max = (nf_max + 3) & ~3;  // keeps the row blocks after the panel 16-byte aligned
+    const size_t sm = ((size_t)P * nf_max + (size_t)P * small_cols<T>()) * sizeof(T);
+    HSIM_CUDA(cudaFuncSetAttribute(k_solve_fwd_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const bool vec = (reinterpret_cast<uintptr_t>(X) % 16 == 0) && ((size_t)ldx * sizeof(T)) % 16 == 0;
+    k_solve_fwd_small<T><<<dim3((unsigned)n_nodes, cdiv(k, small_cols<T>())), 256, sm, s>>>(fd, nodes, arena, k, X,
+                                                                                             ldx, vec, nf_max);
+    HSIM_LAUNCHED();
+}
+
+template <typename T>
+void solve_bwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int nf_max, const T *arena,
+                     int k, T *X, int ldx) {
+    if (n_nodes <= 0 || k <= 0) return;
+    nf_max = (nf_max + 3) & ~3;
+    const size_t sm = ((size_t)P * nf_max + 2 * (size_t)P * small_cols<T>()) * sizeof(T);
+    HSIM_CUDA(cudaFuncSetAttribute(k_solve_bwd_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const bool vec = (reinterpret_cast<uintptr_t>(X) % 16 == 0) && ((size_t)ldx * sizeof(T)) % 16 == 0;
+    k_solve_bwd_small<T><<<dim3((unsigned)n_nodes, cdiv(k, small_cols<T>())), 256, sm, s>>>(fd, nodes, arena, k, X,
+                                                                                             ldx, vec, nf_max);
+    HSIM_LAUNCHED();
+}
+
 #define HSIM_FRONT_INSTANTIATE(T)                                                                                  \
     template void front_assemble<T>(cudaStream_t, int64_t, const int *, const int *, const int64_t *,            \
                                     const double *, const double *, const double *, double, T *);               \
@@ -598,7 +769,9 @@ void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
     template void solve_diag<T>(cudaStream_t, int, int, const T *, T *, int);                                    \
     template void solve_bwd_upd<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, const T *, int, T *, \
                                    int);                                                                         \
-    template void solve_bwd_tri<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int);
+    template void solve_bwd_tri<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int); \
+    template void solve_fwd_small<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int); \
+    template void solve_bwd_small<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int);
 
 HSIM_FRONT_INSTANTIATE(float)
 HSIM_FRONT_INSTANTIATE(double)

@@ -155,6 +155,15 @@ void solve_bwd_upd(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
 template <typename T>
 void solve_bwd_tri(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
                    const T *arena, int k, T *X, int ldx);
+// fused forward / backward solve of single-panel fronts (ns <= kPanel,
+// nf <= kSmallNf): triangle and update in one launch per tree height
+constexpr int kSmallNf = 320;
+template <typename T>
+void solve_fwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int nf_max, const T *arena,
+                     int k, T *X, int ldx);
+template <typename T>
+void solve_bwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int nf_max, const T *arena,
+                     int k, T *X, int ldx);
 
 // ---- FP64-accurate products on BF16 tensor cores (k_ozaki.cu) --------------
 constexpr int kOzakiSlices = 6;
