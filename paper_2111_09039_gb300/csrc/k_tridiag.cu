@@ -241,10 +241,13 @@ __global__ void k_tri_bisect(int n, int m, const double *__restrict__ d, const d
         if (!okh) hi = fmin(ghi, hi + w);
         w *= 2.0;
     }
-    // FP64 multisection
+    // FP64 multisection to 2 eps max(|lambda|, ||T||): the absolute accuracy
+    // of a dense symmetric eigensolve (a relative stop alone would drive the
+    // bracket of an eigenvalue at zero down to pivmin)
+    const double atol = 2.0 * DBL_EPSILON * tn + pivmin;
     for (int round = 0; round < 40; ++round) {
         const double mid = 0.5 * (lo + hi);
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin || mid == lo || mid == hi) break;
+        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + atol || mid == lo || mid == hi) break;
         const double x = lo + (hi - lo) * (lane + 1) / 33.0;
         const bool le = sturm_count(n, d, e2, x, pivmin) <= i;
         const unsigned bal = __ballot_sync(0xffffffffu, le);
