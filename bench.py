@@ -503,7 +503,14 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
                            "fp64_equivalent_tflops": (gram_flops + upd_flops) / (ms_tc * 1e-3) / 1e12
                            if ms_tc > 0 else 0.0, "ms_per_step": ms_tc}
         kernels["update"] = kernels["gram"]
-    top = dict(kernels.get(dom, kernels["ritz"] if dom == "coarse" else kernels["gram"]))
+    # the top-level entry is the single kernel with the most GPU time: the
+    # FP64-accurate product kernel (mixed) or the FP64 Gram (FP64 path); the
+    # solve and Ritz phases are spread over several kernels (ncu launch lists)
+    top = dict(kernels["gram"])
+    if precision != "fp64":
+        top["traffic"] = None
+        top["traffic_note"] = ("ncu capture of one 200,000 x 750 Gram launch: 4.88 GB DRAM read+write against "
+                               "3.69 GB of digit operands (1.32 x)")
     top["dominant_phase"] = dom
     top["phase_ms"] = phases
     top["kernels"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <mutex>
 #include <cstdint>
 #include <cstdio>
 #include <stdexcept>
@@ -49,6 +50,20 @@ extern std::atomic<uint64_t> g_launches;
         if (e_ != cudaSuccess)                                                            \
             ::hsim::fail(HSIM_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_) + \
                                           " (" __FILE__ ":" + std::to_string(__LINE__) + ")"); \
+    } while (0)
+
+// Raise a kernel's dynamic shared-memory limit once per process to the largest
+// size any of its launches uses.  The limit is a process-wide attribute of the
+// function: setting it per launch to that launch's size races with launches
+// of the same kernel from other host threads (batched solves).
+#define HSIM_SMEM_LIMIT_ONCE(func, max_bytes)                                                        \
+    do {                                                                                              \
+        static std::once_flag once_;                                                                  \
+        static cudaError_t err_ = cudaSuccess;                                                        \
+        std::call_once(once_, [&] {                                                                   \
+            err_ = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(max_bytes)); \
+        });                                                                                           \
+        HSIM_CUDA(err_);                                                                              \
     } while (0)
 
 // Owning device buffer.

@@ -735,7 +735,7 @@ void solve_fwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n
     if (n_nodes <= 0 || k <= 0) return;
     nf_max = (nf_max + 3) & ~3;  // keeps the row blocks after the panel 16-byte aligned
     const size_t sm = ((size_t)P * nf_max + (size_t)P * small_cols<T>()) * sizeof(T);
-    HSIM_CUDA(cudaFuncSetAttribute(k_solve_fwd_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HSIM_SMEM_LIMIT_ONCE(k_solve_fwd_small<T>, ((size_t)P * kSmallNf + (size_t)P * small_cols<T>()) * sizeof(T));
     const bool vec = (reinterpret_cast<uintptr_t>(X) % 16 == 0) && ((size_t)ldx * sizeof(T)) % 16 == 0;
     k_solve_fwd_small<T><<<dim3((unsigned)n_nodes, cdiv(k, small_cols<T>())), 256, sm, s>>>(fd, nodes, arena, k, X,
                                                                                              ldx, vec, nf_max);
@@ -748,7 +748,8 @@ void solve_bwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n
     if (n_nodes <= 0 || k <= 0) return;
     nf_max = (nf_max + 3) & ~3;
     const size_t sm = ((size_t)P * nf_max + 2 * (size_t)P * small_cols<T>()) * sizeof(T);
-    HSIM_CUDA(cudaFuncSetAttribute(k_solve_bwd_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    HSIM_SMEM_LIMIT_ONCE(k_solve_bwd_small<T>,
+                         ((size_t)P * kSmallNf + 2 * (size_t)P * small_cols<T>()) * sizeof(T));
     const bool vec = (reinterpret_cast<uintptr_t>(X) % 16 == 0) && ((size_t)ldx * sizeof(T)) % 16 == 0;
     k_solve_bwd_small<T><<<dim3((unsigned)n_nodes, cdiv(k, small_cols<T>())), 256, sm, s>>>(fd, nodes, arena, k, X,
                                                                                              ldx, vec, nf_max);

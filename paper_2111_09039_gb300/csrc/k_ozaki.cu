@@ -472,7 +472,7 @@ void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int rows_p
                        N <= rows_py && k_len % TC_K == 0,
                    "ozaki product: operand layout not supported");
     HSIM_CHECK_ARG(!lower || M == N, "ozaki product: lower triangle needs a square result");
-    HSIM_CUDA(cudaFuncSetAttribute(k_ozaki_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    HSIM_SMEM_LIMIT_ONCE(k_ozaki_tc, TC_SMEM);
     int k_split = (int)((k_len + splits - 1) / splits);
     k_split = (k_split + kFlush - 1) / kFlush * kFlush;
     splits = (int)cdiv(k_len, k_split);

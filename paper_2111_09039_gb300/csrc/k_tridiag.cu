@@ -44,6 +44,7 @@ inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b);
 
 constexpr int kTriThreads = 256;
 constexpr double kClusterTol = 1e-5;  // relative to ||T||
+constexpr size_t kTriSmemMax = 200 * 1024;  // dynamic shared memory limit of k_tridiag and k_tri_back
 
 // sum over the block (256 threads); `red` holds 8 doubles; result in all threads
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -440,8 +441,8 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     }
     // 1. tridiagonalisation (one CTA per SM, two grid barriers per column)
     const size_t smem = 2 * (size_t)n * sizeof(double);
-    HSIM_CHECK_ARG(smem <= 200 * 1024, "sym_eig: matrix too large for the tridiagonalisation kernel");
-    HSIM_CUDA(cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HSIM_CHECK_ARG(smem <= kTriSmemMax, "sym_eig: matrix too large for the tridiagonalisation kernel");
+    HSIM_SMEM_LIMIT_ONCE(k_tridiag, kTriSmemMax);
     int per_sm = 0, dev = 0, sms = 0;
     HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, kTriThreads, smem));
     HSIM_CUDA(cudaGetDevice(&dev));
@@ -489,9 +490,9 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     HSIM_LAUNCHED();
     if (detail) cudaEventRecord(t3, s);
     // 4. back transformation
-    const int per_cta = std::max(1, std::min(8, (int)((200 * 1024) / ((size_t)n * sizeof(double)))));
+    const int per_cta = std::max(1, std::min(8, (int)(kTriSmemMax / ((size_t)n * sizeof(double)))));
     const size_t bsm = (size_t)per_cta * n * sizeof(double);
-    HSIM_CUDA(cudaFuncSetAttribute(k_tri_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    HSIM_SMEM_LIMIT_ONCE(k_tri_back, kTriSmemMax);
     k_tri_back<<<cdiv(m, per_cta), kTriThreads, bsm, s>>>(n, m, per_cta, Vh, tau, Z, X, ldx);
     HSIM_LAUNCHED();
     HSIM_CUDA(cudaMemcpyAsync(evals, lam, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
