@@ -5,11 +5,13 @@
 //   1. Householder tridiagonalisation Q^T A Q = T in one cooperative launch:
 //      per column k every CTA rebuilds the reflector v_k = (1, x_2..)/(x_1 -
 //      beta) from the column below the diagonal (so no barrier is needed to
-//      share it), warps compute p = tau A22 v over the rows of the trailing
-//      block, one grid barrier, every CTA forms w = p - (tau/2)(p.v) v, warps
-//      apply A22 -= v w^T + w v^T to their rows, one grid barrier.  The
-//      reflectors are kept row-wise in Vh (contiguous for the back
-//      transformation).
+//      share it), computes p = tau A22 v over its rows of the trailing block,
+//      forms w = p - (tau/2)(p.v) v and applies A22 -= v w^T + w v^T to its
+//      rows.  Where the matrix fits in the CTAs' shared memory (n up to about
+//      1650 on 152 SMs) each CTA keeps its rows there and one grid barrier per
+//      column suffices (k_tridiag_rows); otherwise the rows stay in global
+//      memory with two barriers per column (k_tridiag).  The reflectors are
+//      kept row-wise in Vh (contiguous for the back transformation).
 //   2. Eigenvalues of T by multisection on Sturm counts, one warp per index
 //      (ascending by construction): FP32 rounds, an FP64 check of the
 //      bracket, FP64 rounds.
@@ -18,8 +20,9 @@
 //      iterations from a hashed random start; eigenvalues closer than
 //      1e-5 ||T|| form a cluster whose vectors are made orthogonal to the
 //      previous ones of the cluster in every iteration (one warp per cluster).
-//   4. Back transformation X = Q Z, reflectors applied in reverse order, a
-//      few eigenvectors per CTA held in shared memory.
+//   4. Back transformation X = Q Z, reflectors applied in reverse order: one
+//      warp per eigenvector held in registers (n <= 2048), else a few
+//      eigenvectors per CTA held in shared memory.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -123,6 +126,184 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag(int n, double *__restri
     if (blockIdx.x == 0 && tid == 0) {
         d[n - 1] = A[(size_t)(n - 1) * n + (n - 1)];
         tau[n - 1] = 0.0;
+    }
+}
+
+// Tridiagonalisation with the matrix resident in shared memory.  CTA b owns
+// the rows b, b + G, b + 2G, ... (full length n), so the product p = t A22 v
+// and the rank-2 update of every column read and write only shared memory,
+// and one grid barrier per column suffices: before it every CTA writes its
+// entries of p, and the owner of row k+1 writes that row as it stands before
+// the update of column k; after it every CTA forms w and, from that row, the
+// updated row k+1, which by symmetry is the next column to reduce.  The update
+// of column k is applied to the owned rows in the same pass as the product of
+// column k+1.  The arithmetic per column is that of k_tridiag.
+// Shared memory: R n (owned rows, R = ceil(n / G) <= RMAX) + 4 n doubles.
+template <int RMAX>
+__global__ void __launch_bounds__(kTriThreads) k_tridiag_rows(int n, const double *__restrict__ A, double *__restrict__ d,
+                                                            double *__restrict__ e, double *__restrict__ tau,
+                                                            double *__restrict__ Vh, double *__restrict__ pbuf,
+                                                            double *__restrict__ rbuf) {
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ double sm[];
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int R = (n - b + G - 1) / G;          // rows owned by this CTA
+    const int Rmax = (n + G - 1) / G;
+    double *rows = sm;                           // Rmax x n
+    double *xs = rows + (size_t)Rmax * n;        // row k: xs[i] = A[k, k + i]
+    double *v = xs + n, *vp = v + n, *w = vp + n;  // reflector of column k, of column k - 1; w of column k - 1
+    __shared__ double red[kTriThreads / 32];
+    __shared__ double redr[kTriThreads / 32][RMAX];
+    for (int i = 0; i < R; ++i) {
+        const double *src = A + (size_t)(b + i * G) * n;
+        for (int j = tid; j < n; j += kTriThreads) rows[(size_t)i * n + j] = src[j];
+    }
+    for (int j = tid; j < n; j += kTriThreads) xs[j] = A[j];
+    __syncthreads();
+    for (int k = 0; k + 1 < n; ++k) {
+        const int L = n - k - 1;
+        // reflector of y = xs[1 .. L] (column k below the diagonal)
+        double part = 0.0;
+        for (int i = 1 + tid; i < L; i += kTriThreads) part += xs[1 + i] * xs[1 + i];
+        const double sigma = block_sum(part, red);
+        const double x0 = xs[1];
+        double beta = x0, t = 0.0, scale = 0.0;
+        if (sigma != 0.0) {
+            const double mu = sqrt(x0 * x0 + sigma);
+            beta = x0 >= 0.0 ? -mu : mu;
+            t = (beta - x0) / beta;
+            scale = 1.0 / (x0 - beta);
+        }
+        for (int i = tid; i < L; i += kTriThreads) {
+            const double vi = i == 0 ? 1.0 : (t != 0.0 ? xs[1 + i] * scale : 0.0);
+            v[i] = vi;
+            if (b == 0) Vh[(size_t)k * n + k + 1 + i] = vi;
+        }
+        if (b == 0 && tid == 0) {
+            d[k] = xs[0];
+            e[k] = beta;
+            tau[k] = t;
+        }
+        __syncthreads();
+        // owned rows r >= k + 1: update of column k - 1 (vectors vp, w, index
+        // 0 <-> row k) on columns >= k + 1, then the product with v
+        const int i0 = k + 1 > b ? (k + 1 - b + G - 1) / G : 0;
+        double acc[RMAX];
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) acc[i] = 0.0;
+        double *rb = rbuf + (size_t)(k & 1) * n;
+        for (int j = tid; j < L; j += kTriThreads) {
+            const double vj = v[j];
+            const double vpj = k > 0 ? vp[j + 1] : 0.0, wpj = k > 0 ? w[j + 1] : 0.0;
+#pragma unroll
+            for (int i = 0; i < RMAX; ++i) {
+                if (i < i0 || i >= R) continue;
+                const int r = b + i * G;
+                double *a = rows + (size_t)i * n + k + 1 + j;
+                double x = *a;
+                if (k > 0) x -= vp[r - k] * wpj + w[r - k] * vpj;
+                *a = x;
+                acc[i] += x * vj;
+                if (r == k + 1) rb[j] = x;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RMAX; ++i) {
+            if (i < i0 || i >= R) continue;
+            double s = acc[i];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) redr[wid][i] = s;
+        }
+        __syncthreads();
+        if (tid >= i0 && tid < R) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < kTriThreads / 32; ++q) s += redr[q][tid];
+            pbuf[(size_t)(k & 1) * n + (b + tid * G - k - 1)] = t * s;
+        }
+        grid.sync();
+        // w = p - (t/2)(p.v) v, then row k + 1 after the update of column k
+        const double *pb = pbuf + (size_t)(k & 1) * n;
+        double pv = 0.0;
+        for (int j = tid; j < L; j += kTriThreads) {
+            const double pj = __ldcg(pb + j);
+            w[j] = pj;
+            pv += pj * v[j];
+        }
+        const double K = 0.5 * t * block_sum(pv, red);
+        for (int j = tid; j < L; j += kTriThreads) w[j] -= K * v[j];
+        __syncthreads();
+        const double w0 = w[0];
+        for (int j = tid; j < L; j += kTriThreads) xs[j] = __ldcg(rb + j) - (v[0] * w[j] + w0 * v[j]);
+        double *tmp = vp;
+        vp = v;
+        v = tmp;
+        __syncthreads();
+    }
+    if (b == 0 && tid == 0) {
+        d[n - 1] = xs[0];
+        tau[n - 1] = 0.0;
+    }
+}
+
+// Back transformation X = Q Z with Q = H_0 H_1 ... H_{n-2}: one warp per
+// vector, its entries j = lane + 32 c in registers (n <= 32 C); the reflector
+// of the next step is loaded into registers while the current one is applied
+// and then stored to the other shared-memory buffer (one barrier per step).
+template <int C>
+__global__ void __launch_bounds__(256) k_tri_back_warp(int n, int m, const double *__restrict__ Vh,
+                                                     const double *__restrict__ tau, const double *__restrict__ Z,
+                                                     double *__restrict__ X, int ldx) {
+    __shared__ double vs[2][32 * C];
+    const int lane = threadIdx.x & 31, nthr = blockDim.x;
+    const int i = blockIdx.x * (nthr >> 5) + (threadIdx.x >> 5);
+    constexpr int P = (32 * C + 127) / 128;  // staged entries per thread (blockDim >= 128)
+    double z[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int j = lane + 32 * c;
+        z[c] = (i < m && j < n) ? Z[(size_t)i * n + j] : 0.0;
+    }
+    // reflector k: entries j > k of row k of Vh, zero elsewhere
+    for (int j = threadIdx.x; j < 32 * C; j += nthr) vs[0][j] = (j > n - 2 && j < n) ? Vh[(size_t)(n - 2) * n + j] : 0.0;
+    __syncthreads();
+    int cur = 0;
+    for (int k = n - 2; k >= 0; --k) {
+        double pre[P];
+        const bool more = k > 0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int j = threadIdx.x + q * nthr;
+            pre[q] = (more && j < n && j > k - 1 && j < 32 * C) ? Vh[(size_t)(k - 1) * n + j] : 0.0;
+        }
+        const double t = tau[k];
+        if (t != 0.0) {
+            const double *vk = vs[cur];
+            const int c0 = (k + 1) >> 5;  // entries below k + 1 are zero
+            double s = 0.0;
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                if (c >= c0) s += vk[lane + 32 * c] * z[c];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s *= t;
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                if (c >= c0) z[c] -= s * vk[lane + 32 * c];
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int j = threadIdx.x + q * nthr;
+            if (j < 32 * C) vs[cur ^ 1][j] = pre[q];
+        }
+        cur ^= 1;
+        __syncthreads();
+    }
+    if (i < m) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int j = lane + 32 * c;
+            if (j < n) X[(size_t)j * ldx + i] = z[c];
+        }
     }
 }
 
@@ -421,8 +602,43 @@ size_t sym_eig_work_size(int n, int m) {
     // d e tau p e2 bounds(8) | Vh n^2 | Z m n | lam m | LU 5 n m | pivots n m bytes | cluster starts m + 1 ints
     // | d, e^2 in FP32 (n each)
     return (size_t)5 * n + 8 + (size_t)n * n + (size_t)m * n + m + (size_t)5 * n * m + ((size_t)n * m + 7) / 8 +
-           ((size_t)m + 2) / 2 + 16 + (size_t)n + 8;
+           ((size_t)m + 2) / 2 + 16 + (size_t)n + 8 + (size_t)4 * n + 8;
 }
+
+namespace {
+
+// grid of k_tridiag_rows for an n x n matrix: G CTAs owning ceil(n / G) rows
+// each; 0 if the rows do not fit in shared memory
+int rows_grid(int n, int sms, size_t *smem, int *rmax) {
+    const int G = std::max(1, std::min(sms, (n + 3) / 4));
+    const int R = (n + G - 1) / G;
+    *smem = ((size_t)R * n + 4 * (size_t)n) * sizeof(double);
+    *rmax = R <= 4 ? 4 : R <= 8 ? 8 : 16;
+    return (R <= 16 && *smem <= kTriSmemMax) ? G : 0;
+}
+
+template <int RMAX>
+bool launch_tridiag_rows(cudaStream_t s, int G, size_t smem, int sms, int n, const double *A, double *d, double *e,
+                         double *tau, double *Vh, double *pbuf, double *rbuf) {
+    HSIM_SMEM_LIMIT_ONCE(k_tridiag_rows<RMAX>, kTriSmemMax);
+    int per_sm = 0;
+    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_rows<RMAX>, kTriThreads, smem));
+    if ((int64_t)per_sm * sms < G) return false;
+    int nn = n;
+    void *args[] = {&nn, &A, &d, &e, &tau, &Vh, &pbuf, &rbuf};
+    HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_tridiag_rows<RMAX>, dim3(G), dim3(kTriThreads), args, smem, s));
+    HSIM_LAUNCHED();
+    return true;
+}
+
+template <int C>
+void launch_back_warp(cudaStream_t s, int warps, int n, int m, const double *Vh, const double *tau, const double *Z,
+                      double *X, int ldx) {
+    k_tri_back_warp<C><<<cdiv(m, warps), 32 * warps, 0, s>>>(n, m, Vh, tau, Z, X, ldx);
+    HSIM_LAUNCHED();
+}
+
+}  // namespace
 
 void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, int ldx, double *work) {
     HSIM_CHECK_ARG(n >= 1 && m >= 1 && m <= n, "sym_eig: bad sizes");
@@ -432,6 +648,7 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     int *cst = reinterpret_cast<int *>(reinterpret_cast<double *>(pivf) + ((size_t)n * m + 7) / 8);
     float *d32 = reinterpret_cast<float *>(reinterpret_cast<double *>(cst) + ((size_t)m + 2) / 2 + 8);
     float *e232 = d32 + n;
+    double *pbuf = reinterpret_cast<double *>(e232 + n) + 4, *rbuf = pbuf + 2 * (size_t)n;
     if (n == 1) {
         HSIM_CUDA(cudaMemcpyAsync(evals, A, sizeof(double), cudaMemcpyDeviceToDevice, s));
         const double one = 1.0;
@@ -439,16 +656,9 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
         HSIM_CUDA(cudaStreamSynchronize(s));
         return;
     }
-    // 1. tridiagonalisation (one CTA per SM, two grid barriers per column)
-    const size_t smem = 2 * (size_t)n * sizeof(double);
-    HSIM_CHECK_ARG(smem <= kTriSmemMax, "sym_eig: matrix too large for the tridiagonalisation kernel");
-    HSIM_SMEM_LIMIT_ONCE(k_tridiag, kTriSmemMax);
-    int per_sm = 0, dev = 0, sms = 0;
-    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, kTriThreads, smem));
+    int dev = 0, sms = 0;
     HSIM_CUDA(cudaGetDevice(&dev));
     HSIM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    HSIM_CHECK_ARG(per_sm >= 1, "sym_eig: tridiagonalisation kernel does not fit on an SM");
-    int grid = std::max(1, std::min(sms, (n + 7) / 8));
     // HSIM_TRACE=2: stage times of every call
     static const bool detail = [] {
         const char *ev = std::getenv("HSIM_TRACE");
@@ -463,10 +673,30 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
         cudaEventCreate(&t4);
         cudaEventRecord(t0, s);
     }
-    int nn = n;
-    void *args[] = {&nn, &A, &d, &e, &tau, &Vh, &p};
-    HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_tridiag, dim3(grid), dim3(kTriThreads), args, smem, s));
-    HSIM_LAUNCHED();
+    // 1. tridiagonalisation: rows resident in shared memory (one grid barrier
+    // per column) where they fit, else rows in global memory (two barriers)
+    size_t rsmem = 0;
+    int rmax = 0;
+    const int G = rows_grid(n, sms, &rsmem, &rmax);
+    bool done = false;
+    if (G > 0) {
+        if (rmax == 4) done = launch_tridiag_rows<4>(s, G, rsmem, sms, n, A, d, e, tau, Vh, pbuf, rbuf);
+        else if (rmax == 8) done = launch_tridiag_rows<8>(s, G, rsmem, sms, n, A, d, e, tau, Vh, pbuf, rbuf);
+        else done = launch_tridiag_rows<16>(s, G, rsmem, sms, n, A, d, e, tau, Vh, pbuf, rbuf);
+    }
+    if (!done) {
+        const size_t smem = 2 * (size_t)n * sizeof(double);
+        HSIM_CHECK_ARG(smem <= kTriSmemMax, "sym_eig: matrix too large for the tridiagonalisation kernel");
+        HSIM_SMEM_LIMIT_ONCE(k_tridiag, kTriSmemMax);
+        int per_sm = 0;
+        HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, kTriThreads, smem));
+        HSIM_CHECK_ARG(per_sm >= 1, "sym_eig: tridiagonalisation kernel does not fit on an SM");
+        const int grid = std::max(1, std::min(sms, (n + 7) / 8));
+        int nn = n;
+        void *args[] = {&nn, &A, &d, &e, &tau, &Vh, &p};
+        HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_tridiag, dim3(grid), dim3(kTriThreads), args, smem, s));
+        HSIM_LAUNCHED();
+    }
     // 2. eigenvalues
     k_tri_prep<<<1, kTriThreads, 0, s>>>(n, d, e, e2, bounds, d32, e232);
     HSIM_LAUNCHED();
@@ -489,12 +719,24 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     k_tri_invit<<<nclusters, 32, 0, s>>>(n, d, e, bounds, lam, cst, Z, lu, pivf);
     HSIM_LAUNCHED();
     if (detail) cudaEventRecord(t3, s);
-    // 4. back transformation
-    const int per_cta = std::max(1, std::min(8, (int)(kTriSmemMax / ((size_t)n * sizeof(double)))));
-    const size_t bsm = (size_t)per_cta * n * sizeof(double);
-    HSIM_SMEM_LIMIT_ONCE(k_tri_back, kTriSmemMax);
-    k_tri_back<<<cdiv(m, per_cta), kTriThreads, bsm, s>>>(n, m, per_cta, Vh, tau, Z, X, ldx);
-    HSIM_LAUNCHED();
+    // 4. back transformation: a warp per vector held in registers where n <=
+    // 2048, else a few vectors per CTA in shared memory
+    const int warps = std::max(4, std::min(8, (m + sms - 1) / sms));
+    const int cw = (n + 31) / 32;
+    if (cw <= 4) launch_back_warp<4>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else if (cw <= 8) launch_back_warp<8>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else if (cw <= 16) launch_back_warp<16>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else if (cw <= 24) launch_back_warp<24>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else if (cw <= 32) launch_back_warp<32>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else if (cw <= 48) launch_back_warp<48>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else if (cw <= 64) launch_back_warp<64>(s, warps, n, m, Vh, tau, Z, X, ldx);
+    else {
+        const int per_cta = std::max(1, std::min(8, (int)(kTriSmemMax / ((size_t)n * sizeof(double)))));
+        const size_t bsm = (size_t)per_cta * n * sizeof(double);
+        HSIM_SMEM_LIMIT_ONCE(k_tri_back, kTriSmemMax);
+        k_tri_back<<<cdiv(m, per_cta), kTriThreads, bsm, s>>>(n, m, per_cta, Vh, tau, Z, X, ldx);
+        HSIM_LAUNCHED();
+    }
     HSIM_CUDA(cudaMemcpyAsync(evals, lam, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     // the host vector `starts` must outlive the copy above
     HSIM_CUDA(cudaStreamSynchronize(s));

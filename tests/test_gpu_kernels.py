@@ -319,3 +319,23 @@ def test_ritz_graded_spectrum_and_large_size(hs, ctx):
     np.testing.assert_allclose(lam, ev, atol=200 * np.finfo(float).eps * ev.max())
     np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-11)
     np.testing.assert_allclose(S @ X, X * lam[None, :], atol=200 * np.finfo(float).eps * ev.max())
+
+
+@pytest.mark.parametrize("k", [1400, 1700, 2100])
+def test_ritz_large_sizes_all_kernel_variants(hs, ctx, k):
+    # 1400: shared-memory tridiagonalisation with up to 16 rows per CTA and a
+    # register back transformation of 48 entries per lane; 1700: rows no longer
+    # fit in shared memory (global-memory tridiagonalisation), 64 entries per
+    # lane; 2100: both fall back to the shared-memory-vector back transformation
+    rng = np.random.default_rng(k)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    ev = np.sort(rng.uniform(-3.0, 50.0, k))
+    ev[10:14] = ev[10]  # one cluster of four
+    S = Q @ np.diag(ev) @ Q.T
+    S = 0.5 * (S + S.T)
+    lam, X, _ = hs.ritz(ctx, dev(S), dev(np.eye(k)))
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    tol = 200 * np.finfo(float).eps * np.abs(ev).max()
+    np.testing.assert_allclose(lam, ev, atol=tol)
+    np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-11)
+    np.testing.assert_allclose(S @ X, X * lam[None, :], atol=tol)
