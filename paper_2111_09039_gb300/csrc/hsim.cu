@@ -23,6 +23,7 @@
 #include <set>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "common.h"
@@ -106,6 +107,17 @@ struct LevelData {
     std::vector<std::vector<int>> step_cnt, step_maxnf;
     std::vector<int> ea_maxu;
     k::FrontDev fd{};
+    // inverted-factor solves: largest nf and ns per tree height; the
+    // inversion's 32 x 32 diagonal blocks, its block-doubling levels (two
+    // products each) and the product W = L_bs Linv with its copy-back
+    std::vector<int> h_maxnf, h_maxns;
+    DevBuf<int2> inv_blk;
+    int n_inv_blk = 0;
+    std::vector<DevBuf<k::GemmTask>> inv_p1, inv_p2;
+    std::vector<int> inv_n, inv_tiles;
+    DevBuf<k::GemmTask> inv_w, inv_wc;
+    int inv_nw = 0, inv_tw = 0;
+    int64_t inv_scratch = 0;
 };
 
 struct ProlongData {
@@ -138,11 +150,105 @@ struct hsim_hier {
     std::vector<DevBuf<double>> Sv, Mv;  // level values (internal), index tau
     // mixed precision: FP32 factor and FP32 right-hand-side blocks
     DevBuf<float> arena32, dpos32, X32;
+    // inverted-factor solves: 1 / D, the forward result Y, inversion scratch
+    DevBuf<double> dinvf, ysol, invs;
+    DevBuf<float> dinvf32, ysol32, invs32;
     DevBuf<double> rho;
     DevBuf<unsigned char> oz;  // digit slices of the tensor-core products
 };
 
 namespace {
+
+// Tasks of the front inversion (see k_finv.cu): level bs merges the inverted
+// diagonal blocks [a0, a0 + bs) and [a0 + bs, a0 + 2 bs) of every pivot block,
+//   T = B Ainv (into scratch),  B <- -Cinv T,
+// B being the block of L below Ainv and left of Cinv; then W = L_bs Linv.
+void build_inverse_plan(LevelData &L, cudaStream_t s) {
+    const FrontSymbolic &fs = L.fs;
+    auto tiles = [](int M, int N) {
+        return ((M + k::kGemmTile - 1) / k::kGemmTile) * ((N + k::kGemmTile - 1) / k::kGemmTile);
+    };
+    std::vector<int2> blk;
+    int max_ns = 0;
+    for (int t = 0; t < fs.n_nodes; ++t) {
+        for (int b0 = 0; b0 < fs.ns[t]; b0 += 32) blk.push_back(make_int2(t, b0));
+        max_ns = std::max(max_ns, fs.ns[t]);
+    }
+    L.n_inv_blk = (int)blk.size();
+    L.inv_blk.upload(blk.empty() ? std::vector<int2>{make_int2(0, 0)} : blk, s);
+    L.inv_p1.clear();
+    L.inv_p2.clear();
+    L.inv_n.clear();
+    L.inv_tiles.clear();
+    int64_t scratch = 0;
+    for (int bs = 32; bs < max_ns; bs *= 2) {
+        std::vector<k::GemmTask> p1, p2;
+        int nt = 0;
+        int64_t off = 0;
+        for (int t = 0; t < fs.n_nodes; ++t) {
+            const int ns = fs.ns[t], nf = fs.nf[t];
+            const int64_t F = fs.foff[t];
+            for (int a0 = 0; a0 + bs < ns; a0 += 2 * bs) {
+                const int a1 = a0 + bs, a2 = std::min(a0 + 2 * bs, ns), mc = a2 - a1;
+                k::GemmTask x{};
+                x.a = F + (int64_t)a0 * nf + a1, x.lda = nf;
+                x.b = F + (int64_t)a0 * nf + a0, x.ldb = nf;
+                x.c = off, x.ldc = mc;
+                x.M = mc, x.N = bs, x.K = bs, x.flags = k::kGemmBUnitLower, x.tile0 = nt;
+                k::GemmTask y{};
+                y.a = F + (int64_t)a1 * nf + a1, y.lda = nf;
+                y.b = off, y.ldb = mc;
+                y.c = F + (int64_t)a0 * nf + a1, y.ldc = nf;
+                y.M = mc, y.N = bs, y.K = mc, y.flags = k::kGemmAUnitLower | k::kGemmNeg, y.tile0 = nt;
+                p1.push_back(x);
+                p2.push_back(y);
+                nt += tiles(mc, bs);
+                off += (int64_t)mc * bs;
+            }
+        }
+        scratch = std::max(scratch, off);
+        L.inv_n.push_back((int)p1.size());
+        L.inv_tiles.push_back(nt);
+        L.inv_p1.emplace_back();
+        L.inv_p1.back().upload(p1, s);
+        L.inv_p2.emplace_back();
+        L.inv_p2.back().upload(p2, s);
+    }
+    std::vector<k::GemmTask> w, wc;
+    int nt = 0;
+    int64_t off = 0;
+    for (int t = 0; t < fs.n_nodes; ++t) {
+        const int ns = fs.ns[t], nf = fs.nf[t], nb = nf - ns;
+        if (nb <= 0 || ns <= 0) continue;
+        const int64_t F = fs.foff[t];
+        k::GemmTask x{};
+        x.a = F + ns, x.lda = nf;
+        x.b = F, x.ldb = nf;
+        x.c = off, x.ldc = nb;
+        x.M = nb, x.N = ns, x.K = ns, x.flags = k::kGemmBUnitLower, x.tile0 = nt;
+        k::GemmTask c{};
+        c.a = off, c.lda = nb;
+        c.c = F + ns, c.ldc = nf;
+        c.M = nb, c.N = ns, c.tile0 = nt;
+        w.push_back(x);
+        wc.push_back(c);
+        nt += tiles(nb, ns);
+        off += (int64_t)nb * ns;
+    }
+    scratch = std::max(scratch, off);
+    L.inv_nw = (int)w.size();
+    L.inv_tw = nt;
+    L.inv_w.upload(w, s);
+    L.inv_wc.upload(wc, s);
+    L.inv_scratch = scratch;
+    L.h_maxnf.assign(fs.max_height + 1, 0);
+    L.h_maxns.assign(fs.max_height + 1, 0);
+    for (int h = 0; h <= fs.max_height; ++h)
+        for (int t : fs.by_height[h]) {
+            L.h_maxnf[h] = std::max(L.h_maxnf[h], fs.nf[t]);
+            L.h_maxns[h] = std::max(L.h_maxns[h], fs.ns[t]);
+        }
+}
 
 void upload_level(LevelData &L, cudaStream_t s) {
     L.dpat.upload(L.pat_int, s);
@@ -198,15 +304,30 @@ void upload_level(LevelData &L, cudaStream_t s) {
     L.d_ea.upload(ea.empty() ? std::vector<int>{0} : ea, s);
     L.fd = k::FrontDev{L.d_foff.p, L.d_nf.p, L.d_ns.p, L.d_pstart.p, L.d_rows_off.p, L.d_rows.p, L.d_relmap_off.p,
                        L.d_relmap.p};
+    build_inverse_plan(L, s);
 }
 
 // Numeric LDL^T of K = S - mu M on level L (values in internal order), with
 // the factor stored in precision T.  Returns the number of negative pivots
 // (eigenvalues of (S, M) below mu).  Pivots below rel_tol * max|K_ii| count as
 // a breakdown.
+// Inverts the pivot blocks of all fronts in place and forms W = L_bs Linv
+// (the inverted-factor form of k_finv.cu).
+template <typename T>
+void invert_level_t(cudaStream_t s, LevelData &L, T *arena, DevBuf<T> &scr) {
+    scr.reserve((size_t)std::max<int64_t>(L.inv_scratch, 1));
+    k::inv_diag_blocks(s, L.fd, L.inv_blk.p, L.n_inv_blk, arena);
+    for (size_t lv = 0; lv < L.inv_n.size(); ++lv) {
+        k::gemm_tasks<T>(s, L.inv_p1[lv].p, L.inv_n[lv], L.inv_tiles[lv], arena, arena, scr.p);
+        k::gemm_tasks<T>(s, L.inv_p2[lv].p, L.inv_n[lv], L.inv_tiles[lv], arena, scr.p, arena);
+    }
+    k::gemm_tasks<T>(s, L.inv_w.p, L.inv_nw, L.inv_tw, arena, arena, scr.p);
+    k::copy_tasks<T>(s, L.inv_wc.p, L.inv_nw, L.inv_tw, scr.p, arena);
+}
+
 template <typename T>
 int factor_level_t(hsim_ctx *ctx, LevelData &L, const double *S, const double *M, const double *Md, double mu,
-                   DevBuf<T> &arena, DevBuf<T> &dpos, double rel_tol) {
+                   DevBuf<T> &arena, DevBuf<T> &dpos, DevBuf<T> &dinv, DevBuf<T> &scr, double rel_tol) {
     cudaStream_t s = ctx->stream;
     FrontSymbolic &fs = L.fs;
     arena.reserve((size_t)fs.arena);
@@ -238,6 +359,12 @@ int factor_level_t(hsim_ctx *ctx, LevelData &L, const double *S, const double *M
     }
     // all nodes 0..N-1 are listed in d_hnodes grouped by height
     k::front_diag(s, L.fd, L.d_hnodes.p, fs.n_nodes, (const T *)arena.p, dpos.p, flags + 2);
+    if (std::is_same<T, float>::value) {
+        // FP32 factors are solved in the inverted form (see solve_level_t)
+        dinv.reserve((size_t)L.n);
+        k::reciprocal(s, L.n, (const T *)dpos.p, dinv.p);
+        invert_level_t<T>(s, L, arena.p, scr);
+    }
     HSIM_CUDA(cudaMemcpyAsync(ctx->hflags.data(), flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaStreamSynchronize(s));
     if (ctx->hflags[0] != 0)
@@ -246,22 +373,13 @@ int factor_level_t(hsim_ctx *ctx, LevelData &L, const double *S, const double *M
     return ctx->hflags[2];
 }
 
+// K^-1 X in place with the factor walked panel by panel: per tree height the
+// fused kernels for fronts of one panel, else a triangle and an update launch
+// per 32-column panel; then D^-1; then the backward sweep.
 template <typename T>
-void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T *X, int k, int ldx) {
+void solve_level_panels(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T *X, int k, int ldx) {
     cudaStream_t s = ctx->stream;
     const FrontSymbolic &fs = L.fs;
-    // HSIM_TRACE=2: time of every tree height of the forward and backward sweeps
-    const bool detail = trace_level() >= 2;
-    std::vector<cudaEvent_t> ev;
-    auto mark = [&] {
-        if (!detail) return;
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        cudaEventRecord(e, s);
-        ev.push_back(e);
-    };
-    mark();
-    // heights whose fronts are all one panel wide and small: fused kernels
     auto small = [&](int h) { return L.step_cnt[h].size() == 1 && L.step_maxnf[h][0] <= k::kSmallNf; };
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
@@ -275,10 +393,8 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
                 k::solve_fwd_upd(s, L.fd, nodes, cnt, k0, L.step_maxnf[h][kst] - k0 - 1, arena, k, X, ldx);
             }
         }
-        mark();
     }
     k::solve_diag(s, L.n, k, dpos, X, ldx);
-    mark();
     for (int h = fs.max_height; h >= 0; --h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         if (small(h)) {
@@ -291,6 +407,47 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
                 k::solve_bwd_tri(s, L.fd, nodes, cnt, k0, arena, k, X, ldx);
             }
         }
+    }
+}
+
+// K^-1 X in place (X: n x k, leading dimension ldx, internal order).
+// FP32 factors are in the inverted form: one forward product per tree height
+// upwards, one backward product per height downwards (k_finv.cu), Y holding
+// the forward result.  FP64 factors are solved panel by panel (k_front.cu):
+// at the FP64 rate of this GPU the inverted form's extra work on the
+// triangular blocks costs more than the launch chains it removes.
+template <typename T>
+void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, const T *dinv, DevBuf<T> &Y, T *X,
+                   int k, int ldx) {
+    cudaStream_t s = ctx->stream;
+    const FrontSymbolic &fs = L.fs;
+    if (!std::is_same<T, float>::value) {
+        solve_level_panels(ctx, L, arena, dpos, X, k, ldx);
+        return;
+    }
+    Y.reserve((size_t)L.n * ldx);
+    // HSIM_TRACE=2: time of every tree height of the forward and backward sweeps
+    const bool detail = trace_level() >= 2;
+    std::vector<cudaEvent_t> ev;
+    auto mark = [&] {
+        if (!detail) return;
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+    };
+    mark();
+    for (int h = 0; h <= fs.max_height; ++h) {
+        const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
+        const int cnt = (int)(L.hnodes_off[h + 1] - L.hnodes_off[h]);
+        k::solve_fwd_inv(s, L.fd, nodes, cnt, L.h_maxnf[h], arena, k, X, Y.p, ldx);
+        mark();
+    }
+    mark();  // the diagonal is applied inside the backward products
+    for (int h = fs.max_height; h >= 0; --h) {
+        const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
+        const int cnt = (int)(L.hnodes_off[h + 1] - L.hnodes_off[h]);
+        k::solve_bwd_inv(s, L.fd, nodes, cnt, L.h_maxns[h], arena, dinv, k, X, Y.p, ldx);
         mark();
     }
     if (detail) {
@@ -301,13 +458,10 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
             float a = 0, b = 0;
             cudaEventElapsedTime(&a, ev[h], ev[h + 1]);
             cudaEventElapsedTime(&b, ev[2 * H - h], ev[2 * H - h + 1]);
-            line += " h" + std::to_string(h) + "(" + std::to_string(L.hnodes_off[h + 1] - L.hnodes_off[h]) + " fronts, " +
-                    std::to_string(L.step_cnt[h].size()) + " steps) " + std::to_string(a).substr(0, 5) + "/" +
+            line += " h" + std::to_string(h) + "(" + std::to_string(L.hnodes_off[h + 1] - L.hnodes_off[h]) +
+                    " fronts, nf<=" + std::to_string(L.h_maxnf[h]) + ") " + std::to_string(a).substr(0, 5) + "/" +
                     std::to_string(b).substr(0, 5);
         }
-        float dg = 0;
-        cudaEventElapsedTime(&dg, ev[H], ev[H + 1]);
-        line += " diag " + std::to_string(dg).substr(0, 5);
         std::fprintf(stderr, "%s\n", line.c_str());
         for (auto e : ev) cudaEventDestroy(e);
     }
@@ -315,11 +469,11 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, T
 
 int factor_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, const double *S, const double *M, const double *Md,
                  double mu) {
-    return factor_level_t<double>(ctx, L, S, M, Md, mu, H->arena, H->dpos, 1e-13);
+    return factor_level_t<double>(ctx, L, S, M, Md, mu, H->arena, H->dpos, H->dinvf, H->invs, 1e-13);
 }
 
 void solve_level(hsim_ctx *ctx, hsim_hier *H, LevelData &L, double *X, int k, int ldx) {
-    solve_level_t<double>(ctx, L, H->arena.p, H->dpos.p, X, k, ldx);
+    solve_level_t<double>(ctx, L, H->arena.p, H->dpos.p, H->dinvf.p, H->ysol, X, k, ldx);
 }
 
 int subspace_q(int p, const hsim_options &o) {
@@ -508,7 +662,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
         const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
         Timer tf(s);
-        int negp = mixed ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, 1e-7)
+        int negp = mixed ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, H->dinvf32, H->invs32, 1e-7)
                          : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
         inf.ms_factor += tf.stop();
         if (mixed) {
@@ -528,7 +682,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         auto correction_step = [&](const double *X, const double *SX, const double *MX, const double *num,
                                    const double *den, double *Y, int a) {
             k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->X32.p, q32);
-            solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->X32.p, a, q32);
+            solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->dinvf32.p, H->ysol32, H->X32.p, a, q32);
             k::sub_f2d(s, n, a, X, q, H->X32.p, q32, Y, q);
         };
         if (trace_on())

@@ -1,0 +1,449 @@
+// Inverted-factor form of the multifrontal LDL^T for the many-right-hand-side
+// solves of the inverse iterations (Alg. 1, the solve with S - mu M).
+//
+// After the numeric factorisation front t holds, column-major nf x nf, the
+// panel [L_ss; L_bs] (unit lower pivot block, rows of the ancestors) with D on
+// the diagonal.  Walking the pivot block panel by panel makes the solves a
+// chain of small dependent launches; instead every pivot block is inverted once
+// per factorisation and the ancestor block multiplied by the inverse,
+//     Linv = L_ss^-1   (unit lower, stored over L_ss; the diagonal keeps D)
+//     W    = L_bs Linv (stored over L_bs),
+// so that one tree height of the forward and of the backward substitution is
+// one batched product each:
+//     forward:  Y_s = Linv X_s,  X_b -= W X_s
+//     backward: X_s = Linv^T D^-1 Y_s - W^T X_b
+// (X_s: pivot rows of the front, contiguous; X_b: its ancestor rows).  The
+// inversion doubles the block size per level,
+//     [A 0; B C]^-1 = [A^-1 0; -C^-1 (B A^-1)  C^-1],
+// starting from inverted 32 x 32 diagonal blocks; each level is two batched
+// products over all fronts.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.h"
+#include "kernels.h"
+
+namespace hsim {
+namespace k {
+
+namespace {
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---- inversion ---------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_inv_diag32(FrontDev fd, const int2 *__restrict__ blk, T *__restrict__ arena) {
+    __shared__ T Ls[32][33];  // Ls[r][c] = L(b0 + r, b0 + c), r > c
+    __shared__ T Xs[32][33];  // inverse, same indexing
+    const int2 tb = blk[blockIdx.x];
+    const int t = tb.x, b0 = tb.y;
+    const int nf = fd.nf[t], ns = fd.ns[t];
+    const int kb = min(32, ns - b0);
+    T *F = arena + fd.foff[t];
+    const int l = threadIdx.x;
+    // lane l loads row l (coalesced along the column), then solves column l
+    for (int c = 0; c < kb; ++c) Ls[l][c] = (l < kb && l > c) ? F[(int64_t)(b0 + c) * nf + b0 + l] : T(0);
+    __syncwarp();
+    if (l < kb) {
+        Xs[l][l] = T(1);
+        for (int r = l + 1; r < kb; ++r) {
+            T s = Ls[r][l];
+            for (int j = l + 1; j < r; ++j) s += Ls[r][j] * Xs[j][l];
+            Xs[r][l] = -s;
+        }
+    }
+    __syncwarp();
+    for (int c = 0; c < kb; ++c)
+        if (l < kb && l > c) F[(int64_t)(b0 + c) * nf + b0 + l] = Xs[l][c];
+}
+
+template <typename T>
+__device__ __forceinline__ T tri_load(const T *p, int64_t idx, int i, int k, bool unit_lower) {
+    if (!unit_lower) return p[idx];
+    return i > k ? p[idx] : (i == k ? T(1) : T(0));
+}
+
+__device__ __forceinline__ int find_task(const GemmTask *tasks, int ntasks, int tile) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].tile0 <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_tasks(const GemmTask *__restrict__ tasks, int ntasks,
+                                                    const T *__restrict__ Ab, const T *__restrict__ Bb,
+                                                    T *__restrict__ Cb) {
+    constexpr int BT = kGemmTile, BK = 16;
+    __shared__ T As[BK][BT + 1];
+    __shared__ T Bs[BK][BT + 1];
+    const GemmTask tk = tasks[find_task(tasks, ntasks, blockIdx.x)];
+    const int local = blockIdx.x - tk.tile0;
+    const int ntn = (tk.N + BT - 1) / BT;
+    const int m0 = (local / ntn) * BT, n0 = (local % ntn) * BT;
+    const bool ua = tk.flags & kGemmAUnitLower, ub = tk.flags & kGemmBUnitLower;
+    const T *A = Ab + tk.a, *B = Bb + tk.b;
+    T *C = Cb + tk.c;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // tx: rows, ty: columns
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    // a unit lower A has A(i, k) = 0 for k > i; a unit lower B has B(k, j) = 0 for k < j
+    const int kbeg = ub ? (n0 / BK) * BK : 0;
+    const int kend = ua ? min(tk.K, m0 + BT) : tk.K;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BK * BT; idx += 256) {
+            const int i = idx % BT, kk = idx / BT;
+            const int gi = m0 + i, gk = k0 + kk;
+            As[kk][i] = (gi < tk.M && gk < tk.K) ? tri_load(A, (int64_t)gk * tk.lda + gi, gi, gk, ua) : T(0);
+        }
+        for (int idx = threadIdx.x; idx < BK * BT; idx += 256) {
+            const int kk = idx % BK, j = idx / BK;
+            const int gk = k0 + kk, gj = n0 + j;
+            Bs[kk][j] = (gk < tk.K && gj < tk.N) ? tri_load(B, (int64_t)gj * tk.ldb + gk, gk, gj, ub) : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[kk][tx + 16 * u];
+                b[u] = Bs[kk][ty + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+    const T sg = (tk.flags & kGemmNeg) ? T(-1) : T(1);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = m0 + tx + 16 * u;
+        if (i >= tk.M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = n0 + ty + 16 * v;
+            if (j < tk.N) C[(int64_t)j * tk.ldc + i] = sg * acc[u][v];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy_tasks(const GemmTask *__restrict__ tasks, int ntasks,
+                                                    const T *__restrict__ Ab, T *__restrict__ Cb) {
+    constexpr int BT = kGemmTile;
+    const GemmTask tk = tasks[find_task(tasks, ntasks, blockIdx.x)];
+    const int local = blockIdx.x - tk.tile0;
+    const int ntn = (tk.N + BT - 1) / BT;
+    const int m0 = (local / ntn) * BT, n0 = (local % ntn) * BT;
+    for (int idx = threadIdx.x; idx < BT * BT; idx += 256) {
+        const int i = m0 + idx % BT, j = n0 + idx / BT;
+        if (i < tk.M && j < tk.N) Cb[tk.c + (int64_t)j * tk.ldc + i] = Ab[tk.a + (int64_t)j * tk.lda + i];
+    }
+}
+
+template <typename T>
+__global__ void k_reciprocal(int n, const T *__restrict__ x, T *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = T(1) / x[i];
+}
+
+// ---- solves ---------------------------------------------------------------
+
+// four consecutive values of row `row` from column c (zero past k or for an
+// invalid row)
+template <typename T>
+__device__ __forceinline__ void load4(T (&d)[4], const T *X, int64_t row, bool ok, int c, int k, int ldx, bool vec) {
+    const T *p = X + row * ldx + c;
+    if (ok && vec && c + 4 <= k) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p);
+            d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
+        } else {
+            const double2 v0 = reinterpret_cast<const double2 *>(p)[0], v1 = reinterpret_cast<const double2 *>(p)[1];
+            d[0] = v0.x, d[1] = v0.y, d[2] = v1.x, d[3] = v1.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) d[v] = (ok && c + v < k) ? p[v] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T *p, const T (&a)[4], int avail, bool vec) {
+    if (vec && avail >= 4) {
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
+        } else {
+            reinterpret_cast<double2 *>(p)[0] = make_double2(a[0], a[1]);
+            reinterpret_cast<double2 *>(p)[1] = make_double2(a[2], a[3]);
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (v < avail) p[v] = a[v];
+    }
+}
+
+__device__ __forceinline__ void sub4_atomic(float *x, const float (&a)[4], int avail, bool vec) {
+    if (vec && avail >= 4) {
+        atomicAdd(reinterpret_cast<float4 *>(x), make_float4(-a[0], -a[1], -a[2], -a[3]));
+    } else {
+        for (int v = 0; v < 4 && v < avail; ++v) atomicAdd(x + v, -a[v]);
+    }
+}
+__device__ __forceinline__ void sub4_atomic(double *x, const double (&a)[4], int avail, bool) {
+    for (int v = 0; v < 4 && v < avail; ++v) atomicAdd(x + v, -a[v]);
+}
+
+// four consecutive shared-memory values (16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void sts4(T *p, const T (&b)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(b[0], b[1], b[2], b[3]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(b[0], b[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(b[2], b[3]);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void lds4(T (&b)[4], const T *p) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        b[0] = v.x, b[1] = v.y, b[2] = v.z, b[3] = v.w;
+    } else {
+        const double2 v0 = reinterpret_cast<const double2 *>(p)[0], v1 = reinterpret_cast<const double2 *>(p)[1];
+        b[0] = v0.x, b[1] = v0.y, b[2] = v1.x, b[3] = v1.y;
+    }
+}
+
+template <typename T>
+__host__ __device__ constexpr int inv_cols() { return sizeof(T) == 4 ? 128 : 64; }  // columns of a solve tile
+
+// CTA (front of the height, 64-row tile of its nf rows, column tile): rows
+// r < ns of the product go to Y (store), rows r >= ns to the ancestors' rows
+// of X (atomic subtraction: siblings share them).
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_fwd_inv(FrontDev fd, const int *__restrict__ nodes, int rt_per,
+                                                       const T *__restrict__ arena, int k, T *__restrict__ X,
+                                                       T *__restrict__ Y, int ldx, bool vec) {
+    constexpr int BM = 64, BK = 32, BN = inv_cols<T>();
+    constexpr int CG = BN / 4, RGS = 256 / CG, RPT = BM / RGS;
+    __shared__ __align__(16) T As[BK][BM];
+    __shared__ __align__(16) T Bs[BK][BN];
+    const int t = nodes[blockIdx.x / rt_per];
+    const int r0 = (blockIdx.x % rt_per) * BM;
+    const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
+    if (r0 >= nf || ns == 0) return;
+    const int c0 = blockIdx.y * BN;
+    const T *F = arena + fd.foff[t];
+    const int tid = threadIdx.x, cg = (tid % CG) * 4, rg = tid / CG;
+    T acc[RPT][4];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    // Linv(r, j) = 0 for j > r: a tile inside the pivot rows stops at its last row
+    const int kend = (r0 + BM <= ns) ? r0 + BM : ns;
+    for (int k0 = 0; k0 < kend; k0 += BK) {
+        for (int idx = tid; idx < BK * BM; idx += 256) {
+            const int i = idx % BM, kk = idx / BM;
+            const int r = r0 + i, j = k0 + kk;
+            T a = T(0);
+            if (r < nf && j < ns) a = (r >= ns || r > j) ? F[(int64_t)j * nf + r] : (r == j ? T(1) : T(0));
+            As[kk][i] = a;
+        }
+        for (int idx = tid; idx < BK * CG; idx += 256) {
+            const int kk = idx / CG, c = (idx % CG) * 4;
+            T b[4];
+            load4(b, X, (int64_t)ps + k0 + kk, k0 + kk < ns, c0 + c, k, ldx, vec);
+            sts4(&Bs[kk][c], b);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+            T b[4], a[RPT];
+            lds4(b, &Bs[kk][cg]);
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) a[u] = As[kk][rg * RPT + u];
+#pragma unroll
+            for (int u = 0; u < RPT; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+    const int *rows = fd.rows + fd.rows_off[t];
+    const int avail = k - c0 - cg;
+    if (avail <= 0) return;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int r = r0 + rg * RPT + u;
+        if (r >= nf) continue;
+        if (r < ns) store4(Y + (int64_t)(ps + r) * ldx + c0 + cg, acc[u], avail, vec);
+        else sub4_atomic(X + (int64_t)rows[r] * ldx + c0 + cg, acc[u], avail, vec);
+    }
+}
+
+// CTA (front of the height, BM-row tile of its ns pivot rows, column tile);
+// K runs over the front's rows: pivots (Linv^T, Y scaled by D^-1), then the
+// ancestors' rows (-W^T, final X rows gathered).
+template <typename T, int BM>
+__global__ void __launch_bounds__(256) k_solve_bwd_inv(FrontDev fd, const int *__restrict__ nodes, int rt_per,
+                                                       const T *__restrict__ arena, const T *__restrict__ dinv, int k,
+                                                       T *__restrict__ X, const T *__restrict__ Y, int ldx, bool vec) {
+    constexpr int BK = 32, BN = inv_cols<T>();
+    constexpr int CG = BN / 4, RGS = 256 / CG, RPT = BM / RGS;
+    static_assert(RPT >= 1, "tile too small");
+    __shared__ __align__(16) T As[BK][BM + 1];
+    __shared__ __align__(16) T Bs[BK][BN];
+    const int t = nodes[blockIdx.x / rt_per];
+    const int i0 = (blockIdx.x % rt_per) * BM;
+    const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
+    if (i0 >= ns) return;
+    const int c0 = blockIdx.y * BN;
+    const T *F = arena + fd.foff[t];
+    const int *rows = fd.rows + fd.rows_off[t];
+    const int tid = threadIdx.x, cg = (tid % CG) * 4, rg = tid / CG;
+    T acc[RPT][4];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    // Linv^T(i, r) = Linv(r, i) = 0 for r < i: start at the tile's first row
+    for (int k0 = (i0 / BK) * BK; k0 < nf; k0 += BK) {
+        for (int idx = tid; idx < BK * BM; idx += 256) {
+            const int kk = idx % BK, ii = idx / BK;
+            const int i = i0 + ii, r = k0 + kk;
+            T a = T(0);
+            if (i < ns && r < nf) {
+                if (r >= ns) a = -F[(int64_t)i * nf + r];
+                else a = r > i ? F[(int64_t)i * nf + r] : (r == i ? T(1) : T(0));
+            }
+            As[kk][ii] = a;
+        }
+        for (int idx = tid; idx < BK * CG; idx += 256) {
+            const int kk = idx / CG, c = (idx % CG) * 4;
+            const int r = k0 + kk;
+            T b[4];
+            if (r < ns) {
+                load4(b, Y, (int64_t)ps + r, true, c0 + c, k, ldx, vec);
+                const T di = dinv[ps + r];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) b[v] *= di;
+            } else {
+                load4(b, X, r < nf ? (int64_t)rows[r] : 0, r < nf, c0 + c, k, ldx, vec);
+            }
+            sts4(&Bs[kk][c], b);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+            T b[4], a[RPT];
+            lds4(b, &Bs[kk][cg]);
+#pragma unroll
+            for (int u = 0; u < RPT; ++u) a[u] = As[kk][rg * RPT + u];
+#pragma unroll
+            for (int u = 0; u < RPT; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+    const int avail = k - c0 - cg;
+    if (avail <= 0) return;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int i = i0 + rg * RPT + u;
+        if (i < ns) store4(X + (int64_t)(ps + i) * ldx + c0 + cg, acc[u], avail, vec);
+    }
+}
+
+template <typename T>
+bool aligned16(const T *p, int ldx) {
+    return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((size_t)ldx * sizeof(T)) % 16 == 0;
+}
+
+}  // namespace
+
+template <typename T>
+void inv_diag_blocks(cudaStream_t s, const FrontDev &fd, const int2 *blk, int nblk, T *arena) {
+    if (nblk <= 0) return;
+    k_inv_diag32<T><<<nblk, 32, 0, s>>>(fd, blk, arena);
+    HSIM_LAUNCHED();
+}
+
+template <typename T>
+void gemm_tasks(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles, const T *Ab, const T *Bb, T *Cb) {
+    if (ntasks <= 0 || tiles <= 0) return;
+    k_gemm_tasks<T><<<tiles, 256, 0, s>>>(tasks, ntasks, Ab, Bb, Cb);
+    HSIM_LAUNCHED();
+}
+
+template <typename T>
+void copy_tasks(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles, const T *Ab, T *Cb) {
+    if (ntasks <= 0 || tiles <= 0) return;
+    k_copy_tasks<T><<<tiles, 256, 0, s>>>(tasks, ntasks, Ab, Cb);
+    HSIM_LAUNCHED();
+}
+
+template <typename T>
+void reciprocal(cudaStream_t s, int n, const T *x, T *y) {
+    if (n <= 0) return;
+    k_reciprocal<T><<<cdiv(n, 256), 256, 0, s>>>(n, x, y);
+    HSIM_LAUNCHED();
+}
+
+template <typename T>
+void solve_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, const T *arena,
+                   int k, T *X, T *Y, int ldx) {
+    if (n_nodes <= 0 || k <= 0 || max_nf <= 0) return;
+    const int rt = (max_nf + 63) / 64;
+    const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
+    k_solve_fwd_inv<T><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, 0, s>>>(
+        fd, nodes, rt, arena, k, X, Y, ldx, vec);
+    HSIM_LAUNCHED();
+}
+
+template <typename T>
+void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_ns, const T *arena,
+                   const T *dinv, int k, T *X, const T *Y, int ldx) {
+    if (n_nodes <= 0 || k <= 0 || max_ns <= 0) return;
+    const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
+    const dim3 grid_small((unsigned)((int64_t)n_nodes * ((max_ns + 31) / 32)), cdiv(k, inv_cols<T>()));
+    if (max_ns <= 32 || sizeof(T) == 8) {
+        // 32 pivot rows per tile (FP64: 64 columns x 32 rows keeps RPT = 2)
+        k_solve_bwd_inv<T, 32><<<grid_small, 256, 0, s>>>(fd, nodes, (max_ns + 31) / 32, arena, dinv, k, X, Y, ldx,
+                                                         vec);
+    } else {
+        const int rt = (max_ns + 63) / 64;
+        k_solve_bwd_inv<T, 64><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, 0, s>>>(
+            fd, nodes, rt, arena, dinv, k, X, Y, ldx, vec);
+    }
+    HSIM_LAUNCHED();
+}
+
+#define HSIM_FINV_INSTANTIATE(T)                                                                                    \
+    template void inv_diag_blocks<T>(cudaStream_t, const FrontDev &, const int2 *, int, T *);                     \
+    template void gemm_tasks<T>(cudaStream_t, const GemmTask *, int, int, const T *, const T *, T *);             \
+    template void copy_tasks<T>(cudaStream_t, const GemmTask *, int, int, const T *, T *);                        \
+    template void reciprocal<T>(cudaStream_t, int, const T *, T *);                                               \
+    template void solve_fwd_inv<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, T *, \
+                                   int);                                                                          \
+    template void solve_bwd_inv<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, const T *, int, \
+                                   T *, const T *, int);
+HSIM_FINV_INSTANTIATE(float)
+HSIM_FINV_INSTANTIATE(double)
+
+}  // namespace k
+}  // namespace hsim

@@ -129,6 +129,45 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag(int n, double *__restri
     }
 }
 
+// Threads of k_tridiag_rows: one warp per SM sub-partition.  FP64 issues at a
+// 64th of the FP32 rate here, so every FP64 instruction that all warps repeat
+// (reductions, the reflector's scalars) costs its full issue time once per
+// warp on a sub-partition; with one warp each that cost is paid once.
+constexpr int kTrdThreads = 128;
+
+// sum over the block (kTrdThreads threads); result in all threads
+__device__ __forceinline__ double block_sum128(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();  // red may still be read from the previous call
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    return (red[0] + red[1]) + (red[2] + red[3]);
+}
+
+// Sums over the 32 lanes of RMAX values per lane by halving: at the step with
+// offset o every lane keeps the half of its values selected by its lane bit o
+// and adds the partner's copy of that half, so the adds per lane are RMAX - 1
+// plus log2(32 / RMAX) instead of 5 RMAX.  Afterwards lane l holds the total
+// of value l / (32 / RMAX).
+template <int RMAX>
+__device__ __forceinline__ double warp_sum_rows(double (&a)[RMAX], int lane) {
+    int off = 16;
+#pragma unroll
+    for (int h = RMAX / 2; h >= 1; h /= 2) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double keep = up ? a[i + h] : a[i];
+            const double send = up ? a[i] : a[i + h];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+        off >>= 1;
+    }
+    double s = a[0];
+    for (; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    return s;
+}
+
 // Tridiagonalisation with the matrix resident in shared memory.  CTA b owns
 // the rows b, b + G, b + 2G, ... (full length n), so the product p = t A22 v
 // and the rank-2 update of every column read and write only shared memory,
@@ -140,10 +179,11 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag(int n, double *__restri
 // column k+1.  The arithmetic per column is that of k_tridiag.
 // Shared memory: R n (owned rows, R = ceil(n / G) <= RMAX) + 4 n doubles.
 template <int RMAX>
-__global__ void __launch_bounds__(kTriThreads) k_tridiag_rows(int n, const double *__restrict__ A, double *__restrict__ d,
+__global__ void __launch_bounds__(kTrdThreads) k_tridiag_rows(int n, const double *__restrict__ A, double *__restrict__ d,
                                                             double *__restrict__ e, double *__restrict__ tau,
                                                             double *__restrict__ Vh, double *__restrict__ pbuf,
                                                             double *__restrict__ rbuf) {
+    constexpr int NW = kTrdThreads / 32;
     cg::grid_group grid = cg::this_grid();
     extern __shared__ double sm[];
     const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -152,30 +192,32 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag_rows(int n, const doubl
     double *rows = sm;                           // Rmax x n
     double *xs = rows + (size_t)Rmax * n;        // row k: xs[i] = A[k, k + i]
     double *v = xs + n, *vp = v + n, *w = vp + n;  // reflector of column k, of column k - 1; w of column k - 1
-    __shared__ double red[kTriThreads / 32];
-    __shared__ double redr[kTriThreads / 32][RMAX];
+    __shared__ double red[NW];
+    __shared__ double redr[NW][RMAX];
     for (int i = 0; i < R; ++i) {
         const double *src = A + (size_t)(b + i * G) * n;
-        for (int j = tid; j < n; j += kTriThreads) rows[(size_t)i * n + j] = src[j];
+        for (int j = tid; j < n; j += kTrdThreads) rows[(size_t)i * n + j] = src[j];
     }
-    for (int j = tid; j < n; j += kTriThreads) xs[j] = A[j];
+    for (int j = tid; j < n; j += kTrdThreads) xs[j] = A[j];
     __syncthreads();
     for (int k = 0; k + 1 < n; ++k) {
         const int L = n - k - 1;
         // reflector of y = xs[1 .. L] (column k below the diagonal)
         double part = 0.0;
-        for (int i = 1 + tid; i < L; i += kTriThreads) part += xs[1 + i] * xs[1 + i];
-        const double sigma = block_sum(part, red);
+        for (int i = 1 + tid; i < L; i += kTrdThreads) part = fma(xs[1 + i], xs[1 + i], part);
+        const double sigma = block_sum128(part, red);
         const double x0 = xs[1];
         double beta = x0, t = 0.0, scale = 0.0;
         if (sigma != 0.0) {
-            const double mu = sqrt(x0 * x0 + sigma);
+            const double mu = sqrt(fma(x0, x0, sigma));
             beta = x0 >= 0.0 ? -mu : mu;
-            t = (beta - x0) / beta;
-            scale = 1.0 / (x0 - beta);
+            // t = (beta - x0) / beta and scale = 1 / (x0 - beta) from one division
+            const double dlt = x0 - beta, inv = 1.0 / (beta * dlt);
+            t = -dlt * dlt * inv;
+            scale = beta * inv;
         }
-        for (int i = tid; i < L; i += kTriThreads) {
-            const double vi = i == 0 ? 1.0 : (t != 0.0 ? xs[1 + i] * scale : 0.0);
+        for (int i = tid; i < L; i += kTrdThreads) {
+            const double vi = i == 0 ? 1.0 : xs[1 + i] * scale;
             v[i] = vi;
             if (b == 0) Vh[(size_t)k * n + k + 1 + i] = vi;
         }
@@ -192,7 +234,7 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag_rows(int n, const doubl
 #pragma unroll
         for (int i = 0; i < RMAX; ++i) acc[i] = 0.0;
         double *rb = rbuf + (size_t)(k & 1) * n;
-        for (int j = tid; j < L; j += kTriThreads) {
+        for (int j = tid; j < L; j += kTrdThreads) {
             const double vj = v[j];
             const double vpj = k > 0 ? vp[j + 1] : 0.0, wpj = k > 0 ? w[j + 1] : 0.0;
 #pragma unroll
@@ -203,38 +245,34 @@ __global__ void __launch_bounds__(kTriThreads) k_tridiag_rows(int n, const doubl
                 double x = *a;
                 if (k > 0) x -= vp[r - k] * wpj + w[r - k] * vpj;
                 *a = x;
-                acc[i] += x * vj;
+                acc[i] = fma(x, vj, acc[i]);
                 if (r == k + 1) rb[j] = x;
             }
         }
-#pragma unroll
-        for (int i = 0; i < RMAX; ++i) {
-            if (i < i0 || i >= R) continue;
-            double s = acc[i];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) redr[wid][i] = s;
-        }
+        const double rs = warp_sum_rows<RMAX>(acc, lane);
+        if ((lane & (32 / RMAX - 1)) == 0) redr[wid][lane / (32 / RMAX)] = rs;
         __syncthreads();
         if (tid >= i0 && tid < R) {
             double s = 0.0;
 #pragma unroll
-            for (int q = 0; q < kTriThreads / 32; ++q) s += redr[q][tid];
+            for (int q = 0; q < NW; ++q) s += redr[q][tid];
             pbuf[(size_t)(k & 1) * n + (b + tid * G - k - 1)] = t * s;
         }
         grid.sync();
         // w = p - (t/2)(p.v) v, then row k + 1 after the update of column k
         const double *pb = pbuf + (size_t)(k & 1) * n;
         double pv = 0.0;
-        for (int j = tid; j < L; j += kTriThreads) {
+        for (int j = tid; j < L; j += kTrdThreads) {
             const double pj = __ldcg(pb + j);
+            xs[j] = __ldcg(rb + j);
             w[j] = pj;
-            pv += pj * v[j];
+            pv = fma(pj, v[j], pv);
         }
-        const double K = 0.5 * t * block_sum(pv, red);
-        for (int j = tid; j < L; j += kTriThreads) w[j] -= K * v[j];
+        const double K = 0.5 * t * block_sum128(pv, red);
+        for (int j = tid; j < L; j += kTrdThreads) w[j] -= K * v[j];
         __syncthreads();
         const double w0 = w[0];
-        for (int j = tid; j < L; j += kTriThreads) xs[j] = __ldcg(rb + j) - (v[0] * w[j] + w0 * v[j]);
+        for (int j = tid; j < L; j += kTrdThreads) xs[j] -= v[0] * w[j] + w0 * v[j];
         double *tmp = vp;
         vp = v;
         v = tmp;
@@ -386,60 +424,86 @@ __device__ __forceinline__ int sturm_count32(int n, const float *__restrict__ d,
     return c;
 }
 
-// lambda_i, i < m: one warp per eigenvalue, 32-point multisection (each lane
-// counts at one interior point; the bracket shrinks 33-fold per round).  FP32
-// rounds first (the FP32 pipe is ~60x the FP64 pipe) down to 1e-5 ||T||, then
-// the bracket is checked with FP64 counts and widened until it holds, then
-// FP64 rounds to full precision.
-__global__ void k_tri_bisect(int n, int m, const double *__restrict__ d, const double *__restrict__ e2,
+// lambda_i, i < m: G eigenvalues per warp, L = 32 / G lanes each (L >= 2),
+// multisection with L interior points (the bracket shrinks (L + 1)-fold per
+// round).  FP32 rounds first (the FP32 pipe is ~60x the FP64 pipe) down to
+// 1e-5 ||T||, then the bracket is checked with FP64 counts and widened until
+// it holds, then FP64 rounds to full precision.  The FP64 rounds dominate and
+// the FP64 unit is shared by the warps of an SM, so the launch uses about one
+// warp per SM with G = ceil(m / SMs): fewer points per eigenvalue cost more
+// rounds but much less FP64 work in total.
+__device__ __forceinline__ int group_le(bool le, int gbase, int L) {
+    const unsigned bal = __ballot_sync(0xffffffffu, le);
+    const unsigned g = (L == 32) ? bal : (bal >> gbase) & ((1u << L) - 1u);
+    // lanes 0..j-1 of the group have count <= i (monotone up to rounding): take the highest
+    return g == 0 ? 0 : 32 - __clz(g);
+}
+
+__global__ void k_tri_bisect(int n, int m, int G, const double *__restrict__ d, const double *__restrict__ e2,
                              const float *__restrict__ d32, const float *__restrict__ e232,
                              const double *__restrict__ bounds, double *__restrict__ lam) {
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (i >= m) return;  // uniform per warp
+    const int lane = threadIdx.x & 31, warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int L = 32 / G, gi = lane / L, li = lane % L, gbase = gi * L;
+    const int i = warp * G + gi;
+    const bool valid = gi < G && i < m;
+    if (warp * G >= m) return;  // uniform per warp
     const double glo = bounds[0], ghi = bounds[1], tn = bounds[2], pivmin = bounds[3];
+    const double sect = 1.0 / (L + 1);
     double lo = glo, hi = ghi;
     // FP32 multisection
     const float pivmin32 = fmaxf((float)fmin(pivmin / DBL_MIN * FLT_MIN, 1e30), FLT_MIN / FLT_EPSILON);
-    for (int round = 0; round < 12 && hi - lo > 1e-5 * tn; ++round) {
-        const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-        const bool le = sturm_count32(n, d32, e232, (float)x, pivmin32) <= i;
-        const unsigned bal = __ballot_sync(0xffffffffu, le);
-        // lanes 0..j-1 have count <= i (monotone up to FP32 noise): take the highest
-        const int nle = bal == 0 ? 0 : 32 - __clz(bal);
-        const double nlo = nle > 0 ? lo + (hi - lo) * nle / 33.0 : lo;
-        const double nhi = nle < 32 ? lo + (hi - lo) * (nle + 1) / 33.0 : hi;
-        lo = nlo;
-        hi = nhi;
+    for (int round = 0; round < 64; ++round) {
+        const bool go = valid && hi - lo > 1e-5 * tn;
+        if (!__any_sync(0xffffffffu, go)) break;
+        const double x = lo + (hi - lo) * ((li + 1) * sect);
+        const bool le = go && sturm_count32(n, d32, e232, (float)x, pivmin32) <= i;
+        const int nle = group_le(le, gbase, L);
+        if (go) {
+            const double nlo = nle > 0 ? lo + (hi - lo) * (nle * sect) : lo;
+            const double nhi = nle < L ? lo + (hi - lo) * ((nle + 1) * sect) : hi;
+            lo = nlo;
+            hi = nhi;
+        }
     }
     // FP64 check: count(lo) <= i < count(hi), widen otherwise
     double w = fmax(hi - lo, 1e-5 * tn);
+    bool checked = !valid;
     for (int t = 0; t < 64; ++t) {
-        const double x = lane == 0 ? lo : hi;
-        const int c = (lane < 2) ? sturm_count(n, d, e2, x, pivmin) : 0;
-        const int clo = __shfl_sync(0xffffffffu, c, 0), chi = __shfl_sync(0xffffffffu, c, 1);
-        const bool okl = clo <= i || lo <= glo, okh = chi > i || hi >= ghi;
-        if (okl && okh) break;
-        if (!okl) lo = fmax(glo, lo - w);
-        if (!okh) hi = fmin(ghi, hi + w);
-        w *= 2.0;
+        if (!__any_sync(0xffffffffu, !checked)) break;
+        const double x = li == 0 ? lo : hi;
+        const int c = (!checked && li < 2) ? sturm_count(n, d, e2, x, pivmin) : 0;
+        const int clo = __shfl_sync(0xffffffffu, c, gbase), chi = __shfl_sync(0xffffffffu, c, gbase + 1);
+        if (!checked) {
+            const bool okl = clo <= i || lo <= glo, okh = chi > i || hi >= ghi;
+            if (okl && okh) {
+                checked = true;
+            } else {
+                if (!okl) lo = fmax(glo, lo - w);
+                if (!okh) hi = fmin(ghi, hi + w);
+                w *= 2.0;
+            }
+        }
     }
     // FP64 multisection to 2 eps max(|lambda|, ||T||): the absolute accuracy
     // of a dense symmetric eigensolve (a relative stop alone would drive the
     // bracket of an eigenvalue at zero down to pivmin)
     const double atol = 2.0 * DBL_EPSILON * tn + pivmin;
-    for (int round = 0; round < 40; ++round) {
+    for (int round = 0; round < 200; ++round) {
         const double mid = 0.5 * (lo + hi);
-        if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + atol || mid == lo || mid == hi) break;
-        const double x = lo + (hi - lo) * (lane + 1) / 33.0;
-        const bool le = sturm_count(n, d, e2, x, pivmin) <= i;
-        const unsigned bal = __ballot_sync(0xffffffffu, le);
-        const int nle = bal == 0 ? 0 : 32 - __clz(bal);
-        const double nlo = nle > 0 ? lo + (hi - lo) * nle / 33.0 : lo;
-        const double nhi = nle < 32 ? lo + (hi - lo) * (nle + 1) / 33.0 : hi;
-        lo = nlo;
-        hi = nhi;
+        const bool go = valid && !(hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + atol || mid == lo ||
+                                   mid == hi);
+        if (!__any_sync(0xffffffffu, go)) break;
+        const double x = lo + (hi - lo) * ((li + 1) * sect);
+        const bool le = go && sturm_count(n, d, e2, x, pivmin) <= i;
+        const int nle = group_le(le, gbase, L);
+        if (go) {
+            const double nlo = nle > 0 ? lo + (hi - lo) * (nle * sect) : lo;
+            const double nhi = nle < L ? lo + (hi - lo) * ((nle + 1) * sect) : hi;
+            lo = nlo;
+            hi = nhi;
+        }
     }
-    if (lane == 0) lam[i] = 0.5 * (lo + hi);
+    if (valid && li == 0) lam[i] = 0.5 * (lo + hi);
 }
 
 // uniform in [-1, 1) from a 64-bit hash (splitmix64 finaliser)
@@ -622,11 +686,11 @@ bool launch_tridiag_rows(cudaStream_t s, int G, size_t smem, int sms, int n, con
                          double *tau, double *Vh, double *pbuf, double *rbuf) {
     HSIM_SMEM_LIMIT_ONCE(k_tridiag_rows<RMAX>, kTriSmemMax);
     int per_sm = 0;
-    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_rows<RMAX>, kTriThreads, smem));
+    HSIM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag_rows<RMAX>, kTrdThreads, smem));
     if ((int64_t)per_sm * sms < G) return false;
     int nn = n;
     void *args[] = {&nn, &A, &d, &e, &tau, &Vh, &pbuf, &rbuf};
-    HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_tridiag_rows<RMAX>, dim3(G), dim3(kTriThreads), args, smem, s));
+    HSIM_CUDA(cudaLaunchCooperativeKernel((void *)k_tridiag_rows<RMAX>, dim3(G), dim3(kTrdThreads), args, smem, s));
     HSIM_LAUNCHED();
     return true;
 }
@@ -701,7 +765,9 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     k_tri_prep<<<1, kTriThreads, 0, s>>>(n, d, e, e2, bounds, d32, e232);
     HSIM_LAUNCHED();
     if (detail) cudaEventRecord(t1, s);
-    k_tri_bisect<<<cdiv((int64_t)m * 32, 128), 128, 0, s>>>(n, m, d, e2, d32, e232, bounds, lam);
+    // about one warp per SM: G eigenvalues per warp (L = 32 / G >= 2 lanes each)
+    const int per_warp = std::max(1, std::min(16, (m + sms - 1) / sms));
+    k_tri_bisect<<<(m + per_warp - 1) / per_warp, 32, 0, s>>>(n, m, per_warp, d, e2, d32, e232, bounds, lam);
     HSIM_LAUNCHED();
     if (detail) cudaEventRecord(t2, s);
     // 3. clusters on the host, then inverse iteration

@@ -165,6 +165,40 @@ template <typename T>
 void solve_bwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int nf_max, const T *arena,
                      int k, T *X, int ldx);
 
+// ---- inverted-factor solves (k_finv.cu) ------------------------------------
+// One product of the front inversion, all operands column-major:
+//   C = (+/-) A B,  A(i, k) = Abase[a + k lda + i],  B(k, j) = Bbase[b + j ldb + k],
+//   C(i, j) = Cbase[c + j ldc + i],
+// with A or B read as unit lower triangular (diagonal 1, upper part 0; the
+// stored diagonal and upper part are not read) when flagged.  tile0 is the
+// first 64 x 64 output tile of the task in the launch (prefix over tasks).
+struct GemmTask {
+    int64_t a, b, c;
+    int M, N, K, lda, ldb, ldc, tile0, flags;
+};
+constexpr int kGemmAUnitLower = 1, kGemmBUnitLower = 2, kGemmNeg = 4;
+constexpr int kGemmTile = 64;
+// inverse of the unit lower 32 x 32 diagonal blocks (t, b0) of the pivot
+// blocks, in place
+template <typename T>
+void inv_diag_blocks(cudaStream_t s, const FrontDev &fd, const int2 *blk, int nblk, T *arena);
+template <typename T>
+void gemm_tasks(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles, const T *Ab, const T *Bb, T *Cb);
+// Cb[c + j ldc + i] = Ab[a + j lda + i], i < M, j < N, per task (64 x 64 tiles)
+template <typename T>
+void copy_tasks(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles, const T *Ab, T *Cb);
+template <typename T>
+void reciprocal(cudaStream_t s, int n, const T *x, T *y);
+// forward substitution of one tree height on the inverted fronts:
+// Y[pivots of t] = Linv_t X[pivots of t], X[ancestor rows of t] -= W_t X[pivots of t]
+template <typename T>
+void solve_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, const T *arena,
+                   int k, T *X, T *Y, int ldx);
+// backward substitution of one tree height: X[pivots of t] = Linv_t^T D^-1 Y[pivots of t] - W_t^T X[ancestor rows]
+template <typename T>
+void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_ns, const T *arena,
+                   const T *dinv, int k, T *X, const T *Y, int ldx);
+
 // ---- FP64-accurate products on BF16 tensor cores (k_ozaki.cu) --------------
 constexpr int kOzakiSlices = 6;
 // digit slices of an FP64 block in the tiled layout of k_ozaki.cu: rows
