@@ -146,7 +146,7 @@ def main():
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz"],
+    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz", "ritz_tc"],
                     help="time one step-level kernel on random data instead of the solve (profiling)")
     ap.add_argument("--rows", type=int, default=200000)
     ap.add_argument("--cols", type=int, default=750)
@@ -321,12 +321,13 @@ def run_kernel(args):
         f = hs.gram if args.kernel == "gram" else hs.gram_tc
         fn = lambda: f(ctx, A, B)
         flops, nbytes = 2.0 * n * q * q, 16.0 * n * q
-    elif args.kernel == "ritz":
+    elif args.kernel in ("ritz", "ritz_tc"):
         # q x q symmetric S_bar and SPD M_bar with random eigenvectors
         Sb = P + P.t()
         C = torch.randn((q, q), dtype=torch.float64, device="cuda:0", generator=g)
         Mb = torch.eye(q, dtype=torch.float64, device="cuda:0") + (C @ C.t()) / (10.0 * q)
-        fn = lambda: hs.ritz(ctx, Sb, Mb)
+        tc = args.kernel == "ritz_tc"
+        fn = lambda: hs.ritz(ctx, Sb, Mb, tc=tc)
         flops, nbytes = 0.0, 16.0 * q * q
     else:
         f = hs.gemm_update if args.kernel == "update" else hs.gemm_update_tc
@@ -343,7 +344,7 @@ def run_kernel(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(1, args.steps)
     extra = {}
-    if args.kernel == "ritz":
+    if args.kernel in ("ritz", "ritz_tc"):
         extra["sweeps"] = fn()[2]
     print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms, **extra,
                       "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12,

@@ -245,14 +245,21 @@ hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int k, int m, const double
                                 const double *B_dev, int ldb, double *C_dev, int ldc);
 
 /* Dense generalised symmetric eigenproblem S_bar X = M_bar X Lambda (Alg. 1,
- * dense eigenproblem step; also the coarsest level of Alg. 3): Cholesky of
- * M_bar, cyclic Jacobi on C^-1 S_bar C^-T, back-transformation.  S_bar and
- * M_bar are k x k row-major (read only); evals (k) ascending; X (k x k,
+ * dense eigenproblem step; also the coarsest level of Alg. 3): LDL^T of
+ * M_bar = C C^T, Householder tridiagonalisation, multisection and inverse
+ * iteration on A = C^-1 S_bar C^-T, back-transformation, all in FP64.  S_bar
+ * and M_bar are k x k row-major (read only); evals (k) ascending; X (k x k,
  * row-major, column j = eigenvector j, X^T M_bar X = I).  Returns
  * HSIM_E_NOT_SPD if M_bar is not positive definite.  sweeps_out (host) may
- * be NULL. */
+ * be NULL (always 0).  Scratch is allocated per call. */
 hsim_status hsim_ritz(hsim_ctx *ctx, int k, const double *Sbar_dev, const double *Mbar_dev,
                       double *evals_dev, double *X_dev, int *sweeps_out);
+/* The same solve as done by the mixed-precision path: C^-1 is formed
+ * explicitly (in-place inversion of L by block doubling, FP64) and the three
+ * transforms A = (C^-1 S_bar) C^-T and X = C^-T V are FP64-accurate products
+ * on BF16 tensor cores (as hsim_gram_tc).  Arguments and errors as hsim_ritz. */
+hsim_status hsim_ritz_tc(hsim_ctx *ctx, int k, const double *Sbar_dev, const double *Mbar_dev,
+                         double *evals_dev, double *X_dev, int *sweeps_out);
 
 /* Galerkin restriction C = U^T A U of a level matrix (Alg. 3): A is n x n
  * CSR, U is n x nc CSR; C is returned in the CSR pattern computed on the

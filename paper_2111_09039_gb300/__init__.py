@@ -307,14 +307,15 @@ def gemm_update(ctx: Context, A, B):
     return C
 
 
-def ritz(ctx: Context, Sbar, Mbar):
+def ritz(ctx: Context, Sbar, Mbar, tc: bool = False):
+    """Dense Ritz solve; tc=True: the mixed path's variant (hsim_ritz_tc)."""
     torch = _torch()
     k = Sbar.shape[0]
     lam = torch.empty(k, dtype=torch.float64, device=Sbar.device)
     X = torch.empty((k, k), dtype=torch.float64, device=Sbar.device)
     sweeps = ctypes.c_int()
-    check(lib().hsim_ritz(ctx.handle, k, ptr(Sbar.contiguous()), ptr(Mbar.contiguous()), ptr(lam), ptr(X),
-                          ctypes.byref(sweeps)))
+    fn = lib().hsim_ritz_tc if tc else lib().hsim_ritz
+    check(fn(ctx.handle, k, ptr(Sbar.contiguous()), ptr(Mbar.contiguous()), ptr(lam), ptr(X), ctypes.byref(sweeps)))
     return lam, X, sweeps.value
 
 

@@ -89,6 +89,7 @@ _SIGS = {
     "hsim_gram_tc": (I, [P, I, I, I, P, I, P, I, P]),
     "hsim_gemm_update_tc": (I, [P, I, I, I, P, I, P, I, P, I]),
     "hsim_ritz": (I, [P, I, P, P, P, P, P]),
+    "hsim_ritz_tc": (I, [P, I, P, P, P, P, P]),
     "hsim_galerkin": (I, [P, I, I, P, P, P, P, P, P, P, P, P, P]),
     "hsim_free": (None, [P]),
     "hsim_level_pattern": (I, [P, I, P, P, P, P]),

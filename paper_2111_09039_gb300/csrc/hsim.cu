@@ -159,88 +159,31 @@ struct hsim_hier {
 
 namespace {
 
-// Tasks of the front inversion (see k_finv.cu): level bs merges the inverted
-// diagonal blocks [a0, a0 + bs) and [a0 + bs, a0 + 2 bs) of every pivot block,
-//   T = B Ainv (into scratch),  B <- -Cinv T,
-// B being the block of L below Ainv and left of Cinv; then W = L_bs Linv.
+// Device copies of the front inversion's tasks (k::inverse_plan) and the
+// per-height maxima of nf and ns for the inverted-factor solves.
 void build_inverse_plan(LevelData &L, cudaStream_t s) {
     const FrontSymbolic &fs = L.fs;
-    auto tiles = [](int M, int N) {
-        return ((M + k::kGemmTile - 1) / k::kGemmTile) * ((N + k::kGemmTile - 1) / k::kGemmTile);
-    };
-    std::vector<int2> blk;
-    int max_ns = 0;
-    for (int t = 0; t < fs.n_nodes; ++t) {
-        for (int b0 = 0; b0 < fs.ns[t]; b0 += 32) blk.push_back(make_int2(t, b0));
-        max_ns = std::max(max_ns, fs.ns[t]);
-    }
-    L.n_inv_blk = (int)blk.size();
-    L.inv_blk.upload(blk.empty() ? std::vector<int2>{make_int2(0, 0)} : blk, s);
+    k::InversePlan P = k::inverse_plan(fs.nf, fs.ns, fs.foff);
+    L.n_inv_blk = (int)P.blk.size();
+    L.inv_blk.upload(P.blk.empty() ? std::vector<int2>{make_int2(0, 0)} : P.blk, s);
     L.inv_p1.clear();
     L.inv_p2.clear();
     L.inv_n.clear();
-    L.inv_tiles.clear();
-    int64_t scratch = 0;
-    for (int bs = 32; bs < max_ns; bs *= 2) {
-        std::vector<k::GemmTask> p1, p2;
-        int nt = 0;
-        int64_t off = 0;
-        for (int t = 0; t < fs.n_nodes; ++t) {
-            const int ns = fs.ns[t], nf = fs.nf[t];
-            const int64_t F = fs.foff[t];
-            for (int a0 = 0; a0 + bs < ns; a0 += 2 * bs) {
-                const int a1 = a0 + bs, a2 = std::min(a0 + 2 * bs, ns), mc = a2 - a1;
-                k::GemmTask x{};
-                x.a = F + (int64_t)a0 * nf + a1, x.lda = nf;
-                x.b = F + (int64_t)a0 * nf + a0, x.ldb = nf;
-                x.c = off, x.ldc = mc;
-                x.M = mc, x.N = bs, x.K = bs, x.flags = k::kGemmBUnitLower, x.tile0 = nt;
-                k::GemmTask y{};
-                y.a = F + (int64_t)a1 * nf + a1, y.lda = nf;
-                y.b = off, y.ldb = mc;
-                y.c = F + (int64_t)a0 * nf + a1, y.ldc = nf;
-                y.M = mc, y.N = bs, y.K = mc, y.flags = k::kGemmAUnitLower | k::kGemmNeg, y.tile0 = nt;
-                p1.push_back(x);
-                p2.push_back(y);
-                nt += tiles(mc, bs);
-                off += (int64_t)mc * bs;
-            }
-        }
-        scratch = std::max(scratch, off);
-        L.inv_n.push_back((int)p1.size());
-        L.inv_tiles.push_back(nt);
+    L.inv_tiles = P.tiles;
+    for (size_t lv = 0; lv < P.p1.size(); ++lv) {
+        L.inv_n.push_back((int)P.p1[lv].size());
         L.inv_p1.emplace_back();
-        L.inv_p1.back().upload(p1, s);
+        L.inv_p1.back().upload(P.p1[lv], s);
         L.inv_p2.emplace_back();
-        L.inv_p2.back().upload(p2, s);
+        L.inv_p2.back().upload(P.p2[lv], s);
     }
-    std::vector<k::GemmTask> w, wc;
-    int nt = 0;
-    int64_t off = 0;
-    for (int t = 0; t < fs.n_nodes; ++t) {
-        const int ns = fs.ns[t], nf = fs.nf[t], nb = nf - ns;
-        if (nb <= 0 || ns <= 0) continue;
-        const int64_t F = fs.foff[t];
-        k::GemmTask x{};
-        x.a = F + ns, x.lda = nf;
-        x.b = F, x.ldb = nf;
-        x.c = off, x.ldc = nb;
-        x.M = nb, x.N = ns, x.K = ns, x.flags = k::kGemmBUnitLower, x.tile0 = nt;
-        k::GemmTask c{};
-        c.a = off, c.lda = nb;
-        c.c = F + ns, c.ldc = nf;
-        c.M = nb, c.N = ns, c.tile0 = nt;
-        w.push_back(x);
-        wc.push_back(c);
-        nt += tiles(nb, ns);
-        off += (int64_t)nb * ns;
-    }
-    scratch = std::max(scratch, off);
-    L.inv_nw = (int)w.size();
-    L.inv_tw = nt;
-    L.inv_w.upload(w, s);
-    L.inv_wc.upload(wc, s);
-    L.inv_scratch = scratch;
+    L.inv_nw = (int)P.w.size();
+    L.inv_tw = P.wtiles;
+    L.inv_w.upload(P.w, s);
+    L.inv_wc.upload(P.wc, s);
+    L.inv_scratch = P.scratch;
+    // the uploads read the host vectors of P
+    HSIM_CUDA(cudaStreamSynchronize(s));
     L.h_maxnf.assign(fs.max_height + 1, 0);
     L.h_maxns.assign(fs.max_height + 1, 0);
     for (int h = 0; h <= fs.max_height; ++h)
@@ -519,11 +462,12 @@ void apply_S(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int l
 
 // Rayleigh-Ritz on q x q reduced matrices; throws on failure
 // lowest m (<= 0: all q) Ritz pairs of the q x q problem
+// tc: transforms as FP64-accurate tensor-core products (mixed path)
 void ritz_step(hsim_ctx *ctx, hsim_hier *H, int q, const double *Sbar, const double *Mbar, double *lam, double *X,
-               int ldx, int *sweeps, int m = 0) {
+               int ldx, int *sweeps, int m, bool tc) {
     H->ritz_work.reserve(k::ritz_work_size(q));
     int rc = k::ritz(ctx->stream, q, Sbar, q, Mbar, q, lam, X, ldx, H->ritz_work.p, sweeps, ctx->flags.p,
-                     ctx->hflags.data(), m);
+                     ctx->hflags.data(), m, tc);
     if (rc != 0) fail(HSIM_E_NOT_SPD, "reduced mass matrix is not positive definite (q = " + std::to_string(q) + ")");
 }
 
@@ -589,7 +533,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     H->coarseX.reserve((size_t)nc * nc);
     H->coarseLam.reserve(nc);
     int sweeps = 0;
-    ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps, q);
+    ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps, q,
+              o.precision == HSIM_MIXED);
     inf.coarse_sweeps = sweeps;
     inf.ms_coarse = tm.stop();
     std::vector<double> lam_h(q);
@@ -777,7 +722,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             if (mixed) inf.ms_gram += (ph[2] += ts.stop());
             else inf.ms_gram += (ph[2] = ts.stop());
             // dense eigenproblem (Alg. 1): Ritz values ascending, M-orthonormal
-            ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps);
+            ritz_step(ctx, H, q, H->Sbar.p, H->Mbar.p, H->lam.p, H->phibar.p, q, &sweeps, 0, mixed);
             inf.ritz_calls += 1;
             inf.ritz_sweeps += sweeps;
             k::diag_scale(s, q, q, H->colw.p, H->phibar.p, q, H->phibar.p, q);  // W Phi_bar
@@ -1290,8 +1235,9 @@ hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int kk, int m, const doubl
     });
 }
 
-hsim_status hsim_ritz(hsim_ctx *ctx, int kk, const double *Sbar, const double *Mbar, double *evals, double *X,
-                      int *sweeps_out) {
+namespace {
+hsim_status ritz_entry(hsim_ctx *ctx, int kk, const double *Sbar, const double *Mbar, double *evals, double *X,
+                       int *sweeps_out, bool tc) {
     return guard([&] {
         HSIM_CHECK_ARG(ctx && Sbar && Mbar && evals && X, "NULL argument");
         HSIM_CHECK_ARG(kk >= 1, "bad size");
@@ -1299,11 +1245,22 @@ hsim_status hsim_ritz(hsim_ctx *ctx, int kk, const double *Sbar, const double *M
         DevBuf<double> work(k::ritz_work_size(kk));
         int sw = 0;
         int rc = k::ritz(ctx->stream, kk, Sbar, kk, Mbar, kk, evals, X, kk, work.p, &sw, ctx->flags.p,
-                         ctx->hflags.data());
+                         ctx->hflags.data(), 0, tc);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
         if (sweeps_out) *sweeps_out = sw;
         if (rc != 0) fail(HSIM_E_NOT_SPD, "M_bar is not positive definite");
     });
+}
+}  // namespace
+
+hsim_status hsim_ritz(hsim_ctx *ctx, int kk, const double *Sbar, const double *Mbar, double *evals, double *X,
+                      int *sweeps_out) {
+    return ritz_entry(ctx, kk, Sbar, Mbar, evals, X, sweeps_out, false);
+}
+
+hsim_status hsim_ritz_tc(hsim_ctx *ctx, int kk, const double *Sbar, const double *Mbar, double *evals, double *X,
+                         int *sweeps_out) {
+    return ritz_entry(ctx, kk, Sbar, Mbar, evals, X, sweeps_out, true);
 }
 
 hsim_status hsim_galerkin(hsim_ctx *ctx, int n, int nc, const int32_t *A_ptr, const int32_t *A_col,

@@ -372,6 +372,12 @@ struct DenseFront {
     DevBuf<int64_t> foff, rows_off, relmap_off;
     DevBuf<int> nf, ns, pstart, rows, relmap, node;
     FrontDev fd{};
+    // in-place inversion of the unit lower factor (inverse_plan of one front)
+    DevBuf<int2> blk;
+    int nblk = 0;
+    std::vector<DevBuf<GemmTask>> p1, p2;
+    std::vector<int> ntask, tiles;
+    int64_t scratch = 0;
 };
 
 DenseFront &dense_front(int k, cudaStream_t s) {
@@ -395,6 +401,18 @@ DenseFront &dense_front(int k, cudaStream_t s) {
     d->rows.upload(rows, s);
     d->relmap.upload(std::vector<int>{0}, s);
     d->node.upload(std::vector<int>{0}, s);
+    InversePlan P = inverse_plan({k}, {k}, {0});
+    d->nblk = (int)P.blk.size();
+    d->blk.upload(P.blk, s);
+    for (size_t lv = 0; lv < P.p1.size(); ++lv) {
+        d->ntask.push_back((int)P.p1[lv].size());
+        d->p1.emplace_back();
+        d->p1.back().upload(P.p1[lv], s);
+        d->p2.emplace_back();
+        d->p2.back().upload(P.p2[lv], s);
+    }
+    d->tiles = P.tiles;
+    d->scratch = P.scratch;
     HSIM_CUDA(cudaStreamSynchronize(s));
     d->fd = FrontDev{d->foff.p, d->nf.p, d->ns.p, d->pstart.p, d->rows_off.p, d->rows.p, d->relmap_off.p, d->relmap.p};
     auto &ref = *d;
@@ -497,7 +515,23 @@ void scale_sym_unit_diag(cudaStream_t s, int q, double *S, double *M, int lda, d
 }
 
 size_t ritz_work_size(int k) {
-    return 3 * (size_t)k * k + 2 * (size_t)k + 64 + sym_eig_work_size(k, k);
+    const size_t kk = (size_t)k * k;
+    // F W T d | sym_eig work | tensor-core path: Cr Cc V, inversion scratch
+    // (at most k^2), digit slices of two k x k operands
+    const size_t oz = (ozaki_rows_scratch(k, k) + ozaki_cols_scratch(k, k) + 7) / 8;
+    return 3 * kk + 2 * (size_t)k + 64 + sym_eig_work_size(k, k) + 4 * kk + oz + 48;
+}
+
+// Cr = D^-1/2 Linv (row-major) and Cc = Cr^T (row-major) from the inverted
+// factor F (column-major: Linv strictly below the diagonal, unit diagonal)
+__global__ void k_cinv(int k, const double *__restrict__ F, const double *__restrict__ d, double *__restrict__ Cr,
+                       double *__restrict__ Cc) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)k * k) return;
+    const int i = (int)(idx / k), j = (int)(idx % k);
+    const double v = (i > j ? F[(size_t)j * k + i] : (i == j ? 1.0 : 0.0)) * rsqrt(d[i]);
+    Cr[(size_t)i * k + j] = v;
+    Cc[(size_t)j * k + i] = v;
 }
 
 // X[i, 0:cols] *= 1/sqrt(d[i])
@@ -509,7 +543,7 @@ __global__ void k_rows_rsqrt(int rows, int cols, const double *__restrict__ d, d
 }
 
 int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals, double *X,
-         int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host, int m) {
+         int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host, int m, bool tc) {
     // work layout: F (k*k) | W (k*k) | T (k*k) | d (k) | eigensolver work
     if (m <= 0 || m > k) m = k;
     const size_t kk = (size_t)k * k;
@@ -532,6 +566,40 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     HSIM_CUDA(cudaMemcpyAsync(flag_host, flag_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaStreamSynchronize(s));
     if (flag_host[0] != 0 || flag_host[2] != 0) return 1;  // not positive definite
+    if (sweeps) *sweeps = 0;
+    if (tc) {
+        // Cinv = D^-1/2 L^-1 explicitly (L inverted in place by block
+        // doubling), then the three transforms as FP64-accurate tensor-core
+        // products: A = (Cinv S_bar) Cinv^T, X = Cinv^T V
+        const size_t kk = (size_t)k * k;
+        double *Cr = ework + sym_eig_work_size(k, k) + 8, *Cc = Cr + kk, *V = Cc + kk, *scr = V + kk;
+        // digit slices are read by bulk copies: 256-byte aligned base
+        unsigned char *oz = reinterpret_cast<unsigned char *>(
+            (reinterpret_cast<uintptr_t>(scr + kk) + 255) & ~static_cast<uintptr_t>(255));
+        const size_t rb = ozaki_rows_scratch(k, k);
+        HSIM_CHECK_ARG(df.scratch <= (int64_t)kk, "ritz: inversion scratch");
+        inv_diag_blocks<double>(s, df.fd, df.blk.p, df.nblk, F);
+        for (size_t lv = 0; lv < df.p1.size(); ++lv) {
+            gemm_tasks<double>(s, df.p1[lv].p, df.ntask[lv], df.tiles[lv], F, F, scr);
+            gemm_tasks<double>(s, df.p2[lv].p, df.ntask[lv], df.tiles[lv], F, scr, F);
+        }
+        k_cinv<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, F, d, Cr, Cc);
+        HSIM_LAUNCHED();
+        OzakiOperand a = ozaki_split_rows(s, k, k, Cr, k, oz);
+        OzakiOperand b = ozaki_split_cols(s, k, k, Sbar, lds, oz + rb);
+        ozaki_product(s, a, b, a.kp, W, k, 0);
+        a = ozaki_split_rows(s, k, k, W, k, oz);
+        b = ozaki_split_cols(s, k, k, Cc, k, oz + rb);
+        ozaki_product(s, a, b, a.kp, T, k, 0);
+        k_symmetrize<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, T, k);
+        HSIM_LAUNCHED();
+        sym_eig(s, k, m, T, evals, V, m, ework);
+        a = ozaki_split_rows(s, k, k, Cc, k, oz);
+        b = ozaki_split_cols(s, k, m, V, m, oz + rb);
+        ozaki_product(s, a, b, a.kp, X, ldx, 0);
+        ozaki_check(s);
+        return 0;
+    }
     // A = C^-1 S_bar C^-T: W = D^-1/2 L^-1 S_bar, T = D^-1/2 L^-1 W^T
     copy_matrix(s, k, k, Sbar, lds, W, k);
     auto forward = [&](double *Y) {
@@ -554,7 +622,6 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     HSIM_LAUNCHED();
     // lowest m eigenpairs of A (ascending), eigenvectors into X (k x m)
     sym_eig(s, k, m, T, evals, X, ldx, ework);
-    if (sweeps) *sweeps = 0;
     // X = C^-T V = L^-T D^-1/2 V
     k_rows_rsqrt<<<cdiv((int64_t)k * m, 256), 256, 0, s>>>(k, m, d, X, ldx);
     HSIM_LAUNCHED();

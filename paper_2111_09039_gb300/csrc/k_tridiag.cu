@@ -428,10 +428,11 @@ __device__ __forceinline__ int sturm_count32(int n, const float *__restrict__ d,
 // multisection with L interior points (the bracket shrinks (L + 1)-fold per
 // round).  FP32 rounds first (the FP32 pipe is ~60x the FP64 pipe) down to
 // 1e-5 ||T||, then the bracket is checked with FP64 counts and widened until
-// it holds, then FP64 rounds to full precision.  The FP64 rounds dominate and
-// the FP64 unit is shared by the warps of an SM, so the launch uses about one
-// warp per SM with G = ceil(m / SMs): fewer points per eigenvalue cost more
-// rounds but much less FP64 work in total.
+// it holds, then FP64 rounds to full precision.  The FP64 rounds dominate; FP64
+// issues at about one warp instruction per 64 cycles per SM sub-partition, so
+// the launch gives each sub-partition about one warp, with G = ceil(m / (4 SMs)):
+// fewer points per eigenvalue cost more rounds, a second warp on a
+// sub-partition doubles every round.
 __device__ __forceinline__ int group_le(bool le, int gbase, int L) {
     const unsigned bal = __ballot_sync(0xffffffffu, le);
     const unsigned g = (L == 32) ? bal : (bal >> gbase) & ((1u << L) - 1u);
@@ -766,8 +767,11 @@ void sym_eig(cudaStream_t s, int n, int m, double *A, double *evals, double *X, 
     HSIM_LAUNCHED();
     if (detail) cudaEventRecord(t1, s);
     // about one warp per SM: G eigenvalues per warp (L = 32 / G >= 2 lanes each)
-    const int per_warp = std::max(1, std::min(16, (m + sms - 1) / sms));
-    k_tri_bisect<<<(m + per_warp - 1) / per_warp, 32, 0, s>>>(n, m, per_warp, d, e2, d32, e232, bounds, lam);
+    // FP64 issues per SM sub-partition: about one warp on each of the 4 x SMs
+    // sub-partitions (blocks of four warps, one per sub-partition)
+    const int per_warp = std::max(1, std::min(16, (m + 4 * sms - 1) / (4 * sms)));
+    const int nwarps = (m + per_warp - 1) / per_warp;
+    k_tri_bisect<<<(nwarps + 3) / 4, 128, 0, s>>>(n, m, per_warp, d, e2, d32, e232, bounds, lam);
     HSIM_LAUNCHED();
     if (detail) cudaEventRecord(t2, s);
     // 3. clusters on the host, then inverse iteration

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 struct __nv_bfloat16;
 
@@ -100,9 +101,11 @@ void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *
                    const double *lam, const double *dinv, double *out);
 // dense symmetric generalised eigensolver, k x k: LDL^T of M_bar, the lowest
 // m (<= 0: all k) pairs of C^-1 S_bar C^-T by sym_eig, X (k x m) = C^-T V;
-// returns 0 ok, 1 not SPD; *sweeps = 0 (kept for the Jacobi variant's report)
+// returns 0 ok, 1 not SPD; *sweeps = 0 (kept for the Jacobi variant's report).
+// tc: C^-1 formed explicitly and the transforms done as FP64-accurate
+// tensor-core products (else FP64 triangular solves on the front kernels).
 int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals,
-         double *X, int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host, int m = 0);
+         double *X, int ldx, double *work, int *sweeps, int *flag_dev, int *flag_host, int m = 0, bool tc = false);
 // ---- tridiagonal eigensolver (k_tridiag.cu) ----------------------------------
 // lowest m eigenpairs of the symmetric n x n A (row-major, ld n, destroyed):
 // evals ascending (m), X (n x m, ld ldx) orthonormal eigenvectors; work of
@@ -178,6 +181,21 @@ struct GemmTask {
 };
 constexpr int kGemmAUnitLower = 1, kGemmBUnitLower = 2, kGemmNeg = 4;
 constexpr int kGemmTile = 64;
+// Tasks of the in-place inversion of the pivot blocks of fronts (nf[t] x
+// nf[t] column-major at foff[t], ns[t] pivots): the 32 x 32 diagonal blocks;
+// per block-doubling level bs = 32, 64, ... the products T = B Ainv (into
+// scratch) and B <- -Cinv T for every pair of inverted diagonal blocks
+// [a0, a0 + bs), [a0 + bs, a0 + 2 bs); then W = L_bs Linv (into scratch) and
+// its copy over L_bs.  scratch: elements needed by the largest pass.
+struct InversePlan {
+    std::vector<int2> blk;
+    std::vector<std::vector<GemmTask>> p1, p2;
+    std::vector<int> tiles;
+    std::vector<GemmTask> w, wc;
+    int wtiles = 0;
+    int64_t scratch = 0;
+};
+InversePlan inverse_plan(const std::vector<int> &nf, const std::vector<int> &ns, const std::vector<int64_t> &foff);
 // inverse of the unit lower 32 x 32 diagonal blocks (t, b0) of the pivot
 // blocks, in place
 template <typename T>

@@ -339,3 +339,50 @@ def test_ritz_large_sizes_all_kernel_variants(hs, ctx, k):
     np.testing.assert_allclose(lam, ev, atol=tol)
     np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-11)
     np.testing.assert_allclose(S @ X, X * lam[None, :], atol=tol)
+
+
+# ---- mixed-path Ritz solve: explicit C^-1, transforms on tensor cores --------
+@pytest.mark.parametrize("k", [1, 2, 31, 33, 75, 200, 301, 750])
+def test_ritz_tc_matches_scipy_eigh(hs, ctx, k):
+    # M_bar with condition 1e3 (the Ritz problems of the solve have unit
+    # diagonal and moderate condition); the products are accurate to about
+    # K 2^-47 of the row/column maxima, so the bounds are those of the FP64
+    # variant times a small factor
+    S, M = _spd_pair(k, 100 + k)
+    lam, X, _ = hs.ritz(ctx, dev(S), dev(M), tc=True)
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    ref = sla.eigh(S, M, eigvals_only=True)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(lam, ref, rtol=1e-10, atol=1e-10 * scale)
+    np.testing.assert_allclose(X.T @ M @ X, np.eye(k), atol=1e-9)
+    np.testing.assert_allclose(X.T @ S @ X, np.diag(lam), atol=1e-9 * scale)
+    assert np.all(np.diff(lam) >= 0)
+
+
+def test_ritz_tc_clusters_and_fp64_agreement(hs, ctx):
+    # spectrum with pairs and a cluster of four; both variants give the same
+    # eigenvalues and span the same invariant subspaces
+    k = 120
+    rng = np.random.default_rng(12)
+    d = np.sort(rng.uniform(0.0, 30.0, k))
+    d[40:42] = d[40]
+    d[80:84] = d[80]
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    S = Q @ np.diag(d) @ Q.T
+    S = 0.5 * (S + S.T)
+    _, M = _spd_pair(k, 13, cond=50.0)
+    # transform to the generalised problem S2 x = lam M x with known eigenvalues d
+    Lm = np.linalg.cholesky(M)
+    S2 = Lm @ S @ Lm.T
+    lam_t, X_t, _ = hs.ritz(ctx, dev(S2), dev(M), tc=True)
+    lam_f, X_f, _ = hs.ritz(ctx, dev(S2), dev(M))
+    lam_t, X_t, lam_f, X_f = (a.cpu().numpy() for a in (lam_t, X_t, lam_f, X_f))
+    np.testing.assert_allclose(lam_t, d, atol=1e-10 * d.max())
+    np.testing.assert_allclose(lam_t, lam_f, atol=1e-10 * d.max())
+    np.testing.assert_allclose(X_t.T @ M @ X_t, np.eye(k), atol=1e-9)
+    np.testing.assert_allclose(S2 @ X_t, M @ X_t * lam_t[None, :], atol=1e-9 * d.max())
+    # cluster subspaces: projector onto the cluster's columns agrees
+    for a, b in ((40, 42), (80, 84)):
+        Pt = X_t[:, a:b] @ X_t[:, a:b].T @ M
+        Pf = X_f[:, a:b] @ X_f[:, a:b].T @ M
+        np.testing.assert_allclose(Pt, Pf, atol=1e-8)
