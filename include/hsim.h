@@ -222,6 +222,16 @@ hsim_status hsim_eig_grad(hsim_ctx *ctx, int n, int n_tris, const double *V_dev,
 hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
                       const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
                       int ldx, double *Y_dev, int ldy);
+/* The same product as done by the mixed-precision path: FP64 values and X
+ * are carried as pairs of FP32 values (double-float arithmetic on the FP32
+ * pipe): each term carries a few units of 2^-46 |A[r, c] X[c, j]| (FP64:
+ * 2^-53), so the result is within about 2^-42 sum_c |A[r, c] X[c, j]| for
+ * rows of up to ~20 entries; values of magnitude below 2^-90 keep only FP32
+ * accuracy.  Arguments as hsim_spmm; scratch for
+ * the split values is allocated per call. */
+hsim_status hsim_spmm_df(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
+                         const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
+                         int ldx, double *Y_dev, int ldy);
 
 /* G = A^T B (k_a x k_b, row-major, ld k_b) for tall A (n x k_a, ld lda) and
  * B (n x k_b, ld ldb): the reduced matrices Psi^T S Psi, Psi^T M Psi of Alg. 1. */

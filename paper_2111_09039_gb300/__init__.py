@@ -263,13 +263,15 @@ def eigenvalues(ctx: Context, hier: Hierarchy, V, F, p: int, tol: float, options
 
 
 # ---- step-level entry points -------------------------------------------------
-def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None):
+def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None, df: bool = False):
+    """Y = A X (CSR A); df=True: the mixed path's double-float variant (hsim_spmm_df)."""
     torch = _torch()
     n_rows = row_ptr.numel() - 1
     k = X.shape[1]
     Y = torch.empty((n_rows, k), dtype=torch.float64, device=X.device)
-    check(lib().hsim_spmm(ctx.handle, n_rows, n_cols if n_cols is not None else X.shape[0], ptr(row_ptr),
-                          ptr(col), ptr(val), k, ptr(X), X.stride(0), ptr(Y), k))
+    fn = lib().hsim_spmm_df if df else lib().hsim_spmm
+    check(fn(ctx.handle, n_rows, n_cols if n_cols is not None else X.shape[0], ptr(row_ptr), ptr(col), ptr(val), k,
+             ptr(X), X.stride(0), ptr(Y), k))
     return Y
 
 

@@ -8,6 +8,8 @@
 // row's nonzeros are broadcast from registers with warp shuffles.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.h"
 #include "kernels.h"
 
@@ -116,6 +118,117 @@ __global__ void k_spmm(int n_rows, const int *__restrict__ ptr, const int *__res
         for (int u = 0; u < kChunk; ++u) {
             int j = c0 + u * kWarp + lane;
             if (j < k) yr[j] = acc[u];
+        }
+    }
+}
+
+// ---- double-float S X (mixed path) -------------------------------------------
+// FP64 multiply-adds issue at a 64th of the FP32 rate here, so an FP64 S X
+// with hundreds of columns is bound by them (nnz k FMAs).  In this variant
+// every FP64 value v is carried as two FP32 values, hi = v truncated to 24
+// significant bits and lo = the next 24 bits (v = hi + lo to 2^-47 |v|), both
+// cut from the FP64 bit pattern with integer operations.  A product s x is
+// formed as p = s_hi x_hi plus its exact rounding error fma(s_hi, x_hi, -p)
+// plus the cross terms s_hi x_lo + s_lo x_hi, and accumulated in (hi, lo)
+// with Knuth's two-sum (the double-float arithmetic of Dekker, 1971); each
+// output is converted back to FP64 once.  Each term carries a few units of
+// 2^-46 |s x| (FP64: 2^-53), the sum about 2^-42 sum |s x| for the ~7-25
+// entries of a mesh row.
+
+// v -> (hi, lo); values outside the FP32 exponent range of hi and lo (|v|
+// above 2^127 or below 2^-97, and zero) go through FP64 conversions
+__device__ __forceinline__ float2 split_df(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 1023 - 97 || e > 1023 + 127) {
+        const float h = (float)v;
+        return make_float2(h, (float)(v - (double)h));
+    }
+    const unsigned long long m = b & 0xfffffffffffffull;
+    const float hi = __int_as_float((int)(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29)));
+    const unsigned rem = (unsigned)(m & 0x1fffffffu);  // value rem 2^(e - 1075)
+    float lo = 0.f;
+    if (rem != 0u) {
+        const int top = 31 - __clz((int)rem);  // leading bit, 0..28
+        const int sh = top - 23;
+        const unsigned mant = sh >= 0 ? (rem >> sh) : (rem << (-sh));
+        const int el = sh + e - 925;  // biased FP32 exponent of mant 2^(sh + e - 1075)
+        if (el > 0) lo = __int_as_float((int)(sign | ((unsigned)el << 23) | (mant & 0x7fffffu)));
+    }
+    return make_float2(hi, lo);
+}
+
+__global__ void k_split_df_vec(int64_t n, const double *__restrict__ v, float2 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = split_df(v[i]);
+}
+
+// X (rows x k, ld ldx) -> X2 (rows x k, ld k); grid (column blocks, rows)
+__global__ void k_split_df(int rows, int k, const double *__restrict__ X, int ldx, float2 *__restrict__ X2) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
+    if (c >= k) return;
+    X2[(size_t)r * k + c] = split_df(X[(size_t)r * ldx + c]);
+}
+
+// exact FP32 -> FP64 conversion from the bit pattern (no FP64 instruction);
+// FP32 subnormals take the conversion instruction
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return (u & 0x7fffffffu) == 0u ? __longlong_as_double((long long)(u & 0x80000000u) << 32) : (double)x;
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                            ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// one warp per row, lane j owns columns j, j + 32, ... (kChunk per pass)
+template <int kChunk>
+__global__ void k_spmm_df(int n_rows, const int *__restrict__ ptr, const int *__restrict__ col,
+                          const float2 *__restrict__ val, int k, const float2 *__restrict__ X2, double *__restrict__ Y,
+                          int ldy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= n_rows) return;
+    const int beg = ptr[row], end = ptr[row + 1];
+    for (int c0 = 0; c0 < k; c0 += kChunk * 32) {
+        float ah[kChunk], al[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) ah[u] = al[u] = 0.f;
+        for (int e0 = beg; e0 < end; e0 += 32) {
+            int my_c = 0;
+            float2 my_v = make_float2(0.f, 0.f);
+            if (e0 + lane < end) {
+                my_c = col[e0 + lane];
+                my_v = val[e0 + lane];
+            }
+            const int cnt = min(32, end - e0);
+            for (int t = 0; t < cnt; ++t) {
+                const int c = __shfl_sync(0xffffffffu, my_c, t);
+                const float sh = __shfl_sync(0xffffffffu, my_v.x, t), sl = __shfl_sync(0xffffffffu, my_v.y, t);
+                const float2 *xr = X2 + (size_t)c * k;
+#pragma unroll
+                for (int u = 0; u < kChunk; ++u) {
+                    const int j = c0 + u * 32 + lane;
+                    if (j < k) {
+                        // explicit round-to-nearest operations: the
+                        // two-sum must not be contracted into an FMA
+                        const float2 x = xr[j];
+                        const float p = __fmul_rn(sh, x.x);
+                        const float t2 = fmaf(sh, x.y, fmaf(sl, x.x, fmaf(sh, x.x, -p)));
+                        const float s1 = __fadd_rn(ah[u], p), bb = __fsub_rn(s1, ah[u]);
+                        const float err = __fadd_rn(__fsub_rn(ah[u], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+                        al[u] = __fadd_rn(al[u], __fadd_rn(err, t2));
+                        ah[u] = s1;
+                    }
+                }
+            }
+        }
+        double *yr = Y + (size_t)row * ldy;
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            const int j = c0 + u * 32 + lane;
+            if (j < k) yr[j] = f2d_bits(ah[u]) + f2d_bits(al[u]);
         }
     }
 }
@@ -400,6 +513,30 @@ void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const doub
         k_spmm<double, 8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
     else
         k_spmm<double, 24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
+    HSIM_LAUNCHED();
+}
+
+void split_df_values(cudaStream_t s, int64_t n, const double *v, float2 *out) {
+    if (n <= 0) return;
+    k_split_df_vec<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, v, out);
+    HSIM_LAUNCHED();
+}
+
+void spmm_df(cudaStream_t s, int n_rows, int n_cols, const int *ptr, const int *col, const float2 *val, int k,
+             const double *X, int ldx, float2 *X2, double *Y, int ldy) {
+    if (n_rows <= 0 || k <= 0) return;
+    for (int r0 = 0; r0 < n_cols; r0 += 65535) {
+        const int rows = std::min(65535, n_cols - r0);
+        k_split_df<<<dim3((unsigned)((k + 255) / 256), (unsigned)rows), 256, 0, s>>>(rows, k, X + (size_t)r0 * ldx, ldx,
+                                                                                  X2 + (size_t)r0 * k);
+        HSIM_LAUNCHED();
+    }
+    const int warps = 8;
+    unsigned g = grid1d(n_rows, warps);
+    if (k <= 32 * 8)
+        k_spmm_df<8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X2, Y, ldy);
+    else
+        k_spmm_df<24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X2, Y, ldy);
     HSIM_LAUNCHED();
 }
 
