@@ -387,7 +387,7 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         const int cnt = (int)(L.hnodes_off[h + 1] - L.hnodes_off[h]);
-        k::solve_fwd_inv(s, L.fd, nodes, cnt, L.h_maxnf[h], arena, k, X, Y.p, ldx);
+        k::solve_fwd_inv(s, L.fd, nodes, cnt, L.h_maxnf[h], L.h_maxns[h], arena, k, X, Y.p, ldx);
         mark();
     }
     mark();  // the diagonal is applied inside the backward products
@@ -724,9 +724,13 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             inf.ms_solve += (ph[0] = ts.stop());
             // S Psi, M Psi (Alg. 1, reduced matrices).  The columns of Psi are
             // scaled to unit M-norm on the q x q side: with W = diag(M_bar)^-1/2,
-            // S_bar = W Psi^T S Psi W, M_bar = W Psi^T M Psi W and Phi = Psi (W Phi_bar)
-            apply_M(ctx, H, tau, q, H->Psi.p, q, H->MP.p, q);
-            apply_S(ctx, H, tau, q, H->Psi.p, q, H->SP.p, q);
+            // S_bar = W Psi^T S Psi W, M_bar = W Psi^T M Psi W and Phi = Psi (W Phi_bar).
+            // The locked columns of Psi are copies of Phi's, whose S Phi and
+            // M Phi from the last convergence test are still in SP and MP (the
+            // inverse iterations write columns >= locked only): only the
+            // active columns are multiplied.
+            apply_M(ctx, H, tau, q - locked, H->Psi.p + locked, q, H->MP.p + locked, q);
+            apply_S(ctx, H, tau, q - locked, H->Psi.p + locked, q, H->SP.p + locked, q);
             inf.ms_spmm += (ph[1] = ts.stop());
             if (mixed) {
                 // FP64-accurate Grams on BF16 tensor cores: Psi split once

@@ -232,17 +232,34 @@ __device__ __forceinline__ void lds4(T (&b)[4], const T *p) {
 template <typename T>
 __host__ __device__ constexpr int inv_cols() { return sizeof(T) == 4 ? 128 : 64; }  // columns of a solve tile
 
+// Both solve kernels: 256 threads, output tile BM x BN (BN = 128 FP32
+// columns), K in steps of 32 through two shared-memory stages; the next
+// step's operands are loaded into registers while the current one is
+// multiplied, then stored to the other stage (one barrier per step).
+constexpr int kInvBK = 32;
+
+template <typename T, int BM>
+constexpr size_t fwd_inv_smem(int stages) { return (size_t)stages * kInvBK * (BM + inv_cols<T>()) * sizeof(T); }
+template <typename T, int BM>
+constexpr size_t bwd_inv_smem(int stages) { return (size_t)stages * kInvBK * (BM + 1 + inv_cols<T>()) * sizeof(T); }
+
 // CTA (front of the height, BM-row tile of its nf rows, column tile): rows
 // r < ns of the product go to Y (store), rows r >= ns to the ancestors' rows
 // of X (atomic subtraction: siblings share them).
-template <typename T, int BM>
-__global__ void __launch_bounds__(256) k_solve_fwd_inv(FrontDev fd, const int *__restrict__ nodes, int rt_per,
+template <typename T, int BM, int STAGES>
+__global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_fwd_inv(FrontDev fd, const int *__restrict__ nodes,
+                                                                          int rt_per,
                                                        const T *__restrict__ arena, int k, T *__restrict__ X,
                                                        T *__restrict__ Y, int ldx, bool vec) {
-    constexpr int BK = 32, BN = inv_cols<T>();
+    constexpr int BK = kInvBK, BN = inv_cols<T>();
     constexpr int CG = BN / 4, RGS = 256 / CG, RPT = BM / RGS;
-    __shared__ __align__(16) T As[BK][BM];
-    __shared__ __align__(16) T Bs[BK][BN];
+    constexpr int AE = BK * BM / 256, BE = BK * CG / 256;  // per-thread loads of one step
+    static_assert(BK * BM % 256 == 0 && BK * CG % 256 == 0, "tile");
+    // stage-major [2][BK][BN + BM]: B first (16-byte rows), then A; launches
+    // whose fronts all have ns <= BK (one step) allocate stage 0 only
+    extern __shared__ __align__(16) unsigned char inv_smem[];
+    T *const base = reinterpret_cast<T *>(inv_smem);
+    constexpr int STAGE = BK * (BN + BM);
     const int t = nodes[blockIdx.x / rt_per];
     const int r0 = (blockIdx.x % rt_per) * BM;
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
@@ -255,35 +272,70 @@ __global__ void __launch_bounds__(256) k_solve_fwd_inv(FrontDev fd, const int *_
     for (int u = 0; u < RPT; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    // Linv(r, j) = 0 for j > r: a tile inside the pivot rows stops at its last row
-    const int kend = (r0 + BM <= ns) ? r0 + BM : ns;
-    for (int k0 = 0; k0 < kend; k0 += BK) {
-        for (int idx = tid; idx < BK * BM; idx += 256) {
-            const int i = idx % BM, kk = idx / BM;
+    T ra[AE], rb[BE][4];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < AE; ++q) {
+            const int idx = tid + 256 * q, i = idx % BM, kk = idx / BM;
             const int r = r0 + i, j = k0 + kk;
             T a = T(0);
             if (r < nf && j < ns) a = (r >= ns || r > j) ? F[(int64_t)j * nf + r] : (r == j ? T(1) : T(0));
-            As[kk][i] = a;
+            ra[q] = a;
         }
-        for (int idx = tid; idx < BK * CG; idx += 256) {
-            const int kk = idx / CG, c = (idx % CG) * 4;
-            T b[4];
-            load4(b, X, (int64_t)ps + k0 + kk, k0 + kk < ns, c0 + c, k, ldx, vec);
-            sts4(&Bs[kk][c], b);
+#pragma unroll
+        for (int q = 0; q < BE; ++q) {
+            const int idx = tid + 256 * q, kk = idx / CG, c = (idx % CG) * 4;
+            load4(rb[q], X, (int64_t)ps + k0 + kk, k0 + kk < ns, c0 + c, k, ldx, vec);
         }
-        __syncthreads();
+    };
+    auto store = [&](int st) {
+        T *bs = base + st * STAGE, *as = bs + BK * BN;
+#pragma unroll
+        for (int q = 0; q < AE; ++q) {
+            const int idx = tid + 256 * q;
+            as[(idx / BM) * BM + idx % BM] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < BE; ++q) {
+            const int idx = tid + 256 * q;
+            sts4(bs + (idx / CG) * BN + (idx % CG) * 4, rb[q]);
+        }
+    };
+    auto compute = [&](int st) {
+        const T *bs = base + st * STAGE, *as = bs + BK * BN;
 #pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
             T b[4], a[RPT];
-            lds4(b, &Bs[kk][cg]);
+            lds4(b, bs + kk * BN + cg);
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) a[u] = As[kk][rg * RPT + u];
+            for (int u = 0; u < RPT; ++u) a[u] = as[kk * BM + rg * RPT + u];
 #pragma unroll
             for (int u = 0; u < RPT; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
         }
+    };
+    // Linv(r, j) = 0 for j > r: a tile inside the pivot rows stops at its last row
+    const int kend = (r0 + BM <= ns) ? r0 + BM : ns;
+    if constexpr (STAGES == 1) {
+        for (int k0 = 0; k0 < kend; k0 += BK) {
+            load(k0);
+            store(0);
+            __syncthreads();
+            compute(0);
+            __syncthreads();
+        }
+    } else {
+        load(0);
+        store(0);
         __syncthreads();
+        for (int k0 = 0, st = 0; k0 < kend; k0 += BK, st ^= 1) {
+            const bool more = k0 + BK < kend;
+            if (more) load(k0 + BK);
+            compute(st);
+            if (more) store(st ^ 1);
+            __syncthreads();
+        }
     }
     const int *rows = fd.rows + fd.rows_off[t];
     const int avail = k - c0 - cg;
@@ -300,15 +352,18 @@ __global__ void __launch_bounds__(256) k_solve_fwd_inv(FrontDev fd, const int *_
 // CTA (front of the height, BM-row tile of its ns pivot rows, column tile);
 // K runs over the front's rows: pivots (Linv^T, Y scaled by D^-1), then the
 // ancestors' rows (-W^T, final X rows gathered).
-template <typename T, int BM>
-__global__ void __launch_bounds__(256) k_solve_bwd_inv(FrontDev fd, const int *__restrict__ nodes, int rt_per,
+template <typename T, int BM, int STAGES>
+__global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(FrontDev fd, const int *__restrict__ nodes,
+                                                                          int rt_per,
                                                        const T *__restrict__ arena, const T *__restrict__ dinv, int k,
                                                        T *__restrict__ X, const T *__restrict__ Y, int ldx, bool vec) {
-    constexpr int BK = 32, BN = inv_cols<T>();
+    constexpr int BK = kInvBK, BN = inv_cols<T>(), LDA = BM + 1;
     constexpr int CG = BN / 4, RGS = 256 / CG, RPT = BM / RGS;
-    static_assert(RPT >= 1, "tile too small");
-    __shared__ __align__(16) T As[BK][BM + 1];
-    __shared__ __align__(16) T Bs[BK][BN];
+    constexpr int AE = BK * BM / 256, BE = BK * CG / 256;
+    static_assert(RPT >= 1 && BK * BM % 256 == 0 && BK * CG % 256 == 0, "tile");
+    extern __shared__ __align__(16) unsigned char inv_smem[];
+    T *Bs = reinterpret_cast<T *>(inv_smem);  // [STAGES][BK][BN] (16-byte aligned rows)
+    T *As = Bs + STAGES * BK * BN;            // [STAGES][BK][BM + 1]
     const int t = nodes[blockIdx.x / rt_per];
     const int i0 = (blockIdx.x % rt_per) * BM;
     const int nf = fd.nf[t], ns = fd.ns[t], ps = fd.pstart[t];
@@ -322,45 +377,81 @@ __global__ void __launch_bounds__(256) k_solve_bwd_inv(FrontDev fd, const int *_
     for (int u = 0; u < RPT; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-    // Linv^T(i, r) = Linv(r, i) = 0 for r < i: start at the tile's first row
-    for (int k0 = (i0 / BK) * BK; k0 < nf; k0 += BK) {
-        for (int idx = tid; idx < BK * BM; idx += 256) {
-            const int kk = idx % BK, ii = idx / BK;
+    T ra[AE], rb[BE][4];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < AE; ++q) {
+            const int idx = tid + 256 * q, kk = idx % BK, ii = idx / BK;
             const int i = i0 + ii, r = k0 + kk;
             T a = T(0);
             if (i < ns && r < nf) {
                 if (r >= ns) a = -F[(int64_t)i * nf + r];
                 else a = r > i ? F[(int64_t)i * nf + r] : (r == i ? T(1) : T(0));
             }
-            As[kk][ii] = a;
+            ra[q] = a;
         }
-        for (int idx = tid; idx < BK * CG; idx += 256) {
-            const int kk = idx / CG, c = (idx % CG) * 4;
+#pragma unroll
+        for (int q = 0; q < BE; ++q) {
+            const int idx = tid + 256 * q, kk = idx / CG, c = (idx % CG) * 4;
             const int r = k0 + kk;
-            T b[4];
             if (r < ns) {
-                load4(b, Y, (int64_t)ps + r, true, c0 + c, k, ldx, vec);
+                load4(rb[q], Y, (int64_t)ps + r, true, c0 + c, k, ldx, vec);
                 const T di = dinv[ps + r];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) b[v] *= di;
+                for (int v = 0; v < 4; ++v) rb[q][v] *= di;
             } else {
-                load4(b, X, r < nf ? (int64_t)rows[r] : 0, r < nf, c0 + c, k, ldx, vec);
+                load4(rb[q], X, r < nf ? (int64_t)rows[r] : 0, r < nf, c0 + c, k, ldx, vec);
             }
-            sts4(&Bs[kk][c], b);
         }
-        __syncthreads();
+    };
+    auto store = [&](int st) {
+        T *as = As + st * BK * LDA, *bs = Bs + st * BK * BN;
+#pragma unroll
+        for (int q = 0; q < AE; ++q) {
+            const int idx = tid + 256 * q;
+            as[(idx % BK) * LDA + idx / BK] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < BE; ++q) {
+            const int idx = tid + 256 * q;
+            sts4(bs + (idx / CG) * BN + (idx % CG) * 4, rb[q]);
+        }
+    };
+    auto compute = [&](int st) {
+        const T *as = As + st * BK * LDA, *bs = Bs + st * BK * BN;
 #pragma unroll 8
         for (int kk = 0; kk < BK; ++kk) {
             T b[4], a[RPT];
-            lds4(b, &Bs[kk][cg]);
+            lds4(b, bs + kk * BN + cg);
 #pragma unroll
-            for (int u = 0; u < RPT; ++u) a[u] = As[kk][rg * RPT + u];
+            for (int u = 0; u < RPT; ++u) a[u] = as[kk * LDA + rg * RPT + u];
 #pragma unroll
             for (int u = 0; u < RPT; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
         }
+    };
+    // Linv^T(i, r) = Linv(r, i) = 0 for r < i: start at the tile's first row
+    const int kbeg = (i0 / BK) * BK;
+    if constexpr (STAGES == 1) {
+        for (int k0 = kbeg; k0 < nf; k0 += BK) {
+            load(k0);
+            store(0);
+            __syncthreads();
+            compute(0);
+            __syncthreads();
+        }
+    } else {
+        load(kbeg);
+        store(0);
         __syncthreads();
+        for (int k0 = kbeg, st = 0; k0 < nf; k0 += BK, st ^= 1) {
+            const bool more = k0 + BK < nf;
+            if (more) load(k0 + BK);
+            compute(st);
+            if (more) store(st ^ 1);
+            __syncthreads();
+        }
     }
     const int avail = k - c0 - cg;
     if (avail <= 0) return;
@@ -470,18 +561,39 @@ void reciprocal(cudaStream_t s, int n, const T *x, T *y) {
     HSIM_LAUNCHED();
 }
 
-template <typename T>
-void solve_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, const T *arena,
-                   int k, T *X, T *Y, int ldx) {
-    if (n_nodes <= 0 || k <= 0 || max_nf <= 0) return;
-    const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
-    // 64-row tiles also for the lowest heights (nf <= ~100): one 128-row tile
-    // per front (pivot rows read once) measured slower, 786 against 685 ms of
-    // solves per 10^6-vertex solve
-    const int rt = (max_nf + 63) / 64;
-    k_solve_fwd_inv<T, 64><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, 0, s>>>(
+template <typename T, int STAGES>
+void launch_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int rt, const T *arena, int k,
+                    T *X, T *Y, int ldx, bool vec) {
+    constexpr size_t sm = fwd_inv_smem<T, 64>(STAGES);
+    HSIM_SMEM_LIMIT_ONCE((k_solve_fwd_inv<T, 64, STAGES>), sm);
+    k_solve_fwd_inv<T, 64, STAGES><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, sm, s>>>(
         fd, nodes, rt, arena, k, X, Y, ldx, vec);
     HSIM_LAUNCHED();
+}
+
+template <typename T, int BM, int STAGES>
+void launch_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int rt, const T *arena,
+                    const T *dinv, int k, T *X, const T *Y, int ldx, bool vec) {
+    constexpr size_t sm = bwd_inv_smem<T, BM>(STAGES);
+    HSIM_SMEM_LIMIT_ONCE((k_solve_bwd_inv<T, BM, STAGES>), sm);
+    k_solve_bwd_inv<T, BM, STAGES><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, sm, s>>>(
+        fd, nodes, rt, arena, dinv, k, X, Y, ldx, vec);
+    HSIM_LAUNCHED();
+}
+
+// One K step per tile when every front of the height has ns <= 32 (the
+// lowest heights): single-stage kernels (fewer registers, more CTAs per SM);
+// otherwise the pipelined two-stage kernels.  64-row tiles also for the
+// lowest heights: one 128-row tile per front (pivot rows read once) measured
+// slower, 786 against 685 ms of solves per 10^6-vertex solve.
+template <typename T>
+void solve_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, int max_ns,
+                   const T *arena, int k, T *X, T *Y, int ldx) {
+    if (n_nodes <= 0 || k <= 0 || max_nf <= 0) return;
+    const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
+    const int rt = (max_nf + 63) / 64;
+    if (max_ns <= kInvBK) launch_fwd_inv<T, 1>(s, fd, nodes, n_nodes, rt, arena, k, X, Y, ldx, vec);
+    else launch_fwd_inv<T, 2>(s, fd, nodes, n_nodes, rt, arena, k, X, Y, ldx, vec);
 }
 
 template <typename T>
@@ -489,30 +601,22 @@ void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
                    const T *dinv, int k, T *X, const T *Y, int ldx) {
     if (n_nodes <= 0 || k <= 0 || max_ns <= 0) return;
     const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
-    const dim3 grid_small((unsigned)((int64_t)n_nodes * ((max_ns + 31) / 32)), cdiv(k, inv_cols<T>()));
-    if (max_ns <= 32 || sizeof(T) == 8) {
-        // 32 pivot rows per tile (FP64: 64 columns x 32 rows keeps RPT = 2)
-        k_solve_bwd_inv<T, 32><<<grid_small, 256, 0, s>>>(fd, nodes, (max_ns + 31) / 32, arena, dinv, k, X, Y, ldx,
-                                                         vec);
-    } else {
-        const int rt = (max_ns + 63) / 64;
-        k_solve_bwd_inv<T, 64><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, 0, s>>>(
-            fd, nodes, rt, arena, dinv, k, X, Y, ldx, vec);
-    }
-    HSIM_LAUNCHED();
+    if (max_ns <= 32) launch_bwd_inv<T, 32, 1>(s, fd, nodes, n_nodes, 1, arena, dinv, k, X, Y, ldx, vec);
+    else launch_bwd_inv<T, 64, 2>(s, fd, nodes, n_nodes, (max_ns + 63) / 64, arena, dinv, k, X, Y, ldx, vec);
 }
 
 #define HSIM_FINV_INSTANTIATE(T)                                                                                    \
     template void inv_diag_blocks<T>(cudaStream_t, const FrontDev &, const int2 *, int, T *);                     \
     template void gemm_tasks<T>(cudaStream_t, const GemmTask *, int, int, const T *, const T *, T *);             \
     template void copy_tasks<T>(cudaStream_t, const GemmTask *, int, int, const T *, T *);                        \
-    template void reciprocal<T>(cudaStream_t, int, const T *, T *);                                               \
-    template void solve_fwd_inv<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, T *, \
-                                   int);                                                                          \
-    template void solve_bwd_inv<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, const T *, int, \
-                                   T *, const T *, int);
+    template void reciprocal<T>(cudaStream_t, int, const T *, T *);
 HSIM_FINV_INSTANTIATE(float)
 HSIM_FINV_INSTANTIATE(double)
+// the inverted-form solves serve the FP32 factor only
+template void solve_fwd_inv<float>(cudaStream_t, const FrontDev &, const int *, int, int, int, const float *, int,
+                                   float *, float *, int);
+template void solve_bwd_inv<float>(cudaStream_t, const FrontDev &, const int *, int, int, const float *,
+                                   const float *, int, float *, const float *, int);
 
 }  // namespace k
 }  // namespace hsim

@@ -216,8 +216,8 @@ void reciprocal(cudaStream_t s, int n, const T *x, T *y);
 // forward substitution of one tree height on the inverted fronts:
 // Y[pivots of t] = Linv_t X[pivots of t], X[ancestor rows of t] -= W_t X[pivots of t]
 template <typename T>
-void solve_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, const T *arena,
-                   int k, T *X, T *Y, int ldx);
+void solve_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, int max_ns,
+                   const T *arena, int k, T *X, T *Y, int ldx);
 // backward substitution of one tree height: X[pivots of t] = Linv_t^T D^-1 Y[pivots of t] - W_t^T X[ancestor rows]
 template <typename T>
 void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_ns, const T *arena,
