@@ -642,7 +642,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 fail(HSIM_E_BREAKDOWN, "FP32 factor of the positive definite shifted matrix has " +
                                            std::to_string(negp) + " negative pivot(s)");
             H->X32.reserve((size_t)n * q32);
-            H->rho.reserve(2 * (size_t)q);
+            H->rho.reserve(3 * (size_t)q);
         }
         // One inverse iteration in correction form (mixed path): for any
         // scalar rho, K^-1 M psi = (psi - K^-1 (S psi - rho M psi)) / (rho - mu).
@@ -653,7 +653,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         // [0, a) with leading dimension q; num / den give rho per column.
         auto correction_step = [&](const double *X, const double *SX, const double *MX, const double *num,
                                    const double *den, double *Y, int a) {
-            k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->X32.p, q32);
+            k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->rho.p + 2 * q, H->X32.p, q32);
             solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->dinvf32.p, H->ysol32, H->X32.p, a, q32);
             k::sub_f2d(s, n, a, X, q, H->X32.p, q32, Y, q);
         };
@@ -695,8 +695,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                     double *Pa = H->Psi.p + locked;
                     apply_S(ctx, H, tau, a, Pa, q, H->SP.p + locked, q);
                     apply_M(ctx, H, tau, a, Pa, q, H->MP.p + locked, q);
-                    k::col_dots(s, n, a, Pa, q, H->SP.p + locked, q, nullptr, H->rho.p);
-                    k::col_dots(s, n, a, Pa, q, H->MP.p + locked, q, nullptr, H->rho.p + q);
+                    k::col_dots2_mixed(s, n, a, Pa, q, H->SP.p + locked, H->MP.p + locked, q, H->rho.p,
+                                       H->rho.p + q);
                     correction_step(Pa, H->SP.p + locked, H->MP.p + locked, H->rho.p, H->rho.p + q, Pa, a);
                 }
             } else {
@@ -778,7 +778,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             apply_S(ctx, H, tau, q, H->Phi.p, q, H->SP.p, q);
             apply_M(ctx, H, tau, q, H->Phi.p, q, H->MP.p, q);
             // only the pairs i < p enter the test and the locking
-            k::residual_sums(s, n, p, H->SP.p, q, H->MP.p, q, H->lam.p, dinv, H->res_sums.p);
+            if (mixed) k::residual_sums_mixed(s, n, p, H->SP.p, q, H->MP.p, q, H->lam.p, dinv, H->res_sums.p);
+            else k::residual_sums(s, n, p, H->SP.p, q, H->MP.p, q, H->lam.p, dinv, H->res_sums.p);
             HSIM_CUDA(cudaMemcpyAsync(rs.data(), H->res_sums.p, 3 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->lam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaStreamSynchronize(s));

@@ -16,6 +16,7 @@
 
 #include "common.h"
 #include "host.h"
+#include "fpconv.h"
 #include "kernels.h"
 
 namespace cg = cooperative_groups;
@@ -186,6 +187,52 @@ __global__ void k_residual_sums(int n, int k, const T *__restrict__ SP, int lds,
         atomicAdd(&out[3 * j], a0);
         atomicAdd(&out[3 * j + 1], a1);
         atomicAdd(&out[3 * j + 2], a2);
+    }
+}
+
+// Mixed path, the Rayleigh quotients of the correction step: w1 = diag(X^T Y1),
+// w2 = diag(X^T Y2) in one pass over X, products and sums in FP32 over a
+// block of rows (the correction form is exact for any quotient; an FP32
+// accurate one keeps the corrections small).
+__global__ void k_col_dots2_mixed(int n, int k, const double *__restrict__ X, int ldx, const double *__restrict__ Y1,
+                                  const double *__restrict__ Y2, int ldy, double *__restrict__ w1,
+                                  double *__restrict__ w2) {
+    const int r_beg = blockIdx.x * kRowsPerBlock;
+    const int r_end = min(n, r_beg + kRowsPerBlock);
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
+        float a1 = 0.f, a2 = 0.f;
+        for (int r = r_beg; r < r_end; ++r) {
+            const float x = d2f_trunc(X[(size_t)r * ldx + j]);
+            a1 = fmaf(x, d2f_trunc(Y1[(size_t)r * ldy + j]), a1);
+            a2 = fmaf(x, d2f_trunc(Y2[(size_t)r * ldy + j]), a2);
+        }
+        atomicAdd(&w1[j], (double)a1);
+        atomicAdd(&w2[j], (double)a2);
+    }
+}
+
+// Mixed path: the residual s - lambda m in FP64 (it cancels), the three sums of
+// squares (positive terms, well conditioned) in FP32 over a block of rows
+// before the FP64 atomics: one FP64 instruction per element instead of seven.
+__global__ void k_residual_sums_mixed(int n, int k, const double *__restrict__ SP, int lds,
+                                      const double *__restrict__ MP, int ldm, const double *__restrict__ lam,
+                                      const double *__restrict__ dinv, double *__restrict__ out) {
+    const int r_beg = blockIdx.x * kRowsPerBlock;
+    const int r_end = min(n, r_beg + kRowsPerBlock);
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
+        const double l = lam[j];
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        for (int r = r_beg; r < r_end; ++r) {
+            const double sv = SP[(size_t)r * lds + j], mv = MP[(size_t)r * ldm + j];
+            const float rr = d2f_trunc(fma(-l, mv, sv)), sf = d2f_trunc(sv), mf = d2f_trunc(mv);
+            const float w = dinv ? d2f_trunc(dinv[r]) : 1.f;
+            a0 = fmaf(w * rr, rr, a0);
+            a1 = fmaf(w * sf, sf, a1);
+            a2 = fmaf(w * mf, mf, a2);
+        }
+        atomicAdd(&out[3 * j], (double)a0);
+        atomicAdd(&out[3 * j + 1], (double)a1);
+        atomicAdd(&out[3 * j + 2], (double)a2);
     }
 }
 
@@ -477,6 +524,25 @@ void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *
     if (n <= 0 || k <= 0) return;
     dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
     k_residual_sums<T><<<g, 256, 0, s>>>(n, k, SP, lds, MP, ldm, lam, dinv, out);
+    HSIM_LAUNCHED();
+}
+
+void col_dots2_mixed(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y1, const double *Y2,
+                     int ldy, double *w1, double *w2) {
+    HSIM_CUDA(cudaMemsetAsync(w1, 0, (size_t)k * sizeof(double), s));
+    HSIM_CUDA(cudaMemsetAsync(w2, 0, (size_t)k * sizeof(double), s));
+    if (n <= 0 || k <= 0) return;
+    dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
+    k_col_dots2_mixed<<<g, 256, 0, s>>>(n, k, X, ldx, Y1, Y2, ldy, w1, w2);
+    HSIM_LAUNCHED();
+}
+
+void residual_sums_mixed(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
+                         const double *lam, const double *dinv, double *out) {
+    HSIM_CUDA(cudaMemsetAsync(out, 0, (size_t)3 * k * sizeof(double), s));
+    if (n <= 0 || k <= 0) return;
+    dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
+    k_residual_sums_mixed<<<g, 256, 0, s>>>(n, k, SP, lds, MP, ldm, lam, dinv, out);
     HSIM_LAUNCHED();
 }
 

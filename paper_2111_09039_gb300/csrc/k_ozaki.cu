@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "common.h"
+#include "fpconv.h"
 #include "kernels.h"
 
 namespace hsim {
@@ -447,7 +448,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int c = 0; c < 32; ++c) {
                 const int j = j0 + c0 + c;
                 if (j < N && (!lower || j <= i)) {
-                    const double v = ldexp((double)hi[c] + (double)lo[c], ex[i] + ey[j] - 14);
+                    // exact conversions and the power-of-two scaling on the
+                    // bit patterns: one FP64 instruction per output
+                    const double v = scale2(f2d_bits(hi[c]) + f2d_bits(lo[c]), ex[i] + ey[j] - 14);
                     if (atomic) atomicAdd(&C[(size_t)i * ldc + j], v);
                     else C[(size_t)i * ldc + j] = v;
                     if (lower && j < i) {

@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include "common.h"
+#include "fpconv.h"
 #include "kernels.h"
 
 namespace hsim {
@@ -171,17 +172,6 @@ __global__ void k_split_df(int rows, int k, const double *__restrict__ X, int ld
     X2[(size_t)r * k + c] = split_df(X[(size_t)r * ldx + c]);
 }
 
-// exact FP32 -> FP64 conversion from the bit pattern (no FP64 instruction);
-// FP32 subnormals take the conversion instruction
-__device__ __forceinline__ double f2d_bits(float x) {
-    const unsigned u = __float_as_uint(x);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u) return (u & 0x7fffffffu) == 0u ? __longlong_as_double((long long)(u & 0x80000000u) << 32) : (double)x;
-    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
-                                            ((unsigned long long)(e + 896u) << 52) |
-                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
-}
-
 // one warp per row, lane j owns columns j, j + 32, ... (kChunk per pass)
 template <int kChunk>
 __global__ void k_spmm_df(int n_rows, const int *__restrict__ ptr, const int *__restrict__ col,
@@ -279,18 +269,12 @@ __global__ void k_shifted_residual(int n_rows, const int *__restrict__ ptr, cons
 }
 
 __global__ void k_axpy_matrix(int n, int k, const double *__restrict__ X, int ldx, double *__restrict__ Y, int ldy) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n * k) return;
-    int i = (int)(idx / k), j = (int)(idx % k);
-    Y[(size_t)i * ldy + j] += X[(size_t)i * ldx + j];
+    HSIM_FOR_RC(i, n, j, k) Y[(size_t)i * ldy + j] += X[(size_t)i * ldx + j];
 }
 
 __global__ void k_diag_scale(int n, int k, const double *__restrict__ d, const double *__restrict__ X, int ldx,
                              double *__restrict__ Y, int ldy) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n * k) return;
-    int i = (int)(idx / k), j = (int)(idx % k);
-    Y[(size_t)i * ldy + j] = d[i] * X[(size_t)i * ldx + j];
+    HSIM_FOR_RC(i, n, j, k) Y[(size_t)i * ldy + j] = d[i] * X[(size_t)i * ldx + j];
 }
 
 __device__ __forceinline__ int find_col(const int *__restrict__ c, int lo, int hi, int key) {
@@ -359,18 +343,12 @@ __global__ void k_gather_values_i(int64_t n, const int *__restrict__ map, const 
 
 __global__ void k_gather_rows(int n, int k, const int *__restrict__ perm, const double *__restrict__ X, int ldx,
                               double *__restrict__ Y, int ldy) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n * k) return;
-    int i = (int)(idx / k), j = (int)(idx % k);
-    Y[(size_t)i * ldy + j] = X[(size_t)perm[i] * ldx + j];
+    HSIM_FOR_RC(i, n, j, k) Y[(size_t)i * ldy + j] = X[(size_t)perm[i] * ldx + j];
 }
 
 __global__ void k_copy_matrix(int rows, int cols, const double *__restrict__ X, int ldx, double *__restrict__ Y,
                               int ldy) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)rows * cols) return;
-    int i = (int)(idx / cols), j = (int)(idx % cols);
-    Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j];
+    HSIM_FOR_RC(i, rows, j, cols) Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j];
 }
 
 __global__ void k_densify(int n, const int *__restrict__ ptr, const int *__restrict__ col,
@@ -445,24 +423,26 @@ __global__ void k_add_f2d(int rows, int cols, const float *__restrict__ X, int l
     Y[(size_t)i * ldy + j] += (double)X[(size_t)i * ldx + j];
 }
 
-// R (FP32) = SP - rho_j MP, rho_j = num[j] / den[j] (den NULL: rho_j = num[j])
+// rho_j = num[j] / den[j] (den NULL: rho_j = num[j]), once per column
+__global__ void k_rho(int cols, const double *__restrict__ num, const double *__restrict__ den,
+                      double *__restrict__ rho) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < cols) rho[j] = den ? num[j] / den[j] : num[j];
+}
+
+// R (FP32) = SP - rho_j MP: the difference in FP64 (it cancels), then
+// truncated to FP32
 __global__ void k_residual_f32(int rows, int cols, const double *__restrict__ SP, int lds,
-                               const double *__restrict__ MP, int ldm, const double *__restrict__ num,
-                               const double *__restrict__ den, float *__restrict__ R, int ldr) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)rows * cols) return;
-    int i = (int)(idx / cols), j = (int)(idx % cols);
-    double rho = den ? num[j] / den[j] : num[j];
-    R[(size_t)i * ldr + j] = (float)(SP[(size_t)i * lds + j] - rho * MP[(size_t)i * ldm + j]);
+                               const double *__restrict__ MP, int ldm, const double *__restrict__ rho,
+                               float *__restrict__ R, int ldr) {
+    HSIM_FOR_RC(i, rows, j, cols) R[(size_t)i * ldr + j] =
+        d2f_trunc(fma(-rho[j], MP[(size_t)i * ldm + j], SP[(size_t)i * lds + j]));
 }
 
 // Y (FP64) = X - Z (FP32)
 __global__ void k_sub_f2d(int rows, int cols, const double *__restrict__ X, int ldx, const float *__restrict__ Z,
                           int ldz, double *__restrict__ Y, int ldy) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)rows * cols) return;
-    int i = (int)(idx / cols), j = (int)(idx % cols);
-    Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j] - (double)Z[(size_t)i * ldz + j];
+    HSIM_FOR_RC(i, rows, j, cols) Y[(size_t)i * ldy + j] = X[(size_t)i * ldx + j] - f2d_bits(Z[(size_t)i * ldz + j]);
 }
 
 template <typename T>
@@ -567,13 +547,13 @@ void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col
 
 void axpy_matrix(cudaStream_t s, int n, int k, const double *X, int ldx, double *Y, int ldy) {
     if (n <= 0 || k <= 0) return;
-    k_axpy_matrix<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, X, ldx, Y, ldy);
+    k_axpy_matrix<<<grid_rc(n, k), 256, 0, s>>>(n, k, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 
 void diag_scale(cudaStream_t s, int n, int k, const double *d, const double *X, int ldx, double *Y, int ldy) {
     if (n <= 0 || k <= 0) return;
-    k_diag_scale<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, d, X, ldx, Y, ldy);
+    k_diag_scale<<<grid_rc(n, k), 256, 0, s>>>(n, k, d, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 
@@ -604,13 +584,13 @@ void gather_values_i(cudaStream_t s, int64_t n, const int *map, const double *in
 
 void gather_rows(cudaStream_t s, int n, int k, const int *perm, const double *X, int ldx, double *Y, int ldy) {
     if (n <= 0 || k <= 0) return;
-    k_gather_rows<<<grid1d((int64_t)n * k, 256), 256, 0, s>>>(n, k, perm, X, ldx, Y, ldy);
+    k_gather_rows<<<grid_rc(n, k), 256, 0, s>>>(n, k, perm, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 
 void copy_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, double *Y, int ldy) {
     if (rows <= 0 || cols <= 0) return;
-    k_copy_matrix<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
+    k_copy_matrix<<<grid_rc(rows, cols), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 
@@ -652,15 +632,17 @@ void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double
     HSIM_LAUNCHED();
 }
 void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *MP, int ldm,
-                  const double *num, const double *den, float *R, int ldr) {
+                  const double *num, const double *den, double *rho, float *R, int ldr) {
     if (rows <= 0 || cols <= 0) return;
-    k_residual_f32<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, SP, lds, MP, ldm, num, den, R, ldr);
+    k_rho<<<(cols + 255) / 256, 256, 0, s>>>(cols, num, den, rho);
+    HSIM_LAUNCHED();
+    k_residual_f32<<<grid_rc(rows, cols), 256, 0, s>>>(rows, cols, SP, lds, MP, ldm, rho, R, ldr);
     HSIM_LAUNCHED();
 }
 void sub_f2d(cudaStream_t s, int rows, int cols, const double *X, int ldx, const float *Z, int ldz, double *Y,
              int ldy) {
     if (rows <= 0 || cols <= 0) return;
-    k_sub_f2d<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Z, ldz, Y, ldy);
+    k_sub_f2d<<<grid_rc(rows, cols), 256, 0, s>>>(rows, cols, X, ldx, Z, ldz, Y, ldy);
     HSIM_LAUNCHED();
 }
 void copy_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, float *Y, int ldy) {

@@ -71,9 +71,11 @@ void convert_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx
 void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
 // Y (FP64) += X (FP32)
 void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
-// R (FP32) = SP - rho MP column-wise, rho_j = num[j] / den[j] (den NULL: num[j])
+// R (FP32) = SP - rho MP column-wise, rho_j = num[j] / den[j] (den NULL: num[j]),
+// formed once per column into rho (cols doubles of scratch); the difference
+// in FP64, then truncated to FP32
 void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *MP, int ldm,
-                  const double *num, const double *den, float *R, int ldr);
+                  const double *num, const double *den, double *rho, float *R, int ldr);
 // Y (FP64) = X - Z (FP32)
 void sub_f2d(cudaStream_t s, int rows, int cols, const double *X, int ldx, const float *Z, int ldz, double *Y,
              int ldy);
@@ -105,6 +107,14 @@ void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, T *X, int l
 template <typename T>
 void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *MP, int ldm,
                    const double *lam, const double *dinv, double *out);
+// w1 = diag(X^T Y1), w2 = diag(X^T Y2) (mixed path, FP32 products and sums
+// per 256-row block, FP64 totals)
+void col_dots2_mixed(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y1, const double *Y2,
+                     int ldy, double *w1, double *w2);
+// residual_sums of the mixed path: the residual in FP64, the sums of squares
+// accumulated in FP32 over 256-row blocks (relative accuracy ~1e-6)
+void residual_sums_mixed(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
+                         const double *lam, const double *dinv, double *out);
 // dense symmetric generalised eigensolver, k x k: LDL^T of M_bar, the lowest
 // m (<= 0: all k) pairs of C^-1 S_bar C^-T by sym_eig, X (k x m) = C^-T V;
 // returns 0 ok, 1 not SPD; *sweeps = 0 (kept for the Jacobi variant's report).
