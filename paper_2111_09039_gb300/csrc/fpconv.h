@@ -48,8 +48,10 @@ __device__ __forceinline__ double scale2(double x, int e) {
     for (int i = blockIdx.y; i < (rows); i += gridDim.y)                                \
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (cols); j += gridDim.x * blockDim.x)
 
+// at most 2048 row strides: each block walks many rows (launching one block
+// per row of a 10^6-row block spends the time in block scheduling)
 inline dim3 grid_rc(int rows, int cols, int threads = 256) {
     const int cx = (cols + threads - 1) / threads;
-    const int ry = rows < 65535 ? (rows > 0 ? rows : 1) : 65535;
+    const int ry = rows < 2048 ? (rows > 0 ? rows : 1) : 2048;
     return dim3((unsigned)(cx > 0 ? cx : 1), (unsigned)ry);
 }
