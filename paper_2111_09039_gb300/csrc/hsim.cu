@@ -651,9 +651,11 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         // FP64 psi it corrects; the factor 1 / (rho - mu) > 0 is dropped (the
         // columns are rescaled before the Gram).  X, SX, MX: FP64, columns
         // [0, a) with leading dimension q; num / den give rho per column.
+        // MX == nullptr: M is the diagonal Md0int (level 0) and M X is not formed
         auto correction_step = [&](const double *X, const double *SX, const double *MX, const double *num,
                                    const double *den, double *Y, int a) {
-            k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->rho.p + 2 * q, H->X32.p, q32);
+            if (MX) k::residual_f32(s, n, a, SX, q, MX, q, num, den, H->rho.p + 2 * q, H->X32.p, q32);
+            else k::residual_f32_diag(s, n, a, SX, q, X, q, H->Md0int.p, num, den, H->rho.p + 2 * q, H->X32.p, q32);
             solve_level_t<float>(ctx, L, H->arena32.p, H->dpos32.p, H->dinvf32.p, H->ysol32, H->X32.p, a, q32);
             k::sub_f2d(s, n, a, X, q, H->X32.p, q32, Y, q);
         };
@@ -694,10 +696,18 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 for (int extra = 1; extra < o.inv_iters; ++extra) {
                     double *Pa = H->Psi.p + locked;
                     apply_S(ctx, H, tau, a, Pa, q, H->SP.p + locked, q);
-                    apply_M(ctx, H, tau, a, Pa, q, H->MP.p + locked, q);
-                    k::col_dots2_mixed(s, n, a, Pa, q, H->SP.p + locked, H->MP.p + locked, q, H->rho.p,
-                                       H->rho.p + q);
-                    correction_step(Pa, H->SP.p + locked, H->MP.p + locked, H->rho.p, H->rho.p + q, Pa, a);
+                    if (tau == 0) {
+                        // diagonal M: M Psi enters only through m_i psi_i (MP is
+                        // recomputed for the Gram below)
+                        k::col_dots2_diag_mixed(s, n, a, Pa, q, H->SP.p + locked, q, H->Md0int.p, H->rho.p,
+                                                H->rho.p + q);
+                        correction_step(Pa, H->SP.p + locked, nullptr, H->rho.p, H->rho.p + q, Pa, a);
+                    } else {
+                        apply_M(ctx, H, tau, a, Pa, q, H->MP.p + locked, q);
+                        k::col_dots2_mixed(s, n, a, Pa, q, H->SP.p + locked, H->MP.p + locked, q, H->rho.p,
+                                           H->rho.p + q);
+                        correction_step(Pa, H->SP.p + locked, H->MP.p + locked, H->rho.p, H->rho.p + q, Pa, a);
+                    }
                 }
             } else {
                 k::copy_matrix(s, n, a, H->MP.p + locked, q, H->Psi.p + locked, q);

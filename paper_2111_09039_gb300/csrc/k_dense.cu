@@ -211,6 +211,24 @@ __global__ void k_col_dots2_mixed(int n, int k, const double *__restrict__ X, in
     }
 }
 
+// as k_col_dots2_mixed with Y2 = diag(m) X: w2 = sum m_i x_i^2
+__global__ void k_col_dots2_diag_mixed(int n, int k, const double *__restrict__ X, int ldx,
+                                       const double *__restrict__ Y1, int ldy, const double *__restrict__ m,
+                                       double *__restrict__ w1, double *__restrict__ w2) {
+    const int r_beg = blockIdx.x * kRowsPerBlock;
+    const int r_end = min(n, r_beg + kRowsPerBlock);
+    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
+        float a1 = 0.f, a2 = 0.f;
+        for (int r = r_beg; r < r_end; ++r) {
+            const float x = d2f_trunc(X[(size_t)r * ldx + j]);
+            a1 = fmaf(x, d2f_trunc(Y1[(size_t)r * ldy + j]), a1);
+            a2 = fmaf(d2f_trunc(m[r]) * x, x, a2);
+        }
+        atomicAdd(&w1[j], (double)a1);
+        atomicAdd(&w2[j], (double)a2);
+    }
+}
+
 // Mixed path: the residual s - lambda m in FP64 (it cancels), the three sums of
 // squares (positive terms, well conditioned) in FP32 over a block of rows
 // before the FP64 atomics: one FP64 instruction per element instead of seven.
@@ -534,6 +552,16 @@ void col_dots2_mixed(cudaStream_t s, int n, int k, const double *X, int ldx, con
     if (n <= 0 || k <= 0) return;
     dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
     k_col_dots2_mixed<<<g, 256, 0, s>>>(n, k, X, ldx, Y1, Y2, ldy, w1, w2);
+    HSIM_LAUNCHED();
+}
+
+void col_dots2_diag_mixed(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y1, int ldy,
+                          const double *m, double *w1, double *w2) {
+    HSIM_CUDA(cudaMemsetAsync(w1, 0, (size_t)k * sizeof(double), s));
+    HSIM_CUDA(cudaMemsetAsync(w2, 0, (size_t)k * sizeof(double), s));
+    if (n <= 0 || k <= 0) return;
+    dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
+    k_col_dots2_diag_mixed<<<g, 256, 0, s>>>(n, k, X, ldx, Y1, ldy, m, w1, w2);
     HSIM_LAUNCHED();
 }
 

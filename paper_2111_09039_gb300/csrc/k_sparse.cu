@@ -532,6 +532,14 @@ __global__ void k_residual_f32(int rows, int cols, const double *__restrict__ SP
         d2f_trunc(fma(-rho[j], MP[(size_t)i * ldm + j], SP[(size_t)i * lds + j]));
 }
 
+// R (FP32) = SP - rho_j m_i X with M = diag(m): M X is not formed
+__global__ void k_residual_f32_diag(int rows, int cols, const double *__restrict__ SP, int lds,
+                                    const double *__restrict__ X, int ldx, const double *__restrict__ m,
+                                    const double *__restrict__ rho, float *__restrict__ R, int ldr) {
+    HSIM_FOR_RC(i, rows, j, cols) R[(size_t)i * ldr + j] =
+        d2f_trunc(fma(-rho[j] * m[i], X[(size_t)i * ldx + j], SP[(size_t)i * lds + j]));
+}
+
 // Y (FP64) = X - Z (FP32)
 __global__ void k_sub_f2d(int rows, int cols, const double *__restrict__ X, int ldx, const float *__restrict__ Z,
                           int ldz, double *__restrict__ Y, int ldy) {
@@ -730,6 +738,14 @@ void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds,
     k_rho<<<(cols + 255) / 256, 256, 0, s>>>(cols, num, den, rho);
     HSIM_LAUNCHED();
     k_residual_f32<<<grid_rc(rows, cols), 256, 0, s>>>(rows, cols, SP, lds, MP, ldm, rho, R, ldr);
+    HSIM_LAUNCHED();
+}
+void residual_f32_diag(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *X, int ldx,
+                       const double *m, const double *num, const double *den, double *rho, float *R, int ldr) {
+    if (rows <= 0 || cols <= 0) return;
+    k_rho<<<(cols + 255) / 256, 256, 0, s>>>(cols, num, den, rho);
+    HSIM_LAUNCHED();
+    k_residual_f32_diag<<<grid_rc(rows, cols), 256, 0, s>>>(rows, cols, SP, lds, X, ldx, m, rho, R, ldr);
     HSIM_LAUNCHED();
 }
 void sub_f2d(cudaStream_t s, int rows, int cols, const double *X, int ldx, const float *Z, int ldz, double *Y,

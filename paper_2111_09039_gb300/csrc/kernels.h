@@ -76,6 +76,9 @@ void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double
 // in FP64, then truncated to FP32
 void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *MP, int ldm,
                   const double *num, const double *den, double *rho, float *R, int ldr);
+// the same with M = diag(m): R = SP - rho_j m_i X
+void residual_f32_diag(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *X, int ldx,
+                       const double *m, const double *num, const double *den, double *rho, float *R, int ldr);
 // Y (FP64) = X - Z (FP32)
 void sub_f2d(cudaStream_t s, int rows, int cols, const double *X, int ldx, const float *Z, int ldz, double *Y,
              int ldy);
@@ -111,6 +114,9 @@ void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *
 // per 256-row block, FP64 totals)
 void col_dots2_mixed(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y1, const double *Y2,
                      int ldy, double *w1, double *w2);
+// col_dots2_mixed with Y2 = diag(m) X (M not formed)
+void col_dots2_diag_mixed(cudaStream_t s, int n, int k, const double *X, int ldx, const double *Y1, int ldy,
+                          const double *m, double *w1, double *w2);
 // residual_sums of the mixed path: the residual in FP64, the sums of squares
 // accumulated in FP32 over 256-row blocks (relative accuracy ~1e-6)
 void residual_sums_mixed(cudaStream_t s, int n, int k, const double *SP, int lds, const double *MP, int ldm,
