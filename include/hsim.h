@@ -294,6 +294,16 @@ hsim_status hsim_level_pattern(const hsim_hier *hier, int tau, int *n, int64_t *
 hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *hier, int tau, const double *S_val_dev,
                                const double *M_val_dev, double mu, int k, double *B_dev, int ldb,
                                int *negative_pivots);
+/* The same solve as done by the mixed-precision path: the factorisation in
+ * FP32 rewritten into the inverted form (pivot blocks inverted once, one
+ * batched product per tree height and direction) and the solve in FP32; B
+ * and X stay FP64 (converted at the boundary).  Meant for positive definite
+ * K (mu below the spectrum), as the mixed path shifts; accuracy about the
+ * condition of K times 2^-24.  Pivots below 1e-7 max|K_ii| fail with
+ * HSIM_E_BREAKDOWN. */
+hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *hier, int tau, const double *S_val_dev,
+                                   const double *M_val_dev, double mu, int k, double *B_dev, int ldb,
+                                   int *negative_pivots);
 
 /* Allocation-free variant of hsim_ritz, for callers that cannot let a
  * library allocate device memory (a framework that reserves the whole

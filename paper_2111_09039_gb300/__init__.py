@@ -344,12 +344,14 @@ def galerkin(ctx: Context, n: int, nc: int, A_ptr: np.ndarray, A_col: np.ndarray
     return rp, cl, vals
 
 
-def shifted_solve(ctx: Context, hier: Hierarchy, tau: int, S_val, M_val, mu: float, B):
-    """X = (S - mu M)^-1 B on level tau (natural order); returns (X, #negative pivots)."""
+def shifted_solve(ctx: Context, hier: Hierarchy, tau: int, S_val, M_val, mu: float, B, f32: bool = False):
+    """X = (S - mu M)^-1 B on level tau (natural order); returns (X, #negative pivots).
+    f32=True: the mixed path's FP32 inverted-factor solve (hsim_shifted_solve_f32)."""
     X = B.clone().contiguous()
     neg = ctypes.c_int()
-    check(lib().hsim_shifted_solve(ctx.handle, hier.handle, tau, ptr(S_val), ptr(M_val), float(mu), X.shape[1],
-                                   ptr(X), X.stride(0), ctypes.byref(neg)))
+    fn = lib().hsim_shifted_solve_f32 if f32 else lib().hsim_shifted_solve
+    check(fn(ctx.handle, hier.handle, tau, ptr(S_val), ptr(M_val), float(mu), X.shape[1], ptr(X), X.stride(0),
+             ctypes.byref(neg)))
     return X, neg.value
 
 

@@ -1423,4 +1423,32 @@ hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *h, int tau, const doubl
     });
 }
 
+hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *h, int tau, const double *S_val, const double *M_val,
+                                   double mu, int kk, double *B, int ldb, int *neg) {
+    return guard([&] {
+        HSIM_CHECK_ARG(ctx && h && S_val && M_val && B, "NULL argument");
+        HSIM_CHECK_ARG(tau >= 0 && tau + 1 < h->T, "level has no sparse factorisation");
+        HSIM_CHECK_ARG(kk >= 1 && ldb >= kk, "bad sizes");
+        DeviceGuard dg(ctx->device);
+        cudaStream_t s = ctx->stream;
+        LevelData &L = h->lev[tau];
+        DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(tau == 0 ? (size_t)L.n : (size_t)L.dpat.nnz);
+        k::gather_values(s, L.dpat.nnz, L.dvmap.p, S_val, Sv.p);
+        if (tau == 0) k::gather_values_i(s, L.n, L.d_perm.p, M_val, Mv.p);
+        else k::gather_values(s, L.dpat.nnz, L.dvmap.p, M_val, Mv.p);
+        int negp = factor_level_t<float>(ctx, L, Sv.p, tau == 0 ? nullptr : Mv.p, tau == 0 ? Mv.p : nullptr, mu,
+                                         h->arena32, h->dpos32, h->dinvf32, h->invs32, 1e-7);
+        DevBuf<double> X((size_t)L.n * kk);
+        k::gather_rows(s, L.n, kk, L.d_perm.p, B, ldb, X.p, kk);
+        const int ld = (kk + 3) & ~3;  // 16-byte rows (vector atomics of the forward products)
+        DevBuf<float> X32((size_t)L.n * ld);
+        k::convert_matrix(s, L.n, kk, X.p, kk, X32.p, ld);
+        solve_level_t<float>(ctx, L, h->arena32.p, h->dpos32.p, h->dinvf32.p, h->ysol32, X32.p, kk, ld);
+        k::convert_matrix(s, L.n, kk, X32.p, ld, X.p, kk);
+        k::gather_rows(s, L.n, kk, L.d_iperm.p, X.p, kk, B, ldb);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        if (neg) *neg = negp;
+    });
+}
+
 }  // extern "C"

@@ -228,6 +228,32 @@ def test_shifted_solve_matches_scipy(hs, ctx, torus_case, tau, mu):
     assert neg == int((ev < mu_eff).sum())
 
 
+@pytest.mark.parametrize("tau,mu,k", [(0, -50.0, 9), (0, -5.0, 130), (1, -70.0, 9), (1, -70.0, 130)])
+def test_shifted_solve_f32_inverted_form(hs, ctx, torus_case, tau, mu, k):
+    # the mixed path's FP32 factor in inverted form (pivot blocks inverted,
+    # one batched product per tree height) on positive definite shifts; the
+    # error bound is the condition of K times a small multiple of 2^-24
+    w, mesh, s, H, hier = torus_case
+    S0 = assembly.stiffness(mesh)
+    M0 = assembly.lumped_mass(mesh)
+    S, M = galerkin.level_matrices(S0, M0, H.U)
+    rp, cl = hier.level_pattern(tau)
+    St = S[tau].tocsr()
+    Mt = M[tau].tocsr()
+    Sv = _values_in(St, rp, cl)
+    Mv = M0 if tau == 0 else _values_in(Mt, rp, cl)
+    B = np.random.default_rng(10 + tau).standard_normal((St.shape[0], k))
+    X, neg = hs.shifted_solve(ctx, hier, tau, dev(Sv), dev(Mv), mu, dev(B), f32=True)
+    K = (St - mu * Mt).tocsc()
+    Xr = spla.spsolve(K, B)
+    Xr = Xr.reshape(B.shape)
+    ev = sla.eigh(St.toarray(), Mt.toarray(), eigvals_only=True)
+    cond = (ev.max() - mu) / (ev.min() - mu) * (Mt.diagonal().max() / Mt.diagonal().min())
+    err = np.abs(X.cpu().numpy() - Xr).max() / np.abs(Xr).max()
+    assert err < 50 * cond * 2.0 ** -24, (err, cond)
+    assert neg == 0
+
+
 def _values_in(A, rp, cl):
     """values of A in the CSR pattern (rp, cl) (zeros where A has none)"""
     A = A.tocsr()
