@@ -141,7 +141,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed FP64 solves for the mixed-vs-FP64 comparison (0 = skip)")
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--sample-cols", type=int, default=8)
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
@@ -255,7 +255,9 @@ def main():
     S_d = torch.empty_like(S)
     Md_d = torch.empty_like(Md)
     e2e_ms = []
-    for _ in range(max(0, args.e2e_steps)):
+    # one untimed step first: the first device-to-host copy into the freshly
+    # pinned 4 GB buffer pays a one-time setup that no later call sees
+    for step in range(max(0, args.e2e_steps) + (1 if args.e2e_steps > 0 else 0)):
         barrier()
         t1 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -266,7 +268,8 @@ def main():
             lam_h.copy_(lam_d, non_blocking=True)
             vec_h.copy_(Phi_d.t(), non_blocking=True)
         stream.synchronize()
-        e2e_ms.append((time.perf_counter() - t1) * 1000.0)
+        if step > 0:
+            e2e_ms.append((time.perf_counter() - t1) * 1000.0)
     h2d = S.numel() * 8 + Md.numel() * 8
     d2h = p * 8 + p * hier.n * 8
 
@@ -289,8 +292,8 @@ def main():
                    "levels": hier.sizes, "precision": args.precision, "parallelism": "replicas" if world > 1 else "1 gpu",
                    "l2": "working set > L2 (n x q float64 blocks of 6 GB)"},
         "hier_build_s": hier_s, "max_residual_check": res,
-        "e2e": ({"value": min(e2e_ms) / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-                if e2e_ms else None),
+        "e2e": ({"value": sum(e2e_ms) / len(e2e_ms) / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d,
+                 "d2h_bytes_per_step": d2h, "steps": len(e2e_ms), "warmup": 1} if e2e_ms else None),
         "gpu_launches": int(round(launches)),
         "fp64_gpu": fp64,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "info": info,
