@@ -336,6 +336,15 @@ hsim_status hsim_ritz_noalloc(void *cuda_stream, int k, const double *Sbar_dev, 
 hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int32_t *col, const double *val,
                                 int leaf_size, int nrhs, const double *B, double *X,
                                 int *negative_pivots, int64_t *nnz_L);
+/* The same host replay for the inverted form of the mixed path's solves
+ * (FP64 on the host): after the factorisation every pivot block is inverted
+ * in place by the tasks of the GPU's inversion plan (32 x 32 diagonal blocks,
+ * block doubling, W = L_bs Linv), then one product per front and direction
+ * in the GPU's order of tree heights.  Arguments and results as
+ * hsim_check_symbolic.  Needs no GPU. */
+hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, const double *val,
+                                int leaf_size, int nrhs, const double *B, double *X,
+                                int *negative_pivots, int64_t *nnz_L);
 
 #ifdef __cplusplus
 }

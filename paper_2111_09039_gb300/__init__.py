@@ -355,8 +355,9 @@ def shifted_solve(ctx: Context, hier: Hierarchy, tau: int, S_val, M_val, mu: flo
     return X, neg.value
 
 
-def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32):
-    """Host replay of the factorisation over the symbolic analysis (no GPU)."""
+def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32, inverted: bool = False):
+    """Host replay of the factorisation over the symbolic analysis (no GPU);
+    inverted=True: the inverted-factor solve of the mixed path (hsim_check_inverted)."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.float64)
@@ -366,6 +367,7 @@ def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32):
     X = np.empty_like(B)
     neg = ctypes.c_int()
     nnzL = ctypes.c_int64()
-    check(lib().hsim_check_symbolic(len(row_ptr) - 1, ptr(row_ptr), ptr(col), ptr(val), leaf_size, B.shape[1],
-                                    ptr(B), ptr(X), ctypes.byref(neg), ctypes.byref(nnzL)))
+    fn = lib().hsim_check_inverted if inverted else lib().hsim_check_symbolic
+    check(fn(len(row_ptr) - 1, ptr(row_ptr), ptr(col), ptr(val), leaf_size, B.shape[1], ptr(B), ptr(X),
+             ctypes.byref(neg), ctypes.byref(nnzL)))
     return X, neg.value, nnzL.value

@@ -3,88 +3,106 @@
 // arithmetic as the GPU kernels of k_front.cu (front arena layout, panels of
 // kPanel columns, extend-add through relmap, row lists of the solves).  It
 // lets the symbolic analysis be checked on a machine without a GPU; the
-// solver itself never calls it.
+// solver itself never calls it.  hsim_check_inverted replays the inverted
+// form of the FP32 solves (k_finv.cu) the same way: the inversion tasks of
+// k::inverse_plan executed with the semantics of k_gemm_tasks, then one
+// product per front and direction.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 
 #include "host.h"
+#include "kernels.h"
 
 using namespace hsim;
+
+namespace {
+
+// assembly and numeric LDL^T of A over its symbolic analysis, as the GPU
+// kernels do them; fills fs, the arena and the number of negative pivots
+void factor_host(int n, const int32_t *ptr, const int32_t *col, const double *val, int leaf_size, FrontSymbolic &fs,
+                 std::vector<double> &arena, int &neg) {
+    Csr A;
+    A.n_rows = A.n_cols = n;
+    A.ptr.assign(ptr, ptr + n + 1);
+    A.col.assign(col, col + A.ptr[n]);
+    A.val.assign(val, val + A.ptr[n]);
+    fs = analyse(A, leaf_size);
+    std::vector<int64_t> vmap;
+    Csr Ai = permute_symmetric(A, fs.iperm, &vmap);
+    std::vector<int64_t> dst = assembly_map(fs, Ai);
+    arena.assign(fs.arena, 0.0);
+    for (int64_t e = 0; e < Ai.nnz(); ++e) {
+        if (dst[e] < 0) continue;
+        if (dst[e] >= fs.arena) fail(HSIM_E_INTERNAL, "assembly destination outside the arena");
+        arena[dst[e]] = A.val[vmap[e]];
+    }
+    neg = 0;
+    for (int h = 0; h <= fs.max_height; ++h) {
+        for (int c : fs.ea_children[h]) {
+            int p = fs.parent[c];
+            int u = fs.nf[c] - fs.ns[c];
+            const double *Fc = arena.data() + fs.foff[c];
+            double *Fp = arena.data() + fs.foff[p];
+            const int *rel = fs.relmap.data() + fs.relmap_off[c];
+            for (int j = 0; j < u; ++j)
+                for (int i = j; i < u; ++i) {
+                    int64_t di = (int64_t)rel[j] * fs.nf[p] + rel[i];
+                    if (rel[i] < rel[j] || di >= (int64_t)fs.nf[p] * fs.nf[p])
+                        fail(HSIM_E_INTERNAL, "extend-add outside the parent's lower triangle");
+                    Fp[di] += Fc[(int64_t)(fs.ns[c] + j) * fs.nf[c] + fs.ns[c] + i];
+                }
+        }
+        for (int t : fs.by_height[h]) {
+            const int nf = fs.nf[t], ns = fs.ns[t];
+            double *F = arena.data() + fs.foff[t];
+            for (int k0 = 0; k0 < ns; k0 += kPanel) {
+                int kb = std::min(kPanel, ns - k0);
+                // panel: LDL^T of the diagonal block, then rows below
+                for (int j = 0; j < kb; ++j) {
+                    double d = F[(int64_t)(k0 + j) * nf + k0 + j];
+                    for (int r = j + 1; r < kb; ++r) {
+                        double l = F[(int64_t)(k0 + j) * nf + k0 + r] / d;
+                        for (int c = j + 1; c <= r; ++c)
+                            F[(int64_t)(k0 + c) * nf + k0 + r] -= l * d * F[(int64_t)(k0 + j) * nf + k0 + c] / d;
+                    }
+                    for (int r = j + 1; r < kb; ++r) F[(int64_t)(k0 + j) * nf + k0 + r] /= d;
+                }
+                for (int r = k0 + kb; r < nf; ++r) {
+                    double x[kPanel];
+                    for (int c = 0; c < kb; ++c) {
+                        double v = F[(int64_t)(k0 + c) * nf + r];
+                        for (int cc = 0; cc < c; ++cc) v -= x[cc] * F[(int64_t)(k0 + cc) * nf + k0 + c];
+                        x[c] = v;
+                    }
+                    for (int c = 0; c < kb; ++c) F[(int64_t)(k0 + c) * nf + r] = x[c] / F[(int64_t)(k0 + c) * nf + k0 + c];
+                }
+                // trailing update
+                for (int c = k0 + kb; c < nf; ++c)
+                    for (int r = c; r < nf; ++r) {
+                        double acc = 0.0;
+                        for (int kk = 0; kk < kb; ++kk)
+                            acc += F[(int64_t)(k0 + kk) * nf + r] * F[(int64_t)(k0 + kk) * nf + k0 + kk] *
+                                   F[(int64_t)(k0 + kk) * nf + c];
+                        F[(int64_t)c * nf + r] -= acc;
+                    }
+            }
+            for (int i = 0; i < ns; ++i) neg += F[(int64_t)i * nf + i] < 0.0;
+        }
+    }
+}
+
+}  // namespace
 
 extern "C" hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int32_t *col, const double *val,
                                            int leaf_size, int nrhs, const double *B, double *X, int *neg_pivots,
                                            int64_t *nnz_L) {
     try {
         HSIM_CHECK_ARG(n > 0 && ptr && col && val && B && X && nrhs >= 1, "bad arguments");
-        Csr A;
-        A.n_rows = A.n_cols = n;
-        A.ptr.assign(ptr, ptr + n + 1);
-        A.col.assign(col, col + A.ptr[n]);
-        A.val.assign(val, val + A.ptr[n]);
-        FrontSymbolic fs = analyse(A, leaf_size);
-        std::vector<int64_t> vmap;
-        Csr Ai = permute_symmetric(A, fs.iperm, &vmap);
-        std::vector<int64_t> dst = assembly_map(fs, Ai);
-        std::vector<double> arena(fs.arena, 0.0);
-        for (int64_t e = 0; e < Ai.nnz(); ++e) {
-            if (dst[e] < 0) continue;
-            if (dst[e] >= fs.arena) fail(HSIM_E_INTERNAL, "assembly destination outside the arena");
-            arena[dst[e]] = A.val[vmap[e]];
-        }
+        FrontSymbolic fs;
+        std::vector<double> arena;
         int neg = 0;
-        for (int h = 0; h <= fs.max_height; ++h) {
-            for (int c : fs.ea_children[h]) {
-                int p = fs.parent[c];
-                int u = fs.nf[c] - fs.ns[c];
-                const double *Fc = arena.data() + fs.foff[c];
-                double *Fp = arena.data() + fs.foff[p];
-                const int *rel = fs.relmap.data() + fs.relmap_off[c];
-                for (int j = 0; j < u; ++j)
-                    for (int i = j; i < u; ++i) {
-                        int64_t di = (int64_t)rel[j] * fs.nf[p] + rel[i];
-                        if (rel[i] < rel[j] || di >= (int64_t)fs.nf[p] * fs.nf[p])
-                            fail(HSIM_E_INTERNAL, "extend-add outside the parent's lower triangle");
-                        Fp[di] += Fc[(int64_t)(fs.ns[c] + j) * fs.nf[c] + fs.ns[c] + i];
-                    }
-            }
-            for (int t : fs.by_height[h]) {
-                const int nf = fs.nf[t], ns = fs.ns[t];
-                double *F = arena.data() + fs.foff[t];
-                for (int k0 = 0; k0 < ns; k0 += kPanel) {
-                    int kb = std::min(kPanel, ns - k0);
-                    // panel: LDL^T of the diagonal block, then rows below
-                    for (int j = 0; j < kb; ++j) {
-                        double d = F[(int64_t)(k0 + j) * nf + k0 + j];
-                        for (int r = j + 1; r < kb; ++r) {
-                            double l = F[(int64_t)(k0 + j) * nf + k0 + r] / d;
-                            for (int c = j + 1; c <= r; ++c)
-                                F[(int64_t)(k0 + c) * nf + k0 + r] -= l * d * F[(int64_t)(k0 + j) * nf + k0 + c] / d;
-                        }
-                        for (int r = j + 1; r < kb; ++r) F[(int64_t)(k0 + j) * nf + k0 + r] /= d;
-                    }
-                    for (int r = k0 + kb; r < nf; ++r) {
-                        double x[kPanel];
-                        for (int c = 0; c < kb; ++c) {
-                            double v = F[(int64_t)(k0 + c) * nf + r];
-                            for (int cc = 0; cc < c; ++cc) v -= x[cc] * F[(int64_t)(k0 + cc) * nf + k0 + c];
-                            x[c] = v;
-                        }
-                        for (int c = 0; c < kb; ++c) F[(int64_t)(k0 + c) * nf + r] = x[c] / F[(int64_t)(k0 + c) * nf + k0 + c];
-                    }
-                    // trailing update
-                    for (int c = k0 + kb; c < nf; ++c)
-                        for (int r = c; r < nf; ++r) {
-                            double acc = 0.0;
-                            for (int kk = 0; kk < kb; ++kk)
-                                acc += F[(int64_t)(k0 + kk) * nf + r] * F[(int64_t)(k0 + kk) * nf + k0 + kk] *
-                                       F[(int64_t)(k0 + kk) * nf + c];
-                            F[(int64_t)c * nf + r] -= acc;
-                        }
-                }
-                for (int i = 0; i < ns; ++i) neg += F[(int64_t)i * nf + i] < 0.0;
-            }
-        }
+        factor_host(n, ptr, col, val, leaf_size, fs, arena, neg);
         // solve in the internal order
         std::vector<double> Y((size_t)n * nrhs);
         for (int pos = 0; pos < n; ++pos)
@@ -139,6 +157,130 @@ extern "C" hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int3
             }
         for (int pos = 0; pos < n; ++pos)
             std::memcpy(&X[(size_t)fs.perm[pos] * nrhs], &Y[(size_t)pos * nrhs], nrhs * sizeof(double));
+        if (neg_pivots) *neg_pivots = neg;
+        if (nnz_L) *nnz_L = fs.nnz_L;
+        return HSIM_OK;
+    } catch (const Error &e) {
+        return e.status;
+    } catch (...) {
+        return HSIM_E_INTERNAL;
+    }
+}
+
+namespace {
+
+// C = (+/-) A B of one inversion task, with the operand reads of k_gemm_tasks
+void run_task(const k::GemmTask &tk, const double *Ab, const double *Bb, double *Cb) {
+    const bool ua = tk.flags & k::kGemmAUnitLower, ub = tk.flags & k::kGemmBUnitLower;
+    auto at = [&](int i, int kk) {
+        if (!ua) return Ab[tk.a + (int64_t)kk * tk.lda + i];
+        return i > kk ? Ab[tk.a + (int64_t)kk * tk.lda + i] : (i == kk ? 1.0 : 0.0);
+    };
+    auto bt = [&](int kk, int j) {
+        if (!ub) return Bb[tk.b + (int64_t)j * tk.ldb + kk];
+        return kk > j ? Bb[tk.b + (int64_t)j * tk.ldb + kk] : (kk == j ? 1.0 : 0.0);
+    };
+    const double sg = (tk.flags & k::kGemmNeg) ? -1.0 : 1.0;
+    std::vector<double> out((size_t)tk.M * tk.N);
+    for (int j = 0; j < tk.N; ++j)
+        for (int i = 0; i < tk.M; ++i) {
+            double acc = 0.0;
+            for (int kk = 0; kk < tk.K; ++kk) acc += at(i, kk) * bt(kk, j);
+            out[(size_t)j * tk.M + i] = sg * acc;
+        }
+    for (int j = 0; j < tk.N; ++j)
+        for (int i = 0; i < tk.M; ++i) Cb[tk.c + (int64_t)j * tk.ldc + i] = out[(size_t)j * tk.M + i];
+}
+
+}  // namespace
+
+extern "C" hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, const double *val,
+                                           int leaf_size, int nrhs, const double *B, double *X, int *neg_pivots,
+                                           int64_t *nnz_L) {
+    try {
+        HSIM_CHECK_ARG(n > 0 && ptr && col && val && B && X && nrhs >= 1, "bad arguments");
+        FrontSymbolic fs;
+        std::vector<double> arena;
+        int neg = 0;
+        factor_host(n, ptr, col, val, leaf_size, fs, arena, neg);
+        // inversion: 32 x 32 diagonal blocks, block-doubling levels, W = L_bs Linv
+        k::InversePlan P = k::inverse_plan(fs.nf, fs.ns, fs.foff);
+        for (const int2 &b : P.blk) {
+            const int t = b.x, b0 = b.y, nf = fs.nf[t], kb = std::min(32, fs.ns[t] - b0);
+            double *F = arena.data() + fs.foff[t];
+            double Lb[32][32] = {}, Xb[32][32] = {};
+            for (int r = 0; r < kb; ++r)
+                for (int c = 0; c < r; ++c) Lb[r][c] = F[(int64_t)(b0 + c) * nf + b0 + r];
+            for (int c = 0; c < kb; ++c) {
+                Xb[c][c] = 1.0;
+                for (int r = c + 1; r < kb; ++r) {
+                    double acc = Lb[r][c];
+                    for (int j = c + 1; j < r; ++j) acc += Lb[r][j] * Xb[j][c];
+                    Xb[r][c] = -acc;
+                }
+            }
+            for (int r = 0; r < kb; ++r)
+                for (int c = 0; c < r; ++c) F[(int64_t)(b0 + c) * nf + b0 + r] = Xb[r][c];
+        }
+        std::vector<double> scr((size_t)std::max<int64_t>(P.scratch, 1));
+        for (size_t lv = 0; lv < P.p1.size(); ++lv) {
+            for (const k::GemmTask &tk : P.p1[lv]) run_task(tk, arena.data(), arena.data(), scr.data());
+            for (const k::GemmTask &tk : P.p2[lv]) run_task(tk, arena.data(), scr.data(), arena.data());
+        }
+        for (const k::GemmTask &tk : P.w) run_task(tk, arena.data(), arena.data(), scr.data());
+        for (const k::GemmTask &tk : P.wc)
+            for (int j = 0; j < tk.N; ++j)
+                for (int i = 0; i < tk.M; ++i)
+                    arena[tk.c + (int64_t)j * tk.ldc + i] = scr[tk.a + (int64_t)j * tk.lda + i];
+        // forward per height: Y_s = Linv X_s, X_b -= W X_s (k_solve_fwd_inv)
+        std::vector<double> Xi((size_t)n * nrhs), Y((size_t)n * nrhs, 0.0);
+        for (int pos = 0; pos < n; ++pos)
+            std::memcpy(&Xi[(size_t)pos * nrhs], &B[(size_t)fs.perm[pos] * nrhs], nrhs * sizeof(double));
+        auto row = [&](int t, int r) { return fs.rows[fs.rows_off[t] + r]; };
+        std::vector<double> acc(nrhs);
+        for (int h = 0; h <= fs.max_height; ++h)
+            for (int t : fs.by_height[h]) {
+                const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+                const double *F = arena.data() + fs.foff[t];
+                for (int r = 0; r < nf; ++r) {
+                    std::fill(acc.begin(), acc.end(), 0.0);
+                    for (int j = 0; j < ns; ++j) {
+                        const double a = (r >= ns || r > j) ? F[(int64_t)j * nf + r] : (r == j ? 1.0 : 0.0);
+                        if (a != 0.0)
+                            for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)(ps + j) * nrhs + c];
+                    }
+                    if (r < ns) {
+                        for (int c = 0; c < nrhs; ++c) Y[(size_t)(ps + r) * nrhs + c] = acc[c];
+                    } else {
+                        const int g = row(t, r);
+                        if (g < 0 || g >= n) fail(HSIM_E_INTERNAL, "front row outside the matrix");
+                        for (int c = 0; c < nrhs; ++c) Xi[(size_t)g * nrhs + c] -= acc[c];
+                    }
+                }
+            }
+        // backward per height: X_s = Linv^T D^-1 Y_s - W^T X_b (k_solve_bwd_inv)
+        for (int h = fs.max_height; h >= 0; --h)
+            for (int t : fs.by_height[h]) {
+                const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+                const double *F = arena.data() + fs.foff[t];
+                for (int i = 0; i < ns; ++i) {
+                    std::fill(acc.begin(), acc.end(), 0.0);
+                    for (int r = i; r < nf; ++r) {
+                        if (r < ns) {
+                            const double a = r > i ? F[(int64_t)i * nf + r] : 1.0;
+                            const double dinv = 1.0 / F[(int64_t)r * nf + r];
+                            for (int c = 0; c < nrhs; ++c) acc[c] += a * Y[(size_t)(ps + r) * nrhs + c] * dinv;
+                        } else {
+                            const double a = -F[(int64_t)i * nf + r];
+                            const int g = row(t, r);
+                            for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)g * nrhs + c];
+                        }
+                    }
+                    for (int c = 0; c < nrhs; ++c) Xi[(size_t)(ps + i) * nrhs + c] = acc[c];
+                }
+            }
+        for (int pos = 0; pos < n; ++pos)
+            std::memcpy(&X[(size_t)fs.perm[pos] * nrhs], &Xi[(size_t)pos * nrhs], nrhs * sizeof(double));
         if (neg_pivots) *neg_pivots = neg;
         if (nnz_L) *nnz_L = fs.nnz_L;
         return HSIM_OK;

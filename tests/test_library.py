@@ -102,3 +102,55 @@ def test_symbolic_replay_disconnected_and_tiny(hs):
     X3, neg3, _ = hs.check_symbolic(K3.indptr, K3.indices, K3.data, np.eye(3), 32)
     np.testing.assert_allclose(X3, np.linalg.inv(K3.toarray()), rtol=1e-14)
     assert neg3 == 0
+
+
+# ---- inverted form of the mixed path's solves (host replay) -----------------
+@pytest.mark.parametrize("leaf,mu", [(4, -5.0), (16, 300.0), (32, -50.0), (64, 300.0)])
+def test_inverted_replay_solves_level0(hs, leaf, mu):
+    # the pivot blocks inverted by the GPU's inversion plan, then one product
+    # per front and direction; also for indefinite shifts (mu = 300) where
+    # the explicit inverses are those of an LDL^T without pivoting
+    mesh = synth.bumpy_torus(40, 36, 2)
+    S, M, K = _shifted(mesh, mu)
+    B = np.random.default_rng(leaf).standard_normal((mesh.n, 3))
+    X, neg, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, leaf, inverted=True)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-8 * np.abs(Xr).max()
+    X0, neg0, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, leaf)
+    assert neg == neg0
+
+
+def test_inverted_replay_large_separators(hs):
+    # an 80 x 80 torus grid: separators of 80 to 160 vertices, so the
+    # inversion runs several block-doubling levels with partial blocks
+    mesh = synth.bumpy_torus(80, 80, 5)
+    S, M, K = _shifted(mesh, -20.0)
+    B = np.random.default_rng(11).standard_normal((mesh.n, 2))
+    X, neg, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, 32, inverted=True)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-9 * np.abs(Xr).max()
+    assert neg == 0
+
+
+def test_inverted_replay_galerkin_level_and_forest(hs):
+    w, mesh, s = synth.make_workload("bumpy_torus_64")
+    H = hierarchy.build_hierarchy(mesh, w.p, w.levels, s)
+    S0 = assembly.stiffness(mesh)
+    M0 = assembly.lumped_mass(mesh)
+    S, M = galerkin.level_matrices(S0, M0, H.U)
+    K = (S[1] + 40.0 * M[1]).tocsr()
+    K.sort_indices()
+    B = np.random.default_rng(5).standard_normal((K.shape[0], 4))
+    X, neg, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, 32, inverted=True)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-9 * np.abs(Xr).max()
+    assert neg == 0
+    # two disjoint tori: a forest of two elimination trees
+    a = synth.bumpy_torus(12, 10, 1)
+    b = synth.bumpy_torus(9, 11, 2)
+    m2 = synth.Mesh(V=np.concatenate([a.V, b.V + 5.0]), F=np.concatenate([a.F, b.F + a.n]))
+    S2, M2, K2 = _shifted(m2, -1.0)
+    B2 = np.random.default_rng(0).standard_normal((m2.n, 2))
+    X2, _, _ = hs.check_symbolic(K2.indptr, K2.indices, K2.data, B2, 8, inverted=True)
+    Xr2 = spla.spsolve(K2.tocsc(), B2)
+    assert np.abs(X2 - Xr2).max() <= 1e-9 * np.abs(Xr2).max()
