@@ -255,8 +255,8 @@ def main():
     S_d = torch.empty_like(S)
     Md_d = torch.empty_like(Md)
     e2e_ms = []
-    # one untimed step first: the first device-to-host copy into the freshly
-    # pinned 4 GB buffer pays a one-time setup that no later call sees
+    # one untimed step first (first use of the pinned buffers and of the
+    # output allocations), then the mean of the timed steps
     for step in range(max(0, args.e2e_steps) + (1 if args.e2e_steps > 0 else 0)):
         barrier()
         t1 = time.perf_counter()
