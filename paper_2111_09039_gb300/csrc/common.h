@@ -52,18 +52,23 @@ extern std::atomic<uint64_t> g_launches;
                                           " (" __FILE__ ":" + std::to_string(__LINE__) + ")"); \
     } while (0)
 
-// Raise a kernel's dynamic shared-memory limit once per process to the largest
-// size any of its launches uses.  The limit is a process-wide attribute of the
-// function: setting it per launch to that launch's size races with launches
-// of the same kernel from other host threads (batched solves).
+// Raise a kernel's dynamic shared-memory limit once per device to the largest
+// size any of its launches uses.  The limit is an attribute of the function
+// on the current device shared by all host threads: setting it per launch to
+// that launch's size races with launches of the same kernel from other
+// threads (batched solves).
+constexpr int kMaxDevices = 64;
 #define HSIM_SMEM_LIMIT_ONCE(func, max_bytes)                                                        \
     do {                                                                                              \
-        static std::once_flag once_;                                                                  \
-        static cudaError_t err_ = cudaSuccess;                                                        \
-        std::call_once(once_, [&] {                                                                   \
-            err_ = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(max_bytes)); \
+        static std::once_flag once_[::hsim::kMaxDevices];                                             \
+        static cudaError_t err_[::hsim::kMaxDevices] = {};                                            \
+        int dev_ = 0;                                                                                 \
+        HSIM_CUDA(cudaGetDevice(&dev_));                                                              \
+        if (dev_ < 0 || dev_ >= ::hsim::kMaxDevices) ::hsim::fail(HSIM_E_CUDA, "device index above 63"); \
+        std::call_once(once_[dev_], [&] {                                                             \
+            err_[dev_] = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(max_bytes)); \
         });                                                                                           \
-        HSIM_CUDA(err_);                                                                              \
+        HSIM_CUDA(err_[dev_]);                                                                        \
     } while (0)
 
 // Owning device buffer.
