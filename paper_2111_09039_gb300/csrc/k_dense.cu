@@ -28,14 +28,13 @@ namespace {
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// SMs of the current device (queried per call: a process may drive GPUs of
+// different sizes; the attribute query costs about a microsecond)
 int sm_count() {
-    static const int n = [] {
-        int dev = 0, c = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-        return c > 0 ? c : 1;
-    }();
-    return n;
+    int dev = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    return c > 0 ? c : 1;
 }
 
 constexpr int TB = 64;  // output tile

@@ -195,14 +195,13 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
     lo = __fadd_rn(lo, err);
 }
 
+// SMs of the current device (queried per call: a process may drive GPUs of
+// different sizes; the attribute query costs about a microsecond)
 int sm_count_oz() {
-    static const int n = [] {
-        int dev = 0, c = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-        return c > 0 ? c : 1;
-    }();
-    return n;
+    int dev = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    return c > 0 ? c : 1;
 }
 
 // tcgen05 form of the same product (5th-generation tensor cores, TMEM).
