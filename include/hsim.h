@@ -61,11 +61,14 @@ typedef struct {
     int precision;       /* HSIM_FP64: every step in FP64, the paper's shift.
                             HSIM_MIXED: shift below the spectrum,
                             mu = -max(lambda_ref, 0.01 Lambda_{q-1}) (K positive
-                            definite), FP32 factor and FP32 solves of inverse
-                            iterations in correction form against FP64 bases; Gram
-                            products and basis update on BF16 tensor cores with
-                            FP64-accurate digit splitting (hsim_gram_tc); Ritz and
-                            residuals FP64 */
+                            definite), FP32 factor in inverted form and FP32 solves
+                            of the inverse iterations in correction form against
+                            FP64 bases (hsim_shifted_solve_f32); Gram products,
+                            basis update and the Ritz transforms on BF16 tensor
+                            cores with FP64-accurate digit splitting
+                            (hsim_gram_tc, hsim_ritz_tc); dense eigensolver and
+                            residual vectors FP64 (sums of squares of the
+                            convergence test accumulated in FP32 per row block) */
     int start_vertex;    /* first vertex of farthest-point sampling (Alg. 2) */
     int leaf_size;       /* nested-dissection leaf size (tuning, default 32) */
     int q;               /* subspace size; <= 0 selects max(ceil(1.5p), p+8) */
@@ -222,13 +225,13 @@ hsim_status hsim_eig_grad(hsim_ctx *ctx, int n, int n_tris, const double *V_dev,
 hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
                       const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
                       int ldx, double *Y_dev, int ldy);
-/* The same product as done by the mixed-precision path: FP64 values and X
- * are carried as pairs of FP32 values (double-float arithmetic on the FP32
- * pipe): each term carries a few units of 2^-46 |A[r, c] X[c, j]| (FP64:
- * 2^-53), so the result is within about 2^-42 sum_c |A[r, c] X[c, j]| for
- * rows of up to ~20 entries; values of magnitude below 2^-90 keep only FP32
- * accuracy.  Arguments as hsim_spmm; scratch for
- * the split values is allocated per call. */
+/* A double-float variant of hsim_spmm: FP64 values and X are carried as
+ * pairs of FP32 values (arithmetic on the FP32 pipe): each term carries a few
+ * units of 2^-46 |A[r, c] X[c, j]| (FP64: 2^-53), so the result is within
+ * about 2^-42 sum_c |A[r, c] X[c, j]| for rows of up to ~20 entries; values
+ * of magnitude below 2^-90 keep only FP32 accuracy.  The solve does not use
+ * it (on this GPU it measured slower than the FP64 product).  Arguments as
+ * hsim_spmm; scratch for the split values is allocated per call. */
 hsim_status hsim_spmm_df(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
                          const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
                          int ldx, double *Y_dev, int ldy);
