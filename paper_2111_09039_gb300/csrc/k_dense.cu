@@ -1,7 +1,8 @@
 // Dense FP64 kernels of the subspace iteration (Alg. 1):
 //   gram        S_bar = Psi^T (S Psi), M_bar = Psi^T (M Psi)  (tall-skinny, split-K)
 //   gemm_nn     Phi = Psi Phi_bar                                (basis update)
-//   col_dots    column M-norms, residual sums of eq. conv2
+//   residual sums of eq. conv2 (FP64, and the mixed path's FP32-accumulated
+//               form), Rayleigh quotients of the mixed correction step
 //   ritz        S_bar Phi_bar = M_bar Phi_bar Lambda_bar: M_bar = L D L^T
 //               (front kernels on one dense front), A = C^-1 S_bar C^-T with
 //               C = L D^1/2, the lowest eigenpairs of A by the tridiagonal
@@ -143,28 +144,7 @@ __global__ void __launch_bounds__(256) k_gemm_nn(int n, int kk, int m, const T *
 
 constexpr int kRowsPerBlock = 256;
 
-template <typename T>
-__global__ void k_col_dots(int n, int k, const T *__restrict__ X, int ldx, const T *__restrict__ Y, int ldy,
-                           const double *__restrict__ d, double *__restrict__ w) {
-    const int r_beg = blockIdx.x * kRowsPerBlock;
-    const int r_end = min(n, r_beg + kRowsPerBlock);
-    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < k; j += gridDim.y * blockDim.x) {
-        double acc = 0.0;
-        for (int r = r_beg; r < r_end; ++r) {
-            double v = (double)X[(size_t)r * ldx + j] * (double)Y[(size_t)r * ldy + j];
-            acc += d ? v * d[r] : v;
-        }
-        atomicAdd(&w[j], acc);
-    }
-}
 
-template <typename T>
-__global__ void k_scale_cols_rsqrt(int n, int k, const double *__restrict__ w, T *__restrict__ X, int ldx) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n * k) return;
-    int i = (int)(idx / k), j = (int)(idx % k);
-    X[(size_t)i * ldx + j] = (T)((double)X[(size_t)i * ldx + j] * rsqrt(w[j]));
-}
 
 template <typename T>
 __global__ void k_residual_sums(int n, int k, const T *__restrict__ SP, int lds, const T *__restrict__ MP,
@@ -518,21 +498,7 @@ void gemm_nn(cudaStream_t s, int n, int kk, int m, const T *A, int lda, const do
     HSIM_LAUNCHED();
 }
 
-template <typename T>
-void col_dots(cudaStream_t s, int n, int k, const T *X, int ldx, const T *Y, int ldy, const double *d, double *w) {
-    HSIM_CUDA(cudaMemsetAsync(w, 0, (size_t)k * sizeof(double), s));
-    if (n <= 0 || k <= 0) return;
-    dim3 g(cdiv(n, kRowsPerBlock), cdiv(k, 256));
-    k_col_dots<T><<<g, 256, 0, s>>>(n, k, X, ldx, Y, ldy, d, w);
-    HSIM_LAUNCHED();
-}
 
-template <typename T>
-void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, T *X, int ldx) {
-    if (n <= 0 || k <= 0) return;
-    k_scale_cols_rsqrt<T><<<cdiv((int64_t)n * k, 256), 256, 0, s>>>(n, k, w, X, ldx);
-    HSIM_LAUNCHED();
-}
 
 template <typename T>
 void residual_sums(cudaStream_t s, int n, int k, const T *SP, int lds, const T *MP, int ldm, const double *lam,
@@ -576,8 +542,6 @@ void residual_sums_mixed(cudaStream_t s, int n, int k, const double *SP, int lds
 #define HSIM_DENSE_INSTANTIATE(T)                                                                              \
     template void gram<T>(cudaStream_t, int, int, int, const T *, int, const T *, int, double *, int, bool);  \
     template void gemm_nn<T>(cudaStream_t, int, int, int, const T *, int, const double *, int, T *, int);    \
-    template void col_dots<T>(cudaStream_t, int, int, const T *, int, const T *, int, const double *, double *); \
-    template void scale_cols_rsqrt<T>(cudaStream_t, int, int, const double *, T *, int);                       \
     template void residual_sums<T>(cudaStream_t, int, int, const T *, int, const T *, int, const double *,     \
                                    const double *, double *);
 

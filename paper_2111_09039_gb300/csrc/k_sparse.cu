@@ -508,13 +508,6 @@ __global__ void k_convert_matrix(int rows, int cols, const Tin *__restrict__ X, 
     Y[(size_t)i * ldy + j] = (Tout)X[(size_t)i * ldx + j];
 }
 
-// Y (FP64) += X (FP32)
-__global__ void k_add_f2d(int rows, int cols, const float *__restrict__ X, int ldx, double *__restrict__ Y, int ldy) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)rows * cols) return;
-    int i = (int)(idx / cols), j = (int)(idx % cols);
-    Y[(size_t)i * ldy + j] += (double)X[(size_t)i * ldx + j];
-}
 
 // rho_j = num[j] / den[j] (den NULL: rho_j = num[j]), once per column
 __global__ void k_rho(int cols, const double *__restrict__ num, const double *__restrict__ den,
@@ -621,17 +614,6 @@ void spmm_df(cudaStream_t s, int n_rows, int n_cols, const int *ptr, const int *
     HSIM_LAUNCHED();
 }
 
-void spmm_f(cudaStream_t s, int n_rows, const int *ptr, const int *col, const float *val, int k, const float *X,
-            int ldx, float *Y, int ldy) {
-    if (n_rows <= 0 || k <= 0) return;
-    const int warps = 8;
-    unsigned g = grid1d(n_rows, warps);
-    if (k <= 32 * 8)
-        k_spmm<float, 8><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
-    else
-        k_spmm<float, 24><<<g, warps * 32, 0, s>>>(n_rows, ptr, col, val, k, X, ldx, Y, ldy);
-    HSIM_LAUNCHED();
-}
 
 void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *S, const double *M,
                       const double *Md, double mu, int k, const double *X, int ldx, const double *B, int ldb,
@@ -725,11 +707,6 @@ void convert_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx
 void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy) {
     if (rows <= 0 || cols <= 0) return;
     k_convert_matrix<float, double><<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
-    HSIM_LAUNCHED();
-}
-void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy) {
-    if (rows <= 0 || cols <= 0) return;
-    k_add_f2d<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(rows, cols, X, ldx, Y, ldy);
     HSIM_LAUNCHED();
 }
 void residual_f32(cudaStream_t s, int rows, int cols, const double *SP, int lds, const double *MP, int ldm,

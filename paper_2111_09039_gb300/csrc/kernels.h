@@ -33,8 +33,6 @@ void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const doub
 void split_df_values(cudaStream_t s, int64_t n, const double *v, float2 *out);
 void spmm_df(cudaStream_t s, int n_rows, int n_cols, const int *ptr, const int *col, const float2 *val, int k,
              const double *X, int ldx, float2 *X2, double *Y, int ldy);
-void spmm_f(cudaStream_t s, int n_rows, const int *ptr, const int *col, const float *val, int k,
-            const float *X, int ldx, float *Y, int ldy);
 // R = B - (S - mu M) X with M in S's pattern (M) or diagonal (Md)
 void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *S,
                       const double *M, const double *Md, double mu, int k, const double *X, int ldx,
@@ -69,8 +67,6 @@ void copy_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, d
 // strided type conversions and FP32 helpers of the mixed-precision path
 void convert_matrix(cudaStream_t s, int rows, int cols, const double *X, int ldx, float *Y, int ldy);
 void convert_matrix(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
-// Y (FP64) += X (FP32)
-void add_f2d(cudaStream_t s, int rows, int cols, const float *X, int ldx, double *Y, int ldy);
 // R (FP32) = SP - rho MP column-wise, rho_j = num[j] / den[j] (den NULL: num[j]),
 // formed once per column into rho (cols doubles of scratch); the difference
 // in FP64, then truncated to FP32
@@ -98,13 +94,6 @@ void gram(cudaStream_t s, int n, int ka, int kb, const T *A, int lda, const T *B
 template <typename T>
 void gemm_nn(cudaStream_t s, int n, int k, int m, const T *A, int lda, const double *B, int ldb,
              T *C, int ldc);
-// w_j = sum_i X[i,j] * Y[i,j] * (d ? d[i] : 1)   (column dot products in FP64, w overwritten)
-template <typename T>
-void col_dots(cudaStream_t s, int n, int k, const T *X, int ldx, const T *Y, int ldy,
-              const double *d, double *w);
-// X[:, j] *= 1/sqrt(w[j])
-template <typename T>
-void scale_cols_rsqrt(cudaStream_t s, int n, int k, const double *w, T *X, int ldx);
 // residual sums: out[3j+0] = sum w R^2, +1 = sum w (S Phi)^2, +2 = sum w (M Phi)^2
 // with R = SPhi - lam * MPhi; w = dinv (M^{-1}-norm) or 1 (2-norm)
 template <typename T>
