@@ -348,6 +348,27 @@ hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int32_t *col, c
 hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, const double *val,
                                 int leaf_size, int nrhs, const double *B, double *X,
                                 int *negative_pivots, int64_t *nnz_L);
+/* Host replay of the mesh part of hsim_build_hierarchy: the level sizes
+ * (eqs. nT-1 and growthRate), the farthest-point order (Alg. 2) and the
+ * prolongations U^tau (eq. basis, rows normalised to one), computed by the
+ * host code that hsim_build_hierarchy runs before its device uploads.  Needs
+ * no GPU; the solver never uses it.
+ *   n_verts, n_tris, V_host, F_host, L2_host, p, opts: as hsim_build_hierarchy
+ *     (opts NULL = defaults; levels, start_vertex, sigma and q are used).
+ *   levels, sizes, U_nnz (host, required): T, n^0..n^{T-1} (room for 8) and
+ *     the entries of U^0..U^{T-2} (room for 7).
+ *   order, U_ptr, U_col, U_val (host, each may be NULL, e.g. in a first call
+ *     that learns the sizes): the first n^1 vertices of farthest-point
+ *     sampling (nothing when T = 1), then the CSR arrays of U^0, U^1, ... one
+ *     after another: U_ptr holds n^tau + 1 offsets per U^tau (local to that
+ *     U^tau), U_col (coarse-level index) and U_val U_nnz[tau] entries each.
+ * Errors: HSIM_E_INVALID_ARG for a bad mesh or arguments (as
+ * hsim_build_hierarchy, and when a connected component of the mesh holds no
+ * coarse vertex); nothing is written then. */
+hsim_status hsim_check_hierarchy(int n_verts, int n_tris, const double *V_host, const int32_t *F_host,
+                                 const double *L2_host, int p, const hsim_options *opts, int *levels,
+                                 int *sizes, int64_t *U_nnz, int32_t *order, int32_t *U_ptr,
+                                 int32_t *U_col, double *U_val);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ from ._lib import HSIM_FP64, HSIM_MIXED, HsimError, Info, Options, check, defaul
 
 __all__ = ["Context", "Hierarchy", "assemble", "solve", "spmm", "gram", "gemm_update", "gram_tc",
            "gemm_update_tc", "ritz",
-           "galerkin", "shifted_solve", "check_symbolic", "default_options", "HsimError",
+           "galerkin", "shifted_solve", "check_symbolic", "check_hierarchy", "default_options", "HsimError",
            "HSIM_FP64", "HSIM_MIXED", "kernel_launches", "solve_batched", "eig_grad", "eigenvalues"]
 
 
@@ -371,3 +371,31 @@ def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32, inverted: bool = F
     check(fn(len(row_ptr) - 1, ptr(row_ptr), ptr(col), ptr(val), leaf_size, B.shape[1], ptr(B), ptr(X),
              ctypes.byref(neg), ctypes.byref(nnzL)))
     return X, neg.value, nnzL.value
+
+
+def check_hierarchy(F, V=None, L2=None, p: int = 50, options: Options | None = None, **kw):
+    """Host replay of the mesh part of the hierarchy (hsim_check_hierarchy, no
+    GPU): (sizes, farthest-point order, [U^tau as (rows, cols, row_ptr, col, val)])."""
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    n = int(V.shape[0]) if V is not None else int(F.max()) + 1
+    Vh = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
+    Lh = None if L2 is None else np.ascontiguousarray(L2, dtype=np.float64)
+    o = options if options is not None else default_options(**kw)
+    T = ctypes.c_int()
+    sizes = (ctypes.c_int * 8)()
+    nnz = (ctypes.c_int64 * 7)()
+    args = (n, F.shape[0], ptr(Vh), ptr(F), ptr(Lh), p, ctypes.byref(o), ctypes.byref(T), sizes, nnz)
+    check(lib().hsim_check_hierarchy(*args, None, None, None, None))
+    sz = list(sizes[: T.value])
+    nz = list(nnz[: T.value - 1])
+    order = np.empty(sz[1] if T.value > 1 else 0, dtype=np.int32)
+    rp = np.empty(sum(sz[t] + 1 for t in range(T.value - 1)), dtype=np.int32)
+    cl = np.empty(sum(nz), dtype=np.int32)
+    vl = np.empty(sum(nz), dtype=np.float64)
+    check(lib().hsim_check_hierarchy(*args, ptr(order), ptr(rp), ptr(cl), ptr(vl)))
+    U, po, eo = [], 0, 0
+    for t in range(T.value - 1):
+        U.append((sz[t], sz[t + 1], rp[po:po + sz[t] + 1], cl[eo:eo + nz[t]], vl[eo:eo + nz[t]]))
+        po += sz[t] + 1
+        eo += nz[t]
+    return sz, order, U

@@ -23,6 +23,21 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count);
 Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int nc,
                  bool fine_is_mesh, double sigma, double *rho_out, int *fallback_rows);
 
+// The mesh-dependent part of a hierarchy (Sec. 4.1): level sizes, the
+// farthest-point order of Alg. 2 and every prolongation U^tau in natural
+// (mesh / sampling) order.  levels <= 0 selects 3, or 2 when p <= 200; the
+// subspace size q must fit the coarsest level.
+struct HostHierarchy {
+    MeshGraph g;
+    std::vector<int> sizes;     // n^tau, tau = 0..T-1 (at most 8 levels)
+    std::vector<int> order;     // first n^1 vertices of farthest-point sampling
+    std::vector<Csr> U;         // U^tau: n^tau x n^{tau+1}, tau = 0..T-2
+    std::vector<double> rho;    // support radius of U^tau
+    std::vector<int> fallback;  // rows of U^tau with no centre inside rho
+};
+HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
+                                   int levels, int start_vertex, double sigma, int q);
+
 // ---- sparse pattern algebra -------------------------------------------
 Csr mesh_pattern(const MeshGraph &g);                 // edges + diagonal, sorted
 Csr transpose_pattern(const Csr &A);                  // pattern (and values if present)

@@ -6,7 +6,9 @@
 // solver itself never calls it.  hsim_check_inverted replays the inverted
 // form of the FP32 solves (k_finv.cu) the same way: the inversion tasks of
 // k::inverse_plan executed with the semantics of k_gemm_tasks, then one
-// product per front and direction.
+// product per front and direction.  hsim_check_hierarchy returns the mesh
+// part of a hierarchy (level sizes, farthest-point order, prolongations) from
+// the host code that hsim_build_hierarchy runs before its device uploads.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -283,6 +285,38 @@ extern "C" hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int3
             std::memcpy(&X[(size_t)fs.perm[pos] * nrhs], &Xi[(size_t)pos * nrhs], nrhs * sizeof(double));
         if (neg_pivots) *neg_pivots = neg;
         if (nnz_L) *nnz_L = fs.nnz_L;
+        return HSIM_OK;
+    } catch (const Error &e) {
+        return e.status;
+    } catch (...) {
+        return HSIM_E_INTERNAL;
+    }
+}
+
+extern "C" hsim_status hsim_check_hierarchy(int n, int m, const double *V, const int32_t *F, const double *L2, int p,
+                                            const hsim_options *opts, int *levels, int *sizes, int64_t *U_nnz,
+                                            int32_t *order, int32_t *U_ptr, int32_t *U_col, double *U_val) {
+    try {
+        HSIM_CHECK_ARG(levels && sizes && U_nnz, "NULL argument");
+        hsim_options o;
+        hsim_default_options(&o);
+        if (opts) o = *opts;
+        const int q = o.q > 0 ? o.q : std::max((int)std::ceil(1.5 * p), p + 8);
+        HostHierarchy h = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, q);
+        const int T = (int)h.sizes.size();
+        *levels = T;
+        for (int t = 0; t < T; ++t) sizes[t] = h.sizes[t];
+        for (int t = 0; t + 1 < T; ++t) U_nnz[t] = h.U[t].nnz();
+        if (order && !h.order.empty()) std::memcpy(order, h.order.data(), h.order.size() * sizeof(int32_t));
+        int64_t po = 0, eo = 0;
+        for (int t = 0; t + 1 < T; ++t) {
+            const Csr &U = h.U[t];
+            if (U_ptr) std::memcpy(U_ptr + po, U.ptr.data(), U.ptr.size() * sizeof(int32_t));
+            if (U_col) std::memcpy(U_col + eo, U.col.data(), U.col.size() * sizeof(int32_t));
+            if (U_val) std::memcpy(U_val + eo, U.val.data(), U.val.size() * sizeof(double));
+            po += (int64_t)U.ptr.size();
+            eo += U.nnz();
+        }
         return HSIM_OK;
     } catch (const Error &e) {
         return e.status;

@@ -218,6 +218,7 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
         for (int r = 0; r < nf; ++r)
             if (!covered[r]) {
                 int v = fine_is_mesh ? r : order[r];
+                HSIM_CHECK_ARG(label[v] >= 0, "a connected component of the mesh holds no coarse vertex");
                 trips.push_back({r, label[v], 1.0});
             }
     }
@@ -241,6 +242,27 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
         }
     }
     return U;
+}
+
+HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
+                                   int levels, int start_vertex, double sigma, int q) {
+    HSIM_CHECK_ARG(p >= 1, "p must be >= 1");
+    HSIM_CHECK_ARG(sigma > 0.0, "sigma must be positive");
+    HostHierarchy h;
+    h.g = build_mesh_graph(n, m, V, F, L2);
+    HSIM_CHECK_ARG(start_vertex >= 0 && start_vertex < n, "start_vertex out of range");
+    h.sizes = level_sizes(n, p, levels > 0 ? levels : (p <= 200 ? 2 : 3));
+    const int T = (int)h.sizes.size();
+    HSIM_CHECK_ARG(T <= 8, "at most 8 levels");
+    HSIM_CHECK_ARG(q <= h.sizes[T - 1], "p too large for the mesh");
+    if (T > 1) h.order = farthest_point_order(h.g, start_vertex, h.sizes[1]);
+    h.U.resize(T - 1);
+    h.rho.assign(T - 1, 0.0);
+    h.fallback.assign(T - 1, 0);
+    for (int tau = 0; tau + 1 < T; ++tau)
+        h.U[tau] = prolongation(h.g, h.order, h.sizes[tau], h.sizes[tau + 1], tau == 0, sigma, &h.rho[tau],
+                                &h.fallback[tau]);
+    return h;
 }
 
 }  // namespace hsim

@@ -858,22 +858,21 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     H->m = m;
     H->p = p;
     H->opts = o;
-    int T = o.levels > 0 ? o.levels : (p <= 200 ? 2 : 3);
-    MeshGraph g = build_mesh_graph(n, m, V, F, L2);
-    H->sizes = level_sizes(n, p, T);
-    T = (int)H->sizes.size();
+    HostHierarchy hh = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, subspace_q(p, o));
+    H->sizes = hh.sizes;
+    const int T = (int)H->sizes.size();
     H->T = T;
-    HSIM_CHECK_ARG(T <= 8, "at most 8 levels");
-    HSIM_CHECK_ARG(subspace_q(p, o) <= H->sizes[T - 1], "p too large for the mesh");
-    if (T > 1) H->order = farthest_point_order(g, o.start_vertex, H->sizes[1]);
+    H->order = std::move(hh.order);
     // natural patterns and prolongations
     H->lev.resize(T);
-    H->pro.resize(T > 0 ? T - 1 : 0);
+    H->pro.resize(T - 1);
     H->lev[0].n = n;
-    H->lev[0].pat_nat = mesh_pattern(g);
+    H->lev[0].pat_nat = mesh_pattern(hh.g);
     for (int tau = 0; tau + 1 < T; ++tau) {
         ProlongData &P = H->pro[tau];
-        P.U_nat = prolongation(g, H->order, H->sizes[tau], H->sizes[tau + 1], tau == 0, o.sigma, &P.rho, &P.fallback);
+        P.U_nat = std::move(hh.U[tau]);
+        P.rho = hh.rho[tau];
+        P.fallback = hh.fallback[tau];
         Csr Ut = transpose_pattern(P.U_nat);
         Csr AU = pattern_product(H->lev[tau].pat_nat, P.U_nat);
         H->lev[tau + 1].n = H->sizes[tau + 1];

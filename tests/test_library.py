@@ -154,3 +154,86 @@ def test_inverted_replay_galerkin_level_and_forest(hs):
     X2, _, _ = hs.check_symbolic(K2.indptr, K2.indices, K2.data, B2, 8, inverted=True)
     Xr2 = spla.spsolve(K2.tocsc(), B2)
     assert np.abs(X2 - Xr2).max() <= 1e-9 * np.abs(Xr2).max()
+
+
+# ---- hierarchy construction (host code of hsim_build_hierarchy) -------------
+def _open_patch(nx, ny, seed):
+    """A jittered, gently curved nx x ny grid patch with a boundary."""
+    rng = np.random.default_rng(seed)
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    x = (i + rng.uniform(-0.2, 0.2, i.shape)) / nx
+    y = (j + rng.uniform(-0.2, 0.2, j.shape)) / ny
+    V = np.stack([x.ravel(), y.ravel(), 0.1 * np.sin(3 * x.ravel()) * np.cos(2 * y.ravel())], 1)
+    a = (j[:-1, :-1] * nx + i[:-1, :-1]).ravel()
+    F = np.concatenate([np.stack([a, a + 1, a + nx + 1], 1), np.stack([a, a + nx + 1, a + nx], 1)])
+    return synth.Mesh(V=V, F=F.astype(np.int32))
+
+
+def _two_tori():
+    a = synth.bumpy_torus(40, 30, 1)
+    b = synth.bumpy_torus(36, 28, 2)
+    return synth.Mesh(V=np.concatenate([a.V, b.V + 5.0]), F=np.concatenate([a.F, b.F + a.n]))
+
+
+def _hierarchy_case(name):
+    if name == "bumpy_torus_64":
+        w, mesh, s = synth.make_workload(name)
+        return mesh, w.p, w.levels, s, 7.0
+    if name == "flat_torus_64":
+        w, mesh, s = synth.make_workload(name)
+        return mesh, w.p, w.levels, s, 7.0
+    if name == "icosphere3_noise":
+        w, mesh, s = synth.make_workload(name)
+        return mesh, w.p, 3, s, 7.0
+    if name == "open_patch":
+        return _open_patch(70, 60, 3), 30, 3, 17, 7.0
+    if name == "two_tori":
+        return _two_tori(), 20, 2, 5, 7.0
+    if name == "narrow_support":
+        # sigma = 0.5: many fine vertices see no centre inside rho
+        w, mesh, s = synth.make_workload("bumpy_torus_64")
+        return mesh, w.p, w.levels, s, 0.5
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["bumpy_torus_64", "flat_torus_64", "icosphere3_noise", "open_patch",
+                                  "two_tori", "narrow_support"])
+def test_hierarchy_matches_oracle_on_host(hs, name):
+    # level sizes and the farthest-point order exactly; the prolongations'
+    # patterns exactly and their values to the rounding of the row sums
+    mesh, p, levels, s, sigma = _hierarchy_case(name)
+    H = hierarchy.build_hierarchy(mesh, p, levels, s, sigma)
+    sizes, order, U = hs.check_hierarchy(mesh.F, V=mesh.V, L2=mesh.L2, p=p, levels=levels,
+                                         start_vertex=s, sigma=sigma)
+    assert sizes == H.sizes
+    np.testing.assert_array_equal(order, H.order)
+    assert len(U) == len(H.U)
+    for (r, c, rp, cl, vl), Uo in zip(U, H.U):
+        assert (r, c) == Uo.shape
+        np.testing.assert_array_equal(rp, Uo.indptr)
+        np.testing.assert_array_equal(cl, Uo.indices)
+        np.testing.assert_allclose(vl, Uo.data, rtol=1e-15, atol=0)
+    if name == "narrow_support":
+        assert H.fallback_rows[0] > 0
+    if name == "two_tori":
+        # the second sample is the first vertex of the other component
+        assert order[1] == 40 * 30
+
+
+def test_hierarchy_single_level_and_errors(hs):
+    mesh = synth.bumpy_torus(30, 30, 4)
+    sizes, order, U = hs.check_hierarchy(mesh.F, V=mesh.V, p=20, levels=3, start_vertex=0)
+    assert sizes == [900] and len(order) == 0 and U == []      # n <= n^{T-1}: one dense level
+    with pytest.raises(hs.HsimError) as e:
+        hs.check_hierarchy(mesh.F, V=mesh.V, p=900, levels=1)  # q = 1350 > n
+    assert e.value.name == "HSIM_E_INVALID_ARG"
+    with pytest.raises(hs.HsimError):
+        hs.check_hierarchy(mesh.F, V=mesh.V, p=20, levels=2, start_vertex=900)
+    # 1,001 disjoint triangles and 1,000 coarse vertices: one component is
+    # left without a centre, which no prolongation row can reach
+    F = np.arange(3 * 1001, dtype=np.int32).reshape(-1, 3)
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((3 * 1001, 3))
+    with pytest.raises(hs.HsimError) as e:
+        hs.check_hierarchy(F, V=V, p=20, levels=2)
+    assert e.value.name == "HSIM_E_INVALID_ARG"
