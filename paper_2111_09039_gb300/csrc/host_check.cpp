@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "host.h"
 #include "kernels.h"
@@ -19,6 +20,25 @@
 using namespace hsim;
 
 namespace {
+
+// Status and hsim_last_error() message of the exception being handled.
+hsim_status caught() {
+    try {
+        throw;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return HSIM_E_NOMEM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return HSIM_E_INTERNAL;
+    } catch (...) {
+        set_last_error("unknown error");
+        return HSIM_E_INTERNAL;
+    }
+}
 
 // assembly and numeric LDL^T of A over its symbolic analysis, as the GPU
 // kernels do them; fills fs, the arena and the number of negative pivots
@@ -162,10 +182,8 @@ extern "C" hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int3
         if (neg_pivots) *neg_pivots = neg;
         if (nnz_L) *nnz_L = fs.nnz_L;
         return HSIM_OK;
-    } catch (const Error &e) {
-        return e.status;
     } catch (...) {
-        return HSIM_E_INTERNAL;
+        return caught();
     }
 }
 
@@ -286,10 +304,8 @@ extern "C" hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int3
         if (neg_pivots) *neg_pivots = neg;
         if (nnz_L) *nnz_L = fs.nnz_L;
         return HSIM_OK;
-    } catch (const Error &e) {
-        return e.status;
     } catch (...) {
-        return HSIM_E_INTERNAL;
+        return caught();
     }
 }
 
@@ -318,9 +334,7 @@ extern "C" hsim_status hsim_check_hierarchy(int n, int m, const double *V, const
             eo += U.nnz();
         }
         return HSIM_OK;
-    } catch (const Error &e) {
-        return e.status;
     } catch (...) {
-        return HSIM_E_INTERNAL;
+        return caught();
     }
 }

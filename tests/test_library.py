@@ -237,3 +237,4 @@ def test_hierarchy_single_level_and_errors(hs):
     with pytest.raises(hs.HsimError) as e:
         hs.check_hierarchy(F, V=V, p=20, levels=2)
     assert e.value.name == "HSIM_E_INVALID_ARG"
+    assert "component" in str(e.value)
