@@ -472,9 +472,8 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
                        "achieved": jac, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": jac / FP64_PEAK_TFLOPS,
                        "peak_source": "GB300 nominal FP64 (1.25 TFLOP/s; a DFMA probe measured 1.19)",
                        "traffic": None, "flops_per_call": (4.0 / 3.0 + 2.0) * q ** 3, "calls_per_step": calls,
-                       "launches_per_step": 5 * calls, "note": "time includes the LDL^T of M_bar and the "
-                       "triangular transforms of the Rayleigh-Ritz step; the tridiagonalisation takes two grid "
-                       "barriers per column"}
+                       "note": "time includes the LDL^T of M_bar and the triangular transforms of the "
+                       "Rayleigh-Ritz step; the tridiagonalisation takes one grid barrier per column"}
     # supernodal triangular solves: 4 nnz(L) flops per right-hand side
     sflops = avg("solve_flops")
     ms_solve = phases["solve"]
