@@ -167,3 +167,77 @@ def test_planted_swapped_ritz_matrices_is_caught(monkeypatch):
     with pytest.raises((AssertionError, sim.NoConvergence, np.linalg.LinAlgError)):
         r = sim.hsim(mesh, 20, 2, 1e-10, 5, max_iters=5)
         np.testing.assert_allclose(r.lam, lam_ref, rtol=1e-8)
+
+
+def test_residual_closed_form_finest_level():
+    """eq. conv2 with the M^-1-norm on exact eigenpairs mixed by a known
+    amount.  For M-orthonormal eigenvectors phi_a, phi_b and
+    Phi = phi_a + e phi_b taken with the value lambda_a:
+    ||S Phi - lambda_a M Phi||_{M^-1} = e |lambda_b - lambda_a| and
+    ||S Phi||_{M^-1} = sqrt(lambda_a^2 + e^2 lambda_b^2).  For the constant
+    vector (lambda_0 = 0) the denominator is lambda_ref ||M Phi||_{M^-1}
+    with lambda_ref the first value above 1e-8 of the largest.  The lumped M
+    of a noisy torus is far from a multiple of I, so a Euclidean norm in place
+    of the M^-1-norm gives other values."""
+    mesh = synth.bumpy_torus(14, 12, 3)
+    S = assembly.stiffness(mesh)
+    Md = assembly.lumped_mass(mesh)
+    assert Md.max() / Md.min() > 1.5
+    lam, Phi = sim.dense_reference(S, Md, 12)
+    M = sp.diags(Md)
+    e = 1e-3
+    a, b = 3, 7
+    X = Phi.copy()
+    X[:, 0] += e * Phi[:, b]
+    X[:, a] += e * Phi[:, b]
+    vals = lam.copy()
+    vals[0] = 0.0                                  # ascending, as the Ritz values are
+    got = sim.residuals(S, M, X, vals, m_inverse_diag=1.0 / Md)
+    want_a = e * abs(lam[b] - lam[a]) / np.sqrt(lam[a] ** 2 + e ** 2 * lam[b] ** 2)
+    lam_ref = lam[1]                               # first value above 1e-8 * lam[-1]
+    want_0 = e * lam[b] / max(e * lam[b], lam_ref * np.sqrt(1.0 + e ** 2))
+    np.testing.assert_allclose(got[[0, a]], [want_0, want_a], rtol=1e-7)
+    # exact pairs have residuals at rounding level
+    exact = [i for i in range(12) if i not in (0, a)]
+    assert got[exact].max() < 1e-12
+
+
+def test_residual_closed_form_coarse_level():
+    """On coarser levels eq. conv2 takes the Euclidean norm; with M = I the
+    same closed form holds with orthonormal eigenvectors."""
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    d = np.sort(rng.uniform(1.0, 50.0, 40))
+    A = sp.csr_matrix((Q * d[None, :]) @ Q.T)
+    I = sp.identity(40, format="csr")
+    e = 1e-2
+    X = (Q[:, 2] + e * Q[:, 9])[:, None]
+    got = sim.residuals(A, I, np.concatenate([X, Q[:, 3:6]], 1), np.concatenate([[d[2]], d[3:6]]))
+    want = e * (d[9] - d[2]) / np.sqrt(d[2] ** 2 + e ** 2 * d[9] ** 2)
+    np.testing.assert_allclose(got[0], want, rtol=1e-9)
+    assert got[1:].max() < 1e-13
+
+
+def test_planted_residual_mistakes_are_caught():
+    """The closed form above rejects a Euclidean norm on the finest level and
+    a denominator without lambda_ref."""
+    mesh = synth.bumpy_torus(14, 12, 3)
+    S = assembly.stiffness(mesh)
+    Md = assembly.lumped_mass(mesh)
+    lam, Phi = sim.dense_reference(S, Md, 12)
+    M = sp.diags(Md)
+    e, a, b = 1e-3, 3, 7
+    X = Phi.copy()
+    X[:, 0] += e * Phi[:, b]
+    X[:, a] += e * Phi[:, b]
+    vals = lam.copy()
+    vals[0] = 0.0
+    want_a = e * abs(lam[b] - lam[a]) / np.sqrt(lam[a] ** 2 + e ** 2 * lam[b] ** 2)
+    want_0 = e * lam[b] / max(e * lam[b], lam[1] * np.sqrt(1.0 + e ** 2))
+    euclid = sim.residuals(S, M, X, vals)                     # norm mistake
+    assert abs(euclid[a] / want_a - 1.0) > 1e-3
+    SP, MP = S @ X, M @ X
+    R = SP - MP * vals[None, :]
+    w = (1.0 / Md)[:, None]
+    plain = np.sqrt((R * R * w).sum(0)) / np.sqrt((SP * SP * w).sum(0))   # no lambda_ref
+    assert abs(plain[0] / want_0 - 1.0) > 1e-3
