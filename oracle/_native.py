@@ -33,6 +33,8 @@ def lib():
         P = ctypes.c_void_p
         _lib.oracle_fps.argtypes = [I, P, P, P, I, I, P, P]
         _lib.oracle_fps.restype = I
+        _lib.oracle_fps_among.argtypes = [I, P, P, P, I, I, P, P, P]
+        _lib.oracle_fps_among.restype = I
         _lib.oracle_balls.argtypes = [I, P, P, P, I, P, D, L, P, P, P]
         _lib.oracle_balls.restype = L
         _lib.oracle_nearest.argtypes = [I, P, P, P, I, P, P, P]
@@ -44,11 +46,21 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def fps(ptr, idx, w, start: int, count: int):
+def fps(ptr, idx, w, start: int, count: int, candidates=None):
+    """Farthest-point order of `count` vertices from `start`; with a boolean
+    `candidates` mask only those vertices are chosen (distances still run over
+    the whole graph)."""
     n = len(ptr) - 1
     order = np.empty(count, dtype=np.int32)
     field = np.empty(n, dtype=np.float64)
-    rc = lib().oracle_fps(n, _p(ptr), _p(idx), _p(w), int(start), int(count), _p(order), _p(field))
+    if candidates is None:
+        rc = lib().oracle_fps(n, _p(ptr), _p(idx), _p(w), int(start), int(count), _p(order), _p(field))
+    else:
+        cand = np.ascontiguousarray(candidates, dtype=np.uint8)
+        if not cand[start] or count > int(cand.sum()):
+            raise ValueError("start must be a candidate and count at most the number of candidates")
+        rc = lib().oracle_fps_among(n, _p(ptr), _p(idx), _p(w), int(start), int(count), _p(cand),
+                                    _p(order), _p(field))
     if rc != 0:
         raise MemoryError("oracle_fps failed")
     return order, field

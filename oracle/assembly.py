@@ -80,6 +80,19 @@ def lumped_mass(mesh) -> np.ndarray:
     return M
 
 
+def boundary_vertices(mesh) -> np.ndarray:
+    """Sorted ids of the vertices on the mesh boundary: the endpoints of every
+    edge that exactly one triangle holds (Sec. 5, surfaces with boundary)."""
+    F = np.asarray(mesh.F, dtype=np.int64)
+    a = np.concatenate([F[:, 0], F[:, 1], F[:, 2]])
+    b = np.concatenate([F[:, 1], F[:, 2], F[:, 0]])
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    key = lo * mesh.n + hi
+    uniq, count = np.unique(key, return_counts=True)
+    once = uniq[count == 1]
+    return np.unique(np.concatenate([once // mesh.n, once % mesh.n]))
+
+
 def total_area(mesh) -> float:
     """Surface area A, the plain sum of the triangle areas in triangle order."""
     total = 0.0

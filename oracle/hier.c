@@ -87,10 +87,13 @@ static int relax_from(int src, const int *ptr, const int *idx, const double *w,
 }
 
 /* Farthest-point sampling (Alg. 2): order[0] = start, then repeatedly the
- * vertex with the largest distance to the chosen set (lowest index on ties).
- * Returns 0, or -1 on allocation failure. */
-int oracle_fps(int n, const int *ptr, const int *idx, const double *w, int start,
-               int count, int *order, double *field_out) {
+ * candidate vertex with the largest distance to the chosen set (lowest index
+ * on ties).  cand == NULL makes every vertex a candidate; otherwise only the
+ * vertices with cand[v] != 0 are chosen, while distances still run over the
+ * whole graph.  count must not exceed the number of candidates.  Returns 0,
+ * or -1 on allocation failure. */
+int oracle_fps_among(int n, const int *ptr, const int *idx, const double *w, int start,
+                     int count, const unsigned char *cand, int *order, double *field_out) {
     double *dist = (double *)malloc((size_t)n * sizeof(double));
     heap_t h = {0, 0, 0};
     if (!dist) return -1;
@@ -98,9 +101,9 @@ int oracle_fps(int n, const int *ptr, const int *idx, const double *w, int start
     order[0] = start;
     int rc = relax_from(start, ptr, idx, w, dist, &h);
     for (int k = 1; k < count && rc == 0; ++k) {
-        int best = 0;
-        for (int v = 1; v < n; ++v)
-            if (dist[v] > dist[best]) best = v;
+        int best = -1;
+        for (int v = 0; v < n; ++v)
+            if ((!cand || cand[v]) && (best < 0 || dist[v] > dist[best])) best = v;
         order[k] = best;
         rc = relax_from(best, ptr, idx, w, dist, &h);
     }
@@ -108,6 +111,11 @@ int oracle_fps(int n, const int *ptr, const int *idx, const double *w, int start
     free(dist);
     free(h.a);
     return rc;
+}
+
+int oracle_fps(int n, const int *ptr, const int *idx, const double *w, int start,
+               int count, int *order, double *field_out) {
+    return oracle_fps_among(n, ptr, idx, w, start, count, 0, order, field_out);
 }
 
 /* For every centre c (mesh vertex ids centres[0..nc)), all mesh vertices v

@@ -18,6 +18,13 @@ design notes):
   the count for which each fine vertex sees about sigma centres (eq. radius).
 * a fine vertex with no centre closer than rho takes weight 1 on its nearest
   centre (multi-source Dijkstra, lowest centre index on ties).
+* Dirichlet boundary (Sec. 5, same hierarchy and basis construction): the
+  degrees of freedom are the interior vertices, and the construction runs over
+  them: level sizes from their count, farthest-point sampling that chooses
+  only interior vertices (distances over the whole surface), level-0 rows in
+  increasing vertex id.  Every centre then keeps its own row; with centres on
+  the boundary and boundary rows dropped, U^0 loses columns' leading entries
+  and the coarse mass matrices become singular.
 """
 from __future__ import annotations
 
@@ -56,32 +63,48 @@ class Hierarchy:
     rho: list = field(default_factory=list)
     area: float = 0.0
     fallback_rows: list = field(default_factory=list)
+    dofs: np.ndarray | None = None     # level-0 vertices when not all (Dirichlet)
 
     def level_vertices(self, tau: int) -> np.ndarray:
         if tau == 0:
+            if self.dofs is not None:
+                return self.dofs
             return np.arange(self.sizes[0], dtype=np.int32)
         return self.order[: self.sizes[tau]]
 
 
-def build_hierarchy(mesh, p: int, levels: int, start_vertex: int, sigma: float = 7.0) -> Hierarchy:
-    sizes = level_sizes(mesh.n, p, levels)
+def build_hierarchy(mesh, p: int, levels: int, start_vertex: int, sigma: float = 7.0,
+                    dofs=None) -> Hierarchy:
+    """dofs: sorted mesh vertex ids of the level-0 unknowns (None = every
+    vertex; the interior vertices for a Dirichlet boundary)."""
+    n = mesh.n
+    n0 = n if dofs is None else len(dofs)
+    sizes = level_sizes(n0, p, levels)
     ptr, idx, w = edge_graph(mesh)
     A = total_area(mesh)
+    dofs = None if dofs is None else np.asarray(dofs, dtype=np.int32)
     if len(sizes) == 1:
-        return Hierarchy(sizes=sizes, order=np.zeros(0, dtype=np.int32), area=A)
-    order, _ = _native.fps(ptr, idx, w, start_vertex, sizes[1])
-    H = Hierarchy(sizes=sizes, order=order, area=A)
-    n = mesh.n
+        return Hierarchy(sizes=sizes, order=np.zeros(0, dtype=np.int32), area=A, dofs=dofs)
+    cand = None
+    if dofs is not None:
+        cand = np.zeros(n, dtype=bool)
+        cand[dofs] = True
+    order, _ = _native.fps(ptr, idx, w, start_vertex, sizes[1], cand)
+    H = Hierarchy(sizes=sizes, order=order, area=A, dofs=dofs)
     rank = np.full(n, -1, dtype=np.int64)
     rank[order] = np.arange(len(order))
+    row0 = np.arange(n, dtype=np.int64)
+    if dofs is not None:
+        row0 = np.full(n, -1, dtype=np.int64)
+        row0[dofs] = np.arange(len(dofs))
     for tau in range(len(sizes) - 1):
         nf, nc = sizes[tau], sizes[tau + 1]
         rho = math.sqrt(sigma * A / (nc * math.pi))
         centres = order[:nc]
         kc, v, d = _native.balls(ptr, idx, w, centres, rho)
         if tau == 0:
-            row = v.astype(np.int64)
-            keep = np.ones(len(v), dtype=bool)
+            row = row0[v]
+            keep = row >= 0
         else:
             row = rank[v]
             keep = (row >= 0) & (row < nf)
@@ -93,7 +116,7 @@ def build_hierarchy(mesh, p: int, levels: int, start_vertex: int, sigma: float =
         missing = np.nonzero(~covered)[0]
         if len(missing):
             label, _ = _native.nearest(ptr, idx, w, centres)
-            fine_ids = missing if tau == 0 else order[missing]
+            fine_ids = (missing if dofs is None else dofs[missing]) if tau == 0 else order[missing]
             row = np.concatenate([row, missing])
             col = np.concatenate([col, label[fine_ids].astype(np.int64)])
             wt = np.concatenate([wt, np.ones(len(missing))])

@@ -29,6 +29,13 @@ Steps and readings (each listed in the design notes):
 * At most ``max_iters`` (100) iterations per level, else NoConvergence.
 * Output: the p lowest pairs, ascending; each eigenvector's entry of largest
   magnitude is made positive.
+* Surfaces with boundary (Sec. 5): the cotan S and lumped M of an open mesh
+  carry the natural (Neumann) condition as they are.  Dirichlet: the boundary
+  vertices (endpoints of edges that one triangle holds) are eliminated: S^0
+  and M^0 are restricted to the interior vertices, and the hierarchy is built
+  over the interior vertices (see oracle.hierarchy).  The coarse spaces are
+  subspaces of the interior space and the coarse problems Rayleigh-Ritz
+  restrictions of the Dirichlet problem.
 
 Parity unpinned: iteration counts (only the paper's qualitative patterns
 apply) and eigenvectors inside a cluster that straddles index p.
@@ -43,7 +50,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .assembly import lumped_mass, stiffness
+from .assembly import boundary_vertices, lumped_mass, stiffness
 from .galerkin import level_matrices
 from .hierarchy import build_hierarchy, subspace_size
 
@@ -141,6 +148,7 @@ class HsimResult:
     hierarchy: object
     S: list
     M: list
+    interior: np.ndarray | None = None   # Dirichlet: mesh vertex of each row of Phi
 
 
 def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
@@ -166,19 +174,29 @@ def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
     return lam, Phi, iters, shifts, coarse
 
 
-def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100):
-    """Full HSIM (Alg. 3) on a mesh: p lowest eigenpairs of S Phi = lambda M Phi."""
+def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100, boundary="neumann"):
+    """Full HSIM (Alg. 3) on a mesh: p lowest eigenpairs of S Phi = lambda M Phi.
+    boundary="dirichlet" eliminates the boundary vertices (rows of Phi are then
+    the interior vertices, listed in the result's ``interior``)."""
+    if boundary not in ("neumann", "dirichlet"):
+        raise ValueError(boundary)
     S0 = stiffness(mesh)
     M0 = lumped_mass(mesh)
-    H = build_hierarchy(mesh, p, levels, start_vertex, sigma)
-    S, M = level_matrices(S0, M0, H.U)
+    interior = None
+    if boundary == "dirichlet":
+        interior = np.setdiff1d(np.arange(mesh.n), boundary_vertices(mesh))
+        S0 = S0[interior][:, interior].tocsr()
+        M0 = M0[interior]
+    H = build_hierarchy(mesh, p, levels, start_vertex, sigma, dofs=interior)
+    U = H.U
+    S, M = level_matrices(S0, M0, U)
     if len(S) == 1:
         q = subspace_size(p)
         lam, Phi = sla.eigh(S0.toarray(), np.diag(M0), subset_by_index=[0, q - 1])
         iters, shifts, coarse = [], [], [lam]
     else:
-        lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, H.U, p, eps, alpha, max_iters)
-    return HsimResult(lam[:p], normalise_signs(Phi[:, :p]), iters, shifts, coarse, H, S, M)
+        lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, U, p, eps, alpha, max_iters)
+    return HsimResult(lam[:p], normalise_signs(Phi[:, :p]), iters, shifts, coarse, H, S, M, interior)
 
 
 def dense_reference(S, M_diag_or_matrix, count):

@@ -16,6 +16,9 @@ available, so the families below stand in for them:
 * ``displaced_icosphere`` icosphere of a given subdivision, each vertex moved
                         radially by a smooth random field made of 16 real
                         spherical harmonics of degree <= 8, amplitude 0.05.
+* ``flat_square``      unit square, N x N right-triangulated grid: a surface
+                        with boundary (Dirichlet spectrum in closed form).
+* ``bumpy_patch``      open jittered grid patch with a smooth height field.
 * ``bumpy_torus``      torus (R, r) sampled on an Nu x Nv parameter grid, with
                         per-vertex jitter inside a disc of radius 0.1 * grid
                         step in the (u, v) plane and 32 Gaussian bumps along
@@ -103,6 +106,40 @@ def flat_torus(N: int = 64) -> Mesh:
     L2[half:, 1] = h2
     L2[half:, 2] = 2.0 * h2
     return Mesh(V=None, F=F, L2=L2, name=f"flat_torus_{N}", meta={"N": N, "h": 1.0 / N})
+
+
+def grid_patch_faces(nx: int, ny: int) -> np.ndarray:
+    """Faces of an open nx x ny grid of squares ((nx+1)(ny+1) vertices);
+    vertex (i, j) has index j*(nx+1) + i, every square split along a-c as in
+    grid_torus_faces."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    a = (j * (nx + 1) + i).ravel()
+    b = a + 1
+    c = a + nx + 2
+    d = a + nx + 1
+    F = np.concatenate([np.stack([a, b, c], 1), np.stack([a, c, d], 1)], 0)
+    return F.astype(np.int32)
+
+
+def flat_square(N: int = 64) -> Mesh:
+    """Unit square cut into N x N right-triangulated squares (h = 1/N), in the
+    plane z = 0: a surface with boundary whose interior cotan matrix is the
+    five-point Laplacian (exact coordinates for N a power of two)."""
+    i, j = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="xy")
+    V = np.stack([i.ravel() / N, j.ravel() / N, np.zeros(i.size)], 1)
+    return Mesh(V=V, F=grid_patch_faces(N, N), name=f"flat_square_{N}", meta={"N": N, "h": 1.0 / N})
+
+
+def bumpy_patch(nx: int, ny: int, seed: int) -> Mesh:
+    """An open, gently curved grid patch over [0, 1] x [0, ny/nx]: per-vertex
+    jitter of up to 0.2 grid steps in the plane and a smooth height field."""
+    rng = np.random.default_rng(seed)
+    i, j = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    x = (i + rng.uniform(-0.2, 0.2, i.shape) * ((i > 0) & (i < nx))) / nx
+    y = (j + rng.uniform(-0.2, 0.2, j.shape) * ((j > 0) & (j < ny))) / nx
+    z = 0.1 * np.sin(3.0 * x) * np.cos(2.0 * y)
+    V = np.stack([x.ravel(), y.ravel(), z.ravel()], 1)
+    return Mesh(V=V, F=grid_patch_faces(nx, ny), name=f"bumpy_patch_{nx}x{ny}_{seed}")
 
 
 # --------------------------------------------------------------------------
