@@ -47,6 +47,14 @@ typedef enum {
 
 enum { HSIM_FP64 = 0, HSIM_MIXED = 1 };
 
+/* Boundary condition on surfaces with boundary (Sec. 5).  NATURAL: the cotan
+ * S and lumped M of the open mesh as they are (Neumann).  DIRICHLET: the
+ * boundary vertices (endpoints of edges that one triangle holds) are
+ * eliminated; the level-0 unknowns are the interior vertices in increasing id
+ * (hsim_hier_dofs) and the hierarchy is built over them (sampling chooses
+ * interior vertices only, distances over the whole surface). */
+enum { HSIM_BOUNDARY_NATURAL = 0, HSIM_BOUNDARY_DIRICHLET = 1 };
+
 /* Solver options.  Defaults (hsim_default_options) follow the paper:
  * sigma = 7 (Sec. 5, support region), alpha = 0.1 (Alg. 3 shift index
  * floor(alpha p)), two inverse iterations per Rayleigh-Ritz step and locking
@@ -76,6 +84,8 @@ typedef struct {
                             inverse iteration of each Rayleigh-Ritz step: 0 =
                             automatic (switched on for a level once its residual
                             stops decreasing), 1 = always, -1 = never */
+    int boundary;        /* HSIM_BOUNDARY_NATURAL (default) or _DIRICHLET; read by
+                            hsim_build_hierarchy, fixed for the hierarchy */
 } hsim_options;
 
 /* Per-solve report (host struct, optional). */
@@ -141,8 +151,16 @@ void hsim_hier_destroy(hsim_hier *hier);
 hsim_status hsim_hier_info(const hsim_hier *hier, int *levels, int *sizes_host,
                            int32_t *order_host);
 
+/* Mesh vertex id of each level-0 unknown (sizes[0] entries, host): the
+ * identity for the natural boundary condition, the interior vertices in
+ * increasing id for a Dirichlet boundary.  Rows of S^0, M^0 and of the
+ * eigenvectors follow this list. */
+hsim_status hsim_hier_dofs(const hsim_hier *hier, int32_t *dofs_host);
+
 /* The CSR pattern of S^0 that hsim_solve expects (rows in mesh order, every
- * mesh edge plus the diagonal), as device pointers owned by the hierarchy. */
+ * mesh edge plus the diagonal; with a Dirichlet boundary the rows and columns
+ * of the interior vertices only, renumbered as hsim_hier_dofs), as device
+ * pointers owned by the hierarchy. */
 hsim_status hsim_hier_pattern(const hsim_hier *hier, int *n, int64_t *nnz,
                               const int32_t **row_ptr_dev, const int32_t **col_dev);
 
@@ -156,8 +174,10 @@ hsim_status hsim_hier_prolongation(const hsim_hier *hier, int tau, int *rows, in
 /* Cotan stiffness S^0 and lumped mass diag(M^0) on the device (Sec. 3.1,
  * eq. massStiffMatrices; S_ij = -1/2 (cot a_ij + cot b_ij), S_ii = -sum_j
  * S_ij, M_ii = sum of A_t/3 over incident triangles), written into the
- * hierarchy's pattern.  Exactly one of V_dev (n x 3) and L2_dev (n_tris x 3)
- * is non-NULL. */
+ * hierarchy's pattern.  An edge that one triangle holds takes one cotangent.
+ * With a Dirichlet boundary the matrices of the whole mesh are restricted to
+ * the interior vertices (diagonals keep the boundary edges' weights).
+ * Exactly one of V_dev (n x 3) and L2_dev (n_tris x 3) is non-NULL. */
 hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *hier, const double *V_dev,
                           const double *L2_dev, double *S_val_dev, double *M_diag_dev);
 
@@ -205,7 +225,11 @@ hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers
  *   F_dev          n_tris x 3 vertex indices in [0, n); triangles of
  *                  positive area (the cotangents divide by it)
  *   evals_dev      p eigenvalues; evecs_dev n x p COLUMN-major, leading
- *                  dimension n (as hsim_solve writes them), M-orthonormal
+ *                  dimension n (as hsim_solve writes them), M-orthonormal;
+ *                  for a Dirichlet boundary the interior eigenvectors
+ *                  scattered to the mesh vertices with zeros on the boundary
+ *                  (S_II and M_II are restrictions of S and M, so the same
+ *                  formula holds)
  *   dloss_dlambda_dev  p weights
  *   dV_dev         out: n x 3 row-major, overwritten
  * All device pointers on the context's device; the call returns after the
@@ -354,21 +378,28 @@ hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, c
  * host code that hsim_build_hierarchy runs before its device uploads.  Needs
  * no GPU; the solver never uses it.
  *   n_verts, n_tris, V_host, F_host, L2_host, p, opts: as hsim_build_hierarchy
- *     (opts NULL = defaults; levels, start_vertex, sigma and q are used).
- *   levels, sizes, U_nnz (host, required): T, n^0..n^{T-1} (room for 8) and
- *     the entries of U^0..U^{T-2} (room for 7).
- *   order, U_ptr, U_col, U_val (host, each may be NULL, e.g. in a first call
- *     that learns the sizes): the first n^1 vertices of farthest-point
- *     sampling (nothing when T = 1), then the CSR arrays of U^0, U^1, ... one
- *     after another: U_ptr holds n^tau + 1 offsets per U^tau (local to that
- *     U^tau), U_col (coarse-level index) and U_val U_nnz[tau] entries each.
+ *     (opts NULL = defaults; levels, start_vertex, sigma, q and boundary are
+ *     used).
+ *   levels, sizes, U_nnz, nnz0 (host, required): T, n^0..n^{T-1} (room for
+ *     8), the entries of U^0..U^{T-2} (room for 7) and of the level-0 pattern.
+ *   dofs, order, U_ptr, U_col, U_val, ptr0, col0, src0 (host, each may be
+ *     NULL, e.g. in a first call that learns the sizes): the mesh vertex of
+ *     each level-0 unknown (n^0 entries, as hsim_hier_dofs), the first n^1
+ *     vertices of farthest-point sampling (nothing when T = 1), then the CSR
+ *     arrays of U^0, U^1, ... one after another: U_ptr holds n^tau + 1
+ *     offsets per U^tau (local to that U^tau), U_col (coarse-level index) and
+ *     U_val U_nnz[tau] entries each; last the level-0 pattern that
+ *     hsim_hier_pattern returns (ptr0: n^0 + 1, col0: nnz0 entries) and for
+ *     each of its entries the entry of the whole mesh's matrix that
+ *     hsim_assemble takes its value from, as row * n_verts + col (src0).
  * Errors: HSIM_E_INVALID_ARG for a bad mesh or arguments (as
  * hsim_build_hierarchy, and when a connected component of the mesh holds no
  * coarse vertex); nothing is written then. */
 hsim_status hsim_check_hierarchy(int n_verts, int n_tris, const double *V_host, const int32_t *F_host,
                                  const double *L2_host, int p, const hsim_options *opts, int *levels,
-                                 int *sizes, int64_t *U_nnz, int32_t *order, int32_t *U_ptr,
-                                 int32_t *U_col, double *U_val);
+                                 int *sizes, int64_t *U_nnz, int64_t *nnz0, int32_t *dofs,
+                                 int32_t *order, int32_t *U_ptr, int32_t *U_col, double *U_val,
+                                 int32_t *ptr0, int32_t *col0, int64_t *src0);
 
 #ifdef __cplusplus
 }

@@ -80,7 +80,7 @@ class Hierarchy:
                                          ctypes.byref(o), ctypes.byref(h)))
         self._h = h
         self.ctx = ctx
-        self.n = n
+        self.n_mesh = n
         self.m = F.shape[0]
         self.p = p
         self.options = o
@@ -89,9 +89,12 @@ class Hierarchy:
         check(lib().hsim_hier_info(h, ctypes.byref(T), sizes, None))
         self.levels = T.value
         self.sizes = list(sizes[: T.value])
+        self.n = self.sizes[0]            # level-0 unknowns (interior vertices for a Dirichlet boundary)
         self.order = np.zeros(self.sizes[1] if self.levels > 1 else 0, dtype=np.int32)
         if self.levels > 1:
             check(lib().hsim_hier_info(h, None, None, ptr(self.order)))
+        self.dofs = np.empty(self.n, dtype=np.int32)   # mesh vertex of each level-0 unknown
+        check(lib().hsim_hier_dofs(h, ptr(self.dofs)))
 
     @property
     def handle(self):
@@ -373,9 +376,13 @@ def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32, inverted: bool = F
     return X, neg.value, nnzL.value
 
 
-def check_hierarchy(F, V=None, L2=None, p: int = 50, options: Options | None = None, **kw):
+def check_hierarchy(F, V=None, L2=None, p: int = 50, options: Options | None = None, return_dofs: bool = False,
+                    return_level0: bool = False, **kw):
     """Host replay of the mesh part of the hierarchy (hsim_check_hierarchy, no
-    GPU): (sizes, farthest-point order, [U^tau as (rows, cols, row_ptr, col, val)])."""
+    GPU): (sizes, farthest-point order, [U^tau as (rows, cols, row_ptr, col, val)]),
+    then the mesh vertex of each level-0 unknown with return_dofs=True and the
+    level-0 pattern (row_ptr, col, source mesh entry row * n + col) with
+    return_level0=True."""
     F = np.ascontiguousarray(F, dtype=np.int32)
     n = int(V.shape[0]) if V is not None else int(F.max()) + 1
     Vh = None if V is None else np.ascontiguousarray(V, dtype=np.float64)
@@ -384,18 +391,30 @@ def check_hierarchy(F, V=None, L2=None, p: int = 50, options: Options | None = N
     T = ctypes.c_int()
     sizes = (ctypes.c_int * 8)()
     nnz = (ctypes.c_int64 * 7)()
-    args = (n, F.shape[0], ptr(Vh), ptr(F), ptr(Lh), p, ctypes.byref(o), ctypes.byref(T), sizes, nnz)
-    check(lib().hsim_check_hierarchy(*args, None, None, None, None))
+    nnz0 = ctypes.c_int64()
+    args = (n, F.shape[0], ptr(Vh), ptr(F), ptr(Lh), p, ctypes.byref(o), ctypes.byref(T), sizes, nnz,
+            ctypes.byref(nnz0))
+    check(lib().hsim_check_hierarchy(*args, *([None] * 8)))
     sz = list(sizes[: T.value])
     nz = list(nnz[: T.value - 1])
+    dofs = np.empty(sz[0], dtype=np.int32)
     order = np.empty(sz[1] if T.value > 1 else 0, dtype=np.int32)
     rp = np.empty(sum(sz[t] + 1 for t in range(T.value - 1)), dtype=np.int32)
     cl = np.empty(sum(nz), dtype=np.int32)
     vl = np.empty(sum(nz), dtype=np.float64)
-    check(lib().hsim_check_hierarchy(*args, ptr(order), ptr(rp), ptr(cl), ptr(vl)))
+    ptr0 = np.empty(sz[0] + 1, dtype=np.int32)
+    col0 = np.empty(nnz0.value, dtype=np.int32)
+    src0 = np.empty(nnz0.value, dtype=np.int64)
+    check(lib().hsim_check_hierarchy(*args, ptr(dofs), ptr(order), ptr(rp), ptr(cl), ptr(vl), ptr(ptr0),
+                                     ptr(col0), ptr(src0)))
     U, po, eo = [], 0, 0
     for t in range(T.value - 1):
         U.append((sz[t], sz[t + 1], rp[po:po + sz[t] + 1], cl[eo:eo + nz[t]], vl[eo:eo + nz[t]]))
         po += sz[t] + 1
         eo += nz[t]
-    return sz, order, U
+    out = (sz, order, U)
+    if return_dofs:
+        out += (dofs,)
+    if return_level0:
+        out += ((ptr0, col0, src0),)
+    return out

@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("inv_iters", ctypes.c_int),
                 ("lock_factor", ctypes.c_double), ("precision", ctypes.c_int),
                 ("start_vertex", ctypes.c_int), ("leaf_size", ctypes.c_int), ("q", ctypes.c_int),
-                ("refine", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -98,7 +98,8 @@ _SIGS = {
     "hsim_shifted_solve_f32": (I, [P, P, I, P, P, D, I, P, I, P]),
     "hsim_check_symbolic": (I, [I, P, P, P, I, I, P, P, P, P]),
     "hsim_check_inverted": (I, [I, P, P, P, I, I, P, P, P, P]),
-    "hsim_check_hierarchy": (I, [I, I, P, P, P, I, P, P, P, P, P, P, P, P]),
+    "hsim_check_hierarchy": (I, [I, I, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "hsim_hier_dofs": (I, [P, P]),
     "hsim_ritz_noalloc": (I, [P, I, P, P, P, P, P]),
 }
 

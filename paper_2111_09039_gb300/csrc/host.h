@@ -19,16 +19,31 @@ struct MeshGraph {
 
 MeshGraph build_mesh_graph(int n, int m, const double *V, const int *F, const double *L2);
 std::vector<int> level_sizes(int n, int p, int levels);
-std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count);
+// Endpoints of the edges that exactly one triangle holds, ascending.
+std::vector<int> boundary_vertices(int n, int m, const int *F);
+// Farthest-point order (Alg. 2); with cand, only vertices with cand[v] != 0
+// are chosen (distances still run over the whole graph).
+std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count,
+                                      const std::vector<char> *cand = nullptr);
+// U^tau; for fine_is_mesh the rows are the mesh vertices, or the vertices
+// listed in dofs (ascending) when dofs is given.
 Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int nc,
-                 bool fine_is_mesh, double sigma, double *rho_out, int *fallback_rows);
+                 bool fine_is_mesh, double sigma, double *rho_out, int *fallback_rows,
+                 const std::vector<int> *dofs = nullptr);
 
 // The mesh-dependent part of a hierarchy (Sec. 4.1): level sizes, the
 // farthest-point order of Alg. 2 and every prolongation U^tau in natural
 // (mesh / sampling) order.  levels <= 0 selects 3, or 2 when p <= 200; the
-// subspace size q must fit the coarsest level.
+// subspace size q must fit the coarsest level.  With a Dirichlet boundary
+// the boundary vertices are eliminated and the construction runs over the
+// interior vertices: level sizes from their count, sampling among them only,
+// U^0 rows for the interior vertices in increasing id.
 struct HostHierarchy {
     MeshGraph g;
+    std::vector<int> dofs;      // Dirichlet: interior vertex ids (empty: every vertex)
+    Csr A_mesh;                 // every mesh edge plus the diagonal (assembly pattern)
+    Csr A0;                     // level-0 pattern: A_mesh, or its interior rows and columns
+    std::vector<int64_t> smap;  // Dirichlet: entry of A_mesh behind each entry of A0
     std::vector<int> sizes;     // n^tau, tau = 0..T-1 (at most 8 levels)
     std::vector<int> order;     // first n^1 vertices of farthest-point sampling
     std::vector<Csr> U;         // U^tau: n^tau x n^{tau+1}, tau = 0..T-2
@@ -36,7 +51,7 @@ struct HostHierarchy {
     std::vector<int> fallback;  // rows of U^tau with no centre inside rho
 };
 HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
-                                   int levels, int start_vertex, double sigma, int q);
+                                   int levels, int start_vertex, double sigma, int q, bool dirichlet);
 
 // ---- sparse pattern algebra -------------------------------------------
 Csr mesh_pattern(const MeshGraph &g);                 // edges + diagonal, sorted
@@ -46,6 +61,9 @@ Csr permute_symmetric(const Csr &A, const std::vector<int> &iperm,
                       std::vector<int64_t> *value_map);  // P A P^T, map new entry -> old entry
 Csr permute_rows_cols(const Csr &A, const std::vector<int> &row_iperm,
                       const std::vector<int> &col_iperm);  // with values
+// A restricted to the rows and columns in keep (ascending), renumbered
+// 0..|keep|-1; value_map: new entry -> entry of A.
+Csr restrict_pattern(const Csr &A, const std::vector<int> &keep, std::vector<int64_t> *value_map);
 
 // ---- supernodal symbolic analysis ---------------------------------------
 // Fronts are the nodes of a nested-dissection tree: every leaf domain and

@@ -311,18 +311,38 @@ extern "C" hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int3
 
 extern "C" hsim_status hsim_check_hierarchy(int n, int m, const double *V, const int32_t *F, const double *L2, int p,
                                             const hsim_options *opts, int *levels, int *sizes, int64_t *U_nnz,
-                                            int32_t *order, int32_t *U_ptr, int32_t *U_col, double *U_val) {
+                                            int64_t *nnz0, int32_t *dofs, int32_t *order, int32_t *U_ptr,
+                                            int32_t *U_col, double *U_val, int32_t *ptr0, int32_t *col0,
+                                            int64_t *src0) {
     try {
-        HSIM_CHECK_ARG(levels && sizes && U_nnz, "NULL argument");
+        HSIM_CHECK_ARG(levels && sizes && U_nnz && nnz0, "NULL argument");
         hsim_options o;
         hsim_default_options(&o);
         if (opts) o = *opts;
         const int q = o.q > 0 ? o.q : std::max((int)std::ceil(1.5 * p), p + 8);
-        HostHierarchy h = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, q);
+        HSIM_CHECK_ARG(o.boundary == HSIM_BOUNDARY_NATURAL || o.boundary == HSIM_BOUNDARY_DIRICHLET,
+                       "unknown boundary condition");
+        HostHierarchy h = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, q,
+                                               o.boundary == HSIM_BOUNDARY_DIRICHLET);
         const int T = (int)h.sizes.size();
         *levels = T;
         for (int t = 0; t < T; ++t) sizes[t] = h.sizes[t];
         for (int t = 0; t + 1 < T; ++t) U_nnz[t] = h.U[t].nnz();
+        if (dofs)
+            for (int i = 0; i < h.sizes[0]; ++i) dofs[i] = h.dofs.empty() ? i : h.dofs[i];
+        // level-0 pattern and, per entry, the mesh entry (row * n + col) its value comes from
+        *nnz0 = h.A0.nnz();
+        if (ptr0) std::memcpy(ptr0, h.A0.ptr.data(), h.A0.ptr.size() * sizeof(int32_t));
+        if (col0) std::memcpy(col0, h.A0.col.data(), h.A0.col.size() * sizeof(int32_t));
+        if (src0) {
+            std::vector<int> row_of(h.A_mesh.nnz());
+            for (int i = 0; i < h.A_mesh.n_rows; ++i)
+                for (int e = h.A_mesh.ptr[i]; e < h.A_mesh.ptr[i + 1]; ++e) row_of[e] = i;
+            for (int64_t k = 0; k < h.A0.nnz(); ++k) {
+                const int64_t e = h.smap.empty() ? k : h.smap[k];
+                src0[k] = (int64_t)row_of[e] * n + h.A_mesh.col[e];
+            }
+        }
         if (order && !h.order.empty()) std::memcpy(order, h.order.data(), h.order.size() * sizeof(int32_t));
         int64_t po = 0, eo = 0;
         for (int t = 0; t + 1 < T; ++t) {

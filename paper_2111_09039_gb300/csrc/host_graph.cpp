@@ -101,9 +101,37 @@ struct MaxItem {
 };
 }  // namespace
 
-std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count) {
+std::vector<int> boundary_vertices(int n, int m, const int *F) {
+    std::vector<int64_t> key;
+    key.reserve((size_t)m * 3);
+    for (int t = 0; t < m; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int64_t a = F[3 * t + k], b = F[3 * t + (k + 1) % 3];
+            key.push_back(std::min(a, b) * n + std::max(a, b));
+        }
+    std::sort(key.begin(), key.end());
+    std::vector<char> on(n, 0);
+    for (size_t i = 0; i < key.size();) {
+        size_t j = i;
+        while (j < key.size() && key[j] == key[i]) ++j;
+        if (j - i == 1) {
+            on[key[i] / n] = 1;
+            on[key[i] % n] = 1;
+        }
+        i = j;
+    }
+    std::vector<int> b;
+    for (int v = 0; v < n; ++v)
+        if (on[v]) b.push_back(v);
+    return b;
+}
+
+std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count, const std::vector<char> *cand) {
     HSIM_CHECK_ARG(start >= 0 && start < g.n, "start vertex out of range");
-    HSIM_CHECK_ARG(count >= 1 && count <= g.n, "bad sample count");
+    HSIM_CHECK_ARG(!cand || (*cand)[start], "start vertex is not a degree of freedom");
+    int ncand = g.n;
+    if (cand) ncand = (int)std::count_if(cand->begin(), cand->end(), [](char c) { return c != 0; });
+    HSIM_CHECK_ARG(count >= 1 && count <= ncand, "bad sample count");
     std::vector<double> dist(g.n, INFINITY);
     std::vector<int> order;
     order.reserve(count);
@@ -131,7 +159,8 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count) 
     // Lazy max-heap: each vertex keeps one entry whose key is >= its current
     // distance (distances only decrease); a stale top is re-keyed.
     std::priority_queue<MaxItem> far;
-    for (int v = 0; v < g.n; ++v) far.push({dist[v], v});
+    for (int v = 0; v < g.n; ++v)
+        if (!cand || (*cand)[v]) far.push({dist[v], v});
     while ((int)order.size() < count) {
         MaxItem top = far.top();
         far.pop();
@@ -146,11 +175,20 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count) 
 }
 
 Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int nc, bool fine_is_mesh,
-                 double sigma, double *rho_out, int *fallback_rows) {
+                 double sigma, double *rho_out, int *fallback_rows, const std::vector<int> *dofs) {
     const double rho = std::sqrt(sigma * g.area / ((double)nc * M_PI));
     *rho_out = rho;
     std::vector<int> rank(g.n, -1);
     for (int k = 0; k < (int)order.size(); ++k) rank[order[k]] = k;
+    // row of each fine vertex: mesh id, position among the listed degrees of
+    // freedom, or position in the sampling order (-1: not on the fine level)
+    std::vector<int> row_of;
+    if (fine_is_mesh && dofs) {
+        row_of.assign(g.n, -1);
+        for (int k = 0; k < (int)dofs->size(); ++k) row_of[(*dofs)[k]] = k;
+    }
+    auto fine_row = [&](int v) { return fine_is_mesh ? (dofs ? row_of[v] : v) : rank[v]; };
+    auto fine_vertex = [&](int r) { return fine_is_mesh ? (dofs ? (*dofs)[r] : r) : order[r]; };
     // triplets (row, centre, weight)
     struct Trip {
         int row, c;
@@ -182,7 +220,7 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
             }
         }
         for (int v : touched) {
-            int row = fine_is_mesh ? v : rank[v];
+            int row = fine_row(v);
             if (row >= 0 && row < nf) trips.push_back({row, c, 1.0 - dist[v] / rho});
             dist[v] = INFINITY;
         }
@@ -217,7 +255,7 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
         }
         for (int r = 0; r < nf; ++r)
             if (!covered[r]) {
-                int v = fine_is_mesh ? r : order[r];
+                int v = fine_vertex(r);
                 HSIM_CHECK_ARG(label[v] >= 0, "a connected component of the mesh holds no coarse vertex");
                 trips.push_back({r, label[v], 1.0});
             }
@@ -245,23 +283,36 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
 }
 
 HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
-                                   int levels, int start_vertex, double sigma, int q) {
+                                   int levels, int start_vertex, double sigma, int q, bool dirichlet) {
     HSIM_CHECK_ARG(p >= 1, "p must be >= 1");
     HSIM_CHECK_ARG(sigma > 0.0, "sigma must be positive");
     HostHierarchy h;
     h.g = build_mesh_graph(n, m, V, F, L2);
     HSIM_CHECK_ARG(start_vertex >= 0 && start_vertex < n, "start_vertex out of range");
-    h.sizes = level_sizes(n, p, levels > 0 ? levels : (p <= 200 ? 2 : 3));
+    std::vector<char> interior;
+    if (dirichlet) {
+        interior.assign(n, 1);
+        for (int v : boundary_vertices(n, m, F)) interior[v] = 0;
+        for (int v = 0; v < n; ++v)
+            if (interior[v]) h.dofs.push_back(v);
+        HSIM_CHECK_ARG(!h.dofs.empty(), "a Dirichlet boundary leaves no interior vertex");
+        HSIM_CHECK_ARG(interior[start_vertex], "start_vertex lies on the Dirichlet boundary");
+    }
+    h.A_mesh = mesh_pattern(h.g);
+    if (dirichlet) h.A0 = restrict_pattern(h.A_mesh, h.dofs, &h.smap);
+    else h.A0 = h.A_mesh;
+    const int n0 = dirichlet ? (int)h.dofs.size() : n;
+    h.sizes = level_sizes(n0, p, levels > 0 ? levels : (p <= 200 ? 2 : 3));
     const int T = (int)h.sizes.size();
     HSIM_CHECK_ARG(T <= 8, "at most 8 levels");
     HSIM_CHECK_ARG(q <= h.sizes[T - 1], "p too large for the mesh");
-    if (T > 1) h.order = farthest_point_order(h.g, start_vertex, h.sizes[1]);
+    if (T > 1) h.order = farthest_point_order(h.g, start_vertex, h.sizes[1], dirichlet ? &interior : nullptr);
     h.U.resize(T - 1);
     h.rho.assign(T - 1, 0.0);
     h.fallback.assign(T - 1, 0);
     for (int tau = 0; tau + 1 < T; ++tau)
         h.U[tau] = prolongation(h.g, h.order, h.sizes[tau], h.sizes[tau + 1], tau == 0, sigma, &h.rho[tau],
-                                &h.fallback[tau]);
+                                &h.fallback[tau], dirichlet ? &h.dofs : nullptr);
     return h;
 }
 

@@ -107,6 +107,30 @@ Csr permute_symmetric(const Csr &A, const std::vector<int> &iperm, std::vector<i
     return B;
 }
 
+Csr restrict_pattern(const Csr &A, const std::vector<int> &keep, std::vector<int64_t> *value_map) {
+    std::vector<int> id(A.n_rows, -1);
+    for (size_t k = 0; k < keep.size(); ++k) {
+        HSIM_CHECK_ARG(keep[k] >= 0 && keep[k] < A.n_rows && (k == 0 || keep[k] > keep[k - 1]),
+                       "restriction indices must ascend within the matrix");
+        id[keep[k]] = (int)k;
+    }
+    Csr B;
+    B.n_rows = B.n_cols = (int)keep.size();
+    B.ptr.assign(keep.size() + 1, 0);
+    if (value_map) value_map->clear();
+    for (size_t k = 0; k < keep.size(); ++k) {
+        const int i = keep[k];
+        for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+            const int j = id[A.col[e]];
+            if (j < 0) continue;
+            B.col.push_back(j);  // ascending: keep ascends and A's columns are sorted
+            if (value_map) value_map->push_back(e);
+        }
+        B.ptr[k + 1] = (int)B.col.size();
+    }
+    return B;
+}
+
 Csr permute_rows_cols(const Csr &A, const std::vector<int> &row_iperm, const std::vector<int> &col_iperm) {
     const int n = A.n_rows;
     std::vector<int> rperm(n);

@@ -136,13 +136,19 @@ struct ProlongData {
 struct hsim_hier {
     hsim_ctx *ctx = nullptr;
     int device = 0;
-    int n = 0, m = 0, p = 0, T = 0;
+    int n = 0, m = 0, p = 0, T = 0;  // n: level-0 unknowns
+    int n_mesh = 0;                    // mesh vertices (n unless a Dirichlet boundary removes some)
     hsim_options opts{};
     std::vector<int> sizes, order;
+    std::vector<int> dofs;             // Dirichlet: mesh id of each level-0 unknown (empty: identity)
     std::vector<LevelData> lev;
     std::vector<ProlongData> pro;
-    // level-0 assembly data (natural pattern)
-    DevCsr pat0;
+    // level-0 pattern of S (natural order) and the assembly data; with a
+    // Dirichlet boundary the assembly runs on the whole mesh's pattern patm,
+    // then S and M are gathered into pat0 (maps d_smap, d_dofs)
+    DevCsr pat0, patm;
+    DevBuf<int64_t> d_smap;
+    DevBuf<int> d_dofs;
     DevBuf<int> dF, d_ecot, d_vt_ptr, d_vt_idx, d_diag_ptr, d_diag_col;
     // workspaces, grown on demand
     DevBuf<double> S0int, M0int, Md0int, dinv0, arena, dpos, ritz_work, Sbar, Mbar, lam, phibar, res_sums,
@@ -854,20 +860,29 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     auto H = std::make_unique<hsim_hier>();
     H->ctx = ctx;
     H->device = ctx->device;
-    H->n = n;
     H->m = m;
     H->p = p;
     H->opts = o;
-    HostHierarchy hh = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, subspace_q(p, o));
+    const bool dirichlet = o.boundary == HSIM_BOUNDARY_DIRICHLET;
+    HostHierarchy hh = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, subspace_q(p, o),
+                                            dirichlet);
     H->sizes = hh.sizes;
     const int T = (int)H->sizes.size();
     H->T = T;
     H->order = std::move(hh.order);
+    H->n_mesh = n;
+    H->n = H->sizes[0];
     // natural patterns and prolongations
     H->lev.resize(T);
     H->pro.resize(T - 1);
-    H->lev[0].n = n;
-    H->lev[0].pat_nat = mesh_pattern(hh.g);
+    H->lev[0].n = H->n;
+    H->lev[0].pat_nat = std::move(hh.A0);
+    const Csr &Amesh = hh.A_mesh;  // every mesh edge plus the diagonal
+    if (dirichlet) {
+        H->d_smap.upload(hh.smap, s);
+        H->d_dofs.upload(hh.dofs, s);
+        H->dofs = std::move(hh.dofs);
+    }
     for (int tau = 0; tau + 1 < T; ++tau) {
         ProlongData &P = H->pro[tau];
         P.U_nat = std::move(hh.U[tau]);
@@ -913,15 +928,17 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
         P.dT.upload(P.T_pat, s);
     }
     {
-        std::vector<int> dp(n + 1), dc(n);
-        for (int i = 0; i <= n; ++i) dp[i] = i;
-        for (int i = 0; i < n; ++i) dc[i] = i;
+        const int n0 = H->n;  // the level-0 mass matrix is diagonal: identity pattern
+        std::vector<int> dp(n0 + 1), dc(n0);
+        for (int i = 0; i <= n0; ++i) dp[i] = i;
+        for (int i = 0; i < n0; ++i) dc[i] = i;
         H->d_diag_ptr.upload(dp, s);
         H->d_diag_col.upload(dc, s);
     }
-    // level-0 assembly data in the natural pattern
-    const Csr &A0 = H->lev[0].pat_nat;
-    H->pat0.upload(A0, s);
+    // level-0 assembly data in the natural pattern of the whole mesh
+    const Csr &A0 = Amesh;
+    H->pat0.upload(H->lev[0].pat_nat, s);
+    if (dirichlet) H->patm.upload(A0, s);
     std::vector<int> ecot(2 * (size_t)A0.nnz(), -1);
     auto find = [&](int i, int j) -> int64_t {
         auto b = A0.col.begin() + A0.ptr[i], e = A0.col.begin() + A0.ptr[i + 1];
@@ -965,6 +982,8 @@ hsim_options checked(const hsim_options *o) {
     HSIM_CHECK_ARG(r.inv_iters >= 1, "inv_iters must be >= 1");
     HSIM_CHECK_ARG(r.precision == HSIM_FP64 || r.precision == HSIM_MIXED, "unknown precision");
     HSIM_CHECK_ARG(r.refine >= -1 && r.refine <= 1, "refine must be -1, 0 or 1");
+    HSIM_CHECK_ARG(r.boundary == HSIM_BOUNDARY_NATURAL || r.boundary == HSIM_BOUNDARY_DIRICHLET,
+                   "unknown boundary condition");
     return r;
 }
 
@@ -989,6 +1008,7 @@ void hsim_default_options(hsim_options *o) {
     o->leaf_size = 32;
     o->q = 0;
     o->refine = 0;
+    o->boundary = HSIM_BOUNDARY_NATURAL;
 }
 
 const char *hsim_last_error(void) { return g_last_error.c_str(); }
@@ -1054,6 +1074,16 @@ hsim_status hsim_hier_info(const hsim_hier *h, int *levels, int *sizes, int32_t 
     });
 }
 
+hsim_status hsim_hier_dofs(const hsim_hier *h, int32_t *dofs) {
+    return guard([&] {
+        HSIM_CHECK_ARG(h && dofs, "NULL argument");
+        if (h->dofs.empty())
+            for (int i = 0; i < h->n; ++i) dofs[i] = i;
+        else
+            std::memcpy(dofs, h->dofs.data(), h->dofs.size() * sizeof(int32_t));
+    });
+}
+
 hsim_status hsim_hier_pattern(const hsim_hier *h, int *n, int64_t *nnz, const int32_t **ptr, const int32_t **col) {
     return guard([&] {
         HSIM_CHECK_ARG(h, "NULL hierarchy");
@@ -1085,11 +1115,21 @@ hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *h, const double *V_dev
         HSIM_CHECK_ARG((V_dev != nullptr) != (L2_dev != nullptr), "exactly one of V and L2 must be given");
         DeviceGuard dg(ctx->device);
         cudaStream_t s = ctx->stream;
-        DevBuf<double> cot((size_t)3 * h->m), area((size_t)h->m);
+        DevBuf<double> cot((size_t)3 * h->m), area((size_t)h->m), Sm, Mm;
         k::triangle_geometry(s, h->m, h->dF.p, V_dev, L2_dev, cot.p, area.p);
-        k::assemble_sm(s, h->n, h->pat0.ptr.p, h->pat0.col.p, h->d_ecot.p, cot.p, h->d_vt_ptr.p, h->d_vt_idx.p, area.p,
-                       S_val, M_diag);
-        HSIM_CUDA(cudaStreamSynchronize(s));
+        if (h->dofs.empty()) {
+            k::assemble_sm(s, h->n, h->pat0.ptr.p, h->pat0.col.p, h->d_ecot.p, cot.p, h->d_vt_ptr.p, h->d_vt_idx.p,
+                           area.p, S_val, M_diag);
+        } else {
+            // Dirichlet: the whole mesh, then the interior rows and columns
+            Sm.alloc((size_t)h->patm.nnz);
+            Mm.alloc((size_t)h->n_mesh);
+            k::assemble_sm(s, h->n_mesh, h->patm.ptr.p, h->patm.col.p, h->d_ecot.p, cot.p, h->d_vt_ptr.p,
+                           h->d_vt_idx.p, area.p, Sm.p, Mm.p);
+            k::gather_values(s, h->pat0.nnz, h->d_smap.p, Sm.p, S_val);
+            k::gather_values_i(s, h->n, h->d_dofs.p, Mm.p, M_diag);
+        }
+        HSIM_CUDA(cudaStreamSynchronize(s));  // before the temporaries are freed
     });
 }
 

@@ -238,3 +238,84 @@ def test_hierarchy_single_level_and_errors(hs):
         hs.check_hierarchy(F, V=V, p=20, levels=2)
     assert e.value.name == "HSIM_E_INVALID_ARG"
     assert "component" in str(e.value)
+
+
+@pytest.mark.parametrize("case", ["square_T2", "square_T3", "patch_T2", "patch_narrow"])
+def test_dirichlet_hierarchy_matches_oracle_on_host(hs, case):
+    # boundary vertices eliminated, hierarchy over the interior vertices:
+    # the library's host code against the oracle, index-exact
+    if case.startswith("square"):
+        mesh, p, levels, sigma = synth.flat_square(64), 20, int(case[-1]), 7.0
+    else:
+        mesh, p, levels = synth.bumpy_patch(60, 50, 8), 20, 2
+        sigma = 0.5 if case == "patch_narrow" else 7.0
+    interior = np.setdiff1d(np.arange(mesh.n), assembly.boundary_vertices(mesh))
+    s = int(interior[len(interior) // 3])
+    H = hierarchy.build_hierarchy(mesh, p, levels, s, sigma, dofs=interior)
+    sizes, order, U, dofs = hs.check_hierarchy(mesh.F, V=mesh.V, p=p, levels=levels, start_vertex=s,
+                                               sigma=sigma, boundary=1, return_dofs=True)
+    np.testing.assert_array_equal(dofs, interior)
+    assert sizes == H.sizes and sizes[0] == len(interior)
+    np.testing.assert_array_equal(order, H.order)
+    for (r, c, rp, cl, vl), Uo in zip(U, H.U):
+        assert (r, c) == Uo.shape
+        np.testing.assert_array_equal(rp, Uo.indptr)
+        np.testing.assert_array_equal(cl, Uo.indices)
+        np.testing.assert_allclose(vl, Uo.data, rtol=1e-15, atol=0)
+    if case == "patch_narrow":
+        assert H.fallback_rows[0] > 0
+    # the natural condition on the same mesh keeps every vertex
+    sizes_n, _, _, dofs_n = hs.check_hierarchy(mesh.F, V=mesh.V, p=p, levels=levels, start_vertex=s,
+                                               return_dofs=True)
+    assert sizes_n[0] == mesh.n
+    np.testing.assert_array_equal(dofs_n, np.arange(mesh.n))
+
+
+def test_dirichlet_hierarchy_errors(hs):
+    mesh = synth.flat_square(40)
+    b = assembly.boundary_vertices(mesh)
+    with pytest.raises(hs.HsimError) as e:       # start vertex on the boundary
+        hs.check_hierarchy(mesh.F, V=mesh.V, p=20, levels=2, start_vertex=int(b[3]), boundary=1)
+    assert e.value.name == "HSIM_E_INVALID_ARG" and "boundary" in str(e.value)
+    with pytest.raises(hs.HsimError):            # unknown condition
+        hs.check_hierarchy(mesh.F, V=mesh.V, p=20, levels=2, start_vertex=100, boundary=2)
+    # a single triangle has no interior vertex
+    with pytest.raises(hs.HsimError) as e:
+        hs.check_hierarchy(np.array([[0, 1, 2]]), V=np.eye(3), p=1, levels=1, boundary=1)
+    assert "interior" in str(e.value)
+    # a closed mesh has no boundary: Dirichlet changes nothing
+    w, torus, s = synth.make_workload("bumpy_torus_64")
+    a = hs.check_hierarchy(torus.F, V=torus.V, p=w.p, levels=w.levels, start_vertex=s)
+    d = hs.check_hierarchy(torus.F, V=torus.V, p=w.p, levels=w.levels, start_vertex=s, boundary=1)
+    assert a[0] == d[0]
+    np.testing.assert_array_equal(a[1], d[1])
+
+
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_level0_pattern_and_assembly_map(hs, boundary):
+    # the level-0 pattern hsim_solve expects: every edge among the level-0
+    # unknowns plus the diagonal, rows in increasing mesh id; each entry takes
+    # its assembled value from the whole mesh's entry (dofs[r], dofs[c])
+    mesh = synth.bumpy_patch(30, 26, 9)
+    interior = np.setdiff1d(np.arange(mesh.n), assembly.boundary_vertices(mesh))
+    s = int(interior[5])
+    sizes, order, U, dofs, (ptr0, col0, src0) = hs.check_hierarchy(
+        mesh.F, V=mesh.V, p=10, levels=2, start_vertex=s, boundary=boundary, return_dofs=True,
+        return_level0=True)
+    keep = interior if boundary else np.arange(mesh.n)
+    np.testing.assert_array_equal(dofs, keep)
+    F = mesh.F.astype(np.int64)
+    a = np.concatenate([F[:, 0], F[:, 1], F[:, 2], np.arange(mesh.n)])
+    b = np.concatenate([F[:, 1], F[:, 2], F[:, 0], np.arange(mesh.n)])
+    A = sp.csr_matrix((np.ones(len(a)), (a, b)), shape=(mesh.n, mesh.n))
+    A = ((A + A.T)[keep][:, keep]).tocsr()
+    A.sort_indices()
+    np.testing.assert_array_equal(ptr0, A.indptr)
+    np.testing.assert_array_equal(col0, A.indices)
+    rows = np.repeat(np.arange(len(keep)), np.diff(ptr0))
+    np.testing.assert_array_equal(src0, keep[rows].astype(np.int64) * mesh.n + keep[col0])
+    # the gathered values are the oracle's S restricted to the unknowns
+    S = assembly.stiffness(mesh)
+    vals = np.asarray(S[src0 // mesh.n, src0 % mesh.n]).ravel()
+    S0 = sp.csr_matrix((vals, col0, ptr0), shape=(len(keep), len(keep)))
+    assert abs(S0 - S[keep][:, keep]).max() == 0.0

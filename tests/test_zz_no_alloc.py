@@ -7,8 +7,8 @@ checks each result against the allocating entry point within the tolerances
 of the other Ritz tests (eigenvalues 1e-10 relative, M-orthonormal
 eigenvectors, eigenvectors equal up to sign for a well-separated spectrum),
 and that a size beyond the fixed limit is refused.  It lives in a file of its
-own that pytest collects last, and passes alone in a fresh process as well
-as after the other tests.
+own that pytest collects after the solver and kernel tests, and passes alone
+in a fresh process as well as after the other tests.
 """
 import ctypes
 
