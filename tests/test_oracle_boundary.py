@@ -164,3 +164,36 @@ def test_boundary_centres_would_make_the_coarse_mass_singular():
     ev_good = np.linalg.eigvalsh(galerkin.restrict(sp.diags(M0), H_int.U[0]).toarray())
     assert ev_bad.min() < 1e-12 * ev_bad.max()
     assert ev_good.min() > 1e-6 * ev_good.max()
+
+
+def test_dirichlet_gradient_through_scattered_eigenvectors():
+    """The shape gradient of Dirichlet eigenvalues is the closed-surface
+    formula applied to the interior eigenvectors scattered to the mesh with
+    zeros on the boundary (S_II and M_II are restrictions of S and M);
+    checked against central finite differences of the dense Dirichlet
+    eigenvalues, also along the boundary vertices' coordinates."""
+    from oracle import gradient
+    m = synth.bumpy_patch(14, 12, 6)
+    I = np.setdiff1d(np.arange(m.n), assembly.boundary_vertices(m))
+    p = 8
+
+    def dirichlet(V):
+        mm = synth.Mesh(V=V, F=m.F)
+        return sim.dense_reference(assembly.stiffness(mm)[I][:, I], assembly.lumped_mass(mm)[I], p)
+
+    lam, Phi_I = dirichlet(m.V)
+    assert np.min(np.diff(lam)) > 1e-4 * lam[-1]
+    Phi = np.zeros((m.n, p))
+    Phi[I] = Phi_I
+    G = gradient.eigenvalue_gradients(m, lam, Phi)
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    b = assembly.boundary_vertices(m)
+    for trial in range(4):
+        D = rng.standard_normal(m.V.shape)
+        if trial == 3:
+            D[I] = 0.0                    # move the boundary vertices only
+        fd = (dirichlet(m.V + h * D)[0] - dirichlet(m.V - h * D)[0]) / (2 * h)
+        an = np.einsum("pvc,vc->p", G, D)
+        np.testing.assert_allclose(an, fd, atol=1e-6 * np.abs(an).max())
+    assert np.abs(G[:, b]).max() > 0.0
