@@ -52,6 +52,13 @@ struct HostHierarchy {
 };
 HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
                                    int levels, int start_vertex, double sigma, int q, bool dirichlet);
+// The two halves of build_host_hierarchy: the mesh graph, the degrees of
+// freedom, the level-0 patterns and the level sizes; then the sampling order
+// and the prolongations (the long sequential part, which the caller may
+// overlap with the symbolic analysis of A0).
+HostHierarchy host_levels(int n, int m, const double *V, const int *F, const double *L2, int p, int levels,
+                          int start_vertex, double sigma, int q, bool dirichlet);
+void host_samples(HostHierarchy &h, int start_vertex, double sigma);
 
 // ---- sparse pattern algebra -------------------------------------------
 Csr mesh_pattern(const MeshGraph &g);                 // edges + diagonal, sorted

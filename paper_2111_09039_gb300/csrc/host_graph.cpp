@@ -12,6 +12,7 @@
 #include <utility>
 
 #include "host.h"
+#include "parallel.h"
 
 namespace hsim {
 
@@ -50,27 +51,53 @@ MeshGraph build_mesh_graph(int n, int m, const double *V, const int *F, const do
         area += 0.25 * std::sqrt(std::max(s16, 0.0));
     }
     g.area = area;
-    // undirected edges with the smallest squared length among their triangles
-    std::vector<std::pair<int64_t, double>> e;
-    e.reserve((size_t)m * 6);
+    // undirected edges with the smallest squared length among their
+    // triangles: both directions of every triangle edge bucketed by the
+    // source vertex, each bucket sorted by (target, squared length) and the
+    // first entry per target kept
+    std::vector<int64_t> bstart(n + 1, 0);
     for (int t = 0; t < m; ++t)
         for (int k = 0; k < 3; ++k) {
-            int a = F[3 * t + (k + 1) % 3], b = F[3 * t + (k + 2) % 3];
-            double l2 = g.l2[3 * (size_t)t + k];
-            e.push_back({(int64_t)a * n + b, l2});
-            e.push_back({(int64_t)b * n + a, l2});
+            bstart[F[3 * t + (k + 1) % 3] + 1]++;
+            bstart[F[3 * t + (k + 2) % 3] + 1]++;
         }
-    std::sort(e.begin(), e.end());
-    g.ptr.assign(n + 1, 0);
-    for (size_t i = 0; i < e.size(); ++i) {
-        if (i > 0 && e[i].first == e[i - 1].first) continue;
-        int u = (int)(e[i].first / n), v = (int)(e[i].first % n);
-        HSIM_CHECK_ARG(u != v, "triangle with repeated vertex");
-        g.ptr[u + 1]++;
-        g.idx.push_back(v);
-        g.w.push_back(std::sqrt(e[i].second));
+    for (int i = 0; i < n; ++i) bstart[i + 1] += bstart[i];
+    std::vector<std::pair<int, double>> bucket(bstart[n]);
+    {
+        std::vector<int64_t> fill(bstart.begin(), bstart.end() - 1);
+        for (int t = 0; t < m; ++t)
+            for (int k = 0; k < 3; ++k) {
+                int a = F[3 * t + (k + 1) % 3], b = F[3 * t + (k + 2) % 3];
+                double l2 = g.l2[3 * (size_t)t + k];
+                bucket[fill[a]++] = {b, l2};
+                bucket[fill[b]++] = {a, l2};
+            }
     }
-    for (int i = 0; i < n; ++i) g.ptr[i + 1] += g.ptr[i];
+    const int nch = chunk_count(n, 4096);
+    std::vector<std::vector<int>> cidx(nch);
+    std::vector<std::vector<double>> cw(nch);
+    std::vector<int> deg(n, 0);
+    parallel_chunks(n, 4096, [&](int ch, int64_t u0, int64_t u1) {
+        for (int64_t u = u0; u < u1; ++u) {
+            auto b = bucket.begin() + bstart[u], e = bucket.begin() + bstart[u + 1];
+            std::sort(b, e);
+            for (auto it = b; it != e; ++it) {
+                if (it != b && it->first == (it - 1)->first) continue;
+                HSIM_CHECK_ARG(it->first != u, "triangle with repeated vertex");
+                cidx[ch].push_back(it->first);
+                cw[ch].push_back(std::sqrt(it->second));
+                deg[u]++;
+            }
+        }
+    });
+    g.ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) g.ptr[i + 1] = g.ptr[i] + deg[i];
+    g.idx.reserve(g.ptr[n]);
+    g.w.reserve(g.ptr[n]);
+    for (int ch = 0; ch < nch; ++ch) {
+        g.idx.insert(g.idx.end(), cidx[ch].begin(), cidx[ch].end());
+        g.w.insert(g.w.end(), cw[ch].begin(), cw[ch].end());
+    }
     return g;
 }
 
@@ -93,12 +120,6 @@ struct MinItem {
 };
 using MinHeap = std::priority_queue<MinItem, std::vector<MinItem>, std::greater<MinItem>>;
 
-struct MaxItem {
-    double d;
-    int v;
-    // larger distance first; among equal distances the lower vertex id first
-    bool operator<(const MaxItem &o) const { return d < o.d || (d == o.d && v > o.v); }
-};
 }  // namespace
 
 std::vector<int> boundary_vertices(int n, int m, const int *F) {
@@ -132,14 +153,32 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count, 
     int ncand = g.n;
     if (cand) ncand = (int)std::count_if(cand->begin(), cand->end(), [](char c) { return c != 0; });
     HSIM_CHECK_ARG(count >= 1 && count <= ncand, "bad sample count");
-    std::vector<double> dist(g.n, INFINITY);
+    const int n = g.n;
+    std::vector<double> dist(n, INFINITY);
     std::vector<int> order;
     order.reserve(count);
+    // The farthest candidate is kept in a tournament tree over blocks of kB
+    // consecutive vertices; a block whose distances changed is rescanned
+    // before the next choice (the lowered region of one sample is small and
+    // local, so few blocks change per sample).
+    constexpr int kB = 512;
+    const int nb = (n + kB - 1) / kB;
+    std::vector<char> dirty(nb, 1);
+    std::vector<int> dirty_list(nb);
+    for (int b = 0; b < nb; ++b) dirty_list[b] = b;
+    auto mark = [&](int v) {
+        const int b = v / kB;
+        if (!dirty[b]) {
+            dirty[b] = 1;
+            dirty_list.push_back(b);
+        }
+    };
     MinHeap heap;
     // Lower the field by the distances from src, following only improving edges.
     auto insert = [&](int src) {
         order.push_back(src);
         dist[src] = 0.0;
+        mark(src);
         heap.push({0.0, src});
         while (!heap.empty()) {
             MinItem it = heap.top();
@@ -150,26 +189,32 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count, 
                 double nd = it.d + g.w[e];
                 if (nd < dist[u]) {
                     dist[u] = nd;
+                    mark(u);
                     heap.push({nd, u});
                 }
             }
         }
     };
+    // a is farther than b: larger distance, the lower vertex id on ties (-1: none)
+    auto farther = [&](int a, int b) {
+        return b < 0 || (a >= 0 && (dist[a] > dist[b] || (dist[a] == dist[b] && a < b)));
+    };
+    int leaves = 1;
+    while (leaves < nb) leaves *= 2;
+    std::vector<int> tree(2 * (size_t)leaves, -1);
     insert(start);
-    // Lazy max-heap: each vertex keeps one entry whose key is >= its current
-    // distance (distances only decrease); a stale top is re-keyed.
-    std::priority_queue<MaxItem> far;
-    for (int v = 0; v < g.n; ++v)
-        if (!cand || (*cand)[v]) far.push({dist[v], v});
     while ((int)order.size() < count) {
-        MaxItem top = far.top();
-        far.pop();
-        if (top.d != dist[top.v]) {
-            far.push({dist[top.v], top.v});
-            continue;
+        for (int b : dirty_list) {
+            int best = -1;
+            for (int v = b * kB, e = std::min(n, (b + 1) * kB); v < e; ++v)
+                if ((!cand || (*cand)[v]) && farther(v, best)) best = v;
+            dirty[b] = 0;
+            int i = leaves + b;
+            tree[i] = best;
+            for (i >>= 1; i >= 1; i >>= 1) tree[i] = farther(tree[2 * i], tree[2 * i + 1]) ? tree[2 * i] : tree[2 * i + 1];
         }
-        insert(top.v);
-        far.push({dist[top.v], top.v});
+        dirty_list.clear();
+        insert(tree[1]);
     }
     return order;
 }
@@ -189,49 +234,57 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
     }
     auto fine_row = [&](int v) { return fine_is_mesh ? (dofs ? row_of[v] : v) : rank[v]; };
     auto fine_vertex = [&](int r) { return fine_is_mesh ? (dofs ? (*dofs)[r] : r) : order[r]; };
-    // triplets (row, centre, weight)
+    // (row, centre, weight) of every fine vertex within rho of a centre: one
+    // truncated Dijkstra per centre, centres split into chunks that run
+    // concurrently; each chunk lists its centres' entries in centre order
     struct Trip {
         int row, c;
         double w;
     };
-    std::vector<Trip> trips;
-    trips.reserve((size_t)nf * 8);
-    std::vector<double> dist(g.n, INFINITY);
-    std::vector<int> touched;
-    MinHeap heap;
-    for (int c = 0; c < nc; ++c) {
-        int s = order[c];
-        touched.clear();
-        dist[s] = 0.0;
-        touched.push_back(s);
-        heap.push({0.0, s});
-        while (!heap.empty()) {
-            MinItem it = heap.top();
-            heap.pop();
-            if (it.d > dist[it.v]) continue;
-            for (int e = g.ptr[it.v]; e < g.ptr[it.v + 1]; ++e) {
-                int u = g.idx[e];
-                double nd = it.d + g.w[e];
-                if (nd < rho && nd < dist[u]) {
-                    if (dist[u] == INFINITY) touched.push_back(u);
-                    dist[u] = nd;
-                    heap.push({nd, u});
+    const int nch = chunk_count(nc, 64);
+    std::vector<std::vector<Trip>> part(nch);
+    parallel_chunks(nc, 64, [&](int ch, int64_t c0, int64_t c1) {
+        std::vector<Trip> &trips = part[ch];
+        std::vector<double> dist(g.n, INFINITY);
+        std::vector<int> touched;
+        MinHeap heap;
+        for (int c = (int)c0; c < (int)c1; ++c) {
+            int s = order[c];
+            touched.clear();
+            dist[s] = 0.0;
+            touched.push_back(s);
+            heap.push({0.0, s});
+            while (!heap.empty()) {
+                MinItem it = heap.top();
+                heap.pop();
+                if (it.d > dist[it.v]) continue;
+                for (int e = g.ptr[it.v]; e < g.ptr[it.v + 1]; ++e) {
+                    int u = g.idx[e];
+                    double nd = it.d + g.w[e];
+                    if (nd < rho && nd < dist[u]) {
+                        if (dist[u] == INFINITY) touched.push_back(u);
+                        dist[u] = nd;
+                        heap.push({nd, u});
+                    }
                 }
             }
+            for (int v : touched) {
+                int row = fine_row(v);
+                if (row >= 0 && row < nf) trips.push_back({row, c, 1.0 - dist[v] / rho});
+                dist[v] = INFINITY;
+            }
         }
-        for (int v : touched) {
-            int row = fine_row(v);
-            if (row >= 0 && row < nf) trips.push_back({row, c, 1.0 - dist[v] / rho});
-            dist[v] = INFINITY;
-        }
-    }
+    });
     // rows without any centre inside the radius: nearest centre, weight one
-    std::vector<char> covered(nf, 0);
-    for (const Trip &t : trips) covered[t.row] = 1;
+    std::vector<int> count(nf, 0);
+    for (const auto &trips : part)
+        for (const Trip &t : trips) count[t.row]++;
+    std::vector<int> fallback_centre(nf, -1);
     int missing = 0;
-    for (int r = 0; r < nf; ++r) missing += !covered[r];
+    for (int r = 0; r < nf; ++r) missing += count[r] == 0;
     *fallback_rows = missing;
     if (missing) {
+        MinHeap heap;
         std::vector<double> nd(g.n, INFINITY);
         std::vector<int> label(g.n, -1);
         for (int c = 0; c < nc; ++c) {
@@ -254,44 +307,53 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
             }
         }
         for (int r = 0; r < nf; ++r)
-            if (!covered[r]) {
+            if (count[r] == 0) {
                 int v = fine_vertex(r);
                 HSIM_CHECK_ARG(label[v] >= 0, "a connected component of the mesh holds no coarse vertex");
-                trips.push_back({r, label[v], 1.0});
+                fallback_centre[r] = label[v];
+                count[r] = 1;
             }
     }
-    std::sort(trips.begin(), trips.end(), [](const Trip &a, const Trip &b) {
-        return a.row < b.row || (a.row == b.row && a.c < b.c);
-    });
+    // CSR by rows; within a row the entries arrive in increasing centre
+    // order (chunks in order, centres in order inside a chunk)
     Csr U;
     U.n_rows = nf;
     U.n_cols = nc;
     U.ptr.assign(nf + 1, 0);
-    U.col.resize(trips.size());
-    U.val.resize(trips.size());
-    for (const Trip &t : trips) U.ptr[t.row + 1]++;
-    for (int r = 0; r < nf; ++r) U.ptr[r + 1] += U.ptr[r];
+    for (int r = 0; r < nf; ++r) U.ptr[r + 1] = U.ptr[r] + count[r];
+    U.col.resize(U.ptr[nf]);
+    U.val.resize(U.ptr[nf]);
+    {
+        std::vector<int> fill(U.ptr.begin(), U.ptr.end() - 1);
+        for (const auto &trips : part)
+            for (const Trip &t : trips) {
+                U.col[fill[t.row]] = t.c;
+                U.val[fill[t.row]++] = t.w;
+            }
+        for (int r = 0; r < nf; ++r)
+            if (fallback_centre[r] >= 0) {
+                U.col[fill[r]] = fallback_centre[r];
+                U.val[fill[r]++] = 1.0;
+            }
+    }
+    // normalise each row: sum in increasing centre order
     for (int r = 0; r < nf; ++r) {
         double sum = 0.0;
-        for (int e = U.ptr[r]; e < U.ptr[r + 1]; ++e) sum += trips[e].w;
-        for (int e = U.ptr[r]; e < U.ptr[r + 1]; ++e) {
-            U.col[e] = trips[e].c;
-            U.val[e] = trips[e].w / sum;
-        }
+        for (int e = U.ptr[r]; e < U.ptr[r + 1]; ++e) sum += U.val[e];
+        for (int e = U.ptr[r]; e < U.ptr[r + 1]; ++e) U.val[e] /= sum;
     }
     return U;
 }
 
-HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
-                                   int levels, int start_vertex, double sigma, int q, bool dirichlet) {
+HostHierarchy host_levels(int n, int m, const double *V, const int *F, const double *L2, int p, int levels,
+                          int start_vertex, double sigma, int q, bool dirichlet) {
     HSIM_CHECK_ARG(p >= 1, "p must be >= 1");
     HSIM_CHECK_ARG(sigma > 0.0, "sigma must be positive");
     HostHierarchy h;
     h.g = build_mesh_graph(n, m, V, F, L2);
     HSIM_CHECK_ARG(start_vertex >= 0 && start_vertex < n, "start_vertex out of range");
-    std::vector<char> interior;
     if (dirichlet) {
-        interior.assign(n, 1);
+        std::vector<char> interior(n, 1);
         for (int v : boundary_vertices(n, m, F)) interior[v] = 0;
         for (int v = 0; v < n; ++v)
             if (interior[v]) h.dofs.push_back(v);
@@ -306,6 +368,17 @@ HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, 
     const int T = (int)h.sizes.size();
     HSIM_CHECK_ARG(T <= 8, "at most 8 levels");
     HSIM_CHECK_ARG(q <= h.sizes[T - 1], "p too large for the mesh");
+    return h;
+}
+
+void host_samples(HostHierarchy &h, int start_vertex, double sigma) {
+    const int T = (int)h.sizes.size();
+    const bool dirichlet = !h.dofs.empty();
+    std::vector<char> interior;
+    if (dirichlet) {
+        interior.assign(h.g.n, 0);
+        for (int v : h.dofs) interior[v] = 1;
+    }
     if (T > 1) h.order = farthest_point_order(h.g, start_vertex, h.sizes[1], dirichlet ? &interior : nullptr);
     h.U.resize(T - 1);
     h.rho.assign(T - 1, 0.0);
@@ -313,6 +386,12 @@ HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, 
     for (int tau = 0; tau + 1 < T; ++tau)
         h.U[tau] = prolongation(h.g, h.order, h.sizes[tau], h.sizes[tau + 1], tau == 0, sigma, &h.rho[tau],
                                 &h.fallback[tau], dirichlet ? &h.dofs : nullptr);
+}
+
+HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, const double *L2, int p,
+                                   int levels, int start_vertex, double sigma, int q, bool dirichlet) {
+    HostHierarchy h = host_levels(n, m, V, F, L2, p, levels, start_vertex, sigma, q, dirichlet);
+    host_samples(h, start_vertex, sigma);
     return h;
 }
 

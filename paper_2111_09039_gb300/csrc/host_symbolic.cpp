@@ -15,6 +15,7 @@
 #include <numeric>
 
 #include "host.h"
+#include "parallel.h"
 
 namespace hsim {
 
@@ -63,22 +64,36 @@ Csr pattern_product(const Csr &A, const Csr &B) {
     C.n_rows = A.n_rows;
     C.n_cols = B.n_cols;
     C.ptr.assign(A.n_rows + 1, 0);
-    std::vector<int> mark(B.n_cols, -1);
-    std::vector<int> row;
-    for (int i = 0; i < A.n_rows; ++i) {
-        row.clear();
-        for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
-            int k = A.col[e];
-            for (int f = B.ptr[k]; f < B.ptr[k + 1]; ++f) {
-                int j = B.col[f];
-                if (mark[j] != i) { mark[j] = i; row.push_back(j); }
+    // row chunks concurrently, each with its own marker array; the chunks'
+    // column lists are concatenated in row order
+    const int nch = chunk_count(A.n_rows, 2048);
+    std::vector<std::vector<int>> part(nch);
+    parallel_chunks(A.n_rows, 2048, [&](int ch, int64_t i0, int64_t i1) {
+        std::vector<int> mark(B.n_cols, -1);
+        std::vector<int> row;
+        std::vector<int> &out = part[ch];
+        for (int i = (int)i0; i < (int)i1; ++i) {
+            row.clear();
+            for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) {
+                int k = A.col[e];
+                for (int f = B.ptr[k]; f < B.ptr[k + 1]; ++f) {
+                    int j = B.col[f];
+                    if (mark[j] != i) { mark[j] = i; row.push_back(j); }
+                }
             }
+            std::sort(row.begin(), row.end());
+            out.insert(out.end(), row.begin(), row.end());
+            C.ptr[i + 1] = (int)row.size();  // row length; prefix-summed below
         }
-        std::sort(row.begin(), row.end());
-        C.col.insert(C.col.end(), row.begin(), row.end());
-        if (C.col.size() > (size_t)INT32_MAX) fail(HSIM_E_INVALID_ARG, "pattern too large for int32 CSR");
-        C.ptr[i + 1] = (int)C.col.size();
+    });
+    int64_t total = 0;
+    for (int i = 0; i < A.n_rows; ++i) {
+        total += C.ptr[i + 1];
+        if (total > (int64_t)INT32_MAX) fail(HSIM_E_INVALID_ARG, "pattern too large for int32 CSR");
+        C.ptr[i + 1] = (int)total;
     }
+    C.col.reserve(total);
+    for (const auto &p : part) C.col.insert(C.col.end(), p.begin(), p.end());
     return C;
 }
 
@@ -89,21 +104,23 @@ Csr permute_symmetric(const Csr &A, const std::vector<int> &iperm, std::vector<i
     Csr B;
     B.n_rows = B.n_cols = n;
     B.ptr.assign(n + 1, 0);
+    for (int p = 0; p < n; ++p) B.ptr[p + 1] = B.ptr[p] + (A.ptr[perm[p] + 1] - A.ptr[perm[p]]);
     B.col.resize(A.nnz());
     if (value_map) value_map->resize(A.nnz());
-    std::vector<std::pair<int, int>> row;
-    for (int p = 0; p < n; ++p) {
-        int i = perm[p];
-        row.clear();
-        for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) row.push_back({iperm[A.col[e]], e});
-        std::sort(row.begin(), row.end());
-        int base = B.ptr[p];
-        for (size_t k = 0; k < row.size(); ++k) {
-            B.col[base + k] = row[k].first;
-            if (value_map) (*value_map)[base + k] = row[k].second;
+    parallel_chunks(n, 4096, [&](int, int64_t p0, int64_t p1) {
+        std::vector<std::pair<int, int>> row;
+        for (int p = (int)p0; p < (int)p1; ++p) {
+            int i = perm[p];
+            row.clear();
+            for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) row.push_back({iperm[A.col[e]], e});
+            std::sort(row.begin(), row.end());
+            int base = B.ptr[p];
+            for (size_t k = 0; k < row.size(); ++k) {
+                B.col[base + k] = row[k].first;
+                if (value_map) (*value_map)[base + k] = row[k].second;
+            }
         }
-        B.ptr[p + 1] = base + (int)row.size();
-    }
+    });
     return B;
 }
 
@@ -139,21 +156,23 @@ Csr permute_rows_cols(const Csr &A, const std::vector<int> &row_iperm, const std
     B.n_rows = A.n_rows;
     B.n_cols = A.n_cols;
     B.ptr.assign(n + 1, 0);
+    for (int p = 0; p < n; ++p) B.ptr[p + 1] = B.ptr[p] + (A.ptr[rperm[p] + 1] - A.ptr[rperm[p]]);
     B.col.resize(A.nnz());
     B.val.resize(A.nnz());
-    std::vector<std::pair<int, double>> row;
-    for (int p = 0; p < n; ++p) {
-        int i = rperm[p];
-        row.clear();
-        for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) row.push_back({col_iperm[A.col[e]], A.val[e]});
-        std::sort(row.begin(), row.end());
-        int base = B.ptr[p];
-        for (size_t k = 0; k < row.size(); ++k) {
-            B.col[base + k] = row[k].first;
-            B.val[base + k] = row[k].second;
+    parallel_chunks(n, 4096, [&](int, int64_t p0, int64_t p1) {
+        std::vector<std::pair<int, double>> row;
+        for (int p = (int)p0; p < (int)p1; ++p) {
+            int i = rperm[p];
+            row.clear();
+            for (int e = A.ptr[i]; e < A.ptr[i + 1]; ++e) row.push_back({col_iperm[A.col[e]], A.val[e]});
+            std::sort(row.begin(), row.end());
+            int base = B.ptr[p];
+            for (size_t k = 0; k < row.size(); ++k) {
+                B.col[base + k] = row[k].first;
+                B.val[base + k] = row[k].second;
+            }
         }
-        B.ptr[p + 1] = base + (int)row.size();
-    }
+    });
     return B;
 }
 

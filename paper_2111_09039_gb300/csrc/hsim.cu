@@ -14,6 +14,7 @@
 #include <atomic>
 #include <chrono>
 #include <functional>
+#include <future>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -864,19 +865,24 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     H->p = p;
     H->opts = o;
     const bool dirichlet = o.boundary == HSIM_BOUNDARY_DIRICHLET;
-    HostHierarchy hh = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, subspace_q(p, o),
-                                            dirichlet);
+    const int leaf = o.leaf_size > 0 ? o.leaf_size : 32;
+    HostHierarchy hh = host_levels(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, subspace_q(p, o), dirichlet);
     H->sizes = hh.sizes;
     const int T = (int)H->sizes.size();
     H->T = T;
-    H->order = std::move(hh.order);
     H->n_mesh = n;
     H->n = H->sizes[0];
-    // natural patterns and prolongations
     H->lev.resize(T);
     H->pro.resize(T - 1);
     H->lev[0].n = H->n;
     H->lev[0].pat_nat = std::move(hh.A0);
+    // the symbolic analysis of level 0 needs only its pattern: it runs on a
+    // worker thread while the sampling and the prolongations are built (the
+    // future is declared after H, so it is joined before H is released)
+    std::future<FrontSymbolic> fs0;
+    if (T > 1) fs0 = std::async(std::launch::async, [&H, leaf] { return analyse(H->lev[0].pat_nat, leaf); });
+    host_samples(hh, o.start_vertex, o.sigma);
+    H->order = std::move(hh.order);
     const Csr &Amesh = hh.A_mesh;  // every mesh edge plus the diagonal
     if (dirichlet) {
         H->d_smap.upload(hh.smap, s);
@@ -894,12 +900,11 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
         H->lev[tau + 1].pat_nat = pattern_product(Ut, AU);
     }
     // orderings and symbolic analyses
-    const int leaf = o.leaf_size > 0 ? o.leaf_size : 32;
-    for (int tau = 0; tau < T; ++tau) {
+    for (int tau = T - 1; tau >= 0; --tau) {
         LevelData &L = H->lev[tau];
         L.dense = (tau == T - 1);
         if (!L.dense) {
-            L.fs = analyse(L.pat_nat, leaf);
+            L.fs = tau == 0 ? fs0.get() : analyse(L.pat_nat, leaf);
         } else {
             L.fs.n = L.n;
             L.fs.perm.resize(L.n);
