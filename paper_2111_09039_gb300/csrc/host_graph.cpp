@@ -173,12 +173,57 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count, 
             dirty_list.push_back(b);
         }
     };
+    // Lower the field by the distances from src, following only improving
+    // edges.  Any order of relaxations that ends with no improving edge gives
+    // the same field (the least rounded path sum to every vertex, as the
+    // rounded sum is monotone in its first operand), so the search may use a
+    // bucket queue of width delta = half the shortest edge: relaxing a vertex
+    // of bucket k lands beyond bucket k, every vertex is final when its bucket
+    // is reached and is expanded once.  Buckets live in a ring of
+    // ceil(longest edge / delta) + 3; a mesh whose edge lengths differ by a
+    // factor above 2^15 uses a binary heap instead.
+    double wmin = INFINITY, wmax = 0.0;
+    for (double w : g.w) {
+        wmin = std::min(wmin, w);
+        wmax = std::max(wmax, w);
+    }
+    const bool buckets = !g.w.empty() && wmax <= 32768.0 * wmin;
+    const double delta = buckets ? 0.5 * wmin : 1.0;
+    const int nring = buckets ? (int)std::ceil(wmax / delta) + 3 : 0;
+    std::vector<std::vector<int>> ring(nring);
+    std::vector<int> stamp(buckets ? n : 0, -1);
     MinHeap heap;
-    // Lower the field by the distances from src, following only improving edges.
     auto insert = [&](int src) {
+        const int id = (int)order.size();
         order.push_back(src);
         dist[src] = 0.0;
         mark(src);
+        if (buckets) {
+            int64_t live = 1;
+            ring[0].push_back(src);
+            for (int64_t k = 0; live > 0; ++k) {
+                std::vector<int> &cur = ring[k % nring];
+                for (size_t i = 0; i < cur.size(); ++i) {
+                    const int v = cur[i];
+                    --live;
+                    if (stamp[v] == id) continue;  // expanded already (pushed more than once)
+                    stamp[v] = id;
+                    const double dv = dist[v];
+                    for (int e = g.ptr[v]; e < g.ptr[v + 1]; ++e) {
+                        int u = g.idx[e];
+                        double nd = dv + g.w[e];
+                        if (nd < dist[u]) {
+                            dist[u] = nd;
+                            mark(u);
+                            ring[(int64_t)(nd / delta) % nring].push_back(u);
+                            ++live;
+                        }
+                    }
+                }
+                cur.clear();
+            }
+            return;
+        }
         heap.push({0.0, src});
         while (!heap.empty()) {
             MinItem it = heap.top();
@@ -241,6 +286,16 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
         int row, c;
         double w;
     };
+    // The searches use the bucket queue of farthest_point_order when the
+    // edge lengths allow it (the distances do not depend on the queue).
+    double wmin = INFINITY, wmax = 0.0;
+    for (double w : g.w) {
+        wmin = std::min(wmin, w);
+        wmax = std::max(wmax, w);
+    }
+    const bool buckets = !g.w.empty() && wmax <= 32768.0 * wmin;
+    const double delta = buckets ? 0.5 * wmin : 1.0;
+    const int nring = buckets ? (int)std::ceil(wmax / delta) + 3 : 0;
     const int nch = chunk_count(nc, 64);
     std::vector<std::vector<Trip>> part(nch);
     parallel_chunks(nc, 64, [&](int ch, int64_t c0, int64_t c1) {
@@ -248,24 +303,51 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
         std::vector<double> dist(g.n, INFINITY);
         std::vector<int> touched;
         MinHeap heap;
+        std::vector<std::vector<int>> ring(nring);
+        std::vector<int> stamp(buckets ? g.n : 0, -1);
         for (int c = (int)c0; c < (int)c1; ++c) {
             int s = order[c];
             touched.clear();
             dist[s] = 0.0;
             touched.push_back(s);
-            heap.push({0.0, s});
-            while (!heap.empty()) {
-                MinItem it = heap.top();
-                heap.pop();
-                if (it.d > dist[it.v]) continue;
-                for (int e = g.ptr[it.v]; e < g.ptr[it.v + 1]; ++e) {
+            int64_t live = 0;  // entries in the bucket ring
+            auto relax = [&](int v, double dv) {
+                for (int e = g.ptr[v]; e < g.ptr[v + 1]; ++e) {
                     int u = g.idx[e];
-                    double nd = it.d + g.w[e];
+                    double nd = dv + g.w[e];
                     if (nd < rho && nd < dist[u]) {
                         if (dist[u] == INFINITY) touched.push_back(u);
                         dist[u] = nd;
-                        heap.push({nd, u});
+                        if (buckets) {
+                            ring[(int64_t)(nd / delta) % nring].push_back(u);
+                            ++live;
+                        } else {
+                            heap.push({nd, u});
+                        }
                     }
+                }
+            };
+            if (buckets) {
+                ring[0].push_back(s);
+                live = 1;
+                for (int64_t k = 0; live > 0; ++k) {
+                    std::vector<int> &cur = ring[k % nring];
+                    for (size_t i = 0; i < cur.size(); ++i) {
+                        const int v = cur[i];
+                        --live;
+                        if (stamp[v] == c) continue;  // expanded already
+                        stamp[v] = c;
+                        relax(v, dist[v]);
+                    }
+                    cur.clear();
+                }
+            } else {
+                heap.push({0.0, s});
+                while (!heap.empty()) {
+                    MinItem it = heap.top();
+                    heap.pop();
+                    if (it.d > dist[it.v]) continue;
+                    relax(it.v, it.d);
                 }
             }
             for (int v : touched) {

@@ -193,11 +193,18 @@ def _hierarchy_case(name):
         # sigma = 0.5: many fine vertices see no centre inside rho
         w, mesh, s = synth.make_workload("bumpy_torus_64")
         return mesh, w.p, w.levels, s, 0.5
+    if name == "short_edge":
+        # one edge 10^6 times shorter than the others: the searches fall
+        # back from the bucket queue to the binary heap
+        mesh = synth.bumpy_patch(40, 36, 12)
+        V = mesh.V.copy()
+        V[1] = V[0] + np.array([1e-8, 0.0, 0.0])
+        return synth.Mesh(V=V, F=mesh.F), 20, 2, 300, 7.0
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("name", ["bumpy_torus_64", "flat_torus_64", "icosphere3_noise", "open_patch",
-                                  "two_tori", "narrow_support"])
+                                  "two_tori", "narrow_support", "short_edge"])
 def test_hierarchy_matches_oracle_on_host(hs, name):
     # level sizes and the farthest-point order exactly; the prolongations'
     # patterns exactly and their values to the rounding of the row sums
