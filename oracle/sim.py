@@ -37,6 +37,13 @@ Steps and readings (each listed in the design notes):
   subspaces of the interior space and the coarse problems Rayleigh-Ritz
   restrictions of the Dirichlet problem.
 
+* Plain SIM (Alg. 1 alone, the paper's comparison without a hierarchy):
+  the same iteration from the initial basis of Sec. 3.2's initialisation
+  heuristic: the diagonal of M as the first column, unit vectors at the
+  q - 2 degrees of freedom with the smallest k_ii / m_ii (ascending ratio,
+  lower index first) as the next ones, and a random last column (an input).
+  The shift is an input of Alg. 1.
+
 Parity unpinned: iteration counts (only the paper's qualitative patterns
 apply) and eigenvectors inside a cluster that straddles index p.
 """
@@ -197,6 +204,30 @@ def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100
     else:
         lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, U, p, eps, alpha, max_iters)
     return HsimResult(lam[:p], normalise_signs(Phi[:, :p]), iters, shifts, coarse, H, S, M, interior)
+
+
+def initial_basis(S, M_diag, q, random_column):
+    """Sec. 3.2, initialisation heuristic: n x q basis [diag(M), e_i for the
+    q - 2 smallest k_ii / m_ii, random_column]."""
+    n = S.shape[0]
+    ratio = S.diagonal() / M_diag
+    idx = np.lexsort((np.arange(n), ratio))[: q - 2]
+    X = np.zeros((n, q))
+    X[:, 0] = M_diag
+    X[idx, np.arange(1, q - 1)] = 1.0
+    X[:, q - 1] = random_column
+    return X
+
+
+def plain_sim(mesh, p, eps, mu, random_column, max_iters=100):
+    """Alg. 1 without a hierarchy on the mesh's S, M from the heuristic
+    initial basis, with shift mu; returns a SimResult (p pairs)."""
+    S = stiffness(mesh)
+    M = lumped_mass(mesh)
+    q = subspace_size(p)
+    X = initial_basis(S, M, q, random_column)
+    r = sim(S, sp.diags(M), X, p, eps, mu, finest=True, max_iters=max_iters)
+    return SimResult(r.lam[:p], normalise_signs(r.Phi[:, :p]), r.iters, r.res, r.history)
 
 
 def dense_reference(S, M_diag_or_matrix, count):
