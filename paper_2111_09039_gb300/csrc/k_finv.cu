@@ -204,9 +204,6 @@ __device__ __forceinline__ void sub4_atomic(float *x, const float (&a)[4], int a
         for (int v = 0; v < 4 && v < avail; ++v) atomicAdd(x + v, -a[v]);
     }
 }
-__device__ __forceinline__ void sub4_atomic(double *x, const double (&a)[4], int avail, bool) {
-    for (int v = 0; v < 4 && v < avail; ++v) atomicAdd(x + v, -a[v]);
-}
 
 // four consecutive shared-memory values (16-byte aligned)
 template <typename T>
