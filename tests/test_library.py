@@ -326,3 +326,18 @@ def test_level0_pattern_and_assembly_map(hs, boundary):
     vals = np.asarray(S[src0 // mesh.n, src0 % mesh.n]).ravel()
     S0 = sp.csr_matrix((vals, col0, ptr0), shape=(len(keep), len(keep)))
     assert abs(S0 - S[keep][:, keep]).max() == 0.0
+
+
+def test_errors_from_worker_threads_reach_the_caller(hs):
+    # an intrinsic mesh whose last triangle repeats a vertex (its squared
+    # lengths are positive, so only the edge bucketing, which runs on worker
+    # threads for this many vertices, can see it)
+    mesh = synth.flat_torus(128)
+    F = mesh.F.copy()
+    F[-1] = [F[-1][0], F[-1][0], F[-1][2]]
+    with pytest.raises(hs.HsimError) as e:
+        hs.check_hierarchy(F, L2=mesh.L2, p=20, levels=2, start_vertex=0)
+    assert e.value.name == "HSIM_E_INVALID_ARG" and "repeated vertex" in str(e.value)
+    # and the library keeps working afterwards
+    sizes, order, U = hs.check_hierarchy(mesh.F, L2=mesh.L2, p=20, levels=2, start_vertex=0)
+    assert sizes == [128 * 128, 1000]
