@@ -31,6 +31,48 @@ def _torch():
     return torch
 
 
+def _on_device(t, name: str, device: int, dtype, numel: int | None = None):
+    """t must be a contiguous CUDA tensor of dtype on cuda:device (with numel
+    elements when given): the library reads it through a raw device pointer,
+    so anything else is refused here."""
+    _check_device(t, name, device)
+    _check_layout(t, name, dtype, numel)
+
+
+def _rows_on_device(t, name: str, device: int, rows: int | None = None, cols: int | None = None):
+    """t must be a 2-D float64 CUDA tensor on cuda:device with unit column
+    stride (rows may be strided, the leading dimension is t.stride(0))."""
+    _check_device(t, name, device)
+    _check_rows(t, name, rows, cols)
+
+
+def _check_device(t, name: str, device: int):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device.type != "cuda" or (t.device.index or 0) != device:
+        raise ValueError(f"{name} must be on cuda:{device}, not {t.device}")
+
+
+def _check_layout(t, name: str, dtype, numel: int | None = None):
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, not {t.numel()}")
+
+
+def _check_rows(t, name: str, rows: int | None = None, cols: int | None = None):
+    torch = _torch()
+    if t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float64 tensor")
+    if t.shape[1] > 0 and (t.stride(1) != 1 or t.stride(0) < t.shape[1]):
+        raise ValueError(f"{name} must have unit column stride and a leading dimension >= its columns")
+    if (rows is not None and t.shape[0] != rows) or (cols is not None and t.shape[1] != cols):
+        raise ValueError(f"{name} must be {rows} x {cols}, not {tuple(t.shape)}")
+
+
 def kernel_launches() -> int:
     return int(lib().hsim_kernel_launches())
 
@@ -181,6 +223,12 @@ def solve(ctx: Context, hier: Hierarchy, S_val, M_diag, p: int, tol: float,
     """HSIM: (eigenvalues (p,), eigenvectors (n, p), info dict) on the GPU."""
     torch = _torch()
     dev = f"cuda:{ctx.device}"
+    _on_device(S_val, "S_val", ctx.device, torch.float64)
+    _on_device(M_diag, "M_diag", ctx.device, torch.float64, hier.n)
+    if not 1 <= p <= hier.n:
+        raise ValueError(f"p must be in [1, {hier.n}]")
+    if S_val.numel() != _pattern_nnz(hier):
+        raise ValueError(f"S_val must have one value per entry of the hierarchy's pattern ({_pattern_nnz(hier)})")
     o = options if options is not None else (default_options(**kw) if kw else hier.options)
     if kw and options is None:
         o.start_vertex = hier.options.start_vertex
@@ -203,6 +251,13 @@ def solve_batched(ctx: Context, hiers, S_vals, M_diags, p, tol: float, options: 
     ps = [int(x) for x in (p if hasattr(p, "__len__") else [p] * k)]
     if not (len(S_vals) == len(M_diags) == len(ps) == k):
         raise ValueError("one S, M and p per hierarchy")
+    for i in range(k):
+        _on_device(S_vals[i], f"S_vals[{i}]", ctx.device, torch.float64)
+        _on_device(M_diags[i], f"M_diags[{i}]", ctx.device, torch.float64, hiers[i].n)
+        if not 1 <= ps[i] <= hiers[i].n:
+            raise ValueError(f"p[{i}] must be in [1, {hiers[i].n}]")
+        if S_vals[i].numel() != _pattern_nnz(hiers[i]):
+            raise ValueError(f"S_vals[{i}] must have one value per entry of its hierarchy's pattern")
     lams = [torch.empty(ps[i], dtype=torch.float64, device=dev) for i in range(k)]
     vecs = [torch.empty((ps[i], hiers[i].n), dtype=torch.float64, device=dev) for i in range(k)]
     arr = lambda xs: (ctypes.c_void_p * max(k, 1))(*[ptr(x) if not isinstance(x, Hierarchy) else x.handle.value
@@ -269,7 +324,11 @@ def eigenvalues(ctx: Context, hier: Hierarchy, V, F, p: int, tol: float, options
 def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None, df: bool = False):
     """Y = A X (CSR A); df=True: the mixed path's double-float variant (hsim_spmm_df)."""
     torch = _torch()
+    _on_device(row_ptr, "row_ptr", ctx.device, torch.int32)
     n_rows = row_ptr.numel() - 1
+    _on_device(col, "col", ctx.device, torch.int32)
+    _on_device(val, "val", ctx.device, torch.float64, col.numel())
+    _rows_on_device(X, "X", ctx.device, n_cols)
     k = X.shape[1]
     Y = torch.empty((n_rows, k), dtype=torch.float64, device=X.device)
     fn = lib().hsim_spmm_df if df else lib().hsim_spmm
@@ -280,6 +339,8 @@ def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None, df: bool
 
 def gram(ctx: Context, A, B):
     torch = _torch()
+    _rows_on_device(A, "A", ctx.device)
+    _rows_on_device(B, "B", ctx.device, A.shape[0])
     G = torch.empty((A.shape[1], B.shape[1]), dtype=torch.float64, device=A.device)
     check(lib().hsim_gram(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
                           B.stride(0), ptr(G)))
@@ -289,6 +350,8 @@ def gram(ctx: Context, A, B):
 def gram_tc(ctx: Context, A, B):
     """A^T B with FP64 accuracy on BF16 tensor cores (digit splitting)."""
     torch = _torch()
+    _rows_on_device(A, "A", ctx.device)
+    _rows_on_device(B, "B", ctx.device, A.shape[0])
     G = torch.empty((A.shape[1], B.shape[1]), dtype=torch.float64, device=A.device)
     check(lib().hsim_gram_tc(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
                              B.stride(0), ptr(G)))
@@ -298,6 +361,8 @@ def gram_tc(ctx: Context, A, B):
 def gemm_update_tc(ctx: Context, A, B):
     """A B with FP64 accuracy on BF16 tensor cores (digit splitting)."""
     torch = _torch()
+    _rows_on_device(A, "A", ctx.device)
+    _rows_on_device(B, "B", ctx.device, A.shape[1])
     C = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=A.device)
     check(lib().hsim_gemm_update_tc(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
                                     B.stride(0), ptr(C), C.stride(0)))
@@ -306,6 +371,8 @@ def gemm_update_tc(ctx: Context, A, B):
 
 def gemm_update(ctx: Context, A, B):
     torch = _torch()
+    _rows_on_device(A, "A", ctx.device)
+    _rows_on_device(B, "B", ctx.device, A.shape[1])
     C = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=A.device)
     check(lib().hsim_gemm_update(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
                                  B.stride(0), ptr(C), C.stride(0)))
@@ -315,12 +382,17 @@ def gemm_update(ctx: Context, A, B):
 def ritz(ctx: Context, Sbar, Mbar, tc: bool = False):
     """Dense Ritz solve; tc=True: the mixed path's variant (hsim_ritz_tc)."""
     torch = _torch()
+    if not isinstance(Sbar, torch.Tensor) or not isinstance(Mbar, torch.Tensor):
+        raise TypeError("Sbar and Mbar must be torch tensors")
     k = Sbar.shape[0]
+    Sbar, Mbar = Sbar.contiguous(), Mbar.contiguous()
+    _rows_on_device(Sbar, "Sbar", ctx.device, k, k)
+    _rows_on_device(Mbar, "Mbar", ctx.device, k, k)
     lam = torch.empty(k, dtype=torch.float64, device=Sbar.device)
     X = torch.empty((k, k), dtype=torch.float64, device=Sbar.device)
     sweeps = ctypes.c_int()
     fn = lib().hsim_ritz_tc if tc else lib().hsim_ritz
-    check(fn(ctx.handle, k, ptr(Sbar.contiguous()), ptr(Mbar.contiguous()), ptr(lam), ptr(X), ctypes.byref(sweeps)))
+    check(fn(ctx.handle, k, ptr(Sbar), ptr(Mbar), ptr(lam), ptr(X), ctypes.byref(sweeps)))
     return lam, X, sweeps.value
 
 
@@ -332,6 +404,8 @@ def galerkin(ctx: Context, n: int, nc: int, A_ptr: np.ndarray, A_col: np.ndarray
     A_col = np.ascontiguousarray(A_col, dtype=np.int32)
     U_ptr = np.ascontiguousarray(U_ptr, dtype=np.int32)
     U_col = np.ascontiguousarray(U_col, dtype=np.int32)
+    _on_device(A_val, "A_val", ctx.device, torch.float64, len(A_col))
+    _on_device(U_val, "U_val", ctx.device, torch.float64, len(U_col))
     nnz = ctypes.c_int64()
     cp, cc, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     check(lib().hsim_galerkin(ctx.handle, n, nc, ptr(A_ptr), ptr(A_col), ptr(A_val), ptr(U_ptr), ptr(U_col),
@@ -350,6 +424,10 @@ def galerkin(ctx: Context, n: int, nc: int, A_ptr: np.ndarray, A_col: np.ndarray
 def shifted_solve(ctx: Context, hier: Hierarchy, tau: int, S_val, M_val, mu: float, B, f32: bool = False):
     """X = (S - mu M)^-1 B on level tau (natural order); returns (X, #negative pivots).
     f32=True: the mixed path's FP32 inverted-factor solve (hsim_shifted_solve_f32)."""
+    torch = _torch()
+    _on_device(S_val, "S_val", ctx.device, torch.float64)
+    _on_device(M_val, "M_val", ctx.device, torch.float64)
+    _rows_on_device(B, "B", ctx.device)
     X = B.clone().contiguous()
     neg = ctypes.c_int()
     fn = lib().hsim_shifted_solve_f32 if f32 else lib().hsim_shifted_solve
