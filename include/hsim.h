@@ -12,7 +12,11 @@
  *   - Pointers named *_dev are CUDA device pointers on the device of the
  *     context; pointers named *_host are host pointers.  The caller owns
  *     every buffer it passes; the library owns the hierarchy, the
- *     factorisations and all workspace.
+ *     factorisations and all workspace.  A device-pointer argument that the
+ *     CUDA runtime classifies as plain (unregistered) host memory or as
+ *     memory of another device is refused with HSIM_E_INVALID_ARG before any
+ *     kernel runs; pinned and managed memory are accepted.  Sizes and
+ *     indices inside device arrays are not checked.
  *   - All device work is issued on the context's stream.  A call returns
  *     after the stream has drained, unless its comment says otherwise.
  *   - Dense matrices are stored row-major unless stated: element (i, j) of

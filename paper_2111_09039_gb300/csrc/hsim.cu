@@ -15,6 +15,7 @@
 #include <chrono>
 #include <functional>
 #include <future>
+#include <initializer_list>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -25,6 +26,7 @@
 #include <string>
 #include <thread>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "common.h"
@@ -68,6 +70,28 @@ hsim_status guard(const std::function<void()> &f) {
 }  // namespace
 
 void hsim::set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+// Kernels read the caller's arrays through raw pointers: plain host memory
+// or memory of another device is refused here, before any launch.  Pinned
+// or managed memory is accepted (the device reaches it); a pointer the
+// runtime cannot classify is let through unchanged.
+void check_device_ptrs(int device, std::initializer_list<std::pair<const char *, const void *>> ptrs) {
+    for (const auto &np : ptrs) {
+        if (!np.second) continue;
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, np.second) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        HSIM_CHECK_ARG(a.type != cudaMemoryTypeUnregistered,
+                       std::string(np.first) + " is host memory; a device pointer is expected");
+        HSIM_CHECK_ARG(a.type != cudaMemoryTypeDevice || a.device == device,
+                       std::string(np.first) + " lives on device " + std::to_string(a.device) +
+                           ", not on the context's device " + std::to_string(device));
+    }
+}
+}  // namespace
 
 struct hsim_ctx {
     int device = 0;
@@ -1119,6 +1143,7 @@ hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *h, const double *V_dev
         HSIM_CHECK_ARG(ctx && h && S_val && M_diag, "NULL argument");
         HSIM_CHECK_ARG((V_dev != nullptr) != (L2_dev != nullptr), "exactly one of V and L2 must be given");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"V", V_dev}, {"L2", L2_dev}, {"S_val", S_val}, {"M_diag", M_diag}});
         cudaStream_t s = ctx->stream;
         DevBuf<double> cot((size_t)3 * h->m), area((size_t)h->m), Sm, Mm;
         k::triangle_geometry(s, h->m, h->dF.p, V_dev, L2_dev, cot.p, area.p);
@@ -1145,6 +1170,7 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *h, const double *S_val, const d
         HSIM_CHECK_ARG(p >= 1 && p <= h->n, "bad p");
         HSIM_CHECK_ARG(tol > 0, "tol must be positive");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_diag", M_diag}, {"evals", evals}, {"evecs", evecs}});
         hsim_options o = checked(opts ? opts : &h->opts);
         run_solve(ctx, h, S_val, M_diag, p, tol, o, evals, evecs, info);
     });
@@ -1168,6 +1194,9 @@ hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers
             HSIM_CHECK_ARG(seen.insert(hiers[i]).second, "hierarchy listed twice (mesh " + std::to_string(i) + ")");
         }
         DeviceGuard dg(ctx->device);
+        for (int i = 0; i < nmesh; ++i)
+            check_device_ptrs(ctx->device, {{"S_vals[i]", S_vals[i]}, {"M_diags[i]", M_diags[i]},
+                                            {"evals[i]", evals[i]}, {"evecs[i]", evecs[i]}});
         const int W = std::max(1, std::min(nmesh, streams > 0 ? streams : 8));
         // inputs produced on the caller's stream are complete before any worker starts
         cudaEvent_t ready;
@@ -1253,6 +1282,8 @@ hsim_status hsim_eig_grad(hsim_ctx *ctx, int n, int m, const double *V, const in
         HSIM_CHECK_ARG(V && dV && (m == 0 || F), "NULL argument");
         HSIM_CHECK_ARG(p == 0 || (evals && evecs && dloss), "NULL argument");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"V", V}, {"F", F}, {"evals", evals}, {"evecs", evecs}, {"dloss", dloss},
+                                        {"dV", dV}});
         k::eig_grad(ctx->stream, n, p == 0 ? 0 : m, p, V, F, evals, evecs, n, dloss, dV);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
     });
@@ -1266,6 +1297,7 @@ hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *ptr,
         if (n_rows == 0 || k == 0) return;
         HSIM_CHECK_ARG(ptr && col && X && Y && (val || n_cols == 0), "NULL argument");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"row_ptr", ptr}, {"col", col}, {"val", val}, {"X", X}, {"Y", Y}});
         k::spmm(ctx->stream, n_rows, ptr, col, val, k, X, ldx, Y, ldy);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
     });
@@ -1279,6 +1311,7 @@ hsim_status hsim_spmm_df(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *p
         if (n_rows == 0 || k == 0) return;
         HSIM_CHECK_ARG(ptr && col && X && Y && (val || n_cols == 0), "NULL argument");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"row_ptr", ptr}, {"col", col}, {"val", val}, {"X", X}, {"Y", Y}});
         int nnz = 0;
         HSIM_CUDA(cudaMemcpy(&nnz, ptr + n_rows, sizeof(int), cudaMemcpyDeviceToHost));
         DevBuf<float2> v2((size_t)std::max(nnz, 1)), X2((size_t)std::max(n_cols, 1) * k);
@@ -1294,6 +1327,7 @@ hsim_status hsim_gram(hsim_ctx *ctx, int n, int ka, int kb, const double *A, int
         HSIM_CHECK_ARG(ctx && A && B && G, "NULL argument");
         HSIM_CHECK_ARG(n >= 0 && ka >= 0 && kb >= 0 && lda >= ka && ldb >= kb, "bad sizes");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"A", A}, {"B", B}, {"G", G}});
         k::gram(ctx->stream, n, ka, kb, A, lda, B, ldb, G, kb, false);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
     });
@@ -1305,6 +1339,7 @@ hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int kk, int m, const double *
         HSIM_CHECK_ARG(ctx && A && B && C, "NULL argument");
         HSIM_CHECK_ARG(n >= 0 && kk >= 0 && m >= 0 && lda >= kk && ldb >= m && ldc >= m, "bad sizes");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"A", A}, {"B", B}, {"C", C}});
         k::gemm_nn(ctx->stream, n, kk, m, A, lda, B, ldb, C, ldc);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
     });
@@ -1316,6 +1351,7 @@ hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int ka, int kb, const double *A, 
         HSIM_CHECK_ARG(ctx && A && B && G, "NULL argument");
         HSIM_CHECK_ARG(n >= 1 && ka >= 1 && kb >= 1 && lda >= ka && ldb >= kb, "bad sizes");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"A", A}, {"B", B}, {"G", G}});
         DevBuf<unsigned char> scratch(k::ozaki_cols_scratch(n, ka) + k::ozaki_cols_scratch(n, kb));
         k::OzakiOperand X = k::ozaki_split_cols(ctx->stream, n, ka, A, lda, scratch.p);
         k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, n, kb, B, ldb, scratch.p + k::ozaki_cols_scratch(n, ka));
@@ -1330,6 +1366,7 @@ hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int kk, int m, const doubl
         HSIM_CHECK_ARG(ctx && A && B && C, "NULL argument");
         HSIM_CHECK_ARG(n >= 1 && kk >= 1 && m >= 1 && lda >= kk && ldb >= m && ldc >= m, "bad sizes");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"A", A}, {"B", B}, {"C", C}});
         DevBuf<unsigned char> scratch(k::ozaki_rows_scratch(n, kk) + k::ozaki_cols_scratch(kk, m));
         k::OzakiOperand X = k::ozaki_split_rows(ctx->stream, n, kk, A, lda, scratch.p);
         k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, kk, m, B, ldb, scratch.p + k::ozaki_rows_scratch(n, kk));
@@ -1345,6 +1382,7 @@ hsim_status ritz_entry(hsim_ctx *ctx, int kk, const double *Sbar, const double *
         HSIM_CHECK_ARG(ctx && Sbar && Mbar && evals && X, "NULL argument");
         HSIM_CHECK_ARG(kk >= 1, "bad size");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"Sbar", Sbar}, {"Mbar", Mbar}, {"evals", evals}, {"X", X}});
         DevBuf<double> work(k::ritz_work_size(kk));
         int sw = 0;
         int rc = k::ritz(ctx->stream, kk, Sbar, kk, Mbar, kk, evals, X, kk, work.p, &sw, ctx->flags.p,
@@ -1373,6 +1411,7 @@ hsim_status hsim_galerkin(hsim_ctx *ctx, int n, int nc, const int32_t *A_ptr, co
         HSIM_CHECK_ARG(ctx && A_ptr && A_col && A_val && U_ptr && U_col && U_val && nnz_out && C_ptr && C_col && C_val,
                        "NULL argument");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"A_val", A_val}, {"U_val", U_val}});
         cudaStream_t s = ctx->stream;
         Csr A, U;
         A.n_rows = A.n_cols = n;
@@ -1451,6 +1490,7 @@ hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *h, int tau, const doubl
         HSIM_CHECK_ARG(tau >= 0 && tau + 1 < h->T, "level has no sparse factorisation");
         HSIM_CHECK_ARG(kk >= 1 && ldb >= kk, "bad sizes");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_val", M_val}, {"B", B}});
         cudaStream_t s = ctx->stream;
         LevelData &L = h->lev[tau];
         DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(tau == 0 ? (size_t)L.n : (size_t)L.dpat.nnz);
@@ -1474,6 +1514,7 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *h, int tau, const d
         HSIM_CHECK_ARG(tau >= 0 && tau + 1 < h->T, "level has no sparse factorisation");
         HSIM_CHECK_ARG(kk >= 1 && ldb >= kk, "bad sizes");
         DeviceGuard dg(ctx->device);
+        check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_val", M_val}, {"B", B}});
         cudaStream_t s = ctx->stream;
         LevelData &L = h->lev[tau];
         DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(tau == 0 ? (size_t)L.n : (size_t)L.dpat.nnz);
