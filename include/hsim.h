@@ -143,6 +143,14 @@ uint64_t hsim_kernel_launches(void);
  * V_host (n x 3 positions) or L2_host (n_tris x 3 squared edge lengths, L2[t*3+k]
  * = edge opposite corner k of triangle t, for intrinsic meshes) must be
  * given; F_host is n_tris x 3 vertex indices.  Result uploaded to the device.
+ * opts->boundary = HSIM_BOUNDARY_DIRICHLET builds the hierarchy over the
+ * interior vertices (see the enum).  The host work uses up to
+ * HSIM_HOST_THREADS threads (default: the hardware concurrency); the result
+ * does not depend on the thread count.
+ * Errors (HSIM_E_INVALID_ARG): vertex index out of range, a degenerate or
+ * non-finite edge, a non-manifold edge, start_vertex out of range (or on a
+ * Dirichlet boundary), q larger than the coarsest level, more than 8 levels,
+ * a connected component without any coarse vertex.
  * ------------------------------------------------------------------------ */
 hsim_status hsim_build_hierarchy(hsim_ctx *ctx, int n_verts, int n_tris, const double *V_host,
                                  const int32_t *F_host, const double *L2_host, int p,
