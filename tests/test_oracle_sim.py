@@ -287,3 +287,19 @@ def test_hierarchy_cuts_finest_level_iterations(mesh_name):
     s = sim.plain_sim(mesh, p, 1e-2, h.shifts[0], rc)
     assert h.iters[0] == 1
     assert s.iters >= 5 * h.iters[0]
+
+
+@pytest.mark.parametrize("which", ["torus", "icosphere"])
+def test_against_arpack_shift_invert(which):
+    """Beyond dense sizes: the oracle's HSIM against SciPy's ARPACK in
+    shift-invert mode (an independent Lanczos code) on ~10^4 vertices."""
+    import scipy.sparse.linalg as spla
+    mesh = synth.bumpy_torus(120, 100, 6) if which == "torus" else synth.displaced_icosphere(5, 4)
+    p = 40
+    S = assembly.stiffness(mesh)
+    M = assembly.lumped_mass(mesh)
+    r = sim.hsim(mesh, p, 2, 1e-10, 11)
+    lam = np.sort(spla.eigsh(S.tocsc(), k=p + 2, M=sp.diags(M).tocsc(), sigma=-1.0, which="LM",
+                             tol=1e-13, return_eigenvectors=False))
+    np.testing.assert_allclose(r.lam[1:], lam[1:p], rtol=1e-10)
+    assert abs(r.lam[0]) < 1e-10 * r.lam[-1]
