@@ -160,8 +160,10 @@ std::vector<int> farthest_point_order(const MeshGraph &g, int start, int count, 
     // The farthest candidate is kept in a tournament tree over blocks of kB
     // consecutive vertices; a block whose distances changed is rescanned
     // before the next choice (the lowered region of one sample is small and
-    // local, so few blocks change per sample).
-    constexpr int kB = 512;
+    // local, so few blocks change per sample; 64 measured fastest among
+    // 32..512 on the 10^6-vertex torus, whose rows of 1000 vertices put each
+    // lowered row segment in about one block).
+    constexpr int kB = 64;
     const int nb = (n + kB - 1) / kB;
     std::vector<char> dirty(nb, 1);
     std::vector<int> dirty_list(nb);
