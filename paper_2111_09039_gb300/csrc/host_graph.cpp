@@ -24,25 +24,29 @@ MeshGraph build_mesh_graph(int n, int m, const double *V, const int *F, const do
     g.n = n;
     g.m = m;
     g.l2.resize((size_t)m * 3);
-    for (int t = 0; t < m; ++t) {
-        for (int k = 0; k < 3; ++k) {
-            int v = F[3 * t + k];
-            HSIM_CHECK_ARG(v >= 0 && v < n, "triangle index out of range");
-        }
-        for (int k = 0; k < 3; ++k) {
-            double l2;
-            if (V) {
-                const double *a = V + 3 * (size_t)F[3 * t + (k + 1) % 3];
-                const double *b = V + 3 * (size_t)F[3 * t + (k + 2) % 3];
-                double e0 = b[0] - a[0], e1 = b[1] - a[1], e2 = b[2] - a[2];
-                l2 = e0 * e0 + e1 * e1 + e2 * e2;
-            } else {
-                l2 = L2[3 * (size_t)t + k];
+    // per triangle, in parallel; an error names the first bad triangle (the
+    // first failing chunk's first failure)
+    parallel_chunks(m, 16384, [&](int, int64_t t0, int64_t t1) {
+        for (int64_t t = t0; t < t1; ++t) {
+            for (int k = 0; k < 3; ++k) {
+                int v = F[3 * t + k];
+                HSIM_CHECK_ARG(v >= 0 && v < n, "triangle index out of range");
             }
-            HSIM_CHECK_ARG(l2 > 0.0 && std::isfinite(l2), "degenerate or non-finite edge");
-            g.l2[3 * (size_t)t + k] = l2;
+            for (int k = 0; k < 3; ++k) {
+                double l2;
+                if (V) {
+                    const double *a = V + 3 * (size_t)F[3 * t + (k + 1) % 3];
+                    const double *b = V + 3 * (size_t)F[3 * t + (k + 2) % 3];
+                    double e0 = b[0] - a[0], e1 = b[1] - a[1], e2 = b[2] - a[2];
+                    l2 = e0 * e0 + e1 * e1 + e2 * e2;
+                } else {
+                    l2 = L2[3 * (size_t)t + k];
+                }
+                HSIM_CHECK_ARG(l2 > 0.0 && std::isfinite(l2), "degenerate or non-finite edge");
+                g.l2[3 * (size_t)t + k] = l2;
+            }
         }
-    }
+    });
     // area: plain sequential sum of the Heron areas
     double area = 0.0;
     for (int t = 0; t < m; ++t) {
