@@ -341,3 +341,31 @@ def test_errors_from_worker_threads_reach_the_caller(hs):
     # and the library keeps working afterwards
     sizes, order, U = hs.check_hierarchy(mesh.F, L2=mesh.L2, p=20, levels=2, start_vertex=0)
     assert sizes == [128 * 128, 1000]
+
+
+def test_hierarchy_independent_of_host_threads(repo_root):
+    # the same hierarchy (sizes, sampling order, prolongations, level-0
+    # pattern) with 1, 3 and the default number of host threads; the thread
+    # count is read once per process, so each run is a fresh interpreter
+    import hashlib
+    import subprocess
+    import sys
+    code = (
+        "import sys, hashlib, numpy as np; sys.path.insert(0, %r)\n"
+        "import synth, paper_2111_09039_gb300 as hs\n"
+        "m = synth.bumpy_torus(200, 150, 5)\n"
+        "sz, order, U, dofs, (p0, c0, s0) = hs.check_hierarchy(m.F, V=m.V, p=60, levels=3, start_vertex=9,"
+        " return_dofs=True, return_level0=True)\n"
+        "h = hashlib.sha256(np.array(sz).tobytes() + order.tobytes() + p0.tobytes() + c0.tobytes())\n"
+        "for (r, c, rp, cl, vl) in U: h.update(rp.tobytes() + cl.tobytes() + vl.tobytes())\n"
+        "print(h.hexdigest())\n" % repo_root)
+    out = []
+    for t in ("1", "3", ""):
+        env = dict(os.environ)
+        env.pop("HSIM_HOST_THREADS", None)
+        if t:
+            env["HSIM_HOST_THREADS"] = t
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        assert r.returncode == 0, r.stderr
+        out.append(r.stdout.strip())
+    assert out[0] == out[1] == out[2]
