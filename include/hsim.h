@@ -90,6 +90,16 @@ typedef struct {
                             stops decreasing), 1 = always, -1 = never */
     int boundary;        /* HSIM_BOUNDARY_NATURAL (default) or _DIRICHLET; read by
                             hsim_build_hierarchy, fixed for the hierarchy */
+    int plain_sim;       /* 1: plain subspace iteration (Alg. 1 alone, the paper's
+                            comparison without a hierarchy).  Read by
+                            hsim_build_hierarchy (a single sparse level, no
+                            sampling or prolongation); hsim_solve then starts from
+                            the initialisation heuristic of Sec. 3.2 (diag(M),
+                            unit vectors at the q - 2 smallest k_ii/m_ii, one
+                            random column, hsim_random_column(seed)) with the
+                            shift sim_shift.  FP64 only. */
+    double sim_shift;    /* plain_sim: the shift mu of Alg. 1 */
+    uint64_t seed;       /* plain_sim: seed of the random column */
 } hsim_options;
 
 /* Per-solve report (host struct, optional). */
@@ -407,6 +417,12 @@ hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, c
  * Errors: HSIM_E_INVALID_ARG for a bad mesh or arguments (as
  * hsim_build_hierarchy, and when a connected component of the mesh holds no
  * coarse vertex); nothing is written then. */
+/* The random column of plain SIM's initial basis (host): entry i is
+ * 2 u_i - 1 with u_i the top 53 bits of the i-th SplitMix64 output (Steele,
+ * Lea and Flood, 2014) from state `seed`, times 2^-53, for the level-0
+ * unknown i (natural order).  Needs no GPU. */
+void hsim_random_column(int n, uint64_t seed, double *out_host);
+
 hsim_status hsim_check_hierarchy(int n_verts, int n_tris, const double *V_host, const int32_t *F_host,
                                  const double *L2_host, int p, const hsim_options *opts, int *levels,
                                  int *sizes, int64_t *U_nnz, int64_t *nnz0, int32_t *dofs,

@@ -219,6 +219,26 @@ def initial_basis(S, M_diag, q, random_column):
     return X
 
 
+def splitmix_column(n, seed):
+    """The random column used with plain SIM: entry i is 2 u_i - 1 with u_i
+    the top 53 bits of the i-th output of SplitMix64 (Steele, Lea and Flood,
+    2014) started from state `seed`, scaled by 2^-53.  Written from the
+    published generator: state += 0x9E3779B97F4A7C15, then
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27;
+    z *= 0x94D049BB133111EB; z ^= z >> 31 (all mod 2^64)."""
+    mask = (1 << 64) - 1
+    out = np.empty(n)
+    state = seed & mask
+    for i in range(n):
+        state = (state + 0x9E3779B97F4A7C15) & mask
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        z ^= z >> 31
+        out[i] = 2.0 * ((z >> 11) * 2.0 ** -53) - 1.0
+    return out
+
+
 def plain_sim(mesh, p, eps, mu, random_column, max_iters=100):
     """Alg. 1 without a hierarchy on the mesh's S, M from the heuristic
     initial basis, with shift mu; returns a SimResult (p pairs)."""

@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
                 ("max_iters", ctypes.c_int), ("inv_iters", ctypes.c_int),
                 ("lock_factor", ctypes.c_double), ("precision", ctypes.c_int),
                 ("start_vertex", ctypes.c_int), ("leaf_size", ctypes.c_int), ("q", ctypes.c_int),
-                ("refine", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("boundary", ctypes.c_int), ("plain_sim", ctypes.c_int),
+                ("sim_shift", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class Info(ctypes.Structure):
@@ -100,6 +101,7 @@ _SIGS = {
     "hsim_check_inverted": (I, [I, P, P, P, I, I, P, P, P, P]),
     "hsim_check_hierarchy": (I, [I, I, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]),
     "hsim_hier_dofs": (I, [P, P]),
+    "hsim_random_column": (None, [I, ctypes.c_uint64, P]),
     "hsim_ritz_noalloc": (I, [P, I, P, P, P, P, P]),
 }
 

@@ -60,6 +60,10 @@ HostHierarchy host_levels(int n, int m, const double *V, const int *F, const dou
                           int start_vertex, double sigma, int q, bool dirichlet);
 void host_samples(HostHierarchy &h, int start_vertex, double sigma);
 
+// out[i] = 2 u_i - 1, u_i = (i-th SplitMix64 output from state seed) >> 11
+// times 2^-53: the random column of plain SIM's initial basis.
+void random_column(int n, uint64_t seed, double *out);
+
 // ---- sparse pattern algebra -------------------------------------------
 Csr mesh_pattern(const MeshGraph &g);                 // edges + diagonal, sorted
 Csr transpose_pattern(const Csr &A);                  // pattern (and values if present)

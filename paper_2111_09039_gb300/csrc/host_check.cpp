@@ -322,8 +322,9 @@ extern "C" hsim_status hsim_check_hierarchy(int n, int m, const double *V, const
         const int q = o.q > 0 ? o.q : std::max((int)std::ceil(1.5 * p), p + 8);
         HSIM_CHECK_ARG(o.boundary == HSIM_BOUNDARY_NATURAL || o.boundary == HSIM_BOUNDARY_DIRICHLET,
                        "unknown boundary condition");
-        HostHierarchy h = build_host_hierarchy(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, q,
-                                               o.boundary == HSIM_BOUNDARY_DIRICHLET);
+        HSIM_CHECK_ARG(o.plain_sim == 0 || o.plain_sim == 1, "plain_sim must be 0 or 1");
+        HostHierarchy h = build_host_hierarchy(n, m, V, F, L2, p, o.plain_sim ? 1 : o.levels, o.start_vertex, o.sigma,
+                                               q, o.boundary == HSIM_BOUNDARY_DIRICHLET);
         const int T = (int)h.sizes.size();
         *levels = T;
         for (int t = 0; t < T; ++t) sizes[t] = h.sizes[t];

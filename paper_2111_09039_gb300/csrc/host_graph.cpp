@@ -433,6 +433,20 @@ Csr prolongation(const MeshGraph &g, const std::vector<int> &order, int nf, int 
     return U;
 }
 
+void random_column(int n, uint64_t seed, double *out) {
+    // SplitMix64 (Steele, Lea and Flood, 2014): state += gamma, then two
+    // xor-shift-multiply rounds and a final xor-shift; output i uses state
+    // seed + (i + 1) gamma, so entries can be produced in any order
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    for (int i = 0; i < n; ++i) {
+        uint64_t z = seed + (uint64_t)(i + 1) * gamma;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        out[i] = 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+    }
+}
+
 HostHierarchy host_levels(int n, int m, const double *V, const int *F, const double *L2, int p, int levels,
                           int start_vertex, double sigma, int q, bool dirichlet) {
     HSIM_CHECK_ARG(p >= 1, "p must be >= 1");

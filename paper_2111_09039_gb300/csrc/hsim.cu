@@ -516,6 +516,55 @@ void ritz_step(hsim_ctx *ctx, hsim_hier *H, int q, const double *Sbar, const dou
 // product (0.99 TFLOP/s, 79 % of the FP64 rate).
 constexpr bool kSpmmDf = false;
 
+// Plain SIM's initial basis (Sec. 3.2, initialisation heuristic) in the
+// level-0 internal order: column 0 = diag(M), columns 1..q-2 = unit vectors at
+// the q - 2 smallest k_ii / m_ii (ascending, the lower vertex first on ties),
+// column q - 1 = random_column(seed) (natural order, then permuted).
+// Expects H->Md0int filled.
+void initial_basis(hsim_ctx *ctx, hsim_hier *H, int q, uint64_t seed, const double *S_val, const double *M_diag,
+                   double *Phi) {
+    cudaStream_t s = ctx->stream;
+    LevelData &L = H->lev[0];
+    const int n = L.n;
+    const Csr &A = L.pat_nat;  // S_val follows this pattern
+    std::vector<int64_t> dpos(n);
+    for (int i = 0; i < n; ++i) {
+        auto b = A.col.begin() + A.ptr[i], e = A.col.begin() + A.ptr[i + 1];
+        auto it = std::lower_bound(b, e, i);
+        if (it == e || *it != i) fail(HSIM_E_INTERNAL, "level-0 pattern without a diagonal entry");
+        dpos[i] = it - A.col.begin();
+    }
+    DevBuf<int64_t> d_dpos;
+    d_dpos.upload(dpos, s);
+    DevBuf<double> d_sdiag((size_t)n);
+    k::gather_values(s, n, d_dpos.p, S_val, d_sdiag.p);
+    std::vector<double> sd(n), md(n);
+    HSIM_CUDA(cudaMemcpyAsync(sd.data(), d_sdiag.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaMemcpyAsync(md.data(), M_diag, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HSIM_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> ratio(n);
+    for (int i = 0; i < n; ++i) ratio[i] = sd[i] / md[i];
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    const int nu = q - 2;
+    std::partial_sort(idx.begin(), idx.begin() + nu, idx.end(),
+                      [&](int a, int b) { return ratio[a] < ratio[b] || (ratio[a] == ratio[b] && a < b); });
+    HSIM_CUDA(cudaMemsetAsync(Phi, 0, (size_t)n * q * sizeof(double), s));
+    k::copy_matrix(s, n, 1, H->Md0int.p, 1, Phi, q);
+    std::vector<double> rc(n), rci(n);
+    random_column(n, seed, rc.data());
+    for (int pos = 0; pos < n; ++pos) rci[pos] = rc[L.fs.perm[pos]];
+    DevBuf<double> d_rc;
+    d_rc.upload(rci, s);
+    k::copy_matrix(s, n, 1, d_rc.p, 1, Phi + (q - 1), q);
+    std::vector<double> ones(nu, 1.0);
+    for (int c = 0; c < nu; ++c) {
+        const int pos = L.fs.iperm[idx[c]];
+        HSIM_CUDA(cudaMemcpyAsync(Phi + (size_t)pos * q + 1 + c, &ones[c], sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    HSIM_CUDA(cudaStreamSynchronize(s));  // before the host and scratch buffers go
+}
+
 void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M_diag, int p, double tol,
                const hsim_options &o, double *evals, double *evecs, hsim_info *info) {
     cudaStream_t s = ctx->stream;
@@ -533,6 +582,10 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     const int q = subspace_q(p, o);
     HSIM_CHECK_ARG(q >= p && q <= H->sizes[T - 1], "subspace size q exceeds the coarsest level");
     inf.q = q;
+    // plain SIM (a hierarchy built with plain_sim): Alg. 1 on the only level
+    // from the initialisation heuristic, FP64
+    const bool plain = H->opts.plain_sim != 0;
+    HSIM_CHECK_ARG(!plain || o.precision == HSIM_FP64, "plain SIM runs in FP64 only");
     LevelData &L0 = H->lev[0];
     const int n0 = L0.n;
     // level-0 values in internal order
@@ -572,27 +625,29 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     // coarsest level: dense generalised eigenproblem (Alg. 3)
     LevelData &Lc = H->lev[T - 1];
     const int nc = Lc.n;
-    H->Sbar.reserve((size_t)nc * nc);
-    H->Mbar.reserve((size_t)nc * nc);
-    if (T == 1) {
-        k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->S0int.p, H->Sbar.p);
-        k::densify_diag(s, nc, M_diag, H->Mbar.p);
-    } else {
-        k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Sv[T - 1].p, H->Sbar.p);
-        k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Mv[T - 1].p, H->Mbar.p);
-    }
-    H->coarseX.reserve((size_t)nc * nc);
-    H->coarseLam.reserve(nc);
-    int sweeps = 0;
-    ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps, q,
-              o.precision == HSIM_MIXED);
-    inf.coarse_sweeps = sweeps;
-    inf.ms_coarse = tm.stop();
     std::vector<double> lam_h(q);
-    HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->coarseLam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
-    HSIM_CUDA(cudaStreamSynchronize(s));
+    int sweeps = 0;
+    if (!plain) {
+        H->Sbar.reserve((size_t)nc * nc);
+        H->Mbar.reserve((size_t)nc * nc);
+        if (T == 1) {
+            k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->S0int.p, H->Sbar.p);
+            k::densify_diag(s, nc, M_diag, H->Mbar.p);
+        } else {
+            k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Sv[T - 1].p, H->Sbar.p);
+            k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Mv[T - 1].p, H->Mbar.p);
+        }
+        H->coarseX.reserve((size_t)nc * nc);
+        H->coarseLam.reserve(nc);
+        ritz_step(ctx, H, nc, H->Sbar.p, H->Mbar.p, H->coarseLam.p, H->coarseX.p, nc, &sweeps, q,
+                  o.precision == HSIM_MIXED);
+        inf.coarse_sweeps = sweeps;
+        inf.ms_coarse = tm.stop();
+        HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->coarseLam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
+        HSIM_CUDA(cudaStreamSynchronize(s));
+    }
     H->signs.reserve(std::max(p, 1));
-    if (T == 1) {
+    if (T == 1 && !plain) {
         HSIM_CUDA(cudaMemcpyAsync(evals, H->coarseLam.p, p * sizeof(double), cudaMemcpyDeviceToDevice, s));
         k::output_evecs(s, nc, p, nullptr, H->coarseX.p, nc, evecs, H->signs.p);
         HSIM_CUDA(cudaStreamSynchronize(s));
@@ -615,20 +670,24 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     const double *Xc = H->coarseX.p;
     int ldxc = nc;
     std::vector<double> rs(3 * (size_t)q), res(q);
-    for (int tau = T - 2; tau >= 0; --tau) {
+    for (int tau = plain ? 0 : T - 2; tau >= 0; --tau) {
         LevelData &L = H->lev[tau];
-        ProlongData &P = H->pro[tau];
         const int n = L.n;
-        // prolongation of the basis (Alg. 3)
         Timer tp(s);
-        k::spmm(s, n, P.dU.ptr.p, P.dU.col.p, P.dUval.p, q, Xc, ldxc, H->Phi.p, q);
+        if (plain) {
+            initial_basis(ctx, H, q, o.seed, S_val, M_diag, H->Phi.p);
+        } else {
+            // prolongation of the basis (Alg. 3)
+            ProlongData &P = H->pro[tau];
+            k::spmm(s, n, P.dU.ptr.p, P.dU.col.p, P.dUval.p, q, Xc, ldxc, H->Phi.p, q);
+        }
         inf.ms_prolong += tp.stop();
         // shift (Alg. 3): Lambda_j of the coarser level, j = floor(alpha p); for
         // j = 0 mirrored below zero to -lambda_ref so that S - mu M stays away
-        // from the constant null vector
+        // from the constant null vector.  Plain SIM: the given shift (Alg. 1).
         int j = (int)std::floor(o.alpha * p);
-        double mu = lam_h[j];
-        if (j == 0) {
+        double mu = plain ? o.sim_shift : lam_h[j];
+        if (!plain && j == 0) {
             mu = -lam_h[q - 1];
             for (int i = 0; i < q; ++i)
                 if (lam_h[i] > 1e-8 * lam_h[q - 1]) {
@@ -890,7 +949,10 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     H->opts = o;
     const bool dirichlet = o.boundary == HSIM_BOUNDARY_DIRICHLET;
     const int leaf = o.leaf_size > 0 ? o.leaf_size : 32;
-    HostHierarchy hh = host_levels(n, m, V, F, L2, p, o.levels, o.start_vertex, o.sigma, subspace_q(p, o), dirichlet);
+    // plain SIM: one sparse level (no sampling, no prolongation)
+    const bool plain = o.plain_sim != 0;
+    HostHierarchy hh =
+        host_levels(n, m, V, F, L2, p, plain ? 1 : o.levels, o.start_vertex, o.sigma, subspace_q(p, o), dirichlet);
     H->sizes = hh.sizes;
     const int T = (int)H->sizes.size();
     H->T = T;
@@ -926,9 +988,9 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     // orderings and symbolic analyses
     for (int tau = T - 1; tau >= 0; --tau) {
         LevelData &L = H->lev[tau];
-        L.dense = (tau == T - 1);
+        L.dense = (tau == T - 1) && !plain;
         if (!L.dense) {
-            L.fs = tau == 0 ? fs0.get() : analyse(L.pat_nat, leaf);
+            L.fs = (tau == 0 && fs0.valid()) ? fs0.get() : analyse(L.pat_nat, leaf);
         } else {
             L.fs.n = L.n;
             L.fs.perm.resize(L.n);
@@ -1013,6 +1075,8 @@ hsim_options checked(const hsim_options *o) {
     HSIM_CHECK_ARG(r.refine >= -1 && r.refine <= 1, "refine must be -1, 0 or 1");
     HSIM_CHECK_ARG(r.boundary == HSIM_BOUNDARY_NATURAL || r.boundary == HSIM_BOUNDARY_DIRICHLET,
                    "unknown boundary condition");
+    HSIM_CHECK_ARG(r.plain_sim == 0 || r.plain_sim == 1, "plain_sim must be 0 or 1");
+    HSIM_CHECK_ARG(std::isfinite(r.sim_shift), "sim_shift must be finite");
     return r;
 }
 
@@ -1038,6 +1102,13 @@ void hsim_default_options(hsim_options *o) {
     o->q = 0;
     o->refine = 0;
     o->boundary = HSIM_BOUNDARY_NATURAL;
+    o->plain_sim = 0;
+    o->sim_shift = 0.0;
+    o->seed = 0;
+}
+
+void hsim_random_column(int n, uint64_t seed, double *out) {
+    if (n > 0 && out) random_column(n, seed, out);
 }
 
 const char *hsim_last_error(void) { return g_last_error.c_str(); }

@@ -369,3 +369,22 @@ def test_hierarchy_independent_of_host_threads(repo_root):
         assert r.returncode == 0, r.stderr
         out.append(r.stdout.strip())
     assert out[0] == out[1] == out[2]
+
+
+def test_random_column_matches_the_oracle(hs):
+    # the library's SplitMix64 column (plain SIM's initial basis) and the
+    # oracle's, written separately from the same published generator
+    import ctypes
+    from oracle import sim
+    for n, seed in [(1, 0), (7, 0), (5000, 2 ** 64 - 3), (1234, 987654321)]:
+        out = np.empty(n)
+        hs.lib().hsim_random_column(n, ctypes.c_uint64(seed), out.ctypes.data_as(ctypes.c_void_p))
+        np.testing.assert_array_equal(out, sim.splitmix_column(n, seed))
+
+
+def test_plain_sim_hierarchy_is_one_level(hs):
+    mesh = synth.bumpy_torus(80, 60, 7)
+    sizes, order, U = hs.check_hierarchy(mesh.F, V=mesh.V, p=20, levels=3, start_vertex=5, plain_sim=1)
+    assert sizes == [mesh.n] and len(order) == 0 and U == []
+    with pytest.raises(hs.HsimError):
+        hs.check_hierarchy(mesh.F, V=mesh.V, p=20, plain_sim=2)

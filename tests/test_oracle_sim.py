@@ -303,3 +303,17 @@ def test_against_arpack_shift_invert(which):
                              tol=1e-13, return_eigenvectors=False))
     np.testing.assert_allclose(r.lam[1:], lam[1:p], rtol=1e-10)
     assert abs(r.lam[0]) < 1e-10 * r.lam[-1]
+
+
+def test_splitmix_column_reference_values(repo_root):
+    """The oracle's generator reproduces SplitMix64's reference outputs for
+    state 0 (tests/golden/splitmix64_seed0.txt), mapped to [-1, 1)."""
+    import os
+    path = os.path.join(repo_root, "tests", "golden", "splitmix64_seed0.txt")
+    ref = [int(l, 16) for l in open(path) if l.strip() and not l.startswith("#")]
+    col = sim.splitmix_column(len(ref), 0)
+    want = np.array([2.0 * ((z >> 11) * 2.0 ** -53) - 1.0 for z in ref])
+    np.testing.assert_array_equal(col, want)
+    big = sim.splitmix_column(20000, 12345)
+    assert abs(big.mean()) < 0.02 and abs(big.var() - 1.0 / 3.0) < 0.01
+    assert big.min() >= -1.0 and big.max() < 1.0
