@@ -168,12 +168,18 @@ def main():
                     help="time the batched solve of this many seeded meshes (5k-80k vertices, p = 50) "
                          "against sequential solves instead of the 10^6-vertex workload")
     ap.add_argument("--streams", type=int, default=0, help="worker streams of the batched solve (0 = 8)")
+    ap.add_argument("--compare-sim", action="store_true",
+                    help="time plain SIM (Alg. 1 from the initialisation heuristic) against HSIM on --workload "
+                         "(FP64, both with the shift HSIM takes on the finest level) instead of the benchmark")
     args = ap.parse_args()
     if args.kernel:
         run_kernel(args)
         return
     if args.batch:
         run_batch(args)
+        return
+    if args.compare_sim:
+        run_compare_sim(args)
         return
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -370,6 +376,44 @@ def run_kernel(args):
     print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms, **extra,
                       "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12,
                       "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}), flush=True)
+
+
+def run_compare_sim(args):
+    """HSIM against plain SIM (the paper's SIM column of Table vsAll) on one
+    workload, FP64: HSIM first, then plain SIM with the shift HSIM used on the
+    finest level, so that only the starting subspace differs.  Device time of
+    each solve (CUDA events, after one untimed solve of each)."""
+    import torch
+
+    import paper_2111_09039_gb300 as hs
+    import synth
+    w, mesh, start = synth.make_workload(args.workload)
+    tol = args.tol if args.tol is not None else 1e-2
+    ctx = hs.Context(0)
+    V = torch.as_tensor(mesh.V, device="cuda:0")
+    hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, levels=w.levels, start_vertex=start)
+    S, Md = hs.assemble(ctx, hier, V=V)
+    flat = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, start_vertex=start, plain_sim=1)
+    S1, Md1 = hs.assemble(ctx, flat, V=V)
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        out = fn()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1000.0, out
+
+    t_h, (lam_h, _, info_h) = timed(lambda: hs.solve(ctx, hier, S, Md, w.p, tol, max_iters=args.max_iters))
+    mu = info_h["shift"][0]
+    t_s, (lam_s, _, info_s) = timed(lambda: hs.solve(ctx, flat, S1, Md1, w.p, tol, sim_shift=mu, seed=1,
+                                                     max_iters=args.max_iters))
+    dl = float(((lam_h - lam_s).abs() / lam_h.abs().clamp_min(float(lam_h[1]))).max())
+    print(json.dumps({"mode": "compare_sim", "workload": args.workload, "vertices": mesh.n, "p": w.p, "tol": tol,
+                      "hsim_s": t_h, "hsim_iters": info_h["iters"], "sim_s": t_s, "sim_iters": info_s["iters"][0],
+                      "speedup_hsim_vs_sim": t_s / t_h, "shift": mu, "max_rel_eigenvalue_diff": dl,
+                      "dtype": "f64", "data": "synthetic"}), flush=True)
 
 
 def run_batch(args):
