@@ -423,6 +423,16 @@ hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, c
  * unknown i (natural order).  Needs no GPU. */
 void hsim_random_column(int n, uint64_t seed, double *out_host);
 
+/* Host part of plain SIM's initial basis, as hsim_solve builds it for a
+ * level of n unknowns whose elimination order is perm (perm[pos] = natural
+ * index): unit_pos[c] (q - 2 entries) = row, in that order, of the unit
+ * vector of column 1 + c (the q - 2 smallest sdiag[i]/mdiag[i], ascending,
+ * the lower natural index first on ties); rand_int[pos] (n entries) =
+ * hsim_random_column(seed) at natural index perm[pos].  Column 0 is
+ * mdiag[perm[pos]].  Host arrays; needs no GPU; the solver never calls it. */
+hsim_status hsim_check_plain_basis(int n, const double *sdiag, const double *mdiag, const int32_t *perm,
+                                   int q, uint64_t seed, int32_t *unit_pos, double *rand_int);
+
 hsim_status hsim_check_hierarchy(int n_verts, int n_tris, const double *V_host, const int32_t *F_host,
                                  const double *L2_host, int p, const hsim_options *opts, int *levels,
                                  int *sizes, int64_t *U_nnz, int64_t *nnz0, int32_t *dofs,

@@ -102,6 +102,7 @@ _SIGS = {
     "hsim_check_hierarchy": (I, [I, I, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]),
     "hsim_hier_dofs": (I, [P, P]),
     "hsim_random_column": (None, [I, ctypes.c_uint64, P]),
+    "hsim_check_plain_basis": (I, [I, P, P, P, I, ctypes.c_uint64, P, P]),
     "hsim_ritz_noalloc": (I, [P, I, P, P, P, P, P]),
 }
 

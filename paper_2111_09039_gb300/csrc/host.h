@@ -64,6 +64,15 @@ void host_samples(HostHierarchy &h, int start_vertex, double sigma);
 // times 2^-53: the random column of plain SIM's initial basis.
 void random_column(int n, uint64_t seed, double *out);
 
+// Host part of plain SIM's initial basis (Sec. 3.2, initialisation
+// heuristic) for a level whose elimination order is perm (perm[pos] =
+// natural index, iperm its inverse): unit_pos[c] = internal row of the unit
+// vector of column 1 + c (the q - 2 smallest sdiag/mdiag, ascending, the
+// lower natural index first on ties); rand_int[pos] = random_column(seed) at
+// natural index perm[pos].
+void plain_basis(int n, const double *sdiag, const double *mdiag, const int *perm, const int *iperm, int q,
+                 uint64_t seed, std::vector<int> *unit_pos, std::vector<double> *rand_int);
+
 // ---- sparse pattern algebra -------------------------------------------
 Csr mesh_pattern(const MeshGraph &g);                 // edges + diagonal, sorted
 Csr transpose_pattern(const Csr &A);                  // pattern (and values if present)

@@ -359,3 +359,23 @@ extern "C" hsim_status hsim_check_hierarchy(int n, int m, const double *V, const
         return caught();
     }
 }
+
+extern "C" hsim_status hsim_check_plain_basis(int n, const double *sdiag, const double *mdiag, const int32_t *perm,
+                                              int q, uint64_t seed, int32_t *unit_pos, double *rand_int) {
+    try {
+        HSIM_CHECK_ARG(sdiag && mdiag && perm && unit_pos && rand_int, "NULL argument");
+        std::vector<int> p(perm, perm + n), ip(n, -1);
+        for (int i = 0; i < n; ++i) {
+            HSIM_CHECK_ARG(p[i] >= 0 && p[i] < n && ip[p[i]] < 0, "perm is not a permutation");
+            ip[p[i]] = i;
+        }
+        std::vector<int> up;
+        std::vector<double> rc;
+        plain_basis(n, sdiag, mdiag, p.data(), ip.data(), q, seed, &up, &rc);
+        std::memcpy(unit_pos, up.data(), up.size() * sizeof(int32_t));
+        std::memcpy(rand_int, rc.data(), rc.size() * sizeof(double));
+        return HSIM_OK;
+    } catch (...) {
+        return caught();
+    }
+}

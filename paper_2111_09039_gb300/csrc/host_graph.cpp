@@ -447,6 +447,24 @@ void random_column(int n, uint64_t seed, double *out) {
     }
 }
 
+void plain_basis(int n, const double *sdiag, const double *mdiag, const int *perm, const int *iperm, int q,
+                 uint64_t seed, std::vector<int> *unit_pos, std::vector<double> *rand_int) {
+    HSIM_CHECK_ARG(n >= 1 && q >= 2 && q <= n, "plain SIM needs 2 <= q <= n");
+    std::vector<double> ratio(n);
+    for (int i = 0; i < n; ++i) ratio[i] = sdiag[i] / mdiag[i];
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    const int nu = q - 2;
+    std::partial_sort(idx.begin(), idx.begin() + nu, idx.end(),
+                      [&](int a, int b) { return ratio[a] < ratio[b] || (ratio[a] == ratio[b] && a < b); });
+    unit_pos->resize(nu);
+    for (int c = 0; c < nu; ++c) (*unit_pos)[c] = iperm[idx[c]];
+    std::vector<double> rc(n);
+    random_column(n, seed, rc.data());
+    rand_int->resize(n);
+    for (int pos = 0; pos < n; ++pos) (*rand_int)[pos] = rc[perm[pos]];
+}
+
 HostHierarchy host_levels(int n, int m, const double *V, const int *F, const double *L2, int p, int levels,
                           int start_vertex, double sigma, int q, bool dirichlet) {
     HSIM_CHECK_ARG(p >= 1, "p must be >= 1");

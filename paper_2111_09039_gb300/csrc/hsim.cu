@@ -542,26 +542,18 @@ void initial_basis(hsim_ctx *ctx, hsim_hier *H, int q, uint64_t seed, const doub
     HSIM_CUDA(cudaMemcpyAsync(sd.data(), d_sdiag.p, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaMemcpyAsync(md.data(), M_diag, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     HSIM_CUDA(cudaStreamSynchronize(s));
-    std::vector<double> ratio(n);
-    for (int i = 0; i < n; ++i) ratio[i] = sd[i] / md[i];
-    std::vector<int> idx(n);
-    for (int i = 0; i < n; ++i) idx[i] = i;
-    const int nu = q - 2;
-    std::partial_sort(idx.begin(), idx.begin() + nu, idx.end(),
-                      [&](int a, int b) { return ratio[a] < ratio[b] || (ratio[a] == ratio[b] && a < b); });
+    std::vector<int> unit_pos;
+    std::vector<double> rci;
+    plain_basis(n, sd.data(), md.data(), L.fs.perm.data(), L.fs.iperm.data(), q, seed, &unit_pos, &rci);
     HSIM_CUDA(cudaMemsetAsync(Phi, 0, (size_t)n * q * sizeof(double), s));
     k::copy_matrix(s, n, 1, H->Md0int.p, 1, Phi, q);
-    std::vector<double> rc(n), rci(n);
-    random_column(n, seed, rc.data());
-    for (int pos = 0; pos < n; ++pos) rci[pos] = rc[L.fs.perm[pos]];
     DevBuf<double> d_rc;
     d_rc.upload(rci, s);
     k::copy_matrix(s, n, 1, d_rc.p, 1, Phi + (q - 1), q);
-    std::vector<double> ones(nu, 1.0);
-    for (int c = 0; c < nu; ++c) {
-        const int pos = L.fs.iperm[idx[c]];
-        HSIM_CUDA(cudaMemcpyAsync(Phi + (size_t)pos * q + 1 + c, &ones[c], sizeof(double), cudaMemcpyHostToDevice, s));
-    }
+    std::vector<double> ones(unit_pos.size(), 1.0);
+    for (size_t c = 0; c < unit_pos.size(); ++c)
+        HSIM_CUDA(cudaMemcpyAsync(Phi + (size_t)unit_pos[c] * q + 1 + c, &ones[c], sizeof(double),
+                                  cudaMemcpyHostToDevice, s));
     HSIM_CUDA(cudaStreamSynchronize(s));  // before the host and scratch buffers go
 }
 

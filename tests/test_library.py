@@ -388,3 +388,30 @@ def test_plain_sim_hierarchy_is_one_level(hs):
     assert sizes == [mesh.n] and len(order) == 0 and U == []
     with pytest.raises(hs.HsimError):
         hs.check_hierarchy(mesh.F, V=mesh.V, p=20, plain_sim=2)
+
+
+@pytest.mark.parametrize("order_seed", [8, 32])
+def test_plain_basis_matches_the_oracle(hs, order_seed):
+    # the initial basis plain SIM starts from, assembled from the library's
+    # host part in an elimination order, against the oracle's basis (natural
+    # order) permuted the same way
+    import ctypes
+    from oracle import sim
+    mesh = synth.bumpy_torus(40, 36, 2)
+    S = assembly.stiffness(mesh)
+    M = assembly.lumped_mass(mesh)
+    n, q, seed = mesh.n, 30, 77
+    perm = np.random.default_rng(order_seed).permutation(n).astype(np.int32)   # any elimination order
+    sd = np.ascontiguousarray(S.diagonal())
+    unit = np.empty(q - 2, dtype=np.int32)
+    rnd = np.empty(n)
+    st = hs.lib().hsim_check_plain_basis(n, sd.ctypes.data_as(ctypes.c_void_p), M.ctypes.data_as(ctypes.c_void_p),
+                                         perm.ctypes.data_as(ctypes.c_void_p), q, ctypes.c_uint64(seed),
+                                         unit.ctypes.data_as(ctypes.c_void_p), rnd.ctypes.data_as(ctypes.c_void_p))
+    assert st == 0
+    X = np.zeros((n, q))
+    X[:, 0] = M[perm]
+    X[unit, np.arange(1, q - 1)] = 1.0
+    X[:, q - 1] = rnd
+    ref = sim.initial_basis(S, M, q, sim.splitmix_column(n, seed))
+    np.testing.assert_array_equal(X, ref[perm])
