@@ -1550,7 +1550,7 @@ hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *h, int tau, const doubl
                                double mu, int kk, double *B, int ldb, int *neg) {
     return guard([&] {
         HSIM_CHECK_ARG(ctx && h && S_val && M_val && B, "NULL argument");
-        HSIM_CHECK_ARG(tau >= 0 && tau + 1 < h->T, "level has no sparse factorisation");
+        HSIM_CHECK_ARG(tau >= 0 && tau < h->T && !h->lev[tau].dense, "level has no sparse factorisation");
         HSIM_CHECK_ARG(kk >= 1 && ldb >= kk, "bad sizes");
         DeviceGuard dg(ctx->device);
         check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_val", M_val}, {"B", B}});
@@ -1574,7 +1574,7 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *h, int tau, const d
                                    double mu, int kk, double *B, int ldb, int *neg) {
     return guard([&] {
         HSIM_CHECK_ARG(ctx && h && S_val && M_val && B, "NULL argument");
-        HSIM_CHECK_ARG(tau >= 0 && tau + 1 < h->T, "level has no sparse factorisation");
+        HSIM_CHECK_ARG(tau >= 0 && tau < h->T && !h->lev[tau].dense, "level has no sparse factorisation");
         HSIM_CHECK_ARG(kk >= 1 && ldb >= kk, "bad sizes");
         DeviceGuard dg(ctx->device);
         check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_val", M_val}, {"B", B}});
