@@ -168,6 +168,9 @@ def main():
                     help="time the batched solve of this many seeded meshes (5k-80k vertices, p = 50) "
                          "against sequential solves instead of the 10^6-vertex workload")
     ap.add_argument("--streams", type=int, default=0, help="worker streams of the batched solve (0 = 8)")
+    ap.add_argument("--sweep", default=None, choices=["levels", "sigma", "alpha"],
+                    help="solve --workload for a range of one parameter (the paper's level, support and shift "
+                         "tables) and print iteration counts and times, instead of the benchmark")
     ap.add_argument("--compare-sim", action="store_true",
                     help="time plain SIM (Alg. 1 from the initialisation heuristic) against HSIM on --workload "
                          "(FP64, both with the shift HSIM takes on the finest level) instead of the benchmark")
@@ -180,6 +183,9 @@ def main():
         return
     if args.compare_sim:
         run_compare_sim(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -376,6 +382,45 @@ def run_kernel(args):
     print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms, **extra,
                       "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12,
                       "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}), flush=True)
+
+
+def run_sweep(args):
+    """One JSON line per value of the swept parameter (T in 2..5, sigma in
+    3..11, alpha in 0.05..1/3, as in the paper's level, support and shift
+    tables): hierarchy build time (host wall clock), solve time (CUDA events,
+    after one untimed solve) and iterations per level."""
+    import torch
+
+    import paper_2111_09039_gb300 as hs
+    import synth
+    w, mesh, start = synth.make_workload(args.workload)
+    tol = args.tol if args.tol is not None else w.tol
+    prec = hs.HSIM_FP64 if args.precision == "fp64" else hs.HSIM_MIXED
+    values = {"levels": [2, 3, 4, 5], "sigma": [3.0, 5.0, 7.0, 9.0, 11.0],
+              "alpha": [0.05, 0.1, 0.2, 1.0 / 3.0]}[args.sweep]
+    ctx = hs.Context(0)
+    V = torch.as_tensor(mesh.V, device="cuda:0")
+    for v in values:
+        kw = {"levels": w.levels, "sigma": 7.0, "alpha": 0.1}
+        kw[args.sweep] = v
+        t0 = time.perf_counter()
+        hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, start_vertex=start, precision=prec, levels=kw["levels"],
+                            sigma=kw["sigma"])
+        S, Md = hs.assemble(ctx, hier, V=V)
+        torch.cuda.synchronize()
+        t_h = time.perf_counter() - t0
+        solve = lambda: hs.solve(ctx, hier, S, Md, w.p, tol, precision=prec, alpha=kw["alpha"],
+                                 max_iters=args.max_iters)
+        solve()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        lam, _, info = solve()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "sweep", "parameter": args.sweep, "value": v, "workload": args.workload,
+                          "p": w.p, "tol": tol, "precision": args.precision, "levels": info["sizes"],
+                          "iters": info["iters"], "hier_s": t_h, "solve_s": e0.elapsed_time(e1) / 1000.0,
+                          "max_residual": info["max_residual"]}), flush=True)
 
 
 def run_compare_sim(args):
