@@ -415,3 +415,22 @@ def test_plain_basis_matches_the_oracle(hs, order_seed):
     X[:, q - 1] = rnd
     ref = sim.initial_basis(S, M, q, sim.splitmix_column(n, seed))
     np.testing.assert_array_equal(X, ref[perm])
+
+
+def test_every_status_entry_refuses_null_arguments(hs):
+    # each entry point that returns a status, called with NULL pointers and
+    # zero sizes, returns an error (no crash, no exception across the ABI)
+    # and leaves a message; the void entries accept NULL
+    import ctypes
+    from paper_2111_09039_gb300 import _lib
+    L = hs.lib()
+    for name, (res, args) in _lib._SIGS.items():
+        fn = getattr(L, name)
+        vals = [None if a is ctypes.c_void_p else a(0) for a in args]
+        if res is ctypes.c_int:
+            st = fn(*vals)
+            assert st != 0, name
+            assert L.hsim_last_error(), name
+        elif name in ("hsim_destroy", "hsim_hier_destroy", "hsim_free", "hsim_default_options",
+                      "hsim_random_column"):
+            fn(*vals)
