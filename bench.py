@@ -461,21 +461,43 @@ def run_compare_sim(args):
                       "dtype": "f64", "data": "synthetic"}), flush=True)
 
 
+def batch_shard(sizes, world):
+    """Independent meshes onto ranks: largest first onto the least loaded rank
+    (the lower rank on ties); one ascending index list per rank.  The meshes
+    share nothing, so the ranks exchange only their times."""
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        out[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(o) for o in out]
+
+
 def run_batch(args):
     """Batched solve of `args.batch` seeded meshes (displaced geodesic
     icospheres and bumpy tori, 5k-80k vertices, p = 50, T = 2, tol 1e-5, mixed
     precision) against the same solves one after the other.  Both are timed on
     the host around the calls, with the device synchronised on both sides
     (the batched call spans several streams); inputs resident, workspaces
-    allocated by the warm-up."""
+    allocated by the warm-up.  Under torchrun the meshes are split over the
+    ranks (batch_shard) and the times are the maxima over ranks."""
     import torch
 
     import paper_2111_09039_gb300 as hs
     import synth
     from synth import workloads
 
-    ctx = hs.Context(0)
-    items = synth.batch(count=args.batch)
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    ctx = hs.Context(local)
+    everything = synth.batch(count=args.batch)
+    mine = batch_shard([m.n for m, _ in everything], world)[rank]
+    items = [everything[i] for i in mine]
     p, T, tol = workloads.BATCH_P, workloads.BATCH_LEVELS, args.tol or workloads.BATCH_TOL
     t0 = time.perf_counter()
     hiers = [hs.Hierarchy(ctx, m.F, V=m.V, p=p, levels=T, start_vertex=st, precision=hs.HSIM_MIXED)
@@ -483,7 +505,7 @@ def run_batch(args):
     hier_s = time.perf_counter() - t0
     S, M = [], []
     for (m, _), h in zip(items, hiers):
-        s_, md = hs.assemble(ctx, h, V=torch.as_tensor(m.V, device="cuda:0"))
+        s_, md = hs.assemble(ctx, h, V=torch.as_tensor(m.V, device=dev))
         S.append(s_)
         M.append(md)
     opts = hs.default_options(precision=hs.HSIM_MIXED, levels=T, max_iters=args.max_iters)
@@ -493,10 +515,12 @@ def run_batch(args):
 
     def timed(fn):
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t = time.perf_counter()
         out = fn()
         torch.cuda.synchronize()
-        return time.perf_counter() - t, out
+        return max_over_ranks(time.perf_counter() - t, world, dev), out
 
     seq, bat = [], []
     l0 = hs.kernel_launches()
@@ -509,20 +533,24 @@ def run_batch(args):
             return [hs.solve(ctx, h, S[i], M[i], p, tol, options=opts) for i, h in enumerate(hiers)]
         dt, out_s = timed(one_by_one)
         seq.append(dt)
-    res = max(check_residual(h, S[i], M[i], out_b[i][0], out_b[i][1], ctx) for i, h in enumerate(hiers))
-    dl = max(float(((out_b[i][0] - out_s[i][0]).abs() / out_s[i][0].abs().clamp_min(out_s[i][0][1])).max())
-             for i in range(len(hiers)))
+    res = max([check_residual(h, S[i], M[i], out_b[i][0], out_b[i][1], ctx) for i, h in enumerate(hiers)] + [0.0])
+    dl = max([float(((out_b[i][0] - out_s[i][0]).abs() / out_s[i][0].abs().clamp_min(out_s[i][0][1])).max())
+              for i in range(len(hiers))] + [0.0])
+    res, dl = max_over_ranks(res, world, dev), max_over_ranks(dl, world, dev)
     vb, vs = min(bat), min(seq)
-    line = {"metric": f"s for {len(hiers)} independent meshes ({min(m.n for m, _ in items)}-"
-                      f"{max(m.n for m, _ in items)} vertices), {p} lowest eigenpairs each, resid<={tol:g}",
-            "value": vb, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup),
+    if rank != 0:
+        return
+    line = {"metric": f"s for {len(everything)} independent meshes ({min(m.n for m, _ in everything)}-"
+                      f"{max(m.n for m, _ in everything)} vertices), {p} lowest eigenpairs each, resid<={tol:g}",
+            "value": vb, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": max(1, args.warmup),
+            "scaling": "strong", "meshes_per_rank": [len(x) for x in batch_shard([m.n for m, _ in everything], world)],
             "higher_is_better": False, "mode": "batched", "streams": args.streams or 8,
             "sequential_s": vs, "speedup_batched_vs_sequential": vs / vb,
-            "vertices_total": int(sum(m.n for m, _ in items)), "max_residual_check": res,
+            "vertices_total": int(sum(m.n for m, _ in everything)), "max_residual_check": res,
             "max_rel_eigenvalue_diff_batched_vs_sequential": dl, "hier_build_s": hier_s,
             "gpu_launches": int(round(launches)), "dtype": "bf16+f32+f64", "data": "synthetic",
-            "config": {"workload": f"batch of {len(hiers)} (seed 4)", "p": p, "levels": T, "tol": tol,
-                       "precision": "mixed"},
+            "config": {"workload": f"batch of {len(everything)} (seed 4)", "p": p, "levels": T, "tol": tol,
+                       "precision": "mixed", "parallelism": f"meshes split over {world} rank(s)"},
             "timing": "host clock around the call, device synchronised on both sides"}
     print(json.dumps(line), flush=True)
 

@@ -65,3 +65,20 @@ def test_dist_setup_reads_the_environment(monkeypatch):
     for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
         monkeypatch.delenv(k)
     assert bench.dist_setup() == (1, 0, 0)
+
+
+def test_batch_shard_covers_every_mesh_once_and_balances():
+    import bench
+    import synth
+    sizes = [m.n for m, _ in synth.batch(count=64)]
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.batch_shard(sizes, world)
+        assert len(parts) == world
+        flat = sorted(i for part in parts for i in part)
+        assert flat == list(range(64))
+        loads = [sum(sizes[i] for i in part) for part in parts]
+        # greedy largest-first: no rank carries more than the mean plus the largest mesh
+        assert max(loads) <= sum(sizes) / world + max(sizes)
+        assert parts == bench.batch_shard(sizes, world)        # deterministic
+    parts = bench.batch_shard([5, 3], 4)                       # more ranks than meshes
+    assert parts == [[0], [1], [], []]
