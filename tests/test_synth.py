@@ -48,3 +48,28 @@ def test_batch_recipe_is_seeded_and_in_range():
     for i, (m, _) in enumerate(b1):
         assert 1000 <= m.n <= 7000
         assert ("icosphere" in m.name) == (i % 2 == 0)
+
+
+def test_flat_square_and_bumpy_patch():
+    import numpy as np
+    from synth import meshes
+    sq = meshes.flat_square(8)
+    assert sq.n == 81 and sq.m == 128
+    assert np.all(sq.V[:, 2] == 0.0) and sq.V.min() == 0.0 and sq.V.max() == 1.0
+    # every square split along the same diagonal, counter-clockwise in the plane
+    a, b, c = sq.V[sq.F[:, 0]], sq.V[sq.F[:, 1]], sq.V[sq.F[:, 2]]
+    cross = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
+    np.testing.assert_allclose(cross, 1.0 / 64, rtol=1e-15)
+    p1 = meshes.bumpy_patch(10, 7, 3)
+    p2 = meshes.bumpy_patch(10, 7, 3)
+    assert p1.n == 11 * 8 and p1.m == 2 * 70
+    np.testing.assert_array_equal(p1.V, p2.V)                     # seeded
+    assert not np.array_equal(p1.V, meshes.bumpy_patch(10, 7, 4).V)
+    # the outline stays a rectangle: x is fixed on the left and right sides,
+    # y on the bottom and top (the jitter slides boundary vertices along it)
+    i = np.arange(p1.n) % 11
+    j = np.arange(p1.n) // 11
+    side = (i == 0) | (i == 10)
+    cap = (j == 0) | (j == 7)
+    np.testing.assert_array_equal(p1.V[side, 0], i[side] / 10)
+    np.testing.assert_array_equal(p1.V[cap, 1], j[cap] / 10)
