@@ -132,7 +132,9 @@ def flat_square(N: int = 64) -> Mesh:
 
 def bumpy_patch(nx: int, ny: int, seed: int) -> Mesh:
     """An open, gently curved grid patch over [0, 1] x [0, ny/nx]: per-vertex
-    jitter of up to 0.2 grid steps in the plane and a smooth height field."""
+    jitter of up to 0.2 grid steps in the plane (x kept on the left and right
+    sides, y on the bottom and top, so the outline stays a rectangle) and a
+    smooth height field."""
     rng = np.random.default_rng(seed)
     i, j = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
     x = (i + rng.uniform(-0.2, 0.2, i.shape) * ((i > 0) & (i < nx))) / nx
