@@ -158,10 +158,10 @@ def main():
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "spmm_df", "ritz", "ritz_tc"],
+    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz", "ritz_tc"],
                     help="time one step-level kernel on random data instead of the solve (profiling)")
     ap.add_argument("--mesh-nu", type=int, default=0,
-                    help="--kernel spmm/spmm_df: an nu x nu bumpy torus instead of the workload's mesh")
+                    help="--kernel spmm: an nu x nu bumpy torus instead of the workload's mesh")
     ap.add_argument("--rows", type=int, default=200000)
     ap.add_argument("--cols", type=int, default=750)
     ap.add_argument("--batch", type=int, default=0,
@@ -336,7 +336,7 @@ def run_kernel(args):
     A = torch.randn((n, q), dtype=torch.float64, device="cuda:0", generator=g)
     B = torch.randn((n, q), dtype=torch.float64, device="cuda:0", generator=g)
     P = torch.randn((q, q), dtype=torch.float64, device="cuda:0", generator=g)
-    if args.kernel in ("spmm", "spmm_df"):
+    if args.kernel == "spmm":
         import synth
         if args.mesh_nu > 0:
             mesh = synth.bumpy_torus(args.mesh_nu, args.mesh_nu, 3)
@@ -347,8 +347,7 @@ def run_kernel(args):
         S, Md = hs.assemble(ctx, hier, V=torch.as_tensor(mesh.V, device="cuda:0"))
         rp, cl = hier.pattern()
         A = torch.randn((mesh.n, q), dtype=torch.float64, device="cuda:0", generator=g)
-        df = args.kernel == "spmm_df"
-        fn = lambda: hs.spmm(ctx, rp, cl, S, A, df=df)
+        fn = lambda: hs.spmm(ctx, rp, cl, S, A)
         flops, nbytes = 2.0 * S.numel() * q, 16.0 * mesh.n * q + 12.0 * S.numel()
     elif args.kernel in ("gram", "gram_tc"):
         f = hs.gram if args.kernel == "gram" else hs.gram_tc

@@ -271,17 +271,6 @@ hsim_status hsim_eig_grad(hsim_ctx *ctx, int n, int n_tris, const double *V_dev,
 hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
                       const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
                       int ldx, double *Y_dev, int ldy);
-/* A double-float variant of hsim_spmm: FP64 values and X are carried as
- * pairs of FP32 values (arithmetic on the FP32 pipe): each term carries a few
- * units of 2^-46 |A[r, c] X[c, j]| (FP64: 2^-53), so the result is within
- * about 2^-42 sum_c |A[r, c] X[c, j]| for rows of up to ~20 entries; values
- * of magnitude below 2^-90 keep only FP32 accuracy.  The solve does not use
- * it (on this GPU it measured slower than the FP64 product).  Arguments as
- * hsim_spmm; scratch for the split values is allocated per call. */
-hsim_status hsim_spmm_df(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *row_ptr_dev,
-                         const int32_t *col_dev, const double *val_dev, int k, const double *X_dev,
-                         int ldx, double *Y_dev, int ldy);
-
 /* G = A^T B (k_a x k_b, row-major, ld k_b) for tall A (n x k_a, ld lda) and
  * B (n x k_b, ld ldb): the reduced matrices Psi^T S Psi, Psi^T M Psi of Alg. 1. */
 hsim_status hsim_gram(hsim_ctx *ctx, int n, int k_a, int k_b, const double *A_dev, int lda,
@@ -358,7 +347,15 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *hier, int tau, cons
  * library allocate device memory (a framework that reserves the whole
  * device pool for its own allocator, a latency-bound loop that must not enter
  * the driver's allocator, a host that forbids allocations by plugins).  The
- * paper has no counterpart; it is the same Rayleigh-Ritz solve as hsim_ritz.
+ * paper has no counterpart.  It is the same Rayleigh-Ritz reduction as
+ * hsim_ritz (LDL^T of M_bar = C C^T, standard problem C^-1 S_bar C^-T,
+ * X = C^-T V), but the standard problem is solved by a parallel cyclic FP64
+ * Jacobi instead of the tridiagonal eigensolver: sweeps_out (host, may be
+ * NULL) receives the number of Jacobi sweeps (hsim_ritz reports 0 there).
+ * Eigenvalues agree with hsim_ritz to rounding; eigenvectors up to sign.
+ * Fails with HSIM_E_NOT_SPD if M_bar is not positive definite and with
+ * HSIM_E_NO_CONVERGENCE if the sweeps still rotate after 40 sweeps (outputs
+ * then undefined).
  *
  * Its scratch is one fixed device array inside this library, sized for
  * k <= HSIM_RITZ_NOALLOC_MAX (about 3.2 MB on every device that loads the
@@ -366,8 +363,10 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *hier, int tau, cons
  * HSIM_E_INVALID_ARG.  No cudaMalloc or cudaFree is called.  The caller owns
  * the inputs Sbar_dev, Mbar_dev (k x k row-major, read only) and the outputs
  * evals_dev (k) and X_dev (k x k row-major), all on the current device; work
- * is issued on cuda_stream (a cudaStream_t, NULL = legacy default stream) and
- * the call returns after that stream drained.  The first call on a device
+ * is issued on cuda_stream (a cudaStream_t, NULL = legacy default stream).
+ * The call synchronizes that stream several times (after the factorisation
+ * of M_bar and after every sweep, to read the rotation count) and returns
+ * only after the stream has drained.  The first call on a device
  * (made while it is current) looks up the array's device address, so make
  * it before any stream capture.  All calls share the array: calls that
  * overlap on the GPU (other streams or host threads) race and must be

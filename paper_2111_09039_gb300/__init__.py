@@ -321,8 +321,8 @@ def eigenvalues(ctx: Context, hier: Hierarchy, V, F, p: int, tol: float, options
 
 
 # ---- step-level entry points -------------------------------------------------
-def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None, df: bool = False):
-    """Y = A X (CSR A); df=True: the mixed path's double-float variant (hsim_spmm_df)."""
+def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None):
+    """Y = A X (CSR A, FP64)."""
     torch = _torch()
     _on_device(row_ptr, "row_ptr", ctx.device, torch.int32)
     n_rows = row_ptr.numel() - 1
@@ -331,8 +331,7 @@ def spmm(ctx: Context, row_ptr, col, val, X, n_cols: int | None = None, df: bool
     _rows_on_device(X, "X", ctx.device, n_cols)
     k = X.shape[1]
     Y = torch.empty((n_rows, k), dtype=torch.float64, device=X.device)
-    fn = lib().hsim_spmm_df if df else lib().hsim_spmm
-    check(fn(ctx.handle, n_rows, n_cols if n_cols is not None else X.shape[0], ptr(row_ptr), ptr(col), ptr(val), k,
+    check(lib().hsim_spmm(ctx.handle, n_rows, n_cols if n_cols is not None else X.shape[0], ptr(row_ptr), ptr(col), ptr(val), k,
              ptr(X), X.stride(0), ptr(Y), k))
     return Y
 

@@ -85,7 +85,6 @@ _SIGS = {
     "hsim_eig_grad": (I, [P, I, I, P, P, I, P, P, P, P]),
     "hsim_solve_batched": (I, [P, I, P, P, P, P, D, P, P, P, P, I]),
     "hsim_spmm": (I, [P, I, I, P, P, P, I, P, I, P, I]),
-    "hsim_spmm_df": (I, [P, I, I, P, P, P, I, P, I, P, I]),
     "hsim_gram": (I, [P, I, I, I, P, I, P, I, P]),
     "hsim_gemm_update": (I, [P, I, I, I, P, I, P, I, P, I]),
     "hsim_gram_tc": (I, [P, I, I, I, P, I, P, I, P]),

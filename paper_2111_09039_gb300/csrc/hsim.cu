@@ -184,10 +184,6 @@ struct hsim_hier {
     // inverted-factor solves: 1 / D, the forward result Y, inversion scratch
     DevBuf<double> dinvf, ysol, invs;
     DevBuf<float> dinvf32, ysol32, invs32;
-    // mixed path: S X in double-float arithmetic on level df_level (S values
-    // split into FP32 pairs, X2 the split of X)
-    int df_level = -1;
-    DevBuf<float2> Sdf, X2;
     DevBuf<double> rho;
     DevBuf<unsigned char> oz;  // digit slices of the tensor-core products
 };
@@ -491,11 +487,6 @@ void apply_M(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int l
 }
 void apply_S(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int ldx, double *Y, int ldy) {
     LevelData &L = H->lev[tau];
-    if (tau == H->df_level) {
-        H->X2.reserve((size_t)L.n * k);
-        k::spmm_df(ctx->stream, L.n, L.n, L.dpat.ptr.p, L.dpat.col.p, H->Sdf.p, k, X, ldx, H->X2.p, Y, ldy);
-        return;
-    }
     const double *v = tau == 0 ? H->S0int.p : H->Sv[tau].p;
     k::spmm(ctx->stream, L.n, L.dpat.ptr.p, L.dpat.col.p, v, k, X, ldx, Y, ldy);
 }
@@ -510,11 +501,6 @@ void ritz_step(hsim_ctx *ctx, hsim_hier *H, int q, const double *Sbar, const dou
                      ctx->hflags.data(), m, tc);
     if (rc != 0) fail(HSIM_E_NOT_SPD, "reduced mass matrix is not positive definite (q = " + std::to_string(q) + ")");
 }
-
-// The double-float S X (k_sparse.cu) is not used by the solve: measured at
-// 10^6 vertices and 750 columns it takes 23 ms against 10.6 ms for the FP64
-// product (0.99 TFLOP/s, 79 % of the FP64 rate).
-constexpr bool kSpmmDf = false;
 
 // Plain SIM's initial basis (Sec. 3.2, initialisation heuristic) in the
 // level-0 internal order: column 0 = diag(M), columns 1..q-2 = unit vectors at
@@ -560,12 +546,6 @@ void initial_basis(hsim_ctx *ctx, hsim_hier *H, int q, uint64_t seed, const doub
 void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M_diag, int p, double tol,
                const hsim_options &o, double *evals, double *evecs, hsim_info *info) {
     cudaStream_t s = ctx->stream;
-    // the split S values belong to this solve only (also when it throws)
-    struct DfReset {
-        hsim_hier *H;
-        ~DfReset() { H->df_level = -1; }
-    } df_reset{H};
-    H->df_level = -1;
     Timer tm(s), total(s);
     hsim_info inf{};
     const int T = H->T;
@@ -695,13 +675,6 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         // pairs, (lambda_i - mu) / (lambda_q - mu), changes by about 1 %.
         const bool mixed = o.precision == HSIM_MIXED;
         const int q32 = (q + 3) & ~3;  // FP32 block rows 16-byte aligned (vector atomics)
-        // mixed path: S X of this level in double-float arithmetic (FP32 pipe)
-        H->df_level = -1;
-        if (mixed && kSpmmDf) {
-            H->Sdf.reserve((size_t)L.dpat.nnz);
-            k::split_df_values(s, L.dpat.nnz, tau == 0 ? H->S0int.p : H->Sv[tau].p, H->Sdf.p);
-            H->df_level = tau;
-        }
         if (mixed) {
             double lam_ref = lam_h[q - 1];
             for (int i = 0; i < q; ++i)
@@ -1362,24 +1335,6 @@ hsim_status hsim_spmm(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *ptr,
         DeviceGuard dg(ctx->device);
         check_device_ptrs(ctx->device, {{"row_ptr", ptr}, {"col", col}, {"val", val}, {"X", X}, {"Y", Y}});
         k::spmm(ctx->stream, n_rows, ptr, col, val, k, X, ldx, Y, ldy);
-        HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
-    });
-}
-
-hsim_status hsim_spmm_df(hsim_ctx *ctx, int n_rows, int n_cols, const int32_t *ptr, const int32_t *col,
-                         const double *val, int k, const double *X, int ldx, double *Y, int ldy) {
-    return guard([&] {
-        HSIM_CHECK_ARG(ctx, "NULL context");
-        HSIM_CHECK_ARG(n_rows >= 0 && n_cols >= 0 && k >= 0 && ldx >= k && ldy >= k, "bad sizes");
-        if (n_rows == 0 || k == 0) return;
-        HSIM_CHECK_ARG(ptr && col && X && Y && (val || n_cols == 0), "NULL argument");
-        DeviceGuard dg(ctx->device);
-        check_device_ptrs(ctx->device, {{"row_ptr", ptr}, {"col", col}, {"val", val}, {"X", X}, {"Y", Y}});
-        int nnz = 0;
-        HSIM_CUDA(cudaMemcpy(&nnz, ptr + n_rows, sizeof(int), cudaMemcpyDeviceToHost));
-        DevBuf<float2> v2((size_t)std::max(nnz, 1)), X2((size_t)std::max(n_cols, 1) * k);
-        k::split_df_values(ctx->stream, nnz, val, v2.p);
-        k::spmm_df(ctx->stream, n_rows, n_cols, ptr, col, v2.p, k, X, ldx, X2.p, Y, ldy);
         HSIM_CUDA(cudaStreamSynchronize(ctx->stream));
     });
 }

@@ -698,9 +698,12 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
 // reserves the whole device pool for its own caching allocator (a cudaMalloc
 // from inside would fail or fragment it), a latency-bound loop that must not
 // enter the driver's allocator, or a host that forbids allocations by plugins.
-// For them hsim_ritz_noalloc runs the same Ritz solve as hsim_ritz with all of
-// its scratch taken from one fixed, file-scope device array (about 3.2 MB per
-// device that loads the library, held until the process exits).  Its address
+// For them hsim_ritz_noalloc runs the same Rayleigh-Ritz reduction as
+// hsim_ritz (LDL^T of M_bar = C C^T, then the standard problem
+// C^-1 S_bar C^-T), solved by a parallel cyclic FP64 Jacobi rather than the
+// tridiagonal eigensolver of hsim_ritz, with all of its scratch taken from
+// one fixed, file-scope device array (about 3.2 MB per device that loads the
+// library, held until the process exits).  Its address
 // is looked up once per device with cudaGetSymbolAddress, by the first call
 // made while that device is current; that first call should therefore come
 // before any stream capture.  Every call shares the array: calls whose work
@@ -712,6 +715,7 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
 namespace {
 
 constexpr int kNoAllocMaxK = HSIM_RITZ_NOALLOC_MAX;
+constexpr int kMaxJacobiSweeps = 40;
 constexpr size_t kNoAllocWork = (size_t)6 * kNoAllocMaxK * kNoAllocMaxK + 4 * (size_t)kNoAllocMaxK + 64;
 // byte offsets inside the scratch array
 constexpr size_t kOffWork = 0;
@@ -756,8 +760,12 @@ __global__ void k_noalloc_front(int k, int64_t *i64, int *i32, int *rows) {
     }
 }
 
-// The Ritz solve of ritz(), with the dense front description and the work
-// area supplied by the caller.
+// The Rayleigh-Ritz solve with the dense front description and the work area
+// supplied by the caller: LDL^T of M_bar on the front kernels, the two
+// triangular transforms, then cyclic Jacobi sweeps until a sweep applies no
+// rotation.  Returns 0 on success, 1 if M_bar is not positive definite, 2 if
+// the Jacobi sweeps still rotated after kMaxJacobiSweeps sweeps (the
+// spectrum is then not converged and the vectors not M-orthonormal).
 int ritz_on(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals, double *X,
             int ldx, double *work, const FrontDev &fd, const int *node, int *sweeps, int *flag_dev, int *flag_host) {
     const size_t kk = (size_t)k * k;
@@ -809,7 +817,7 @@ int ritz_on(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mb
     int sw = 0;
     unsigned long long hrot = 1;
     double *pA = A, *pA2 = A2, *pV = V, *pV2 = V2;
-    while (hrot != 0 && sw < 40) {
+    while (hrot != 0 && sw < kMaxJacobiSweeps) {
         HSIM_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
         int kk_ = k, mm = m, ld = k;
         void *args[] = {&kk_, &mm, &pA, &pA2, &pV, &pV2, &cs, &ld, &tol, &abs_tol, &rot};
@@ -824,6 +832,7 @@ int ritz_on(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mb
         ++sw;
     }
     if (sweeps) *sweeps = sw;
+    if (hrot != 0) return 2;
     int *rk = reinterpret_cast<int *>(W);
     k_rank<<<cdiv(k, 128), 128, 0, s>>>(k, pA, k, rk, evals);
     HSIM_LAUNCHED();
@@ -870,7 +879,10 @@ extern "C" hsim_status hsim_ritz_noalloc(void *cuda_stream, int k, const double 
                             flag_host);
         HSIM_CUDA(cudaStreamSynchronize(s));
         if (sweeps_out) *sweeps_out = sw;
-        if (rc != 0) fail(HSIM_E_NOT_SPD, "M_bar is not positive definite");
+        if (rc == 1) fail(HSIM_E_NOT_SPD, "M_bar is not positive definite");
+        if (rc == 2)
+            fail(HSIM_E_NO_CONVERGENCE, "hsim_ritz_noalloc: Jacobi sweeps still rotating after " +
+                                            std::to_string(sw) + " sweeps");
         return HSIM_OK;
     } catch (const Error &e) {
         set_last_error(e.what());

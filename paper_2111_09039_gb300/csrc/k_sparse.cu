@@ -123,84 +123,6 @@ __global__ void k_spmm(int n_rows, const int *__restrict__ ptr, const int *__res
     }
 }
 
-// ---- double-float S X (mixed path) -------------------------------------------
-// FP64 multiply-adds issue at a 64th of the FP32 rate here, so an FP64 S X
-// with hundreds of columns is bound by them (nnz k FMAs).  In this variant
-// every FP64 value v is carried as two FP32 values, hi = v truncated to 24
-// significant bits and lo = the next 24 bits (v = hi + lo to 2^-47 |v|), both
-// cut from the FP64 bit pattern with integer operations.  A product s x is
-// formed as p = s_hi x_hi plus its exact rounding error fma(s_hi, x_hi, -p)
-// plus the cross terms s_hi x_lo + s_lo x_hi, and accumulated in (hi, lo)
-// with Knuth's two-sum (the double-float arithmetic of Dekker, 1971); each
-// output is converted back to FP64 once.  Each term carries a few units of
-// 2^-46 |s x| (FP64: 2^-53), the sum about 2^-42 sum |s x| for the ~7-25
-// entries of a mesh row.
-
-// v -> (hi, lo); values outside the FP32 exponent range of hi and lo (|v|
-// above 2^127 or below 2^-97, and zero) go through FP64 conversions
-__device__ __forceinline__ float2 split_df(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e < 1023 - 97 || e > 1023 + 127) {
-        const float h = (float)v;
-        return make_float2(h, (float)(v - (double)h));
-    }
-    const unsigned long long m = b & 0xfffffffffffffull;
-    const float hi = __int_as_float((int)(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29)));
-    const unsigned rem = (unsigned)(m & 0x1fffffffu);  // value rem 2^(e - 1075)
-    float lo = 0.f;
-    if (rem != 0u) {
-        const int top = 31 - __clz((int)rem);  // leading bit, 0..28
-        const int sh = top - 23;
-        const unsigned mant = sh >= 0 ? (rem >> sh) : (rem << (-sh));
-        const int el = sh + e - 925;  // biased FP32 exponent of mant 2^(sh + e - 1075)
-        if (el > 0) lo = __int_as_float((int)(sign | ((unsigned)el << 23) | (mant & 0x7fffffu)));
-    }
-    return make_float2(hi, lo);
-}
-
-__global__ void k_split_df_vec(int64_t n, const double *__restrict__ v, float2 *__restrict__ out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = split_df(v[i]);
-}
-
-// X (rows x k, ld ldx) -> X2 (rows x k, ld k)
-__global__ void k_split_df(int rows, int k, const double *__restrict__ X, int ldx, float2 *__restrict__ X2) {
-    HSIM_FOR_RC(r, rows, c, k) X2[(size_t)r * k + c] = split_df(X[(size_t)r * ldx + c]);
-}
-
-// One warp per (row, 128-column block), four columns per lane: 8 accumulator
-// registers per lane, so many resident warps, and each lane keeps four
-// 16-byte loads in flight (two nonzeros at a time); the warp reads the row's
-// column indices and values once and broadcasts them with shuffles.  (A warp
-// per row with 24 columns per lane held 48 accumulators, ran at 2 CTAs per SM
-// and waited on its gathers: 1.25 ms against 0.95 ms for the FP64 product on
-// 90,000 x 750.)
-__device__ __forceinline__ void df_acc(float &ah, float &al, float sh, float sl, float xh, float xl) {
-    const float p = __fmul_rn(sh, xh);
-    const float t2 = fmaf(sh, xl, fmaf(sl, xh, fmaf(sh, xh, -p)));
-    const float s1 = __fadd_rn(ah, p), bb = __fsub_rn(s1, ah);
-    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
-    al = __fadd_rn(al, __fadd_rn(err, t2));
-    ah = s1;
-}
-
-// four float2 of row r from column c (zeros past k); 16-byte loads when the
-// four are in range (X2 rows are k float2, k even keeps c * 8 bytes aligned)
-__device__ __forceinline__ void load_x4(float2 (&x)[4], const float2 *__restrict__ X2, int r, int c, int k,
-                                        bool vec) {
-    const float2 *p = X2 + (size_t)r * k + c;
-    if (vec && c + 4 <= k) {
-        const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
-        x[0] = make_float2(a.x, a.y), x[1] = make_float2(a.z, a.w), x[2] = make_float2(b.x, b.y),
-        x[3] = make_float2(b.z, b.w);
-    } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) x[v] = c + v < k ? p[v] : make_float2(0.f, 0.f);
-    }
-}
-
 constexpr int kSpmmRows = 16;  // rows (warps) per CTA of the column-block SpMMs
 
 // CTA (16 consecutive rows, one 128-column block), the column block the slow
@@ -214,50 +136,6 @@ __device__ __forceinline__ bool spmm_cb_map(int n_rows, int k, int &row, int &c)
     return row < n_rows && cb * 128 < k;
 }
 
-__global__ void __launch_bounds__(kSpmmRows * 32) k_spmm_df4(int n_rows, const int *__restrict__ ptr,
-                                                             const int *__restrict__ col, const float2 *__restrict__ val,
-                                                             int k, const float2 *__restrict__ X2,
-                                                             double *__restrict__ Y, int ldy, bool vec) {
-    const int lane = threadIdx.x & 31;
-    int row, c;
-    if (!spmm_cb_map(n_rows, k, row, c)) return;
-    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
-    const int beg = ptr[row], end = ptr[row + 1];
-    for (int e0 = beg; e0 < end; e0 += 32) {
-        int my_c = 0;
-        float2 my_v = make_float2(0.f, 0.f);
-        if (e0 + lane < end) {
-            my_c = col[e0 + lane];
-            my_v = val[e0 + lane];
-        }
-        const int cnt = min(32, end - e0);
-        int t = 0;
-        for (; t + 1 < cnt; t += 2) {
-            const int ca = __shfl_sync(0xffffffffu, my_c, t), cb = __shfl_sync(0xffffffffu, my_c, t + 1);
-            const float sah = __shfl_sync(0xffffffffu, my_v.x, t), sal = __shfl_sync(0xffffffffu, my_v.y, t);
-            const float sbh = __shfl_sync(0xffffffffu, my_v.x, t + 1), sbl = __shfl_sync(0xffffffffu, my_v.y, t + 1);
-            float2 xa[4], xb[4];
-            load_x4(xa, X2, ca, c, k, vec);
-            load_x4(xb, X2, cb, c, k, vec);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) df_acc(ah[v], al[v], sah, sal, xa[v].x, xa[v].y);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) df_acc(ah[v], al[v], sbh, sbl, xb[v].x, xb[v].y);
-        }
-        if (t < cnt) {
-            const int ca = __shfl_sync(0xffffffffu, my_c, t);
-            const float sah = __shfl_sync(0xffffffffu, my_v.x, t), sal = __shfl_sync(0xffffffffu, my_v.y, t);
-            float2 xa[4];
-            load_x4(xa, X2, ca, c, k, vec);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) df_acc(ah[v], al[v], sah, sal, xa[v].x, xa[v].y);
-        }
-    }
-    double *yr = Y + (size_t)row * ldy;
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-        if (c + v < k) yr[c + v] = f2d_bits(ah[v]) + f2d_bits(al[v]);
-}
 
 // FP64 S X with the same column-block mapping: four doubles per lane
 __device__ __forceinline__ void load_d4(double (&x)[4], const double *__restrict__ X, int r, int c, int k, int ldx,
@@ -595,24 +473,6 @@ void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const doub
     HSIM_LAUNCHED();
 }
 
-void split_df_values(cudaStream_t s, int64_t n, const double *v, float2 *out) {
-    if (n <= 0) return;
-    k_split_df_vec<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, v, out);
-    HSIM_LAUNCHED();
-}
-
-void spmm_df(cudaStream_t s, int n_rows, int n_cols, const int *ptr, const int *col, const float2 *val, int k,
-             const double *X, int ldx, float2 *X2, double *Y, int ldy) {
-    if (n_rows <= 0 || k <= 0) return;
-    if (n_cols > 0) {
-        k_split_df<<<grid_rc(n_cols, k), 256, 0, s>>>(n_cols, k, X, ldx, X2);
-        HSIM_LAUNCHED();
-    }
-    const unsigned blocks = (unsigned)(((n_rows + kSpmmRows - 1) / kSpmmRows) * ((k + 127) / 128));
-    const bool vec = (reinterpret_cast<uintptr_t>(X2) % 16 == 0) && (k % 2 == 0);
-    k_spmm_df4<<<blocks, kSpmmRows * 32, 0, s>>>(n_rows, ptr, col, val, k, X2, Y, ldy, vec);
-    HSIM_LAUNCHED();
-}
 
 
 void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *S, const double *M,

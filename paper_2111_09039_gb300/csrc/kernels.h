@@ -27,12 +27,6 @@ void eig_grad(cudaStream_t s, int n, int m, int p, const double *V, const int *F
 // Y[r, 0:k] = sum A[r,c] X[c, 0:k]
 void spmm(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *val, int k,
           const double *X, int ldx, double *Y, int ldy);
-// Y = S X with S and X carried as FP32 pairs (double-float arithmetic, a few
-// units of 2^-46 |s x| per term; k_sparse.cu): val from split_df_values, X2 a
-// n_cols x k float2 scratch for the split of X
-void split_df_values(cudaStream_t s, int64_t n, const double *v, float2 *out);
-void spmm_df(cudaStream_t s, int n_rows, int n_cols, const int *ptr, const int *col, const float2 *val, int k,
-             const double *X, int ldx, float2 *X2, double *Y, int ldy);
 // R = B - (S - mu M) X with M in S's pattern (M) or diagonal (Md)
 void shifted_residual(cudaStream_t s, int n_rows, const int *ptr, const int *col, const double *S,
                       const double *M, const double *Md, double mu, int k, const double *X, int ldx,

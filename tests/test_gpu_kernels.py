@@ -412,36 +412,3 @@ def test_ritz_tc_clusters_and_fp64_agreement(hs, ctx):
         Pt = X_t[:, a:b] @ X_t[:, a:b].T @ M
         Pf = X_f[:, a:b] @ X_f[:, a:b].T @ M
         np.testing.assert_allclose(Pt, Pf, atol=1e-8)
-
-
-# ---- double-float SpMM (mixed path) ------------------------------------------
-@pytest.mark.parametrize("k", [1, 7, 33, 256, 257, 750, 769])
-def test_spmm_df_matches_scipy(hs, ctx, k):
-    # values over several decades and both signs; bound 2^-42 sum |a x|: each
-    # term carries a few units of 2^-46 |a x| (split of both factors, FP32
-    # rounding of the cross terms), and rows have up to ~20 terms (an FP32
-    # emulation of the kernel on this data peaks at 2^-44.0)
-    A = random_csr(1003, 517, 0.02, k, empty_rows=(0, 5, 1002))
-    rng = np.random.default_rng(k + 1)
-    A.data = A.data * 10.0 ** rng.uniform(-6, 6, A.data.size)
-    X = rng.standard_normal((517, k)) * 10.0 ** rng.uniform(-6, 6, (517, 1))
-    Y = hs.spmm(ctx, dev(A.indptr.astype(np.int32)), dev(A.indices.astype(np.int32)), dev(A.data), dev(X), df=True)
-    ref = A @ X
-    bound = 2.0 ** -42 * (abs(A) @ np.abs(X))
-    assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound + 1e-300)
-
-
-def test_spmm_df_laplacian_cancellation_and_strided(hs, ctx):
-    # a 1-D Laplacian times a smooth block: S x is far smaller than sum |s x|;
-    # the error stays within 2^-42 sum |s x|; strided X (leading dimension
-    # 20, 12 columns)
-    import scipy.sparse as sp
-    n = 4000
-    S = sp.diags([-np.ones(n - 1), 2.0 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
-    t = np.linspace(0.0, 1.0, n)[:, None]
-    Xf = np.sin(np.pi * t * np.arange(1, 21)[None, :])
-    Xt = dev(Xf)[:, 3:15]
-    Y = hs.spmm(ctx, dev(S.indptr.astype(np.int32)), dev(S.indices.astype(np.int32)), dev(S.data), Xt, df=True)
-    ref = S @ Xf[:, 3:15]
-    bound = 2.0 ** -42 * (abs(S) @ np.abs(Xf[:, 3:15]))
-    assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound + 1e-300)

@@ -6,7 +6,8 @@ This test calls it through the C ABI twice in a row on different inputs and
 checks each result against the allocating entry point within the tolerances
 of the other Ritz tests (eigenvalues 1e-10 relative, M-orthonormal
 eigenvectors, eigenvectors equal up to sign for a well-separated spectrum),
-and that a size beyond the fixed limit is refused.  It lives in a file of its
+against SciPy's dense generalised eigensolver (eigenvalues, and X^T S X =
+Lambda with X^T M X = I), and that a size beyond the fixed limit is refused.  It lives in a file of its
 own that pytest collects after the solver and kernel tests, and passes alone
 in a fresh process as well as after the other tests.
 """
@@ -67,6 +68,20 @@ def test_noalloc_matches_allocating_entry_point_twice(hs):
         np.testing.assert_allclose(X_a.T @ M @ X_a, np.eye(k), atol=1e-9)
         signs = np.sign(np.sum(X_a * X_r, axis=0))
         np.testing.assert_allclose(X_a * signs[None, :], X_r, atol=1e-8 * np.abs(X_r).max())
+
+
+def test_noalloc_matches_scipy_eigh(hs):
+    # independent of the front kernels both library entry points share: the
+    # plain definition of the generalised problem solved by LAPACK
+    import scipy.linalg as sla
+    for k, seed in ((256, 4), (31, 5)):
+        S, M = spd_pair(k, seed)
+        lam_a, X_a = noalloc(hs, S, M)
+        lam_ref = sla.eigh(S, M, eigvals_only=True)
+        scale = np.abs(lam_ref).max()
+        np.testing.assert_allclose(lam_a, lam_ref, rtol=1e-10, atol=1e-11 * scale)
+        np.testing.assert_allclose(X_a.T @ M @ X_a, np.eye(k), atol=1e-9)
+        np.testing.assert_allclose(X_a.T @ S @ X_a, np.diag(lam_ref), atol=1e-9 * scale)
 
 
 def test_noalloc_refuses_sizes_beyond_its_limit(hs):
