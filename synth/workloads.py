@@ -41,6 +41,10 @@ WORKLOADS = {
     # bumpy torus R=1, r=0.3 on a 1000 x 1000 grid (10^6 vertices)
     "bumpy_torus_1000": Workload("bumpy_torus_1000", "bumpy_torus", (1000, 1000, 3), p=500,
                                  levels=3, tol=1e-5, seed=3),
+    # a 250,000-vertex member of the bumpy-torus family with the benchmark's p and
+    # levels (stored oracle eigenvalues at tol 1e-10 for the parity tests)
+    "bumpy_torus_500": Workload("bumpy_torus_500", "bumpy_torus", (500, 500, 3), p=500,
+                                levels=3, tol=1e-10, seed=3),
     # icosphere subdivision 6 (40,962 vertices), noise seed 5: spectral loss source
     "icosphere6_grad": Workload("icosphere6_grad", "displaced_icosphere", (6, 5), p=50,
                                 levels=2, tol=1e-10, seed=5),
