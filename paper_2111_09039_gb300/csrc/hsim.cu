@@ -142,6 +142,13 @@ struct LevelData {
     std::vector<int> inv_n, inv_tiles;
     DevBuf<k::GemmTask> inv_w, inv_wc;
     int inv_nw = 0, inv_tw = 0;
+    // the same tasks numbered in 128 x 128 tiles for the tensor-core products
+    // (FP32 factors): block-doubling levels, and the W products of fronts with
+    // at least kTcMinPivots pivots (the others stay on the CUDA cores)
+    std::vector<DevBuf<k::GemmTask>> inv_p1_tc, inv_p2_tc;
+    std::vector<int> inv_tiles_tc;
+    DevBuf<k::GemmTask> inv_w_tc, inv_w_cc;
+    int inv_nw_tc = 0, inv_tw_tc = 0, inv_nw_cc = 0, inv_tw_cc = 0;
     int64_t inv_scratch = 0;
 };
 
@@ -192,9 +199,61 @@ namespace {
 
 // Device copies of the front inversion's tasks (k::inverse_plan) and the
 // per-height maxima of nf and ns for the inverted-factor solves.
+// Tensor-core FP32 products (k_tc32.cu) replace the CUDA-core kernels of the
+// FP32 factorisation and solves where they measured faster (10^6-vertex
+// level 0, 750 right-hand sides): the block-doubling inversion levels of 64
+// and more and the W products of fronts with at least kTcMinPivots pivots
+// (factor and inversion 1.1 ms faster), and the forward products of tree
+// heights whose fronts reach kTcMinFwdPivots pivots (0.6 ms faster per
+// solve).  The backward products (K runs over all nf rows of few large
+// fronts) and the rank-32 Schur updates of the right-looking factorisation
+// (one 32-deep K step per tile) measured slower on the tensor cores (+2.6 and
+// +8 ms) and stay on the CUDA cores.  HSIM_TC32=0 keeps every FP32 product on
+// the CUDA cores (for comparison; read at every factorisation and solve).
+constexpr int kTcMinPivots = 128, kTcMinFwdPivots = 300;
+bool tc32_enabled() {
+    const char *e = std::getenv("HSIM_TC32");
+    return !(e && *e == '0');
+}
+
+int number_tiles(std::vector<k::GemmTask> &tasks, int tile) {
+    int nt = 0;
+    for (auto &t : tasks) {
+        t.tile0 = nt;
+        nt += ((t.M + tile - 1) / tile) * ((t.N + tile - 1) / tile);
+    }
+    return nt;
+}
+
 void build_inverse_plan(LevelData &L, cudaStream_t s) {
     const FrontSymbolic &fs = L.fs;
     k::InversePlan P = k::inverse_plan(fs.nf, fs.ns, fs.foff);
+    {
+        L.inv_p1_tc.clear();
+        L.inv_p2_tc.clear();
+        L.inv_tiles_tc.clear();
+        for (size_t lv = 0; lv < P.p1.size(); ++lv) {
+            std::vector<k::GemmTask> a = P.p1[lv], b = P.p2[lv];
+            L.inv_tiles_tc.push_back(k::gemm_tiles_tc(a));
+            k::gemm_tiles_tc(b);
+            L.inv_p1_tc.emplace_back();
+            L.inv_p1_tc.back().upload(a, s);
+            L.inv_p2_tc.emplace_back();
+            L.inv_p2_tc.back().upload(b, s);
+            HSIM_CUDA(cudaStreamSynchronize(s));  // the uploads read a and b
+        }
+        std::vector<k::GemmTask> wt, wc;
+        for (const auto &t : P.w) (t.K >= kTcMinPivots ? wt : wc).push_back(t);
+        L.inv_nw_tc = (int)wt.size();
+        L.inv_tw_tc = k::gemm_tiles_tc(wt);
+        L.inv_nw_cc = (int)wc.size();
+        L.inv_tw_cc = number_tiles(wc, k::kGemmTile);
+        if (wt.empty()) wt.push_back(k::GemmTask{});
+        if (wc.empty()) wc.push_back(k::GemmTask{});
+        L.inv_w_tc.upload(wt, s);
+        L.inv_w_cc.upload(wc, s);
+        HSIM_CUDA(cudaStreamSynchronize(s));
+    }
     L.n_inv_blk = (int)P.blk.size();
     L.inv_blk.upload(P.blk.empty() ? std::vector<int2>{make_int2(0, 0)} : P.blk, s);
     L.inv_p1.clear();
@@ -291,6 +350,24 @@ template <typename T>
 void invert_level_t(cudaStream_t s, LevelData &L, T *arena, DevBuf<T> &scr) {
     scr.reserve((size_t)std::max<int64_t>(L.inv_scratch, 1));
     k::inv_diag_blocks(s, L.fd, L.inv_blk.p, L.n_inv_blk, arena);
+    if constexpr (std::is_same<T, float>::value) {
+        if (tc32_enabled()) {
+            // block doubling: bs = 32 on the CUDA cores, 64 and up on the tensor cores
+            for (size_t lv = 0; lv < L.inv_n.size(); ++lv) {
+                if (lv == 0) {
+                    k::gemm_tasks<T>(s, L.inv_p1[lv].p, L.inv_n[lv], L.inv_tiles[lv], arena, arena, scr.p);
+                    k::gemm_tasks<T>(s, L.inv_p2[lv].p, L.inv_n[lv], L.inv_tiles[lv], arena, scr.p, arena);
+                } else {
+                    k::gemm_tasks_tc(s, L.inv_p1_tc[lv].p, L.inv_n[lv], L.inv_tiles_tc[lv], arena, arena, scr.p);
+                    k::gemm_tasks_tc(s, L.inv_p2_tc[lv].p, L.inv_n[lv], L.inv_tiles_tc[lv], arena, scr.p, arena);
+                }
+            }
+            k::gemm_tasks_tc(s, L.inv_w_tc.p, L.inv_nw_tc, L.inv_tw_tc, arena, arena, scr.p);
+            k::gemm_tasks<T>(s, L.inv_w_cc.p, L.inv_nw_cc, L.inv_tw_cc, arena, arena, scr.p);
+            k::copy_tasks<T>(s, L.inv_wc.p, L.inv_nw, L.inv_tw, scr.p, arena);
+            return;
+        }
+    }
     for (size_t lv = 0; lv < L.inv_n.size(); ++lv) {
         k::gemm_tasks<T>(s, L.inv_p1[lv].p, L.inv_n[lv], L.inv_tiles[lv], arena, arena, scr.p);
         k::gemm_tasks<T>(s, L.inv_p2[lv].p, L.inv_n[lv], L.inv_tiles[lv], arena, scr.p, arena);
@@ -414,7 +491,14 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         const int cnt = (int)(L.hnodes_off[h + 1] - L.hnodes_off[h]);
-        k::solve_fwd_inv(s, L.fd, nodes, cnt, L.h_maxnf[h], L.h_maxns[h], arena, k, X, Y.p, ldx);
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc32_enabled() && L.h_maxns[h] >= kTcMinFwdPivots)
+                k::solve_fwd_tc(s, L.fd, nodes, cnt, L.h_maxnf[h], arena, k, X, Y.p, ldx);
+            else
+                k::solve_fwd_inv(s, L.fd, nodes, cnt, L.h_maxnf[h], L.h_maxns[h], arena, k, X, Y.p, ldx);
+        } else {
+            k::solve_fwd_inv(s, L.fd, nodes, cnt, L.h_maxnf[h], L.h_maxns[h], arena, k, X, Y.p, ldx);
+        }
         mark();
     }
     mark();  // the diagonal is applied inside the backward products
@@ -848,7 +932,10 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             HSIM_CUDA(cudaMemcpyAsync(rs.data(), H->res_sums.p, 3 * p * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaMemcpyAsync(lam_h.data(), H->lam.p, q * sizeof(double), cudaMemcpyDeviceToHost, s));
             HSIM_CUDA(cudaStreamSynchronize(s));
-            if (mixed) k::ozaki_check(s);
+            if (mixed) {
+                k::ozaki_check(s);
+                k::tc32_check(s);
+            }
             inf.ms_residual += (ph[5] = ts.stop());
             double lam_ref = lam_h[q - 1];
             for (int i = 0; i < q; ++i)
@@ -1521,6 +1608,7 @@ hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *h, int tau, const doubl
         solve_level(ctx, h, L, X.p, kk, kk);
         k::gather_rows(s, L.n, kk, L.d_iperm.p, X.p, kk, B, ldb);
         HSIM_CUDA(cudaStreamSynchronize(s));
+        k::tc32_check(s);
         if (neg) *neg = negp;
     });
 }
@@ -1550,6 +1638,7 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *h, int tau, const d
         k::convert_matrix(s, L.n, kk, X32.p, ld, X.p, kk);
         k::gather_rows(s, L.n, kk, L.d_iperm.p, X.p, kk, B, ldb);
         HSIM_CUDA(cudaStreamSynchronize(s));
+        k::tc32_check(s);
         if (neg) *neg = negp;
     });
 }

@@ -201,6 +201,20 @@ struct InversePlan {
     int64_t scratch = 0;
 };
 InversePlan inverse_plan(const std::vector<int> &nf, const std::vector<int> &ns, const std::vector<int64_t> &foff);
+
+// FP32-accurate products on the tcgen05 tensor cores (k_tc32.cu: operands
+// split into two TF32 halves, three MMAs per K step, FP32 accumulators in
+// TMEM; 128 x 128 output tiles).  The same operations as solve_fwd_inv and
+// gemm_tasks for FP32 fronts.
+void solve_fwd_tc(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int max_nf, const float *arena,
+                  int k, float *X, float *Y, int ldx);
+void gemm_tasks_tc(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles, const float *Ab, const float *Bb,
+                   float *Cb);
+// numbers the tasks' 128 x 128 tiles consecutively (tile0); returns the total
+int gemm_tiles_tc(std::vector<GemmTask> &tasks);
+// fails with HSIM_E_TIMEOUT (and clears the flag) if a product's bounded
+// mbarrier wait gave up since the last check
+void tc32_check(cudaStream_t s);
 // inverse of the unit lower 32 x 32 diagonal blocks (t, b0) of the pivot
 // blocks, in place
 template <typename T>
