@@ -121,14 +121,23 @@ def max_over_ranks(value, world, device):
     return float(t.item())
 
 
+# Iterations per level (finest first) that the mixed GPU solve takes on each
+# benchmark workload (its info["iters"]); the reference arm's CPU model charges
+# the oracle the same number of subspace iterations.
+GPU_ITERS = {"bumpy_torus_1000": [8, 13, 0]}
+
+
 def run_reference(args, world, rank):
-    """CPU oracle, bounded sample per step; rank 0 only."""
+    """CPU oracle, bounded sample per step; rank 0 only.  Each sample runs in
+    a fresh subprocess (the oracle's solve workers are forked from it)."""
     if rank != 0:
         return
-    from oracle import baseline
+    iters = GPU_ITERS.get(args.workload)
     samples = []
     for i in range(args.warmup + args.steps):
-        r = baseline.sample(args.workload, cols=args.sample_cols)
+        r = cpu_baseline(args.workload, {"iters": iters})
+        if "error" in r:
+            raise RuntimeError(r["error"])
         if i >= args.warmup:
             samples.append(r)
     v = sum(s["value"] for s in samples) / len(samples)
@@ -137,7 +146,7 @@ def run_reference(args, world, rank):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload},
             "cpu_baseline": {"kind": "oracle", "cores": samples[-1]["cores"], "sample": samples[-1]["sample"],
-                             "value": v, "unit": "s"},
+                             "value": v, "unit": "s", "model": samples[-1].get("model")},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -153,8 +162,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="timed FP64 solves for the mixed-vs-FP64 comparison (0 = skip)")
     ap.add_argument("--tol", type=float, default=None)
-    ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--sample-cols", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -257,22 +265,35 @@ def main():
     S_d = torch.empty_like(S)
     Md_d = torch.empty_like(Md)
     e2e_ms = []
+    seg = {"h2d": [], "solve": [], "d2h": []}
     # one untimed step first (first use of the pinned buffers and of the
-    # output allocations), then the mean of the timed steps
+    # output allocations), then the mean of the timed steps; host clock
+    # marks after the input copy and after the solve split each step into
+    # its segments (the marks synchronise the stream, which the copies and
+    # the solve's own convergence tests do anyway)
     for step in range(max(0, args.e2e_steps) + (1 if args.e2e_steps > 0 else 0)):
         barrier()
         t1 = time.perf_counter()
         with torch.cuda.stream(stream):
             S_d.copy_(S_h, non_blocking=True)
             Md_d.copy_(Md_h, non_blocking=True)
+        stream.synchronize()
+        t2 = time.perf_counter()
         lam_d, Phi_d, _ = hs.solve(ctx, hier, S_d, Md_d, p, tol, options=opts)
+        stream.synchronize()
+        t3 = time.perf_counter()
         with torch.cuda.stream(stream):
             lam_h.copy_(lam_d, non_blocking=True)
             vec_h.copy_(Phi_d.t(), non_blocking=True)
         stream.synchronize()
+        t4 = time.perf_counter()
         if step > 0:
-            e2e_ms.append((time.perf_counter() - t1) * 1000.0)
+            e2e_ms.append((t4 - t1) * 1000.0)
+            seg["h2d"].append(t2 - t1)
+            seg["solve"].append(t3 - t2)
+            seg["d2h"].append(t4 - t3)
     e2e_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev) if e2e_ms else None
+    e2e_seg = {k: sum(v) / len(v) for k, v in seg.items()} if e2e_ms else None
     h2d = S.numel() * 8 + Md.numel() * 8
     d2h = p * 8 + p * hier.n * 8
 
@@ -305,7 +326,7 @@ def main():
     roof = roofline(info, infos, hier, p, peaks, peak_src, args.precision)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(args.workload, info, args.sample_cols)
+        cpu = cpu_baseline(args.workload, info)
     line = {
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -316,7 +337,8 @@ def main():
                    "l2": "working set > L2 (n x q float64 blocks of 6 GB)"},
         "hier_build_s": hier_s, "hier_plus_solve_s": hier_s + ms / 1000.0, "max_residual_check": res,
         "e2e": ({"value": e2e_mean / 1000.0, "unit": "s", "h2d_bytes_per_step": h2d,
-                 "d2h_bytes_per_step": d2h, "steps": len(e2e_ms), "warmup": 1} if e2e_ms else None),
+                 "d2h_bytes_per_step": d2h, "steps": len(e2e_ms), "warmup": 1,
+                 "segments_s": e2e_seg} if e2e_ms else None),
         "gpu_launches": int(round(launches)),
         "fp64_gpu": fp64,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "info": info,
@@ -645,9 +667,23 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
     # solve and Ritz phases are spread over several kernels (ncu launch lists)
     top = dict(kernels["gram"])
     if precision != "fp64":
+        # achieved = the method's work (FP64 products of the two Grams and the
+        # update) / the kernel's time; the BF16 pipe occupancy of the 21
+        # digit-pair products is reported beside it
+        ms_tc = top["ms_per_step"]
+        fp64_eq = top["fp64_equivalent_tflops"]
+        top["bf16_pipe"] = {"achieved": top["achieved"], "frac": top["frac"], "unit": "TFLOP/s",
+                            "note": "21 BF16 digit-pair products per FP64 product (emulation work)"}
+        top["achieved"] = fp64_eq
+        top["frac"] = fp64_eq / top["peak"]
+        top["work"] = ("method FLOPs: FP64 products of the Grams Psi^T [S Psi | M Psi] (n q (q+1) each, lower "
+                       "triangles) and the update Psi Phi_bar (2 n q^2) of every subspace iteration")
         top["traffic"] = None
-        top["traffic_note"] = ("ncu capture of one 200,000 x 750 Gram launch: 4.88 GB DRAM read+write against "
-                               "3.69 GB of digit operands (1.32 x)")
+        tr = tc_traffic(sizes, iters, q)
+        if tr is not None:
+            top["traffic"] = tr["per_launch"]
+            top["traffic_note"] = tr["note"]
+            top["algorithmic_bytes_per_launch"] = tr["algorithmic_per_launch"]
     top["dominant_phase"] = dom
     top["phase_ms"] = phases
     top["kernels"] = {k: {kk: v[kk] for kk in ("kernel", "bound", "achieved", "peak", "unit", "frac")}
@@ -655,12 +691,42 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
     return top
 
 
-def cpu_baseline(workload, info, cols):
-    """FP64 oracle on a bounded sample, in a fresh process (no CUDA state)."""
+# DRAM bytes (read + write) per operand row of one k_ozaki_tc launch, from
+# one ncu capture of each product shape at 200,000 rows, q = 750
+# (profiles/ozaki_tc_traffic_n200k_q750.md); None until captured for the
+# kernel as it is now.
+TC_TRAFFIC_PER_ROW = {"gram": None, "update": None}
+
+
+def tc_traffic(sizes, iters, q):
+    """Per-launch DRAM traffic of k_ozaki_tc over one solve, scaled from the
+    200,000-row captures by the rows each launch processes (traffic grows in
+    proportion to the rows), against the algorithmic bytes (the BF16 digit
+    slices read once: 6 slices x 2 bytes per operand value; the update's FP64
+    output, 8 bytes per value)."""
+    if TC_TRAFFIC_PER_ROW["gram"] is None or TC_TRAFFIC_PER_ROW["update"] is None:
+        return None
+    qp = (q + 31) // 32 * 32
+    tot, alg, launches = 0.0, 0.0, 0
+    for t in range(len(sizes) - 1):
+        n = sizes[t]
+        # two Grams (Psi against S Psi, Psi against M Psi) and one update per iteration
+        tot += iters[t] * (2 * TC_TRAFFIC_PER_ROW["gram"] * n + TC_TRAFFIC_PER_ROW["update"] * n)
+        # Gram: both operands' slices (2 x 12 bytes per value); update: Psi's
+        # slices plus the FP64 output Phi
+        alg += iters[t] * (2 * 24.0 * n * qp + (12.0 * n * qp + 8.0 * n * q))
+        launches += 3 * iters[t]
+    return {"per_launch": tot / launches, "algorithmic_per_launch": alg / launches,
+            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram and one update launch at "
+                    "200,000 x 750, scaled by rows to every launch of the solve and averaged per launch"}
+
+
+def cpu_baseline(workload, info):
+    """FP64 oracle on a bounded sample, in a fresh process (no CUDA state; its
+    solve workers are forked from it)."""
     cmd = [sys.executable, "-c",
            "import json,sys; sys.path.insert(0, %r); from oracle import baseline; "
-           "print(json.dumps(baseline.sample(%r, cols=%d, iters=%s)))" % (ROOT, workload, cols,
-                                                                           json.dumps(info["iters"]))]
+           "print(json.dumps(baseline.sample(%r, iters=%s)))" % (ROOT, workload, json.dumps(info["iters"]))]
     try:
         out = subprocess.run(cmd, capture_output=True, text=True, timeout=1200)
         return json.loads(out.stdout.strip().splitlines()[-1])
