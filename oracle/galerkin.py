@@ -15,10 +15,11 @@ def restrict(A: sp.spmatrix, U: sp.csr_matrix) -> sp.csr_matrix:
     return C
 
 
-def level_matrices(S0: sp.csr_matrix, M0_diag, U_list):
-    """Lists [S^0..S^{T-1}] and [M^0..M^{T-1}] (M^0 as a sparse diagonal)."""
+def level_matrices(S0: sp.csr_matrix, M0, U_list):
+    """Lists [S^0..S^{T-1}] and [M^0..M^{T-1}]; M0 is the diagonal of a lumped
+    mass matrix (1-D array) or a sparse matrix (consistent mass)."""
     S = [S0.tocsr()]
-    M = [sp.diags(M0_diag).tocsr()]
+    M = [sp.csr_matrix(M0) if sp.issparse(M0) else sp.diags(M0).tocsr()]
     for U in U_list:
         S.append(restrict(S[-1], U))
         M.append(restrict(M[-1], U))

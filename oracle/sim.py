@@ -13,8 +13,10 @@ Steps and readings (each listed in the design notes):
   M_bar = Psi^T M Psi; solve S_bar Phi_bar = M_bar Phi_bar Lambda_bar;
   Phi = Psi Phi_bar } until the convergence test holds for i < p.
 * Convergence test (eq. conv2): ||S Phi_i - lambda_i M Phi_i|| / den_i < eps
-  with the M^{-1}-norm on the finest level (M diagonal) and the Euclidean
-  norm on coarser levels (Sec. 5, termination criterion).  den_i =
+  with the M^{-1}-norm on the finest level and the Euclidean norm on coarser
+  levels (Sec. 5, termination criterion).  With a consistent (non-diagonal)
+  M on the finest level (Sec. 7) the M^{-1}-norm is evaluated exactly,
+  ||x||^2 = x^T (M^{-1} x) with M^{-1} x from a sparse LU of M.  den_i =
   max(||S Phi_i||, lambda_ref ||M Phi_i||) where lambda_ref is the first Ritz
   value above 1e-8 * Lambda_{q-1}: the plain denominator vanishes for the
   constant eigenvector of a closed surface.
@@ -57,7 +59,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from .assembly import boundary_vertices, lumped_mass, stiffness
+from .assembly import boundary_vertices, consistent_mass, lumped_mass, stiffness
 from .galerkin import level_matrices
 from .hierarchy import build_hierarchy, subspace_size
 
@@ -66,12 +68,18 @@ class NoConvergence(RuntimeError):
     pass
 
 
-def residuals(S, M, Phi, lam, m_inverse_diag=None):
-    """Relative residuals of eq. conv2 for every column of Phi."""
+def residuals(S, M, Phi, lam, m_inverse_diag=None, m_solve=None):
+    """Relative residuals of eq. conv2 for every column of Phi: M^{-1}-norms
+    with a diagonal M (m_inverse_diag = 1 / diag(M)) or a general one
+    (m_solve(X) = M^{-1} X), else Euclidean norms."""
     SP = S @ Phi
     MP = M @ Phi
     R = SP - MP * lam[None, :]
-    if m_inverse_diag is not None:
+    if m_solve is not None:
+        nr = np.sqrt(np.maximum(np.sum(R * m_solve(R), axis=0), 0.0))
+        ns = np.sqrt(np.maximum(np.sum(SP * m_solve(SP), axis=0), 0.0))
+        nm = np.sqrt(np.maximum(np.sum(MP * m_solve(MP), axis=0), 0.0))
+    elif m_inverse_diag is not None:
         nr = np.sqrt(np.sum(R * R * m_inverse_diag[:, None], axis=0))
         ns = np.sqrt(np.sum(SP * SP * m_inverse_diag[:, None], axis=0))
         nm = np.sqrt(np.sum(MP * MP * m_inverse_diag[:, None], axis=0))
@@ -101,7 +109,12 @@ def sim(S, M, Phi, p, eps, mu, finest: bool, max_iters=100, inv_iters=2, lock_fa
     M = M.tocsr()
     K = (S - mu * M).tocsc()
     lu = spla.splu(K)
-    minv = 1.0 / M.diagonal() if finest else None
+    minv, msolve = None, None
+    if finest:
+        if M.nnz == M.shape[0] and np.all(M.indices == np.arange(M.shape[0])):
+            minv = 1.0 / M.diagonal()
+        else:
+            msolve = spla.splu(M.tocsc()).solve
     Phi = np.array(Phi, dtype=np.float64, copy=True)
     locked = 0
     history = []
@@ -114,7 +127,7 @@ def sim(S, M, Phi, p, eps, mu, finest: bool, max_iters=100, inv_iters=2, lock_fa
         Mbar = Psi.T @ (M @ Psi)
         lam, Phibar = sla.eigh(Sbar, Mbar)
         Phi = Psi @ Phibar
-        res = residuals(S, M, Phi, lam, minv)
+        res = residuals(S, M, Phi, lam, minv, msolve)
         history.append(float(res[:p].max()))
         if np.all(res[:p] < eps):
             return SimResult(lam, Phi, it, res, history)
@@ -181,25 +194,31 @@ def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
     return lam, Phi, iters, shifts, coarse
 
 
-def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100, boundary="neumann"):
+def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100, boundary="neumann",
+         mass="lumped"):
     """Full HSIM (Alg. 3) on a mesh: p lowest eigenpairs of S Phi = lambda M Phi.
     boundary="dirichlet" eliminates the boundary vertices (rows of Phi are then
-    the interior vertices, listed in the result's ``interior``)."""
+    the interior vertices, listed in the result's ``interior``).
+    mass="consistent" uses the consistent mass matrix on the finest level
+    (Sec. 7; the coarse levels are its Galerkin restrictions)."""
     if boundary not in ("neumann", "dirichlet"):
         raise ValueError(boundary)
+    if mass not in ("lumped", "consistent"):
+        raise ValueError(mass)
     S0 = stiffness(mesh)
-    M0 = lumped_mass(mesh)
+    M0 = lumped_mass(mesh) if mass == "lumped" else consistent_mass(mesh)
     interior = None
     if boundary == "dirichlet":
         interior = np.setdiff1d(np.arange(mesh.n), boundary_vertices(mesh))
         S0 = S0[interior][:, interior].tocsr()
-        M0 = M0[interior]
+        M0 = M0[interior] if mass == "lumped" else M0[interior][:, interior].tocsr()
     H = build_hierarchy(mesh, p, levels, start_vertex, sigma, dofs=interior)
     U = H.U
     S, M = level_matrices(S0, M0, U)
     if len(S) == 1:
         q = subspace_size(p)
-        lam, Phi = sla.eigh(S0.toarray(), np.diag(M0), subset_by_index=[0, q - 1])
+        Mdense = M0.toarray() if sp.issparse(M0) else np.diag(M0)
+        lam, Phi = sla.eigh(S0.toarray(), Mdense, subset_by_index=[0, q - 1])
         iters, shifts, coarse = [], [], [lam]
     else:
         lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, U, p, eps, alpha, max_iters)
