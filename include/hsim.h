@@ -59,6 +59,19 @@ enum { HSIM_FP64 = 0, HSIM_MIXED = 1 };
  * interior vertices only, distances over the whole surface). */
 enum { HSIM_BOUNDARY_NATURAL = 0, HSIM_BOUNDARY_DIRICHLET = 1 };
 
+/* Mass matrix of the finest level (hsim_options.mass, read by
+ * hsim_build_hierarchy).  LUMPED: M^0 diagonal, M_ii = sum of A_t / 3 over the
+ * triangles of vertex i (the paper's experiments).  CONSISTENT: the exact
+ * integral M_ij = int phi_i phi_j (A_t / 6 on the diagonal, A_t / 12 per
+ * edge), a non-diagonal M in S's pattern (Sec. 7: HSIM handles generalised
+ * problems with non-diagonal M unchanged).  With the consistent M the
+ * M^-1-norms of the finest level's convergence test (eq. conv2) are bounded
+ * through the lumped mass M_L (its row sums): every element satisfies
+ * M_L / 4 <= M <= M_L, so ||x||_{M_L^-1} <= ||x||_{M^-1} <= 2 ||x||_{M_L^-1},
+ * and the test uses twice the lumped-norm ratio, an upper bound of the exact
+ * one (hsim_info.max_residual reports that bound). */
+enum { HSIM_MASS_LUMPED = 0, HSIM_MASS_CONSISTENT = 1 };
+
 /* Solver options.  Defaults (hsim_default_options) follow the paper:
  * sigma = 7 (Sec. 5, support region), alpha = 0.1 (Alg. 3 shift index
  * floor(alpha p)), two inverse iterations per Rayleigh-Ritz step and locking
@@ -100,6 +113,9 @@ typedef struct {
                             shift sim_shift.  FP64 only. */
     double sim_shift;    /* plain_sim: the shift mu of Alg. 1 */
     uint64_t seed;       /* plain_sim: seed of the random column */
+    int mass;            /* HSIM_MASS_LUMPED (default) or HSIM_MASS_CONSISTENT; read by
+                            hsim_build_hierarchy, fixed for the hierarchy (not with
+                            plain_sim) */
 } hsim_options;
 
 /* Per-solve report (host struct, optional). */
@@ -193,10 +209,13 @@ hsim_status hsim_hier_prolongation(const hsim_hier *hier, int tau, int *rows, in
                                    int64_t *nnz, int32_t *row_ptr_host, int32_t *col_host,
                                    double *val_host);
 
-/* Cotan stiffness S^0 and lumped mass diag(M^0) on the device (Sec. 3.1,
+/* Cotan stiffness S^0 and mass M^0 on the device (Sec. 3.1,
  * eq. massStiffMatrices; S_ij = -1/2 (cot a_ij + cot b_ij), S_ii = -sum_j
- * S_ij, M_ii = sum of A_t/3 over incident triangles), written into the
- * hierarchy's pattern.  An edge that one triangle holds takes one cotangent.
+ * S_ij), S written into the hierarchy's pattern.  M_diag_dev receives, for a
+ * hierarchy built with mass = HSIM_MASS_LUMPED, the n diagonal entries
+ * M_ii = sum of A_t/3 over incident triangles; with HSIM_MASS_CONSISTENT the
+ * consistent mass in S's pattern (nnz values, A_t/6 on the diagonal and
+ * A_t/12 per edge).  An edge that one triangle holds takes one cotangent.
  * With a Dirichlet boundary the matrices of the whole mesh are restricted to
  * the interior vertices (diagonals keep the boundary edges' weights).
  * Exactly one of V_dev (n x 3) and L2_dev (n_tris x 3) is non-NULL. */
@@ -205,7 +224,9 @@ hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *hier, const double *V_
 
 /* HSIM (Alg. 3): the p lowest eigenpairs of S Phi = lambda M Phi.
  *   S_val_dev   values of S^0 in the hierarchy's pattern (hsim_hier_pattern)
- *   M_diag_dev  diagonal of the lumped mass M^0 (n)
+ *   M_diag_dev  M^0 as hsim_assemble writes it: the lumped diagonal (n), or
+ *               for a hierarchy with mass = HSIM_MASS_CONSISTENT its values in
+ *               S's pattern (nnz)
  *   tol         relative residual tolerance of eq. conv2 (M^{-1}-norm)
  *   evals_dev   out: p eigenvalues, ascending
  *   evecs_dev   out: n x p, COLUMN-major (evecs[i + k n] = Phi_k(i)),
@@ -242,7 +263,9 @@ hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers
  * For the spectral loss sum_i (lambda_i - lambda*_i)^2 pass
  * dloss_dlambda[i] = 2 (lambda_i - lambda*_i).  Valid for simple
  * eigenvalues; inside a cluster of equal eigenvalues only a loss symmetric
- * in the cluster has a gradient.
+ * in the cluster has a gradient.  The derivative is the one of the lumped
+ * mass (eigenpairs of a hierarchy built with HSIM_MASS_CONSISTENT need the
+ * consistent mass's derivative, which this entry does not form).
  *   V_dev          n x 3 positions (row-major)
  *   F_dev          n_tris x 3 vertex indices in [0, n); triangles of
  *                  positive area (the cotangents divide by it)

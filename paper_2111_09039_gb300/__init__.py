@@ -18,12 +18,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import HSIM_FP64, HSIM_MIXED, HsimError, Info, Options, check, default_options, lib, ptr
+from ._lib import (HSIM_FP64, HSIM_MASS_CONSISTENT, HSIM_MASS_LUMPED, HSIM_MIXED, HsimError, Info, Options, check,
+                   default_options, lib, ptr)
 
 __all__ = ["Context", "Hierarchy", "assemble", "solve", "spmm", "gram", "gemm_update", "gram_tc",
            "gemm_update_tc", "ritz",
            "galerkin", "shifted_solve", "check_symbolic", "check_hierarchy", "default_options", "HsimError",
-           "HSIM_FP64", "HSIM_MIXED", "kernel_launches", "solve_batched", "eig_grad", "eigenvalues"]
+           "HSIM_FP64", "HSIM_MIXED", "HSIM_MASS_LUMPED", "HSIM_MASS_CONSISTENT", "kernel_launches", "solve_batched", "eig_grad", "eigenvalues"]
 
 
 def _torch():
@@ -200,12 +201,19 @@ def _tensor_at(addr: int, nbytes: int):
     return torch.as_tensor(h, device="cuda")
 
 
+def _mass_len(hier: Hierarchy) -> int:
+    """Entries of M^0 as the library takes it: the lumped diagonal (n) or the
+    consistent mass in S's pattern (nnz)."""
+    return int(_pattern_nnz(hier)) if hier.options.mass == HSIM_MASS_CONSISTENT else hier.n
+
+
 def assemble(ctx: Context, hier: Hierarchy, V=None, L2=None):
-    """Cotan S^0 values (hierarchy pattern) and lumped mass diagonal on the GPU."""
+    """Cotan S^0 values (hierarchy pattern) and the mass M^0 (lumped diagonal,
+    or consistent values in the same pattern) on the GPU."""
     torch = _torch()
     dev = f"cuda:{ctx.device}"
     S = torch.empty(int(_pattern_nnz(hier)), dtype=torch.float64, device=dev)
-    Md = torch.empty(hier.n, dtype=torch.float64, device=dev)
+    Md = torch.empty(_mass_len(hier), dtype=torch.float64, device=dev)
     Vt = None if V is None else torch.as_tensor(V, dtype=torch.float64, device=dev).contiguous()
     Lt = None if L2 is None else torch.as_tensor(L2, dtype=torch.float64, device=dev).contiguous()
     check(lib().hsim_assemble(ctx.handle, hier.handle, ptr(Vt), ptr(Lt), ptr(S), ptr(Md)))
@@ -224,7 +232,7 @@ def solve(ctx: Context, hier: Hierarchy, S_val, M_diag, p: int, tol: float,
     torch = _torch()
     dev = f"cuda:{ctx.device}"
     _on_device(S_val, "S_val", ctx.device, torch.float64)
-    _on_device(M_diag, "M_diag", ctx.device, torch.float64, hier.n)
+    _on_device(M_diag, "M_diag", ctx.device, torch.float64, _mass_len(hier))
     if not 1 <= p <= hier.n:
         raise ValueError(f"p must be in [1, {hier.n}]")
     if S_val.numel() != _pattern_nnz(hier):

@@ -13,6 +13,8 @@ LIB_PATH = os.path.join(HERE, "libhsim.so")
 
 HSIM_FP64 = 0
 HSIM_MIXED = 1
+HSIM_MASS_LUMPED = 0
+HSIM_MASS_CONSISTENT = 1
 
 STATUS = {0: "HSIM_OK", 1: "HSIM_E_INVALID_ARG", 2: "HSIM_E_NOMEM", 3: "HSIM_E_CUDA",
           4: "HSIM_E_BREAKDOWN", 5: "HSIM_E_NOT_SPD", 6: "HSIM_E_NO_CONVERGENCE",
@@ -32,7 +34,7 @@ class Options(ctypes.Structure):
                 ("lock_factor", ctypes.c_double), ("precision", ctypes.c_int),
                 ("start_vertex", ctypes.c_int), ("leaf_size", ctypes.c_int), ("q", ctypes.c_int),
                 ("refine", ctypes.c_int), ("boundary", ctypes.c_int), ("plain_sim", ctypes.c_int),
-                ("sim_shift", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("sim_shift", ctypes.c_double), ("seed", ctypes.c_uint64), ("mass", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -561,13 +561,18 @@ struct Timer {
     }
 };
 
-// M Y on level tau: diagonal at tau = 0, CSR otherwise
+// level 0 carries the lumped (diagonal) mass unless the hierarchy was built
+// with the consistent one
+bool consistent_mass(const hsim_hier *H) { return H->opts.mass == HSIM_MASS_CONSISTENT; }
+
+// M Y on level tau: diagonal at tau = 0 (lumped mass), CSR otherwise
 void apply_M(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int ldx, double *Y, int ldy) {
     LevelData &L = H->lev[tau];
-    if (tau == 0)
+    if (tau == 0 && !consistent_mass(H))
         k::diag_scale(ctx->stream, L.n, k, H->Md0int.p, X, ldx, Y, ldy);
     else
-        k::spmm(ctx->stream, L.n, L.dpat.ptr.p, L.dpat.col.p, H->Mv[tau].p, k, X, ldx, Y, ldy);
+        k::spmm(ctx->stream, L.n, L.dpat.ptr.p, L.dpat.col.p, tau == 0 ? H->M0int.p : H->Mv[tau].p, k, X, ldx, Y,
+                ldy);
 }
 void apply_S(hsim_ctx *ctx, hsim_hier *H, int tau, int k, const double *X, int ldx, double *Y, int ldy) {
     LevelData &L = H->lev[tau];
@@ -649,7 +654,14 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     H->Md0int.reserve(n0);
     H->dinv0.reserve(n0);
     k::gather_values(s, L0.dpat.nnz, L0.dvmap.p, S_val, H->S0int.p);
-    if (T > 1 || !L0.dense) {
+    const bool cm = consistent_mass(H);
+    if (cm) {
+        // consistent M^0 in S's pattern; its row sums are the lumped mass M_L,
+        // whose inverse bounds the M^-1-norms of the convergence test
+        H->M0int.reserve(L0.dpat.nnz);
+        k::gather_values(s, L0.dpat.nnz, L0.dvmap.p, M_diag, H->M0int.p);
+        k::row_sums(s, n0, L0.dpat.ptr.p, H->M0int.p, H->Md0int.p);
+    } else if (T > 1 || !L0.dense) {
         k::gather_values_i(s, n0, L0.dense ? nullptr : L0.d_perm.p, M_diag, H->Md0int.p);
     }
     H->Sv.resize(T);
@@ -664,12 +676,12 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         const double *Sf = tau == 0 ? H->S0int.p : H->Sv[tau].p;
         k::galerkin_au(s, Lf.n, Lf.dpat.ptr.p, Lf.dpat.col.p, Sf, P.dU.ptr.p, P.dU.col.p, P.dUval.p, P.dT.ptr.p,
                        P.dT.col.p, H->tval_s.p);
-        if (tau == 0)
+        if (tau == 0 && !cm)
             k::galerkin_au(s, Lf.n, H->d_diag_ptr.p, H->d_diag_col.p, H->Md0int.p, P.dU.ptr.p, P.dU.col.p, P.dUval.p,
                            P.dT.ptr.p, P.dT.col.p, H->tval_m.p);
         else
-            k::galerkin_au(s, Lf.n, Lf.dpat.ptr.p, Lf.dpat.col.p, H->Mv[tau].p, P.dU.ptr.p, P.dU.col.p, P.dUval.p,
-                           P.dT.ptr.p, P.dT.col.p, H->tval_m.p);
+            k::galerkin_au(s, Lf.n, Lf.dpat.ptr.p, Lf.dpat.col.p, tau == 0 ? H->M0int.p : H->Mv[tau].p, P.dU.ptr.p,
+                           P.dU.col.p, P.dUval.p, P.dT.ptr.p, P.dT.col.p, H->tval_m.p);
         H->Sv[tau + 1].reserve(Lc.dpat.nnz);
         H->Mv[tau + 1].reserve(Lc.dpat.nnz);
         k::galerkin_utt(s, Lc.n, P.dUt.ptr.p, P.dUt.col.p, P.dUtval.p, P.dT.ptr.p, P.dT.col.p, H->tval_s.p,
@@ -688,7 +700,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         H->Mbar.reserve((size_t)nc * nc);
         if (T == 1) {
             k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->S0int.p, H->Sbar.p);
-            k::densify_diag(s, nc, M_diag, H->Mbar.p);
+            if (cm) k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->M0int.p, H->Mbar.p);
+            else k::densify_diag(s, nc, M_diag, H->Mbar.p);
         } else {
             k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Sv[T - 1].p, H->Sbar.p);
             k::densify(s, nc, Lc.dpat.ptr.p, Lc.dpat.col.p, H->Mv[T - 1].p, H->Mbar.p);
@@ -770,8 +783,8 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
         }
         inf.shift[tau] = mu;
         const double *Sx = tau == 0 ? H->S0int.p : H->Sv[tau].p;
-        const double *Mx = tau == 0 ? nullptr : H->Mv[tau].p;
-        const double *Mdx = tau == 0 ? H->Md0int.p : nullptr;
+        const double *Mx = tau == 0 ? (cm ? H->M0int.p : nullptr) : H->Mv[tau].p;
+        const double *Mdx = (tau == 0 && !cm) ? H->Md0int.p : nullptr;
         Timer tf(s);
         int negp = mixed ? factor_level_t<float>(ctx, L, Sx, Mx, Mdx, mu, H->arena32, H->dpos32, H->dinvf32, H->invs32, 1e-7)
                          : factor_level(ctx, H, L, Sx, Mx, Mdx, mu);
@@ -803,7 +816,10 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                          n, q, mu, negp, L.fs.n_nodes, (long long)L.fs.nnz_L);
         inf.factor_nnz[tau] = L.fs.nnz_L;
         inf.factor_flops[tau] = L.fs.flops;
-        // 1 / diag(M) for the M^-1 norm of the finest level (Sec. 5, termination criterion)
+        // 1 / diag(M) for the M^-1 norm of the finest level (Sec. 5, termination
+        // criterion); with the consistent M, 1 / diag(M_L) of the lumped mass and
+        // twice the resulting ratio (M_L / 4 <= M <= M_L bounds the exact norms)
+        const double norm_bound = (tau == 0 && cm) ? 2.0 : 1.0;
         const double *dinv = nullptr;
         if (tau == 0) {
             H->dinv0.reserve(n);
@@ -835,7 +851,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
                 for (int extra = 1; extra < o.inv_iters; ++extra) {
                     double *Pa = H->Psi.p + locked;
                     apply_S(ctx, H, tau, a, Pa, q, H->SP.p + locked, q);
-                    if (tau == 0) {
+                    if (tau == 0 && !cm) {
                         // diagonal M: M Psi enters only through m_i psi_i (MP is
                         // recomputed for the Gram below)
                         k::col_dots2_diag_mixed(s, n, a, Pa, q, H->SP.p + locked, q, H->Md0int.p, H->rho.p,
@@ -946,7 +962,7 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             maxres = 0.0;
             for (int i = 0; i < p; ++i) {
                 double den = std::max(std::sqrt(rs[3 * i + 1]), lam_ref * std::sqrt(rs[3 * i + 2]));
-                res[i] = std::sqrt(rs[3 * i]) / den;
+                res[i] = norm_bound * std::sqrt(rs[3 * i]) / den;
                 maxres = std::max(maxres, res[i]);
             }
             if (trace_on())
@@ -1129,6 +1145,8 @@ hsim_options checked(const hsim_options *o) {
                    "unknown boundary condition");
     HSIM_CHECK_ARG(r.plain_sim == 0 || r.plain_sim == 1, "plain_sim must be 0 or 1");
     HSIM_CHECK_ARG(std::isfinite(r.sim_shift), "sim_shift must be finite");
+    HSIM_CHECK_ARG(r.mass == HSIM_MASS_LUMPED || r.mass == HSIM_MASS_CONSISTENT, "unknown mass matrix");
+    HSIM_CHECK_ARG(r.plain_sim == 0 || r.mass == HSIM_MASS_LUMPED, "plain SIM takes the lumped mass matrix");
     return r;
 }
 
@@ -1157,6 +1175,7 @@ void hsim_default_options(hsim_options *o) {
     o->plain_sim = 0;
     o->sim_shift = 0.0;
     o->seed = 0;
+    o->mass = HSIM_MASS_LUMPED;
 }
 
 void hsim_random_column(int n, uint64_t seed, double *out) {
@@ -1269,18 +1288,20 @@ hsim_status hsim_assemble(hsim_ctx *ctx, const hsim_hier *h, const double *V_dev
         check_device_ptrs(ctx->device, {{"V", V_dev}, {"L2", L2_dev}, {"S_val", S_val}, {"M_diag", M_diag}});
         cudaStream_t s = ctx->stream;
         DevBuf<double> cot((size_t)3 * h->m), area((size_t)h->m), Sm, Mm;
+        const bool cm = consistent_mass(h);
         k::triangle_geometry(s, h->m, h->dF.p, V_dev, L2_dev, cot.p, area.p);
         if (h->dofs.empty()) {
             k::assemble_sm(s, h->n, h->pat0.ptr.p, h->pat0.col.p, h->d_ecot.p, cot.p, h->d_vt_ptr.p, h->d_vt_idx.p,
-                           area.p, S_val, M_diag);
+                           area.p, S_val, M_diag, cm);
         } else {
             // Dirichlet: the whole mesh, then the interior rows and columns
             Sm.alloc((size_t)h->patm.nnz);
-            Mm.alloc((size_t)h->n_mesh);
+            Mm.alloc(cm ? (size_t)h->patm.nnz : (size_t)h->n_mesh);
             k::assemble_sm(s, h->n_mesh, h->patm.ptr.p, h->patm.col.p, h->d_ecot.p, cot.p, h->d_vt_ptr.p,
-                           h->d_vt_idx.p, area.p, Sm.p, Mm.p);
+                           h->d_vt_idx.p, area.p, Sm.p, Mm.p, cm);
             k::gather_values(s, h->pat0.nnz, h->d_smap.p, Sm.p, S_val);
-            k::gather_values_i(s, h->n, h->d_dofs.p, Mm.p, M_diag);
+            if (cm) k::gather_values(s, h->pat0.nnz, h->d_smap.p, Mm.p, M_diag);
+            else k::gather_values_i(s, h->n, h->d_dofs.p, Mm.p, M_diag);
         }
         HSIM_CUDA(cudaStreamSynchronize(s));  // before the temporaries are freed
     });
@@ -1598,11 +1619,12 @@ hsim_status hsim_shifted_solve(hsim_ctx *ctx, hsim_hier *h, int tau, const doubl
         check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_val", M_val}, {"B", B}});
         cudaStream_t s = ctx->stream;
         LevelData &L = h->lev[tau];
-        DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(tau == 0 ? (size_t)L.n : (size_t)L.dpat.nnz);
+        const bool diag_m = tau == 0 && !consistent_mass(h);  // M_val: n diagonal values, else S's pattern
+        DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(diag_m ? (size_t)L.n : (size_t)L.dpat.nnz);
         k::gather_values(s, L.dpat.nnz, L.dvmap.p, S_val, Sv.p);
-        if (tau == 0) k::gather_values_i(s, L.n, L.d_perm.p, M_val, Mv.p);
+        if (diag_m) k::gather_values_i(s, L.n, L.d_perm.p, M_val, Mv.p);
         else k::gather_values(s, L.dpat.nnz, L.dvmap.p, M_val, Mv.p);
-        int negp = factor_level(ctx, h, L, Sv.p, tau == 0 ? nullptr : Mv.p, tau == 0 ? Mv.p : nullptr, mu);
+        int negp = factor_level(ctx, h, L, Sv.p, diag_m ? nullptr : Mv.p, diag_m ? Mv.p : nullptr, mu);
         DevBuf<double> X((size_t)L.n * kk);
         k::gather_rows(s, L.n, kk, L.d_perm.p, B, ldb, X.p, kk);
         solve_level(ctx, h, L, X.p, kk, kk);
@@ -1623,11 +1645,12 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *h, int tau, const d
         check_device_ptrs(ctx->device, {{"S_val", S_val}, {"M_val", M_val}, {"B", B}});
         cudaStream_t s = ctx->stream;
         LevelData &L = h->lev[tau];
-        DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(tau == 0 ? (size_t)L.n : (size_t)L.dpat.nnz);
+        const bool diag_m = tau == 0 && !consistent_mass(h);  // M_val: n diagonal values, else S's pattern
+        DevBuf<double> Sv((size_t)L.dpat.nnz), Mv(diag_m ? (size_t)L.n : (size_t)L.dpat.nnz);
         k::gather_values(s, L.dpat.nnz, L.dvmap.p, S_val, Sv.p);
-        if (tau == 0) k::gather_values_i(s, L.n, L.d_perm.p, M_val, Mv.p);
+        if (diag_m) k::gather_values_i(s, L.n, L.d_perm.p, M_val, Mv.p);
         else k::gather_values(s, L.dpat.nnz, L.dvmap.p, M_val, Mv.p);
-        int negp = factor_level_t<float>(ctx, L, Sv.p, tau == 0 ? nullptr : Mv.p, tau == 0 ? Mv.p : nullptr, mu,
+        int negp = factor_level_t<float>(ctx, L, Sv.p, diag_m ? nullptr : Mv.p, diag_m ? Mv.p : nullptr, mu,
                                          h->arena32, h->dpos32, h->dinvf32, h->invs32, 1e-7);
         DevBuf<double> X((size_t)L.n * kk);
         k::gather_rows(s, L.n, kk, L.d_perm.p, B, ldb, X.p, kk);

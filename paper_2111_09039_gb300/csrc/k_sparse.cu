@@ -51,11 +51,15 @@ __global__ void k_triangle_geometry(int m, const int *__restrict__ F, const doub
         cot[3 * (size_t)t + k] = (l[(k + 1) % 3] + l[(k + 2) % 3] - l[k]) / (4.0 * A);
 }
 
+// ecot[2e], ecot[2e + 1]: corner indices 3 t + k of the (up to two)
+// triangles t that hold edge e (-1 if none).  M: the lumped diagonal (n), or
+// with `consistent` the consistent mass in S's pattern: A_t / 12 per
+// triangle of an edge, A_t / 6 per triangle of the vertex on the diagonal.
 __global__ void k_assemble_sm(int n, const int *__restrict__ ptr, const int *__restrict__ col,
                               const int *__restrict__ ecot, const double *__restrict__ cot,
                               const int *__restrict__ vt_ptr, const int *__restrict__ vt_idx,
                               const double *__restrict__ area, double *__restrict__ S,
-                              double *__restrict__ M) {
+                              double *__restrict__ M, bool consistent) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double diag = 0.0;
@@ -65,18 +69,29 @@ __global__ void k_assemble_sm(int n, const int *__restrict__ ptr, const int *__r
             de = e;
             continue;
         }
-        double c = 0.0;
+        double c = 0.0, me = 0.0;
         int a = ecot[2 * (size_t)e], b = ecot[2 * (size_t)e + 1];
-        if (a >= 0) c += cot[a];
-        if (b >= 0) c += cot[b];
+        if (a >= 0) c += cot[a], me += area[a / 3] / 12.0;
+        if (b >= 0) c += cot[b], me += area[b / 3] / 12.0;
         double v = -0.5 * c;
         S[e] = v;
         diag -= v;
+        if (consistent) M[e] = me;
     }
     if (de >= 0) S[de] = diag;
     double mm = 0.0;
-    for (int e = vt_ptr[i]; e < vt_ptr[i + 1]; ++e) mm += area[vt_idx[e]] / 3.0;
-    M[i] = mm;
+    for (int e = vt_ptr[i]; e < vt_ptr[i + 1]; ++e) mm += area[vt_idx[e]] / (consistent ? 6.0 : 3.0);
+    if (!consistent) M[i] = mm;
+    else if (de >= 0) M[de] = mm;
+}
+
+__global__ void k_row_sums(int n, const int *__restrict__ ptr, const double *__restrict__ val,
+                           double *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int e = ptr[i]; e < ptr[i + 1]; ++e) s += val[e];
+    out[i] = s;
 }
 
 // One warp per row; each lane owns columns lane, lane+32, ...  Up to
@@ -450,9 +465,17 @@ void triangle_geometry(cudaStream_t s, int m, const int *F, const double *V, con
     HSIM_LAUNCHED();
 }
 
+void row_sums(cudaStream_t s, int n, const int *ptr, const double *val, double *out) {
+    if (n <= 0) return;
+    k_row_sums<<<grid1d(n, 256), 256, 0, s>>>(n, ptr, val, out);
+    HSIM_LAUNCHED();
+}
+
 void assemble_sm(cudaStream_t s, int n, const int *ptr, const int *col, const int *ecot, const double *cot,
-                 const int *vt_ptr, const int *vt_idx, const double *area, double *S_val, double *M_diag) {
-    k_assemble_sm<<<grid1d(n, 256), 256, 0, s>>>(n, ptr, col, ecot, cot, vt_ptr, vt_idx, area, S_val, M_diag);
+                 const int *vt_ptr, const int *vt_idx, const double *area, double *S_val, double *M_diag,
+                 bool consistent) {
+    k_assemble_sm<<<grid1d(n, 256), 256, 0, s>>>(n, ptr, col, ecot, cot, vt_ptr, vt_idx, area, S_val, M_diag,
+                                                 consistent);
     HSIM_LAUNCHED();
 }
 

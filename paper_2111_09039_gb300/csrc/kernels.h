@@ -17,10 +17,13 @@ void triangle_geometry(cudaStream_t s, int m, const int *F, const double *V, con
                        double *cot, double *area);
 // S values in a CSR pattern: off-diagonal -1/2 sum of the opposite cotangents
 // listed in ecot (two slots per entry, -1 = none), diagonal = -row sum;
-// M diagonal = sum of incident areas / 3 (vertex -> triangle CSR vt_ptr/vt_idx)
+// M diagonal = sum of incident areas / 3 (vertex -> triangle CSR vt_ptr/vt_idx),
+// or with `consistent` the consistent mass in the same pattern
 void assemble_sm(cudaStream_t s, int n, const int *ptr, const int *col, const int *ecot,
                  const double *cot, const int *vt_ptr, const int *vt_idx, const double *area,
-                 double *S_val, double *M_diag);
+                 double *S_val, double *M_diag, bool consistent);
+// out[i] = sum of row i of a CSR matrix
+void row_sums(cudaStream_t s, int n, const int *ptr, const double *val, double *out);
 // dV = sum_i dloss[i] d lambda_i / dV (k_grad.cu); dV is zeroed first
 void eig_grad(cudaStream_t s, int n, int m, int p, const double *V, const int *F, const double *evals,
               const double *evecs, int ld, const double *dloss, double *dV);
