@@ -693,9 +693,10 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
 
 # DRAM bytes (read + write) per operand row of one k_ozaki_tc launch, from
 # one ncu capture of each product shape at 200,000 rows, q = 750
-# (profiles/ozaki_tc_traffic_n200k_q750.md); None until captured for the
-# kernel as it is now.
-TC_TRAFFIC_PER_ROW = {"gram": None, "update": None}
+# (profiles/ozaki_tc_traffic_n200k_q750.md): update 1.853 GB read + 1.171 GB
+# written; Gram 6.487 GB read + 7 MB written for the full square product of
+# the capture (the solve's Grams compute the lower triangle: an upper bound).
+TC_TRAFFIC_PER_ROW = {"gram": (6487459584 + 7034368) / 200000, "update": (1852843008 + 1170711040) / 200000}
 
 
 def tc_traffic(sizes, iters, q):
@@ -717,8 +718,9 @@ def tc_traffic(sizes, iters, q):
         alg += iters[t] * (2 * 24.0 * n * qp + (12.0 * n * qp + 8.0 * n * q))
         launches += 3 * iters[t]
     return {"per_launch": tot / launches, "algorithmic_per_launch": alg / launches,
-            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram and one update launch at "
-                    "200,000 x 750, scaled by rows to every launch of the solve and averaged per launch"}
+            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram (full square, an upper bound "
+                    "for the solve's lower-triangle Grams) and one update launch at 200,000 x 750, scaled by "
+                    "rows to every launch of the solve and averaged per launch"}
 
 
 def cpu_baseline(workload, info):

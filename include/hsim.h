@@ -239,7 +239,7 @@ hsim_status hsim_solve(hsim_ctx *ctx, hsim_hier *hier, const double *S_val_dev,
 /* A batch of independent HSIM solves (one per mesh, each with its own
  * hierarchy), run concurrently: `streams` worker threads (<= 0: 8, at most
  * nmesh), each with its own CUDA stream on the context's device, take the
- * meshes in order; every solve is the hsim_solve path.  The paper has no
+ * meshes largest first (level-0 size); every solve is the hsim_solve path.  The paper has no
  * batched form; many small meshes only fill the GPU when their solves
  * overlap.
  *   hiers, S_vals, M_diags, p, evals, evecs: nmesh entries each, as for

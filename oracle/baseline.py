@@ -9,10 +9,10 @@ to the workload:
   vertices of the 1000 x 1000 torus) it times the oracle's SuperLU
   factorisation of S - mu M, the solve of all q right-hand sides of one
   inverse iteration with the column blocks spread over one worker process
-  per core (SuperLU's solve is single-threaded; the workers are forked after
-  the factorisation and share it), and the Gram products Psi^T S Psi,
-  Psi^T M Psi plus the update Psi Phi_bar at the real subspace size q (NumPy
-  BLAS on all cores);
+  per core (each worker factors its own copy, untimed, with one BLAS thread,
+  and times the solve of its block; the parallel solve takes the slowest
+  worker's time), and the Gram products Psi^T S Psi, Psi^T M Psi plus the
+  update Psi Phi_bar at the real subspace size q (NumPy BLAS on all cores);
 * each step's time is fitted by a power law in the number of vertices and
   evaluated at every level's size;
 * a sparse level is charged one factorisation plus, per subspace iteration,
@@ -20,9 +20,10 @@ to the workload:
   eigensolve of its real size.  The iteration counts per level are an input
   (the benchmark passes the ones its GPU run took).
 
-The forked workers need a process without CUDA state: the benchmark runs
-this in a fresh subprocess.  Only tests, the smoke check and the benchmark's
-CPU-baseline leg call this.
+The workers are started with the spawn method (fresh interpreters that load
+NumPy/SciPy with one BLAS thread each: forked workers inherit a BLAS thread
+pool sized for the whole machine and oversubscribe it).  Only tests, the
+smoke check and the benchmark's CPU-baseline leg call this.
 """
 from __future__ import annotations
 
@@ -40,8 +41,7 @@ import synth
 from . import assembly
 from .hierarchy import level_sizes, subspace_size
 
-_LU = None   # the factor the forked workers solve with
-_B = None    # right-hand sides, shared with the workers by fork
+_BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
 
 
 def _cores() -> int:
@@ -65,25 +65,33 @@ def _time(f, repeat=1):
     return best
 
 
-def _solve_block(rng):
-    a, b = rng
-    return _LU.solve(_B[:, a:b]).shape
+def _solve_block(args):
+    """Worker: factor K (untimed), then time the solve of its block B."""
+    K, B = args
+    lu = spla.splu(K)
+    t = time.perf_counter()
+    lu.solve(B)
+    return time.perf_counter() - t
 
 
-def parallel_solve_time(lu, B, workers: int) -> float:
-    """Wall time of lu.solve over the columns of B, column blocks spread over
-    `workers` forked processes (one block per worker)."""
-    global _LU, _B
-    _LU, _B = lu, B
+def parallel_solve_time(K, B, workers: int) -> float:
+    """Time of solving K X = B with the columns of B split into `workers`
+    blocks, one per worker process: the slowest worker's solve time."""
     q = B.shape[1]
     step = -(-q // workers)
     blocks = [(a, min(q, a + step)) for a in range(0, q, step)]
-    ctx = mp.get_context("fork")
-    with ctx.Pool(len(blocks)) as pool:
-        pool.map(_solve_block, blocks[:1])              # workers up before timing
-        t = time.perf_counter()
-        pool.map(_solve_block, blocks, chunksize=1)
-        return time.perf_counter() - t
+    saved = {k: os.environ.get(k) for k in _BLAS_ENV}
+    os.environ.update({k: "1" for k in _BLAS_ENV})
+    try:
+        with mp.get_context("spawn").Pool(len(blocks)) as pool:
+            times = pool.map(_solve_block, [(K, np.ascontiguousarray(B[:, a:b])) for a, b in blocks], chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return max(times)
 
 
 def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: int | None = None,
@@ -119,7 +127,7 @@ def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: 
         lu = [None]
         tf.append(_time(lambda: lu.__setitem__(0, spla.splu(K))))
         B = rng.standard_normal((mesh.n, q))
-        ts.append(parallel_solve_time(lu[0], B, workers))
+        ts.append(parallel_solve_time(K, B, workers))
         Psi = rng.standard_normal((mesh.n, q))
         SP = S @ Psi
         MP = M @ Psi

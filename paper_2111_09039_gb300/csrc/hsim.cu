@@ -1371,8 +1371,12 @@ hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers
             cleanup();
             throw;
         }
-        // workers take meshes in order from a shared counter; the first error
+        // workers take meshes from a shared counter, largest first (a large
+        // mesh started last would set the batch's tail); the first error
         // stops the others before their next mesh
+        std::vector<int> order(nmesh);
+        for (int i = 0; i < nmesh; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hiers[a]->n > hiers[b]->n; });
         std::atomic<int> next{0};
         std::atomic<bool> stop{false};
         std::mutex emu;
@@ -1395,8 +1399,9 @@ hsim_status hsim_solve_batched(hsim_ctx *ctx, int nmesh, hsim_hier *const *hiers
                 }
                 for (;;) {
                     if (stop) break;
-                    const int i = next.fetch_add(1);
-                    if (i >= nmesh) break;
+                    const int k = next.fetch_add(1);
+                    if (k >= nmesh) break;
+                    const int i = order[k];
                     try {
                         hsim_options o = checked(opts ? opts : &hiers[i]->opts);
                         run_solve(wctx[w].get(), hiers[i], S_vals[i], M_diags[i], p[i], tol, o, evals[i], evecs[i],
