@@ -171,6 +171,7 @@ def main():
     ap.add_argument("--mesh-nu", type=int, default=0,
                     help="--kernel spmm: an nu x nu bumpy torus instead of the workload's mesh")
     ap.add_argument("--rows", type=int, default=200000)
+    ap.add_argument("--digits", type=int, default=6, choices=[5, 6], help="--kernel gram_tc: digits per value")
     ap.add_argument("--cols", type=int, default=750)
     ap.add_argument("--batch", type=int, default=0,
                     help="time the batched solve of this many seeded meshes (5k-80k vertices, p = 50) "
@@ -323,7 +324,7 @@ def main():
     if rank != 0:
         return
     peaks, peak_src = load_peaks()
-    roof = roofline(info, infos, hier, p, peaks, peak_src, args.precision)
+    roof = roofline(info, infos, hier, p, peaks, peak_src, args.precision, tol)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args.workload, info)
@@ -372,8 +373,7 @@ def run_kernel(args):
         fn = lambda: hs.spmm(ctx, rp, cl, S, A)
         flops, nbytes = 2.0 * S.numel() * q, 16.0 * mesh.n * q + 12.0 * S.numel()
     elif args.kernel in ("gram", "gram_tc"):
-        f = hs.gram if args.kernel == "gram" else hs.gram_tc
-        fn = lambda: f(ctx, A, B)
+        fn = (lambda: hs.gram(ctx, A, B)) if args.kernel == "gram" else (lambda: hs.gram_tc(ctx, A, B, args.digits))
         flops, nbytes = 2.0 * n * q * q, 16.0 * n * q
     elif args.kernel in ("ritz", "ritz_tc"):
         # q x q symmetric S_bar and SPD M_bar with random eigenvectors
@@ -594,7 +594,11 @@ def check_residual(hier, S, Md, lam, Phi, ctx):
     return float((nr / torch.maximum(ns, lref * nm)).max().item())
 
 
-def roofline(info, infos, hier, p, peaks, peak_src, precision):
+# the library's Grams take five digits per value from this tolerance up (six below)
+GRAM_FIVE_DIGIT_TOL = 1e-6
+
+
+def roofline(info, infos, hier, p, peaks, peak_src, precision, tol):
     """Achieved rate against the peak for the kernels of the solve; the
     top-level entry is the kernel of the dominant phase."""
     q = info["q"]
@@ -647,11 +651,13 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
                            if phases["update"] > 0 else 0.0}
         kernels["update"] = kernels["gram"]
     else:
-        # tensor-core products: 21 digit-pair products (6 digits, pairs s+t <= 5)
-        # of 2 n q(q+1)/2 BF16 flops for each symmetric Gram (two per
-        # iteration) and 2 n q^2 for the update, timed without the digit split
-        pairs = 21
-        tc_flops = pairs * (2.0 * gram_flops / 2.0 + upd_flops)
+        # tensor-core products: digit-pair products (d digits: pairs s + t < d,
+        # d (d + 1) / 2 of them) of 2 n q(q+1)/2 BF16 flops for each symmetric
+        # Gram (two per iteration; 5 digits at tol >= 1e-6, else 6) and 21 of
+        # 2 n q^2 for the update, timed without the digit split
+        gd = 5 if tol >= GRAM_FIVE_DIGIT_TOL else 6
+        gram_pairs, upd_pairs = gd * (gd + 1) // 2, 21
+        tc_flops = gram_pairs * gram_flops + upd_pairs * upd_flops
         ms_tc = avg("ms_tc_product")
         peak = peaks.get("bf16_tflops_sustained", 1743.3)
         ach = tc_flops / (ms_tc * 1e-3) / 1e12 if ms_tc > 0 else 0.0
@@ -673,13 +679,14 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
         ms_tc = top["ms_per_step"]
         fp64_eq = top["fp64_equivalent_tflops"]
         top["bf16_pipe"] = {"achieved": top["achieved"], "frac": top["frac"], "unit": "TFLOP/s",
-                            "note": "21 BF16 digit-pair products per FP64 product (emulation work)"}
+                            "note": f"{gram_pairs} (Grams) and {upd_pairs} (update) BF16 digit-pair products "
+                                    "per FP64 product (emulation work)"}
         top["achieved"] = fp64_eq
         top["frac"] = fp64_eq / top["peak"]
         top["work"] = ("method FLOPs: FP64 products of the Grams Psi^T [S Psi | M Psi] (n q (q+1) each, lower "
                        "triangles) and the update Psi Phi_bar (2 n q^2) of every subspace iteration")
         top["traffic"] = None
-        tr = tc_traffic(sizes, iters, q)
+        tr = tc_traffic(sizes, iters, q, gd)
         if tr is not None:
             top["traffic"] = tr["per_launch"]
             top["traffic_note"] = tr["note"]
@@ -693,13 +700,14 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision):
 
 # DRAM bytes (read + write) per operand row of one k_ozaki_tc launch, from
 # one ncu capture of each product shape at 200,000 rows, q = 750
-# (profiles/ozaki_tc_traffic_n200k_q750.md): update 1.853 GB read + 1.171 GB
-# written; Gram 6.487 GB read + 7 MB written for the full square product of
-# the capture (the solve's Grams compute the lower triangle: an upper bound).
-TC_TRAFFIC_PER_ROW = {"gram": (6487459584 + 7034368) / 200000, "update": (1852843008 + 1170711040) / 200000}
+# (profiles/ozaki_tc_traffic_n200k_q750.md): update (6 digits) 1.853 GB read +
+# 1.171 GB written; Gram with the solve's 5 digits 3.669 GB read + 3 MB written
+# for the full square product of the capture (the solve's Grams compute the
+# lower triangle: an upper bound).
+TC_TRAFFIC_PER_ROW = {"gram": (3668899840 + 2990336) / 200000, "update": (1852843008 + 1170711040) / 200000}
 
 
-def tc_traffic(sizes, iters, q):
+def tc_traffic(sizes, iters, q, gram_digits=6):
     """Per-launch DRAM traffic of k_ozaki_tc over one solve, scaled from the
     200,000-row captures by the rows each launch processes (traffic grows in
     proportion to the rows), against the algorithmic bytes (the BF16 digit
@@ -713,14 +721,14 @@ def tc_traffic(sizes, iters, q):
         n = sizes[t]
         # two Grams (Psi against S Psi, Psi against M Psi) and one update per iteration
         tot += iters[t] * (2 * TC_TRAFFIC_PER_ROW["gram"] * n + TC_TRAFFIC_PER_ROW["update"] * n)
-        # Gram: both operands' slices (2 x 12 bytes per value); update: Psi's
-        # slices plus the FP64 output Phi
-        alg += iters[t] * (2 * 24.0 * n * qp + (12.0 * n * qp + 8.0 * n * q))
+        # Gram: both operands' slices (2 x 2 d bytes per value); update: Psi's
+        # six slices plus the FP64 output Phi
+        alg += iters[t] * (2 * 4.0 * gram_digits * n * qp + (12.0 * n * qp + 8.0 * n * q))
         launches += 3 * iters[t]
     return {"per_launch": tot / launches, "algorithmic_per_launch": alg / launches,
-            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one Gram (full square, an upper bound "
-                    "for the solve's lower-triangle Grams) and one update launch at 200,000 x 750, scaled by "
-                    "rows to every launch of the solve and averaged per launch"}
+            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 5-digit Gram (full square, an "
+                    "upper bound for the solve's lower-triangle Grams) and one 6-digit update launch at "
+                    "200,000 x 750, scaled by rows to every launch of the solve and averaged per launch"}
 
 
 def cpu_baseline(workload, info):

@@ -91,7 +91,8 @@ typedef struct {
                             FP64 bases (hsim_shifted_solve_f32); Gram products,
                             basis update and the Ritz transforms on BF16 tensor
                             cores with FP64-accurate digit splitting
-                            (hsim_gram_tc, hsim_ritz_tc); dense eigensolver and
+                            (hsim_gram_tc, hsim_ritz_tc; the Grams with 5 digits
+                            per value at tol >= 1e-6); dense eigensolver and
                             residual vectors FP64 (sums of squares of the
                             convergence test accumulated in FP32 per row block) */
     int start_vertex;    /* first vertex of farthest-point sampling (Alg. 2) */
@@ -309,9 +310,11 @@ hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int k, int m, const double *A
  * per row or column into 6 integer digits of at most 8 bits, digit products
  * are accumulated exactly in FP32 over chunks of 128 and summed in FP64; the
  * result matches the FP64 product to about 2^-47 of the row/column maxima.
+ * hsim_gram_tc takes `digits` = 6 (that accuracy) or 5 (2^-39, 15 digit
+ * products instead of 21; the solve's Grams at tolerances >= 1e-6).
  * Arguments as hsim_gram and hsim_gemm_update (G is ka x kb, ld kb). */
 hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int k_a, int k_b, const double *A_dev, int lda,
-                         const double *B_dev, int ldb, double *G_dev);
+                         const double *B_dev, int ldb, double *G_dev, int digits);
 hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int k, int m, const double *A_dev, int lda,
                                 const double *B_dev, int ldb, double *C_dev, int ldc);
 

@@ -354,14 +354,15 @@ def gram(ctx: Context, A, B):
     return G
 
 
-def gram_tc(ctx: Context, A, B):
-    """A^T B with FP64 accuracy on BF16 tensor cores (digit splitting)."""
+def gram_tc(ctx: Context, A, B, digits: int = 6):
+    """A^T B on BF16 tensor cores by digit splitting: 6 digits per value (FP64
+    accuracy) or 5."""
     torch = _torch()
     _rows_on_device(A, "A", ctx.device)
     _rows_on_device(B, "B", ctx.device, A.shape[0])
     G = torch.empty((A.shape[1], B.shape[1]), dtype=torch.float64, device=A.device)
     check(lib().hsim_gram_tc(ctx.handle, A.shape[0], A.shape[1], B.shape[1], ptr(A), A.stride(0), ptr(B),
-                             B.stride(0), ptr(G)))
+                             B.stride(0), ptr(G), int(digits)))
     return G
 
 

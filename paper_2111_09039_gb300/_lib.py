@@ -89,7 +89,7 @@ _SIGS = {
     "hsim_spmm": (I, [P, I, I, P, P, P, I, P, I, P, I]),
     "hsim_gram": (I, [P, I, I, I, P, I, P, I, P]),
     "hsim_gemm_update": (I, [P, I, I, I, P, I, P, I, P, I]),
-    "hsim_gram_tc": (I, [P, I, I, I, P, I, P, I, P]),
+    "hsim_gram_tc": (I, [P, I, I, I, P, I, P, I, P, I]),
     "hsim_gemm_update_tc": (I, [P, I, I, I, P, I, P, I, P, I]),
     "hsim_ritz": (I, [P, I, P, P, P, P, P]),
     "hsim_ritz_tc": (I, [P, I, P, P, P, P, P]),

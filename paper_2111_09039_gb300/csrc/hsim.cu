@@ -211,6 +211,8 @@ namespace {
 // +8 ms) and stay on the CUDA cores.  HSIM_TC32=0 keeps every FP32 product on
 // the CUDA cores (for comparison; read at every factorisation and solve).
 constexpr int kTcMinPivots = 128, kTcMinFwdPivots = 300;
+// mixed path: the Grams take 5 digits per value at tolerances from this up, 6 below
+constexpr double kGramFiveDigitTol = 1e-6;
 bool tc32_enabled() {
     const char *e = std::getenv("HSIM_TC32");
     return !(e && *e == '0');
@@ -898,12 +900,17 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
             apply_S(ctx, H, tau, q - locked, H->Psi.p + locked, q, H->SP.p + locked, q);
             inf.ms_spmm += (ph[1] = ts.stop());
             if (mixed) {
-                // FP64-accurate Grams on BF16 tensor cores: Psi split once
+                // Grams on BF16 tensor cores, Psi split once.  Gram errors rotate the
+                // Ritz basis inside span(Psi) (the subspace itself is unaffected) and
+                // add about E / lambda_i to the residual of pair i: five digits
+                // (2^-39 of the column maxima) leave ~1e-8 at lambda_q / lambda_1 ~ 10^3,
+                // enough below tolerances of 1e-6 and up; tighter ones take six.
+                const int gd = tol >= kGramFiveDigitTol ? 5 : 6;
                 const size_t part = k::ozaki_cols_scratch(n, q);
                 H->oz.reserve(3 * part);
-                k::OzakiOperand X = k::ozaki_split_cols(s, n, q, H->Psi.p, q, H->oz.p);
-                k::OzakiOperand YS = k::ozaki_split_cols(s, n, q, H->SP.p, q, H->oz.p + part);
-                k::OzakiOperand YM = k::ozaki_split_cols(s, n, q, H->MP.p, q, H->oz.p + 2 * part);
+                k::OzakiOperand X = k::ozaki_split_cols(s, n, q, H->Psi.p, q, H->oz.p, gd);
+                k::OzakiOperand YS = k::ozaki_split_cols(s, n, q, H->SP.p, q, H->oz.p + part, gd);
+                k::OzakiOperand YM = k::ozaki_split_cols(s, n, q, H->MP.p, q, H->oz.p + 2 * part, gd);
                 const double t_split = ts.stop();
                 k::ozaki_product(s, X, YS, X.kp, H->Sbar.p, q, 0, true);
                 k::ozaki_product(s, X, YM, X.kp, H->Mbar.p, q, 0, true);
@@ -1477,15 +1484,17 @@ hsim_status hsim_gemm_update(hsim_ctx *ctx, int n, int kk, int m, const double *
 }
 
 hsim_status hsim_gram_tc(hsim_ctx *ctx, int n, int ka, int kb, const double *A, int lda, const double *B, int ldb,
-                         double *G) {
+                         double *G, int digits) {
     return guard([&] {
         HSIM_CHECK_ARG(ctx && A && B && G, "NULL argument");
         HSIM_CHECK_ARG(n >= 1 && ka >= 1 && kb >= 1 && lda >= ka && ldb >= kb, "bad sizes");
+        HSIM_CHECK_ARG(digits == 5 || digits == 6, "digits must be 5 or 6");
         DeviceGuard dg(ctx->device);
         check_device_ptrs(ctx->device, {{"A", A}, {"B", B}, {"G", G}});
         DevBuf<unsigned char> scratch(k::ozaki_cols_scratch(n, ka) + k::ozaki_cols_scratch(n, kb));
-        k::OzakiOperand X = k::ozaki_split_cols(ctx->stream, n, ka, A, lda, scratch.p);
-        k::OzakiOperand Y = k::ozaki_split_cols(ctx->stream, n, kb, B, ldb, scratch.p + k::ozaki_cols_scratch(n, ka));
+        k::OzakiOperand X = k::ozaki_split_cols(ctx->stream, n, ka, A, lda, scratch.p, digits);
+        k::OzakiOperand Y =
+            k::ozaki_split_cols(ctx->stream, n, kb, B, ldb, scratch.p + k::ozaki_cols_scratch(n, ka), digits);
         k::ozaki_product(ctx->stream, X, Y, X.kp, G, kb, 0);
         k::ozaki_check(ctx->stream);
     });

@@ -4,15 +4,16 @@
 // update Phi = Psi Phi_bar of Alg. 1 are the dominant dense work of the
 // subspace iteration; in FP64 they run at the GB300's 1.2 TFLOP/s FP64 rate.
 // Here each FP64 operand is split, against one power of two per row (or per
-// column), into kSlices integer digits of at most 8 bits,
+// column), into SL integer digits of at most 8 bits (SL = 6, or 5 where 39
+// bits suffice),
 //     x = 2^(e-7) * sum_s d_s 2^(-8 s),   |d_0| <= 128, |d_s| <= 128,
 // which BF16 represents exactly.  A digit product is an integer of at most
 // 2^14, so up to 1024 of them sum exactly in an FP32 accumulator: the tensor
 // cores compute sum_r d_s(x_ir) d_t(y_jr) with no rounding, grouped by
-// D = s + t (pairs with D >= kSlices are dropped), over K-chunks of 128, and
+// D = s + t (pairs with D >= SL are dropped), over K-chunks of 128, and
 // every chunk is flushed into FP32 TwoSum pairs.  The result equals the FP64
-// product up to the dropped tail, about 2^-47 of max|x_i.| max|y_j.| per
-// term.
+// product up to the dropped tail, about 2^-(8 SL - 1) of max|x_i.| max|y_j.|
+// per term (2^-47 with six digits).
 //
 // Kernel shape: C (FP64, M x N) (+)= X Y^T with X (M x K) and Y (N x K) both
 // K-contiguous digit slices, on the tcgen05 tensor cores (TMA-fed shared
@@ -32,7 +33,7 @@ namespace k {
 
 namespace {
 
-constexpr int kSlices = kOzakiSlices;
+constexpr int kSlices = kOzakiSlices;  // the most digits an operand holds (scratch sizing)
 constexpr int TKs = 32;      // K padding of the digit slices (one pipeline stage)
 constexpr int kFlush = 128;  // K rows per exact FP32 chunk
 
@@ -71,17 +72,19 @@ __global__ void k_col_exps(int R, int C, const double *__restrict__ X, int ldx, 
     }
 }
 
-// Digits of x against the group exponent e (|x| < 2^e): T = round(x 2^(47-e))
-// as an integer (|T| <= 2^47, ties to even), written in balanced base 256,
-//     T = sum_s d_s 2^(8 (5 - s)),  d_1..d_5 in [-128, 127],  |d_0| <= 128,
-// so x = 2^(e-7) sum_s d_s 2^(-8 s) up to 2^(e-48).
+// Digits of x against the group exponent e (|x| < 2^e): T = round(x 2^(B-e)),
+// B = 8 SL - 1, as an integer (|T| <= 2^B, ties to even), written in balanced
+// base 256,
+//     T = sum_s d_s 2^(8 (SL - 1 - s)),  d_1..d_{SL-1} in [-128, 127],  |d_0| <= 128,
+// so x = 2^(e-7) sum_s d_s 2^(-8 s) up to 2^(e-B-1).
+template <int SL>
 __device__ __forceinline__ void split_value(double x, int e, __nv_bfloat16 *out, size_t stride) {
     const long long bits = __double_as_longlong(x);
     int E = (int)((bits >> 52) & 0x7FF);
     long long M = bits & 0xFFFFFFFFFFFFFLL;
     if (E == 0) E = 1;
     else M |= 1LL << 52;
-    const int sh = E - 1075 + 47 - e;  // x 2^(47-e) = +-M 2^sh, sh <= -6 when |x| < 2^e
+    const int sh = E - 1075 + (8 * SL - 1) - e;  // x 2^(B-e) = +-M 2^sh, sh <= B - 53 when |x| < 2^e
     long long T = 0;
     if (M != 0 && sh > -54) {
         if (sh >= 0) {
@@ -96,7 +99,7 @@ __device__ __forceinline__ void split_value(double x, int e, __nv_bfloat16 *out,
     }
     if (bits < 0) T = -T;
 #pragma unroll
-    for (int s = kSlices - 1; s >= 1; --s) {
+    for (int s = SL - 1; s >= 1; --s) {
         int d = (int)(T & 255);
         if (d >= 128) d -= 256;
         out[(size_t)s * stride] = __int2bfloat16_rn(d);
@@ -107,37 +110,40 @@ __device__ __forceinline__ void split_value(double x, int e, __nv_bfloat16 *out,
 
 // Global layout of the digit slices ("tiled"): for K-chunk kc = k / 32,
 // slice s, row r (rows padded to rows_p, a multiple of 128) and k,
-//     offset = ((kc * kSlices + s) * rows_p + 8 (r / 8)) * 32 + 64 ((k % 32) / 8)
+//     offset = ((kc * SL + s) * rows_p + 8 (r / 8)) * 32 + 64 ((k % 32) / 8)
 //              + 8 (r % 8) + k % 8     (BF16 elements),
 // i.e. 8 x 8 core matrices (8 rows x 16 bytes) ordered [kc][s][r/8][k%32/8].
 // A 32-deep K step of any 128 (or 64) consecutive rows of one slice is then
 // one contiguous 8 KB (4 KB) block that a bulk copy moves straight into the
 // core-matrix order the tensor-core descriptors read.
+template <int SL>
 __device__ __forceinline__ size_t tiled_off(int s, int r, int k, int rows_p) {
-    return (((size_t)(k >> 5) * kSlices + s) * (size_t)rows_p + (size_t)(r & ~7)) * 32 + (size_t)((k & 31) >> 3) * 64 +
+    return (((size_t)(k >> 5) * SL + s) * (size_t)rows_p + (size_t)(r & ~7)) * 32 + (size_t)((k & 31) >> 3) * 64 +
            (size_t)(r & 7) * 8 + (size_t)(k & 7);
 }
 
 // digits of the 8 values v[0..7] (consecutive k of one row, exponent e) as
 // one 16-byte vector per slice
+template <int SL>
 __device__ __forceinline__ void split8_store(const double (&v)[8], int e, __nv_bfloat16 *out, size_t off,
                                              int rows_p) {
-    __nv_bfloat16 d[kSlices][8];
+    __nv_bfloat16 d[SL][8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        __nv_bfloat16 one[kSlices];
-        split_value(v[t], e, one, 1);
+        __nv_bfloat16 one[SL];
+        split_value<SL>(v[t], e, one, 1);
 #pragma unroll
-        for (int sl = 0; sl < kSlices; ++sl) d[sl][t] = one[sl];
+        for (int sl = 0; sl < SL; ++sl) d[sl][t] = one[sl];
     }
     const size_t slice_step = (size_t)rows_p * 32;  // next slice within the same K-chunk
 #pragma unroll
-    for (int sl = 0; sl < kSlices; ++sl)
+    for (int sl = 0; sl < SL; ++sl)
         *reinterpret_cast<uint4 *>(out + off + sl * slice_step) = *reinterpret_cast<const uint4 *>(d[sl]);
 }
 
 // split a row-major R x K block per row (K = columns): one thread per row and
 // 8-wide K group; a warp covers one 8-row group x one 32-deep K-chunk
+template <int SL>
 __global__ void k_split_rows_tiled(int R, int K, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
                                    __nv_bfloat16 *__restrict__ out, int rows_p, int kp) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -149,12 +155,13 @@ __global__ void k_split_rows_tiled(int R, int K, const double *__restrict__ X, i
     double v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = (r < R && k0 + t < K) ? X[(size_t)r * ldx + k0 + t] : 0.0;
-    split8_store(v, r < R ? ex[r] : -1074, out, tiled_off(0, r, k0, rows_p), rows_p);
+    split8_store<SL>(v, r < R ? ex[r] : -1074, out, tiled_off<SL>(0, r, k0, rows_p), rows_p);
 }
 
 // split a row-major K x C block per column (operand row r = column r, K =
 // rows of X), transposed through shared memory: a block handles 32 columns x
 // a 32-deep K-chunk
+template <int SL>
 __global__ void k_split_cols_tiled(int K, int C, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
                                    __nv_bfloat16 *__restrict__ out, int rows_p) {
     __shared__ double tile[32][33];
@@ -172,7 +179,7 @@ __global__ void k_split_cols_tiled(int K, int C, const double *__restrict__ X, i
     double v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) v[t] = tile[kg * 8 + t][lc];
-    split8_store(v, r < C ? ex[r] : -1074, out, tiled_off(0, r, kc * 32 + kg * 8, rows_p), rows_p);
+    split8_store<SL>(v, r < C ? ex[r] : -1074, out, tiled_off<SL>(0, r, kc * 32 + kg * 8, rows_p), rows_p);
 }
 
 __global__ void k_fill_int(int n, int v, int *__restrict__ x) {
@@ -230,10 +237,11 @@ int sm_count_oz() {
 constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_STAGES = 3;
 constexpr int TC_THREADS = 320, TC_DRAIN = 256;  // 10 warps, 8 of them drain TMEM
 constexpr int TC_KG = TC_K / 8;
-constexpr uint32_t TC_A_BYTES = 16u * TC_M * kSlices * TC_KG;  // 49,152
-constexpr uint32_t TC_B_BYTES = 16u * TC_N * kSlices * TC_KG;  // 24,576
-constexpr uint32_t TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;  // + alignment slack
+// stage sizes for SL digit slices: X 128 rows, Y 64 rows (SL = 6: 49,152 + 24,576 bytes)
+template <int SL> __host__ __device__ constexpr uint32_t tc_a_bytes() { return 16u * TC_M * SL * TC_KG; }
+template <int SL> __host__ __device__ constexpr uint32_t tc_b_bytes() { return 16u * TC_N * SL * TC_KG; }
+template <int SL> __host__ __device__ constexpr uint32_t tc_stage_bytes() { return tc_a_bytes<SL>() + tc_b_bytes<SL>(); }
+template <int SL> constexpr size_t tc_smem() { return (size_t)TC_STAGES * tc_stage_bytes<SL>() + 1024; }
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s per barrier wait
 
@@ -318,6 +326,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
+template <int SL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_ozaki_tc(int M, int N, const __nv_bfloat16 *__restrict__ Xs, int rows_px, const __nv_bfloat16 *__restrict__ Ys,
                int rows_py, const int *__restrict__ ex, const int *__restrict__ ey, double *__restrict__ C, int ldc,
@@ -364,16 +373,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (kt >= TC_STAGES) ok = mbar_wait(smem_addr(&empty_bar[st]), ((kt / TC_STAGES) & 1) ^ 1);
                 if (!ok) break;
                 const uint32_t fb = smem_addr(&full_bar[st]);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(TC_STAGE_BYTES)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(tc_stage_bytes<SL>())
                              : "memory");
-                const uint32_t a_dst = smem0 + st * TC_STAGE_BYTES;
+                const uint32_t a_dst = smem0 + st * tc_stage_bytes<SL>();
                 const size_t kc = (size_t)(k_beg + kt * TC_K) / TC_K;
 #pragma unroll 1
-                for (int sl = 0; sl < kSlices; ++sl) {
-                    bulk_load(a_dst + sl * (TC_A_BYTES / kSlices),
-                              Xs + ((kc * kSlices + sl) * rows_px + i0) * TC_K, TC_A_BYTES / kSlices, fb);
-                    bulk_load(a_dst + TC_A_BYTES + sl * (TC_B_BYTES / kSlices),
-                              Ys + ((kc * kSlices + sl) * rows_py + j0) * TC_K, TC_B_BYTES / kSlices, fb);
+                for (int sl = 0; sl < SL; ++sl) {
+                    bulk_load(a_dst + sl * (tc_a_bytes<SL>() / SL),
+                              Xs + ((kc * SL + sl) * rows_px + i0) * TC_K, tc_a_bytes<SL>() / SL, fb);
+                    bulk_load(a_dst + tc_a_bytes<SL>() + sl * (tc_b_bytes<SL>() / SL),
+                              Ys + ((kc * SL + sl) * rows_py + j0) * TC_K, tc_b_bytes<SL>() / SL, fb);
                 }
                 issued = kt + 1;
             }
@@ -394,15 +403,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (ok && chunk_first && chunk > 0) ok = mbar_wait(smem_addr(&acce_bar), (chunk - 1) & 1);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t a_base = smem0 + st * TC_STAGE_BYTES, b_base = a_base + TC_A_BYTES;
+                const uint32_t a_base = smem0 + st * tc_stage_bytes<SL>(), b_base = a_base + tc_a_bytes<SL>();
 #pragma unroll
                 for (int k16 = 0; k16 < TC_K / 16; ++k16) {
                     const uint32_t a_k = a_base + 2 * k16 * LBO, b_k = b_base + 2 * k16 * LBO;
 #pragma unroll
-                    for (int sl = 0; sl < kSlices; ++sl) {
-                        const uint64_t ad = umma_desc(a_k + sl * (TC_A_BYTES / kSlices), LBO, SBO);
+                    for (int sl = 0; sl < SL; ++sl) {
+                        const uint64_t ad = umma_desc(a_k + sl * (tc_a_bytes<SL>() / SL), LBO, SBO);
                         const int acc = (chunk_first && k16 == 0 && sl == 0) ? 0 : 1;
-                        const int ncols = TC_N * (kSlices - sl);  // Y_0 .. Y_{5-s}
+                        const int ncols = TC_N * (SL - sl);  // Y_0 .. Y_{SL-1-s}
                         const int n1 = ncols > 256 ? 256 : ncols;
                         umma_f16(tmem + TC_N * sl, ad, umma_desc(b_k, LBO, SBO), umma_idesc(TC_M, n1), acc);
                         if (ncols > 256)  // rows 256.. of [Y_0 .. Y_5]: 32 row groups further
@@ -431,7 +440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-            for (int d = 0; d < kSlices; ++d) {
+            for (int d = 0; d < SL; ++d) {
                 const float w = __int_as_float((127 - 8 * d) << 23);  // 2^(-8 d), exact
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + TC_N * d + c0, r);
@@ -467,6 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
+template <int SL>
 void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int rows_px, const __nv_bfloat16 *Ys,
                int rows_py, const int *ex, const int *ey, double *C, int ldc, int k_len, int splits, int lower) {
     auto aligned16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
@@ -474,12 +484,12 @@ void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int rows_p
                        N <= rows_py && k_len % TC_K == 0,
                    "ozaki product: operand layout not supported");
     HSIM_CHECK_ARG(!lower || M == N, "ozaki product: lower triangle needs a square result");
-    HSIM_SMEM_LIMIT_ONCE(k_ozaki_tc, TC_SMEM);
+    HSIM_SMEM_LIMIT_ONCE(k_ozaki_tc<SL>, tc_smem<SL>());
     int k_split = (int)((k_len + splits - 1) / splits);
     k_split = (k_split + kFlush - 1) / kFlush * kFlush;
     splits = (int)cdiv(k_len, k_split);
     dim3 g(cdiv(N, TC_N), cdiv(M, TC_M), (unsigned)splits);
-    k_ozaki_tc<<<g, TC_THREADS, TC_SMEM, s>>>(M, N, Xs, rows_px, Ys, rows_py, ex, ey, C, ldc, k_len, k_split,
+    k_ozaki_tc<SL><<<g, TC_THREADS, tc_smem<SL>(), s>>>(M, N, Xs, rows_px, Ys, rows_py, ex, ey, C, ldc, k_len, k_split,
                                                splits > 1 ? 1 : 0, lower);
     HSIM_LAUNCHED();
 }
@@ -488,7 +498,7 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// Scratch: kSlices x rows_p x kp BF16 digits (tiled layout) then rows_p
+// Scratch: (up to) kSlices x rows_p x kp BF16 digits (tiled layout) then rows_p
 // exponents, rounded to whole 256-byte blocks so operands placed back to back
 // in one buffer stay aligned for the bulk copies.
 static size_t operand_bytes(int rows, int kdim) {
@@ -500,36 +510,44 @@ static size_t operand_bytes(int rows, int kdim) {
 size_t ozaki_cols_scratch(int n, int cols) { return operand_bytes(cols, n); }
 size_t ozaki_rows_scratch(int rows, int k) { return operand_bytes(rows, k); }
 
-static OzakiOperand make_operand(int rows, int kdim, void *scratch) {
+static OzakiOperand make_operand(int rows, int kdim, void *scratch, int digits) {
+    HSIM_CHECK_ARG(digits == 5 || digits == 6, "ozaki product: 5 or 6 digits per value");
     OzakiOperand op;
+    op.digits = digits;
     op.rows = rows;
     op.rows_p = round_up(std::max(rows, 1), TC_M);
     op.kp = round_up(std::max(kdim, 1), TKs);
     op.slices = static_cast<__nv_bfloat16 *>(scratch);
-    op.exps = reinterpret_cast<int *>(op.slices + (size_t)kSlices * op.rows_p * op.kp);
+    op.exps = reinterpret_cast<int *>(op.slices + (size_t)digits * op.rows_p * op.kp);
     return op;
 }
 
-OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch) {
-    OzakiOperand op = make_operand(cols, n, scratch);
+OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch, int digits) {
+    OzakiOperand op = make_operand(cols, n, scratch, digits);
     if (n <= 0 || cols <= 0) return op;
     k_fill_int<<<cdiv(cols, 256), 256, 0, s>>>(cols, -1074, op.exps);
     HSIM_LAUNCHED();
     k_col_exps<<<dim3(cdiv(n, 256), cdiv(cols, 256)), 256, 0, s>>>(n, cols, X, ldx, op.exps);
     HSIM_LAUNCHED();
-    k_split_cols_tiled<<<dim3(op.kp / 32, cdiv(op.rows_p, 32)), 128, 0, s>>>(n, cols, X, ldx, op.exps, op.slices,
-                                                                          op.rows_p);
+    const dim3 g(op.kp / 32, cdiv(op.rows_p, 32));
+    if (digits == 5) k_split_cols_tiled<5><<<g, 128, 0, s>>>(n, cols, X, ldx, op.exps, op.slices, op.rows_p);
+    else k_split_cols_tiled<6><<<g, 128, 0, s>>>(n, cols, X, ldx, op.exps, op.slices, op.rows_p);
     HSIM_LAUNCHED();
     return op;
 }
 
-OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch) {
-    OzakiOperand op = make_operand(rows, k, scratch);
+OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch, int digits) {
+    OzakiOperand op = make_operand(rows, k, scratch, digits);
     if (rows <= 0) return op;
     k_row_exps<<<cdiv(rows, 8), 256, 0, s>>>(rows, k, X, ldx, op.exps);
     HSIM_LAUNCHED();
     const int64_t warps = (int64_t)(op.rows_p / 8) * (op.kp / 32);
-    k_split_rows_tiled<<<cdiv(warps * 32, 256), 256, 0, s>>>(rows, k, X, ldx, op.exps, op.slices, op.rows_p, op.kp);
+    if (digits == 5)
+        k_split_rows_tiled<5><<<cdiv(warps * 32, 256), 256, 0, s>>>(rows, k, X, ldx, op.exps, op.slices, op.rows_p,
+                                                                   op.kp);
+    else
+        k_split_rows_tiled<6><<<cdiv(warps * 32, 256), 256, 0, s>>>(rows, k, X, ldx, op.exps, op.slices, op.rows_p,
+                                                                   op.kp);
     HSIM_LAUNCHED();
     return op;
 }
@@ -538,6 +556,7 @@ void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y,
                    int splits, bool lower) {
     if (X.rows <= 0 || Y.rows <= 0) return;
     HSIM_CHECK_ARG(X.kp == Y.kp, "ozaki_product: operands split over different K");
+    HSIM_CHECK_ARG(X.digits == Y.digits, "ozaki_product: operands split into different digit counts");
     if (splits <= 0) {
         // split K so that tiles x splits fills whole waves of one CTA per SM
         const int64_t tx = cdiv(X.rows, TC_M), ty = cdiv(Y.rows, TC_N);
@@ -562,8 +581,12 @@ void ozaki_product(cudaStream_t s, const OzakiOperand &X, const OzakiOperand &Y,
         if (ldc == Y.rows) HSIM_CUDA(cudaMemsetAsync(C, 0, (size_t)X.rows * Y.rows * sizeof(double), s));
         else HSIM_CUDA(cudaMemset2DAsync(C, (size_t)ldc * sizeof(double), 0, (size_t)Y.rows * sizeof(double), X.rows, s));
     }
-    launch_tc(s, X.rows, Y.rows, X.slices, X.rows_p, Y.slices, Y.rows_p, X.exps, Y.exps, C, ldc, X.kp, splits,
-              lower ? 1 : 0);
+    if (X.digits == 5)
+        launch_tc<5>(s, X.rows, Y.rows, X.slices, X.rows_p, Y.slices, Y.rows_p, X.exps, Y.exps, C, ldc, X.kp, splits,
+                     lower ? 1 : 0);
+    else
+        launch_tc<6>(s, X.rows, Y.rows, X.slices, X.rows_p, Y.slices, Y.rows_p, X.exps, Y.exps, C, ldc, X.kp, splits,
+                     lower ? 1 : 0);
 }
 
 void ozaki_check(cudaStream_t s) {

@@ -243,9 +243,10 @@ void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
 constexpr int kOzakiSlices = 6;
 // digit slices of an FP64 block in the tiled layout of k_ozaki.cu: rows
 // padded to rows_p (multiple of 128), K to kp (multiple of 32), zero filled;
-// one exponent per row
+// one exponent per row; `digits` slices of 8 bits (6: 47 bits per value, the
+// FP64-accurate form; 5: 39 bits)
 struct OzakiOperand {
-    int rows = 0, rows_p = 0, kp = 0;
+    int rows = 0, rows_p = 0, kp = 0, digits = kOzakiSlices;
     __nv_bfloat16 *slices = nullptr;
     int *exps = nullptr;
 };
@@ -254,9 +255,11 @@ struct OzakiOperand {
 size_t ozaki_cols_scratch(int n, int cols);
 size_t ozaki_rows_scratch(int rows, int k);
 // split X (row-major, K = n rows) per column into a transposed operand
-OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch);
+OzakiOperand ozaki_split_cols(cudaStream_t s, int n, int cols, const double *X, int ldx, void *scratch,
+                              int digits = kOzakiSlices);
 // split X (row-major rows x k, K = k) per row
-OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch);
+OzakiOperand ozaki_split_rows(cudaStream_t s, int rows, int k, const double *X, int ldx, void *scratch,
+                              int digits = kOzakiSlices);
 // C (X.rows x Y.rows, FP64) = X Y^T over K = k_len (= X.kp); splits <= 0 chooses a
 // split-K count (C accumulated with atomics), 1 stores directly; lower: C is
 // symmetric, only tiles meeting the lower triangle run and the epilogue

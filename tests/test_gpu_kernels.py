@@ -271,21 +271,26 @@ def _values_in(A, rp, cl):
 
 
 # ---- FP64-accurate products on BF16 tensor cores ----------------------------
-def _ozaki_bound(X, Y, K):
-    """K * 2^-45 * (row/col max of |X|) * (row/col max of |Y|): the digit split
-    keeps 47 bits per value relative to its group maximum."""
-    return K * 2.0 ** -45 * np.abs(X).max(axis=1)[:, None] * np.abs(Y).max(axis=1)[None, :]
+def _ozaki_bound(X, Y, K, digits=6):
+    """K * 2^-(8 d - 3) * (row/col max of |X|) * (row/col max of |Y|): the digit
+    split keeps 8 d - 1 bits per value relative to its group maximum (47 with
+    six digits, 39 with five)."""
+    return K * 2.0 ** -(8 * digits - 3) * np.abs(X).max(axis=1)[:, None] * np.abs(Y).max(axis=1)[None, :]
 
 
 @pytest.mark.parametrize("n,ka,kb", [(1, 1, 1), (1000, 30, 30), (4099, 75, 150), (70001, 130, 65)])
-def test_gram_tc_matches_fp64(hs, ctx, n, ka, kb):
+@pytest.mark.parametrize("digits", [6, 5])
+def test_gram_tc_matches_fp64(hs, ctx, n, ka, kb, digits):
     rng = np.random.default_rng(n + 7)
     A = rng.standard_normal((n, ka)) * np.exp(rng.standard_normal((n, 1)))
     B = rng.standard_normal((n, kb))
-    G = hs.gram_tc(ctx, dev(A), dev(B)).cpu().numpy()
+    G = hs.gram_tc(ctx, dev(A), dev(B), digits=digits).cpu().numpy()
     ref = A.T @ B
-    bound = _ozaki_bound(A.T, B.T, n) + 8 * n * EPS * (np.abs(A).T @ np.abs(B))
+    bound = _ozaki_bound(A.T, B.T, n, digits) + 8 * n * EPS * (np.abs(A).T @ np.abs(B))
     assert np.all(np.abs(G - ref) <= bound)
+    if digits == 5:
+        # five digits are not six: the error exceeds the six-digit bound somewhere
+        assert np.any(np.abs(G - ref) > _ozaki_bound(A.T, B.T, n, 6) / n) or n == 1
 
 
 @pytest.mark.parametrize("n,k,m", [(1, 1, 1), (1000, 30, 30), (4099, 75, 75), (20011, 131, 67), (3001, 750, 750)])
@@ -299,13 +304,14 @@ def test_gemm_update_tc_matches_fp64(hs, ctx, n, k, m):
     assert np.all(np.abs(C - ref) <= bound)
 
 
-def test_gram_tc_exact_on_small_integers(hs, ctx):
+@pytest.mark.parametrize("digits", [6, 5])
+def test_gram_tc_exact_on_small_integers(hs, ctx, digits):
     """Integers with few significant bits are represented exactly by the
     digits: the product must equal the exact integer result."""
     rng = np.random.default_rng(5)
     A = rng.integers(-1000, 1000, size=(3000, 40)).astype(np.float64)
     B = rng.integers(-1000, 1000, size=(3000, 24)).astype(np.float64)
-    G = hs.gram_tc(ctx, dev(A), dev(B)).cpu().numpy()
+    G = hs.gram_tc(ctx, dev(A), dev(B), digits=digits).cpu().numpy()
     np.testing.assert_array_equal(G, A.T @ B)
 
 
