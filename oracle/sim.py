@@ -103,12 +103,13 @@ class SimResult:
     history: list = field(default_factory=list)
 
 
-def sim(S, M, Phi, p, eps, mu, finest: bool, max_iters=100, inv_iters=2, lock_factor=0.1):
-    """Alg. 1 with the HSIM refinements of Sec. 4.2."""
+def sim(S, M, Phi, p, eps, mu, finest: bool, max_iters=100, inv_iters=2, lock_factor=0.1, factor=None):
+    """Alg. 1 with the HSIM refinements of Sec. 4.2.  `factor(K)` returns an
+    object whose solve(B) applies K^-1 (default: SuperLU, scipy's splu)."""
     S = S.tocsr()
     M = M.tocsr()
     K = (S - mu * M).tocsc()
-    lu = spla.splu(K)
+    lu = (factor or spla.splu)(K)
     minv, msolve = None, None
     if finest:
         if M.nnz == M.shape[0] and np.all(M.indices == np.arange(M.shape[0])):
@@ -172,7 +173,7 @@ class HsimResult:
 
 
 def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
-                  inv_iters=2, lock_factor=0.1):
+                  inv_iters=2, lock_factor=0.1, factor=None):
     """Alg. 3 after the hierarchy is built: coarse dense solve, then SIM on
     every finer level starting from the prolonged basis."""
     T = len(S_levels)
@@ -186,7 +187,7 @@ def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
         Phi = U_list[tau] @ Phi
         mu = shift(lam, p, alpha)
         r = sim(S_levels[tau], M_levels[tau], Phi, p, eps, mu, finest=(tau == 0),
-                max_iters=max_iters, inv_iters=inv_iters, lock_factor=lock_factor)
+                max_iters=max_iters, inv_iters=inv_iters, lock_factor=lock_factor, factor=factor)
         lam, Phi = r.lam, r.Phi
         iters.append(r.iters)
         shifts.append(mu)
@@ -195,7 +196,7 @@ def hsim_matrices(S_levels, M_levels, U_list, p, eps, alpha=0.1, max_iters=100,
 
 
 def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100, boundary="neumann",
-         mass="lumped"):
+         mass="lumped", factor=None):
     """Full HSIM (Alg. 3) on a mesh: p lowest eigenpairs of S Phi = lambda M Phi.
     boundary="dirichlet" eliminates the boundary vertices (rows of Phi are then
     the interior vertices, listed in the result's ``interior``).
@@ -221,7 +222,7 @@ def hsim(mesh, p, levels, eps, start_vertex, sigma=7.0, alpha=0.1, max_iters=100
         lam, Phi = sla.eigh(S0.toarray(), Mdense, subset_by_index=[0, q - 1])
         iters, shifts, coarse = [], [], [lam]
     else:
-        lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, U, p, eps, alpha, max_iters)
+        lam, Phi, iters, shifts, coarse = hsim_matrices(S, M, U, p, eps, alpha, max_iters, factor=factor)
     return HsimResult(lam[:p], normalise_signs(Phi[:, :p]), iters, shifts, coarse, H, S, M, interior)
 
 

@@ -8,10 +8,13 @@ eigenvalue counts by Sylvester's law of inertia that show the result is the
 lowest p pairs: the count below the midpoint between consecutive returned
 eigenvalues at a few indices, and the count just above the last one.
 
-Usage:  python tests/golden/make_golden.py bumpy_torus_500 icosphere7_noise
+Usage:  python tests/golden/make_golden.py [--workers N] bumpy_torus_500 icosphere7_noise
 Each workload writes tests/golden/oracle_eigs_<workload>.txt (a few
 kilobytes): '#' header lines, then one eigenvalue per line (repr, 17
-significant digits), ascending.
+significant digits), ascending.  --workers N spreads every solve's columns
+over N processes, each holding its own SuperLU factor of the same matrix and
+solving its column block exactly as the oracle's single factor would (each
+column's solve is independent of the others).
 """
 from __future__ import annotations
 
@@ -19,8 +22,11 @@ import os
 import sys
 import time
 
+import multiprocessing as mp
+
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
@@ -31,10 +37,57 @@ import synth  # noqa: E402
 from oracle import assembly, inertia, sim  # noqa: E402
 
 
-def make(name: str) -> str:
+_LU = None
+
+
+def _worker_init(K):
+    global _LU
+    _LU = spla.splu(K)
+
+
+def _worker_solve(B):
+    return _LU.solve(B)
+
+
+class ParallelLU:
+    """splu(K) held by each of `workers` spawned processes; solve(B) solves
+    contiguous column blocks of B in parallel and concatenates them."""
+
+    def __init__(self, K, workers):
+        self.workers = workers
+        # one BLAS thread per worker (the variables are read when a worker
+        # imports NumPy; this process keeps its own thread pool)
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({k: "1" for k in keys})
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_worker_init, initargs=(K,))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def solve(self, B):
+        B = np.asarray(B)
+        k = B.shape[1]
+        step = -(-k // self.workers)
+        blocks = [np.ascontiguousarray(B[:, a:a + step]) for a in range(0, k, step)]
+        return np.hstack(self.pool.map(_worker_solve, blocks))
+
+    def __del__(self):
+        try:
+            self.pool.terminate()
+        except Exception:
+            pass
+
+
+def make(name: str, workers: int = 0) -> str:
     w, mesh, start = synth.make_workload(name)
     t0 = time.time()
-    r = sim.hsim(mesh, w.p, w.levels, w.tol, start)
+    factor = (lambda K: ParallelLU(K, workers)) if workers > 1 else None
+    r = sim.hsim(mesh, w.p, w.levels, w.tol, start, factor=factor)
     t_solve = time.time() - t0
     S = assembly.stiffness(mesh)
     Md = assembly.lumped_mass(mesh)
@@ -62,8 +115,9 @@ def make(name: str) -> str:
         f.write(f"# max residual of eq. conv2 over the {w.p} pairs: {res.max():.3e}\n")
         f.write("# eigenvalue counts below sigma by Sylvester's law of inertia (sigma, count):\n")
         for sigma, _, got in checks:
-            f.write(f"#   {sigma!r} {got}\n")
-        f.write(f"# written by tests/golden/make_golden.py in {t_solve:.0f} s of oracle time\n")
+            f.write(f"#   {float(sigma)!r} {got}\n")
+        f.write(f"# written by tests/golden/make_golden.py in {t_solve:.0f} s of oracle time"
+                f"{f' ({workers} solve workers)' if workers > 1 else ''}\n")
         for v in lam:
             f.write(f"{float(v)!r}\n")
     return path
@@ -76,5 +130,9 @@ def load(name: str) -> np.ndarray:
 
 
 if __name__ == "__main__":
-    for nm in sys.argv[1:]:
-        print(make(nm), flush=True)
+    args = sys.argv[1:]
+    workers = 0
+    if args and args[0] == "--workers":
+        workers, args = int(args[1]), args[2:]
+    for nm in args:
+        print(make(nm, workers), flush=True)
