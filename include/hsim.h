@@ -132,8 +132,10 @@ typedef struct {
            ms_gram, ms_ritz, ms_update, ms_residual, ms_total;
     int q;
     int ritz_calls;        /* Rayleigh-Ritz solves of size q on the SIM levels */
-    int ritz_sweeps;       /* Jacobi sweeps summed over those solves */
-    int coarse_sweeps;     /* Jacobi sweeps of the coarsest dense eigenproblem */
+    int ritz_sweeps;       /* mixed path: Newton-Schulz steps of the reduced mass
+                              matrices' inverse square roots, summed over those
+                              solves (0 for a solve that factored M_bar) */
+    int coarse_sweeps;     /* the same for the coarsest dense eigenproblem */
     double ms_tc_product;  /* HSIM_MIXED: tensor-core product kernels alone (part of
                               ms_gram and ms_update, which include the digit split) */
     double solve_flops;    /* triangular-solve flops, 4 nnz(L) per right-hand side */
@@ -328,10 +330,15 @@ hsim_status hsim_gemm_update_tc(hsim_ctx *ctx, int n, int k, int m, const double
  * be NULL (always 0).  Scratch is allocated per call. */
 hsim_status hsim_ritz(hsim_ctx *ctx, int k, const double *Sbar_dev, const double *Mbar_dev,
                       double *evals_dev, double *X_dev, int *sweeps_out);
-/* The same solve as done by the mixed-precision path: C^-1 is formed
- * explicitly (in-place inversion of L by block doubling, FP64) and the three
- * transforms A = (C^-1 S_bar) C^-T and X = C^-T V are FP64-accurate products
- * on BF16 tensor cores (as hsim_gram_tc).  Arguments and errors as hsim_ritz. */
+/* The same solve as done by the mixed-precision path.  When a Gershgorin
+ * bound puts ||M_bar - I||_2 below 1/2 (the reduced mass matrices of the
+ * solve after the first iteration of a level), W = M_bar^-1/2 comes from a
+ * Newton-Schulz iteration and A = W S_bar W, X = W V; otherwise, or if that
+ * iteration stalls above max|I - W^2 M_bar| = 1e-12, C^-1 is formed
+ * explicitly (LDL^T of M_bar, in-place inversion of L by block doubling, FP64)
+ * and A = (C^-1 S_bar) C^-T, X = C^-T V.  Every product is FP64-accurate on
+ * BF16 tensor cores (as hsim_gram_tc).  sweeps_out: the Newton-Schulz steps
+ * taken, 0 on the factorisation path.  Arguments and errors as hsim_ritz. */
 hsim_status hsim_ritz_tc(hsim_ctx *ctx, int k, const double *Sbar_dev, const double *Mbar_dev,
                          double *evals_dev, double *X_dev, int *sweeps_out);
 

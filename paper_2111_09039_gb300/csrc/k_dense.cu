@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -591,12 +592,98 @@ __global__ void k_cinv(int k, const double *__restrict__ F, const double *__rest
     Cc[(size_t)j * k + i] = v;
 }
 
+// ---- Newton-Schulz inverse square root of a reduced mass matrix -------------
+// Gershgorin bound max_i sum_j |M_ij - delta_ij| of ||M - I||_2 (one warp per
+// row; non-negative doubles order like their bit patterns)
+__global__ void k_gershgorin_dev(int k, const double *__restrict__ M, int ldm, unsigned long long *out) {
+    const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (row >= k) return;
+    double sum = 0.0;
+    for (int j = lane; j < k; j += 32) sum += fabs(M[(size_t)row * ldm + j] - (j == row ? 1.0 : 0.0));
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sum));
+}
+
+// T = (3 I - P) / 2 and max |I - P| (into out, as above)
+__global__ void k_ns_step(int k, const double *__restrict__ P, double *__restrict__ T, unsigned long long *out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (idx < (int64_t)k * k) {
+        const int i = (int)(idx / k), j = (int)(idx % k);
+        const double id = i == j ? 1.0 : 0.0;
+        e = fabs(id - P[idx]);
+        T[idx] = 0.5 * (3.0 * id - P[idx]);
+    }
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(e));
+}
+
 // X[i, 0:cols] *= 1/sqrt(d[i])
 __global__ void k_rows_rsqrt(int rows, int cols, const double *__restrict__ d, double *__restrict__ X, int ldx) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)rows * cols) return;
     int i = (int)(idx / cols), j = (int)(idx % cols);
     X[(size_t)i * ldx + j] *= rsqrt(d[i]);
+}
+
+// C = A B for k x k row-major FP64 blocks as an FP64-accurate tensor-core product
+static void tc_mm(cudaStream_t s, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+                  unsigned char *oz) {
+    OzakiOperand a = ozaki_split_rows(s, k, k, A, lda, oz);
+    OzakiOperand b = ozaki_split_cols(s, k, k, B, ldb, oz + ozaki_rows_scratch(k, k));
+    ozaki_product(s, a, b, a.kp, C, ldc, 0);
+}
+
+// Z = M_bar^-1/2 by the coupled Newton-Schulz iteration Y_0 = M_bar, Z_0 = I,
+// T_j = (3 I - Z_j Y_j) / 2, Y_{j+1} = Y_j T_j, Z_{j+1} = T_j Z_j, which
+// converges quadratically when ||M_bar - I||_2 < 1; products on the tensor
+// cores.  Used when a Gershgorin bound puts ||M_bar - I||_2 below 1/2 (the
+// columns are scaled to unit M-norm, so M_bar is near I once the basis is
+// nearly M-orthonormal).  buf: four k x k scratch blocks.  Returns the block
+// that holds Z, or nullptr if the bound fails or the iteration does not reach
+// max|I - Z Y| < 1e-12 within 12 steps (the caller then factors M_bar); the
+// products carry about 2^-47 of their row and column maxima per term, so the
+// attainable level near I is a few 1e-14 times sqrt(k).  *steps: iterations.
+static const double *ns_inv_sqrt(cudaStream_t s, int k, const double *Mbar, int ldm, double *const buf[4],
+                                 unsigned char *oz, unsigned long long *dmax, int *steps) {
+    auto read_max = [&](double &v) {
+        unsigned long long h = 0;
+        HSIM_CUDA(cudaMemcpyAsync(&h, dmax, sizeof(h), cudaMemcpyDeviceToHost, s));
+        HSIM_CUDA(cudaStreamSynchronize(s));
+        std::memcpy(&v, &h, sizeof(v));
+    };
+    HSIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
+    k_gershgorin_dev<<<cdiv(k, 8), 256, 0, s>>>(k, Mbar, ldm, dmax);
+    HSIM_LAUNCHED();
+    double g = 1.0;
+    read_max(g);
+    if (!(g < 0.5)) return nullptr;
+    double *Y = buf[0], *Z = buf[1], *P = buf[2], *T = buf[3];
+    copy_matrix(s, k, k, Mbar, ldm, Y, k);
+    k_identity<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, Z, k);
+    HSIM_LAUNCHED();
+    double prev = 1.0;
+    for (int it = 0; it < 12; ++it) {
+        tc_mm(s, k, Z, k, Y, k, P, k, oz);  // P = Z Y
+        HSIM_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), s));
+        k_ns_step<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, P, T, dmax);
+        HSIM_LAUNCHED();
+        double e = 1.0;
+        read_max(e);
+        if (e < 1e-12) {
+            k_symmetrize<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, Z, k);
+            HSIM_LAUNCHED();
+            *steps = it;
+            return Z;
+        }
+        if (!(e < 0.5 * prev) && it > 1) return nullptr;  // stopped contracting above the target
+        prev = e;
+        tc_mm(s, k, Y, k, T, k, P, k, oz);  // Y T
+        std::swap(Y, P);
+        tc_mm(s, k, T, k, Z, k, P, k, oz);  // T Z
+        std::swap(Z, P);
+    }
+    return nullptr;
 }
 
 int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar, int ldm, double *evals, double *X,
@@ -609,6 +696,30 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
     double *ework = d + 2 * (size_t)k + 32;
     DenseFront &df = dense_front(k, s);
     const int *node = df.node.p;
+    if (tc) {
+        // M_bar near I: W = M_bar^-1/2 by Newton-Schulz on the tensor cores
+        // (W M_bar W = I), A = W S_bar W, X = W V; no factorisation of M_bar
+        double *Cr = ework + sym_eig_work_size(k, k) + 8, *Cc = Cr + kk, *V = Cc + kk, *scr = V + kk;
+        unsigned char *oz = reinterpret_cast<unsigned char *>(
+            (reinterpret_cast<uintptr_t>(scr + kk) + 255) & ~static_cast<uintptr_t>(255));
+        double *const buf[4] = {F, Cr, Cc, scr};
+        int ns_steps = 0;
+        const double *Wz =
+            ns_inv_sqrt(s, k, Mbar, ldm, buf, oz, reinterpret_cast<unsigned long long *>(flag_dev + 4), &ns_steps);
+        if (Wz) {
+            if (sweeps) *sweeps = ns_steps;
+            tc_mm(s, k, Wz, k, Sbar, lds, W, k, oz);
+            tc_mm(s, k, W, k, Wz, k, T, k, oz);
+            k_symmetrize<<<cdiv((int64_t)k * k, 256), 256, 0, s>>>(k, T, k);
+            HSIM_LAUNCHED();
+            sym_eig(s, k, m, T, evals, V, m, ework);
+            OzakiOperand a = ozaki_split_rows(s, k, k, Wz, k, oz);
+            OzakiOperand b = ozaki_split_cols(s, k, m, V, m, oz + ozaki_rows_scratch(k, k));
+            ozaki_product(s, a, b, a.kp, X, ldx, 0);
+            ozaki_check(s);
+            return 0;
+        }
+    }
     // F = M_bar (symmetric: row-major == column-major); M_bar = L D L^T = C C^T
     copy_matrix(s, k, k, Mbar, ldm, F, k);
     HSIM_CUDA(cudaMemsetAsync(flag_dev, 0, 4 * sizeof(int), s));

@@ -396,6 +396,31 @@ def test_ritz_tc_matches_scipy_eigh(hs, ctx, k):
     assert np.all(np.diff(lam) >= 0)
 
 
+@pytest.mark.parametrize("k,eps", [(750, 2e-3), (200, 1e-1), (33, 0.2)])
+def test_ritz_tc_near_identity_mass(hs, ctx, k, eps):
+    # unit-diagonal M_bar close to I (the reduced mass matrices after the first
+    # iteration of a level): the Newton-Schulz inverse square root path,
+    # Gershgorin bound of ||M_bar - I|| below 1/2; checked against SciPy
+    rng = np.random.default_rng(k)
+    E = rng.standard_normal((k, k))
+    E = 0.5 * (E + E.T)
+    np.fill_diagonal(E, 0.0)
+    E *= eps / np.abs(E).sum(1).max()   # Gershgorin bound of ||M - I|| = eps
+    M = np.eye(k) + E
+    assert np.abs(M - np.eye(k)).sum(1).max() < 0.5
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    S = Q @ np.diag(np.sort(rng.uniform(0.0, 500.0, k))) @ Q.T
+    S = 0.5 * (S + S.T)
+    lam, X, steps = hs.ritz(ctx, dev(S), dev(M), tc=True)
+    assert steps >= 1                      # the Newton-Schulz path was taken
+    lam, X = lam.cpu().numpy(), X.cpu().numpy()
+    ref = sla.eigh(S, M, eigvals_only=True)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(lam, ref, rtol=1e-10, atol=1e-11 * scale)
+    np.testing.assert_allclose(X.T @ M @ X, np.eye(k), atol=1e-11)
+    np.testing.assert_allclose(X.T @ S @ X, np.diag(lam), atol=1e-10 * scale)
+
+
 def test_ritz_tc_clusters_and_fp64_agreement(hs, ctx):
     # spectrum with pairs and a cluster of four; both variants give the same
     # eigenvalues and span the same invariant subspaces
