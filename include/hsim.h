@@ -117,6 +117,10 @@ typedef struct {
     int mass;            /* HSIM_MASS_LUMPED (default) or HSIM_MASS_CONSISTENT; read by
                             hsim_build_hierarchy, fixed for the hierarchy (not with
                             plain_sim) */
+    int hier_device;     /* hsim_build_hierarchy: 1 (default) computes the farthest-point
+                            order and the prolongations U^tau on the context's GPU, 0 on
+                            the host; both give the same order and the same U bit for
+                            bit (Sec. 4.1) */
 } hsim_options;
 
 /* Per-solve report (host struct, optional). */
@@ -160,15 +164,21 @@ const char *hsim_last_error(void);
 uint64_t hsim_kernel_launches(void);
 
 /* --------------------------------------------------------------------------
- * Hierarchy (Sec. 4.1).  Host-side construction, run once per mesh:
+ * Hierarchy (Sec. 4.1), run once per mesh:
  *   - level sizes n^{T-1} = max(ceil(1.5p), 1000) and geometric growth
  *     (eqs. nT-1, growthRate; growth rate read as the (T-1)-th root);
- *   - farthest-point sampling with Dijkstra distances (Alg. 2);
+ *   - farthest-point sampling with shortest-path distances over the edge
+ *     graph (Alg. 2), on the GPU (opts->hier_device = 1, the default: one
+ *     thread-block cluster, several samples per relaxation where the
+ *     straight-line bound proves them independent) or on the host;
  *   - prolongations U^tau (eqs. radius, basis and row normalisation), rows =
- *     level-tau vertices, columns = level-(tau+1) vertices;
- *   - patterns of the Galerkin products S^tau = U^T S U (Alg. 3);
- *   - a nested-dissection ordering and supernodal symbolic analysis for each
- *     level's shifted matrix S^tau - mu M^tau.
+ *     level-tau vertices, columns = level-(tau+1) vertices, on the GPU (one
+ *     truncated search per centre) or on the host; both devices give the
+ *     same order and U bit for bit;
+ *   - on the host: patterns of the Galerkin products S^tau = U^T S U
+ *     (Alg. 3), a nested-dissection ordering (subtrees on worker threads)
+ *     and the supernodal symbolic analysis of each level's shifted matrix
+ *     S^tau - mu M^tau.
  * V_host (n x 3 positions) or L2_host (n_tris x 3 squared edge lengths, L2[t*3+k]
  * = edge opposite corner k of triangle t, for intrinsic meshes) must be
  * given; F_host is n_tris x 3 vertex indices.  Result uploaded to the device.

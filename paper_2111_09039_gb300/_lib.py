@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("lock_factor", ctypes.c_double), ("precision", ctypes.c_int),
                 ("start_vertex", ctypes.c_int), ("leaf_size", ctypes.c_int), ("q", ctypes.c_int),
                 ("refine", ctypes.c_int), ("boundary", ctypes.c_int), ("plain_sim", ctypes.c_int),
-                ("sim_shift", ctypes.c_double), ("seed", ctypes.c_uint64), ("mass", ctypes.c_int)]
+                ("sim_shift", ctypes.c_double), ("seed", ctypes.c_uint64), ("mass", ctypes.c_int),
+                ("hier_device", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

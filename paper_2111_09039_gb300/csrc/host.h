@@ -59,6 +59,27 @@ HostHierarchy build_host_hierarchy(int n, int m, const double *V, const int *F, 
 HostHierarchy host_levels(int n, int m, const double *V, const int *F, const double *L2, int p, int levels,
                           int start_vertex, double sigma, int q, bool dirichlet);
 void host_samples(HostHierarchy &h, int start_vertex, double sigma);
+// The same sampling order and prolongations computed on the current CUDA
+// device (k_hier.cu), equal index for index and bit for bit; V (host, n x 3)
+// lets farthest-point sampling take several samples per relaxation (NULL for
+// meshes given by edge lengths).
+void device_samples(HostHierarchy &h, const double *V, int start_vertex, double sigma, cudaStream_t s);
+
+namespace k {
+// edge graph (and coordinates) of the mesh on the device
+struct DeviceGraph {
+    int n = 0, n_sm = 1;
+    double area = 0.0;
+    DevBuf<int> ptr, idx;
+    DevBuf<double> w, V;
+    void upload(const MeshGraph &g, const double *V_host, cudaStream_t s);
+};
+std::vector<int> fps_device(cudaStream_t s, const DeviceGraph &g, int start, int count,
+                            const std::vector<char> *cand);
+Csr prolongation_device(cudaStream_t s, const DeviceGraph &g, const std::vector<int> &order, int nf, int nc,
+                        bool fine_is_mesh, double sigma, double *rho_out, int *fallback_rows,
+                        const std::vector<int> *dofs);
+}  // namespace k
 
 // out[i] = 2 u_i - 1, u_i = (i-th SplitMix64 output from state seed) >> 11
 // times 2^-53: the random column of plain SIM's initial basis.

@@ -12,7 +12,13 @@
 // the vertices that touch L_{m+1}.  Disconnected pieces are ordered
 // independently.  Every separator and every leaf domain is one dense front.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <exception>
 #include <numeric>
+#include <thread>
 
 #include "host.h"
 #include "parallel.h"
@@ -186,15 +192,37 @@ struct NdNode {
     std::vector<int> children;
 };
 
+// Nodes of a subtree in creation order (children before parents); ids are
+// positions in this list.
+using NdList = std::vector<NdNode>;
+
+// Append `part` to `out`, shifting its node ids; returns the shift.
+int append_nodes(NdList &out, NdList &&part) {
+    const int off = (int)out.size();
+    for (NdNode &nn : part) {
+        for (int &c : nn.children) c += off;
+        out.push_back(std::move(nn));
+    }
+    return off;
+}
+
 struct Nd {
     const Csr &A;
     int leaf;
-    std::vector<NdNode> nodes;
-    std::vector<int> stamp;   // vertex -> set id of the set being split
-    std::vector<int> level;   // BFS level scratch
-    int next_stamp = 1;
+    // vertex -> id of the set being split (relaxed atomics: sets ordered
+    // concurrently are disjoint, but a search reads its neighbours' ids)
+    std::vector<std::atomic<int>> stamp;
+    std::vector<int> level;   // BFS level scratch (written only for members of the set)
+    std::atomic<int> next_stamp{1};
+    int spawn_depth = 0;      // subtrees of this depth or less run on their own threads
 
-    Nd(const Csr &a, int l) : A(a), leaf(l), stamp(a.n_rows, 0), level(a.n_rows, -1) {}
+    Nd(const Csr &a, int l) : A(a), leaf(l), stamp(a.n_rows), level(a.n_rows, -1) {
+        for (auto &x : stamp) x.store(0, std::memory_order_relaxed);
+        int t = host_threads(), d = 0;
+        while ((1 << d) < t) ++d;
+        spawn_depth = d;
+    }
+    int st_of(int v) const { return stamp[v].load(std::memory_order_relaxed); }
 
     // BFS within the set marked `st` from r; fills order and returns levels
     // via level[] (relative to this search); returns number of levels.
@@ -207,7 +235,7 @@ struct Nd {
             int v = order[h];
             for (int e = A.ptr[v]; e < A.ptr[v + 1]; ++e) {
                 int u = A.col[e];
-                if (u == v || stamp[u] != st || level[u] >= 0) continue;
+                if (u == v || st_of(u) != st || level[u] >= 0) continue;
                 level[u] = level[v] + 1;
                 nl = std::max(nl, level[u] + 1);
                 order.push_back(u);
@@ -220,11 +248,13 @@ struct Nd {
     }
     int degree(int v) const { return A.ptr[v + 1] - A.ptr[v]; }
 
-    // returns ids of the roots of the subtrees ordering `W`
-    std::vector<int> run(std::vector<int> W) {
+    // Orders W: appends the nodes of its subtrees to `nodes` (children before
+    // parents) and returns the ids of their roots.  The node list does not
+    // depend on which subtrees ran concurrently.
+    std::vector<int> run(std::vector<int> W, NdList &nodes, int depth) {
         if (W.empty()) return {};
-        int st = next_stamp++;
-        for (int v : W) stamp[v] = st;
+        const int st = next_stamp.fetch_add(1, std::memory_order_relaxed);
+        for (int v : W) stamp[v].store(st, std::memory_order_relaxed);
         std::vector<int> order;
         // connected components
         {
@@ -238,7 +268,7 @@ struct Nd {
             if (comps.size() > 1) {
                 std::vector<int> roots;
                 for (auto &c : comps) {
-                    auto r = run(std::move(c));
+                    auto r = run(std::move(c), nodes, depth);
                     roots.insert(roots.end(), r.begin(), r.end());
                 }
                 return roots;
@@ -287,15 +317,42 @@ struct Nd {
                 bool touches = false;
                 for (int e = A.ptr[v]; e < A.ptr[v + 1] && !touches; ++e) {
                     int u = A.col[e];
-                    touches = (stamp[u] == st && level[u] == m + 1);
+                    touches = (st_of(u) == st && level[u] == m + 1);
                 }
                 (touches ? sep : Apart).push_back(v);
             }
         }
         clear_levels(order);
-        std::vector<int> kids = run(std::move(Apart));
-        std::vector<int> kb = run(std::move(Bpart));
-        kids.insert(kids.end(), kb.begin(), kb.end());
+        std::vector<int> kids;
+        if (depth < spawn_depth && std::min(Apart.size(), Bpart.size()) >= 4096) {
+            // the two halves are disjoint: order the first on another thread
+            NdList la, lb;
+            std::vector<int> ka, kb;
+            std::exception_ptr err;
+            std::thread th([&] {
+                try {
+                    ka = run(std::move(Apart), la, depth + 1);
+                } catch (...) {
+                    err = std::current_exception();
+                }
+            });
+            try {
+                kb = run(std::move(Bpart), lb, depth + 1);
+            } catch (...) {
+                th.join();
+                throw;
+            }
+            th.join();
+            if (err) std::rethrow_exception(err);
+            const int oa = append_nodes(nodes, std::move(la));
+            const int ob = append_nodes(nodes, std::move(lb));
+            for (int k : ka) kids.push_back(k + oa);
+            for (int k : kb) kids.push_back(k + ob);
+        } else {
+            kids = run(std::move(Apart), nodes, depth + 1);
+            std::vector<int> kb = run(std::move(Bpart), nodes, depth + 1);
+            kids.insert(kids.end(), kb.begin(), kb.end());
+        }
         nodes.push_back(NdNode{std::move(sep), std::move(kids)});
         return {(int)nodes.size() - 1};
     }
@@ -310,7 +367,10 @@ FrontSymbolic analyse(const Csr &A, int leaf_size) {
     Nd nd(A, leaf_size);
     std::vector<int> all(n);
     std::iota(all.begin(), all.end(), 0);
-    std::vector<int> roots = nd.run(all);
+    NdList nd_nodes;
+    const auto t_nd = std::chrono::steady_clock::now();
+    std::vector<int> roots = nd.run(all, nd_nodes, 0);
+    const auto t_st = std::chrono::steady_clock::now();
 
     FrontSymbolic fs;
     fs.n = n;
@@ -321,7 +381,7 @@ FrontSymbolic analyse(const Csr &A, int leaf_size) {
         for (int ri = (int)roots.size() - 1; ri >= 0; --ri) stack.push_back({roots[ri], 0});
         while (!stack.empty()) {
             auto &top = stack.back();
-            const NdNode &nn = nd.nodes[top.first];
+            const NdNode &nn = nd_nodes[top.first];
             if (top.second < (int)nn.children.size()) {
                 int c = nn.children[top.second++];
                 stack.push_back({c, 0});
@@ -333,7 +393,7 @@ FrontSymbolic analyse(const Csr &A, int leaf_size) {
     }
     const int N = (int)post.size();
     fs.n_nodes = N;
-    std::vector<int> newid(nd.nodes.size(), -1);
+    std::vector<int> newid(nd_nodes.size(), -1);
     for (int k = 0; k < N; ++k) newid[post[k]] = k;
     fs.perm.resize(n);
     fs.iperm.assign(n, -1);
@@ -343,7 +403,7 @@ FrontSymbolic analyse(const Csr &A, int leaf_size) {
     fs.height.assign(N, 0);
     int pos = 0;
     for (int k = 0; k < N; ++k) {
-        const NdNode &nn = nd.nodes[post[k]];
+        const NdNode &nn = nd_nodes[post[k]];
         fs.pstart[k] = pos;
         fs.ns[k] = (int)nn.verts.size();
         for (int v : nn.verts) {
@@ -413,6 +473,12 @@ FrontSymbolic analyse(const Csr &A, int leaf_size) {
     fs.rows_off[N] = roff;
     fs.foff[N] = aoff;
     fs.relmap_off[N] = moff;
+    if (const char *e = std::getenv("HSIM_TRACE"); e && std::atoi(e) >= 2) {
+        const auto t1 = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[hsim] analyse n=%d: nested dissection %.1f ms, fronts %.1f ms\n", n,
+                     std::chrono::duration<double, std::milli>(t_st - t_nd).count(),
+                     std::chrono::duration<double, std::milli>(t1 - t_st).count());
+    }
     fs.arena = aoff;
     fs.rows.resize(roff);
     fs.relmap.resize(moff);

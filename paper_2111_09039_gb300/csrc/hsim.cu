@@ -1026,8 +1026,18 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     const int leaf = o.leaf_size > 0 ? o.leaf_size : 32;
     // plain SIM: one sparse level (no sampling, no prolongation)
     const bool plain = o.plain_sim != 0;
+    // HSIM_TRACE set: wall time of each part of the build on stderr
+    auto tb = std::chrono::steady_clock::now();
+    auto lap = [&](const char *what) {
+        if (!trace_on()) return;
+        const auto t1 = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[hsim] hierarchy build: %s %.1f ms\n", what,
+                     std::chrono::duration<double, std::milli>(t1 - tb).count());
+        tb = t1;
+    };
     HostHierarchy hh =
         host_levels(n, m, V, F, L2, p, plain ? 1 : o.levels, o.start_vertex, o.sigma, subspace_q(p, o), dirichlet);
+    lap("mesh graph, level-0 pattern, sizes");
     H->sizes = hh.sizes;
     const int T = (int)H->sizes.size();
     H->T = T;
@@ -1042,7 +1052,9 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     // future is declared after H, so it is joined before H is released)
     std::future<FrontSymbolic> fs0;
     if (T > 1) fs0 = std::async(std::launch::async, [&H, leaf] { return analyse(H->lev[0].pat_nat, leaf); });
-    host_samples(hh, o.start_vertex, o.sigma);
+    if (o.hier_device) device_samples(hh, V, o.start_vertex, o.sigma, s);
+    else host_samples(hh, o.start_vertex, o.sigma);
+    lap(o.hier_device ? "sampling and prolongations (GPU)" : "sampling and prolongations (host)");
     H->order = std::move(hh.order);
     const Csr &Amesh = hh.A_mesh;  // every mesh edge plus the diagonal
     if (dirichlet) {
@@ -1060,6 +1072,7 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
         H->lev[tau + 1].n = H->sizes[tau + 1];
         H->lev[tau + 1].pat_nat = pattern_product(Ut, AU);
     }
+    lap("Galerkin patterns");
     // orderings and symbolic analyses
     for (int tau = T - 1; tau >= 0; --tau) {
         LevelData &L = H->lev[tau];
@@ -1083,6 +1096,7 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
         if (C.ptr != H->lev[tau + 1].pat_int.ptr || C.col != H->lev[tau + 1].pat_int.col)
             fail(HSIM_E_INTERNAL, "Galerkin pattern mismatch between orders");
     }
+    lap("orderings and symbolic analyses (level 0 joined)");
     // device uploads
     for (int tau = 0; tau < T; ++tau) upload_level(H->lev[tau], s);
     for (int tau = 0; tau + 1 < T; ++tau) {
@@ -1134,6 +1148,7 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     H->d_vt_idx.upload(vt, s);
     H->dF.upload(Fv, s);
     HSIM_CUDA(cudaStreamSynchronize(s));
+    lap("uploads and assembly maps");
     return H.release();
 }
 
@@ -1154,6 +1169,7 @@ hsim_options checked(const hsim_options *o) {
     HSIM_CHECK_ARG(std::isfinite(r.sim_shift), "sim_shift must be finite");
     HSIM_CHECK_ARG(r.mass == HSIM_MASS_LUMPED || r.mass == HSIM_MASS_CONSISTENT, "unknown mass matrix");
     HSIM_CHECK_ARG(r.plain_sim == 0 || r.mass == HSIM_MASS_LUMPED, "plain SIM takes the lumped mass matrix");
+    HSIM_CHECK_ARG(r.hier_device == 0 || r.hier_device == 1, "hier_device must be 0 or 1");
     return r;
 }
 
@@ -1183,6 +1199,7 @@ void hsim_default_options(hsim_options *o) {
     o->sim_shift = 0.0;
     o->seed = 0;
     o->mass = HSIM_MASS_LUMPED;
+    o->hier_device = 1;
 }
 
 void hsim_random_column(int n, uint64_t seed, double *out) {

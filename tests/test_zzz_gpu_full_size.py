@@ -88,3 +88,19 @@ def test_benchmark_workload_all_pairs(hs):
         sigma = 0.5 * (hi[i] + lo[i + 1])
         assert inertia.eigenvalue_count(S_ref, M_ref, sigma) == i + 1, (i, sigma)
     assert picks[-1] >= p - 26
+
+
+def test_benchmark_workload_device_hierarchy_equals_host(hs):
+    # the 10^6-vertex hierarchy built on the GPU (the default) and on the host:
+    # the same 31,623-vertex sampling order and the same U^0, U^1 bit for bit
+    w, mesh, start = synth.make_workload("bumpy_torus_1000")
+    ctx = hs.Context(0)
+    dev = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, levels=w.levels, start_vertex=start, hier_device=1)
+    host = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=w.p, levels=w.levels, start_vertex=start, hier_device=0)
+    assert dev.sizes == host.sizes == [10 ** 6, 31623, 1000]
+    np.testing.assert_array_equal(dev.order, host.order)
+    for tau in range(2):
+        a, b = dev.prolongation(tau), host.prolongation(tau)
+        assert a[:2] == b[:2]
+        for x, y in zip(a[2:], b[2:]):
+            np.testing.assert_array_equal(x.view(np.uint8), y.view(np.uint8))
