@@ -68,7 +68,7 @@ void device_samples(HostHierarchy &h, const double *V, int start_vertex, double 
 namespace k {
 // edge graph (and coordinates) of the mesh on the device
 struct DeviceGraph {
-    int n = 0, n_sm = 1;
+    int n = 0, n_sm = 1, max_degree = 0;
     double area = 0.0;
     DevBuf<int> ptr, idx;
     DevBuf<double> w, V;

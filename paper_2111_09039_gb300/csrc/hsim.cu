@@ -1012,6 +1012,39 @@ void run_solve(hsim_ctx *ctx, hsim_hier *H, const double *S_val, const double *M
     if (info) *info = inf;
 }
 
+// Per directed mesh edge (entry of the mesh pattern A0), the triangle corners
+// opposite it (two slots, -1 = none); every vertex's triangles (CSR).
+struct AssemblyMaps {
+    std::vector<int> ecot, vcount, vt;
+};
+AssemblyMaps assembly_maps(const Csr &A0, const int32_t *F, int n, int m) {
+    AssemblyMaps am;
+    am.ecot.assign(2 * (size_t)A0.nnz(), -1);
+    auto find = [&](int i, int j) -> int64_t {
+        auto b = A0.col.begin() + A0.ptr[i], e = A0.col.begin() + A0.ptr[i + 1];
+        auto it = std::lower_bound(b, e, j);
+        if (it == e || *it != j) fail(HSIM_E_INTERNAL, "mesh edge missing in pattern");
+        return it - A0.col.begin();
+    };
+    am.vcount.assign(n + 1, 0);
+    for (int t = 0; t < m; ++t)
+        for (int kc = 0; kc < 3; ++kc) {
+            int a = F[3 * t + (kc + 1) % 3], b = F[3 * t + (kc + 2) % 3];
+            for (int64_t e : {find(a, b), find(b, a)}) {
+                if (am.ecot[2 * e] < 0) am.ecot[2 * e] = 3 * t + kc;
+                else if (am.ecot[2 * e + 1] < 0) am.ecot[2 * e + 1] = 3 * t + kc;
+                else fail(HSIM_E_INVALID_ARG, "non-manifold edge (more than two triangles)");
+            }
+            am.vcount[F[3 * t + kc] + 1]++;
+        }
+    for (int i = 0; i < n; ++i) am.vcount[i + 1] += am.vcount[i];
+    am.vt.resize(am.vcount.back());
+    std::vector<int> fill(am.vcount.begin(), am.vcount.end() - 1);
+    for (int t = 0; t < m; ++t)
+        for (int kc = 0; kc < 3; ++kc) am.vt[fill[F[3 * t + kc]]++] = t;
+    return am;
+}
+
 hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F, const double *L2, int p,
                  const hsim_options &o) {
     HSIM_CHECK_ARG(p >= 1, "p must be >= 1");
@@ -1038,6 +1071,10 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     HostHierarchy hh =
         host_levels(n, m, V, F, L2, p, plain ? 1 : o.levels, o.start_vertex, o.sigma, subspace_q(p, o), dirichlet);
     lap("mesh graph, level-0 pattern, sizes");
+    // the assembly maps need only the mesh: built on a worker thread while the
+    // hierarchy is sampled (joined before the uploads)
+    std::future<AssemblyMaps> fam =
+        std::async(std::launch::async, [&hh, F, n, m] { return assembly_maps(hh.A_mesh, F, n, m); });
     H->sizes = hh.sizes;
     const int T = (int)H->sizes.size();
     H->T = T;
@@ -1119,30 +1156,9 @@ hsim_hier *build(hsim_ctx *ctx, int n, int m, const double *V, const int32_t *F,
     const Csr &A0 = Amesh;
     H->pat0.upload(H->lev[0].pat_nat, s);
     if (dirichlet) H->patm.upload(A0, s);
-    std::vector<int> ecot(2 * (size_t)A0.nnz(), -1);
-    auto find = [&](int i, int j) -> int64_t {
-        auto b = A0.col.begin() + A0.ptr[i], e = A0.col.begin() + A0.ptr[i + 1];
-        auto it = std::lower_bound(b, e, j);
-        if (it == e || *it != j) fail(HSIM_E_INTERNAL, "mesh edge missing in pattern");
-        return it - A0.col.begin();
-    };
-    std::vector<int> vcount(n + 1, 0);
+    AssemblyMaps am = fam.get();
+    std::vector<int> &ecot = am.ecot, &vcount = am.vcount, &vt = am.vt;
     std::vector<int> Fv(F, F + 3 * (size_t)m);
-    for (int t = 0; t < m; ++t)
-        for (int kc = 0; kc < 3; ++kc) {
-            int a = F[3 * t + (kc + 1) % 3], b = F[3 * t + (kc + 2) % 3];
-            for (int64_t e : {find(a, b), find(b, a)}) {
-                if (ecot[2 * e] < 0) ecot[2 * e] = 3 * t + kc;
-                else if (ecot[2 * e + 1] < 0) ecot[2 * e + 1] = 3 * t + kc;
-                else fail(HSIM_E_INVALID_ARG, "non-manifold edge (more than two triangles)");
-            }
-            vcount[F[3 * t + kc] + 1]++;
-        }
-    for (int i = 0; i < n; ++i) vcount[i + 1] += vcount[i];
-    std::vector<int> vt(vcount.back());
-    std::vector<int> fill(vcount.begin(), vcount.end() - 1);
-    for (int t = 0; t < m; ++t)
-        for (int kc = 0; kc < 3; ++kc) vt[fill[F[3 * t + kc]]++] = t;
     H->d_ecot.upload(ecot, s);
     H->d_vt_ptr.upload(vcount, s);
     H->d_vt_idx.upload(vt, s);

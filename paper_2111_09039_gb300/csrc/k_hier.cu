@@ -60,14 +60,16 @@ constexpr int kFpsWarps = kFpsThreads / 32;
 constexpr int kFpsBatch = 256;       // samples per relaxation at most
 constexpr int kFpsSlots = 8;         // threads per frontier vertex (one per edge slot)
 constexpr int kFpsMaxCluster = 16;   // CTAs of the sampling cluster at most
-constexpr int kFpsMaxLeaves = 8192;  // tournament-tree leaves (shared memory)
+constexpr int kFpsSoloItems = 2048;  // frontier items (vertex x slot) that CTA 0 relaxes alone
+constexpr int kFpsSoloQueue = 2048;  // frontier entries of the solo rounds kept in shared memory
+constexpr int kFpsMaxLeaves = 4096;  // tournament-tree leaves (shared memory)
+constexpr int kFpsMaxBlock = 2048;   // vertices per block at most (meshes up to 2^23 vertices)
 constexpr double kFpsMargin = 1e-6;  // relative margin of the straight-line test
+constexpr double kFpsMarginSq = (1.0 - kFpsMargin) * (1.0 - kFpsMargin);
 constexpr int kBallThreads = 256;
-// dynamic shared memory of k_fps for L leaves: leaf maxima and vertices, the
-// tree, the batch's coordinates and vertices
-constexpr size_t fps_smem(int L) {
-    return (size_t)L * 8 + 3 * kFpsBatch * 8 + (size_t)L * 4 + 2 * (size_t)L * 4 + kFpsBatch * 4;
-}
+// dynamic shared memory of k_fps for L leaves: the tree's distances and
+// vertices, the batch's coordinates and vertices
+constexpr size_t fps_smem(int L) { return 2 * (size_t)L * 12 + 3 * kFpsBatch * 8 + kFpsBatch * 4; }
 constexpr size_t kFpsMaxSmem = fps_smem(kFpsMaxLeaves);
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
@@ -114,63 +116,134 @@ struct FpsArgs {
     double *dist;                // n, +inf on entry
     int *stamp;                  // n, -1 on entry
     int *q;                      // 2 buffers x C segments x n: frontier queues, one segment per CTA
-    int *excl;                   // n, 0 on entry: taken into the batch being formed
     unsigned *dbm;               // nb bits: block's maximum out of date (all set on entry)
-    int *dirty;                  // nb: the blocks with their bit set (0..nb-1 on entry)
-    int *dirty_cnt;              // nb on entry
+    int *dirty;                  // nb: the flagged blocks, listed after each relaxation
+    int *dirty_cnt;              // 0 on entry
     int *order;                  // count
     int *status;                 // [0]: 0, 1 relaxation did not settle, 2 no candidate left; [1]: done
+    int solo_dup;                // solo rounds may push a vertex twice (see relax_items)
 };
 
-// a is farther than b (block ids; -1 or an empty block loses)
-__device__ __forceinline__ int better(int a, int b, const double *leafd, const int *leafv) {
-    const bool va = a >= 0 && leafv[a] >= 0, vb = b >= 0 && leafv[b] >= 0;
-    if (va && (!vb || leafd[a] > leafd[b] || (leafd[a] == leafd[b] && leafv[a] < leafv[b]))) return a;
-    return b;
+// Tournament tree over the blocks: node i holds the farthest candidate of its
+// subtree, (distance td[i], vertex tv[i]; tv = -1: none); leaves L + b.
+// Node i takes the farther of its children (larger distance, the lower vertex
+// on ties).
+__device__ __forceinline__ void tree_update(double *td, int *tv, int i) {
+    const double d0 = td[2 * i], d1 = td[2 * i + 1];
+    const int v0 = tv[2 * i], v1 = tv[2 * i + 1];
+    const bool left = v0 >= 0 && (v1 < 0 || d0 > d1 || (d0 == d1 && v0 < v1));
+    td[i] = left ? d0 : d1;
+    tv[i] = left ? v0 : v1;
 }
 
-// the farthest candidate of block b not taken into the batch, by one warp;
-// kB / 32 <= 8 vertices per lane, loaded before they are compared
-__device__ void rescan_block(const FpsArgs &a, int b, double *leafd, int *leafv, int lane) {
-    int best = -1;
-    double bd = -1.0;
-    const int v0 = b * a.kB, v1 = min(a.n, v0 + a.kB);
-    constexpr int R = 8;
-    double d[R];
-    int ex[R];
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-        const int v = v0 + lane + 32 * t;
-        const bool in = v < v1 && (!a.cand || a.cand[v]);
-        d[t] = in ? __ldcg(a.dist + v) : 0.0;
-        ex[t] = in ? __ldcg(a.excl + v) : 1;
+// (bd, best) = the farther of (bd, best) and (od, ob)
+__device__ __forceinline__ void farther(double &bd, int &best, double od, int ob) {
+    if (ob >= 0 && (best < 0 || od > bd || (od == bd && ob < best))) {
+        best = ob;
+        bd = od;
     }
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-        const int v = v0 + lane + 32 * t;
-        if (!ex[t] && (best < 0 || d[t] > bd)) {  // ascending v per lane: ties keep the lower id
-            best = v;
-            bd = d[t];
-        }
-    }
+}
+__device__ __forceinline__ void warp_farthest(double &bd, int &best) {
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         const int ob = __shfl_xor_sync(0xffffffffu, best, o);
         const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-        if (ob >= 0 && (best < 0 || od > bd || (od == bd && ob < best))) {
-            best = ob;
-            bd = od;
-        }
-    }
-    if (lane == 0) {
-        leafd[b] = bd;
-        leafv[b] = best;
+        farther(bd, best, od, ob);
     }
 }
 
-__device__ __forceinline__ void mark_dirty(const FpsArgs &a, int b) {
-    const unsigned bit = 1u << (b & 31);
-    if (!(atomicOr(a.dbm + (b >> 5), bit) & bit)) a.dirty[atomicAdd(a.dirty_cnt, 1)] = b;
+// The farthest candidate of block b, by one warp, skipping the block
+// positions whose bit is set in skip (null: none): (bd, best) in every lane,
+// best = -1 if none.  The lanes read 8 vertices each per 256-vertex chunk,
+// all loads first.
+__device__ __forceinline__ void block_max(const FpsArgs &a, int b, int lane, const unsigned *skip, double &bd,
+                                          int &best) {
+    best = -1;
+    bd = -1.0;
+    const int v0 = b * a.kB, v1 = min(a.n, v0 + a.kB);
+    for (int c0 = v0; c0 < v1; c0 += 256) {
+        constexpr int R = 8;
+        double d[R];
+        bool in[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int v = c0 + lane + 32 * t;
+            in[t] = v < v1 && (!a.cand || a.cand[v]);
+            if (in[t] && skip) in[t] = !((skip[(v - v0) >> 5] >> ((v - v0) & 31)) & 1u);
+            d[t] = in[t] ? __ldcg(a.dist + v) : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int v = c0 + lane + 32 * t;
+            if (in[t] && (best < 0 || d[t] > bd)) {  // ascending v per lane: ties keep the lower id
+                best = v;
+                bd = d[t];
+            }
+        }
+    }
+    warp_farthest(bd, best);
+}
+
+// block_max written to leaf b of (td, tv) by lane 0
+__device__ __forceinline__ void rescan_block(const FpsArgs &a, int b, double *td, int *tv, int lane) {
+    double bd;
+    int best;
+    block_max(a, b, lane, nullptr, bd, best);
+    if (lane == 0) {
+        td[b] = bd;
+        tv[b] = best;
+    }
+}
+
+// flag block b as out of date (no result: the relaxation does not wait for it)
+__device__ __forceinline__ void mark_dirty(const FpsArgs &a, int b) { atomicOr(a.dbm + (b >> 5), 1u << (b & 31)); }
+
+// One Bellman-Ford round r over the frontier (the first nseg segments of queue
+// buffer r & 1 with cnt[k] entries each): items it = first, first + stride,
+// ... of (frontier vertex, edge slot); a neighbour whose distance drops is
+// pushed once into this CTA's segment `rank` of buffer (r + 1) & 1 and its
+// block flagged.
+// SOLO (CTA 0 alone, at most kFpsSoloItems items): the atomic minimum is
+// issued without a plain load first, and with a.solo_dup a neighbour lowered
+// twice in the round is pushed twice (the host allows it when a round's
+// pushes, at most kFpsSoloItems / kFpsSlots vertices times the largest
+// degree, fit in a segment); a duplicate is expanded twice with the same
+// distance, which changes nothing.
+//
+// sq_in / sq_out (solo rounds, shared memory): the first kFpsSoloQueue
+// entries of segment 0 of the current / next frontier are read from / pushed
+// to shared memory instead of the global queue (later entries stay global).
+template <bool SOLO>
+__device__ __forceinline__ void relax_items(const FpsArgs &a, int r, const int *cnt, int nseg, int64_t first,
+                                            int64_t stride, size_t qbuf, int rank, int *s_cnt, const int *sq_in,
+                                            int *sq_out) {
+    const int *qc = a.q + (size_t)(r & 1) * qbuf;
+    int *qn = a.q + (size_t)((r + 1) & 1) * qbuf + (size_t)rank * a.n;
+    const int tag = r + 1;
+    int total = 0;
+    for (int k = 0; k < nseg; ++k) total += cnt[k];
+    const int64_t items = (int64_t)total * kFpsSlots;
+    for (int64_t it = first; it < items; it += stride) {
+        int j = (int)(it / kFpsSlots);
+        const int slot = (int)(it % kFpsSlots);
+        int seg = 0;
+        while (j >= cnt[seg]) j -= cnt[seg++];
+        const int v = (sq_in && seg == 0 && j < kFpsSoloQueue) ? sq_in[j] : qc[(size_t)seg * a.n + j];
+        const int e0 = a.ptr[v], e1 = a.ptr[v + 1];
+        const double dv = __ldcg(a.dist + v);
+        for (int e = e0 + slot; e < e1; e += kFpsSlots) {
+            const int u = a.idx[e];
+            const double nd = dv + a.w[e];
+            if ((SOLO || nd < __ldcg(a.dist + u)) && lower(a.dist + u, nd)) {
+                if ((SOLO && a.solo_dup) || atomicExch(a.stamp + u, tag) != tag) {
+                    const int pos = atomicAdd(&s_cnt[(r + 1) % 3], 1);
+                    if (sq_out && pos < kFpsSoloQueue) sq_out[pos] = u;
+                    else qn[pos] = u;
+                }
+                mark_dirty(a, u / a.kB);
+            }
+        }
+    }
 }
 
 // One cluster of C CTAs.  CTA 0 holds the tournament tree and forms the
@@ -183,24 +256,24 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
     const int rank = (int)cl.block_rank(), C = (int)cl.num_blocks();
     extern __shared__ __align__(16) unsigned char sm[];
     const int L = a.L;
-    double *leafd = reinterpret_cast<double *>(sm);               // L
-    double *bx = leafd + L;                                       // kFpsBatch x 3
-    int *leafv = reinterpret_cast<int *>(bx + 3 * kFpsBatch);     // L
-    int *tree = leafv + L;                                        // 2L (leaves fixed: tree[L + b] = b)
-    int *bv = tree + 2 * L;                                       // kFpsBatch
+    double *td = reinterpret_cast<double *>(sm);                  // 2L tree distances
+    double *bx = td + 2 * L;                                      // kFpsBatch x 3
+    int *tv = reinterpret_cast<int *>(bx + 3 * kFpsBatch);        // 2L tree vertices
+    int *bv = tv + 2 * L;                                         // kFpsBatch
     __shared__ int s_cnt[3];  // pushes into this CTA's segment, by round mod 3
-    __shared__ int s_nbatch, s_norder;
+    __shared__ int s_nbatch, s_norder, s_r;
+    __shared__ long long s_rounds;
+    __shared__ unsigned s_skip[kFpsMaxBlock / 32];  // batch members in the block being rescanned
+    __shared__ int s_q[2][kFpsSoloQueue];          // frontier queues of the solo rounds
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    double *leafd0 = cl.map_shared_rank(leafd, 0);
-    int *leafv0 = cl.map_shared_rank(leafv, 0);
+    double *leafd0 = cl.map_shared_rank(td, 0) + L;
+    int *leafv0 = cl.map_shared_rank(tv, 0) + L;
 
-    if (rank == 0) {
-        for (int i = tid; i < L; i += kFpsThreads) {
-            leafd[i] = -1.0;
-            leafv[i] = -1;
+    if (rank == 0)
+        for (int i = tid; i < 2 * L; i += kFpsThreads) {
+            td[i] = -1.0;
+            tv[i] = -1;
         }
-        for (int i = tid; i < 2 * L; i += kFpsThreads) tree[i] = (i >= L && i - L < a.nb) ? i - L : -1;
-    }
     if (tid == 0) {
         s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
         s_nbatch = 1;
@@ -219,7 +292,6 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
                 const int sv = bv[j];
                 a.order[no + j] = sv;
                 lower(a.dist + sv, 0.0);
-                __stcg(a.excl + sv, 0);
                 q0[j] = sv;
                 mark_dirty(a, sv / a.kB);
             }
@@ -230,7 +302,9 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
             }
         }
         cl.sync();
-        // Bellman-Ford rounds following improving edges only
+        // Bellman-Ford rounds following improving edges only.  While the
+        // frontier is small, CTA 0 runs the rounds alone (block barriers
+        // instead of cluster barriers) and hands a larger frontier back.
         int64_t rounds = 0;
         for (;;) {
             int cnt[kFpsMaxCluster];
@@ -240,50 +314,83 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
                 total += cnt[k];
             }
             if (total == 0) break;
+            if (C > 1 && (int64_t)total * kFpsSlots <= kFpsSoloItems) {
+                if (rank == 0) {
+                    int nseg = C, tot = 0;
+                    bool in_smem = false;  // the frontier's first entries are in s_q[r & 1]
+                    for (;;) {
+                        tot = 0;
+                        for (int k = 0; k < nseg; ++k) tot += cnt[k];
+                        if (tot == 0 || (int64_t)tot * kFpsSlots > kFpsSoloItems) break;
+                        if (++rounds > (int64_t)a.n + 2) {
+                            if (tid == 0) atomicExch(a.status, 1);
+                            break;
+                        }
+                        if (tid == 0) s_cnt[(r + 2) % 3] = 0;
+                        relax_items<true>(a, r, cnt, nseg, tid, kFpsThreads, qbuf, 0, s_cnt,
+                                          in_smem ? s_q[r & 1] : nullptr, s_q[(r + 1) & 1]);
+                        in_smem = true;
+                        ++r;
+                        __syncthreads();
+                        cnt[0] = s_cnt[r % 3];  // pushes of this CTA only from now on
+                        nseg = 1;
+                    }
+                    // a frontier handed back to the cluster goes to the global queue
+                    if (in_smem && tot > 0) {
+                        int *qg = a.q + (size_t)(r & 1) * qbuf;
+                        for (int j = tid; j < min(tot, kFpsSoloQueue); j += kFpsThreads) qg[j] = s_q[r & 1][j];
+                    }
+                    if (tid == 0) {
+                        s_r = r;
+                        s_rounds = rounds;
+                    }
+                    // the whole frontier is in this CTA's segment: clear the others' counts
+                    for (int k = 1 + tid; k < C; k += kFpsThreads) {
+                        int *o = cl.map_shared_rank(s_cnt, k);
+                        o[0] = o[1] = o[2] = 0;
+                    }
+                }
+                cl.sync();
+                r = *cl.map_shared_rank(&s_r, 0);
+                rounds = *cl.map_shared_rank(&s_rounds, 0);
+                if (__ldcg(a.status) != 0) return;  // uniform after the barrier
+                continue;
+            }
             if (++rounds > (int64_t)a.n + 2) {  // uniform: every thread counts the same rounds
                 if (rank == 0 && tid == 0) atomicExch(a.status, 1);
                 return;
             }
             if (tid == 0) s_cnt[(r + 2) % 3] = 0;  // read by everyone in round r - 1
-            const int *qc = a.q + (size_t)(r & 1) * qbuf;
-            int *qn = a.q + (size_t)((r + 1) & 1) * qbuf + (size_t)rank * a.n;
-            const int tag = r + 1;
-            const int64_t items = (int64_t)total * kFpsSlots;
-            for (int64_t it = (int64_t)rank * kFpsThreads + tid; it < items; it += (int64_t)C * kFpsThreads) {
-                int j = (int)(it / kFpsSlots);
-                const int slot = (int)(it % kFpsSlots);
-                int seg = 0;
-                while (j >= cnt[seg]) j -= cnt[seg++];
-                const int v = qc[(size_t)seg * a.n + j];
-                const int e0 = a.ptr[v], e1 = a.ptr[v + 1];
-                const double dv = __ldcg(a.dist + v);
-                for (int e = e0 + slot; e < e1; e += kFpsSlots) {
-                    const int u = a.idx[e];
-                    const double nd = dv + a.w[e];
-                    if (nd < __ldcg(a.dist + u) && lower(a.dist + u, nd)) {
-                        if (atomicExch(a.stamp + u, tag) != tag) qn[atomicAdd(&s_cnt[(r + 1) % 3], 1)] = u;
-                        mark_dirty(a, u / a.kB);
-                    }
-                }
-            }
+            relax_items<false>(a, r, cnt, C, (int64_t)rank * kFpsThreads + tid, (int64_t)C * kFpsThreads, qbuf, rank,
+                               s_cnt, nullptr, nullptr);
             ++r;
             cl.sync();
         }
+        // list the flagged blocks (all CTAs over the flag words)
+        const int nwords = (a.nb + 31) >> 5;
+        for (int wd = rank * kFpsThreads + tid; wd < nwords; wd += C * kFpsThreads) {
+            unsigned bits = __ldcg(a.dbm + wd);
+            if (!bits) continue;
+            __stcg(a.dbm + wd, 0u);
+            const int pos = atomicAdd(a.dirty_cnt, __popc(bits));
+            for (int k = 0; bits; ++k) {
+                const int b = (wd << 5) + __ffs(bits) - 1;
+                bits &= bits - 1;
+                a.dirty[pos + k] = b;
+            }
+        }
+        cl.sync();
         // rescan the blocks whose distances changed (all CTAs), then CTA 0
         // updates their tree paths and forms the next batch
         const int ndirty = __ldcg(a.dirty_cnt);
         for (int k = rank * kFpsWarps + warp; k < ndirty; k += C * kFpsWarps) {
             const int b = a.dirty[k];
             rescan_block(a, b, leafd0, leafv0, lane);
-            if (lane == 0) atomicAnd(a.dbm + (b >> 5), ~(1u << (b & 31)));
         }
         cl.sync();
         if (rank == 0) {
             for (int lvl = 1; (L >> lvl) >= 1; ++lvl) {
-                for (int k = tid; k < ndirty; k += kFpsThreads) {
-                    const int node = (L + a.dirty[k]) >> lvl;
-                    tree[node] = better(tree[2 * node], tree[2 * node + 1], leafd, leafv);
-                }
+                for (int k = tid; k < ndirty; k += kFpsThreads) tree_update(td, tv, (L + a.dirty[k]) >> lvl);
                 __syncthreads();
             }
             if (tid == 0) atomicExch(a.dirty_cnt, 0);
@@ -291,27 +398,42 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
                 if (tid == 0) atomicExch(a.status + 1, 1);
             } else if (warp == 0) {
                 // candidates in order while each is farther, in a straight
-                // line, from every member than its own distance
+                // line, from every member than its own distance; a taken
+                // candidate's block is rescanned without the batch's members
                 int nb = 0;
                 const int norder = s_norder;
                 for (;;) {
-                    const int rb = tree[1];
-                    const int c = rb >= 0 ? leafv[rb] : -1;
+                    const int c = tv[1];
                     if (c < 0) break;
-                    const double dc = leafd[rb];
+                    const double dc = td[1];
+                    const int b = c / a.kB, v0 = b * a.kB;
+                    // c's block without c and the batch's members, computed
+                    // before the test so that its loads overlap c's coordinates
+                    for (int i = lane; i < (a.kB >> 5); i += 32) s_skip[i] = 0u;
+                    __syncwarp();
+                    if (lane == 0) atomicOr(&s_skip[(c - v0) >> 5], 1u << ((c - v0) & 31));
+                    for (int j = lane; j < nb; j += 32) {
+                        const int m = bv[j] - v0;
+                        if (m >= 0 && m < a.kB) atomicOr(&s_skip[m >> 5], 1u << (m & 31));
+                    }
+                    __syncwarp();
                     double cx = 0.0, cy = 0.0, cz = 0.0;
                     if (a.V) {
                         cx = a.V[3 * (int64_t)c];
                         cy = a.V[3 * (int64_t)c + 1];
                         cz = a.V[3 * (int64_t)c + 2];
                     }
+                    double bd;
+                    int best;
+                    block_max(a, b, lane, s_skip, bd, best);
                     if (nb > 0) {
                         bool ok = a.V != nullptr && dc > 0.0;
                         if (ok)
                             for (int j = lane; j < nb; j += 32) {
+                                // |x_j - x_c| (1 - margin) >= dc, compared squared
                                 const double dx = bx[3 * j] - cx, dy = bx[3 * j + 1] - cy, dz = bx[3 * j + 2] - cz;
-                                const double e = sqrt(dx * dx + dy * dy + dz * dz);
-                                if (!(e * (1.0 - kFpsMargin) >= dc)) ok = false;
+                                const double e2 = dx * dx + dy * dy + dz * dz;
+                                if (!(e2 * kFpsMarginSq >= dc * dc)) ok = false;
                             }
                         if (!__all_sync(0xffffffffu, ok)) break;
                     }
@@ -320,16 +442,11 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
                         bx[3 * nb] = cx;
                         bx[3 * nb + 1] = cy;
                         bx[3 * nb + 2] = cz;
-                        __stcg(a.excl + c, 1);
+                        td[L + b] = bd;
+                        tv[L + b] = best;
+                        for (int i = (L + b) >> 1; i >= 1; i >>= 1) tree_update(td, tv, i);
                     }
-                    __syncwarp();
                     ++nb;
-                    const int b = c / a.kB;
-                    rescan_block(a, b, leafd, leafv, lane);
-                    __syncwarp();
-                    if (lane == 0)
-                        for (int i = (L + b) >> 1; i >= 1; i >>= 1)
-                            tree[i] = better(tree[2 * i], tree[2 * i + 1], leafd, leafv);
                     __syncwarp();
                     if (norder + nb >= a.count || nb >= kFpsBatch) break;
                 }
@@ -342,10 +459,6 @@ __global__ void __launch_bounds__(kFpsThreads, 1) k_fps(const FpsArgs a) {
         cl.sync();
         if (__ldcg(a.status) != 0 || __ldcg(a.status + 1) != 0) return;  // uniform after the barrier
     }
-}
-
-__global__ void k_iota(int n, int *x) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = i;
 }
 
 // ---- truncated searches of the prolongations -------------------------------------
@@ -585,6 +698,8 @@ int read_int(cudaStream_t s, const int *p) {
 void DeviceGraph::upload(const MeshGraph &g, const double *V_host, cudaStream_t s) {
     n = g.n;
     area = g.area;
+    max_degree = 0;
+    for (int v = 0; v < g.n; ++v) max_degree = std::max(max_degree, g.ptr[v + 1] - g.ptr[v]);
     ptr.upload(g.ptr, s);
     idx.upload(g.idx, s);
     w.upload(g.w, s);
@@ -607,10 +722,9 @@ std::vector<int> fps_device(cudaStream_t s, const DeviceGraph &g, int start, int
     int ncand = n;
     if (cand) ncand = (int)std::count_if(cand->begin(), cand->end(), [](char c) { return c != 0; });
     HSIM_CHECK_ARG(count >= 1 && count <= ncand, "bad sample count");
-    // blocks of kB vertices (a multiple of 32, at most 256 so that a lane
-    // scans at most 8) and at most kFpsMaxLeaves blocks
+    // blocks of kB vertices (a multiple of 32), at most kFpsMaxLeaves blocks
     const int kB = 32 * std::max(1, (int)cdiv(n, 32LL * kFpsMaxLeaves));
-    HSIM_CHECK_ARG(kB <= 256, "mesh too large for the GPU farthest-point sampling (2^21 vertices at most)");
+    HSIM_CHECK_ARG(kB <= kFpsMaxBlock, "mesh too large for the GPU farthest-point sampling (2^23 vertices at most)");
     const int nb = (int)cdiv(n, kB);
     int L = 1;
     while (L < nb) L *= 2;
@@ -643,7 +757,7 @@ std::vector<int> fps_device(cudaStream_t s, const DeviceGraph &g, int start, int
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     DevBuf<double> dist(n);
-    DevBuf<int> stamp(n), q(2 * (size_t)C * n), excl(n), dirty(nb), order(count), status(2), dirty_cnt(1);
+    DevBuf<int> stamp(n), q(2 * (size_t)C * n), dirty(nb), order(count), status(2), dirty_cnt(1);
     DevBuf<unsigned> dbm(cdiv(nb, 32));
     DevBuf<unsigned char> dcand;
     if (cand) {
@@ -654,14 +768,16 @@ std::vector<int> fps_device(cudaStream_t s, const DeviceGraph &g, int start, int
     }
     fill(s, n, INFINITY, dist.p);
     fill(s, n, -1, stamp.p);
-    fill(s, n, 0, excl.p);
     fill(s, 2, 0, status.p);
-    fill(s, 1, nb, dirty_cnt.p);
-    fill(s, cdiv(nb, 32), -1, reinterpret_cast<int *>(dbm.p));  // every block out of date
-    k_iota<<<cdiv(nb, 256), 256, 0, s>>>(nb, dirty.p);
-    HSIM_LAUNCHED();
+    fill(s, 1, 0, dirty_cnt.p);
+    // every block out of date (bits past nb stay clear)
+    std::vector<unsigned> bits(cdiv(nb, 32), 0xffffffffu);
+    if (nb % 32) bits.back() = (1u << (nb % 32)) - 1u;
+    HSIM_CUDA(cudaMemcpyAsync(dbm.p, bits.data(), bits.size() * sizeof(unsigned), cudaMemcpyHostToDevice, s));
+    // a solo round pushes at most (kFpsSoloItems / kFpsSlots) * max_degree entries
+    const int solo_dup = (int64_t)(kFpsSoloItems / kFpsSlots) * g.max_degree <= n ? 1 : 0;
     FpsArgs a{n, g.ptr.p, g.idx.p, g.w.p, g.V.p, dcand.p, start, count, kB, nb, L, dist.p, stamp.p, q.p,
-              excl.p, dbm.p, dirty.p, dirty_cnt.p, order.p, status.p};
+              dbm.p, dirty.p, dirty_cnt.p, order.p, status.p, solo_dup};
     HSIM_CUDA(cudaLaunchKernelEx(&cfg, k_fps, a));
     HSIM_LAUNCHED();
     const int st = read_int(s, status.p);
