@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <functional>
 #include <future>
 #include <initializer_list>
@@ -150,6 +151,12 @@ struct LevelData {
     DevBuf<k::GemmTask> inv_w_tc, inv_w_cc;
     int inv_nw_tc = 0, inv_tw_tc = 0, inv_nw_cc = 0, inv_tw_cc = 0;
     int64_t inv_scratch = 0;
+    // blocked FP32 factorisation of the heights with fronts of kTcMinSchurFront
+    // or more: per height and block of kSchurBlock pivot columns, the offset of
+    // its trailing-update tiles in schur_tasks (schur_off[h].size() = blocks + 1;
+    // empty: the height is factored panel by panel)
+    std::vector<std::vector<int64_t>> schur_off;
+    DevBuf<k::SchurTask> schur_tasks;
 };
 
 struct ProlongData {
@@ -211,6 +218,10 @@ namespace {
 // +8 ms) and stay on the CUDA cores.  HSIM_TC32=0 keeps every FP32 product on
 // the CUDA cores (for comparison; read at every factorisation and solve).
 constexpr int kTcMinPivots = 128, kTcMinFwdPivots = 300;
+// FP32 factorisation: heights whose largest front has this many rows are
+// factored in blocks of k::kSchurBlock pivot columns, the trailing update of
+// each block on the tensor cores (rank kSchurBlock instead of rank 32)
+constexpr int kTcMinSchurFront = 512;
 // mixed path: the Grams take 5 digits per value at tolerances from this up, 6 below
 constexpr double kGramFiveDigitTol = 1e-6;
 bool tc32_enabled() {
@@ -255,6 +266,32 @@ void build_inverse_plan(LevelData &L, cudaStream_t s) {
         L.inv_w_tc.upload(wt, s);
         L.inv_w_cc.upload(wc, s);
         HSIM_CUDA(cudaStreamSynchronize(s));
+    }
+    // trailing-update tiles of the blocked factorisation
+    {
+        std::vector<k::SchurTask> tasks;
+        L.schur_off.assign(fs.max_height + 1, {});
+        constexpr int B = k::kSchurBlock;
+        for (int h = 0; h <= fs.max_height; ++h) {
+            int maxnf = 0, maxns = 0;
+            for (int t : fs.by_height[h]) {
+                maxnf = std::max(maxnf, fs.nf[t]);
+                maxns = std::max(maxns, fs.ns[t]);
+            }
+            if (maxnf < kTcMinSchurFront) continue;
+            for (int K0 = 0; K0 < maxns; K0 += B) {
+                L.schur_off[h].push_back((int64_t)tasks.size());
+                for (int t : fs.by_height[h]) {
+                    if (fs.ns[t] <= K0 || fs.nf[t] <= K0 + B) continue;
+                    const int nt = (fs.nf[t] - K0 - B + B - 1) / B;
+                    for (int ti = 0; ti < nt; ++ti)
+                        for (int tj = 0; tj <= ti; ++tj) tasks.push_back(k::SchurTask{t, ti * B, tj * B});
+                }
+            }
+            L.schur_off[h].push_back((int64_t)tasks.size());
+        }
+        L.schur_tasks.upload(tasks.empty() ? std::vector<k::SchurTask>{k::SchurTask{}} : tasks, s);
+        HSIM_CUDA(cudaStreamSynchronize(s));  // the upload reads tasks
     }
     L.n_inv_blk = (int)P.blk.size();
     L.inv_blk.upload(P.blk.empty() ? std::vector<int2>{make_int2(0, 0)} : P.blk, s);
@@ -402,12 +439,24 @@ int factor_level_t(hsim_ctx *ctx, LevelData &L, const double *S, const double *M
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         int nea = (int)(L.ea_off[h + 1] - L.ea_off[h]);
         if (nea > 0) k::front_extend_add(s, L.fd, L.d_parent.p, L.d_ea.p + L.ea_off[h], nea, L.ea_maxu[h], arena.p);
+        // FP32 fronts of the largest heights: blocks of kSchurBlock columns,
+        // the panels' updates restricted to the block, then the block's
+        // trailing update on the tensor cores; otherwise panel by panel
+        const bool blocked = std::is_same<T, float>::value && tc32_enabled() && !L.schur_off[h].empty();
+        constexpr int spb = k::kSchurBlock / kPanel;  // panels per block
         for (size_t kst = 0; kst < L.step_cnt[h].size(); ++kst) {
             int cnt = L.step_cnt[h][kst];
             int k0 = (int)kst * kPanel;
             int mrows = L.step_maxnf[h][kst] - k0 - 1;
             k::front_panel(s, L.fd, nodes, cnt, k0, mrows, arena.p, tol, flags);
-            k::front_update(s, L.fd, nodes, cnt, k0, mrows, arena.p);
+            const int K0 = (int)(kst / spb) * k::kSchurBlock;
+            k::front_update(s, L.fd, nodes, cnt, k0, mrows, arena.p, blocked ? K0 + k::kSchurBlock : INT_MAX);
+            const bool block_end = (kst + 1) % spb == 0 || kst + 1 == L.step_cnt[h].size();
+            if (blocked && block_end) {
+                const size_t b = kst / spb;
+                const int64_t t0 = L.schur_off[h][b], t1 = L.schur_off[h][b + 1];
+                k::schur_tc(s, L.fd, L.schur_tasks.p + t0, (int)(t1 - t0), K0, reinterpret_cast<float *>(arena.p));
+            }
         }
     }
     // all nodes 0..N-1 are listed in d_hnodes grouped by height

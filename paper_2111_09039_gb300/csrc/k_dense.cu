@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -728,7 +729,7 @@ int ritz(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mbar,
         int k0 = st * kPanel;
         int kb = std::min(kPanel, k - k0);
         front_panel(s, df.fd, node, 1, k0, k - k0 - kb, F, 1e-300, flag_dev);
-        front_update(s, df.fd, node, 1, k0, k - k0 - kb, F);
+        front_update(s, df.fd, node, 1, k0, k - k0 - kb, F, INT_MAX);
     }
     front_diag(s, df.fd, node, 1, F, d, flag_dev + 2);
     HSIM_CUDA(cudaMemcpyAsync(flag_host, flag_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -891,7 +892,7 @@ int ritz_on(cudaStream_t s, int k, const double *Sbar, int lds, const double *Mb
         int k0 = st * kPanel;
         int kb = std::min(kPanel, k - k0);
         front_panel(s, fd, node, 1, k0, k - k0 - kb, F, 1e-300, flag_dev);
-        front_update(s, fd, node, 1, k0, k - k0 - kb, F);
+        front_update(s, fd, node, 1, k0, k - k0 - kb, F, INT_MAX);
     }
     front_diag(s, fd, node, 1, F, d, flag_dev + 2);
     HSIM_CUDA(cudaMemcpyAsync(flag_host, flag_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));

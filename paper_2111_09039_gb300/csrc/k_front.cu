@@ -20,6 +20,9 @@
 // of a right-hand-side block is a contiguous, coalesced segment.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "common.h"
 #include "host.h"
 #include "kernels.h"
@@ -177,10 +180,11 @@ __global__ void __launch_bounds__(128) k_front_panel(FrontDev fd, const int *__r
     }
 }
 
-// A22 -= L21 D L21^T on 64 x 64 lower-triangular tiles of the trailing block
+// A22 -= L21 D L21^T on 64 x 64 lower-triangular tiles of the trailing block;
+// with ntj > 0 only the columns below c_end (tile y = ti * ntj + tj)
 template <typename T>
 __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__restrict__ nodes, int k0,
-                                                      T *__restrict__ arena) {
+                                                      T *__restrict__ arena, int c_end, int ntj) {
     __shared__ T Lr[P][64];
     __shared__ T Lc[P][64];
     const int t = nodes[blockIdx.x];
@@ -192,10 +196,17 @@ __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__
     if (m <= 0) return;
     const int nt = (m + 63) / 64;
     int ti, tj;
-    tri_index(blockIdx.y, ti, tj);
+    if (ntj > 0) {
+        ti = (int)(blockIdx.y / ntj);
+        tj = (int)(blockIdx.y % ntj);
+        if (ti < tj) return;
+    } else {
+        tri_index(blockIdx.y, ti, tj);
+    }
     if (ti >= nt) return;
     T *F = arena + fd.foff[t];
     const int r0 = base + ti * 64, c0 = base + tj * 64;
+    if (c0 >= c_end) return;
     for (int idx = threadIdx.x; idx < P * 64; idx += blockDim.x) {
         int i = idx & 63, kk = idx >> 6;
         T vr = 0.0, vc = 0.0;
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(256) k_front_update(FrontDev fd, const int *__
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             int c = c0 + tx + 16 * v;
-            if (c < nf && r >= c) F[(int64_t)c * nf + r] -= acc[u][v];
+            if (c < nf && r >= c && c < c_end) F[(int64_t)c * nf + r] -= acc[u][v];
         }
     }
 }
@@ -663,11 +674,15 @@ void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nod
 }
 
 template <typename T>
-void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_trail, T *arena) {
+void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0, int max_trail, T *arena,
+                  int c_end) {
     if (n_nodes <= 0 || max_trail <= 0) return;
     int64_t Tt = (max_trail + 63) / 64;
-    dim3 g((unsigned)n_nodes, (unsigned)(Tt * (Tt + 1) / 2));
-    k_front_update<T><<<g, 256, 0, s>>>(fd, nodes, k0, arena);
+    // column tiles below c_end (the trailing part starts after k0's first pivot)
+    const int64_t ntj = c_end == INT_MAX ? 0 : std::min<int64_t>(Tt, (c_end - k0 + 62) / 64 + 1);
+    if (c_end != INT_MAX && ntj <= 0) return;
+    dim3 g((unsigned)n_nodes, (unsigned)(ntj > 0 ? Tt * ntj : Tt * (Tt + 1) / 2));
+    k_front_update<T><<<g, 256, 0, s>>>(fd, nodes, k0, arena, c_end, (int)ntj);
     HSIM_LAUNCHED();
 }
 
@@ -761,7 +776,7 @@ void solve_bwd_small(cudaStream_t s, const FrontDev &fd, const int *nodes, int n
                                     const double *, const double *, const double *, double, T *);               \
     template void front_extend_add<T>(cudaStream_t, const FrontDev &, const int *, const int *, int, int, T *);  \
     template void front_panel<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, T *, double, int *);  \
-    template void front_update<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, T *);              \
+    template void front_update<T>(cudaStream_t, const FrontDev &, const int *, int, int, int, T *, int);         \
     template void front_maxdiag<T>(cudaStream_t, const FrontDev &, int, const T *, unsigned long long *);        \
     template void front_diag<T>(cudaStream_t, const FrontDev &, const int *, int, const T *, T *, int *);        \
     template void solve_fwd_tri<T>(cudaStream_t, const FrontDev &, const int *, int, int, const T *, int, T *, int); \

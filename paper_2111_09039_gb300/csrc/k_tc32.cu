@@ -34,12 +34,12 @@
 // contiguous (B(kk, j) = B[j ldb + kk] of the inversion products).
 //
 // Operations (functors below): the forward products of the inverted-form
-// solves (k_finv.cu) for the tree heights with the largest fronts, and the
-// batched products of the pivot-block inversion (GemmTask lists).  The same
-// engine measured slower than the CUDA-core kernels for the backward products
-// (K over all rows of few large fronts) and for the rank-32 Schur updates of
-// the right-looking factorisation (one K step per tile), which therefore stay
-// on the CUDA cores.
+// solves (k_finv.cu) for the tree heights with the largest fronts, the
+// batched products of the pivot-block inversion (GemmTask lists), and the
+// rank-128 Schur-complement updates of the blocked factorisation of large
+// fronts.  The same engine measured slower than the CUDA-core kernels for the
+// backward products (K over all rows of few large fronts) and for rank-32
+// updates (one K step per tile), which therefore stay on the CUDA cores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -357,6 +357,53 @@ struct GemmTaskOp {
     }
 };
 
+// Schur-complement update after a block of kSchurBlock pivot columns [K0, K0
+// + kSchurBlock) of the blocked FP32 factorisation (CTA = one 128 x 128 tile
+// (m0, n0) of a front's trailing part, which starts at column K0 +
+// kSchurBlock): F(r, c) -= sum_kk L(r, K0 + kk) d_kk L(c, K0 + kk) for r >= c,
+// d_kk the pivot on the diagonal, L the unit-lower factor's columns below it.
+struct SchurOp {
+    static constexpr bool kAKContig = false, kBKContig = false;  // front columns (rows contiguous)
+    FrontDev fd;
+    const SchurTask *tasks;
+    int K0;
+    float *arena;
+    struct Tile {
+        float *F;
+        int nf, r0, c0, kb, ke;
+    };
+    __device__ bool tile(Tile &T) const {
+        const SchurTask tk = tasks[blockIdx.x];
+        T.nf = fd.nf[tk.node];
+        T.F = arena + fd.foff[tk.node];
+        T.r0 = K0 + kSchurBlock + tk.m0;
+        T.c0 = K0 + kSchurBlock + tk.n0;
+        T.kb = 0;
+        T.ke = min(kSchurBlock, fd.ns[tk.node] - K0);
+        return T.ke > 0 && T.r0 < T.nf && T.c0 < T.nf;
+    }
+    __device__ float a(const Tile &T, int m, int kk) const {
+        const int r = T.r0 + m;
+        if (r >= T.nf || kk >= T.ke) return 0.f;
+        return T.F[(int64_t)(K0 + kk) * T.nf + r];
+    }
+    __device__ float b(const Tile &T, int n, int kk) const {
+        const int c = T.c0 + n;
+        if (c >= T.nf || kk >= T.ke) return 0.f;
+        const float *col = T.F + (int64_t)(K0 + kk) * T.nf;
+        return col[c] * col[K0 + kk];
+    }
+    __device__ void store(const Tile &T, int m, int n0, const float (&v)[32]) const {
+        const int r = T.r0 + m;
+        if (r >= T.nf) return;
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+            const int c = T.c0 + n0 + cc;
+            if (c < T.nf && r >= c) T.F[(int64_t)c * T.nf + r] -= v[cc];
+        }
+    }
+};
+
 template <class Op>
 void launch(cudaStream_t s, dim3 grid, const Op &op) {
     HSIM_SMEM_LIMIT_ONCE(k_tc32<Op>, SMEM);
@@ -375,6 +422,11 @@ void solve_fwd_tc(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_no
     if (n_nodes <= 0 || k <= 0 || max_nf <= 0) return;
     FwdSolveOp op{fd, nodes, (int)cdiv(max_nf, BM), k, ldx, arena, X, Y, aligned16f(X, ldx) && aligned16f(Y, ldx)};
     launch(s, dim3((unsigned)((int64_t)n_nodes * op.rt), cdiv(k, BN)), op);
+}
+
+void schur_tc(cudaStream_t s, const FrontDev &fd, const SchurTask *tasks, int ntasks, int K0, float *arena) {
+    if (ntasks <= 0) return;
+    launch(s, dim3((unsigned)ntasks), SchurOp{fd, tasks, K0, arena});
 }
 
 void gemm_tasks_tc(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles, const float *Ab, const float *Bb,

@@ -142,9 +142,11 @@ void front_extend_add(cudaStream_t s, const FrontDev &fd, const int *parent, con
 template <typename T>
 void front_panel(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
                  int max_rows, T *arena, double pivot_tol, int *flags);
+// c_end (front-local column): only the trailing columns below c_end are
+// updated (the blocked factorisation's in-block updates); INT_MAX: all
 template <typename T>
 void front_update(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int k0,
-                  int max_trail, T *arena);
+                  int max_trail, T *arena, int c_end);
 // max |F_t[i,i]| over the pivots of nodes 0..n_nodes-1 (bit pattern of a
 // non-negative double, atomically maximised into *out)
 template <typename T>
@@ -215,6 +217,16 @@ void gemm_tasks_tc(cudaStream_t s, const GemmTask *tasks, int ntasks, int tiles,
                    float *Cb);
 // numbers the tasks' 128 x 128 tiles consecutively (tile0); returns the total
 int gemm_tiles_tc(std::vector<GemmTask> &tasks);
+// Schur-complement update of the blocked FP32 factorisation after a block of
+// kSchurBlock pivot columns [K0, K0 + kSchurBlock): for every listed tile
+// (node, m0, n0) of a front's trailing part (rows and columns from K0 +
+// kSchurBlock on, lower triangle), F(r, c) -= sum_kk L(r, kk) d_kk L(c, kk)
+// over the node's pivots kk of the block.
+constexpr int kSchurBlock = 128;
+struct SchurTask {
+    int node, m0, n0;
+};
+void schur_tc(cudaStream_t s, const FrontDev &fd, const SchurTask *tasks, int ntasks, int K0, float *arena);
 // fails with HSIM_E_TIMEOUT (and clears the flag) if a product's bounded
 // mbarrier wait gave up since the last check
 void tc32_check(cudaStream_t s);

@@ -3,10 +3,12 @@ operand split into two TF32 halves) in the mixed path's factorisation and
 solves (Sec. 3.2, direct solver; Alg. 1 solves with one factor of
 K = S - mu M per level), through the C ABI entry hsim_shifted_solve_f32.
 
-The mesh is large enough that its elimination tree has separators of a few
-hundred vertices, so every tensor-core operation runs: block-doubling
+The meshes are large enough that their elimination trees have separators of
+a few hundred vertices, so every tensor-core operation runs: block-doubling
 inversion levels of 64 and more, W products of fronts with 128 pivots and
-more, forward products of the heights whose fronts have 300 pivots or more.  The bar is
+more, forward products of the heights whose fronts have 300 pivots or more,
+and the blocked factorisation of the heights whose fronts have 512 rows or
+more (rank-128 Schur-complement updates of each block of 128 pivots).  The bar is
 the backward error ||B - K X||_F / (||K||_1 ||X||_F), computed in FP64 by
 SciPy, against the same solve with every product on the CUDA cores
 (HSIM_TC32=0): the tensor-core products carry about 2^-21 of sum |a b| against
@@ -40,10 +42,10 @@ def backward_error(K, X, B):
     return np.linalg.norm(R) / (spla.norm(K, 1) * np.linalg.norm(X))
 
 
-@pytest.mark.parametrize("mu,k", [(-5.0, 256), (-500.0, 37)])
-def test_tensor_core_solve_backward_error(hs, monkeypatch, mu, k):
+@pytest.mark.parametrize("grid,mu,k", [(200, -5.0, 256), (200, -500.0, 37), (320, -5.0, 64)])
+def test_tensor_core_solve_backward_error(hs, monkeypatch, grid, mu, k):
     import torch
-    mesh = synth.bumpy_torus(200, 200, 5)
+    mesh = synth.bumpy_torus(grid, grid, 5)
     ctx = hs.Context(0)
     hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=50, levels=2, start_vertex=11, precision=hs.HSIM_MIXED)
     S = assembly.stiffness(mesh)
