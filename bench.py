@@ -166,7 +166,8 @@ def main():
     ap.add_argument("--max-iters", type=int, default=100)
     ap.add_argument("--leaf-size", type=int, default=0, help="nested-dissection leaf size (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz", "ritz_tc"],
+    ap.add_argument("--kernel", default=None, choices=["gram", "gram_tc", "update", "update_tc", "spmm", "ritz", "ritz_tc",
+                                                       "factor_tc", "hierarchy"],
                     help="time one step-level kernel on random data instead of the solve (profiling)")
     ap.add_argument("--mesh-nu", type=int, default=0,
                     help="--kernel spmm: an nu x nu bumpy torus instead of the workload's mesh")
@@ -354,6 +355,9 @@ def run_kernel(args):
 
     import paper_2111_09039_gb300 as hs
     ctx = hs.Context(0)
+    if args.kernel == "hierarchy":
+        run_hierarchy(args, hs, ctx)
+        return
     g = torch.Generator(device="cuda:0").manual_seed(0)
     n, q = args.rows, args.cols
     A = torch.randn((n, q), dtype=torch.float64, device="cuda:0", generator=g)
@@ -372,6 +376,19 @@ def run_kernel(args):
         A = torch.randn((mesh.n, q), dtype=torch.float64, device="cuda:0", generator=g)
         fn = lambda: hs.spmm(ctx, rp, cl, S, A)
         flops, nbytes = 2.0 * S.numel() * q, 16.0 * mesh.n * q + 12.0 * S.numel()
+    elif args.kernel == "factor_tc":
+        # FP32 factorisation (blocked, tensor-core Schur updates on large
+        # fronts) and inverted-form solve of S - mu M, mu = -5, level 0 of a
+        # --mesh-nu x --mesh-nu bumpy torus, --cols right-hand sides
+        import synth
+        nu = args.mesh_nu if args.mesh_nu > 0 else 320
+        mesh = synth.bumpy_torus(nu, nu, 5)
+        hier = hs.Hierarchy(ctx, mesh.F, V=mesh.V, p=50, levels=2, start_vertex=11, precision=hs.HSIM_MIXED)
+        S, Md = hs.assemble(ctx, hier, V=torch.as_tensor(mesh.V, device="cuda:0"))
+        n = mesh.n
+        X0 = torch.randn((n, q), dtype=torch.float64, device="cuda:0", generator=g)
+        fn = lambda: hs.shifted_solve(ctx, hier, 0, S, Md, -5.0, X0, f32=True)
+        flops, nbytes = 0.0, 8.0 * n * q
     elif args.kernel in ("gram", "gram_tc"):
         fn = (lambda: hs.gram(ctx, A, B)) if args.kernel == "gram" else (lambda: hs.gram_tc(ctx, A, B, args.digits))
         flops, nbytes = 2.0 * n * q * q, 16.0 * n * q
@@ -403,6 +420,34 @@ def run_kernel(args):
     print(json.dumps({"kernel": args.kernel, "rows": n, "cols": q, "ms": ms, **extra,
                       "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12,
                       "algorithmic_gbs": nbytes / (ms * 1e-3) / 1e9}), flush=True)
+
+
+def run_hierarchy(args, hs, ctx):
+    """Wall time of hsim_build_hierarchy on --workload: the farthest-point
+    order and prolongations on the GPU (the default) and on the host, one
+    untimed GPU build first, `steps` timed builds each."""
+    import time
+
+    import torch
+
+    import synth
+    w, mesh, start = synth.make_workload(args.workload)
+    kw = dict(V=mesh.V) if mesh.V is not None else dict(L2=mesh.L2)
+
+    def build(dev):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        h = hs.Hierarchy(ctx, mesh.F, p=w.p, levels=w.levels, start_vertex=start, hier_device=dev, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        h.close()
+        return dt
+
+    build(1)
+    out = {"kernel": "hierarchy", "workload": args.workload, "vertices": mesh.n}
+    for dev, key in ((1, "gpu_s"), (0, "host_s")):
+        out[key] = min(build(dev) for _ in range(max(1, args.steps)))
+    print(json.dumps(out), flush=True)
 
 
 def run_sweep(args):
