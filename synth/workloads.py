@@ -42,9 +42,11 @@ WORKLOADS = {
     "bumpy_torus_1000": Workload("bumpy_torus_1000", "bumpy_torus", (1000, 1000, 3), p=500,
                                  levels=3, tol=1e-5, seed=3),
     # a 250,000-vertex member of the bumpy-torus family with the benchmark's p and
-    # levels (stored oracle eigenvalues at tol 1e-10 for the parity tests)
+    # levels (stored oracle eigenvalues for the parity tests).  tol 1e-9: the FP64
+    # oracle's eq. conv2 residuals stop near 1.8e-10 on this mesh (unit roundoff
+    # times lambda_max / lambda_1, about 5.5e5), so 1e-10 is out of FP64's reach
     "bumpy_torus_500": Workload("bumpy_torus_500", "bumpy_torus", (500, 500, 3), p=500,
-                                levels=3, tol=1e-10, seed=3),
+                                levels=3, tol=1e-9, seed=3),
     # icosphere subdivision 6 (40,962 vertices), noise seed 5: spectral loss source
     "icosphere6_grad": Workload("icosphere6_grad", "displaced_icosphere", (6, 5), p=50,
                                 levels=2, tol=1e-10, seed=5),

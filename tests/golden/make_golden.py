@@ -129,6 +129,15 @@ def load(name: str) -> np.ndarray:
     return np.array([float(x) for x in open(path) if x.strip() and not x.startswith("#")])
 
 
+def load_tol(name: str) -> float:
+    """The tolerance the stored eigenvalues were computed at (header line)."""
+    path = os.path.join(HERE, f"oracle_eigs_{name}.txt")
+    for line in open(path):
+        if line.startswith("#") and "tol = " in line:
+            return float(line.split("tol = ")[1].split(",")[0])
+    raise ValueError(f"{path}: no tolerance in the header")
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
     workers = 0
