@@ -409,9 +409,9 @@ hsim_status hsim_shifted_solve_f32(hsim_ctx *ctx, hsim_hier *hier, int tau, cons
  * is issued on cuda_stream (a cudaStream_t, NULL = legacy default stream).
  * The call synchronizes that stream several times (after the factorisation
  * of M_bar and after every sweep, to read the rotation count) and returns
- * only after the stream has drained.  The first call on a device
- * (made while it is current) looks up the array's device address, so make
- * it before any stream capture.  All calls share the array: calls that
+ * only after the stream has drained, so it cannot be captured into a CUDA
+ * graph.  The first call on a device (made while it is current) looks up the
+ * array's device address.  All calls share the array: calls that
  * overlap on the GPU (other streams or host threads) race and must be
  * serialised by the caller. */
 #define HSIM_RITZ_NOALLOC_MAX 256
