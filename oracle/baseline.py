@@ -94,27 +94,21 @@ def parallel_solve_time(K, B, workers: int) -> float:
     return max(times)
 
 
-def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: int | None = None,
-           **_ignored) -> dict:
+def fit(workload: str = "bumpy_torus_1000", grids=None, workers: int | None = None) -> dict:
+    """Time the oracle's steps on the smaller meshes of the workload's recipe
+    and fit the power laws (see the module docstring)."""
     w = synth.WORKLOADS[workload]
     if w.family == "bumpy_torus":
         nu, nv, seed = w.params
-        n_full = nu * nv
         base = max(nu, nv)
         grids = grids or [base // 6, base // 4, base // 3]
         make = lambda g: synth.bumpy_torus(g, max(4, int(round(g * nv / nu))), seed)
     else:
-        full = w.mesh()
-        n_full = full.n
         sub, seed = w.params[0], w.params[1]
         grids = grids or [max(2, sub - 3), max(2, sub - 2)]
         make = lambda g: synth.displaced_icosphere(g, seed)
     workers = workers or _cores()
-    p = w.p
-    q = subspace_size(p)
-    sizes = level_sizes(n_full, p, w.levels)
-    if iters is None:
-        raise ValueError("iteration counts per level are an input of the baseline model")
+    q = subspace_size(w.p)
     rng = np.random.default_rng(0)
     ns, tf, ts, tg = [], [], [], []
     for g in grids:
@@ -134,25 +128,52 @@ def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: 
         Pb = rng.standard_normal((q, q))
         tg.append(_time(lambda: (Psi.T @ SP, Psi.T @ MP, Psi @ Pb)))
         ns.append(mesh.n)
-    f_fac, e_fac = _fit(ns, tf)
-    f_sol, e_sol = _fit(ns, ts)
-    f_gram, e_gram = _fit(ns, tg)
+    return {"workers": workers, "q": q, "ns": ns, "factor": tf, "solve": ts, "gram": tg,
+            "fits": {k: _fit(ns, t) for k, t in (("factor", tf), ("solve", ts), ("gram", tg))}}
+
+
+def predict(model: dict, sizes, iters, coarse_s: float) -> float:
+    """Modelled oracle time of an HSIM run with the given level sizes and
+    iterations per level: per sparse level one factorisation plus, per
+    subspace iteration, two q-column solves and one Gram/update step; plus
+    the coarsest level's dense eigensolve (coarse_s, timed)."""
+    f = {k: v[0] for k, v in model["fits"].items()}
     total = 0.0
     for tau in range(len(sizes) - 1):
         n = sizes[tau]
-        total += f_fac(n) + iters[tau] * (2.0 * f_sol(n) + f_gram(n))
-    nc = sizes[-1]
+        total += f["factor"](n) + iters[tau] * (2.0 * f["solve"](n) + f["gram"](n))
+    return total + coarse_s
+
+
+def coarse_time(nc: int, q: int) -> float:
+    """Time of SciPy's dense generalised eigensolve of the coarsest level's
+    size (lowest q pairs)."""
+    rng = np.random.default_rng(0)
     A = rng.standard_normal((nc, nc))
     A = A @ A.T
     Bm = np.eye(nc) + 0.01 * (A / np.abs(A).max())
-    total += _time(lambda: sla.eigh(A, Bm, subset_by_index=[0, q - 1]))
+    return _time(lambda: sla.eigh(A, Bm, subset_by_index=[0, q - 1]))
+
+
+def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: int | None = None,
+           **_ignored) -> dict:
+    w = synth.WORKLOADS[workload]
+    if iters is None:
+        raise ValueError("iteration counts per level are an input of the baseline model")
+    n_full = w.params[0] * w.params[1] if w.family == "bumpy_torus" else w.mesh().n
+    sizes = level_sizes(n_full, w.p, w.levels)
+    model = fit(workload, grids, workers)
+    q, workers = model["q"], model["workers"]
+    total = predict(model, sizes, iters, coarse_time(sizes[-1], q))
+    ns, tf, ts, tg = model["ns"], model["factor"], model["solve"], model["gram"]
+    e_fac, e_sol, e_gram = (model["fits"][k][1] for k in ("factor", "solve", "gram"))
     wall = float(sum(tf) + sum(ts) + sum(tg))
     return {
         "kind": "oracle", "value": total, "unit": "s", "cores": workers,
         "model": {"grids_vertices": ns, "factor_s": tf, "solve_q_cols_s": ts, "gram_update_s": tg,
                   "exponents": {"factor": e_fac, "solve": e_sol, "gram_update": e_gram},
                   "levels": sizes, "iters": list(iters), "q": q},
-        "sample": (f"oracle steps timed on {len(grids)} smaller meshes of the same recipe ({ns} vertices): "
+        "sample": (f"oracle steps timed on {len(ns)} smaller meshes of the same recipe ({ns} vertices): "
                    f"SuperLU factor of S - mu M, solve of q={q} right-hand sides over {workers} worker "
                    f"processes, Gram+update at q={q} (BLAS on all cores); power laws (exponents factor "
                    f"{e_fac:.2f}, solve {e_sol:.2f}, gram {e_gram:.2f}) evaluated at levels {sizes} with "
@@ -160,7 +181,77 @@ def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: 
     }
 
 
+class _ParallelFactor:
+    """splu(K) held by `workers` spawned processes; solve(B) splits the columns
+    of B over them (the solve the model times)."""
+
+    def __init__(self, K, workers):
+        self.workers = workers
+        saved = {k: os.environ.get(k) for k in _BLAS_ENV}
+        os.environ.update({k: "1" for k in _BLAS_ENV})
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_init_lu, initargs=(K,))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def solve(self, B):
+        B = np.asarray(B)
+        step = -(-B.shape[1] // self.workers)
+        blocks = [np.ascontiguousarray(B[:, a:a + step]) for a in range(0, B.shape[1], step)]
+        return np.hstack(self.pool.map(_solve_with_lu, blocks))
+
+    def __del__(self):
+        try:
+            self.pool.terminate()
+        except Exception:
+            pass
+
+
+_LU = None
+
+
+def _init_lu(K):
+    global _LU
+    _LU = spla.splu(K)
+
+
+def _solve_with_lu(B):
+    return _LU.solve(B)
+
+
+def validate(grid: int = 300, workload: str = "bumpy_torus_1000", tol: float = 1e-5,
+             workers: int | None = None) -> dict:
+    """Check the model against a whole oracle HSIM: the oracle (Alg. 3, solves
+    spread over `workers` processes as the model assumes) on a grid x grid
+    member of the workload's recipe, timed end to end, against the model
+    fitted on the workload's sample meshes and evaluated at this mesh's level
+    sizes with the iteration counts the oracle took."""
+    from . import sim
+    w = synth.WORKLOADS[workload]
+    nu, nv, seed = w.params
+    mesh = synth.bumpy_torus(grid, max(4, int(round(grid * nv / nu))), seed)
+    workers = workers or _cores()
+    start = w.start_vertex(mesh.n)
+    t = time.perf_counter()
+    r = sim.hsim(mesh, w.p, w.levels, tol, start, factor=lambda K: _ParallelFactor(K, workers))
+    measured = time.perf_counter() - t
+    sizes = r.hierarchy.sizes
+    # iterations per sparse level, finest first (the oracle reports coarse to fine)
+    iters = list(reversed(r.iters)) + [0]
+    model = fit(workload, None, workers)
+    predicted = predict(model, sizes, iters, coarse_time(sizes[-1], model["q"]))
+    return {"grid": grid, "vertices": mesh.n, "levels": sizes, "iters": iters, "workers": workers,
+            "measured_s": measured, "predicted_s": predicted, "ratio": measured / predicted}
+
+
 if __name__ == "__main__":
     import json
     import sys
-    print(json.dumps(sample(sys.argv[1] if len(sys.argv) > 1 else "bumpy_torus_1000", iters=[8, 13, 0])))
+    if len(sys.argv) > 1 and sys.argv[1] == "--validate":
+        print(json.dumps(validate(int(sys.argv[2]) if len(sys.argv) > 2 else 300)))
+    else:
+        print(json.dumps(sample(sys.argv[1] if len(sys.argv) > 1 else "bumpy_torus_1000", iters=[8, 13, 0])))
