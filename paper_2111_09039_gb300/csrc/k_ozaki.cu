@@ -10,8 +10,10 @@
 // which BF16 represents exactly.  A digit product is an integer of at most
 // 2^14, so up to 1024 of them sum exactly in an FP32 accumulator: the tensor
 // cores compute sum_r d_s(x_ir) d_t(y_jr) with no rounding, grouped by
-// D = s + t (pairs with D >= SL are dropped), over K-chunks of 128, and
-// every chunk is flushed into FP32 TwoSum pairs.  The result equals the FP64
+// D = s + t (pairs with D >= SL are dropped).  The sum for D = SL - 1 takes
+// SL digit pairs per K row, so K-chunks of flush_k<SL>() rows (192 for five
+// digits, 160 for six: at most 1024 / SL, a multiple of the 32-row stage)
+// stay exact, and every chunk is flushed into FP32 TwoSum pairs.  The result equals the FP64
 // product up to the dropped tail, about 2^-(8 SL - 1) of max|x_i.| max|y_j.|
 // per term (2^-47 with six digits).
 //
@@ -35,7 +37,6 @@ namespace {
 
 constexpr int kSlices = kOzakiSlices;  // the most digits an operand holds (scratch sizing)
 constexpr int TKs = 32;      // K padding of the digit slices (one pipeline stage)
-constexpr int kFlush = 128;  // K rows per exact FP32 chunk
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
@@ -228,7 +229,7 @@ int sm_count_oz() {
 //
 // Warp roles (320 threads): warp 0 issues the TMA loads, warp 1 owns the
 // TMEM allocation and issues the MMAs (one thread), warps 2..9 drain TMEM:
-// after every 128 K-rows (the exact-FP32 chunk) they read acc_0..acc_5 and
+// after every exact-FP32 chunk of flush_k<SL>() K rows they read acc_0..acc_5 and
 // add 2^-8D acc_D into FP32 (hi, lo) TwoSum pairs held in registers, one
 // TMEM lane (output row) and 32 of the 64 columns per thread.  Every wait on an mbarrier gives up
 // after a bounded number of polls, records an error flag the host checks,
@@ -237,6 +238,10 @@ int sm_count_oz() {
 constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_STAGES = 3;
 constexpr int TC_THREADS = 320, TC_DRAIN = 256;  // 10 warps, 8 of them drain TMEM
 constexpr int TC_KG = TC_K / 8;
+// K rows per exact FP32 chunk: SL digit pairs per row for the sum D = SL - 1,
+// each at most 2^14, so chunk x SL <= 1024 keeps the FP32 sums exact
+template <int SL> __host__ __device__ constexpr int flush_k() { return (1024 / SL) / TC_K * TC_K; }
+static_assert(flush_k<5>() == 192 && flush_k<6>() == 160, "exact chunk lengths");
 // stage sizes for SL digit slices: X 128 rows, Y 64 rows (SL = 6: 49,152 + 24,576 bytes)
 template <int SL> __host__ __device__ constexpr uint32_t tc_a_bytes() { return 16u * TC_M * SL * TC_KG; }
 template <int SL> __host__ __device__ constexpr uint32_t tc_b_bytes() { return 16u * TC_N * SL * TC_KG; }
@@ -339,6 +344,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int k_beg = blockIdx.z * k_split;
     const int k_end = min(k_len, k_beg + k_split);
     const int nk = k_end > k_beg ? (k_end - k_beg) / TC_K : 0;
+    constexpr int kFlush = flush_k<SL>();
     const int nchunks = (nk + (kFlush / TC_K) - 1) / (kFlush / TC_K);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // stages on a 1024-byte boundary
@@ -486,6 +492,7 @@ void launch_tc(cudaStream_t s, int M, int N, const __nv_bfloat16 *Xs, int rows_p
     HSIM_CHECK_ARG(!lower || M == N, "ozaki product: lower triangle needs a square result");
     HSIM_SMEM_LIMIT_ONCE(k_ozaki_tc<SL>, tc_smem<SL>());
     int k_split = (int)((k_len + splits - 1) / splits);
+    constexpr int kFlush = flush_k<SL>();
     k_split = (k_split + kFlush - 1) / kFlush * kFlush;
     splits = (int)cdiv(k_len, k_split);
     dim3 g(cdiv(N, TC_N), cdiv(M, TC_M), (unsigned)splits);
