@@ -11,14 +11,19 @@ to the workload:
   inverse iteration with the column blocks spread over one worker process
   per core (each worker factors its own copy, untimed, with one BLAS thread,
   and times the solve of its block; the parallel solve takes the slowest
-  worker's time), and the Gram products Psi^T S Psi, Psi^T M Psi plus the
-  update Psi Phi_bar at the real subspace size q (NumPy BLAS on all cores);
-* each step's time is fitted by a power law in the number of vertices and
-  evaluated at every level's size;
-* a sparse level is charged one factorisation plus, per subspace iteration,
-  two q-column solves and one Gram/update step; the coarsest level one dense
-  eigensolve of its real size.  The iteration counts per level are an input
-  (the benchmark passes the ones its GPU run took).
+  worker's time), and the rest of one subspace iteration as oracle/sim.py
+  does it (M-normalisation, S Psi and M Psi, the Grams, the update Psi
+  Phi_bar, the residuals of eq. conv2; NumPy BLAS on all cores);
+* each of these is fitted by a power law in the number of vertices and
+  evaluated at every level's size; the q x q eigensolve of an iteration and
+  the start-up of the worker processes are timed once;
+* a sparse level is charged the worker start-up and one factorisation plus,
+  per subspace iteration, two q-column solves, the rest of the iteration and
+  the q x q eigensolve; the coarsest level one dense eigensolve of its real
+  size.  The iteration counts per level are an input (the benchmark passes
+  the ones its GPU run took).
+* validate() checks the model against the oracle's whole HSIM, timed end to
+  end on a mid-size member of the recipe.
 
 The workers are started with the spawn method (fresh interpreters that load
 NumPy/SciPy with one BLAS thread each: forked workers inherit a BLAS thread
@@ -123,25 +128,73 @@ def fit(workload: str = "bumpy_torus_1000", grids=None, workers: int | None = No
         B = rng.standard_normal((mesh.n, q))
         ts.append(parallel_solve_time(K, B, workers))
         Psi = rng.standard_normal((mesh.n, q))
-        SP = S @ Psi
-        MP = M @ Psi
         Pb = rng.standard_normal((q, q))
-        tg.append(_time(lambda: (Psi.T @ SP, Psi.T @ MP, Psi @ Pb)))
+        lam = np.linspace(1.0, 100.0, q)
+        tg.append(_time(lambda: _iteration_rest(S, M, Md, Psi, Pb, lam)))
         ns.append(mesh.n)
     return {"workers": workers, "q": q, "ns": ns, "factor": tf, "solve": ts, "gram": tg,
+            "ritz": ritz_time(q), "pool": pool_start_time(workers),
             "fits": {k: _fit(ns, t) for k, t in (("factor", tf), ("solve", ts), ("gram", tg))}}
+
+
+def _iteration_rest(S, M, Md, Psi, Pb, lam):
+    """The oracle's work per subspace iteration besides the solves and the
+    q x q eigensolve (oracle/sim.py): M-normalisation of Psi, S Psi and
+    M Psi, the Grams, the update Psi Phi_bar and the residuals of eq. conv2."""
+    from . import sim
+    Psi = Psi / np.sqrt(np.einsum("ij,ij->j", Psi, M @ Psi))[None, :]
+    Sbar = Psi.T @ (S @ Psi)
+    Mbar = Psi.T @ (M @ Psi)
+    Phi = Psi @ Pb
+    return Sbar, Mbar, sim.residuals(S, M, Phi, lam, 1.0 / Md)
+
+
+def ritz_time(q: int) -> float:
+    """Time of the oracle's q x q generalised eigensolve of one iteration."""
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((q, q))
+    A = A + A.T
+    B = rng.standard_normal((q, q))
+    B = np.eye(q) + (B @ B.T) / (10.0 * q)
+    return _time(lambda: sla.eigh(A, B), repeat=3)
+
+
+def pool_start_time(workers: int) -> float:
+    """Start-up of the worker processes that hold a level's factor (spawned
+    interpreters importing NumPy and SciPy), paid once per sparse level."""
+    saved = {k: os.environ.get(k) for k in _BLAS_ENV}
+    os.environ.update({k: "1" for k in _BLAS_ENV})
+    try:
+        t = time.perf_counter()
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_noop, range(workers), chunksize=1)
+        return time.perf_counter() - t
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _noop(i):
+    import scipy.sparse.linalg  # noqa: F401  (what a factor worker imports)
+    return i
 
 
 def predict(model: dict, sizes, iters, coarse_s: float) -> float:
     """Modelled oracle time of an HSIM run with the given level sizes and
-    iterations per level: per sparse level one factorisation plus, per
-    subspace iteration, two q-column solves and one Gram/update step; plus
-    the coarsest level's dense eigensolve (coarse_s, timed)."""
+    iterations per level: per sparse level the worker start-up and one
+    factorisation plus, per subspace iteration, two q-column solves, the
+    rest of the iteration (normalisation, S Psi and M Psi, Grams, update,
+    residuals) and the q x q eigensolve; plus the coarsest level's dense
+    eigensolve (coarse_s, timed)."""
     f = {k: v[0] for k, v in model["fits"].items()}
     total = 0.0
     for tau in range(len(sizes) - 1):
         n = sizes[tau]
-        total += f["factor"](n) + iters[tau] * (2.0 * f["solve"](n) + f["gram"](n))
+        total += model["pool"] + f["factor"](n)
+        total += iters[tau] * (2.0 * f["solve"](n) + f["gram"](n) + model["ritz"])
     return total + coarse_s
 
 
@@ -170,13 +223,15 @@ def sample(workload: str = "bumpy_torus_1000", iters=None, grids=None, workers: 
     wall = float(sum(tf) + sum(ts) + sum(tg))
     return {
         "kind": "oracle", "value": total, "unit": "s", "cores": workers,
-        "model": {"grids_vertices": ns, "factor_s": tf, "solve_q_cols_s": ts, "gram_update_s": tg,
-                  "exponents": {"factor": e_fac, "solve": e_sol, "gram_update": e_gram},
+        "model": {"grids_vertices": ns, "factor_s": tf, "solve_q_cols_s": ts, "iteration_rest_s": tg,
+                  "ritz_q_s": model["ritz"], "worker_start_s": model["pool"],
+                  "exponents": {"factor": e_fac, "solve": e_sol, "iteration_rest": e_gram},
                   "levels": sizes, "iters": list(iters), "q": q},
         "sample": (f"oracle steps timed on {len(ns)} smaller meshes of the same recipe ({ns} vertices): "
                    f"SuperLU factor of S - mu M, solve of q={q} right-hand sides over {workers} worker "
-                   f"processes, Gram+update at q={q} (BLAS on all cores); power laws (exponents factor "
-                   f"{e_fac:.2f}, solve {e_sol:.2f}, gram {e_gram:.2f}) evaluated at levels {sizes} with "
+                   f"processes, the rest of an iteration (normalisation, S Psi, M Psi, Grams, update, "
+                   f"residuals; BLAS on all cores) and the q x q eigensolve; power laws (exponents factor "
+                   f"{e_fac:.2f}, solve {e_sol:.2f}, rest {e_gram:.2f}) evaluated at levels {sizes} with "
                    f"{list(iters)} iterations per level; {wall:.1f} s of timed oracle work"),
     }
 
