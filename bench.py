@@ -749,7 +749,7 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision, tol):
 # 1.171 GB written; Gram with the solve's 5 digits 3.669 GB read + 3 MB written
 # for the full square product of the capture (the solve's Grams compute the
 # lower triangle: an upper bound).
-TC_TRAFFIC_PER_ROW = {"gram": (3668899840 + 2990336) / 200000, "update": (1852843008 + 1170711040) / 200000}
+TC_TRAFFIC_PER_ROW = {"gram": (3090402816 + 3154688) / 200000, "update": (1852248576 + 1170459392) / 200000}
 
 
 def tc_traffic(sizes, iters, q, gram_digits=6):
