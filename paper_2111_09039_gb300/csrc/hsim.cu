@@ -157,6 +157,11 @@ struct LevelData {
     // empty: the height is factored panel by panel)
     std::vector<std::vector<int64_t>> schur_off;
     DevBuf<k::SchurTask> schur_tasks;
+    // FP32 solves of heights 0 and 1 in one launch each way: the fused fronts
+    // of height 1 with their children (fuse_cid[fuse_cptr[i] ..
+    // fuse_cptr[i + 1])), the leaves and height-1 fronts solved per height
+    DevBuf<int> fuse_par, fuse_cptr, fuse_cid, fuse_rest0, fuse_rest1;
+    int fuse_n = 0, fuse_n0 = 0, fuse_n1 = 0, fuse_rows = 0, fuse_front = 0;
 };
 
 struct ProlongData {
@@ -228,6 +233,16 @@ bool tc32_enabled() {
     const char *e = std::getenv("HSIM_TC32");
     return !(e && *e == '0');
 }
+// FP32 solves: each front of height 1 with its leaves in one CTA per column
+// tile (k::solve_fwd_fused / solve_bwd_fused), for parents whose CTA needs at
+// most kFuseSmemCap bytes of shared memory (three CTAs per SM); the others
+// per height.  HSIM_FUSE=0 solves every height separately (for comparison;
+// read at every solve).
+constexpr size_t kFuseSmemCap = 72 * 1024;
+bool fuse_enabled() {
+    const char *e = std::getenv("HSIM_FUSE");
+    return !(e && *e == '0');
+}
 
 int number_tiles(std::vector<k::GemmTask> &tasks, int tile) {
     int nt = 0;
@@ -236,6 +251,61 @@ int number_tiles(std::vector<k::GemmTask> &tasks, int tile) {
         nt += ((t.M + tile - 1) / tile) * ((t.N + tile - 1) / tile);
     }
     return nt;
+}
+
+// Heights 0 and 1 of the FP32 solves: every front of height 1 whose fused
+// CTA fits kFuseSmemCap and has at most k::fused_max_pivots() pivots is
+// solved with its children (all leaves) in one CTA; the rest per height.
+// Not planned when either height reaches the tensor-core forward products.
+void build_fuse_plan(LevelData &L, cudaStream_t s) {
+    const FrontSymbolic &fs = L.fs;
+    L.fuse_n = L.fuse_n0 = L.fuse_n1 = L.fuse_rows = L.fuse_front = 0;
+    if (fs.max_height < 1 || L.h_maxns[0] >= kTcMinFwdPivots || L.h_maxns[1] >= kTcMinFwdPivots) return;
+    std::vector<int> slot(fs.n_nodes, -1);
+    const auto &h1 = fs.by_height[1];
+    for (size_t i = 0; i < h1.size(); ++i) slot[h1[i]] = (int)i;
+    std::vector<std::vector<int>> kids(h1.size());
+    for (int t : fs.by_height[0])
+        if (fs.parent[t] >= 0 && slot[fs.parent[t]] >= 0) kids[slot[fs.parent[t]]].push_back(t);
+    std::vector<char> fused(h1.size(), 0);
+    std::vector<int> par, cptr{0}, cid, rest0, rest1;
+    for (size_t i = 0; i < h1.size(); ++i) {
+        const int P = h1[i];
+        int rows_f = fs.nf[P], nfc_max = 0;
+        int64_t front = k::fused_front_size(fs.nf[P], fs.ns[P]);
+        for (int c : kids[i]) {
+            rows_f += fs.ns[c];
+            nfc_max = std::max(nfc_max, fs.nf[c]);
+            front = std::max(front, k::fused_front_size(fs.nf[c], fs.ns[c]));
+        }
+        const int rows = std::max(rows_f, fs.nf[P] + nfc_max);
+        if (fs.ns[P] > k::fused_max_pivots() || k::fused_smem(rows, (int)front) > kFuseSmemCap) {
+            rest1.push_back(P);
+            continue;
+        }
+        fused[i] = 1;
+        par.push_back(P);
+        cid.insert(cid.end(), kids[i].begin(), kids[i].end());
+        cptr.push_back((int)cid.size());
+        L.fuse_rows = std::max(L.fuse_rows, rows);
+        L.fuse_front = std::max(L.fuse_front, (int)front);
+    }
+    for (int t : fs.by_height[0])
+        if (!(fs.parent[t] >= 0 && slot[fs.parent[t]] >= 0 && fused[slot[fs.parent[t]]])) rest0.push_back(t);
+    if (par.empty()) return;
+    L.fuse_n = (int)par.size();
+    L.fuse_n0 = (int)rest0.size();
+    L.fuse_n1 = (int)rest1.size();
+    auto nz = [](std::vector<int> &v) -> std::vector<int> & {
+        if (v.empty()) v.push_back(0);
+        return v;
+    };
+    L.fuse_par.upload(par, s);
+    L.fuse_cptr.upload(cptr, s);
+    L.fuse_cid.upload(nz(cid), s);
+    L.fuse_rest0.upload(nz(rest0), s);
+    L.fuse_rest1.upload(nz(rest1), s);
+    HSIM_CUDA(cudaStreamSynchronize(s));  // the uploads read the host vectors
 }
 
 void build_inverse_plan(LevelData &L, cudaStream_t s) {
@@ -320,6 +390,7 @@ void build_inverse_plan(LevelData &L, cudaStream_t s) {
             L.h_maxnf[h] = std::max(L.h_maxnf[h], fs.nf[t]);
             L.h_maxns[h] = std::max(L.h_maxns[h], fs.ns[t]);
         }
+    build_fuse_plan(L, s);
 }
 
 void upload_level(LevelData &L, cudaStream_t s) {
@@ -539,9 +610,27 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
         ev.push_back(e);
     };
     mark();
+    const bool fused = L.fuse_n > 0 && fuse_enabled();
     for (int h = 0; h <= fs.max_height; ++h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         const int cnt = (int)(L.hnodes_off[h + 1] - L.hnodes_off[h]);
+        if constexpr (std::is_same<T, float>::value) {
+            if (fused && h <= 1) {
+                // leaves of unfused parents first, then the fused fronts with
+                // their leaves; the unfused fronts of height 1 after both
+                if (h == 0) {
+                    k::solve_fwd_inv(s, L.fd, L.fuse_rest0.p, L.fuse_n0, L.h_maxnf[0], L.h_maxns[0], arena, k, X,
+                                     Y.p, ldx);
+                    k::solve_fwd_fused(s, L.fd, L.fuse_par.p, L.fuse_n, L.fuse_cptr.p, L.fuse_cid.p, L.fuse_rows,
+                                       L.fuse_front, arena, k, X, Y.p, ldx);
+                } else {
+                    k::solve_fwd_inv(s, L.fd, L.fuse_rest1.p, L.fuse_n1, L.h_maxnf[1], L.h_maxns[1], arena, k, X,
+                                     Y.p, ldx);
+                }
+                mark();
+                continue;
+            }
+        }
         if constexpr (std::is_same<T, float>::value) {
             if (tc32_enabled() && L.h_maxns[h] >= kTcMinFwdPivots)
                 k::solve_fwd_tc(s, L.fd, nodes, cnt, L.h_maxnf[h], arena, k, X, Y.p, ldx);
@@ -556,13 +645,32 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
     for (int h = fs.max_height; h >= 0; --h) {
         const int *nodes = L.d_hnodes.p + L.hnodes_off[h];
         const int cnt = (int)(L.hnodes_off[h + 1] - L.hnodes_off[h]);
+        if constexpr (std::is_same<T, float>::value) {
+            if (fused && h <= 1) {
+                // the unfused fronts of height 1 and the fused fronts with
+                // their leaves, then the leaves of unfused parents
+                if (h == 1) {
+                    k::solve_bwd_inv(s, L.fd, L.fuse_rest1.p, L.fuse_n1, L.h_maxns[1], arena, dinv, k, X, Y.p, ldx);
+                    k::solve_bwd_fused(s, L.fd, L.fuse_par.p, L.fuse_n, L.fuse_cptr.p, L.fuse_cid.p, L.fuse_rows,
+                                       L.fuse_front, arena, dinv, k, X, Y.p, ldx);
+                } else {
+                    k::solve_bwd_inv(s, L.fd, L.fuse_rest0.p, L.fuse_n0, L.h_maxns[0], arena, dinv, k, X, Y.p, ldx);
+                }
+                mark();
+                continue;
+            }
+        }
         k::solve_bwd_inv(s, L.fd, nodes, cnt, L.h_maxns[h], arena, dinv, k, X, Y.p, ldx);
         mark();
     }
     if (detail) {
         cudaEventSynchronize(ev.back());
         const int H = fs.max_height + 1;
-        std::string line = "[hsim] solve n=" + std::to_string(L.n) + " rhs=" + std::to_string(k) + " fwd/bwd ms per height:";
+        std::string line = "[hsim] solve n=" + std::to_string(L.n) + " rhs=" + std::to_string(k);
+        if (fused)
+            line += " fused " + std::to_string(L.fuse_n) + " height-1 fronts (unfused: " + std::to_string(L.fuse_n0) +
+                    " leaves, " + std::to_string(L.fuse_n1) + " height-1 fronts)";
+        line += " fwd/bwd ms per height:";
         for (int h = 0; h < H; ++h) {
             float a = 0, b = 0;
             cudaEventElapsedTime(&a, ev[h], ev[h + 1]);

@@ -459,6 +459,255 @@ __global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(Fron
     }
 }
 
+// ---- the lowest two tree heights fused ------------------------------------------
+//
+// A front P of height 1 and its children (all leaves) in one CTA per column
+// tile of kFuseCols right-hand sides.  Shared memory holds P's nf_P rows and
+// the children's rows of the tile.  Forward: each child's product updates
+// P's pivot rows in place and accumulates its updates of P's ancestor rows
+// (the rows of P beyond its pivots, which a child's ancestor rows map into
+// through relmap) as deltas; then P's product; the deltas reach X once, by
+// atomic subtraction (siblings of P share those rows).  Backward: P's pivot
+// rows from D^-1 Y and P's ancestor rows, then each child's pivot rows from
+// D^-1 Y and P's rows, all read from shared memory.  The products of the
+// per-height kernels, in another summation order.
+//
+// Each thread owns a 4 x 4 block of the output (four rows, four columns);
+// the front block is staged with its triangle masked (unit diagonal, zeros
+// beyond it) and its leading dimension padded to a multiple of four, so one
+// 16-byte load gives the four rows' coefficients of a step.
+constexpr int kFuseCols = 64;
+constexpr int kFuseCG = kFuseCols / 4, kFuseRG = 256 / kFuseCG;  // 16 column groups, 16 row groups
+constexpr int kFusePass = 4 * kFuseRG;                            // output rows per pass
+constexpr int kFuseMaxPiv = 2 * kFusePass;                        // pivots of P at most (two passes)
+
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+
+// acc[u][v] += sum_{j in [jb, je)} A[j * lda + r0 + u] * B[j * kFuseCols + c + v]
+__device__ __forceinline__ void mac4x4(float (&acc)[4][4], const float *A, int lda, int r0, const float *B, int c,
+                                       int jb, int je) {
+#pragma unroll 4
+    for (int j = jb; j < je; ++j) {
+        const float4 a = *reinterpret_cast<const float4 *>(A + (size_t)j * lda + r0);
+        const float4 b = *reinterpret_cast<const float4 *>(B + (size_t)j * kFuseCols + c);
+        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+    }
+}
+
+__device__ __forceinline__ void zero4x4(float (&acc)[4][4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+}
+
+// forward operand: As[j * pad4(nf) + r] = A(r, j) (unit lower Linv on the
+// pivot rows, W below), zero on the padding rows
+__device__ __forceinline__ void stage_fwd(const float *__restrict__ F, int nf, int ns, float *As) {
+    const int nfp = pad4(nf), n = ns * nfp;
+    for (int e = threadIdx.x; e < n; e += 256) {
+        const int j = e / nfp, r = e - j * nfp;
+        float a = 0.f;
+        if (r < nf) a = (r >= ns || r > j) ? F[(size_t)j * nf + r] : (r == j ? 1.f : 0.f);
+        As[e] = a;
+    }
+}
+
+// backward operand: At[r * pad4(ns) + i] = Linv(r, i) on the pivot rows,
+// -W(r, i) below, zero on the padding columns
+__device__ __forceinline__ void stage_bwd(const float *__restrict__ F, int nf, int ns, float *At) {
+    const int nsp = pad4(ns), n = nf * nsp;
+    for (int e = threadIdx.x; e < n; e += 256) {
+        const int r = e / nsp, i = e - r * nsp;
+        float a = 0.f;
+        if (i < ns) {
+            const float f = F[(size_t)i * nf + r];
+            a = r >= ns ? -f : (r > i ? f : (r == i ? 1.f : 0.f));
+        }
+        At[e] = a;
+    }
+}
+
+__device__ __forceinline__ void add4(float *p, const float (&a)[4], float sg) {
+    float4 d = *reinterpret_cast<float4 *>(p);
+    d.x += sg * a[0];
+    d.y += sg * a[1];
+    d.z += sg * a[2];
+    d.w += sg * a[3];
+    *reinterpret_cast<float4 *>(p) = d;
+}
+
+__global__ void __launch_bounds__(256) k_solve_fwd_fused(FrontDev fd, const int *__restrict__ parents,
+                                                         const int *__restrict__ child_ptr,
+                                                         const int *__restrict__ child_ids,
+                                                         const float *__restrict__ arena, int k, float *__restrict__ X,
+                                                         float *__restrict__ Y, int ldx, int max_rows, bool vec) {
+    extern __shared__ __align__(16) float fsm[];
+    float *Xs = fsm;                                 // max_rows x kFuseCols
+    float *Fs = fsm + (size_t)max_rows * kFuseCols;  // a staged front block
+    const int P = parents[blockIdx.x];
+    const int nfP = fd.nf[P], nsP = fd.ns[P], psP = fd.pstart[P];
+    const int c0 = blockIdx.y * kFuseCols;
+    const int tid = threadIdx.x, cg = (tid % kFuseCG) * 4, rg = tid / kFuseCG;
+    const int avail = k - c0 - cg;
+    const int cb = child_ptr[blockIdx.x], ce = child_ptr[blockIdx.x + 1];
+    // P's pivot rows from X, its ancestor rows as zero deltas, then the
+    // children's pivot rows
+    for (int r = rg; r < nfP; r += kFuseRG) {
+        float v[4];
+        load4(v, X, (int64_t)psP + r, r < nsP, c0 + cg, k, ldx, vec);
+        sts4(Xs + (size_t)r * kFuseCols + cg, v);
+    }
+    int off = nfP;
+    for (int ci = cb; ci < ce; ++ci) {
+        const int c = child_ids[ci], nsc = fd.ns[c], psc = fd.pstart[c];
+        for (int r = rg; r < nsc; r += kFuseRG) {
+            float v[4];
+            load4(v, X, (int64_t)psc + r, true, c0 + cg, k, ldx, vec);
+            sts4(Xs + (size_t)(off + r) * kFuseCols + cg, v);
+        }
+        off += nsc;
+    }
+    off = nfP;
+    for (int ci = cb; ci < ce; ++ci) {
+        const int c = child_ids[ci], nfc = fd.nf[c], nsc = fd.ns[c], psc = fd.pstart[c];
+        __syncthreads();  // the previous block is no longer read (first child: Xs loaded)
+        stage_fwd(arena + fd.foff[c], nfc, nsc, Fs);
+        __syncthreads();
+        const int *rel = fd.relmap + fd.relmap_off[c];
+        const float *xc = Xs + (size_t)off * kFuseCols;
+        for (int r0 = rg * 4; r0 < nfc; r0 += kFusePass) {
+            float acc[4][4];
+            zero4x4(acc);
+            mac4x4(acc, Fs, pad4(nfc), r0, xc, cg, 0, min(r0 + 4, nsc));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = r0 + u;
+                if (r >= nfc) break;
+                if (r < nsc) {
+                    if (avail > 0) store4(Y + (int64_t)(psc + r) * ldx + c0 + cg, acc[u], avail, vec);
+                } else {  // P's row relmap(r): a pivot value, or a delta subtracted at the end
+                    const int pr = rel[r - nsc];
+                    add4(Xs + (size_t)pr * kFuseCols + cg, acc[u], pr < nsP ? -1.f : 1.f);
+                }
+            }
+        }
+        off += nsc;
+    }
+    // P: its pivot rows are final
+    __syncthreads();
+    stage_fwd(arena + fd.foff[P], nfP, nsP, Fs);
+    __syncthreads();
+    for (int r0 = rg * 4; r0 < nfP; r0 += kFusePass) {
+        float acc[4][4];
+        zero4x4(acc);
+        mac4x4(acc, Fs, pad4(nfP), r0, Xs, cg, 0, min(r0 + 4, nsP));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u;
+            if (r >= nfP) break;
+            if (r < nsP) {
+                if (avail > 0) store4(Y + (int64_t)(psP + r) * ldx + c0 + cg, acc[u], avail, vec);
+            } else {
+                add4(Xs + (size_t)r * kFuseCols + cg, acc[u], 1.f);
+            }
+        }
+    }
+    __syncthreads();
+    if (avail <= 0) return;
+    const int *rowsP = fd.rows + fd.rows_off[P];
+    for (int r = nsP + rg; r < nfP; r += kFuseRG) {
+        float d[4];
+        lds4(d, Xs + (size_t)r * kFuseCols + cg);
+        sub4_atomic(X + (int64_t)rowsP[r] * ldx + c0 + cg, d, avail, vec);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_solve_bwd_fused(FrontDev fd, const int *__restrict__ parents,
+                                                         const int *__restrict__ child_ptr,
+                                                         const int *__restrict__ child_ids,
+                                                         const float *__restrict__ arena,
+                                                         const float *__restrict__ dinv, int k, float *__restrict__ X,
+                                                         const float *__restrict__ Y, int ldx, int max_rows, bool vec) {
+    extern __shared__ __align__(16) float fsm[];
+    float *Xs = fsm;
+    float *Fs = fsm + (size_t)max_rows * kFuseCols;
+    const int P = parents[blockIdx.x];
+    const int nfP = fd.nf[P], nsP = fd.ns[P], psP = fd.pstart[P];
+    const int c0 = blockIdx.y * kFuseCols;
+    const int tid = threadIdx.x, cg = (tid % kFuseCG) * 4, rg = tid / kFuseCG;
+    const int avail = k - c0 - cg;
+    const int cb = child_ptr[blockIdx.x], ce = child_ptr[blockIdx.x + 1];
+    const int *rowsP = fd.rows + fd.rows_off[P];
+    // P's pivot rows: D^-1 Y; its ancestor rows: final X
+    for (int r = rg; r < nfP; r += kFuseRG) {
+        float v[4];
+        if (r < nsP) {
+            load4(v, Y, (int64_t)psP + r, true, c0 + cg, k, ldx, vec);
+            const float di = dinv[psP + r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] *= di;
+        } else {
+            load4(v, X, (int64_t)rowsP[r], true, c0 + cg, k, ldx, vec);
+        }
+        sts4(Xs + (size_t)r * kFuseCols + cg, v);
+    }
+    stage_bwd(arena + fd.foff[P], nfP, nsP, Fs);
+    __syncthreads();
+    // X_P = Linv^T D^-1 Y_P - W^T X_anc: rows i0.. of the output (two passes at most)
+    float acc[2][4][4];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        zero4x4(acc[p]);
+        const int i0 = rg * 4 + p * kFusePass;
+        if (i0 < nsP) mac4x4(acc[p], Fs, pad4(nsP), i0, Xs, cg, i0, nfP);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = rg * 4 + p * kFusePass + u;
+            if (i >= nsP) continue;
+            sts4(Xs + (size_t)i * kFuseCols + cg, acc[p][u]);
+            if (avail > 0) store4(X + (int64_t)(psP + i) * ldx + c0 + cg, acc[p][u], avail, vec);
+        }
+    // children: D^-1 Y of their pivot rows, then copies of P's rows they read
+    float *vc = Xs + (size_t)nfP * kFuseCols;
+    for (int ci = cb; ci < ce; ++ci) {
+        const int c = child_ids[ci], nfc = fd.nf[c], nsc = fd.ns[c], psc = fd.pstart[c];
+        const int *rel = fd.relmap + fd.relmap_off[c];
+        __syncthreads();  // P's rows written; the previous child's rows and block no longer read
+        for (int r = rg; r < nfc; r += kFuseRG) {
+            float v[4];
+            if (r < nsc) {
+                load4(v, Y, (int64_t)psc + r, true, c0 + cg, k, ldx, vec);
+                const float di = dinv[psc + r];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] *= di;
+            } else {
+                lds4(v, Xs + (size_t)rel[r - nsc] * kFuseCols + cg);
+            }
+            sts4(vc + (size_t)r * kFuseCols + cg, v);
+        }
+        stage_bwd(arena + fd.foff[c], nfc, nsc, Fs);
+        __syncthreads();
+        for (int i0 = rg * 4; i0 < nsc; i0 += kFusePass) {
+            float a[4][4];
+            zero4x4(a);
+            mac4x4(a, Fs, pad4(nsc), i0, vc, cg, i0, nfc);
+            if (avail <= 0) continue;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u < nsc) store4(X + (int64_t)(psc + i0 + u) * ldx + c0 + cg, a[u], avail, vec);
+        }
+    }
+}
+
 template <typename T>
 bool aligned16(const T *p, int ldx) {
     return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && ((size_t)ldx * sizeof(T)) % 16 == 0;
@@ -600,6 +849,40 @@ void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
     const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
     if (max_ns <= 32) launch_bwd_inv<T, 32, 1>(s, fd, nodes, n_nodes, 1, arena, dinv, k, X, Y, ldx, vec);
     else launch_bwd_inv<T, 64, 2>(s, fd, nodes, n_nodes, (max_ns + 63) / 64, arena, dinv, k, X, Y, ldx, vec);
+}
+
+size_t fused_smem(int max_rows, int max_front) {
+    return ((size_t)max_rows * kFuseCols + (size_t)max_front) * sizeof(float);
+}
+
+int64_t fused_front_size(int nf, int ns) { return std::max<int64_t>((int64_t)ns * pad4(nf), (int64_t)nf * pad4(ns)); }
+
+int fused_max_pivots() { return kFuseMaxPiv; }
+
+void solve_fwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
+                     const int *child_ids, int max_rows, int max_front, const float *arena, int k, float *X, float *Y,
+                     int ldx) {
+    if (n_parents <= 0 || k <= 0) return;
+    const size_t sm = fused_smem(max_rows, max_front);
+    HSIM_SMEM_LIMIT_ONCE(k_solve_fwd_fused, kFusedSmemMax);
+    HSIM_CHECK_ARG(sm <= kFusedSmemMax, "fused solve: shared memory");
+    const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
+    k_solve_fwd_fused<<<dim3((unsigned)n_parents, cdiv(k, kFuseCols)), 256, sm, s>>>(
+        fd, parents, child_ptr, child_ids, arena, k, X, Y, ldx, max_rows, vec);
+    HSIM_LAUNCHED();
+}
+
+void solve_bwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
+                     const int *child_ids, int max_rows, int max_front, const float *arena, const float *dinv, int k,
+                     float *X, const float *Y, int ldx) {
+    if (n_parents <= 0 || k <= 0) return;
+    const size_t sm = fused_smem(max_rows, max_front);
+    HSIM_SMEM_LIMIT_ONCE(k_solve_bwd_fused, kFusedSmemMax);
+    HSIM_CHECK_ARG(sm <= kFusedSmemMax, "fused solve: shared memory");
+    const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
+    k_solve_bwd_fused<<<dim3((unsigned)n_parents, cdiv(k, kFuseCols)), 256, sm, s>>>(
+        fd, parents, child_ptr, child_ids, arena, dinv, k, X, Y, ldx, max_rows, vec);
+    HSIM_LAUNCHED();
 }
 
 #define HSIM_FINV_INSTANTIATE(T)                                                                                    \
