@@ -238,7 +238,7 @@ bool tc32_enabled() {
 // most kFuseSmemCap bytes of shared memory (three CTAs per SM); the others
 // per height.  HSIM_FUSE=0 solves every height separately (for comparison;
 // read at every solve).
-constexpr size_t kFuseSmemCap = 72 * 1024;
+constexpr size_t kFuseSmemCap = 74 * 1024;
 bool fuse_enabled() {
     const char *e = std::getenv("HSIM_FUSE");
     return !(e && *e == '0');
@@ -253,10 +253,11 @@ int number_tiles(std::vector<k::GemmTask> &tasks, int tile) {
     return nt;
 }
 
-// Heights 0 and 1 of the FP32 solves: every front of height 1 whose fused
-// CTA fits kFuseSmemCap and has at most k::fused_max_pivots() pivots is
-// solved with its children (all leaves) in one CTA; the rest per height.
-// Not planned when either height reaches the tensor-core forward products.
+// Heights 0 and 1 of the FP32 solves: every front of height 1 within the
+// fused kernels' limits (pivots, ancestor rows, children) whose CTA, sized
+// for the largest front and rows of the launch, fits kFuseSmemCap is solved
+// with its children (all leaves) in one CTA; the rest per height.  Not
+// planned when either height reaches the tensor-core forward products.
 void build_fuse_plan(LevelData &L, cudaStream_t s) {
     const FrontSymbolic &fs = L.fs;
     L.fuse_n = L.fuse_n0 = L.fuse_n1 = L.fuse_rows = L.fuse_front = 0;
@@ -271,15 +272,15 @@ void build_fuse_plan(LevelData &L, cudaStream_t s) {
     std::vector<int> par, cptr{0}, cid, rest0, rest1;
     for (size_t i = 0; i < h1.size(); ++i) {
         const int P = h1[i];
-        int rows_f = fs.nf[P], nfc_max = 0;
-        int64_t front = k::fused_front_size(fs.nf[P], fs.ns[P]);
+        int rows = fs.nf[P], front = k::fused_front_size(fs.nf[P], fs.ns[P]);
         for (int c : kids[i]) {
-            rows_f += fs.ns[c];
-            nfc_max = std::max(nfc_max, fs.nf[c]);
+            rows += fs.ns[c];
             front = std::max(front, k::fused_front_size(fs.nf[c], fs.ns[c]));
         }
-        const int rows = std::max(rows_f, fs.nf[P] + nfc_max);
-        if (fs.ns[P] > k::fused_max_pivots() || k::fused_smem(rows, (int)front) > kFuseSmemCap) {
+        // one launch: the largest rows and block over the fused parents size every CTA
+        if (fs.ns[P] > k::fused_max_pivots() || fs.nf[P] - fs.ns[P] > k::fused_max_ancestors() ||
+            (int)kids[i].size() > k::fused_max_children() ||
+            k::fused_smem(std::max(rows, L.fuse_rows), std::max(front, L.fuse_front)) > kFuseSmemCap) {
             rest1.push_back(P);
             continue;
         }
@@ -288,7 +289,7 @@ void build_fuse_plan(LevelData &L, cudaStream_t s) {
         cid.insert(cid.end(), kids[i].begin(), kids[i].end());
         cptr.push_back((int)cid.size());
         L.fuse_rows = std::max(L.fuse_rows, rows);
-        L.fuse_front = std::max(L.fuse_front, (int)front);
+        L.fuse_front = std::max(L.fuse_front, front);
     }
     for (int t : fs.by_height[0])
         if (!(fs.parent[t] >= 0 && slot[fs.parent[t]] >= 0 && fused[slot[fs.parent[t]]])) rest0.push_back(t);
@@ -622,7 +623,7 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
                     k::solve_fwd_inv(s, L.fd, L.fuse_rest0.p, L.fuse_n0, L.h_maxnf[0], L.h_maxns[0], arena, k, X,
                                      Y.p, ldx);
                     k::solve_fwd_fused(s, L.fd, L.fuse_par.p, L.fuse_n, L.fuse_cptr.p, L.fuse_cid.p, L.fuse_rows,
-                                       L.fuse_front, arena, k, X, Y.p, ldx);
+                                       L.fuse_front, arena, dinv, k, X, Y.p, ldx);
                 } else {
                     k::solve_fwd_inv(s, L.fd, L.fuse_rest1.p, L.fuse_n1, L.h_maxnf[1], L.h_maxns[1], arena, k, X,
                                      Y.p, ldx);
@@ -652,7 +653,7 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
                 if (h == 1) {
                     k::solve_bwd_inv(s, L.fd, L.fuse_rest1.p, L.fuse_n1, L.h_maxns[1], arena, dinv, k, X, Y.p, ldx);
                     k::solve_bwd_fused(s, L.fd, L.fuse_par.p, L.fuse_n, L.fuse_cptr.p, L.fuse_cid.p, L.fuse_rows,
-                                       L.fuse_front, arena, dinv, k, X, Y.p, ldx);
+                                       L.fuse_front, arena, k, X, Y.p, ldx);
                 } else {
                     k::solve_bwd_inv(s, L.fd, L.fuse_rest0.p, L.fuse_n0, L.h_maxns[0], arena, dinv, k, X, Y.p, ldx);
                 }

@@ -463,34 +463,98 @@ __global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(Fron
 //
 // A front P of height 1 and its children (all leaves) in one CTA per column
 // tile of kFuseCols right-hand sides.  Shared memory holds P's nf_P rows and
-// the children's rows of the tile.  Forward: each child's product updates
-// P's pivot rows in place and accumulates its updates of P's ancestor rows
-// (the rows of P beyond its pivots, which a child's ancestor rows map into
-// through relmap) as deltas; then P's product; the deltas reach X once, by
-// atomic subtraction (siblings of P share those rows).  Backward: P's pivot
-// rows from D^-1 Y and P's ancestor rows, then each child's pivot rows from
-// D^-1 Y and P's rows, all read from shared memory.  The products of the
-// per-height kernels, in another summation order.
+// the children's pivot rows of the tile.  Forward: each child's product
+// updates P's pivot rows in place and accumulates its updates of P's
+// ancestor rows (the rows of P beyond its pivots, which a child's ancestor
+// rows map into through relmap) as deltas; then P's product; the deltas
+// reach X once, by atomic subtraction (siblings of P share those rows).  The
+// forward stores D^-1 Y for these fronts (the product the backward reads;
+// the same rounding as scaling in the backward).  Backward: P's pivot rows
+// from D^-1 Y and P's ancestor rows, then each child's pivot rows from D^-1 Y
+// and P's rows, all read from shared memory.  The products of the per-height
+// kernels, summed in another order.
 //
-// Each thread owns a 4 x 4 block of the output (four rows, four columns);
-// the front block is staged with its triangle masked (unit diagonal, zeros
-// beyond it) and its leading dimension padded to a multiple of four, so one
-// 16-byte load gives the four rows' coefficients of a step.
+// Every global operand arrives by cp.async: the tile's rows at the start,
+// each front's block (with its relmap and D^-1) while the previous front is
+// multiplied (two buffers).  Each thread owns a 4 x 4 block of the output
+// (four rows, four columns); a front block is staged with its leading
+// dimension padded to a multiple of four, so one 16-byte load gives the four
+// rows' coefficients of a step, and the unit-triangular diagonal 4 x 4
+// blocks are masked in registers.
 constexpr int kFuseCols = 64;
 constexpr int kFuseCG = kFuseCols / 4, kFuseRG = 256 / kFuseCG;  // 16 column groups, 16 row groups
-constexpr int kFusePass = 4 * kFuseRG;                            // output rows per pass
-constexpr int kFuseMaxPiv = 2 * kFusePass;                        // pivots of P at most (two passes)
+constexpr int kFuseMaxPiv = 4 * kFuseRG;                          // pivots of P at most (one pass)
+constexpr int kFuseMaxAnc = 8 * kFuseRG;                          // ancestor rows of P at most
+constexpr int kFuseMaxKids = 8;                                   // children of P at most
 
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 
-// acc[u][v] += sum_{j in [jb, je)} A[j * lda + r0 + u] * B[j * kFuseCols + c + v]
-__device__ __forceinline__ void mac4x4(float (&acc)[4][4], const float *A, int lda, int r0, const float *B, int c,
-                                       int jb, int je) {
+// front buffer: the staged block, then relmap (ints), then D^-1 of the pivots
+__host__ __device__ constexpr int fuse_block(int nf, int ns) {
+    return pad4(ns * pad4(nf) > nf * pad4(ns) ? ns * pad4(nf) : nf * pad4(ns));
+}
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// four values of row `row` from column c into shared memory (zero past k)
+__device__ __forceinline__ void row4_async(float *dst, const float *X, int64_t row, int c, int k, int ldx, bool vec) {
+    const float *p = X + row * ldx + c;
+    if (vec) {
+        const int n = k - c >= 4 ? 4 : (k - c > 0 ? k - c : 0);
+        cp_async16(dst, n > 0 ? p : X, 4 * n);
+    } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cp_async4(dst + v, c + v < k ? p + v : X, c + v < k ? 4 : 0);
+    }
+}
+
+struct FuseMeta {
+    int nf, ns, ps;
+    int64_t foff, roff;
+};
+
+// the block of front m, its relmap and (forward) D^-1 of its pivots into buf;
+// forward layout As[j * pad4(nf) + r] = F(r, j), backward At[r * pad4(ns) + i] = F(r, i)
+template <bool FWD>
+__device__ __forceinline__ void stage_front(const FuseMeta &m, const float *__restrict__ arena,
+                                            const int *__restrict__ relmap, const float *__restrict__ dinv,
+                                            float *buf) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const float *F = arena + m.foff;
+    for (int j = warp; j < m.ns; j += 8)
+        for (int r = lane; r < m.nf; r += 32) {
+            float *d = FWD ? buf + (size_t)j * pad4(m.nf) + r : buf + (size_t)r * pad4(m.ns) + j;
+            cp_async4(d, F + (size_t)j * m.nf + r, 4);
+        }
+    int *rel = reinterpret_cast<int *>(buf + fuse_block(m.nf, m.ns));
+    for (int i = threadIdx.x; i < m.nf - m.ns; i += 256) cp_async4(rel + i, relmap + m.roff + i, 4);
+    if (FWD) {
+        float *ds = buf + fuse_block(m.nf, m.ns) + pad4(m.nf - m.ns);
+        for (int i = threadIdx.x; i < m.ns; i += 256) cp_async4(ds + i, dinv + m.ps + i, 4);
+    }
+}
+
+// acc[u][v] += SIGN * sum_{j in [jb, je)} A[j * lda + r0 + u] * B(j)[c + v], B(j) the
+// shared-memory row j of B, or row idx[j - ib] when idx is given
+template <int SIGN>
+__device__ __forceinline__ void mac4x4(float (&acc)[4][4], const float *A, int lda, int r0, const float *B,
+                                       const int *idx, int ib, int c, int jb, int je) {
 #pragma unroll 4
     for (int j = jb; j < je; ++j) {
         const float4 a = *reinterpret_cast<const float4 *>(A + (size_t)j * lda + r0);
-        const float4 b = *reinterpret_cast<const float4 *>(B + (size_t)j * kFuseCols + c);
-        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+        const int br = idx ? idx[j - ib] : j;
+        const float4 b = *reinterpret_cast<const float4 *>(B + (size_t)br * kFuseCols + c);
+        const float av[4] = {SIGN * a.x, SIGN * a.y, SIGN * a.z, SIGN * a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -505,33 +569,6 @@ __device__ __forceinline__ void zero4x4(float (&acc)[4][4]) {
         for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
 }
 
-// forward operand: As[j * pad4(nf) + r] = A(r, j) (unit lower Linv on the
-// pivot rows, W below), zero on the padding rows
-__device__ __forceinline__ void stage_fwd(const float *__restrict__ F, int nf, int ns, float *As) {
-    const int nfp = pad4(nf), n = ns * nfp;
-    for (int e = threadIdx.x; e < n; e += 256) {
-        const int j = e / nfp, r = e - j * nfp;
-        float a = 0.f;
-        if (r < nf) a = (r >= ns || r > j) ? F[(size_t)j * nf + r] : (r == j ? 1.f : 0.f);
-        As[e] = a;
-    }
-}
-
-// backward operand: At[r * pad4(ns) + i] = Linv(r, i) on the pivot rows,
-// -W(r, i) below, zero on the padding columns
-__device__ __forceinline__ void stage_bwd(const float *__restrict__ F, int nf, int ns, float *At) {
-    const int nsp = pad4(ns), n = nf * nsp;
-    for (int e = threadIdx.x; e < n; e += 256) {
-        const int r = e / nsp, i = e - r * nsp;
-        float a = 0.f;
-        if (i < ns) {
-            const float f = F[(size_t)i * nf + r];
-            a = r >= ns ? -f : (r > i ? f : (r == i ? 1.f : 0.f));
-        }
-        At[e] = a;
-    }
-}
-
 __device__ __forceinline__ void add4(float *p, const float (&a)[4], float sg) {
     float4 d = *reinterpret_cast<float4 *>(p);
     d.x += sg * a[0];
@@ -541,83 +578,124 @@ __device__ __forceinline__ void add4(float *p, const float (&a)[4], float sg) {
     *reinterpret_cast<float4 *>(p) = d;
 }
 
-__global__ void __launch_bounds__(256) k_solve_fwd_fused(FrontDev fd, const int *__restrict__ parents,
+// forward product of one staged front on rows r0..r0+3 (column-major As,
+// unit lower triangle on the pivot rows): xs holds its pivot rows
+__device__ __forceinline__ void fwd_rows(float (&acc)[4][4], const float *As, int nf, int ns, int r0, const float *xs,
+                                         int cg) {
+    zero4x4(acc);
+    const int lda = pad4(nf), jd = min(r0, ns);
+    mac4x4<1>(acc, As, lda, r0, xs, nullptr, 0, cg, 0, jd);
+    for (int j = r0; j < min(r0 + 4, ns); ++j) {  // the diagonal block
+        const float4 b = *reinterpret_cast<const float4 *>(xs + (size_t)j * kFuseCols + cg);
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u;
+            const float a = (r >= ns || r > j) ? As[(size_t)j * lda + r] : (r == j ? 1.f : 0.f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += a * bv[v];
+        }
+    }
+}
+
+// backward product of one staged front on outputs i0..i0+3 (row-major At),
+// rows r in [kb, ke) of the contraction: rows r < ns of B from xs (D^-1 Y),
+// rows r >= ns from anc (row rel[r - ns] of anc when rel is given, else row r)
+__device__ __forceinline__ void bwd_rows(float (&acc)[4][4], const float *At, int nf, int ns, int i0, int kb, int ke,
+                                         const float *xs, const float *anc, const int *rel, int cg) {
+    zero4x4(acc);
+    const int lda = pad4(ns), rd = min(i0 + 4, ns);
+    for (int r = max(kb, i0); r < min(ke, rd); ++r) {  // the diagonal block
+        const float4 b = *reinterpret_cast<const float4 *>(xs + (size_t)r * kFuseCols + cg);
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            const float a = r > i ? At[(size_t)r * lda + i] : (r == i ? 1.f : 0.f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += a * bv[v];
+        }
+    }
+    mac4x4<1>(acc, At, lda, i0, xs, nullptr, 0, cg, max(kb, rd), min(ke, ns));
+    mac4x4<-1>(acc, At, lda, i0, anc, rel, ns, cg, max(kb, ns), min(ke, nf));
+}
+
+__device__ __forceinline__ void load_meta(FuseMeta *meta, const FrontDev &fd, int P, const int *child_ids, int cb,
+                                          int nk, bool p_first) {
+    const int t = threadIdx.x;
+    if (t <= nk) {
+        const int node = p_first ? (t == 0 ? P : child_ids[cb + t - 1]) : (t < nk ? child_ids[cb + t] : P);
+        meta[t] = FuseMeta{fd.nf[node], fd.ns[node], fd.pstart[node], fd.foff[node], fd.relmap_off[node]};
+    }
+}
+
+__global__ void __launch_bounds__(256, 3) k_solve_fwd_fused(FrontDev fd, const int *__restrict__ parents,
                                                          const int *__restrict__ child_ptr,
                                                          const int *__restrict__ child_ids,
-                                                         const float *__restrict__ arena, int k, float *__restrict__ X,
-                                                         float *__restrict__ Y, int ldx, int max_rows, bool vec) {
+                                                         const float *__restrict__ arena,
+                                                         const float *__restrict__ dinv, int k, float *__restrict__ X,
+                                                         float *__restrict__ Y, int ldx, int max_rows, int max_front,
+                                                         bool vec) {
     extern __shared__ __align__(16) float fsm[];
-    float *Xs = fsm;                                 // max_rows x kFuseCols
-    float *Fs = fsm + (size_t)max_rows * kFuseCols;  // a staged front block
+    __shared__ FuseMeta meta[kFuseMaxKids + 1];  // children, then P
+    float *Xs = fsm;                                        // max_rows x kFuseCols
+    float *const Fb = fsm + (size_t)max_rows * kFuseCols;  // two buffers of max_front floats
     const int P = parents[blockIdx.x];
-    const int nfP = fd.nf[P], nsP = fd.ns[P], psP = fd.pstart[P];
+    const int cb = child_ptr[blockIdx.x], nk = child_ptr[blockIdx.x + 1] - cb;
+    load_meta(meta, fd, P, child_ids, cb, nk, false);
+    __syncthreads();
+    const int nfP = meta[nk].nf, nsP = meta[nk].ns, psP = meta[nk].ps;
     const int c0 = blockIdx.y * kFuseCols;
     const int tid = threadIdx.x, cg = (tid % kFuseCG) * 4, rg = tid / kFuseCG;
     const int avail = k - c0 - cg;
-    const int cb = child_ptr[blockIdx.x], ce = child_ptr[blockIdx.x + 1];
-    // P's pivot rows from X, its ancestor rows as zero deltas, then the
-    // children's pivot rows
+    // group 0: P's pivot rows, the children's pivot rows, the first block;
+    // P's ancestor rows start as zero deltas
     for (int r = rg; r < nfP; r += kFuseRG) {
-        float v[4];
-        load4(v, X, (int64_t)psP + r, r < nsP, c0 + cg, k, ldx, vec);
-        sts4(Xs + (size_t)r * kFuseCols + cg, v);
+        float *d = Xs + (size_t)r * kFuseCols + cg;
+        if (r < nsP) row4_async(d, X, (int64_t)psP + r, c0 + cg, k, ldx, vec);
+        else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    int off = nfP;
-    for (int ci = cb; ci < ce; ++ci) {
-        const int c = child_ids[ci], nsc = fd.ns[c], psc = fd.pstart[c];
-        for (int r = rg; r < nsc; r += kFuseRG) {
-            float v[4];
-            load4(v, X, (int64_t)psc + r, true, c0 + cg, k, ldx, vec);
-            sts4(Xs + (size_t)(off + r) * kFuseCols + cg, v);
-        }
-        off += nsc;
-    }
-    off = nfP;
-    for (int ci = cb; ci < ce; ++ci) {
-        const int c = child_ids[ci], nfc = fd.nf[c], nsc = fd.ns[c], psc = fd.pstart[c];
-        __syncthreads();  // the previous block is no longer read (first child: Xs loaded)
-        stage_fwd(arena + fd.foff[c], nfc, nsc, Fs);
+    for (int t = 0, off = nfP; t < nk; off += meta[t].ns, ++t)
+        for (int r = rg; r < meta[t].ns; r += kFuseRG)
+            row4_async(Xs + (size_t)(off + r) * kFuseCols + cg, X, (int64_t)meta[t].ps + r, c0 + cg, k, ldx, vec);
+    stage_front<true>(meta[0], arena, fd.relmap, dinv, Fb);
+    cp_async_commit();
+    if (nk >= 1) stage_front<true>(meta[1], arena, fd.relmap, dinv, Fb + max_front);
+    cp_async_commit();
+    for (int t = 0, off = nfP; t <= nk; ++t) {
+        const FuseMeta m = meta[t];
+        const float *As = Fb + (t & 1) * max_front;
+        const int *rel = reinterpret_cast<const int *>(As + fuse_block(m.nf, m.ns));
+        const float *ds = As + fuse_block(m.nf, m.ns) + pad4(m.nf - m.ns);
+        cp_async_wait<1>();
         __syncthreads();
-        const int *rel = fd.relmap + fd.relmap_off[c];
-        const float *xc = Xs + (size_t)off * kFuseCols;
-        for (int r0 = rg * 4; r0 < nfc; r0 += kFusePass) {
+        const bool isP = t == nk;
+        const float *xs = isP ? Xs : Xs + (size_t)off * kFuseCols;
+        for (int r0 = 4 * rg; r0 < m.nf; r0 += 4 * kFuseRG) {
             float acc[4][4];
-            zero4x4(acc);
-            mac4x4(acc, Fs, pad4(nfc), r0, xc, cg, 0, min(r0 + 4, nsc));
+            fwd_rows(acc, As, m.nf, m.ns, r0, xs, cg);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int r = r0 + u;
-                if (r >= nfc) break;
-                if (r < nsc) {
-                    if (avail > 0) store4(Y + (int64_t)(psc + r) * ldx + c0 + cg, acc[u], avail, vec);
-                } else {  // P's row relmap(r): a pivot value, or a delta subtracted at the end
-                    const int pr = rel[r - nsc];
+                if (r >= m.nf) break;
+                if (r < m.ns) {
+                    const float di = ds[r];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] *= di;
+                    if (avail > 0) store4(Y + (int64_t)(m.ps + r) * ldx + c0 + cg, acc[u], avail, vec);
+                } else if (isP) {  // a delta of P's ancestor row r
+                    add4(Xs + (size_t)r * kFuseCols + cg, acc[u], 1.f);
+                } else {           // P's row relmap(r): a pivot value, or a delta
+                    const int pr = rel[r - m.ns];
                     add4(Xs + (size_t)pr * kFuseCols + cg, acc[u], pr < nsP ? -1.f : 1.f);
                 }
             }
         }
-        off += nsc;
+        if (!isP) off += m.ns;
+        __syncthreads();  // buffer t & 1 is free
+        if (t + 2 <= nk) stage_front<true>(meta[t + 2], arena, fd.relmap, dinv, Fb + (t & 1) * max_front);
+        cp_async_commit();
     }
-    // P: its pivot rows are final
-    __syncthreads();
-    stage_fwd(arena + fd.foff[P], nfP, nsP, Fs);
-    __syncthreads();
-    for (int r0 = rg * 4; r0 < nfP; r0 += kFusePass) {
-        float acc[4][4];
-        zero4x4(acc);
-        mac4x4(acc, Fs, pad4(nfP), r0, Xs, cg, 0, min(r0 + 4, nsP));
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int r = r0 + u;
-            if (r >= nfP) break;
-            if (r < nsP) {
-                if (avail > 0) store4(Y + (int64_t)(psP + r) * ldx + c0 + cg, acc[u], avail, vec);
-            } else {
-                add4(Xs + (size_t)r * kFuseCols + cg, acc[u], 1.f);
-            }
-        }
-    }
-    __syncthreads();
     if (avail <= 0) return;
     const int *rowsP = fd.rows + fd.rows_off[P];
     for (int r = nsP + rg; r < nfP; r += kFuseRG) {
@@ -627,84 +705,81 @@ __global__ void __launch_bounds__(256) k_solve_fwd_fused(FrontDev fd, const int 
     }
 }
 
-__global__ void __launch_bounds__(256) k_solve_bwd_fused(FrontDev fd, const int *__restrict__ parents,
+__global__ void __launch_bounds__(256, 3) k_solve_bwd_fused(FrontDev fd, const int *__restrict__ parents,
                                                          const int *__restrict__ child_ptr,
                                                          const int *__restrict__ child_ids,
-                                                         const float *__restrict__ arena,
-                                                         const float *__restrict__ dinv, int k, float *__restrict__ X,
-                                                         const float *__restrict__ Y, int ldx, int max_rows, bool vec) {
+                                                         const float *__restrict__ arena, int k, float *__restrict__ X,
+                                                         const float *__restrict__ Y, int ldx, int max_rows,
+                                                         int max_front, bool vec) {
     extern __shared__ __align__(16) float fsm[];
+    __shared__ FuseMeta meta[kFuseMaxKids + 1];  // P, then the children
     float *Xs = fsm;
-    float *Fs = fsm + (size_t)max_rows * kFuseCols;
+    float *const Fb = fsm + (size_t)max_rows * kFuseCols;  // two buffers of max_front floats
     const int P = parents[blockIdx.x];
-    const int nfP = fd.nf[P], nsP = fd.ns[P], psP = fd.pstart[P];
+    const int cb = child_ptr[blockIdx.x], nk = child_ptr[blockIdx.x + 1] - cb;
+    load_meta(meta, fd, P, child_ids, cb, nk, true);
+    __syncthreads();
+    const int nfP = meta[0].nf, nsP = meta[0].ns, psP = meta[0].ps;
     const int c0 = blockIdx.y * kFuseCols;
     const int tid = threadIdx.x, cg = (tid % kFuseCG) * 4, rg = tid / kFuseCG;
     const int avail = k - c0 - cg;
-    const int cb = child_ptr[blockIdx.x], ce = child_ptr[blockIdx.x + 1];
     const int *rowsP = fd.rows + fd.rows_off[P];
-    // P's pivot rows: D^-1 Y; its ancestor rows: final X
-    for (int r = rg; r < nfP; r += kFuseRG) {
-        float v[4];
-        if (r < nsP) {
-            load4(v, Y, (int64_t)psP + r, true, c0 + cg, k, ldx, vec);
-            const float di = dinv[psP + r];
+    // group 0: D^-1 Y of P's and the children's pivot rows (the forward
+    // stored it), P's ancestor rows of X (final), P's block
+    int anc[kFuseMaxAnc / kFuseRG];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] *= di;
-        } else {
-            load4(v, X, (int64_t)rowsP[r], true, c0 + cg, k, ldx, vec);
-        }
-        sts4(Xs + (size_t)r * kFuseCols + cg, v);
+    for (int q = 0; q < kFuseMaxAnc / kFuseRG; ++q) {
+        const int r = nsP + rg + q * kFuseRG;
+        anc[q] = r < nfP ? rowsP[r] : 0;
     }
-    stage_bwd(arena + fd.foff[P], nfP, nsP, Fs);
-    __syncthreads();
-    // X_P = Linv^T D^-1 Y_P - W^T X_anc: rows i0.. of the output (two passes at most)
-    float acc[2][4][4];
+    for (int r = rg; r < nsP; r += kFuseRG)
+        row4_async(Xs + (size_t)r * kFuseCols + cg, Y, (int64_t)psP + r, c0 + cg, k, ldx, vec);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        zero4x4(acc[p]);
-        const int i0 = rg * 4 + p * kFusePass;
-        if (i0 < nsP) mac4x4(acc[p], Fs, pad4(nsP), i0, Xs, cg, i0, nfP);
+    for (int q = 0; q < kFuseMaxAnc / kFuseRG; ++q) {
+        const int r = nsP + rg + q * kFuseRG;
+        if (r < nfP) row4_async(Xs + (size_t)r * kFuseCols + cg, X, (int64_t)anc[q], c0 + cg, k, ldx, vec);
     }
-    __syncthreads();
+    for (int t = 1, off = nfP; t <= nk; off += meta[t].ns, ++t)
+        for (int r = rg; r < meta[t].ns; r += kFuseRG)
+            row4_async(Xs + (size_t)(off + r) * kFuseCols + cg, Y, (int64_t)meta[t].ps + r, c0 + cg, k, ldx, vec);
+    stage_front<false>(meta[0], arena, fd.relmap, nullptr, Fb);
+    cp_async_commit();
+    if (nk >= 1) stage_front<false>(meta[1], arena, fd.relmap, nullptr, Fb + max_front);
+    cp_async_commit();
+    for (int t = 0, off = nfP; t <= nk; ++t) {
+        const FuseMeta m = meta[t];
+        const float *At = Fb + (t & 1) * max_front;
+        const int *rel = reinterpret_cast<const int *>(At + fuse_block(m.nf, m.ns));
+        cp_async_wait<1>();
+        __syncthreads();  // also: P's pivot rows of Xs written
+        if (t == 0) {
+            // X_P = Linv^T D^-1 Y_P - W^T X_anc (one pass), then into Xs
+            float acc[4][4];
+            const int i0 = 4 * rg;
+            if (i0 < nsP) bwd_rows(acc, At, nfP, nsP, i0, i0, nfP, Xs, Xs, nullptr, cg);
+            __syncthreads();
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = rg * 4 + p * kFusePass + u;
-            if (i >= nsP) continue;
-            sts4(Xs + (size_t)i * kFuseCols + cg, acc[p][u]);
-            if (avail > 0) store4(X + (int64_t)(psP + i) * ldx + c0 + cg, acc[p][u], avail, vec);
-        }
-    // children: D^-1 Y of their pivot rows, then copies of P's rows they read
-    float *vc = Xs + (size_t)nfP * kFuseCols;
-    for (int ci = cb; ci < ce; ++ci) {
-        const int c = child_ids[ci], nfc = fd.nf[c], nsc = fd.ns[c], psc = fd.pstart[c];
-        const int *rel = fd.relmap + fd.relmap_off[c];
-        __syncthreads();  // P's rows written; the previous child's rows and block no longer read
-        for (int r = rg; r < nfc; r += kFuseRG) {
-            float v[4];
-            if (r < nsc) {
-                load4(v, Y, (int64_t)psc + r, true, c0 + cg, k, ldx, vec);
-                const float di = dinv[psc + r];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] *= di;
-            } else {
-                lds4(v, Xs + (size_t)rel[r - nsc] * kFuseCols + cg);
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u;
+                if (i >= nsP) continue;
+                sts4(Xs + (size_t)i * kFuseCols + cg, acc[u]);
+                if (avail > 0) store4(X + (int64_t)(psP + i) * ldx + c0 + cg, acc[u], avail, vec);
             }
-            sts4(vc + (size_t)r * kFuseCols + cg, v);
-        }
-        stage_bwd(arena + fd.foff[c], nfc, nsc, Fs);
-        __syncthreads();
-        for (int i0 = rg * 4; i0 < nsc; i0 += kFusePass) {
-            float a[4][4];
-            zero4x4(a);
-            mac4x4(a, Fs, pad4(nsc), i0, vc, cg, i0, nfc);
-            if (avail <= 0) continue;
+        } else {
+            const float *xs = Xs + (size_t)off * kFuseCols;
+            for (int i0 = 4 * rg; i0 < m.ns; i0 += 4 * kFuseRG) {
+                float a[4][4];
+                bwd_rows(a, At, m.nf, m.ns, i0, i0, m.nf, xs, Xs, rel, cg);
+                if (avail <= 0) continue;
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (i0 + u < nsc) store4(X + (int64_t)(psc + i0 + u) * ldx + c0 + cg, a[u], avail, vec);
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u < m.ns) store4(X + (int64_t)(m.ps + i0 + u) * ldx + c0 + cg, a[u], avail, vec);
+            }
+            off += m.ns;
         }
+        __syncthreads();  // buffer t & 1 is free
+        if (t + 2 <= nk) stage_front<false>(meta[t + 2], arena, fd.relmap, nullptr, Fb + (t & 1) * max_front);
+        cp_async_commit();
     }
 }
 
@@ -852,36 +927,37 @@ void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
 }
 
 size_t fused_smem(int max_rows, int max_front) {
-    return ((size_t)max_rows * kFuseCols + (size_t)max_front) * sizeof(float);
+    return ((size_t)max_rows * kFuseCols + 2 * (size_t)max_front) * sizeof(float);
 }
 
-int64_t fused_front_size(int nf, int ns) { return std::max<int64_t>((int64_t)ns * pad4(nf), (int64_t)nf * pad4(ns)); }
-
 int fused_max_pivots() { return kFuseMaxPiv; }
+int fused_max_ancestors() { return kFuseMaxAnc; }
+int fused_max_children() { return kFuseMaxKids; }
+int fused_front_size(int nf, int ns) { return fuse_block(nf, ns) + pad4(nf - ns) + pad4(ns); }
 
 void solve_fwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
-                     const int *child_ids, int max_rows, int max_front, const float *arena, int k, float *X, float *Y,
-                     int ldx) {
+                     const int *child_ids, int max_rows, int max_front, const float *arena, const float *dinv, int k,
+                     float *X, float *Y, int ldx) {
     if (n_parents <= 0 || k <= 0) return;
     const size_t sm = fused_smem(max_rows, max_front);
     HSIM_SMEM_LIMIT_ONCE(k_solve_fwd_fused, kFusedSmemMax);
-    HSIM_CHECK_ARG(sm <= kFusedSmemMax, "fused solve: shared memory");
+    HSIM_CHECK_ARG(sm <= kFusedSmemMax && max_front % 4 == 0, "fused solve: shared memory");
     const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
     k_solve_fwd_fused<<<dim3((unsigned)n_parents, cdiv(k, kFuseCols)), 256, sm, s>>>(
-        fd, parents, child_ptr, child_ids, arena, k, X, Y, ldx, max_rows, vec);
+        fd, parents, child_ptr, child_ids, arena, dinv, k, X, Y, ldx, max_rows, max_front, vec);
     HSIM_LAUNCHED();
 }
 
 void solve_bwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
-                     const int *child_ids, int max_rows, int max_front, const float *arena, const float *dinv, int k,
-                     float *X, const float *Y, int ldx) {
+                     const int *child_ids, int max_rows, int max_front, const float *arena, int k, float *X,
+                     const float *Y, int ldx) {
     if (n_parents <= 0 || k <= 0) return;
     const size_t sm = fused_smem(max_rows, max_front);
     HSIM_SMEM_LIMIT_ONCE(k_solve_bwd_fused, kFusedSmemMax);
-    HSIM_CHECK_ARG(sm <= kFusedSmemMax, "fused solve: shared memory");
+    HSIM_CHECK_ARG(sm <= kFusedSmemMax && max_front % 4 == 0, "fused solve: shared memory");
     const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
     k_solve_bwd_fused<<<dim3((unsigned)n_parents, cdiv(k, kFuseCols)), 256, sm, s>>>(
-        fd, parents, child_ptr, child_ids, arena, dinv, k, X, Y, ldx, max_rows, vec);
+        fd, parents, child_ptr, child_ids, arena, k, X, Y, ldx, max_rows, max_front, vec);
     HSIM_LAUNCHED();
 }
 

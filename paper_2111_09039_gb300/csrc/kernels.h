@@ -209,22 +209,25 @@ InversePlan inverse_plan(const std::vector<int> &nf, const std::vector<int> &ns,
 
 // The lowest two tree heights of the FP32 inverted-form solves in one launch
 // each way (k_finv.cu): per listed front of height 1 (parents), its children
-// child_ids[child_ptr[i] .. child_ptr[i + 1]) (leaves) and itself.  max_front
-// bounds the staged block of every front involved (fused_front_size floats
-// each), max_rows both nf + the children's pivots and nf + the largest
-// child's nf; parents have at most fused_max_pivots() pivots.  The results
-// of solve_fwd_inv / solve_bwd_inv on heights 0 and 1 of those fronts,
-// summed in another order.
+// child_ids[child_ptr[i] .. child_ptr[i + 1]) (leaves) and itself.  The
+// forward stores D^-1 Y on these fronts' rows, which only the fused backward
+// reads.  max_front bounds fused_front_size(nf, ns) of every front involved,
+// max_rows nf + the children's pivots of every parent; parents have at most
+// fused_max_pivots() pivots, fused_max_ancestors() rows beyond them and
+// fused_max_children() children.  The results of solve_fwd_inv /
+// solve_bwd_inv on heights 0 and 1 of those fronts, summed in another order.
 constexpr size_t kFusedSmemMax = 160 * 1024;
 size_t fused_smem(int max_rows, int max_front);
 int fused_max_pivots();
-int64_t fused_front_size(int nf, int ns);
+int fused_max_ancestors();
+int fused_max_children();
+int fused_front_size(int nf, int ns);
 void solve_fwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
-                     const int *child_ids, int max_rows, int max_front, const float *arena, int k, float *X, float *Y,
-                     int ldx);
-void solve_bwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
                      const int *child_ids, int max_rows, int max_front, const float *arena, const float *dinv, int k,
-                     float *X, const float *Y, int ldx);
+                     float *X, float *Y, int ldx);
+void solve_bwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
+                     const int *child_ids, int max_rows, int max_front, const float *arena, int k, float *X,
+                     const float *Y, int ldx);
 
 // FP32-accurate products on the tcgen05 tensor cores (k_tc32.cu: operands
 // split into two TF32 halves, three MMAs per K step, FP32 accumulators in
