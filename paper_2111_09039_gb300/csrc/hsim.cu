@@ -676,9 +676,12 @@ void solve_level_t(hsim_ctx *ctx, LevelData &L, const T *arena, const T *dpos, c
             float a = 0, b = 0;
             cudaEventElapsedTime(&a, ev[h], ev[h + 1]);
             cudaEventElapsedTime(&b, ev[2 * H - h], ev[2 * H - h + 1]);
+            // flops of one direction: ns^2 (unit-lower Linv) + 2 (nf - ns) ns per column
+            double gf = 0.0;
+            for (int t : fs.by_height[h]) gf += ((double)fs.ns[t] * fs.ns[t] + 2.0 * (fs.nf[t] - fs.ns[t]) * fs.ns[t]) * k;
             line += " h" + std::to_string(h) + "(" + std::to_string(L.hnodes_off[h + 1] - L.hnodes_off[h]) +
-                    " fronts, nf<=" + std::to_string(L.h_maxnf[h]) + ") " + std::to_string(a).substr(0, 5) + "/" +
-                    std::to_string(b).substr(0, 5);
+                    " fronts, nf<=" + std::to_string(L.h_maxnf[h]) + ", " + std::to_string(gf * 1e-9).substr(0, 5) +
+                    " GF) " + std::to_string(a).substr(0, 5) + "/" + std::to_string(b).substr(0, 5);
         }
         std::fprintf(stderr, "%s\n", line.c_str());
         for (auto e : ev) cudaEventDestroy(e);

@@ -544,27 +544,43 @@ __device__ __forceinline__ void stage_front(const FuseMeta &m, const float *__re
     }
 }
 
-// acc[u][v] += SIGN * sum_{j in [jb, je)} A[j * lda + r0 + u] * B(j)[c + v], B(j) the
-// shared-memory row j of B, or row idx[j - ib] when idx is given
-template <int SIGN>
-__device__ __forceinline__ void mac4x4(float (&acc)[4][4], const float *A, int lda, int r0, const float *B,
-                                       const int *idx, int ib, int c, int jb, int je) {
-#pragma unroll 4
-    for (int j = jb; j < je; ++j) {
-        const float4 a = *reinterpret_cast<const float4 *>(A + (size_t)j * lda + r0);
-        const int br = idx ? idx[j - ib] : j;
-        const float4 b = *reinterpret_cast<const float4 *>(B + (size_t)br * kFuseCols + c);
-        const float av[4] = {SIGN * a.x, SIGN * a.y, SIGN * a.z, SIGN * a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+// R consecutive floats of shared memory (aligned to R floats)
+template <int R>
+__device__ __forceinline__ void lds_rows(float (&a)[R], const float *p) {
+    if constexpr (R == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w;
+    } else if constexpr (R == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        a[0] = v.x, a[1] = v.y;
+    } else {
+        a[0] = *p;
     }
 }
 
-__device__ __forceinline__ void zero4x4(float (&acc)[4][4]) {
+// acc[u][v] += SIGN * sum_{j in [jb, je)} A[j * lda + r0 + u] * B(j)[c + v], u < R, B(j)
+// the shared-memory row j of B, or row idx[j - ib] when idx is given
+template <int SIGN, int R>
+__device__ __forceinline__ void mac_rows(float (&acc)[R][4], const float *A, int lda, int r0, const float *B,
+                                         const int *idx, int ib, int c, int jb, int je) {
+#pragma unroll 4
+    for (int j = jb; j < je; ++j) {
+        float av[R];
+        lds_rows<R>(av, A + (size_t)j * lda + r0);
+        const int br = idx ? idx[j - ib] : j;
+        const float4 b = *reinterpret_cast<const float4 *>(B + (size_t)br * kFuseCols + c);
+        const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < R; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += (SIGN * av[u]) * bv[v];
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void zero_rows(float (&acc)[R][4]) {
+#pragma unroll
+    for (int u = 0; u < R; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
 }
@@ -578,18 +594,28 @@ __device__ __forceinline__ void add4(float *p, const float (&a)[4], float sg) {
     *reinterpret_cast<float4 *>(p) = d;
 }
 
-// forward product of one staged front on rows r0..r0+3 (column-major As,
+// rows per thread for `rows` output rows over the 16 row groups: the fewest
+// rows per thread in the longest group, four rows on ties (fewer shared loads
+// per product)
+__device__ __forceinline__ int pick_rows(int rows) {
+    auto span = [&](int R) { return R * ((rows + R * kFuseRG - 1) / (R * kFuseRG)); };
+    const int s4 = span(4), s2 = span(2), s1 = span(1);
+    return s4 <= s2 && s4 <= s1 ? 4 : (s2 <= s1 ? 2 : 1);
+}
+
+// forward product of one staged front on rows r0..r0+R-1 (column-major As,
 // unit lower triangle on the pivot rows): xs holds its pivot rows
-__device__ __forceinline__ void fwd_rows(float (&acc)[4][4], const float *As, int nf, int ns, int r0, const float *xs,
+template <int R>
+__device__ __forceinline__ void fwd_rows(float (&acc)[R][4], const float *As, int nf, int ns, int r0, const float *xs,
                                          int cg) {
-    zero4x4(acc);
-    const int lda = pad4(nf), jd = min(r0, ns);
-    mac4x4<1>(acc, As, lda, r0, xs, nullptr, 0, cg, 0, jd);
-    for (int j = r0; j < min(r0 + 4, ns); ++j) {  // the diagonal block
+    zero_rows<R>(acc);
+    const int lda = pad4(nf);
+    mac_rows<1, R>(acc, As, lda, r0, xs, nullptr, 0, cg, 0, min(r0, ns));
+    for (int j = r0; j < min(r0 + R, ns); ++j) {  // the diagonal block
         const float4 b = *reinterpret_cast<const float4 *>(xs + (size_t)j * kFuseCols + cg);
         const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < R; ++u) {
             const int r = r0 + u;
             const float a = (r >= ns || r > j) ? As[(size_t)j * lda + r] : (r == j ? 1.f : 0.f);
 #pragma unroll
@@ -598,26 +624,88 @@ __device__ __forceinline__ void fwd_rows(float (&acc)[4][4], const float *As, in
     }
 }
 
-// backward product of one staged front on outputs i0..i0+3 (row-major At),
-// rows r in [kb, ke) of the contraction: rows r < ns of B from xs (D^-1 Y),
-// rows r >= ns from anc (row rel[r - ns] of anc when rel is given, else row r)
-__device__ __forceinline__ void bwd_rows(float (&acc)[4][4], const float *At, int nf, int ns, int i0, int kb, int ke,
-                                         const float *xs, const float *anc, const int *rel, int cg) {
-    zero4x4(acc);
-    const int lda = pad4(ns), rd = min(i0 + 4, ns);
-    for (int r = max(kb, i0); r < min(ke, rd); ++r) {  // the diagonal block
+// backward product of one staged front on outputs i0..i0+R-1 (row-major At):
+// rows r < ns of B from xs (D^-1 Y), rows r >= ns from anc (row rel[r - ns]
+// of anc when rel is given, else row r)
+template <int R>
+__device__ __forceinline__ void bwd_rows(float (&acc)[R][4], const float *At, int nf, int ns, int i0, const float *xs,
+                                         const float *anc, const int *rel, int cg) {
+    zero_rows<R>(acc);
+    const int lda = pad4(ns), rd = min(i0 + R, ns);
+    for (int r = i0; r < rd; ++r) {  // the diagonal block
         const float4 b = *reinterpret_cast<const float4 *>(xs + (size_t)r * kFuseCols + cg);
         const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < R; ++u) {
             const int i = i0 + u;
             const float a = r > i ? At[(size_t)r * lda + i] : (r == i ? 1.f : 0.f);
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] += a * bv[v];
         }
     }
-    mac4x4<1>(acc, At, lda, i0, xs, nullptr, 0, cg, max(kb, rd), min(ke, ns));
-    mac4x4<-1>(acc, At, lda, i0, anc, rel, ns, cg, max(kb, ns), min(ke, nf));
+    mac_rows<1, R>(acc, At, lda, i0, xs, nullptr, 0, cg, rd, ns);
+    mac_rows<-1, R>(acc, At, lda, i0, anc, rel, ns, cg, ns, nf);
+}
+
+// the forward product of front m (a child of P, or P itself) and its outputs:
+// pivot rows to Y (scaled by D^-1), the other rows into P's rows of Xs
+template <int R>
+__device__ __forceinline__ void fwd_front(const FuseMeta &m, const float *As, bool isP, int nsP, const float *xs,
+                                          float *Xs, float *Y, int ldx, int c0, int cg, int rg, int avail, bool vec) {
+    const int *rel = reinterpret_cast<const int *>(As + fuse_block(m.nf, m.ns));
+    const float *ds = As + fuse_block(m.nf, m.ns) + pad4(m.nf - m.ns);
+    for (int r0 = R * rg; r0 < m.nf; r0 += R * kFuseRG) {
+        float acc[R][4];
+        fwd_rows<R>(acc, As, m.nf, m.ns, r0, xs, cg);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int r = r0 + u;
+            if (r >= m.nf) break;
+            if (r < m.ns) {
+                const float di = ds[r];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] *= di;
+                if (avail > 0) store4(Y + (int64_t)(m.ps + r) * ldx + c0 + cg, acc[u], avail, vec);
+            } else if (isP) {  // a delta of P's ancestor row r
+                add4(Xs + (size_t)r * kFuseCols + cg, acc[u], 1.f);
+            } else {           // P's row relmap(r): a pivot value, or a delta
+                const int pr = rel[r - m.ns];
+                add4(Xs + (size_t)pr * kFuseCols + cg, acc[u], pr < nsP ? -1.f : 1.f);
+            }
+        }
+    }
+}
+
+// P's backward product (one pass: ns_P <= 16 R), then its pivot rows into Xs and X
+template <int R>
+__device__ __forceinline__ void bwd_parent(const FuseMeta &m, const float *At, float *Xs, float *X, int ldx, int c0,
+                                           int cg, int rg, int avail, bool vec) {
+    float acc[R][4];
+    const int i0 = R * rg;
+    if (i0 < m.ns) bwd_rows<R>(acc, At, m.nf, m.ns, i0, Xs, Xs, nullptr, cg);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int i = i0 + u;
+        if (i >= m.ns) continue;
+        sts4(Xs + (size_t)i * kFuseCols + cg, acc[u]);
+        if (avail > 0) store4(X + (int64_t)(m.ps + i) * ldx + c0 + cg, acc[u], avail, vec);
+    }
+}
+
+// a child's backward product: its pivot rows of X from xs (D^-1 Y) and P's rows
+template <int R>
+__device__ __forceinline__ void bwd_child(const FuseMeta &m, const float *At, const float *xs, const float *Xs,
+                                          float *X, int ldx, int c0, int cg, int rg, int avail, bool vec) {
+    const int *rel = reinterpret_cast<const int *>(At + fuse_block(m.nf, m.ns));
+    for (int i0 = R * rg; i0 < m.ns; i0 += R * kFuseRG) {
+        float acc[R][4];
+        bwd_rows<R>(acc, At, m.nf, m.ns, i0, xs, Xs, rel, cg);
+        if (avail <= 0) continue;
+#pragma unroll
+        for (int u = 0; u < R; ++u)
+            if (i0 + u < m.ns) store4(X + (int64_t)(m.ps + i0 + u) * ldx + c0 + cg, acc[u], avail, vec);
+    }
 }
 
 __device__ __forceinline__ void load_meta(FuseMeta *meta, const FrontDev &fd, int P, const int *child_ids, int cb,
@@ -665,32 +753,12 @@ __global__ void __launch_bounds__(256, 3) k_solve_fwd_fused(FrontDev fd, const i
     for (int t = 0, off = nfP; t <= nk; ++t) {
         const FuseMeta m = meta[t];
         const float *As = Fb + (t & 1) * max_front;
-        const int *rel = reinterpret_cast<const int *>(As + fuse_block(m.nf, m.ns));
-        const float *ds = As + fuse_block(m.nf, m.ns) + pad4(m.nf - m.ns);
         cp_async_wait<1>();
         __syncthreads();
         const bool isP = t == nk;
         const float *xs = isP ? Xs : Xs + (size_t)off * kFuseCols;
-        for (int r0 = 4 * rg; r0 < m.nf; r0 += 4 * kFuseRG) {
-            float acc[4][4];
-            fwd_rows(acc, As, m.nf, m.ns, r0, xs, cg);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = r0 + u;
-                if (r >= m.nf) break;
-                if (r < m.ns) {
-                    const float di = ds[r];
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] *= di;
-                    if (avail > 0) store4(Y + (int64_t)(m.ps + r) * ldx + c0 + cg, acc[u], avail, vec);
-                } else if (isP) {  // a delta of P's ancestor row r
-                    add4(Xs + (size_t)r * kFuseCols + cg, acc[u], 1.f);
-                } else {           // P's row relmap(r): a pivot value, or a delta
-                    const int pr = rel[r - m.ns];
-                    add4(Xs + (size_t)pr * kFuseCols + cg, acc[u], pr < nsP ? -1.f : 1.f);
-                }
-            }
-        }
+        // four rows per thread (fewer rows per thread measured slower here)
+        fwd_front<4>(m, As, isP, nsP, xs, Xs, Y, ldx, c0, cg, rg, avail, vec);
         if (!isP) off += m.ns;
         __syncthreads();  // buffer t & 1 is free
         if (t + 2 <= nk) stage_front<true>(meta[t + 2], arena, fd.relmap, dinv, Fb + (t & 1) * max_front);
@@ -749,32 +817,19 @@ __global__ void __launch_bounds__(256, 3) k_solve_bwd_fused(FrontDev fd, const i
     for (int t = 0, off = nfP; t <= nk; ++t) {
         const FuseMeta m = meta[t];
         const float *At = Fb + (t & 1) * max_front;
-        const int *rel = reinterpret_cast<const int *>(At + fuse_block(m.nf, m.ns));
         cp_async_wait<1>();
         __syncthreads();  // also: P's pivot rows of Xs written
         if (t == 0) {
-            // X_P = Linv^T D^-1 Y_P - W^T X_anc (one pass), then into Xs
-            float acc[4][4];
-            const int i0 = 4 * rg;
-            if (i0 < nsP) bwd_rows(acc, At, nfP, nsP, i0, i0, nfP, Xs, Xs, nullptr, cg);
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = i0 + u;
-                if (i >= nsP) continue;
-                sts4(Xs + (size_t)i * kFuseCols + cg, acc[u]);
-                if (avail > 0) store4(X + (int64_t)(psP + i) * ldx + c0 + cg, acc[u], avail, vec);
-            }
+            // X_P = Linv^T D^-1 Y_P - W^T X_anc in one pass (ns_P <= 64), then into Xs
+            if (nsP <= kFuseRG) bwd_parent<1>(m, At, Xs, X, ldx, c0, cg, rg, avail, vec);
+            else if (nsP <= 2 * kFuseRG) bwd_parent<2>(m, At, Xs, X, ldx, c0, cg, rg, avail, vec);
+            else bwd_parent<4>(m, At, Xs, X, ldx, c0, cg, rg, avail, vec);
         } else {
             const float *xs = Xs + (size_t)off * kFuseCols;
-            for (int i0 = 4 * rg; i0 < m.ns; i0 += 4 * kFuseRG) {
-                float a[4][4];
-                bwd_rows(a, At, m.nf, m.ns, i0, i0, m.nf, xs, Xs, rel, cg);
-                if (avail <= 0) continue;
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (i0 + u < m.ns) store4(X + (int64_t)(m.ps + i0 + u) * ldx + c0 + cg, a[u], avail, vec);
-            }
+            const int R = pick_rows(m.ns);
+            if (R == 4) bwd_child<4>(m, At, xs, Xs, X, ldx, c0, cg, rg, avail, vec);
+            else if (R == 2) bwd_child<2>(m, At, xs, Xs, X, ldx, c0, cg, rg, avail, vec);
+            else bwd_child<1>(m, At, xs, Xs, X, ldx, c0, cg, rg, avail, vec);
             off += m.ns;
         }
         __syncthreads();  // buffer t & 1 is free
