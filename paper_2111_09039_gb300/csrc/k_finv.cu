@@ -234,6 +234,12 @@ __host__ __device__ constexpr int inv_cols() { return sizeof(T) == 4 ? 128 : 64;
 // step's operands are loaded into registers while the current one is
 // multiplied, then stored to the other stage (one barrier per step).
 constexpr int kInvBK = 32;
+// Backward heights with fewer than kBwdSplitPerSM CTAs per SM split their K
+// range into up to kBwdMaxSplit chunks (10^6-vertex level, 750 columns: 2, 4
+// and 8 CTAs per SM measured 11.7, 11.4 and 11.1 ms of backward per solve
+// against 12.0 ms unsplit; the whole mixed solve 1.707, 1.702 and 1.699 s
+// against 1.724 s)
+constexpr int kBwdSplitPerSM = 8, kBwdMaxSplit = 8;
 
 template <typename T, int BM>
 constexpr size_t fwd_inv_smem(int stages) { return (size_t)stages * kInvBK * (BM + inv_cols<T>()) * sizeof(T); }
@@ -353,7 +359,8 @@ template <typename T, int BM, int STAGES>
 __global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(FrontDev fd, const int *__restrict__ nodes,
                                                                           int rt_per,
                                                        const T *__restrict__ arena, const T *__restrict__ dinv, int k,
-                                                       T *__restrict__ X, const T *__restrict__ Y, int ldx, bool vec) {
+                                                       T *__restrict__ X, const T *__restrict__ Y, int ldx, bool vec,
+                                                       int ksplit) {
     constexpr int BK = kInvBK, BN = inv_cols<T>(), LDA = BM + 1;
     constexpr int CG = BN / 4, RGS = 256 / CG, RPT = BM / RGS;
     constexpr int AE = BK * BM / 256, BE = BK * CG / 256;
@@ -428,10 +435,14 @@ __global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(Fron
                 for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
         }
     };
-    // Linv^T(i, r) = Linv(r, i) = 0 for r < i: start at the tile's first row
-    const int kbeg = (i0 / BK) * BK;
+    // Linv^T(i, r) = Linv(r, i) = 0 for r < i: start at the tile's first row.
+    // Split K: chunk blockIdx.z of ksplit chunks of whole BK steps (the
+    // partial products are added into X, zeroed beforehand)
+    const int kfirst = (i0 / BK) * BK, steps = (nf - kfirst + BK - 1) / BK, cs = (steps + ksplit - 1) / ksplit;
+    const int kbeg = kfirst + (int)blockIdx.z * cs * BK, kend = min(nf, kbeg + cs * BK);
+    if (kbeg >= nf) return;
     if constexpr (STAGES == 1) {
-        for (int k0 = kbeg; k0 < nf; k0 += BK) {
+        for (int k0 = kbeg; k0 < kend; k0 += BK) {
             load(k0);
             store(0);
             __syncthreads();
@@ -442,8 +453,8 @@ __global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(Fron
         load(kbeg);
         store(0);
         __syncthreads();
-        for (int k0 = kbeg, st = 0; k0 < nf; k0 += BK, st ^= 1) {
-            const bool more = k0 + BK < nf;
+        for (int k0 = kbeg, st = 0; k0 < kend; k0 += BK, st ^= 1) {
+            const bool more = k0 + BK < kend;
             if (more) load(k0 + BK);
             compute(st);
             if (more) store(st ^ 1);
@@ -455,8 +466,28 @@ __global__ void __launch_bounds__(256, STAGES == 1 ? 4 : 2) k_solve_bwd_inv(Fron
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
         const int i = i0 + rg * RPT + u;
-        if (i < ns) store4(X + (int64_t)(ps + i) * ldx + c0 + cg, acc[u], avail, vec);
+        if (i >= ns) continue;
+        if constexpr (sizeof(T) == 4) {
+            if (ksplit > 1) {
+                T neg[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) neg[v] = -acc[u][v];
+                sub4_atomic(X + (int64_t)(ps + i) * ldx + c0 + cg, neg, avail, vec);
+                continue;
+            }
+        }
+        store4(X + (int64_t)(ps + i) * ldx + c0 + cg, acc[u], avail, vec);
     }
+}
+
+// X rows [pstart, pstart + ns) of the listed fronts set to zero (columns < k):
+// CTA (front, y) takes rows y, y + gridDim.y, ...
+template <typename T>
+__global__ void k_zero_pivot_rows(FrontDev fd, const int *__restrict__ nodes, int k, T *__restrict__ X, int ldx) {
+    const int t = nodes[blockIdx.x];
+    const int ns = fd.ns[t], ps = fd.pstart[t];
+    for (int r = blockIdx.y; r < ns; r += gridDim.y)
+        for (int c = threadIdx.x; c < k; c += blockDim.x) X[(int64_t)(ps + r) * ldx + c] = T(0);
 }
 
 // ---- the lowest two tree heights fused ------------------------------------------
@@ -949,12 +980,26 @@ void launch_fwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_
 
 template <typename T, int BM, int STAGES>
 void launch_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_nodes, int rt, const T *arena,
-                    const T *dinv, int k, T *X, const T *Y, int ldx, bool vec) {
+                    const T *dinv, int k, T *X, const T *Y, int ldx, bool vec, int ksplit) {
     constexpr size_t sm = bwd_inv_smem<T, BM>(STAGES);
     HSIM_SMEM_LIMIT_ONCE((k_solve_bwd_inv<T, BM, STAGES>), sm);
-    k_solve_bwd_inv<T, BM, STAGES><<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>())), 256, sm, s>>>(
-        fd, nodes, rt, arena, dinv, k, X, Y, ldx, vec);
+    if (ksplit > 1) {
+        k_zero_pivot_rows<T><<<dim3((unsigned)n_nodes, 128), 256, 0, s>>>(fd, nodes, k, X, ldx);
+        HSIM_LAUNCHED();
+    }
+    k_solve_bwd_inv<T, BM, STAGES>
+        <<<dim3((unsigned)((int64_t)n_nodes * rt), cdiv(k, inv_cols<T>()), (unsigned)ksplit), 256, sm, s>>>(
+            fd, nodes, rt, arena, dinv, k, X, Y, ldx, vec, ksplit);
     HSIM_LAUNCHED();
+}
+
+// SMs of the current device (queried per call: a process may drive GPUs of
+// different sizes)
+int device_sms() {
+    int dev = 0, c = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    return c > 0 ? c : 1;
 }
 
 // One K step per tile when every front of the height has ns <= 32 (the
@@ -977,8 +1022,18 @@ void solve_bwd_inv(cudaStream_t s, const FrontDev &fd, const int *nodes, int n_n
                    const T *dinv, int k, T *X, const T *Y, int ldx) {
     if (n_nodes <= 0 || k <= 0 || max_ns <= 0) return;
     const bool vec = aligned16(X, ldx) && aligned16(Y, ldx);
-    if (max_ns <= 32) launch_bwd_inv<T, 32, 1>(s, fd, nodes, n_nodes, 1, arena, dinv, k, X, Y, ldx, vec);
-    else launch_bwd_inv<T, 64, 2>(s, fd, nodes, n_nodes, (max_ns + 63) / 64, arena, dinv, k, X, Y, ldx, vec);
+    if (max_ns <= 32) {
+        launch_bwd_inv<T, 32, 1>(s, fd, nodes, n_nodes, 1, arena, dinv, k, X, Y, ldx, vec, 1);
+        return;
+    }
+    // heights of few large fronts fill few CTAs per SM: their long K ranges are
+    // split (FP32: vector atomic additions into zeroed rows)
+    const int rt = (max_ns + 63) / 64;
+    const int64_t base = (int64_t)n_nodes * rt * cdiv(k, inv_cols<T>());
+    int ksplit = 1;
+    if (sizeof(T) == 4 && base < kBwdSplitPerSM * device_sms())
+        ksplit = (int)std::min<int64_t>(kBwdMaxSplit, (kBwdSplitPerSM * device_sms() + base - 1) / base);
+    launch_bwd_inv<T, 64, 2>(s, fd, nodes, n_nodes, rt, arena, dinv, k, X, Y, ldx, vec, ksplit);
 }
 
 size_t fused_smem(int max_rows, int max_front) {
