@@ -745,8 +745,8 @@ def roofline(info, infos, hier, p, peaks, peak_src, precision, tol):
 
 # DRAM bytes (read + write) per operand row of one k_ozaki_tc launch, from
 # one ncu capture of each product shape at 200,000 rows, q = 750
-# (profiles/ozaki_tc_traffic_n200k_q750.md): update (6 digits) 1.853 GB read +
-# 1.171 GB written; Gram with the solve's 5 digits 3.669 GB read + 3 MB written
+# (profiles/ozaki_tc_traffic_n200k_q750.md): update (6 digits) 1.852 GB read +
+# 1.170 GB written; Gram with the solve's 5 digits 3.090 GB read + 3 MB written
 # for the full square product of the capture (the solve's Grams compute the
 # lower triangle: an upper bound).
 TC_TRAFFIC_PER_ROW = {"gram": (3090402816 + 3154688) / 200000, "update": (1852248576 + 1170459392) / 200000}
@@ -756,8 +756,9 @@ def tc_traffic(sizes, iters, q, gram_digits=6):
     """Per-launch DRAM traffic of k_ozaki_tc over one solve, scaled from the
     200,000-row captures by the rows each launch processes (traffic grows in
     proportion to the rows), against the algorithmic bytes (the BF16 digit
-    slices read once: 6 slices x 2 bytes per operand value; the update's FP64
-    output, 8 bytes per value)."""
+    slices read once: d slices x 2 bytes per operand value, d = gram_digits
+    for the Grams and 6 for the update; the update's FP64 output, 8 bytes per
+    value)."""
     if TC_TRAFFIC_PER_ROW["gram"] is None or TC_TRAFFIC_PER_ROW["update"] is None:
         return None
     qp = (q + 31) // 32 * 32
@@ -778,7 +779,7 @@ def tc_traffic(sizes, iters, q, gram_digits=6):
 
 def cpu_baseline(workload, info):
     """FP64 oracle on a bounded sample, in a fresh process (no CUDA state; its
-    solve workers are forked from it)."""
+    solve workers are spawned from it)."""
     cmd = [sys.executable, "-c",
            "import json,sys; sys.path.insert(0, %r); from oracle import baseline; "
            "print(json.dumps(baseline.sample(%r, iters=%s)))" % (ROOT, workload, json.dumps(info["iters"]))]
