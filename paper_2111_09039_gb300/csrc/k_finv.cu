@@ -507,11 +507,13 @@ __global__ void k_zero_pivot_rows(FrontDev fd, const int *__restrict__ nodes, in
 //
 // Every global operand arrives by cp.async: the tile's rows at the start,
 // each front's block (with its relmap and D^-1) while the previous front is
-// multiplied (two buffers).  Each thread owns a 4 x 4 block of the output
-// (four rows, four columns); a front block is staged with its leading
-// dimension padded to a multiple of four, so one 16-byte load gives the four
-// rows' coefficients of a step, and the unit-triangular diagonal 4 x 4
-// blocks are masked in registers.
+// multiplied (two buffers).  Each thread owns R rows x 4 columns of the
+// output: R = 4 in the forward; in the backward, whose outputs are only the
+// pivot rows (a few per front here), R = 1, 2 or 4, whichever leaves the
+// longest row group shortest.  A front block is staged with its leading
+// dimension padded to a multiple of four, so one shared load of R values
+// gives the R rows' coefficients of a step, and the unit-triangular
+// diagonal R x R blocks are masked in registers.
 constexpr int kFuseCols = 64;
 constexpr int kFuseCG = kFuseCols / 4, kFuseRG = 256 / kFuseCG;  // 16 column groups, 16 row groups
 constexpr int kFuseMaxPiv = 4 * kFuseRG;                          // pivots of P at most (one pass)
