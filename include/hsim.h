@@ -432,10 +432,19 @@ hsim_status hsim_check_symbolic(int n, const int32_t *ptr, const int32_t *col, c
  * in place by the tasks of the GPU's inversion plan (32 x 32 diagonal blocks,
  * block doubling, W = L_bs Linv), then one product per front and direction
  * in the GPU's order of tree heights.  Arguments and results as
- * hsim_check_symbolic.  Needs no GPU. */
+ * hsim_check_symbolic, and:
+ *   fused_h01: nonzero replays tree heights 0 and 1 in the order of the GPU's
+ *     fused launches (each planned front of height 1 with its leaves, its
+ *     rows held apart, D^-1 Y stored by the forward); 0 per height.
+ *   fused_counts (host, may be NULL): 3 ints, the fronts of height 1 that
+ *     the plan fuses, the leaves and the fronts of height 1 it leaves to the
+ *     per-height products (all 0 when fused_h01 is 0 or the tree has one
+ *     height).
+ * Needs no GPU. */
 hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, const double *val,
                                 int leaf_size, int nrhs, const double *B, double *X,
-                                int *negative_pivots, int64_t *nnz_L);
+                                int *negative_pivots, int64_t *nnz_L, int fused_h01,
+                                int *fused_counts);
 /* Host replay of the mesh part of hsim_build_hierarchy: the level sizes
  * (eqs. nT-1 and growthRate), the farthest-point order (Alg. 2) and the
  * prolongations U^tau (eq. basis, rows normalised to one), computed by the

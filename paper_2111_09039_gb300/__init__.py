@@ -444,9 +444,12 @@ def shifted_solve(ctx: Context, hier: Hierarchy, tau: int, S_val, M_val, mu: flo
     return X, neg.value
 
 
-def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32, inverted: bool = False):
+def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32, inverted: bool = False, fused: bool = False):
     """Host replay of the factorisation over the symbolic analysis (no GPU);
-    inverted=True: the inverted-factor solve of the mixed path (hsim_check_inverted)."""
+    inverted=True: the inverted-factor solve of the mixed path
+    (hsim_check_inverted), with fused=True its two lowest tree heights in the
+    order of the fused launches; then the plan's counts (fused fronts of
+    height 1, leaves and fronts of height 1 left per height) come fourth."""
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(col, dtype=np.int32)
     val = np.ascontiguousarray(val, dtype=np.float64)
@@ -456,9 +459,17 @@ def check_symbolic(row_ptr, col, val, B, leaf_size: int = 32, inverted: bool = F
     X = np.empty_like(B)
     neg = ctypes.c_int()
     nnzL = ctypes.c_int64()
-    fn = lib().hsim_check_inverted if inverted else lib().hsim_check_symbolic
-    check(fn(len(row_ptr) - 1, ptr(row_ptr), ptr(col), ptr(val), leaf_size, B.shape[1], ptr(B), ptr(X),
-             ctypes.byref(neg), ctypes.byref(nnzL)))
+    args = (len(row_ptr) - 1, ptr(row_ptr), ptr(col), ptr(val), leaf_size, B.shape[1], ptr(B), ptr(X),
+            ctypes.byref(neg), ctypes.byref(nnzL))
+    if not inverted:
+        if fused:
+            raise ValueError("fused applies to the inverted form")
+        check(lib().hsim_check_symbolic(*args))
+        return X, neg.value, nnzL.value
+    counts = (ctypes.c_int * 3)()
+    check(lib().hsim_check_inverted(*args, 1 if fused else 0, counts))
+    if fused:
+        return X, neg.value, nnzL.value, tuple(counts)
     return X, neg.value, nnzL.value
 
 

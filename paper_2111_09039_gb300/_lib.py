@@ -100,7 +100,7 @@ _SIGS = {
     "hsim_shifted_solve": (I, [P, P, I, P, P, D, I, P, I, P]),
     "hsim_shifted_solve_f32": (I, [P, P, I, P, P, D, I, P, I, P]),
     "hsim_check_symbolic": (I, [I, P, P, P, I, I, P, P, P, P]),
-    "hsim_check_inverted": (I, [I, P, P, P, I, I, P, P, P, P]),
+    "hsim_check_inverted": (I, [I, P, P, P, I, I, P, P, P, P, I, P]),
     "hsim_check_hierarchy": (I, [I, I, P, P, P, I, P, P, P, P, P, P, P, P, P, P, P, P, P]),
     "hsim_hier_dofs": (I, [P, P]),
     "hsim_random_column": (None, [I, ctypes.c_uint64, P]),

@@ -6,7 +6,8 @@
 // solver itself never calls it.  hsim_check_inverted replays the inverted
 // form of the FP32 solves (k_finv.cu) the same way: the inversion tasks of
 // k::inverse_plan executed with the semantics of k_gemm_tasks, then one
-// product per front and direction.  hsim_check_hierarchy returns the mesh
+// product per front and direction, optionally with heights 0 and 1 in the
+// order of the fused kernels (k::fuse_plan).  hsim_check_hierarchy returns the mesh
 // part of a hierarchy (level sizes, farthest-point order, prolongations) from
 // the host code that hsim_build_hierarchy runs before its device uploads.
 #include <algorithm>
@@ -216,7 +217,7 @@ void run_task(const k::GemmTask &tk, const double *Ab, const double *Bb, double 
 
 extern "C" hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int32_t *col, const double *val,
                                            int leaf_size, int nrhs, const double *B, double *X, int *neg_pivots,
-                                           int64_t *nnz_L) {
+                                           int64_t *nnz_L, int fused_h01, int *fused_counts) {
     try {
         HSIM_CHECK_ARG(n > 0 && ptr && col && val && B && X && nrhs >= 1, "bad arguments");
         FrontSymbolic fs;
@@ -252,53 +253,172 @@ extern "C" hsim_status hsim_check_inverted(int n, const int32_t *ptr, const int3
             for (int j = 0; j < tk.N; ++j)
                 for (int i = 0; i < tk.M; ++i)
                     arena[tk.c + (int64_t)j * tk.ldc + i] = scr[tk.a + (int64_t)j * tk.lda + i];
-        // forward per height: Y_s = Linv X_s, X_b -= W X_s (k_solve_fwd_inv)
         std::vector<double> Xi((size_t)n * nrhs), Y((size_t)n * nrhs, 0.0);
         for (int pos = 0; pos < n; ++pos)
             std::memcpy(&Xi[(size_t)pos * nrhs], &B[(size_t)fs.perm[pos] * nrhs], nrhs * sizeof(double));
-        auto row = [&](int t, int r) { return fs.rows[fs.rows_off[t] + r]; };
+        auto row = [&](int t, int r) {
+            const int g = fs.rows[fs.rows_off[t] + r];
+            if (g < 0 || g >= n) fail(HSIM_E_INTERNAL, "front row outside the matrix");
+            return g;
+        };
+        auto front = [&](int t) { return arena.data() + fs.foff[t]; };
+        auto dinv = [&](int t, int r) { return 1.0 / front(t)[(int64_t)r * fs.nf[t] + r]; };
+        // forward coefficient A(r, j): unit lower Linv on the pivot rows, W below
+        auto fwd_a = [&](int t, int r, int j) {
+            const int nf = fs.nf[t], ns = fs.ns[t];
+            return (r >= ns || r > j) ? front(t)[(int64_t)j * nf + r] : (r == j ? 1.0 : 0.0);
+        };
+        // backward coefficient of output i and row r: Linv(r, i), or -W(r, i)
+        auto bwd_a = [&](int t, int r, int i) {
+            const int nf = fs.nf[t], ns = fs.ns[t];
+            if (r >= ns) return -front(t)[(int64_t)i * nf + r];
+            return r > i ? front(t)[(int64_t)i * nf + r] : (r == i ? 1.0 : 0.0);
+        };
         std::vector<double> acc(nrhs);
-        for (int h = 0; h <= fs.max_height; ++h)
-            for (int t : fs.by_height[h]) {
-                const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
-                const double *F = arena.data() + fs.foff[t];
+        // one front of the forward sweep: Y_s = Linv X_s, X_b -= W X_s (k_solve_fwd_inv)
+        auto fwd_front = [&](int t) {
+            const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+            for (int r = 0; r < nf; ++r) {
+                std::fill(acc.begin(), acc.end(), 0.0);
+                for (int j = 0; j < ns; ++j) {
+                    const double a = fwd_a(t, r, j);
+                    if (a != 0.0)
+                        for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)(ps + j) * nrhs + c];
+                }
+                if (r < ns) {
+                    for (int c = 0; c < nrhs; ++c) Y[(size_t)(ps + r) * nrhs + c] = acc[c];
+                } else {
+                    const int g = row(t, r);
+                    for (int c = 0; c < nrhs; ++c) Xi[(size_t)g * nrhs + c] -= acc[c];
+                }
+            }
+        };
+        // one front of the backward sweep: X_s = Linv^T D^-1 Y_s - W^T X_b (k_solve_bwd_inv)
+        auto bwd_front = [&](int t) {
+            const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+            for (int i = 0; i < ns; ++i) {
+                std::fill(acc.begin(), acc.end(), 0.0);
+                for (int r = i; r < nf; ++r) {
+                    const double a = bwd_a(t, r, i);
+                    if (r < ns) {
+                        const double di = dinv(t, r);
+                        for (int c = 0; c < nrhs; ++c) acc[c] += a * Y[(size_t)(ps + r) * nrhs + c] * di;
+                    } else {
+                        const int g = row(t, r);
+                        for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)g * nrhs + c];
+                    }
+                }
+                for (int c = 0; c < nrhs; ++c) Xi[(size_t)(ps + i) * nrhs + c] = acc[c];
+            }
+        };
+        // heights 0 and 1 fused as k_solve_fwd_fused / k_solve_bwd_fused order
+        // them: a parent's rows held apart (pivot values and ancestor deltas),
+        // D^-1 Y stored by the forward for these fronts
+        k::FusePlan Fp;
+        const bool fused = fused_h01 && fs.max_height >= 1;
+        if (fused) Fp = k::fuse_plan(fs.nf, fs.ns, fs.parent, fs.by_height[0], fs.by_height[1], k::kFuseSmemCap);
+        std::vector<double> Xp;
+        auto fwd_fused = [&](int i) {
+            const int pf = Fp.par[i], nfP = fs.nf[pf], nsP = fs.ns[pf], psP = fs.pstart[pf];
+            Xp.assign((size_t)nfP * nrhs, 0.0);
+            for (int r = 0; r < nsP; ++r)
+                for (int c = 0; c < nrhs; ++c) Xp[(size_t)r * nrhs + c] = Xi[(size_t)(psP + r) * nrhs + c];
+            for (int e = Fp.cptr[i]; e < Fp.cptr[i + 1]; ++e) {
+                const int t = Fp.cid[e], nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+                const int *rel = fs.relmap.data() + fs.relmap_off[t];
                 for (int r = 0; r < nf; ++r) {
                     std::fill(acc.begin(), acc.end(), 0.0);
                     for (int j = 0; j < ns; ++j) {
-                        const double a = (r >= ns || r > j) ? F[(int64_t)j * nf + r] : (r == j ? 1.0 : 0.0);
-                        if (a != 0.0)
-                            for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)(ps + j) * nrhs + c];
+                        const double a = fwd_a(t, r, j);
+                        for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)(ps + j) * nrhs + c];
                     }
                     if (r < ns) {
-                        for (int c = 0; c < nrhs; ++c) Y[(size_t)(ps + r) * nrhs + c] = acc[c];
+                        const double di = dinv(t, r);
+                        for (int c = 0; c < nrhs; ++c) Y[(size_t)(ps + r) * nrhs + c] = acc[c] * di;
                     } else {
-                        const int g = row(t, r);
-                        if (g < 0 || g >= n) fail(HSIM_E_INTERNAL, "front row outside the matrix");
-                        for (int c = 0; c < nrhs; ++c) Xi[(size_t)g * nrhs + c] -= acc[c];
+                        const int pr = rel[r - ns];
+                        if (pr < 0 || pr >= nfP) fail(HSIM_E_INTERNAL, "relmap outside the parent");
+                        const double sg = pr < nsP ? -1.0 : 1.0;  // a pivot value, or a delta
+                        for (int c = 0; c < nrhs; ++c) Xp[(size_t)pr * nrhs + c] += sg * acc[c];
                     }
                 }
             }
-        // backward per height: X_s = Linv^T D^-1 Y_s - W^T X_b (k_solve_bwd_inv)
-        for (int h = fs.max_height; h >= 0; --h)
-            for (int t : fs.by_height[h]) {
-                const int nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
-                const double *F = arena.data() + fs.foff[t];
-                for (int i = 0; i < ns; ++i) {
+            for (int r = 0; r < nfP; ++r) {
+                std::fill(acc.begin(), acc.end(), 0.0);
+                for (int j = 0; j < nsP; ++j) {
+                    const double a = fwd_a(pf, r, j);
+                    for (int c = 0; c < nrhs; ++c) acc[c] += a * Xp[(size_t)j * nrhs + c];
+                }
+                if (r < nsP) {
+                    const double di = dinv(pf, r);
+                    for (int c = 0; c < nrhs; ++c) Y[(size_t)(psP + r) * nrhs + c] = acc[c] * di;
+                } else {
+                    for (int c = 0; c < nrhs; ++c) Xp[(size_t)r * nrhs + c] += acc[c];
+                }
+            }
+            for (int r = nsP; r < nfP; ++r) {
+                const int g = row(pf, r);
+                for (int c = 0; c < nrhs; ++c) Xi[(size_t)g * nrhs + c] -= Xp[(size_t)r * nrhs + c];
+            }
+        };
+        auto bwd_fused = [&](int i) {
+            const int pf = Fp.par[i], nfP = fs.nf[pf], nsP = fs.ns[pf], psP = fs.pstart[pf];
+            Xp.assign((size_t)nfP * nrhs, 0.0);
+            for (int r = 0; r < nfP; ++r) {
+                const size_t src = r < nsP ? (size_t)(psP + r) : (size_t)row(pf, r);
+                const double *from = r < nsP ? Y.data() : Xi.data();
+                for (int c = 0; c < nrhs; ++c) Xp[(size_t)r * nrhs + c] = from[src * nrhs + c];
+            }
+            std::vector<double> out((size_t)nsP * nrhs, 0.0);
+            for (int o = 0; o < nsP; ++o)
+                for (int r = o; r < nfP; ++r) {
+                    const double a = bwd_a(pf, r, o);
+                    for (int c = 0; c < nrhs; ++c) out[(size_t)o * nrhs + c] += a * Xp[(size_t)r * nrhs + c];
+                }
+            for (int o = 0; o < nsP; ++o)
+                for (int c = 0; c < nrhs; ++c) {
+                    Xp[(size_t)o * nrhs + c] = out[(size_t)o * nrhs + c];
+                    Xi[(size_t)(psP + o) * nrhs + c] = out[(size_t)o * nrhs + c];
+                }
+            for (int e = Fp.cptr[i]; e < Fp.cptr[i + 1]; ++e) {
+                const int t = Fp.cid[e], nf = fs.nf[t], ns = fs.ns[t], ps = fs.pstart[t];
+                const int *rel = fs.relmap.data() + fs.relmap_off[t];
+                for (int o = 0; o < ns; ++o) {
                     std::fill(acc.begin(), acc.end(), 0.0);
-                    for (int r = i; r < nf; ++r) {
-                        if (r < ns) {
-                            const double a = r > i ? F[(int64_t)i * nf + r] : 1.0;
-                            const double dinv = 1.0 / F[(int64_t)r * nf + r];
-                            for (int c = 0; c < nrhs; ++c) acc[c] += a * Y[(size_t)(ps + r) * nrhs + c] * dinv;
-                        } else {
-                            const double a = -F[(int64_t)i * nf + r];
-                            const int g = row(t, r);
-                            for (int c = 0; c < nrhs; ++c) acc[c] += a * Xi[(size_t)g * nrhs + c];
-                        }
+                    for (int r = o; r < nf; ++r) {
+                        const double a = bwd_a(t, r, o);
+                        const double *b = r < ns ? &Y[(size_t)(ps + r) * nrhs] : &Xp[(size_t)rel[r - ns] * nrhs];
+                        for (int c = 0; c < nrhs; ++c) acc[c] += a * b[c];
                     }
-                    for (int c = 0; c < nrhs; ++c) Xi[(size_t)(ps + i) * nrhs + c] = acc[c];
+                    for (int c = 0; c < nrhs; ++c) Xi[(size_t)(ps + o) * nrhs + c] = acc[c];
                 }
             }
+        };
+        for (int h = 0; h <= fs.max_height; ++h) {
+            if (fused && h == 0) {
+                for (int t : Fp.rest0) fwd_front(t);
+                for (size_t i = 0; i < Fp.par.size(); ++i) fwd_fused((int)i);
+            } else if (fused && h == 1) {
+                for (int t : Fp.rest1) fwd_front(t);
+            } else {
+                for (int t : fs.by_height[h]) fwd_front(t);
+            }
+        }
+        for (int h = fs.max_height; h >= 0; --h) {
+            if (fused && h == 1) {
+                for (int t : Fp.rest1) bwd_front(t);
+                for (size_t i = 0; i < Fp.par.size(); ++i) bwd_fused((int)i);
+            } else if (fused && h == 0) {
+                for (int t : Fp.rest0) bwd_front(t);
+            } else {
+                for (int t : fs.by_height[h]) bwd_front(t);
+            }
+        }
+        if (fused_counts) {
+            fused_counts[0] = fused ? (int)Fp.par.size() : 0;
+            fused_counts[1] = fused ? (int)Fp.rest0.size() : 0;
+            fused_counts[2] = fused ? (int)Fp.rest1.size() : 0;
+        }
         for (int pos = 0; pos < n; ++pos)
             std::memcpy(&X[(size_t)fs.perm[pos] * nrhs], &Xi[(size_t)pos * nrhs], nrhs * sizeof(double));
         if (neg_pivots) *neg_pivots = neg;

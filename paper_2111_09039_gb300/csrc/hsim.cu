@@ -235,10 +235,9 @@ bool tc32_enabled() {
 }
 // FP32 solves: each front of height 1 with its leaves in one CTA per column
 // tile (k::solve_fwd_fused / solve_bwd_fused), for parents whose CTA needs at
-// most kFuseSmemCap bytes of shared memory (three CTAs per SM); the others
+// most k::kFuseSmemCap bytes of shared memory (three CTAs per SM); the others
 // per height.  HSIM_FUSE=0 solves every height separately (for comparison;
 // read at every solve).
-constexpr size_t kFuseSmemCap = 74 * 1024;
 bool fuse_enabled() {
     const char *e = std::getenv("HSIM_FUSE");
     return !(e && *e == '0');
@@ -253,59 +252,29 @@ int number_tiles(std::vector<k::GemmTask> &tasks, int tile) {
     return nt;
 }
 
-// Heights 0 and 1 of the FP32 solves: every front of height 1 within the
-// fused kernels' limits (pivots, ancestor rows, children) whose CTA, sized
-// for the largest front and rows of the launch, fits kFuseSmemCap is solved
-// with its children (all leaves) in one CTA; the rest per height.  Not
-// planned when either height reaches the tensor-core forward products.
+// Heights 0 and 1 of the FP32 solves: the fronts of height 1 of k::fuse_plan
+// solved with their children (all leaves) in one CTA, the rest per height.
+// Not planned when either height reaches the tensor-core forward products.
 void build_fuse_plan(LevelData &L, cudaStream_t s) {
     const FrontSymbolic &fs = L.fs;
     L.fuse_n = L.fuse_n0 = L.fuse_n1 = L.fuse_rows = L.fuse_front = 0;
     if (fs.max_height < 1 || L.h_maxns[0] >= kTcMinFwdPivots || L.h_maxns[1] >= kTcMinFwdPivots) return;
-    std::vector<int> slot(fs.n_nodes, -1);
-    const auto &h1 = fs.by_height[1];
-    for (size_t i = 0; i < h1.size(); ++i) slot[h1[i]] = (int)i;
-    std::vector<std::vector<int>> kids(h1.size());
-    for (int t : fs.by_height[0])
-        if (fs.parent[t] >= 0 && slot[fs.parent[t]] >= 0) kids[slot[fs.parent[t]]].push_back(t);
-    std::vector<char> fused(h1.size(), 0);
-    std::vector<int> par, cptr{0}, cid, rest0, rest1;
-    for (size_t i = 0; i < h1.size(); ++i) {
-        const int P = h1[i];
-        int rows = fs.nf[P], front = k::fused_front_size(fs.nf[P], fs.ns[P]);
-        for (int c : kids[i]) {
-            rows += fs.ns[c];
-            front = std::max(front, k::fused_front_size(fs.nf[c], fs.ns[c]));
-        }
-        // one launch: the largest rows and block over the fused parents size every CTA
-        if (fs.ns[P] > k::fused_max_pivots() || fs.nf[P] - fs.ns[P] > k::fused_max_ancestors() ||
-            (int)kids[i].size() > k::fused_max_children() ||
-            k::fused_smem(std::max(rows, L.fuse_rows), std::max(front, L.fuse_front)) > kFuseSmemCap) {
-            rest1.push_back(P);
-            continue;
-        }
-        fused[i] = 1;
-        par.push_back(P);
-        cid.insert(cid.end(), kids[i].begin(), kids[i].end());
-        cptr.push_back((int)cid.size());
-        L.fuse_rows = std::max(L.fuse_rows, rows);
-        L.fuse_front = std::max(L.fuse_front, front);
-    }
-    for (int t : fs.by_height[0])
-        if (!(fs.parent[t] >= 0 && slot[fs.parent[t]] >= 0 && fused[slot[fs.parent[t]]])) rest0.push_back(t);
-    if (par.empty()) return;
-    L.fuse_n = (int)par.size();
-    L.fuse_n0 = (int)rest0.size();
-    L.fuse_n1 = (int)rest1.size();
+    k::FusePlan F = k::fuse_plan(fs.nf, fs.ns, fs.parent, fs.by_height[0], fs.by_height[1], k::kFuseSmemCap);
+    if (F.par.empty()) return;
+    L.fuse_n = (int)F.par.size();
+    L.fuse_n0 = (int)F.rest0.size();
+    L.fuse_n1 = (int)F.rest1.size();
+    L.fuse_rows = F.rows;
+    L.fuse_front = F.front;
     auto nz = [](std::vector<int> &v) -> std::vector<int> & {
         if (v.empty()) v.push_back(0);
         return v;
     };
-    L.fuse_par.upload(par, s);
-    L.fuse_cptr.upload(cptr, s);
-    L.fuse_cid.upload(nz(cid), s);
-    L.fuse_rest0.upload(nz(rest0), s);
-    L.fuse_rest1.upload(nz(rest1), s);
+    L.fuse_par.upload(F.par, s);
+    L.fuse_cptr.upload(F.cptr, s);
+    L.fuse_cid.upload(nz(F.cid), s);
+    L.fuse_rest0.upload(nz(F.rest0), s);
+    L.fuse_rest1.upload(nz(F.rest1), s);
     HSIM_CUDA(cudaStreamSynchronize(s));  // the uploads read the host vectors
 }
 

@@ -1047,6 +1047,41 @@ int fused_max_ancestors() { return kFuseMaxAnc; }
 int fused_max_children() { return kFuseMaxKids; }
 int fused_front_size(int nf, int ns) { return fuse_block(nf, ns) + pad4(nf - ns) + pad4(ns); }
 
+FusePlan fuse_plan(const std::vector<int> &nf, const std::vector<int> &ns, const std::vector<int> &parent,
+                   const std::vector<int> &h0, const std::vector<int> &h1, size_t smem_cap) {
+    FusePlan F;
+    F.cptr.push_back(0);
+    std::vector<int> slot(nf.size(), -1);
+    for (size_t i = 0; i < h1.size(); ++i) slot[h1[i]] = (int)i;
+    std::vector<std::vector<int>> kids(h1.size());
+    for (int t : h0)
+        if (parent[t] >= 0 && slot[parent[t]] >= 0) kids[slot[parent[t]]].push_back(t);
+    std::vector<char> fused(h1.size(), 0);
+    for (size_t i = 0; i < h1.size(); ++i) {
+        const int P = h1[i];
+        int rows = nf[P], front = fused_front_size(nf[P], ns[P]);
+        for (int c : kids[i]) {
+            rows += ns[c];
+            front = std::max(front, fused_front_size(nf[c], ns[c]));
+        }
+        // one launch: the largest rows and block over the fused parents size every CTA
+        if (ns[P] > kFuseMaxPiv || nf[P] - ns[P] > kFuseMaxAnc || (int)kids[i].size() > kFuseMaxKids ||
+            fused_smem(std::max(rows, F.rows), std::max(front, F.front)) > smem_cap) {
+            F.rest1.push_back(P);
+            continue;
+        }
+        fused[i] = 1;
+        F.par.push_back(P);
+        F.cid.insert(F.cid.end(), kids[i].begin(), kids[i].end());
+        F.cptr.push_back((int)F.cid.size());
+        F.rows = std::max(F.rows, rows);
+        F.front = std::max(F.front, front);
+    }
+    for (int t : h0)
+        if (!(parent[t] >= 0 && slot[parent[t]] >= 0 && fused[slot[parent[t]]])) F.rest0.push_back(t);
+    return F;
+}
+
 void solve_fwd_fused(cudaStream_t s, const FrontDev &fd, const int *parents, int n_parents, const int *child_ptr,
                      const int *child_ids, int max_rows, int max_front, const float *arena, const float *dinv, int k,
                      float *X, float *Y, int ldx) {

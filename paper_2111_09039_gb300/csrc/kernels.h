@@ -217,6 +217,20 @@ InversePlan inverse_plan(const std::vector<int> &nf, const std::vector<int> &ns,
 // fused_max_children() children.  The results of solve_fwd_inv /
 // solve_bwd_inv on heights 0 and 1 of those fronts, summed in another order.
 constexpr size_t kFusedSmemMax = 160 * 1024;
+// Shared memory of one fused CTA at most: three CTAs per SM
+constexpr size_t kFuseSmemCap = 74 * 1024;
+// The fused launches' plan (host): the fronts of height 1 within the fused
+// kernels' limits (pivots, ancestor rows, children) whose CTA, sized for the
+// largest front and rows of the launch, fits smem_cap (par, with children
+// cid[cptr[i] .. cptr[i + 1]) in the order of h0), then the leaves (rest0)
+// and fronts of height 1 (rest1) left to the per-height kernels; rows and
+// front size the launch (max_rows and max_front of solve_fwd_fused).
+struct FusePlan {
+    std::vector<int> par, cptr, cid, rest0, rest1;
+    int rows = 0, front = 0;
+};
+FusePlan fuse_plan(const std::vector<int> &nf, const std::vector<int> &ns, const std::vector<int> &parent,
+                   const std::vector<int> &h0, const std::vector<int> &h1, size_t smem_cap);
 size_t fused_smem(int max_rows, int max_front);
 int fused_max_pivots();
 int fused_max_ancestors();

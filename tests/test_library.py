@@ -157,6 +157,42 @@ def test_inverted_replay_galerkin_level_and_forest(hs):
     assert np.abs(X2 - Xr2).max() <= 1e-9 * np.abs(Xr2).max()
 
 
+@pytest.mark.parametrize("leaf,mu", [(4, -5.0), (16, 300.0), (32, -50.0), (64, 300.0)])
+def test_fused_replay_solves_level0(hs, leaf, mu):
+    # heights 0 and 1 in the order of the fused launches (each planned front of
+    # height 1 with its leaves, its rows held apart, D^-1 Y stored by the
+    # forward): the same solution as the per-height replay and SciPy; the plan
+    # leaves some leaves (under higher fronts) and, with leaves of 64, fronts
+    # beyond the kernels' limits to the per-height products
+    mesh = synth.bumpy_torus(40, 36, 2)
+    S, M, K = _shifted(mesh, mu)
+    B = np.random.default_rng(leaf).standard_normal((mesh.n, 3))
+    X, neg, _, counts = hs.check_symbolic(K.indptr, K.indices, K.data, B, leaf, inverted=True, fused=True)
+    X0, neg0, _ = hs.check_symbolic(K.indptr, K.indices, K.data, B, leaf, inverted=True)
+    Xr = spla.spsolve(K.tocsc(), B)
+    assert np.abs(X - Xr).max() <= 1e-8 * np.abs(Xr).max()
+    assert np.abs(X - X0).max() <= 1e-10 * np.abs(X0).max()
+    assert neg == neg0
+    fused, rest0, rest1 = counts
+    assert fused > 0 and rest0 > 0
+    if leaf == 64:
+        assert rest1 > 0
+
+
+def test_fused_replay_forest_and_open_patch(hs):
+    # two disjoint tori (a forest of two elimination trees) and an open patch
+    a = synth.bumpy_torus(12, 10, 1)
+    b = synth.bumpy_torus(9, 11, 2)
+    m2 = synth.Mesh(V=np.concatenate([a.V, b.V + 5.0]), F=np.concatenate([a.F, b.F + a.n]))
+    for mesh, leaf in ((m2, 8), (synth.bumpy_patch(90, 70, 8), 32)):
+        S, M, K = _shifted(mesh, -5.0)
+        B = np.random.default_rng(2).standard_normal((mesh.n, 2))
+        X, _, _, counts = hs.check_symbolic(K.indptr, K.indices, K.data, B, leaf, inverted=True, fused=True)
+        Xr = spla.spsolve(K.tocsc(), B)
+        assert np.abs(X - Xr).max() <= 1e-9 * np.abs(Xr).max()
+        assert counts[0] > 0
+
+
 # ---- hierarchy construction (host code of hsim_build_hierarchy) -------------
 @pytest.mark.parametrize("name", ["bumpy_torus_64", "flat_torus_64", "icosphere3_noise", "open_patch",
                                   "two_tori", "narrow_support", "short_edge"])
